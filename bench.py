@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: rigid-body force/torque evaluation, bead sum vs pair network.
+
+Workload: 32768 cubes (5x5x5 beads, LJ eps = sigma = 1, r_c = 2.5), packing
+fraction 0.20, seeded lattice placement, random orientations, Maxwell
+velocities at kT = 1, NVE velocity Verlet at dt = 0.002.
+
+One bench step = one full MD step (integrate, cell list, pair list, pair
+force/torque evaluation, per-body reduction and half kick) of the same system
+on each force path: the bead double sum (FP32) and the pair network (FP32
+SIMT; BF16 tensor cores where built).  `value` = body-pair force+torque
+evaluations per second over both paths.  Per-path MD steps/s are reported in
+`paths`.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+system stream; a 256 MiB buffer is written between steps (outside the events)
+so that every step starts with a cold L2.  `--impl reference` times the FP64
+CPU oracle on a bounded sample of the same body pairs instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair force+torque evals/s & MD steps/s, NN vs bead-sum on GB300 at fixed error"
+UNIT = "pair evals/s"
+N_BODIES, PHI, SEED, KT, DT = 32768, 0.20, 3, 1.0, 0.002
+WIDTH, DEPTH = 128, 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--paths", default="beads,nn_fp32")
+    ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
+    ap.add_argument("--ref-sample-pairs", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(rank=0):
+    from paper_2402_12199_gb300 import inputs
+
+    # cube: 125 beads of unit mass, principal moments 500 (5x5x5 lattice at 1 sigma)
+    st, L = inputs.system_state(N_BODIES, PHI, KT, SEED + 1000 * rank, 125.0, [500.0] * 3, "cube")
+    mu, isd = inputs.feature_normalisation(5.0, 4 * math.sqrt(3) + 2.5)
+    flat = inputs.mlp_params(WIDTH, DEPTH, 5, mu=mu, inv_sd=isd)
+    return st, L, flat
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def bead_flops_per_pair(n_beads: int) -> float:
+    # every bead-pair distance: 3 subtractions + 1 multiply + 2 FMA = 8 flops
+    return 8.0 * n_beads * n_beads
+
+
+def nn_flops_per_pair(width: int, depth: int) -> float:
+    # forward GEMMs (10 -> w, (depth-1) x w -> w, w -> 1) and the same again backward
+    fwd = 2 * (10 * width + (depth - 1) * width * width + width)
+    return 2.0 * fwd
+
+
+_PAIR_CACHE = {}
+
+
+def cpu_baseline(st, L, flat, n_sample):
+    """FP64 oracle (single thread) on a bounded sample of the workload's pairs."""
+    import oracle
+    from oracle import bodies, nn
+
+    tmpl = bodies.cube_template()
+    pos = st["pos"][:, :3].astype(np.float64)
+    quat = st["quat"].astype(np.float64)
+    box = np.array([L] * 3)
+    Rc = bodies.pair_cutoff(tmpl)
+    key = (id(st), n_sample)
+    if key not in _PAIR_CACHE:
+        allp = oracle.pairs_bruteforce(pos, box, Rc)
+        rng = np.random.default_rng(0)
+        _PAIR_CACHE[key] = allp[np.sort(rng.choice(len(allp), min(n_sample, len(allp)),
+                                                   replace=False))]
+    pairs = _PAIR_CACHE[key]
+    t0 = time.perf_counter()
+    oracle.forces_beads(pos, quat, box, tmpl, pairs)
+    t_bead = time.perf_counter() - t0
+    import torch
+
+    torch.set_num_threads(1)
+    p = nn.unpack(np.asarray(flat, np.float64), WIDTH, DEPTH)
+    t0 = time.perf_counter()
+    nn.forces_nn(p, pos, quat, box, pairs)
+    t_nn = time.perf_counter() - t0
+    return {"bead_pairs_per_s": len(pairs) / t_bead, "nn_pairs_per_s": len(pairs) / t_nn,
+            "pairs": int(len(pairs)), "t_bead_s": t_bead, "t_nn_s": t_nn}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    st, L, flat = make_inputs(0)
+    res = []
+    for _ in range(args.warmup):
+        cpu_baseline(st, L, flat, args.ref_sample_pairs)
+    for _ in range(args.steps):
+        r = cpu_baseline(st, L, flat, args.ref_sample_pairs)
+        res.append(r)
+    pairs = sum(2 * r["pairs"] for r in res)
+    t = sum(r["t_bead_s"] + r["t_nn_s"] for r in res)
+    v = pairs / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{N_BODIES} cubes (125 beads), phi={PHI}, LJ rc=2.5, "
+                                   f"MLP 10-{WIDTH}x{DEPTH}-1 SiLU; each step a sample of "
+                                   f"{args.ref_sample_pairs} body pairs per path"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.ref_sample_pairs} body pairs x 2 paths per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2402_12199_gb300 import api
+
+    paths = [p for p in args.paths.split(",") if p]
+    st, L, flat = make_inputs(rank)
+    dev_state = {k: torch.from_numpy(st[k]).cuda() for k in ("pos", "quat", "vel", "angmom")}
+    mlp = api.MLP(WIDTH, DEPTH)
+    mlp.set_params(flat)
+    stream = torch.cuda.current_stream()
+    systems = {}
+    for p in paths:
+        s = api.System(N_BODIES, [L] * 3, "cube")
+        s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+        systems[p] = s
+
+    def pcfg(p):
+        if p == "beads":
+            return dict(path=api.RB_PATH_BEADS)
+        return dict(path=api.RB_PATH_NN, mlp=mlp, precision=p.split("_")[1])
+
+    # initial forces and pair counts
+    n_pairs = {}
+    for p, s in systems.items():
+        if p == "beads":
+            s.forces_beads()
+        else:
+            s.forces_nn(mlp, pcfg(p)["precision"])
+        n_pairs[p] = s.build_pairs()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(events):
+        for p, s in systems.items():
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(1, DT, **pcfg(p))
+            e1.record(stream)
+            events[p].append((e0, e1))
+
+    warm = {p: [] for p in paths}
+    for _ in range(args.warmup):
+        one_step(warm)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = {p: [] for p in paths}
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(ev)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    for s in systems.values():
+        s.sync()
+    per_path_ms = {p: [a.elapsed_time(b) for a, b in ev[p]] for p in paths}
+    ms_step = sum(statistics.mean(v) for v in per_path_ms.values())
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    pairs_per_step = sum(n_pairs.values())
+    value = world * pairs_per_step / (ms_step * 1e-3)
+
+    # ---- dominant kernel: the bead-sum pair kernel, timed alone with events
+    roof = None
+    pk, how = peaks()
+    props = torch.cuda.get_device_properties(local)
+    if "beads" in systems:
+        s = systems["beads"]
+        s.build_pairs()
+        for _ in range(3):
+            s.eval_pairs(api.RB_PATH_BEADS)
+        durs = []
+        for _ in range(10):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.eval_pairs(api.RB_PATH_BEADS)
+            b.record(stream)
+            durs.append((a, b))
+        torch.cuda.synchronize()
+        d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
+        flops = bead_flops_per_pair(125) * n_pairs["beads"]
+        achieved = flops / (d_ms * 1e-3) / 1e12
+        peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
+        roof = {"kernel": "k_bead_pairs", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel_ms": d_ms, "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
+                "flops_per_launch": flops}
+
+    # ---- end to end through the public API with host buffers
+    pinned = {k: torch.from_numpy(st[k]).pin_memory() for k in ("pos", "quat", "vel", "angmom")}
+    outs = {k: torch.empty((N_BODIES, 4), dtype=torch.float32).pin_memory()
+            for k in ("pos", "quat", "vel", "angmom")}
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for p, s in systems.items():
+            s.set_state(*(pinned[k] for k in ("pos", "quat", "vel", "angmom")))
+            s.step(1, DT, **pcfg(p))
+            s.get_state(to_host=True)
+            s.energy()
+    torch.cuda.synchronize()
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+    h2d = len(systems) * 4 * N_BODIES * 16
+    d2h = len(systems) * (4 * N_BODIES * 16 + 3 * 8)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(st, L, flat, args.cpu_sample_pairs)
+        v = 2 * cb["pairs"] / (cb["t_bead_s"] + cb["t_nn_s"])
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{cb['pairs']} body pairs of the workload, bead sum and network "
+                         f"(FP64, single thread)", "bead_pairs_per_s": cb["bead_pairs_per_s"],
+               "nn_pairs_per_s": cb["nn_pairs_per_s"]}
+
+    clocks = clk.summary()
+    path_info = {}
+    for p in paths:
+        ms = statistics.mean(per_path_ms[p])
+        path_info[p] = {"ms_per_md_step": ms, "md_steps_per_s": 1e3 / ms,
+                        "pair_evals_per_s": n_pairs[p] / (ms * 1e-3), "pairs": n_pairs[p]}
+    if "beads" in path_info:
+        for p in paths:
+            if p != "beads":
+                path_info[p]["speedup_vs_beads"] = path_info["beads"]["ms_per_md_step"] / path_info[p]["ms_per_md_step"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{N_BODIES} cubes (5x5x5 beads, LJ eps=sigma=1 rc=2.5), "
+                                   f"phi={PHI}, NVE dt={DT}; one MD step per force path "
+                                   f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU random init",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "256 MiB buffer written between steps, outside the per-step events"},
+            "paths": path_info, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * pairs_per_step / e2e_t, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * 7 * len(paths), "clocks": clocks,
+            "peaks_source": how, "wall_s": wall}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * rb.h -- C ABI of the GB300 force/torque library for composite rigid bodies.
+ *
+ * The library evaluates the interaction between rigid anisotropic bodies made
+ * of beads in the two forms of arxiv 2402.12199 (Argun, Fu, Statt):
+ *   - the bead double sum U = sum_i sum_j u_bead(r_ij) over the beads of each
+ *     neighbouring body pair (paper, Methods, first equation), reduced to
+ *     per-body forces and torques;
+ *   - a pair network U ~ g_NN_U(x, Omega) of the centre-of-mass separation in
+ *     the frame of the first body and the relative orientation (paper,
+ *     Methods, "U = g(x, Omega)"), with forces and torques as gradients of that
+ *     energy (SI Sec. 6, f = -dE/dx, tau = -dE/dtheta);
+ * and integrates rigid-body molecular dynamics with either (paper, Results).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an rb_status; rb_last_error() gives a thread-local
+ *     message for the last failure.  No C++ exception crosses the ABI.
+ *   - Array arguments are DEVICE pointers owned by the caller unless the
+ *     argument name ends in _host or a from_host/to_host flag says otherwise.
+ *     Device arrays must be 16-byte aligned and contiguous.
+ *   - "float4 rows" means n x 4 floats.  Body state rows:
+ *       pos    (x, y, z, unused)          space frame, wrapped into [0, L)
+ *       quat   (s, i, j, k)                unit quaternion, body -> space,
+ *                                          active rotation v' = q v q^*
+ *       vel    (vx, vy, vz, unused)
+ *       angmom (Lx, Ly, Lz, unused)        angular momentum in the BODY frame
+ *     Force rows (Fx, Fy, Fz, e) with e = half the energy of the body's pairs;
+ *     torque rows (tx, ty, tz, 0); both in the space frame.
+ *   - Work is enqueued on the CUDA stream given at creation (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream) and is asynchronous,
+ *     except where an output ends in _host, which synchronises that stream.
+ *   - Objects returned through an out-pointer are owned by the library until
+ *     the matching destroy call.
+ */
+#ifndef RB_H
+#define RB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rb_status {
+    RB_OK = 0,
+    RB_EINVAL = 1,     /* bad argument: null pointer, size, shape, box too small */
+    RB_ENOMEM = 2,     /* device or host allocation failed */
+    RB_ECUDA = 3,      /* a CUDA call failed (message has the CUDA error string) */
+    RB_EOVERFLOW = 4,  /* a neighbour or cell capacity was exceeded; results invalid */
+    RB_ENOT_READY = 5, /* serving: the request is still running */
+    RB_ETIMEOUT = 6,   /* serving: rb_wait gave up */
+    RB_EFAULT = 7,     /* non-finite forces or energies detected */
+    RB_EBUSY = 8,      /* serving: no slot or memory for the request now */
+    RB_ENOTSUP = 9     /* combination not supported by this build */
+} rb_status;
+
+enum { RB_SHAPE_CUBE = 0, RB_SHAPE_CYLINDER = 1, RB_SHAPE_CUSTOM = 2 };
+enum { RB_POT_LJ = 0 };
+enum { RB_PATH_BEADS = 0, RB_PATH_NN = 1 };
+enum { RB_FP32 = 0, RB_BF16 = 1 };
+
+/* Thread-local message describing the most recent failure on this thread. */
+const char* rb_last_error(void);
+/* Version of this ABI (incremented on incompatible changes). */
+int32_t rb_abi_version(void);
+
+/* ------------------------------------------------------------------ system */
+
+typedef struct rb_system rb_system;
+
+/* Composite body (paper, Methods: a body is a rigid set of beads).
+ *   RB_SHAPE_CUBE:     5 x 5 x 5 simple-cubic beads at 1 sigma (125 beads)
+ *   RB_SHAPE_CYLINDER: 8 layers of 19 hexagonally packed beads, radius 2
+ *                      sigma, bead-centre length 8 sigma (152 beads)
+ *   RB_SHAPE_CUSTOM:   n_beads body-frame positions in bead_xyz_host (n x 3,
+ *                      copied), centred on the centre of mass, principal axes
+ *                      along x, y, z (off-diagonal inertia must vanish).
+ * At most 256 beads. */
+typedef struct rb_body_type {
+    int32_t shape;
+    int32_t n_beads;
+    const float* bead_xyz_host;
+    float bead_mass;
+} rb_body_type;
+
+/* Bead-bead potential.  RB_POT_LJ: 4 eps ((sigma/r)^12 - (sigma/r)^6) for
+ * r < rcut, shifted to zero energy at rcut (force not shifted). */
+typedef struct rb_bead_potential {
+    int32_t kind;
+    float eps;
+    float sigma;
+    float rcut;
+} rb_bead_potential;
+
+typedef struct rb_system_desc {
+    rb_body_type body;
+    rb_bead_potential pot;
+    float box[3];          /* orthorhombic periodic box; each side >= 2 Rc */
+    int64_t n_bodies;      /* N >= 1 */
+    int32_t max_neighbors; /* per-body cap of body neighbours within Rc (0: 64) */
+} rb_system_desc;
+
+/* Create a system with device storage for N bodies on `cuda_stream`.  The
+ * body-pair cutoff is Rc = 2 r_circ + rcut (r_circ = largest bead-centre
+ * distance from the centre of mass), an exact superset of interacting pairs. */
+rb_status rb_create_system(const rb_system_desc* desc, void* cuda_stream, rb_system** out);
+rb_status rb_destroy_system(rb_system* sys);
+
+/* Body properties: total mass, principal moments of inertia, circumradius,
+ * body-pair cutoff Rc and number of beads (any output may be NULL). */
+rb_status rb_body_info(const rb_system* sys, float* mass_host, float* inertia3_host,
+                       float* r_circ_host, float* pair_cutoff_host, int32_t* n_beads_host);
+/* Body-frame bead positions (n_beads x 3) as used by the kernels. */
+rb_status rb_body_template(const rb_system* sys, float* xyz_host);
+
+/* Copy the state in (float4 rows, see above).  from_host != 0: the pointers
+ * are host memory.  Invalidates cached forces. */
+rb_status rb_set_state(rb_system* sys, const float* pos, const float* quat, const float* vel,
+                       const float* angmom, int32_t from_host);
+/* Copy the state out; any pointer may be NULL. */
+rb_status rb_get_state(const rb_system* sys, float* pos, float* quat, float* vel, float* angmom,
+                       int32_t to_host);
+/* Copy out the forces/torques of the last evaluation (float4 rows). */
+rb_status rb_get_forces(const rb_system* sys, float* force, float* torque, int32_t to_host);
+
+/* Build the cell list and the body-pair list for the current positions:
+ * all unordered pairs i < j with minimum-image |p_j - p_i| < Rc.  If
+ * n_pairs_host is not NULL the stream is synchronised and the count (or an
+ * RB_EOVERFLOW) returned. */
+rb_status rb_build_pairs(rb_system* sys, int64_t* n_pairs_host);
+/* Copy the current pair list (i, j) as int32 pairs into pairs_host (capacity
+ * `cap` pairs, row-major (i, j)); sets *n_pairs_host.  Synchronises. */
+rb_status rb_get_pairs(const rb_system* sys, int32_t* pairs_host, int64_t cap,
+                       int64_t* n_pairs_host);
+
+/* Bead-sum forces and torques (paper, Methods: U = sum_i sum_j u_bead(r_ij)):
+ * rebuilds the pair list, evaluates every listed body pair's full bead double
+ * sum and reduces per body.  force/torque: device float4 rows (N x 4), may be
+ * NULL to keep them only inside the system.  energy_host: total potential
+ * energy (FP64); virial9_host: centre-of-mass virial sum R_ij (x) F_j (FP64,
+ * row-major 3x3); both nullable, and either synchronises the stream. */
+rb_status rb_forces_beads(rb_system* sys, float* force, float* torque, double* energy_host,
+                          double* virial9_host);
+
+/* Evaluate the per-pair results of `path` on the CURRENT pair list only (no
+ * pair-list rebuild, no per-body reduction): one launch of the pair kernel.
+ * Used to time the pair kernels in isolation.  Asynchronous. */
+typedef struct rb_mlp rb_mlp;
+rb_status rb_eval_pairs(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision);
+
+/* Integrate n_steps of NVE velocity Verlet (NO_SQUISH free-rotor split for
+ * the orientation) with forces from `path` (RB_PATH_BEADS, or RB_PATH_NN with
+ * `mlp` at `precision`).  Each step is one CUDA-graph launch; asynchronous. */
+rb_status rb_step(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
+                  int64_t n_steps, float dt);
+
+/* FP64 potential, translational and rotational kinetic energy of the current
+ * state (forces of the last evaluation).  Synchronises. */
+rb_status rb_energy(rb_system* sys, double* e_pot_host, double* ke_trans_host,
+                    double* ke_rot_host);
+
+/* Wait for the system's stream and report any sticky device-side error
+ * (capacity overflow, non-finite values). */
+rb_status rb_sync(rb_system* sys);
+
+/* ------------------------------------------------------------------ network */
+
+/* Pair energy network (paper, Methods and SI Sec. 1: fully connected
+ * feed-forward; the workload's form: 10 inputs, `depth` hidden SiLU layers of
+ * `width`, scalar energy).  Inputs x = [s (3), q_rel (4), rho, 1/rho, rho^2]
+ * with s = R(q_i)^T (p_j - p_i), q_rel = q_i^* (x) q_j made canonical with a
+ * non-negative scalar part, rho = |s|; x_hat = (x - mu) * inv_sd;
+ * E = e_scale (w_o . h_depth + b_o) + e_shift.
+ * Flat FP32 parameter layout: mu[10], inv_sd[10], W1[width x 10], b1[width],
+ * then (W_l[width x width], b_l[width]) for l = 2..depth, w_o[width], b_o,
+ * e_scale, e_shift (row-major W[out][in]). */
+int64_t rb_mlp_n_params(int32_t width, int32_t depth);
+rb_status rb_mlp_create(int32_t width, int32_t depth, void* cuda_stream, rb_mlp** out);
+rb_status rb_mlp_destroy(rb_mlp* mlp);
+rb_status rb_mlp_set_params(rb_mlp* mlp, const float* flat, int64_t n, int32_t from_host);
+rb_status rb_mlp_get_params(const rb_mlp* mlp, float* flat, int64_t n, int32_t to_host);
+
+/* Network forces and torques for the whole system (same outputs and pair
+ * list as rb_forces_beads).  Each unordered pair i < j is evaluated once with
+ * i as the reference body.  RB_FP32: SIMT FP32 arithmetic; RB_BF16: BF16
+ * tensor-core GEMMs with FP32 accumulation. */
+rb_status rb_forces_nn(rb_system* sys, const rb_mlp* mlp, int32_t precision, float* force,
+                       float* torque, double* energy_host, double* virial9_host);
+
+/* Network on explicit pair configurations in the frame of body i (q_i = 1):
+ * cfg: n x 8 floats (s_x, s_y, s_z, 0, q_s, q_i, q_j, q_k).  out: n x 12 floats
+ * (F_j xyz, E, tau_i xyz, 0, tau_j xyz, 0) in the frame of body i.  If
+ * grad_out is not NULL it receives n x 8 floats (dE/ds xyz, 0, dE/dq wxyz) of
+ * the raw (non-canonical) q_rel.  Runs on the mlp's stream. */
+rb_status rb_nn_pairs(const rb_mlp* mlp, int32_t precision, int64_t n, const float* cfg,
+                      float* out, float* grad_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RB_H */

@@ -1,0 +1,104 @@
+"""ctypes loader for the in-tree CUDA library (librb.so) and its C ABI.
+
+Argument marshalling only.  The library must have been built (see
+``build_lib.build``); there is no fallback: a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "_build", "librb.so")
+
+STATUS = {0: "RB_OK", 1: "RB_EINVAL", 2: "RB_ENOMEM", 3: "RB_ECUDA", 4: "RB_EOVERFLOW",
+          5: "RB_ENOT_READY", 6: "RB_ETIMEOUT", 7: "RB_EFAULT", 8: "RB_EBUSY", 9: "RB_ENOTSUP"}
+RB_OK, RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_EOVERFLOW = 0, 1, 2, 3, 4
+RB_ENOT_READY, RB_ETIMEOUT, RB_EFAULT, RB_EBUSY, RB_ENOTSUP = 5, 6, 7, 8, 9
+RB_SHAPE_CUBE, RB_SHAPE_CYLINDER, RB_SHAPE_CUSTOM = 0, 1, 2
+RB_POT_LJ = 0
+RB_PATH_BEADS, RB_PATH_NN = 0, 1
+RB_FP32, RB_BF16 = 0, 1
+
+
+class RBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class rb_body_type(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("n_beads", ctypes.c_int32),
+                ("bead_xyz_host", ctypes.POINTER(ctypes.c_float)), ("bead_mass", ctypes.c_float)]
+
+
+class rb_bead_potential(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("eps", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("rcut", ctypes.c_float)]
+
+
+class rb_system_desc(ctypes.Structure):
+    _fields_ = [("body", rb_body_type), ("pot", rb_bead_potential), ("box", ctypes.c_float * 3),
+                ("n_bodies", ctypes.c_int64), ("max_neighbors", ctypes.c_int32)]
+
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+F32 = ctypes.c_float
+DP = ctypes.POINTER(ctypes.c_double)
+FP = ctypes.POINTER(ctypes.c_float)
+I32P = ctypes.POINTER(ctypes.c_int32)
+I64P = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "rb_last_error": (ctypes.c_char_p, []),
+    "rb_abi_version": (I32, []),
+    "rb_create_system": (I32, [ctypes.POINTER(rb_system_desc), P, ctypes.POINTER(P)]),
+    "rb_destroy_system": (I32, [P]),
+    "rb_body_info": (I32, [P, FP, FP, FP, FP, I32P]),
+    "rb_body_template": (I32, [P, FP]),
+    "rb_set_state": (I32, [P, P, P, P, P, I32]),
+    "rb_get_state": (I32, [P, P, P, P, P, I32]),
+    "rb_get_forces": (I32, [P, P, P, I32]),
+    "rb_build_pairs": (I32, [P, I64P]),
+    "rb_get_pairs": (I32, [P, I32P, I64, I64P]),
+    "rb_forces_beads": (I32, [P, P, P, DP, DP]),
+    "rb_step": (I32, [P, I32, P, I32, I64, F32]),
+    "rb_eval_pairs": (I32, [P, I32, P, I32]),
+    "rb_energy": (I32, [P, DP, DP, DP]),
+    "rb_sync": (I32, [P]),
+    "rb_mlp_n_params": (I64, [I32, I32]),
+    "rb_mlp_create": (I32, [I32, I32, P, ctypes.POINTER(P)]),
+    "rb_mlp_destroy": (I32, [P]),
+    "rb_mlp_set_params": (I32, [P, P, I64, I32]),
+    "rb_mlp_get_params": (I32, [P, P, I64, I32]),
+    "rb_forces_nn": (I32, [P, P, I32, P, P, DP, DP]),
+    "rb_nn_pairs": (I32, [P, I32, I64, P, P, P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(SO):
+                raise RuntimeError(f"CUDA library not built ({SO} missing): run "
+                                   "paper_2402_12199_gb300.build_lib.build() first")
+            L = ctypes.CDLL(SO)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != RB_OK:
+        raise RBError(status, load().rb_last_error().decode(errors="replace"))

@@ -1,0 +1,236 @@
+"""Thin Python binding of the C ABI (argument marshalling only).
+
+Device arrays are torch CUDA tensors (float32, contiguous); host arrays are
+numpy.  Every computation runs inside librb.so; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (RB_BF16, RB_FP32, RB_PATH_BEADS, RB_PATH_NN, RB_SHAPE_CUBE, RB_SHAPE_CUSTOM,
+                   RB_SHAPE_CYLINDER, RBError, check, load)
+
+SHAPES = {"cube": RB_SHAPE_CUBE, "cylinder": RB_SHAPE_CYLINDER, "custom": RB_SHAPE_CUSTOM}
+PRECISION = {"fp32": RB_FP32, "bf16": RB_BF16, RB_FP32: RB_FP32, RB_BF16: RB_BF16}
+
+__all__ = ["System", "MLP", "RBError", "RB_PATH_BEADS", "RB_PATH_NN", "RB_FP32", "RB_BF16"]
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, cols: int) -> int:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous() and t.shape[-1] == cols):
+        raise ValueError(f"expected a contiguous float32 CUDA tensor with {cols} columns")
+    return t.data_ptr()
+
+
+def _ptr(x, cols: int):
+    """(pointer, is_host) for a torch CUDA tensor or a host numpy array."""
+    if x is None:
+        return None, 0
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda:
+            return _dev(x, cols), 0
+        x = x.numpy()
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.shape[-1] != cols:
+        raise ValueError(f"expected {cols} columns")
+    return a, 1
+
+
+class System:
+    """rb_create_system / rb_destroy_system and the per-system calls."""
+
+    def __init__(self, n_bodies: int, box, shape: str = "cube", eps: float = 1.0,
+                 sigma: float = 1.0, rcut: float = 2.5, max_neighbors: int = 0,
+                 template=None, bead_mass: float = 1.0, stream=None):
+        L = load()
+        d = _lib.rb_system_desc()
+        d.body.shape = SHAPES[shape]
+        self._tmpl_keep = None
+        if shape == "custom":
+            t = np.ascontiguousarray(template, dtype=np.float32)
+            self._tmpl_keep = t
+            d.body.n_beads = len(t)
+            d.body.bead_xyz_host = t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        d.body.bead_mass = bead_mass
+        d.pot.kind = 0
+        d.pot.eps, d.pot.sigma, d.pot.rcut = eps, sigma, rcut
+        box = np.broadcast_to(np.asarray(box, dtype=np.float32), (3,))
+        for a in range(3):
+            d.box[a] = float(box[a])
+        d.n_bodies = int(n_bodies)
+        d.max_neighbors = int(max_neighbors)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(L.rb_create_system(ctypes.byref(d), _stream_handle(self.stream), ctypes.byref(h)))
+        self._h = h
+        self.N = int(n_bodies)
+        self.box = np.array(box, dtype=np.float32)
+        m, r, rc = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        I = (ctypes.c_float * 3)()
+        nb = ctypes.c_int32()
+        check(L.rb_body_info(h, ctypes.byref(m), I, ctypes.byref(r), ctypes.byref(rc),
+                             ctypes.byref(nb)))
+        self.mass, self.inertia = m.value, np.array(list(I), dtype=np.float32)
+        self.r_circ, self.pair_cutoff, self.n_beads = r.value, rc.value, nb.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().rb_destroy_system(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def template(self) -> np.ndarray:
+        out = np.zeros((self.n_beads, 3), dtype=np.float32)
+        check(load().rb_body_template(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_state(self, pos=None, quat=None, vel=None, angmom=None):
+        arrs = [_ptr(x, 4) for x in (pos, quat, vel, angmom)]
+        hosts = {h for (_, h) in arrs if _ is not None}
+        if len(hosts) > 1:
+            raise ValueError("pass all host arrays or all device tensors")
+        host = hosts.pop() if hosts else 0
+        ptrs = [(a.ctypes.data if host else a) if a is not None else None for a, _ in arrs]
+        check(load().rb_set_state(self._h, *ptrs, host))
+
+    def get_state(self, to_host: bool = False):
+        if to_host:
+            out = {k: np.zeros((self.N, 4), dtype=np.float32) for k in ("pos", "quat", "vel", "angmom")}
+            ptrs = [out[k].ctypes.data for k in ("pos", "quat", "vel", "angmom")]
+        else:
+            out = {k: torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+                   for k in ("pos", "quat", "vel", "angmom")}
+            ptrs = [out[k].data_ptr() for k in ("pos", "quat", "vel", "angmom")]
+        check(load().rb_get_state(self._h, *ptrs, 1 if to_host else 0))
+        return out
+
+    def get_forces(self):
+        F = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        T = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        check(load().rb_get_forces(self._h, F.data_ptr(), T.data_ptr(), 0))
+        return F, T
+
+    def build_pairs(self) -> int:
+        n = ctypes.c_int64()
+        check(load().rb_build_pairs(self._h, ctypes.byref(n)))
+        return n.value
+
+    def pairs(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        check(load().rb_get_pairs(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+        check(load().rb_get_pairs(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  n.value, ctypes.byref(n)))
+        return out[: n.value]
+
+    def _finish(self, st, F, T, e, v, energy, virial):
+        check(st)
+        res = {"force": F, "torque": T}
+        if energy:
+            res["energy"] = e.value
+        if virial:
+            res["virial"] = np.array(list(v)).reshape(3, 3)
+        return res
+
+    def forces_beads(self, energy: bool = False, virial: bool = False):
+        F = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        T = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        e = ctypes.c_double()
+        v = (ctypes.c_double * 9)()
+        st = load().rb_forces_beads(self._h, F.data_ptr(), T.data_ptr(),
+                                    ctypes.byref(e) if energy else None, v if virial else None)
+        return self._finish(st, F, T, e, v, energy, virial)
+
+    def forces_nn(self, mlp: "MLP", precision="fp32", energy: bool = False, virial: bool = False):
+        F = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        T = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        e = ctypes.c_double()
+        v = (ctypes.c_double * 9)()
+        st = load().rb_forces_nn(self._h, mlp.handle, PRECISION[precision], F.data_ptr(),
+                                 T.data_ptr(), ctypes.byref(e) if energy else None,
+                                 v if virial else None)
+        return self._finish(st, F, T, e, v, energy, virial)
+
+    def step(self, n_steps: int, dt: float, path: int = RB_PATH_BEADS, mlp: "MLP" = None,
+             precision="fp32"):
+        check(load().rb_step(self._h, path, mlp.handle if mlp is not None else None,
+                             PRECISION[precision], int(n_steps), float(dt)))
+
+    def eval_pairs(self, path: int = RB_PATH_BEADS, mlp: "MLP" = None, precision="fp32"):
+        check(load().rb_eval_pairs(self._h, path, mlp.handle if mlp is not None else None,
+                                   PRECISION[precision]))
+
+    def energy(self):
+        e, kt, kr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(load().rb_energy(self._h, ctypes.byref(e), ctypes.byref(kt), ctypes.byref(kr)))
+        return e.value, kt.value, kr.value
+
+    def sync(self):
+        check(load().rb_sync(self._h))
+
+
+class MLP:
+    """rb_mlp_create / rb_mlp_destroy and the network calls."""
+
+    def __init__(self, width: int, depth: int = 3, stream=None):
+        L = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(L.rb_mlp_create(int(width), int(depth), _stream_handle(self.stream), ctypes.byref(h)))
+        self._h = h
+        self.width, self.depth = int(width), int(depth)
+        self.n_params = int(L.rb_mlp_n_params(int(width), int(depth)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().rb_mlp_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, flat):
+        if isinstance(flat, torch.Tensor) and flat.is_cuda:
+            t = flat.contiguous().float()
+            check(load().rb_mlp_set_params(self._h, t.data_ptr(), t.numel(), 0))
+            self._keep = t
+        else:
+            a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32).ravel())
+            check(load().rb_mlp_set_params(self._h, a.ctypes.data, a.size, 1))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(self.n_params, dtype=np.float32)
+        check(load().rb_mlp_get_params(self._h, a.ctypes.data, a.size, 1))
+        return a
+
+    def pairs(self, cfg: torch.Tensor, precision="fp32", grad: bool = False):
+        """rb_nn_pairs on (n, 8) configurations; returns (n, 12) [and (n, 8)]."""
+        n = cfg.shape[0]
+        _dev(cfg, 8)
+        out = torch.empty((n, 12), dtype=torch.float32, device="cuda")
+        g = torch.empty((n, 8), dtype=torch.float32, device="cuda") if grad else None
+        check(load().rb_nn_pairs(self._h, PRECISION[precision], n, cfg.data_ptr(),
+                                 out.data_ptr(), g.data_ptr() if grad else None))
+        return (out, g) if grad else out

@@ -1,0 +1,180 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rb.h"
+
+namespace rb {
+
+// ------------------------------------------------------------- error state
+void set_error(const std::string& msg);
+rb_status fail(rb_status s, const std::string& msg);
+rb_status cuda_fail(cudaError_t e, const char* what);
+
+#define RB_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::rb::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define RB_TRY(call)                          \
+    do {                                      \
+        rb_status s_ = (call);                \
+        if (s_ != RB_OK) return s_;           \
+    } while (0)
+
+// Device-side sticky status bits (rb_system::status_dev).
+enum : unsigned {
+    ST_CELL_OVERFLOW = 1u,
+    ST_NBR_OVERFLOW = 2u,
+    ST_NONFINITE = 4u,
+};
+
+constexpr int kMaxBeads = 256;
+
+// ------------------------------------------------------------- device math
+__host__ __device__ inline float4 qmul(float4 a, float4 b) {
+    // Hamilton product, (w, x, y, z) stored as (x=w, y=x, z=y, w=z) of float4
+    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                       a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                       a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
+                       a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+__host__ __device__ inline float4 qconj(float4 q) { return make_float4(q.x, -q.y, -q.z, -q.w); }
+
+// Rotation matrix rows of unit quaternion q = (s, i, j, k) in (x, y, z, w).
+struct Mat3 {
+    float m[9];
+};
+__host__ __device__ inline Mat3 qmat(float4 q) {
+    const float w = q.x, x = q.y, y = q.z, z = q.w;
+    Mat3 R;
+    R.m[0] = 1.f - 2.f * (y * y + z * z);
+    R.m[1] = 2.f * (x * y - w * z);
+    R.m[2] = 2.f * (x * z + w * y);
+    R.m[3] = 2.f * (x * y + w * z);
+    R.m[4] = 1.f - 2.f * (x * x + z * z);
+    R.m[5] = 2.f * (y * z - w * x);
+    R.m[6] = 2.f * (x * z - w * y);
+    R.m[7] = 2.f * (y * z + w * x);
+    R.m[8] = 1.f - 2.f * (x * x + y * y);
+    return R;
+}
+__host__ __device__ inline float3 mul(const Mat3& R, float3 v) {
+    return make_float3(R.m[0] * v.x + R.m[1] * v.y + R.m[2] * v.z,
+                       R.m[3] * v.x + R.m[4] * v.y + R.m[5] * v.z,
+                       R.m[6] * v.x + R.m[7] * v.y + R.m[8] * v.z);
+}
+__host__ __device__ inline float3 mulT(const Mat3& R, float3 v) {
+    return make_float3(R.m[0] * v.x + R.m[3] * v.y + R.m[6] * v.z,
+                       R.m[1] * v.x + R.m[4] * v.y + R.m[7] * v.z,
+                       R.m[2] * v.x + R.m[5] * v.y + R.m[8] * v.z);
+}
+__host__ __device__ inline float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline float3 xyz(float4 v) { return make_float3(v.x, v.y, v.z); }
+
+// Minimum image of d in an orthorhombic box (round half to even, as rintf).
+__device__ inline float3 min_image(float3 d, float3 L, float3 invL) {
+    d.x -= L.x * rintf(d.x * invL.x);
+    d.y -= L.y * rintf(d.y * invL.y);
+    d.z -= L.z * rintf(d.z * invL.z);
+    return d;
+}
+
+// ------------------------------------------------------------- system
+struct PairList {
+    int max_nbr = 0;
+    int64_t cap_pairs = 0;
+    int* half_count = nullptr;  // N
+    int* half_nbr = nullptr;    // N x max_nbr (j > i, sorted)
+    int* lower_count = nullptr; // N
+    int* lower_nbr = nullptr;   // N x max_nbr (j < i, sorted), replaced by pair ids
+    int* half_off = nullptr;    // N + 1
+    int2* pairs = nullptr;      // cap_pairs
+    int* n_pairs = nullptr;     // device scalar
+};
+
+struct CellList {
+    int nc[3] = {1, 1, 1};
+    float width[3] = {0, 0, 0};
+    int n_cells = 0;
+    int cap = 0;
+    int* count = nullptr;   // n_cells
+    int* bodies = nullptr;  // n_cells x cap
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int path = -1;
+    int precision = -1;
+    const void* mlp = nullptr;
+    uint64_t mlp_version = 0;
+    float dt = 0.f;
+};
+
+}  // namespace rb
+
+struct rb_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int width = 0, depth = 0;
+    int64_t n_params = 0;
+    float* params = nullptr;      // flat FP32 (device)
+    void* tc_weights = nullptr;   // BF16 tensor-core copies (device), built lazily
+    size_t tc_bytes = 0;
+    uint64_t version = 1;         // bumped on every set_params
+    uint64_t tc_version = 0;
+};
+
+struct rb_system {
+    int device = 0;
+    cudaStream_t stream = nullptr;       // caller's stream: all work is ordered on it
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture step graphs
+    // body type
+    int n_beads = 0;
+    float bead_mass = 1.f, mass = 0.f, inertia[3] = {0, 0, 0}, r_circ = 0.f, Rc = 0.f;
+    std::vector<float> tmpl;  // n_beads x 3
+    float4* tmpl_dev = nullptr;
+    // potential
+    float eps = 1.f, sigma = 1.f, rcut = 2.5f, u_shift = 0.f;
+    float box[3] = {0, 0, 0};
+    int64_t N = 0;
+    // state
+    float4 *pos = nullptr, *quat = nullptr, *vel = nullptr, *angmom = nullptr;
+    float4 *force = nullptr, *torque = nullptr;
+    bool forces_valid = false;
+    int forces_path = -1, forces_precision = -1;
+    const rb_mlp* forces_mlp = nullptr;
+    uint64_t forces_mlp_version = 0;
+    // neighbour structures
+    rb::CellList cells;
+    rb::PairList pl;
+    // per-pair results: (F_j, E), (tau_i, 0), (tau_j, 0)
+    float4 *pair_F = nullptr, *pair_ti = nullptr, *pair_tj = nullptr;
+    // energies / status
+    double* red_partials = nullptr;  // reduction scratch
+    int red_blocks = 0;
+    double* red_out = nullptr;       // 16 doubles
+    unsigned* status_dev = nullptr;
+    int num_sms = 0;
+    rb::GraphCache graph;
+};
+
+namespace rb {
+// system.cu
+rb_status build_pairs_async(rb_system* s);
+rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
+rb_status energy_async(rb_system* s);
+// beads.cu
+rb_status bead_pairs_async(rb_system* s);
+// nn.cu
+rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision);
+rb_status check_mlp(const rb_mlp* m);
+}  // namespace rb

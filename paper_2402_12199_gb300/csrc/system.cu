@@ -1,0 +1,871 @@
+// System object, neighbour structures, per-body reduction, integrator, FP64
+// energies and the MD step driver.
+//
+// Paper mapping: the bodies are composite rigid bodies (Methods); forces and
+// torques come from the bead double sum (Methods, first equation) or the pair
+// network (Methods, U = g(x, Omega) ~ g_NN_U; SI Sec. 6); the integrator moves
+// the rigid bodies with them (Results).  The paper does not give an
+// integrator; this one is velocity Verlet with the NO_SQUISH free-rotor split
+// (Miller et al., J. Chem. Phys. 116, 8649 (2002)).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rb_internal.cuh"
+
+namespace rb {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+rb_status fail(rb_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+rb_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RB_ENOMEM : RB_ECUDA;
+}
+
+// ------------------------------------------------------------------ kernels
+
+__device__ inline float wrap1(float x, float L, float invL) {
+    x -= L * floorf(x * invL);
+    if (x >= L) x -= L;
+    if (x < 0.f) x = 0.f;
+    return x;
+}
+
+__global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, float3 invL,
+                              float3 invw, int3 nc, int* __restrict__ count,
+                              int* __restrict__ bodies, int cap, unsigned* status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float4 p = pos[i];
+    float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
+    int cx = min(max(int(x * invw.x), 0), nc.x - 1);
+    int cy = min(max(int(y * invw.y), 0), nc.y - 1);
+    int cz = min(max(int(z * invw.z), 0), nc.z - 1);
+    int c = (cz * nc.y + cy) * nc.x + cx;
+    int slot = atomicAdd(&count[c], 1);
+    if (slot < cap)
+        bodies[c * cap + slot] = i;
+    else
+        atomicOr(status, ST_CELL_OVERFLOW);
+}
+
+__device__ inline void sort_row(int* row, int n) {
+    for (int a = 1; a < n; ++a) {
+        int v = row[a];
+        int b = a - 1;
+        while (b >= 0 && row[b] > v) {
+            row[b + 1] = row[b];
+            --b;
+        }
+        row[b + 1] = v;
+    }
+}
+
+// One thread per body: scan the neighbouring cells, keep j with minimum-image
+// |p_j - p_i| < Rc.  j > i goes to the half row (pairs owned by i), j < i to
+// the lower row (pairs owned by j, mirrored for the reduction).  Rows are
+// sorted by j so the pair order does not depend on the cell fill order.
+__global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, float3 invL,
+                             float3 invw, int3 nc, const int* __restrict__ count,
+                             const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
+                             int* __restrict__ half_count, int* __restrict__ half_nbr,
+                             int* __restrict__ lower_count, int* __restrict__ lower_nbr,
+                             unsigned* status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float4 p = pos[i];
+    float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
+    int c[3] = {min(max(int(x * invw.x), 0), nc.x - 1), min(max(int(y * invw.y), 0), nc.y - 1),
+                min(max(int(z * invw.z), 0), nc.z - 1)};
+    int n_[3] = {nc.x, nc.y, nc.z};
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        if (n_[a] >= 3) { lo[a] = -1; hi[a] = 1; }
+        else if (n_[a] == 2) { lo[a] = 0; hi[a] = 1; }
+        else { lo[a] = 0; hi[a] = 0; }
+    }
+    int* hrow = half_nbr + (size_t)i * max_nbr;
+    int* lrow = lower_nbr + (size_t)i * max_nbr;
+    int nh = 0, nl = 0;
+    const float3 pi = make_float3(p.x, p.y, p.z);
+    for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+        int cz = (c[2] + oz + n_[2]) % n_[2];
+        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+            int cy = (c[1] + oy + n_[1]) % n_[1];
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                int cx = (c[0] + ox + n_[0]) % n_[0];
+                int cell = (cz * n_[1] + cy) * n_[0] + cx;
+                int n = min(count[cell], cap);
+                const int* cb = bodies + (size_t)cell * cap;
+                for (int s = 0; s < n; ++s) {
+                    int j = cb[s];
+                    if (j == i) continue;
+                    float4 q = pos[j];
+                    float3 d = min_image(make_float3(q.x - pi.x, q.y - pi.y, q.z - pi.z), L, invL);
+                    float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+                    if (r2 < Rc2) {
+                        if (j > i) {
+                            if (nh < max_nbr) hrow[nh] = j;
+                            ++nh;
+                        } else {
+                            if (nl < max_nbr) lrow[nl] = j;
+                            ++nl;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (nh + nl > max_nbr) {
+        atomicOr(status, ST_NBR_OVERFLOW);
+        nh = min(nh, max_nbr);
+        nl = min(nl, max_nbr);
+    }
+    sort_row(hrow, nh);
+    sort_row(lrow, nl);
+    half_count[i] = nh;
+    lower_count[i] = nl;
+}
+
+// Exclusive scan of the half-row counts (single block; each thread owns a
+// contiguous chunk).  off[N] and *total receive the number of pairs.
+__global__ void k_scan(const int* __restrict__ cnt, int N, int* __restrict__ off, int* total,
+                       int64_t cap_pairs, unsigned* status) {
+    __shared__ int sh[1024];
+    const int t = threadIdx.x;
+    const int chunk = (N + 1023) / 1024;
+    const int b = t * chunk, e = min(b + chunk, N);
+    int sum = 0;
+    for (int k = b; k < e; ++k) sum += cnt[k];
+    sh[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    int run = sh[t] - sum;
+    for (int k = b; k < e; ++k) {
+        off[k] = run;
+        run += cnt[k];
+    }
+    if (t == 1023) {
+        int tot = sh[1023];
+        if ((int64_t)tot > cap_pairs) {
+            atomicOr(status, ST_NBR_OVERFLOW);
+            tot = (int)cap_pairs;
+        }
+        off[N] = tot;
+        *total = tot;
+    }
+}
+
+// Emit the compact pair list and turn each lower-row entry j (< i) into the
+// index of pair (j, i) inside j's half row.
+__global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_count,
+                            const int* __restrict__ half_nbr, const int* __restrict__ half_off,
+                            const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
+                            int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int off = half_off[i];
+    const int n = half_count[i];
+    const int* hrow = half_nbr + (size_t)i * max_nbr;
+    for (int k = 0; k < n; ++k)
+        if (off + k < cap_pairs) pairs[off + k] = make_int2(i, hrow[k]);
+    int* lrow = lower_nbr + (size_t)i * max_nbr;
+    const int nl = lower_count[i];
+    for (int m = 0; m < nl; ++m) {
+        const int j = lrow[m];
+        const int* jrow = half_nbr + (size_t)j * max_nbr;
+        int a = 0, b = half_count[j] - 1, found = -1;
+        while (a <= b) {
+            int mid = (a + b) >> 1;
+            int v = jrow[mid];
+            if (v == i) { found = mid; break; }
+            if (v < i) a = mid + 1; else b = mid - 1;
+        }
+        if (found < 0 || half_off[j] + found >= cap_pairs) {
+            atomicOr(status, ST_NBR_OVERFLOW);
+            lrow[m] = -1;
+        } else {
+            lrow[m] = half_off[j] + found;
+        }
+    }
+}
+
+// Per-body reduction of the per-pair results in a fixed order (own half row by
+// ascending j, then mirrored pairs by ascending j): no atomics, so results are
+// bit-reproducible.  Optionally applies the second velocity-Verlet half kick.
+__global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
+                         const int* __restrict__ half_count, const int* __restrict__ lower_count,
+                         const int* __restrict__ lower_pair, const float4* __restrict__ pF,
+                         const float4* __restrict__ pti, const float4* __restrict__ ptj,
+                         float4* __restrict__ force, float4* __restrict__ torque, float kick,
+                         float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
+                         const float4* __restrict__ quat, unsigned* status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float3 F = make_float3(0.f, 0.f, 0.f), T = make_float3(0.f, 0.f, 0.f);
+    float e = 0.f;
+    const int off = half_off[i];
+    const int n = (int)min((int64_t)half_count[i], cap_pairs - off);
+    for (int k = 0; k < n; ++k) {
+        float4 f = pF[off + k];
+        float4 t = pti[off + k];
+        F.x -= f.x; F.y -= f.y; F.z -= f.z;
+        T.x += t.x; T.y += t.y; T.z += t.z;
+        e += 0.5f * f.w;
+    }
+    const int nl = lower_count[i];
+    const int* lrow = lower_pair + (size_t)i * max_nbr;
+    for (int m = 0; m < nl; ++m) {
+        int p = lrow[m];
+        if (p < 0) continue;
+        float4 f = pF[p];
+        float4 t = ptj[p];
+        F.x += f.x; F.y += f.y; F.z += f.z;
+        T.x += t.x; T.y += t.y; T.z += t.z;
+        e += 0.5f * f.w;
+    }
+    if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
+          isfinite(T.z) && isfinite(e)))
+        atomicOr(status, ST_NONFINITE);
+    force[i] = make_float4(F.x, F.y, F.z, e);
+    torque[i] = make_float4(T.x, T.y, T.z, 0.f);
+    if (kick != 0.f) {
+        float4 v = vel[i];
+        v.x += kick * F.x * inv_mass;
+        v.y += kick * F.y * inv_mass;
+        v.z += kick * F.z * inv_mass;
+        vel[i] = v;
+        Mat3 R = qmat(quat[i]);
+        float3 tb = mulT(R, T);
+        float4 Lb = angmom[i];
+        Lb.x += kick * tb.x;
+        Lb.y += kick * tb.y;
+        Lb.z += kick * tb.z;
+        angmom[i] = Lb;
+    }
+}
+
+// First half of a velocity-Verlet step: half kick, drift (wrapped), and the
+// NO_SQUISH free rotation about body axes 3, 2, 1, 2, 3 for dt/2, dt/2, dt,
+// dt/2, dt/2; q is renormalised once per step.
+__global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, float3 L,
+                                  float3 invL, float4* __restrict__ pos, float4* __restrict__ quat,
+                                  float4* __restrict__ vel, float4* __restrict__ angmom,
+                                  const float4* __restrict__ force,
+                                  const float4* __restrict__ torque) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float h = 0.5f * dt;
+    float4 f = force[i], t = torque[i];
+    float4 v = vel[i];
+    v.x += h * f.x * inv_mass;
+    v.y += h * f.y * inv_mass;
+    v.z += h * f.z * inv_mass;
+    float4 q = quat[i];
+    Mat3 R = qmat(q);
+    float3 tb = mulT(R, make_float3(t.x, t.y, t.z));
+    float4 Lw = angmom[i];
+    float Lb[3] = {Lw.x + h * tb.x, Lw.y + h * tb.y, Lw.z + h * tb.z};
+    float4 p = pos[i];
+    p.x = wrap1(p.x + dt * v.x, L.x, invL.x);
+    p.y = wrap1(p.y + dt * v.y, L.y, invL.y);
+    p.z = wrap1(p.z + dt * v.z, L.z, invL.z);
+    const float invIk[3] = {invI.x, invI.y, invI.z};
+    const int axes[5] = {2, 1, 0, 1, 2};
+    const float frac[5] = {0.5f, 0.5f, 1.f, 0.5f, 0.5f};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int k = axes[s];
+        const float phi = frac[s] * dt * Lb[k] * invIk[k];
+        float sh, ch, sp, cp;
+        sincosf(0.5f * phi, &sh, &ch);
+        sincosf(phi, &sp, &cp);
+        float4 r = make_float4(ch, 0.f, 0.f, 0.f);
+        if (k == 0) r.y = sh; else if (k == 1) r.z = sh; else r.w = sh;
+        q = qmul(q, r);
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        const float La = Lb[a], Lbb = Lb[b];
+        Lb[a] = cp * La + sp * Lbb;
+        Lb[b] = -sp * La + cp * Lbb;
+    }
+    const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    q.x *= inv; q.y *= inv; q.z *= inv; q.w *= inv;
+    pos[i] = p;
+    quat[i] = q;
+    vel[i] = v;
+    angmom[i] = make_float4(Lb[0], Lb[1], Lb[2], Lw.w);
+}
+
+// Deterministic block reduction of NV doubles; thread 0 writes the block sums.
+template <int NV>
+__device__ inline void block_reduce_write(double (&v)[NV], double* out) {
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) sh[w][k] = v[k];
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < NV; ++k) {
+            double x = lane < nw ? sh[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) out[k] = x;
+        }
+    }
+}
+
+// Bodies: translational and rotational kinetic energy (FP64).
+__global__ void k_energy_bodies(int N, double mass, double3 invI, const float4* __restrict__ vel,
+                                const float4* __restrict__ angmom, double* __restrict__ partial) {
+    double v[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        float4 u = vel[i];
+        float4 L = angmom[i];
+        v[0] += 0.5 * mass * ((double)u.x * u.x + (double)u.y * u.y + (double)u.z * u.z);
+        v[1] += 0.5 * ((double)L.x * L.x * invI.x + (double)L.y * L.y * invI.y +
+                       (double)L.z * L.z * invI.z);
+    }
+    block_reduce_write<2>(v, partial + blockIdx.x * 2);
+}
+
+// Pairs: potential energy and the centre-of-mass virial sum R_ij (x) F_j (FP64).
+__global__ void k_energy_pairs(const int* __restrict__ n_pairs_ptr, const int2* __restrict__ pairs,
+                               const float4* __restrict__ pos, float3 L, float3 invL,
+                               const float4* __restrict__ pF, double* __restrict__ partial) {
+    double v[10];
+    for (int k = 0; k < 10; ++k) v[k] = 0.0;
+    const int n = *n_pairs_ptr;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        int2 ij = pairs[p];
+        float4 a = pos[ij.x], b = pos[ij.y];
+        float3 R = min_image(make_float3(b.x - a.x, b.y - a.y, b.z - a.z), L, invL);
+        float4 f = pF[p];
+        v[0] += f.w;
+        const double r[3] = {R.x, R.y, R.z}, F[3] = {f.x, f.y, f.z};
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) v[1 + 3 * x + y] += r[x] * F[y];
+    }
+    block_reduce_write<10>(v, partial + blockIdx.x * 10);
+}
+
+__global__ void k_energy_final(const double* __restrict__ pb, int nb_b,
+                               const double* __restrict__ pp, int nb_p, double* out) {
+    // one warp per output value, fixed order
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < 2) {
+        double x = 0.0;
+        for (int k = lane; k < nb_b; k += 32) x += pb[k * 2 + w];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) out[1 + w] = x;
+    } else if (w < 12) {
+        const int c = w - 2;
+        double x = 0.0;
+        for (int k = lane; k < nb_p; k += 32) x += pp[k * 10 + c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) {
+            if (c == 0) out[0] = x; else out[3 + c - 1] = x;
+        }
+    }
+}
+
+static inline int blocks_for(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+static inline float3 f3(const float* a) { return make_float3(a[0], a[1], a[2]); }
+static inline float3 inv3(const float* a) { return make_float3(1.f / a[0], 1.f / a[1], 1.f / a[2]); }
+
+rb_status build_pairs_async(rb_system* s) {
+    const int N = (int)s->N;
+    const float3 L = f3(s->box), invL = inv3(s->box);
+    const float3 invw = inv3(s->cells.width);
+    const int3 nc = make_int3(s->cells.nc[0], s->cells.nc[1], s->cells.nc[2]);
+    RB_CUDA(cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream));
+    k_cell_assign<<<blocks_for(N, 256), 256, 0, s->stream>>>(s->pos, N, L, invL, invw, nc,
+                                                             s->cells.count, s->cells.bodies,
+                                                             s->cells.cap, s->status_dev);
+    k_pair_build<<<blocks_for(N, 128), 128, 0, s->stream>>>(
+        s->pos, N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap,
+        s->Rc * s->Rc, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.lower_count,
+        s->pl.lower_nbr, s->status_dev);
+    k_scan<<<1, 1024, 0, s->stream>>>(s->pl.half_count, N, s->pl.half_off, s->pl.n_pairs,
+                                      s->pl.cap_pairs, s->status_dev);
+    k_pair_emit<<<blocks_for(N, 256), 256, 0, s->stream>>>(
+        N, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.half_off, s->pl.lower_count,
+        s->pl.lower_nbr, s->pl.pairs, s->pl.cap_pairs, s->status_dev);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+rb_status reduce_forces_async(rb_system* s, float kick) {
+    const int N = (int)s->N;
+    k_reduce<<<blocks_for(N, 256), 256, 0, s->stream>>>(
+        N, s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count, s->pl.lower_count,
+        s->pl.lower_nbr,
+        s->pair_F, s->pair_ti, s->pair_tj, s->force, s->torque, kick, 1.f / s->mass, s->vel,
+        s->angmom, s->quat, s->status_dev);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+rb_status energy_async(rb_system* s) {
+    const int nb = s->red_blocks;
+    double* pb = s->red_partials;
+    double* pp = s->red_partials + 2 * nb;
+    k_energy_bodies<<<nb, 256, 0, s->stream>>>(
+        (int)s->N, (double)s->mass,
+        make_double3(1.0 / s->inertia[0], 1.0 / s->inertia[1], 1.0 / s->inertia[2]), s->vel,
+        s->angmom, pb);
+    k_energy_pairs<<<nb, 256, 0, s->stream>>>(s->pl.n_pairs, s->pl.pairs, s->pos, f3(s->box),
+                                             inv3(s->box), s->pair_F, pp);
+    k_energy_final<<<1, 384, 0, s->stream>>>(pb, nb, pp, nb, s->red_out);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+static rb_status check_status(rb_system* s) {
+    unsigned st = 0;
+    RB_CUDA(cudaMemcpyAsync(&st, s->status_dev, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            s->stream));
+    RB_CUDA(cudaStreamSynchronize(s->stream));
+    if (st & (ST_CELL_OVERFLOW | ST_NBR_OVERFLOW)) {
+        RB_CUDA(cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream));
+        s->forces_valid = false;
+        return fail(RB_EOVERFLOW, st & ST_CELL_OVERFLOW
+                                      ? "cell capacity exceeded: raise max_neighbors"
+                                      : "neighbour capacity exceeded: raise max_neighbors");
+    }
+    if (st & ST_NONFINITE) {
+        RB_CUDA(cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream));
+        return fail(RB_EFAULT, "non-finite force, torque or energy");
+    }
+    return RB_OK;
+}
+
+// ------------------------------------------------------------------ host side
+
+static std::vector<float> make_template(const rb_body_type& b, std::string& err) {
+    std::vector<float> t;
+    if (b.shape == RB_SHAPE_CUBE) {
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j)
+                for (int k = 0; k < 5; ++k) {
+                    t.push_back(float(i - 2));
+                    t.push_back(float(j - 2));
+                    t.push_back(float(k - 2));
+                }
+    } else if (b.shape == RB_SHAPE_CYLINDER) {
+        // hexagonal disc of radius 2 at spacing 1 (19 points), 8 layers over 8 sigma
+        std::vector<std::pair<double, double>> disc;
+        for (int a = -4; a <= 4; ++a)
+            for (int c = -4; c <= 4; ++c) {
+                double x = a + 0.5 * c, y = c * std::sqrt(3.0) / 2.0;
+                if (x * x + y * y <= 4.0 + 1e-9) disc.push_back({x, y});
+            }
+        for (int l = 0; l < 8; ++l) {
+            double z = (l - 3.5) * (8.0 / 7.0);
+            for (auto& p : disc) {
+                t.push_back((float)p.first);
+                t.push_back((float)p.second);
+                t.push_back((float)z);
+            }
+        }
+    } else if (b.shape == RB_SHAPE_CUSTOM) {
+        if (!b.bead_xyz_host || b.n_beads <= 0) {
+            err = "custom body needs n_beads > 0 and bead_xyz_host";
+            return {};
+        }
+        t.assign(b.bead_xyz_host, b.bead_xyz_host + 3 * (size_t)b.n_beads);
+    } else {
+        err = "unknown body shape";
+        return {};
+    }
+    if (t.size() / 3 > (size_t)kMaxBeads) {
+        err = "too many beads (max 256)";
+        return {};
+    }
+    return t;
+}
+
+}  // namespace rb
+
+using namespace rb;
+
+extern "C" {
+
+const char* rb_last_error(void) { return rb::g_err.c_str(); }
+int32_t rb_abi_version(void) { return 1; }
+
+rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** out) {
+    if (!d || !out) return fail(RB_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->n_bodies < 1 || d->n_bodies > (int64_t)1 << 26)
+        return fail(RB_EINVAL, "n_bodies out of range [1, 2^26]");
+    if (d->pot.kind != RB_POT_LJ) return fail(RB_ENOTSUP, "only the LJ bead potential is built");
+    if (!(d->pot.eps > 0 && d->pot.sigma > 0 && d->pot.rcut > 0))
+        return fail(RB_EINVAL, "potential parameters must be positive");
+    std::string err;
+    std::vector<float> t = make_template(d->body, err);
+    if (t.empty()) return fail(RB_EINVAL, err);
+    rb_system* s = new (std::nothrow) rb_system();
+    if (!s) return fail(RB_ENOMEM, "host allocation");
+    s->stream = (cudaStream_t)stream;
+    cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    s->tmpl = t;
+    s->n_beads = (int)(t.size() / 3);
+    s->bead_mass = d->body.bead_mass > 0 ? d->body.bead_mass : 1.f;
+    double I[9] = {0}, rmax = 0;
+    for (int k = 0; k < s->n_beads; ++k) {
+        double v[3] = {t[3 * k], t[3 * k + 1], t[3 * k + 2]};
+        double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        rmax = std::max(rmax, std::sqrt(r2));
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) I[3 * a + b] += s->bead_mass * ((a == b ? r2 : 0.0) - v[a] * v[b]);
+    }
+    double tr = I[0] + I[4] + I[8];
+    double off = std::fabs(I[1]) + std::fabs(I[2]) + std::fabs(I[5]);
+    if (off > 1e-5 * tr || I[0] <= 0 || I[4] <= 0 || I[8] <= 0) {
+        delete s;
+        return fail(RB_EINVAL, "template inertia must be diagonal and positive (principal axes along x, y, z)");
+    }
+    s->mass = s->bead_mass * s->n_beads;
+    s->inertia[0] = (float)I[0];
+    s->inertia[1] = (float)I[4];
+    s->inertia[2] = (float)I[8];
+    s->r_circ = (float)rmax;
+    s->eps = d->pot.eps;
+    s->sigma = d->pot.sigma;
+    s->rcut = d->pot.rcut;
+    {
+        double sr2 = (double)s->sigma * s->sigma / ((double)s->rcut * s->rcut);
+        double sr6 = sr2 * sr2 * sr2;
+        s->u_shift = (float)(4.0 * s->eps * (sr6 * sr6 - sr6));
+    }
+    s->Rc = (float)(2.0 * rmax + s->rcut);
+    for (int a = 0; a < 3; ++a) {
+        s->box[a] = d->box[a];
+        if (!(d->box[a] >= 2.f * s->Rc)) {
+            delete s;
+            return fail(RB_EINVAL, "every box side must be at least twice the body-pair cutoff Rc");
+        }
+    }
+    s->N = d->n_bodies;
+    s->pl.max_nbr = d->max_neighbors > 0 ? d->max_neighbors : 64;
+    s->pl.cap_pairs = std::max<int64_t>(1, s->N * s->pl.max_nbr / 2);
+    for (int a = 0; a < 3; ++a) {
+        s->cells.nc[a] = std::max(1, (int)std::floor(s->box[a] / s->Rc));
+        s->cells.width[a] = s->box[a] / s->cells.nc[a];
+    }
+    s->cells.n_cells = s->cells.nc[0] * s->cells.nc[1] * s->cells.nc[2];
+    s->cells.cap = std::max(32, 2 * s->pl.max_nbr);
+    s->red_blocks = std::max(1, 2 * s->num_sms);
+
+    const size_t N = (size_t)s->N, mn = (size_t)s->pl.max_nbr, cp = (size_t)s->pl.cap_pairs;
+    auto A = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) \
+    if (e == cudaSuccess) e = A((void**)&(ptr), (bytes))
+    ALLOC(s->tmpl_dev, sizeof(float4) * s->n_beads);
+    ALLOC(s->pos, sizeof(float4) * N);
+    ALLOC(s->quat, sizeof(float4) * N);
+    ALLOC(s->vel, sizeof(float4) * N);
+    ALLOC(s->angmom, sizeof(float4) * N);
+    ALLOC(s->force, sizeof(float4) * N);
+    ALLOC(s->torque, sizeof(float4) * N);
+    ALLOC(s->cells.count, sizeof(int) * s->cells.n_cells);
+    ALLOC(s->cells.bodies, sizeof(int) * (size_t)s->cells.n_cells * s->cells.cap);
+    ALLOC(s->pl.half_count, sizeof(int) * N);
+    ALLOC(s->pl.lower_count, sizeof(int) * N);
+    ALLOC(s->pl.half_nbr, sizeof(int) * N * mn);
+    ALLOC(s->pl.lower_nbr, sizeof(int) * N * mn);
+    ALLOC(s->pl.half_off, sizeof(int) * (N + 1));
+    ALLOC(s->pl.pairs, sizeof(int2) * cp);
+    ALLOC(s->pl.n_pairs, sizeof(int));
+    ALLOC(s->pair_F, sizeof(float4) * cp);
+    ALLOC(s->pair_ti, sizeof(float4) * cp);
+    ALLOC(s->pair_tj, sizeof(float4) * cp);
+    ALLOC(s->red_partials, sizeof(double) * 12 * s->red_blocks);
+    ALLOC(s->red_out, sizeof(double) * 16);
+    ALLOC(s->status_dev, sizeof(unsigned));
+#undef ALLOC
+    if (e != cudaSuccess) {
+        rb_status st = cuda_fail(e, "cudaMalloc (system)");
+        rb_destroy_system(s);
+        return st;
+    }
+    std::vector<float4> t4(s->n_beads);
+    for (int k = 0; k < s->n_beads; ++k) t4[k] = make_float4(t[3 * k], t[3 * k + 1], t[3 * k + 2], 0.f);
+    e = cudaMemcpyAsync(s->tmpl_dev, t4.data(), sizeof(float4) * s->n_beads,
+                        cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->pl.n_pairs, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->angmom, 0, sizeof(float4) * N, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->vel, 0, sizeof(float4) * N, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        rb_status st = cuda_fail(e, "system initialisation");
+        rb_destroy_system(s);
+        return st;
+    }
+    *out = s;
+    return RB_OK;
+}
+
+rb_status rb_destroy_system(rb_system* s) {
+    if (!s) return RB_OK;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    void* ptrs[] = {s->tmpl_dev, s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
+                    s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
+                    s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.pairs, s->pl.n_pairs,
+                    s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete s;
+    return RB_OK;
+}
+
+rb_status rb_body_info(const rb_system* s, float* mass, float* inertia3, float* r_circ,
+                       float* pair_cutoff, int32_t* n_beads) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (mass) *mass = s->mass;
+    if (inertia3)
+        for (int a = 0; a < 3; ++a) inertia3[a] = s->inertia[a];
+    if (r_circ) *r_circ = s->r_circ;
+    if (pair_cutoff) *pair_cutoff = s->Rc;
+    if (n_beads) *n_beads = s->n_beads;
+    return RB_OK;
+}
+
+rb_status rb_body_template(const rb_system* s, float* xyz) {
+    if (!s || !xyz) return fail(RB_EINVAL, "null argument");
+    std::memcpy(xyz, s->tmpl.data(), sizeof(float) * s->tmpl.size());
+    return RB_OK;
+}
+
+rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const float* vel,
+                       const float* angmom, int32_t from_host) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    const size_t b = sizeof(float4) * s->N;
+    const cudaMemcpyKind k = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (pos) RB_CUDA(cudaMemcpyAsync(s->pos, pos, b, k, s->stream));
+    if (quat) RB_CUDA(cudaMemcpyAsync(s->quat, quat, b, k, s->stream));
+    if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
+    if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
+    s->forces_valid = false;
+    return RB_OK;
+}
+
+rb_status rb_get_state(const rb_system* s, float* pos, float* quat, float* vel, float* angmom,
+                       int32_t to_host) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    const size_t b = sizeof(float4) * s->N;
+    const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (pos) RB_CUDA(cudaMemcpyAsync(pos, s->pos, b, k, s->stream));
+    if (quat) RB_CUDA(cudaMemcpyAsync(quat, s->quat, b, k, s->stream));
+    if (vel) RB_CUDA(cudaMemcpyAsync(vel, s->vel, b, k, s->stream));
+    if (angmom) RB_CUDA(cudaMemcpyAsync(angmom, s->angmom, b, k, s->stream));
+    if (to_host) RB_CUDA(cudaStreamSynchronize(s->stream));
+    return RB_OK;
+}
+
+rb_status rb_get_forces(const rb_system* s, float* force, float* torque, int32_t to_host) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    const size_t b = sizeof(float4) * s->N;
+    const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (force) RB_CUDA(cudaMemcpyAsync(force, s->force, b, k, s->stream));
+    if (torque) RB_CUDA(cudaMemcpyAsync(torque, s->torque, b, k, s->stream));
+    if (to_host) RB_CUDA(cudaStreamSynchronize(s->stream));
+    return RB_OK;
+}
+
+rb_status rb_build_pairs(rb_system* s, int64_t* n_pairs) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    RB_TRY(build_pairs_async(s));
+    if (n_pairs) {
+        RB_TRY(check_status(s));
+        int n = 0;
+        RB_CUDA(cudaMemcpy(&n, s->pl.n_pairs, sizeof(int), cudaMemcpyDeviceToHost));
+        *n_pairs = n;
+    }
+    return RB_OK;
+}
+
+rb_status rb_get_pairs(const rb_system* s, int32_t* pairs, int64_t cap, int64_t* n_pairs) {
+    if (!s || !n_pairs) return fail(RB_EINVAL, "null argument");
+    int n = 0;
+    RB_CUDA(cudaStreamSynchronize(s->stream));
+    RB_CUDA(cudaMemcpy(&n, s->pl.n_pairs, sizeof(int), cudaMemcpyDeviceToHost));
+    *n_pairs = n;
+    if (pairs && cap > 0)
+        RB_CUDA(cudaMemcpy(pairs, s->pl.pairs, sizeof(int2) * std::min<int64_t>(cap, n),
+                           cudaMemcpyDeviceToHost));
+    return RB_OK;
+}
+
+static rb_status read_energy(rb_system* s, double* energy, double* virial9) {
+    RB_TRY(energy_async(s));
+    double h[16];
+    RB_CUDA(cudaMemcpyAsync(h, s->red_out, sizeof(double) * 12, cudaMemcpyDeviceToHost, s->stream));
+    RB_TRY(check_status(s));
+    if (energy) *energy = h[0];
+    if (virial9)
+        for (int k = 0; k < 9; ++k) virial9[k] = h[3 + k];
+    return RB_OK;
+}
+
+static rb_status finish_forces(rb_system* s, float* force, float* torque, double* energy,
+                               double* virial9) {
+    const size_t b = sizeof(float4) * s->N;
+    if (force) RB_CUDA(cudaMemcpyAsync(force, s->force, b, cudaMemcpyDeviceToDevice, s->stream));
+    if (torque) RB_CUDA(cudaMemcpyAsync(torque, s->torque, b, cudaMemcpyDeviceToDevice, s->stream));
+    if (energy || virial9) RB_TRY(read_energy(s, energy, virial9));
+    return RB_OK;
+}
+
+rb_status rb_forces_beads(rb_system* s, float* force, float* torque, double* energy,
+                          double* virial9) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    RB_TRY(build_pairs_async(s));
+    RB_TRY(bead_pairs_async(s));
+    RB_TRY(reduce_forces_async(s, 0.f));
+    s->forces_valid = true;
+    s->forces_path = RB_PATH_BEADS;
+    s->forces_precision = RB_FP32;
+    s->forces_mlp = nullptr;
+    return finish_forces(s, force, torque, energy, virial9);
+}
+
+rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* force,
+                       float* torque, double* energy, double* virial9) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    RB_TRY(check_mlp(m));
+    RB_TRY(build_pairs_async(s));
+    RB_TRY(nn_pairs_system_async(s, m, precision));
+    RB_TRY(reduce_forces_async(s, 0.f));
+    s->forces_valid = true;
+    s->forces_path = RB_PATH_NN;
+    s->forces_precision = precision;
+    s->forces_mlp = m;
+    s->forces_mlp_version = m->version;
+    return finish_forces(s, force, torque, energy, virial9);
+}
+
+static rb_status eval_forces_async(rb_system* s, int path, const rb_mlp* m, int precision,
+                                   float kick) {
+    RB_TRY(build_pairs_async(s));
+    if (path == RB_PATH_BEADS)
+        RB_TRY(bead_pairs_async(s));
+    else
+        RB_TRY(nn_pairs_system_async(s, m, precision));
+    return reduce_forces_async(s, kick);
+}
+
+rb_status rb_eval_pairs(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (path == RB_PATH_BEADS) return bead_pairs_async(s);
+    if (path == RB_PATH_NN) {
+        RB_TRY(check_mlp(m));
+        return nn_pairs_system_async(s, m, precision);
+    }
+    return fail(RB_EINVAL, "unknown path");
+}
+
+rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
+                  int64_t n_steps, float dt) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (path != RB_PATH_BEADS && path != RB_PATH_NN) return fail(RB_EINVAL, "unknown path");
+    if (path == RB_PATH_NN) RB_TRY(check_mlp(m));
+    if (path == RB_PATH_BEADS) { m = nullptr; precision = RB_FP32; }
+    if (precision != RB_FP32 && precision != RB_BF16) return fail(RB_EINVAL, "unknown precision");
+    if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
+    const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
+                      s->forces_precision == precision &&
+                      (!m || s->forces_mlp_version == m->version);
+    if (!same) {
+        RB_TRY(eval_forces_async(s, path, m, precision, 0.f));
+        s->forces_valid = true;
+        s->forces_path = path;
+        s->forces_precision = precision;
+        s->forces_mlp = m;
+        s->forces_mlp_version = m ? m->version : 0;
+    }
+    if (n_steps == 0) return RB_OK;
+    GraphCache& g = s->graph;
+    if (!g.exec || g.path != path || g.precision != precision || g.mlp != m || g.dt != dt ||
+        (m && g.mlp_version != m->version)) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        // Capture on a private stream (the caller's stream may be the legacy
+        // default stream, which cannot be captured); launch on the caller's.
+        cudaGraph_t graph;
+        cudaStream_t user = s->stream;
+        s->stream = s->cap_stream;
+        cudaError_t be = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (be != cudaSuccess) {
+            s->stream = user;
+            return cuda_fail(be, "cudaStreamBeginCapture");
+        }
+        const int N = (int)s->N;
+        k_integrate_first<<<blocks_for(N, 256), 256, 0, s->stream>>>(
+            N, dt, 1.f / s->mass,
+            make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
+            f3(s->box), inv3(s->box), s->pos, s->quat, s->vel, s->angmom, s->force, s->torque);
+        rb_status st = eval_forces_async(s, path, m, precision, 0.5f * dt);
+        cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
+        s->stream = user;
+        if (st != RB_OK) {
+            if (ce == cudaSuccess) cudaGraphDestroy(graph);
+            return st;
+        }
+        RB_CUDA(ce);
+        cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        RB_CUDA(ie);
+        g.path = path;
+        g.precision = precision;
+        g.mlp = m;
+        g.mlp_version = m ? m->version : 0;
+        g.dt = dt;
+    }
+    for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
+    return RB_OK;
+}
+
+rb_status rb_energy(rb_system* s, double* e_pot, double* ke_t, double* ke_r) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (!s->forces_valid) return fail(RB_EINVAL, "no force evaluation for the current state");
+    RB_TRY(energy_async(s));
+    double h[16];
+    RB_CUDA(cudaMemcpyAsync(h, s->red_out, sizeof(double) * 12, cudaMemcpyDeviceToHost, s->stream));
+    RB_TRY(check_status(s));
+    if (e_pot) *e_pot = h[0];
+    if (ke_t) *ke_t = h[1];
+    if (ke_r) *ke_r = h[2];
+    return RB_OK;
+}
+
+rb_status rb_sync(rb_system* s) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    return check_status(s);
+}
+
+}  // extern "C"
