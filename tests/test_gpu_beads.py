@@ -63,8 +63,8 @@ def _parity(st, L, tmpl, shape, tol=TOL_F32):
     eF, eT = rel_err(Fg, F), rel_err(Tg, T)
     assert eF < tol and eT < tol, (eF, eT)
     # energy: relative to the sum of |pair energies|
-    _, _, _, pp = oracle.forces_beads(st["pos"][:, :3], st["quat"], [L] * 3, tmpl, pairs,
-                                      per_pair=True)
+    pp = oracle.forces_beads(st["pos"][:, :3], st["quat"], [L] * 3, tmpl, pairs,
+                             per_pair=True)[4]
     scale = np.abs(pp[:, 0]).sum()
     assert abs(res["energy"] - E) <= tol * max(scale, 1e-12), (res["energy"], E)
     assert rel_err(res["virial"], vir) < tol
