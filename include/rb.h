@@ -218,6 +218,18 @@ rb_status rb_forces_nn(rb_system* sys, const rb_mlp* mlp, int32_t precision, flo
 rb_status rb_nn_pairs(const rb_mlp* mlp, int32_t precision, int64_t n, const float* cfg,
                       float* out, float* grad_out);
 
+/* Wait for the network's stream and report sticky device-side errors of
+ * rb_nn_pairs (RB_EFAULT if a tensor-core kernel gave up waiting for an MMA). */
+rb_status rb_mlp_sync(const rb_mlp* mlp);
+
+/* Diagnostic of the tensor-core path: D = A B^T for one 128 x N x K tile with
+ * BF16 operands (A: 128 x K, B: N x K, D: 128 x N, row-major FP32 device
+ * arrays), staged through the same shared-memory layout, descriptors and
+ * tensor-memory read-back as the network kernel.  N in {16, 32, 64, 128},
+ * K in {64, 128}.  Synchronises the stream. */
+rb_status rb_tc_gemm_check(int32_t N, int32_t K, const float* A, const float* B, float* D,
+                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

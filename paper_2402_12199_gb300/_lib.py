@@ -77,6 +77,8 @@ SIGNATURES = {
     "rb_mlp_get_params": (I32, [P, P, I64, I32]),
     "rb_forces_nn": (I32, [P, P, I32, P, P, DP, DP]),
     "rb_nn_pairs": (I32, [P, I32, I64, P, P, P]),
+    "rb_mlp_sync": (I32, [P]),
+    "rb_tc_gemm_check": (I32, [I32, I32, P, P, P, P]),
 }
 
 _lock = threading.Lock()

@@ -233,4 +233,17 @@ class MLP:
         g = torch.empty((n, 8), dtype=torch.float32, device="cuda") if grad else None
         check(load().rb_nn_pairs(self._h, PRECISION[precision], n, cfg.data_ptr(),
                                  out.data_ptr(), g.data_ptr() if grad else None))
+        check(load().rb_mlp_sync(self._h))
         return (out, g) if grad else out
+
+
+def tc_gemm_check(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """rb_tc_gemm_check: D = A B^T on one tensor-core tile (diagnostic)."""
+    K = A.shape[1]
+    N = B.shape[0]
+    A = A.contiguous().float()
+    B = B.contiguous().float()
+    D = torch.empty((A.shape[0], N), dtype=torch.float32, device="cuda")
+    check(load().rb_tc_gemm_check(N, K, A.data_ptr(), B.data_ptr(), D.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream))
+    return D

@@ -28,12 +28,10 @@
 #include <new>
 #include <vector>
 
-#include "rb_internal.cuh"
+#include "nn_common.cuh"
 
 namespace rb {
 
-constexpr int kIn = 10;
-constexpr int kInPad = 16;
 constexpr int kKC = 32;
 
 // Prepared FP32 weights (device), built from the flat parameters:
@@ -51,28 +49,6 @@ __host__ __device__ inline F32Layout f32_layout(int W, int D) {
     L.total = L.w1p + (int64_t)W * kInPad;
     return L;
 }
-// Offsets in the flat parameter vector.
-struct FlatLayout {
-    int64_t mu, inv_sd, W1, b1, Wl, bl, wo, bo, escale, eshift, total;
-    __host__ __device__ int64_t W_(int l, int W) const { return Wl + (int64_t)(l - 2) * (W * W + W); }
-    __host__ __device__ int64_t b_(int l, int W) const { return l == 1 ? b1 : Wl + (int64_t)(l - 2) * (W * W + W) + W * W; }
-};
-__host__ __device__ inline FlatLayout flat_layout(int W, int D) {
-    FlatLayout f;
-    f.mu = 0;
-    f.inv_sd = kIn;
-    f.W1 = 2 * kIn;
-    f.b1 = f.W1 + (int64_t)W * kIn;
-    f.Wl = f.b1 + W;
-    f.bl = 0;
-    f.wo = f.Wl + (int64_t)(D - 1) * (W * W + W);
-    f.bo = f.wo + W;
-    f.escale = f.bo + 1;
-    f.eshift = f.escale + 1;
-    f.total = f.eshift + 1;
-    return f;
-}
-
 __global__ void k_prepare_f32(const float* __restrict__ flat, int W, int D, float* __restrict__ out) {
     const FlatLayout f = flat_layout(W, D);
     const F32Layout L = f32_layout(W, D);
@@ -105,26 +81,6 @@ struct NetArgs {
     FlatLayout fl;
     F32Layout pl;
     int W, D;
-};
-
-struct PairSrc {
-    // system mode
-    const int2* pairs;
-    const int* n_pairs_ptr;
-    const float4* pos;
-    const float4* quat;
-    float3 L, invL;
-    // explicit mode
-    const float4* cfg;  // 2 float4 per pair
-    int64_t n_explicit;
-};
-
-struct PairDst {
-    float4* F;   // system: (F_j, E)  explicit: out rows of 3 float4
-    float4* ti;
-    float4* tj;
-    float4* out;   // explicit mode: n x 3 float4
-    float4* grad;  // explicit mode (nullable): n x 2 float4
 };
 
 __device__ inline float sigmoidf_(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
@@ -170,8 +126,10 @@ __global__ void __launch_bounds__(256, 1)
     float* bias = misc + 32;                   // D x W
     float* wo = bias + (size_t)D * W;          // W
 
-    constexpr int NTO = W / 8;
-    const int to = threadIdx.x % NTO, tp = threadIdx.x / NTO;
+    // pairs vary fastest across a warp: the [unit][pair] stores of a warp hit
+    // consecutive addresses and the weight loads are broadcasts
+    constexpr int NTP = P / 4;
+    const int tp = threadIdx.x % NTP, to = threadIdx.x / NTP;
     const int p0 = tp * 4, o0 = to * 8;
     const float* flat = net.flat;
     for (int t = threadIdx.x; t < kIn; t += blockDim.x) {
@@ -192,38 +150,11 @@ __global__ void __launch_bounds__(256, 1)
         // ---------------- prologue: features of pair p (threads 0..P-1)
         const int p = threadIdx.x;
         const int64_t gp = tile * P + p;
-        bool valid = false;
-        float3 s = make_float3(5.f, 0.f, 0.f);
-        float4 qc = make_float4(1.f, 0.f, 0.f, 0.f);
-        float4 qi = make_float4(1.f, 0.f, 0.f, 0.f);
-        float sgn = 1.f, rho = 5.f;
+        const bool valid = p < P && gp < n_total;
+        const PairGeom geo = load_pair<SYSTEM>(src, gp, valid);
         if (p < P) {
-            if (gp < n_total) {
-                valid = true;
-                float4 qr;
-                if (SYSTEM) {
-                    const int2 ij = src.pairs[gp];
-                    const float4 pi = src.pos[ij.x], pj = src.pos[ij.y];
-                    qi = src.quat[ij.x];
-                    const float4 qj = src.quat[ij.y];
-                    const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z),
-                                               src.L, src.invL);
-                    s = mulT(qmat(qi), R);
-                    qr = qmul(qconj(qi), qj);
-                } else {
-                    const float4 c0 = src.cfg[2 * gp], c1 = src.cfg[2 * gp + 1];
-                    s = make_float3(c0.x, c0.y, c0.z);
-                    qr = c1;
-                }
-                if (qr.x < 0.f) sgn = -1.f;
-                else if (qr.x == 0.f) {
-                    const float first = qr.y != 0.f ? qr.y : (qr.z != 0.f ? qr.z : qr.w);
-                    sgn = first < 0.f ? -1.f : 1.f;
-                }
-                qc = make_float4(sgn * qr.x, sgn * qr.y, sgn * qr.z, sgn * qr.w);
-                rho = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
-            }
-            const float x[kIn] = {s.x, s.y, s.z, qc.x, qc.y, qc.z, qc.w, rho, 1.f / rho, rho * rho};
+            float x[kIn];
+            raw_features(geo, x);
 #pragma unroll
             for (int k = 0; k < kIn; ++k) Xs[k * P + p] = (x[k] - misc[k]) * misc[16 + k];
 #pragma unroll
@@ -315,39 +246,11 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncthreads();
         // ---------------- geometric adjoint (threads 0..P-1)
-        if (p < P && valid) {
+        if (valid) {
             float gx[kIn];
 #pragma unroll
             for (int k = 0; k < kIn; ++k) gx[k] = e_scale * Xs[k * P + p] * misc[16 + k];
-            const float inv_rho = 1.f / rho;
-            const float gr = (gx[7] - gx[8] * inv_rho * inv_rho + 2.f * rho * gx[9]) * inv_rho;
-            const float3 Gs = make_float3(gx[0] + gr * s.x, gx[1] + gr * s.y, gx[2] + gr * s.z);
-            const float Gw = gx[3];
-            const float3 Gv = make_float3(gx[4], gx[5], gx[6]);
-            const float w = qc.x;
-            const float3 v = make_float3(qc.y, qc.z, qc.w);
-            const float3 vxG = cross3(v, Gv);
-            const float3 tj = make_float3(-0.5f * (-Gw * v.x + w * Gv.x + vxG.x),
-                                          -0.5f * (-Gw * v.y + w * Gv.y + vxG.y),
-                                          -0.5f * (-Gw * v.z + w * Gv.z + vxG.z));
-            const float3 sxG = cross3(s, Gs);
-            const float3 ti = make_float3(sxG.x - tj.x, sxG.y - tj.y, sxG.z - tj.z);
-            const float3 Fj = make_float3(-Gs.x, -Gs.y, -Gs.z);
-            if (SYSTEM) {
-                const Mat3 Ri = qmat(qi);
-                const float3 a = mul(Ri, Fj), b = mul(Ri, ti), c = mul(Ri, tj);
-                dst.F[gp] = make_float4(a.x, a.y, a.z, E);
-                dst.ti[gp] = make_float4(b.x, b.y, b.z, 0.f);
-                dst.tj[gp] = make_float4(c.x, c.y, c.z, 0.f);
-            } else {
-                dst.out[3 * gp] = make_float4(Fj.x, Fj.y, Fj.z, E);
-                dst.out[3 * gp + 1] = make_float4(ti.x, ti.y, ti.z, 0.f);
-                dst.out[3 * gp + 2] = make_float4(tj.x, tj.y, tj.z, 0.f);
-                if (dst.grad) {
-                    dst.grad[2 * gp] = make_float4(Gs.x, Gs.y, Gs.z, 0.f);
-                    dst.grad[2 * gp + 1] = make_float4(sgn * Gw, sgn * Gv.x, sgn * Gv.y, sgn * Gv.z);
-                }
-            }
+            write_pair_outputs<SYSTEM>(dst, gp, geo, gx, E);
         }
         __syncthreads();
     }
@@ -372,7 +275,7 @@ static rb_status launch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms, c
     if (smem > 227 * 1024) return fail(RB_ENOTSUP, "network too deep for the FP32 kernel");
     NetArgs net;
     net.flat = m->params;
-    net.prep = reinterpret_cast<const float*>(m->tc_weights);
+    net.prep = m->f32_prep;
     net.fl = flat_layout(m->width, m->depth);
     net.pl = f32_layout(m->width, m->depth);
     net.W = m->width;
@@ -395,7 +298,7 @@ static rb_status dispatch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms,
 
 rb_status check_mlp(const rb_mlp* m) {
     if (!m) return fail(RB_EINVAL, "null network");
-    if (!m->params || !m->tc_weights) return fail(RB_EINVAL, "network parameters not set");
+    if (!m->params || !m->f32_prep) return fail(RB_EINVAL, "network parameters not set");
     return RB_OK;
 }
 
@@ -408,7 +311,8 @@ static int sm_count() {
 
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     RB_TRY(check_mlp(m));
-    if (precision != RB_FP32) return fail(RB_ENOTSUP, "BF16 network path not built yet");
+    if (precision == RB_BF16) return nn_tc_system_async(s, m);
+    if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
     src.pairs = s->pl.pairs;
     src.n_pairs_ptr = s->pl.n_pairs;
@@ -448,8 +352,10 @@ rb_status rb_mlp_create(int32_t width, int32_t depth, void* stream, rb_mlp** out
     m->depth = depth;
     m->n_params = flat_layout(width, depth).total;
     cudaError_t e = cudaMalloc(&m->params, sizeof(float) * m->n_params);
+    if (e == cudaSuccess) e = cudaMalloc(&m->status_dev, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->status_dev, 0, sizeof(unsigned), m->stream);
     if (e != cudaSuccess) {
-        delete m;
+        rb_mlp_destroy(m);
         return cuda_fail(e, "cudaMalloc (network)");
     }
     *out = m;
@@ -460,7 +366,9 @@ rb_status rb_mlp_destroy(rb_mlp* m) {
     if (!m) return RB_OK;
     if (m->stream) cudaStreamSynchronize(m->stream);
     if (m->params) cudaFree(m->params);
-    if (m->tc_weights) cudaFree(m->tc_weights);
+    if (m->f32_prep) cudaFree(m->f32_prep);
+    if (m->bf16_img) cudaFree(m->bf16_img);
+    if (m->status_dev) cudaFree(m->status_dev);
     delete m;
     return RB_OK;
 }
@@ -472,13 +380,11 @@ rb_status rb_mlp_set_params(rb_mlp* m, const float* flat, int64_t n, int32_t fro
                             from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             m->stream));
     const F32Layout L = f32_layout(m->width, m->depth);
-    if (!m->tc_weights) {
-        RB_CUDA(cudaMalloc(&m->tc_weights, sizeof(float) * L.total));
-        m->tc_bytes = sizeof(float) * L.total;
-    }
+    if (!m->f32_prep) RB_CUDA(cudaMalloc(&m->f32_prep, sizeof(float) * L.total));
     k_prepare_f32<<<sm_count() * 4, 256, 0, m->stream>>>(m->params, m->width, m->depth,
-                                                         reinterpret_cast<float*>(m->tc_weights));
+                                                         m->f32_prep);
     RB_CUDA(cudaGetLastError());
+    RB_TRY(nn_tc_prepare(m));
     m->version++;
     return RB_OK;
 }
@@ -497,7 +403,10 @@ rb_status rb_nn_pairs(const rb_mlp* m, int32_t precision, int64_t n, const float
     RB_TRY(check_mlp(m));
     if (n < 0 || (n > 0 && (!cfg || !out))) return fail(RB_EINVAL, "bad pair arrays");
     if (n == 0) return RB_OK;
-    if (precision != RB_FP32) return fail(RB_ENOTSUP, "BF16 network path not built yet");
+    if (precision == RB_BF16)
+        return nn_tc_pairs_async(m, n, reinterpret_cast<const float4*>(cfg),
+                                 reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(grad_out));
+    if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
     src.cfg = reinterpret_cast<const float4*>(cfg);
     src.n_explicit = n;
@@ -505,6 +414,19 @@ rb_status rb_nn_pairs(const rb_mlp* m, int32_t precision, int64_t n, const float
     dst.out = reinterpret_cast<float4*>(out);
     dst.grad = reinterpret_cast<float4*>(grad_out);
     return dispatch_f32<false>(m, m->stream, sm_count(), src, dst);
+}
+
+rb_status rb_mlp_sync(const rb_mlp* m) {
+    if (!m) return fail(RB_EINVAL, "null network");
+    unsigned st = 0;
+    RB_CUDA(cudaMemcpyAsync(&st, m->status_dev, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            m->stream));
+    RB_CUDA(cudaStreamSynchronize(m->stream));
+    if (st) {
+        RB_CUDA(cudaMemsetAsync(m->status_dev, 0, sizeof(unsigned), m->stream));
+        return fail(RB_EFAULT, "tensor-core network kernel timed out waiting for an MMA");
+    }
+    return RB_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,166 @@
+// Pair-network pieces shared by the FP32 (nn.cu) and tensor-core (nn_tc.cu)
+// kernels: parameter layout, pair sources/destinations, the 10 input features
+// and the geometric adjoint from dE/dx to forces and torques.
+//
+// Paper mapping: the pair configuration (separation in the frame of body 1 and
+// the relative orientation, Methods "U = g(x, Omega)"; SI Sec. 1 uses p and q
+// as the raw configuration) and forces/torques as energy gradients (SI Sec. 6:
+// f = -dE/dx, tau = -dE/dtheta), differentiated exactly:
+//   x     = [s, q_c, rho, 1/rho, rho^2], s = R(q_i)^T R_ij, q_c = sign q_i^* q_j
+//   G_s   = dE/ds + (E_rho - E_{1/rho}/rho^2 + 2 rho E_{rho^2}) s / rho
+//   F_j   = -G_s,  tau_j = -1/2 (-G_w v + w G_v + v x G_v) with q_c = (w, v),
+//   tau_i = s x G_s - tau_j           (all in the frame of body i)
+#pragma once
+
+#include "rb_internal.cuh"
+
+namespace rb {
+
+constexpr int kIn = 10;
+constexpr int kInPad = 16;
+
+// Offsets in the flat FP32 parameter vector (layout documented in rb.h).
+struct FlatLayout {
+    int64_t mu, inv_sd, W1, b1, Wl, wo, bo, escale, eshift, total;
+    __host__ __device__ int64_t W_(int l, int W) const {
+        return Wl + (int64_t)(l - 2) * (W * W + W);
+    }
+    __host__ __device__ int64_t b_(int l, int W) const {
+        return l == 1 ? b1 : Wl + (int64_t)(l - 2) * (W * W + W) + W * W;
+    }
+};
+__host__ __device__ inline FlatLayout flat_layout(int W, int D) {
+    FlatLayout f;
+    f.mu = 0;
+    f.inv_sd = kIn;
+    f.W1 = 2 * kIn;
+    f.b1 = f.W1 + (int64_t)W * kIn;
+    f.Wl = f.b1 + W;
+    f.wo = f.Wl + (int64_t)(D - 1) * (W * W + W);
+    f.bo = f.wo + W;
+    f.escale = f.bo + 1;
+    f.eshift = f.escale + 1;
+    f.total = f.eshift + 1;
+    return f;
+}
+
+struct PairSrc {
+    // system mode: pairs of bodies
+    const int2* pairs;
+    const int* n_pairs_ptr;
+    const float4* pos;
+    const float4* quat;
+    float3 L, invL;
+    // explicit mode: configurations in the frame of body i, 2 float4 per pair
+    const float4* cfg;
+    int64_t n_explicit;
+};
+
+struct PairDst {
+    float4* F;     // system: (F_j, E) per pair, space frame
+    float4* ti;    // system: (tau_i, 0)
+    float4* tj;    // system: (tau_j, 0)
+    float4* out;   // explicit: n x 3 float4 (F_j, E), (tau_i, 0), (tau_j, 0), body-i frame
+    float4* grad;  // explicit (nullable): n x 2 float4 (dE/ds, 0), dE/dq_rel (raw sign)
+};
+
+struct PairGeom {
+    float3 s;
+    float4 qc;  // canonical relative orientation
+    float4 qi;  // orientation of body i (identity in explicit mode)
+    float sgn;
+    float rho;
+};
+
+template <bool SYSTEM>
+__device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid) {
+    PairGeom g;
+    g.s = make_float3(5.f, 0.f, 0.f);
+    g.qc = make_float4(1.f, 0.f, 0.f, 0.f);
+    g.qi = make_float4(1.f, 0.f, 0.f, 0.f);
+    g.sgn = 1.f;
+    float4 qr = g.qc;
+    if (valid) {
+        if (SYSTEM) {
+            const int2 ij = src.pairs[gp];
+            const float4 pi = src.pos[ij.x], pj = src.pos[ij.y];
+            g.qi = src.quat[ij.x];
+            const float4 qj = src.quat[ij.y];
+            const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), src.L,
+                                       src.invL);
+            g.s = mulT(qmat(g.qi), R);
+            qr = qmul(qconj(g.qi), qj);
+        } else {
+            const float4 c0 = src.cfg[2 * gp], c1 = src.cfg[2 * gp + 1];
+            g.s = make_float3(c0.x, c0.y, c0.z);
+            qr = c1;
+        }
+        if (qr.x < 0.f) {
+            g.sgn = -1.f;
+        } else if (qr.x == 0.f) {
+            const float first = qr.y != 0.f ? qr.y : (qr.z != 0.f ? qr.z : qr.w);
+            g.sgn = first < 0.f ? -1.f : 1.f;
+        }
+        g.qc = make_float4(g.sgn * qr.x, g.sgn * qr.y, g.sgn * qr.z, g.sgn * qr.w);
+    }
+    g.rho = sqrtf(g.s.x * g.s.x + g.s.y * g.s.y + g.s.z * g.s.z);
+    return g;
+}
+
+__device__ inline void raw_features(const PairGeom& g, float (&x)[kIn]) {
+    x[0] = g.s.x;
+    x[1] = g.s.y;
+    x[2] = g.s.z;
+    x[3] = g.qc.x;
+    x[4] = g.qc.y;
+    x[5] = g.qc.z;
+    x[6] = g.qc.w;
+    x[7] = g.rho;
+    x[8] = 1.f / g.rho;
+    x[9] = g.rho * g.rho;
+}
+
+// gx = dE/dx (raw features).  Writes the outputs of pair gp.
+template <bool SYSTEM>
+__device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const PairGeom& g,
+                                          const float (&gx)[kIn], float E) {
+    const float3 s = g.s;
+    const float inv_rho = 1.f / g.rho;
+    const float gr = (gx[7] - gx[8] * inv_rho * inv_rho + 2.f * g.rho * gx[9]) * inv_rho;
+    const float3 Gs = make_float3(gx[0] + gr * s.x, gx[1] + gr * s.y, gx[2] + gr * s.z);
+    const float Gw = gx[3];
+    const float3 Gv = make_float3(gx[4], gx[5], gx[6]);
+    const float w = g.qc.x;
+    const float3 v = make_float3(g.qc.y, g.qc.z, g.qc.w);
+    const float3 vxG = cross3(v, Gv);
+    const float3 tj = make_float3(-0.5f * (-Gw * v.x + w * Gv.x + vxG.x),
+                                  -0.5f * (-Gw * v.y + w * Gv.y + vxG.y),
+                                  -0.5f * (-Gw * v.z + w * Gv.z + vxG.z));
+    const float3 sxG = cross3(s, Gs);
+    const float3 ti = make_float3(sxG.x - tj.x, sxG.y - tj.y, sxG.z - tj.z);
+    const float3 Fj = make_float3(-Gs.x, -Gs.y, -Gs.z);
+    if (SYSTEM) {
+        const Mat3 Ri = qmat(g.qi);
+        const float3 a = mul(Ri, Fj), b = mul(Ri, ti), c = mul(Ri, tj);
+        dst.F[gp] = make_float4(a.x, a.y, a.z, E);
+        dst.ti[gp] = make_float4(b.x, b.y, b.z, 0.f);
+        dst.tj[gp] = make_float4(c.x, c.y, c.z, 0.f);
+    } else {
+        dst.out[3 * gp] = make_float4(Fj.x, Fj.y, Fj.z, E);
+        dst.out[3 * gp + 1] = make_float4(ti.x, ti.y, ti.z, 0.f);
+        dst.out[3 * gp + 2] = make_float4(tj.x, tj.y, tj.z, 0.f);
+        if (dst.grad) {
+            const float sg = g.sgn;
+            dst.grad[2 * gp] = make_float4(Gs.x, Gs.y, Gs.z, 0.f);
+            dst.grad[2 * gp + 1] = make_float4(sg * Gw, sg * Gv.x, sg * Gv.y, sg * Gv.z);
+        }
+    }
+}
+
+// nn_tc.cu
+rb_status nn_tc_prepare(rb_mlp* m);
+rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m);
+rb_status nn_tc_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
+                            float4* grad);
+
+}  // namespace rb

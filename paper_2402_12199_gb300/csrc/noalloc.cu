@@ -46,7 +46,9 @@ constexpr size_t kOffLowerNbr =
     kOffHalfNbr + align256(sizeof(int) * kNoAllocMaxBodies * kNoAllocMaxNeighbors);
 constexpr size_t kOffHalfOff =
     kOffLowerNbr + align256(sizeof(int) * kNoAllocMaxBodies * kNoAllocMaxNeighbors);
-constexpr size_t kOffPairs = kOffHalfOff + align256(sizeof(int) * (kNoAllocMaxBodies + 1));
+constexpr size_t kOffLocalOff = kOffHalfOff + align256(sizeof(int) * (kNoAllocMaxBodies + 1));
+constexpr size_t kOffBlockSum = kOffLocalOff + align256(sizeof(int) * kNoAllocMaxBodies);
+constexpr size_t kOffPairs = kOffBlockSum + align256(sizeof(int) * (kNoAllocMaxBodies / 1024 + 2));
 constexpr size_t kOffPairF = kOffPairs + align256(sizeof(int2) * kNoAllocMaxPairs);
 constexpr size_t kOffPairTi = kOffPairF + align256(sizeof(float4) * kNoAllocMaxPairs);
 constexpr size_t kOffPairTj = kOffPairTi + align256(sizeof(float4) * kNoAllocMaxPairs);
@@ -169,6 +171,8 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     s.pl.half_nbr = reinterpret_cast<int*>(base + kOffHalfNbr);
     s.pl.lower_nbr = reinterpret_cast<int*>(base + kOffLowerNbr);
     s.pl.half_off = reinterpret_cast<int*>(base + kOffHalfOff);
+    s.pl.local_off = reinterpret_cast<int*>(base + kOffLocalOff);
+    s.pl.block_sum = reinterpret_cast<int*>(base + kOffBlockSum);
     s.pl.pairs = reinterpret_cast<int2*>(base + kOffPairs);
     s.pair_F = reinterpret_cast<float4*>(base + kOffPairF);
     s.pair_ti = reinterpret_cast<float4*>(base + kOffPairTi);

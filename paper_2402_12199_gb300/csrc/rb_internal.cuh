@@ -33,6 +33,7 @@ enum : unsigned {
     ST_CELL_OVERFLOW = 1u,
     ST_NBR_OVERFLOW = 2u,
     ST_NONFINITE = 4u,
+    ST_TC_TIMEOUT = 8u,   // a tensor-core kernel gave up waiting for an MMA
 };
 
 constexpr int kMaxBeads = 256;
@@ -97,6 +98,8 @@ struct PairList {
     int* lower_count = nullptr; // N
     int* lower_nbr = nullptr;   // N x max_nbr (j < i, sorted), replaced by pair ids
     int* half_off = nullptr;    // N + 1
+    int* local_off = nullptr;   // N (offsets inside 1024-body scan blocks)
+    int* block_sum = nullptr;   // N / 1024 + 1 (block totals, then block prefixes)
     int2* pairs = nullptr;      // cap_pairs
     int* n_pairs = nullptr;     // device scalar
 };
@@ -127,10 +130,10 @@ struct rb_mlp {
     int width = 0, depth = 0;
     int64_t n_params = 0;
     float* params = nullptr;      // flat FP32 (device)
-    void* tc_weights = nullptr;   // BF16 tensor-core copies (device), built lazily
-    size_t tc_bytes = 0;
+    float* f32_prep = nullptr;    // transposed/padded FP32 copies for the SIMT kernel
+    void* bf16_img = nullptr;     // BF16 shared-memory image for the tensor-core kernel
+    unsigned* status_dev = nullptr;  // sticky device-side error bits of pair-level calls
     uint64_t version = 1;         // bumped on every set_params
-    uint64_t tc_version = 0;
 };
 
 struct rb_system {

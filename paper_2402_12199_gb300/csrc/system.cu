@@ -68,82 +68,124 @@ __device__ inline void sort_row(int* row, int n) {
     }
 }
 
-// One thread per body: scan the neighbouring cells, keep j with minimum-image
-// |p_j - p_i| < Rc.  j > i goes to the half row (pairs owned by i), j < i to
-// the lower row (pairs owned by j, mirrored for the reduction).  Rows are
-// sorted by j so the pair order does not depend on the cell fill order.
+// One warp per body i: lane c < 27 scans one cell of the 3x3x3 stencil (lanes
+// whose cell repeats a lower lane's, when a box side holds fewer than 3 cells,
+// stay idle) and keeps j with minimum-image |p_j - p_i| < Rc.  j > i goes to
+// the half row (pairs owned by i), j < i to the lower row (pairs owned by j,
+// mirrored for the reduction).  Hits are appended with warp ballots, then
+// lane 0 sorts each row by j so the list does not depend on the cell fill
+// order or on the lane interleaving.
 __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, float3 invL,
                              float3 invw, int3 nc, const int* __restrict__ count,
                              const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
                              int* __restrict__ half_count, int* __restrict__ half_nbr,
                              int* __restrict__ lower_count, int* __restrict__ lower_nbr,
                              unsigned* status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
-    float4 p = pos[i];
-    float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
-    int c[3] = {min(max(int(x * invw.x), 0), nc.x - 1), min(max(int(y * invw.y), 0), nc.y - 1),
-                min(max(int(z * invw.z), 0), nc.z - 1)};
-    int n_[3] = {nc.x, nc.y, nc.z};
-    int lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-        if (n_[a] >= 3) { lo[a] = -1; hi[a] = 1; }
-        else if (n_[a] == 2) { lo[a] = 0; hi[a] = 1; }
-        else { lo[a] = 0; hi[a] = 0; }
+    const float4 p = pos[i];
+    const float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
+    const int c[3] = {min(max(int(x * invw.x), 0), nc.x - 1), min(max(int(y * invw.y), 0), nc.y - 1),
+                      min(max(int(z * invw.z), 0), nc.z - 1)};
+    const int n_[3] = {nc.x, nc.y, nc.z};
+    const int off[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+    bool active = lane < 27;
+    int cell = 0;
+    for (int a = 2; a >= 0; --a) {
+        const int o = off[a];
+        if (n_[a] == 1 && o != 0) active = false;
+        if (n_[a] == 2 && o == -1) active = false;
+        cell = cell * n_[a] + (c[a] + o + n_[a]) % n_[a];
     }
+    const int n = active ? min(count[cell], cap) : 0;
+    int nmax = n;
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
     int* hrow = half_nbr + (size_t)i * max_nbr;
     int* lrow = lower_nbr + (size_t)i * max_nbr;
     int nh = 0, nl = 0;
-    const float3 pi = make_float3(p.x, p.y, p.z);
-    for (int oz = lo[2]; oz <= hi[2]; ++oz) {
-        int cz = (c[2] + oz + n_[2]) % n_[2];
-        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
-            int cy = (c[1] + oy + n_[1]) % n_[1];
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                int cx = (c[0] + ox + n_[0]) % n_[0];
-                int cell = (cz * n_[1] + cy) * n_[0] + cx;
-                int n = min(count[cell], cap);
-                const int* cb = bodies + (size_t)cell * cap;
-                for (int s = 0; s < n; ++s) {
-                    int j = cb[s];
-                    if (j == i) continue;
-                    float4 q = pos[j];
-                    float3 d = min_image(make_float3(q.x - pi.x, q.y - pi.y, q.z - pi.z), L, invL);
-                    float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-                    if (r2 < Rc2) {
-                        if (j > i) {
-                            if (nh < max_nbr) hrow[nh] = j;
-                            ++nh;
-                        } else {
-                            if (nl < max_nbr) lrow[nl] = j;
-                            ++nl;
-                        }
-                    }
-                }
+    const unsigned lt = (1u << lane) - 1u;
+    const int* cb = bodies + (size_t)cell * cap;
+    for (int s = 0; s < nmax; ++s) {
+        int j = -1;
+        bool hit = false;
+        if (s < n) {
+            j = cb[s];
+            if (j != i) {
+                const float4 q = pos[j];
+                const float3 d = min_image(make_float3(q.x - p.x, q.y - p.y, q.z - p.z), L, invL);
+                hit = d.x * d.x + d.y * d.y + d.z * d.z < Rc2;
             }
         }
+        const unsigned bh = __ballot_sync(0xffffffffu, hit && j > i);
+        const unsigned bl = __ballot_sync(0xffffffffu, hit && j < i);
+        if (hit && j > i) {
+            const int k = nh + __popc(bh & lt);
+            if (k < max_nbr) hrow[k] = j;
+        }
+        if (hit && j < i) {
+            const int k = nl + __popc(bl & lt);
+            if (k < max_nbr) lrow[k] = j;
+        }
+        nh += __popc(bh);
+        nl += __popc(bl);
     }
     if (nh + nl > max_nbr) {
-        atomicOr(status, ST_NBR_OVERFLOW);
+        if (lane == 0) atomicOr(status, ST_NBR_OVERFLOW);
         nh = min(nh, max_nbr);
         nl = min(nl, max_nbr);
     }
-    sort_row(hrow, nh);
-    sort_row(lrow, nl);
-    half_count[i] = nh;
-    lower_count[i] = nl;
+    __syncwarp();
+    if (lane == 0) {
+        sort_row(hrow, nh);
+        half_count[i] = nh;
+    } else if (lane == 1) {
+        sort_row(lrow, nl);
+        lower_count[i] = nl;
+    }
 }
 
-// Exclusive scan of the half-row counts (single block; each thread owns a
-// contiguous chunk).  off[N] and *total receive the number of pairs.
-__global__ void k_scan(const int* __restrict__ cnt, int N, int* __restrict__ off, int* total,
-                       int64_t cap_pairs, unsigned* status) {
+// Exclusive scan of the half-row counts in two levels: k_scan_local scans
+// 1024-body blocks (local offsets + one total per block), k_scan_top scans the
+// block totals (single block) and stores the pair count; k_pair_emit adds the
+// block prefix.  All sums are exact integer sums.
+constexpr int kScanBlock = 1024;
+
+__global__ void k_scan_local(const int* __restrict__ cnt, int N, int* __restrict__ local_off,
+                             int* __restrict__ block_sum) {
+    __shared__ int warp_tot[32];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = i < N ? cnt[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+    if (i < N) local_off[i] = before;
+    if (threadIdx.x == kScanBlock - 1) block_sum[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void k_scan_top(int* __restrict__ block_sum, int nb, int N, int* __restrict__ half_off,
+                           int* total, int64_t cap_pairs, unsigned* status) {
     __shared__ int sh[1024];
     const int t = threadIdx.x;
-    const int chunk = (N + 1023) / 1024;
-    const int b = t * chunk, e = min(b + chunk, N);
+    const int chunk = (nb + 1023) / 1024;
+    const int b = t * chunk, e = min(b + chunk, nb);
     int sum = 0;
-    for (int k = b; k < e; ++k) sum += cnt[k];
+    for (int k = b; k < e; ++k) sum += block_sum[k];
     sh[t] = sum;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -154,8 +196,9 @@ __global__ void k_scan(const int* __restrict__ cnt, int N, int* __restrict__ off
     }
     int run = sh[t] - sum;
     for (int k = b; k < e; ++k) {
-        off[k] = run;
-        run += cnt[k];
+        const int c = block_sum[k];
+        block_sum[k] = run;  // exclusive prefix of block k
+        run += c;
     }
     if (t == 1023) {
         int tot = sh[1023];
@@ -163,7 +206,7 @@ __global__ void k_scan(const int* __restrict__ cnt, int N, int* __restrict__ off
             atomicOr(status, ST_NBR_OVERFLOW);
             tot = (int)cap_pairs;
         }
-        off[N] = tot;
+        half_off[N] = tot;
         *total = tot;
     }
 }
@@ -171,12 +214,14 @@ __global__ void k_scan(const int* __restrict__ cnt, int N, int* __restrict__ off
 // Emit the compact pair list and turn each lower-row entry j (< i) into the
 // index of pair (j, i) inside j's half row.
 __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_count,
-                            const int* __restrict__ half_nbr, const int* __restrict__ half_off,
+                            const int* __restrict__ half_nbr, const int* __restrict__ local_off,
+                            const int* __restrict__ block_prefix, int* __restrict__ half_off,
                             const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
                             int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int off = half_off[i];
+    const int off = local_off[i] + block_prefix[i / kScanBlock];
+    half_off[i] = off;
     const int n = half_count[i];
     const int* hrow = half_nbr + (size_t)i * max_nbr;
     for (int k = 0; k < n; ++k)
@@ -193,11 +238,12 @@ __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_cou
             if (v == i) { found = mid; break; }
             if (v < i) a = mid + 1; else b = mid - 1;
         }
-        if (found < 0 || half_off[j] + found >= cap_pairs) {
+        const int offj = local_off[j] + block_prefix[j / kScanBlock];
+        if (found < 0 || offj + found >= cap_pairs) {
             atomicOr(status, ST_NBR_OVERFLOW);
             lrow[m] = -1;
         } else {
-            lrow[m] = half_off[j] + found;
+            lrow[m] = offj + found;
         }
     }
 }
@@ -397,15 +443,19 @@ rb_status build_pairs_async(rb_system* s) {
     k_cell_assign<<<blocks_for(N, 256), 256, 0, s->stream>>>(s->pos, N, L, invL, invw, nc,
                                                              s->cells.count, s->cells.bodies,
                                                              s->cells.cap, s->status_dev);
-    k_pair_build<<<blocks_for(N, 128), 128, 0, s->stream>>>(
+    k_pair_build<<<blocks_for((int64_t)N * 32, 256), 256, 0, s->stream>>>(
         s->pos, N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap,
         s->Rc * s->Rc, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.lower_count,
         s->pl.lower_nbr, s->status_dev);
-    k_scan<<<1, 1024, 0, s->stream>>>(s->pl.half_count, N, s->pl.half_off, s->pl.n_pairs,
-                                      s->pl.cap_pairs, s->status_dev);
+    const int nb = (N + kScanBlock - 1) / kScanBlock;
+    k_scan_local<<<nb, kScanBlock, 0, s->stream>>>(s->pl.half_count, N, s->pl.local_off,
+                                                   s->pl.block_sum);
+    k_scan_top<<<1, 1024, 0, s->stream>>>(s->pl.block_sum, nb, N, s->pl.half_off, s->pl.n_pairs,
+                                          s->pl.cap_pairs, s->status_dev);
     k_pair_emit<<<blocks_for(N, 256), 256, 0, s->stream>>>(
-        N, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.half_off, s->pl.lower_count,
-        s->pl.lower_nbr, s->pl.pairs, s->pl.cap_pairs, s->status_dev);
+        N, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.local_off, s->pl.block_sum,
+        s->pl.half_off, s->pl.lower_count, s->pl.lower_nbr, s->pl.pairs, s->pl.cap_pairs,
+        s->status_dev);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -593,6 +643,8 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     ALLOC(s->pl.half_nbr, sizeof(int) * N * mn);
     ALLOC(s->pl.lower_nbr, sizeof(int) * N * mn);
     ALLOC(s->pl.half_off, sizeof(int) * (N + 1));
+    ALLOC(s->pl.local_off, sizeof(int) * N);
+    ALLOC(s->pl.block_sum, sizeof(int) * ((N + 1023) / 1024 + 1));
     ALLOC(s->pl.pairs, sizeof(int2) * cp);
     ALLOC(s->pl.n_pairs, sizeof(int));
     ALLOC(s->pair_F, sizeof(float4) * cp);
@@ -633,7 +685,8 @@ rb_status rb_destroy_system(rb_system* s) {
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     void* ptrs[] = {s->tmpl_dev, s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
                     s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
-                    s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.pairs, s->pl.n_pairs,
+                    s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
+                    s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
                     s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
