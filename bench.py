@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="beads,nn_fp32")
+    ap.add_argument("--paths", default="beads,nn_fp32,nn_bf16")
     ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
     ap.add_argument("--ref-sample-pairs", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -312,6 +312,33 @@ def main():
                 "kernel_ms": d_ms, "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
                 "flops_per_launch": flops}
 
+    roof_nn = None
+    if "nn_bf16" in systems:
+        s = systems["nn_bf16"]
+        s.build_pairs()
+        for _ in range(3):
+            s.eval_pairs(api.RB_PATH_NN, mlp, "bf16")
+        durs = []
+        for _ in range(10):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.eval_pairs(api.RB_PATH_NN, mlp, "bf16")
+            b.record(stream)
+            durs.append((a, b))
+        torch.cuda.synchronize()
+        d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
+        # tensor-core work actually issued per 128-pair tile: layer-1 K padded to 64,
+        # reverse output N padded to 16
+        tc_flops = 2.0 * 128 * (128 * 64 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
+        flops = tc_flops / 128 * n_pairs["nn_bf16"]
+        achieved = flops / (d_ms * 1e-3) / 1e12
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        roof_nn = {"kernel": "k_nn_tc", "bound": "tensor", "achieved": achieved, "peak": peak,
+                   "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+                   "peak_source": f"bf16_tflops_sustained ({how})", "flops_per_launch": flops,
+                   "mufu_per_pair": 6 * WIDTH, "note": "one tanh.approx per SiLU evaluation"}
+
     # ---- end to end through the public API with host buffers
     pinned = {k: torch.from_numpy(st[k]).pin_memory() for k in ("pos", "quat", "vel", "angmom")}
     outs = {k: torch.empty((N_BODIES, 4), dtype=torch.float32).pin_memory()
@@ -357,7 +384,7 @@ def main():
                                    f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU random init",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
-            "paths": path_info, "roofline": roof, "cpu_baseline": cpu,
+            "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "cpu_baseline": cpu,
             "e2e": {"value": world * pairs_per_step / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * 7 * len(paths), "clocks": clocks,

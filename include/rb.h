@@ -218,6 +218,51 @@ rb_status rb_forces_nn(rb_system* sys, const rb_mlp* mlp, int32_t precision, flo
 rb_status rb_nn_pairs(const rb_mlp* mlp, int32_t precision, int64_t n, const float* cfg,
                       float* out, float* grad_out);
 
+/* ------------------------------------------------------------------ training */
+
+/* Training pairs drawn on the device and labelled by the bead sum (the paper
+ * samples pair configurations from bead-level simulations and fits the energy
+ * network to them: Methods; SI Sec. 1).  Body i sits at the origin with
+ * identity orientation; per sample six uniforms in [0, 1) (device, n x 6):
+ * u0, u1 -> direction (z = 2 u0 - 1, phi = 2 pi u1); u2, u3, u4 -> q_j by
+ * Shoemake's construction (sqrt(1-u2) sin 2pi u3, sqrt(1-u2) cos 2pi u3,
+ * sqrt(u2) sin 2pi u4, sqrt(u2) cos 2pi u4) as (s, i, j, k); u5 -> separation
+ * rho = rho_c + u5 (Rc - rho_c), where rho_c (contact) is the separation along
+ * the direction at which the smallest bead-bead distance equals sigma (40
+ * bisection steps on [0, Rc]).  Outputs (device): cfg n x 8 as rb_nn_pairs'
+ * input, labels n x 12 as rb_nn_pairs' output (bead-sum E, F_j, tau_i, tau_j in
+ * the frame of body i), rho_contact n (nullable).  Uses the body type and
+ * potential of `sys`; runs on its stream. */
+rb_status rb_sample_pairs(const rb_system* sys, int64_t n, const float* uniforms, float* cfg,
+                          float* labels, float* rho_contact);
+
+/* Trainer for `mlp`: Adam state and a workspace for batches of up to
+ * max_batch pairs.  Runs on the network's stream. */
+typedef struct rb_trainer rb_trainer;
+rb_status rb_trainer_create(rb_mlp* mlp, int64_t max_batch, float lr, float beta1, float beta2,
+                            float eps, rb_trainer** out);
+rb_status rb_trainer_destroy(rb_trainer* tr);
+
+/* Force-matching loss over a batch (device cfg n x 8, labels n x 12):
+ *   L = mean_b |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
+ *       + lam_E (E - E*)^2
+ * with the FP32 network's forces/torques (exact energy gradients), and its
+ * gradient with respect to the flat parameters (zero for mu, inv_sd, e_scale,
+ * e_shift, which are not trained).  grad_out: device, n_params (nullable);
+ * loss_host (nullable) synchronises. */
+rb_status rb_train_grad(rb_trainer* tr, int64_t batch, const float* cfg, const float* labels,
+                        float lam_tau, float lam_E, float* grad_out, double* loss_host);
+/* rb_train_grad followed by one Adam step on the trainable parameters. */
+rb_status rb_train_step(rb_trainer* tr, int64_t batch, const float* cfg, const float* labels,
+                        float lam_tau, float lam_E, double* loss_host);
+/* Weight gradient of sum_b [u_b . dE_hat_b/d(s, q_rel) + c_b E_hat_b] (E_hat:
+ * the network output before e_scale/e_shift) for device arrays cfg n x 8,
+ * u_cfg n x 8 (du_s xyz, 0, du_q wxyz), c n; grad_out device n_params.  This
+ * is the second-order product behind double backward through the network's
+ * input gradient. */
+rb_status rb_nn_weight_vjp(rb_trainer* tr, int64_t n, const float* cfg, const float* u_cfg,
+                           const float* c, float* grad_out);
+
 /* Wait for the network's stream and report sticky device-side errors of
  * rb_nn_pairs (RB_EFAULT if a tensor-core kernel gave up waiting for an MMA). */
 rb_status rb_mlp_sync(const rb_mlp* mlp);

@@ -78,6 +78,12 @@ SIGNATURES = {
     "rb_forces_nn": (I32, [P, P, I32, P, P, DP, DP]),
     "rb_nn_pairs": (I32, [P, I32, I64, P, P, P]),
     "rb_mlp_sync": (I32, [P]),
+    "rb_sample_pairs": (I32, [P, I64, P, P, P, P]),
+    "rb_trainer_create": (I32, [P, I64, F32, F32, F32, F32, ctypes.POINTER(P)]),
+    "rb_trainer_destroy": (I32, [P]),
+    "rb_train_grad": (I32, [P, I64, P, P, F32, F32, P, DP]),
+    "rb_train_step": (I32, [P, I64, P, P, F32, F32, DP]),
+    "rb_nn_weight_vjp": (I32, [P, I64, P, P, P, P]),
     "rb_tc_gemm_check": (I32, [I32, I32, P, P, P, P]),
 }
 

@@ -247,3 +247,65 @@ def tc_gemm_check(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     check(load().rb_tc_gemm_check(N, K, A.data_ptr(), B.data_ptr(), D.data_ptr(),
                                   torch.cuda.current_stream().cuda_stream))
     return D
+
+
+class Trainer:
+    """rb_trainer_create / rb_train_grad / rb_train_step / rb_nn_weight_vjp."""
+
+    def __init__(self, mlp: MLP, max_batch: int, lr: float = 1e-3, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8):
+        h = ctypes.c_void_p()
+        check(load().rb_trainer_create(mlp.handle, int(max_batch), lr, beta1, beta2, eps,
+                                       ctypes.byref(h)))
+        self._h = h
+        self.mlp = mlp
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().rb_trainer_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def grad(self, cfg: torch.Tensor, labels: torch.Tensor, lam_tau: float = 1.0,
+             lam_E: float = 0.0):
+        _dev(cfg, 8)
+        _dev(labels, 12)
+        g = torch.empty(self.mlp.n_params, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        check(load().rb_train_grad(self._h, cfg.shape[0], cfg.data_ptr(), labels.data_ptr(),
+                                   lam_tau, lam_E, g.data_ptr(), ctypes.byref(loss)))
+        return loss.value, g
+
+    def step(self, cfg: torch.Tensor, labels: torch.Tensor, lam_tau: float = 1.0,
+             lam_E: float = 0.0, want_loss: bool = True):
+        _dev(cfg, 8)
+        _dev(labels, 12)
+        loss = ctypes.c_double()
+        check(load().rb_train_step(self._h, cfg.shape[0], cfg.data_ptr(), labels.data_ptr(),
+                                   lam_tau, lam_E, ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def weight_vjp(self, cfg: torch.Tensor, u_cfg: torch.Tensor, c: torch.Tensor):
+        _dev(cfg, 8)
+        _dev(u_cfg, 8)
+        c = c.contiguous().float()
+        g = torch.empty(self.mlp.n_params, dtype=torch.float32, device="cuda")
+        check(load().rb_nn_weight_vjp(self._h, cfg.shape[0], cfg.data_ptr(), u_cfg.data_ptr(),
+                                      c.data_ptr(), g.data_ptr()))
+        return g
+
+
+def sample_pairs(system: System, uniforms: torch.Tensor):
+    """rb_sample_pairs: (cfg n x 8, labels n x 12, rho_contact n) on the device."""
+    _dev(uniforms, 6)
+    n = uniforms.shape[0]
+    cfg = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    lab = torch.empty((n, 12), dtype=torch.float32, device="cuda")
+    rc = torch.empty((n,), dtype=torch.float32, device="cuda")
+    check(load().rb_sample_pairs(system.handle, n, uniforms.data_ptr(), cfg.data_ptr(),
+                                 lab.data_ptr(), rc.data_ptr()))
+    return cfg, lab, rc

@@ -302,6 +302,30 @@ rb_status check_mlp(const rb_mlp* m) {
     return RB_OK;
 }
 
+static int sm_count();
+
+rb_status nn_pairs_f32_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
+                             float4* grad) {
+    PairSrc src{};
+    src.cfg = cfg;
+    src.n_explicit = n;
+    PairDst dst{};
+    dst.out = out;
+    dst.grad = grad;
+    return dispatch_f32<false>(m, m->stream, sm_count(), src, dst);
+}
+
+rb_status mlp_refresh(rb_mlp* m) {
+    const F32Layout L = f32_layout(m->width, m->depth);
+    if (!m->f32_prep) RB_CUDA(cudaMalloc(&m->f32_prep, sizeof(float) * L.total));
+    k_prepare_f32<<<sm_count() * 4, 256, 0, m->stream>>>(m->params, m->width, m->depth,
+                                                         m->f32_prep);
+    RB_CUDA(cudaGetLastError());
+    RB_TRY(nn_tc_prepare(m));
+    m->version++;
+    return RB_OK;
+}
+
 static int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -379,14 +403,7 @@ rb_status rb_mlp_set_params(rb_mlp* m, const float* flat, int64_t n, int32_t fro
     RB_CUDA(cudaMemcpyAsync(m->params, flat, sizeof(float) * n,
                             from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             m->stream));
-    const F32Layout L = f32_layout(m->width, m->depth);
-    if (!m->f32_prep) RB_CUDA(cudaMalloc(&m->f32_prep, sizeof(float) * L.total));
-    k_prepare_f32<<<sm_count() * 4, 256, 0, m->stream>>>(m->params, m->width, m->depth,
-                                                         m->f32_prep);
-    RB_CUDA(cudaGetLastError());
-    RB_TRY(nn_tc_prepare(m));
-    m->version++;
-    return RB_OK;
+    return mlp_refresh(m);
 }
 
 rb_status rb_mlp_get_params(const rb_mlp* m, float* flat, int64_t n, int32_t to_host) {

@@ -157,6 +157,10 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
     }
 }
 
+// nn.cu
+rb_status nn_pairs_f32_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
+                             float4* grad);
+rb_status mlp_refresh(rb_mlp* m);  // rebuild the derived weight copies after params change
 // nn_tc.cu
 rb_status nn_tc_prepare(rb_mlp* m);
 rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m);

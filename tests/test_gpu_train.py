@@ -1,0 +1,192 @@
+"""GPU parity of the training path: the on-device pair sampler (contact
+bisection + bead-sum labels), the force-matching loss and its weight
+gradient (forward-over-reverse), the second-order weight product behind the
+autograd wrapper, and Adam steps, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import bodies, nn, sampler
+from paper_2402_12199_gb300 import inputs
+from tests.helpers import TOL_F32, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def cube_system(n=8):
+    from paper_2402_12199_gb300 import api
+
+    return api.System(n, [40.0] * 3, "cube")
+
+
+def lab10(lab12):
+    """(n, 12) library label layout -> (n, 10) oracle layout (E, F_j, tau_i, tau_j)."""
+    lab12 = np.asarray(lab12, dtype=np.float64)
+    return np.concatenate([lab12[:, 3:4], lab12[:, 0:3], lab12[:, 4:7], lab12[:, 8:11]], 1)
+
+
+def cfg7(cfg8):
+    cfg8 = np.asarray(cfg8, dtype=np.float64)
+    return np.concatenate([cfg8[:, :3], cfg8[:, 4:8]], 1)
+
+
+@pytest.mark.parametrize("shape", ["cube", "cylinder"])
+def test_sampler_matches_oracle(shape):
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    tmpl = bodies.cube_template() if shape == "cube" else bodies.cylinder_template()
+    s = api.System(8, [60.0] * 3, shape)
+    u = inputs.sampler_uniforms(48, 5)
+    cfg, lab, rc = api.sample_pairs(s, torch.from_numpy(u).cuda())
+    torch.cuda.synchronize()
+    cfg, lab, rc = cfg.cpu().numpy(), lab.cpu().numpy(), rc.cpu().numpy()
+    d, q = sampler.draws_to_config(u.astype(np.float64))
+    np.testing.assert_allclose(cfg[:, 4:8], q, atol=2e-6)
+    Rc = bodies.pair_cutoff(tmpl)
+    for b in range(0, 48, 6):
+        rc_ref = sampler.contact_distance(d[b], q[b], tmpl, Rc)
+        assert rc[b] == pytest.approx(rc_ref, abs=2e-5)
+    rho = np.linalg.norm(cfg[:, :3], axis=1)
+    assert np.all(rho >= rc - 1e-4) and np.all(rho <= Rc + 1e-4)
+    # labels: the oracle's bead sum at exactly the sampled configurations
+    ref = sampler.label_pairs(cfg7(cfg), tmpl)
+    got = lab10(lab)
+    assert rel_err(got[:, 1:4], ref[:, 1:4]) < TOL_F32
+    assert rel_err(got[:, 4:7], ref[:, 4:7]) < TOL_F32
+    assert rel_err(got[:, 7:10], ref[:, 7:10]) < TOL_F32
+    assert np.abs(got[:, 0] - ref[:, 0]).max() <= TOL_F32 * max(1.0, np.abs(ref[:, 0]).max())
+
+
+def _setup(width, B, seed, lam_tau=0.5, lam_E=0.1):
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    mu, isd = inputs.feature_normalisation(5.0, 9.43)
+    flat = inputs.mlp_params(width, 3, seed, mu=mu, inv_sd=isd, e_scale=1.3, e_shift=0.2)
+    c7 = inputs.pair_configs(B, seed + 1, 5.0, 9.4)
+    rng = np.random.default_rng(seed + 2)
+    lab = rng.standard_normal((B, 10))
+    m = api.MLP(width, 3)
+    m.set_params(flat)
+    tr = api.Trainer(m, max(B, 64))
+    c8 = np.zeros((B, 8), np.float32)
+    c8[:, :3] = c7[:, :3]
+    c8[:, 4:] = c7[:, 3:]
+    l12 = np.zeros((B, 12), np.float32)
+    l12[:, 0:3] = lab[:, 1:4]
+    l12[:, 3] = lab[:, 0]
+    l12[:, 4:7] = lab[:, 4:7]
+    l12[:, 8:11] = lab[:, 7:10]
+    return flat, c7, lab.astype(np.float32), m, tr, torch.from_numpy(c8).cuda(), torch.from_numpy(l12).cuda()
+
+
+@pytest.mark.parametrize("width,B", [(64, 200), (128, 96), (128, 1)])
+def test_force_matching_gradient_parity(width, B):
+    flat, c7, lab, m, tr, c8, l12 = _setup(width, B, width + B)
+    loss, g = tr.grad(c8, l12, 0.5, 0.1)
+    L_ref, g_ref = nn.force_matching_loss(flat.astype(np.float64), width, 3, c7.astype(np.float64),
+                                          lab.astype(np.float64), 0.5, 0.1)
+    assert loss == pytest.approx(L_ref, rel=1e-5)
+    assert rel_err(g.double().cpu().numpy(), g_ref) < 1e-5
+
+
+def test_weight_vjp_is_second_order_product():
+    import torch
+
+    width, B = 64, 50
+    flat, c7, lab, m, tr, c8, l12 = _setup(width, B, 77)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((B, 8)).astype(np.float32)
+    u[:, 3] = 0.0
+    c = rng.standard_normal(B).astype(np.float32)
+    g = tr.weight_vjp(c8, torch.from_numpy(u).cuda(), torch.from_numpy(c).cuda())
+    # oracle: d/dW sum_b [u_b . dE_hat/d(s, q) + c_b E_hat] by autograd
+    ft = torch.as_tensor(flat.astype(np.float64)).requires_grad_(True)
+    p = nn.unpack(ft, width)
+    sq = torch.as_tensor(c7.astype(np.float64)).requires_grad_(True)
+    Eh = (nn.config_energy(p, sq[:, :3], sq[:, 3:]) - p["e_shift"]) / p["e_scale"]
+    (gsq,) = torch.autograd.grad(Eh.sum(), [sq], create_graph=True)
+    uu = torch.as_tensor(np.concatenate([u[:, :3], u[:, 4:]], 1).astype(np.float64))
+    J = (gsq * uu).sum() + (torch.as_tensor(c.astype(np.float64)) * Eh).sum()
+    (gref,) = torch.autograd.grad(J, [ft])
+    gref = gref.numpy().copy()
+    gref[:20] = 0.0
+    gref[-2:] = 0.0
+    assert rel_err(g.double().cpu().numpy(), gref) < 1e-5
+
+
+def test_adam_steps_fit_a_teacher():
+    """Labels from a teacher network: Adam steps on the student's
+    force-matching loss drive the loss down."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    mu, isd = inputs.feature_normalisation(5.0, 9.43)
+    teacher = inputs.mlp_params(64, 3, 100, mu=mu, inv_sd=isd)
+    student = inputs.mlp_params(64, 3, 101, mu=mu, inv_sd=isd)
+    B = 512
+    c7 = inputs.pair_configs(B, 102, 5.0, 9.4)
+    c8 = np.zeros((B, 8), np.float32)
+    c8[:, :3] = c7[:, :3]
+    c8[:, 4:] = c7[:, 3:]
+    c8 = torch.from_numpy(c8).cuda()
+    mt = api.MLP(64, 3)
+    mt.set_params(teacher)
+    lab = mt.pairs(c8, "fp32")
+    ms = api.MLP(64, 3)
+    ms.set_params(student)
+    tr = api.Trainer(ms, B, lr=3e-3)
+    l0 = tr.step(c8, lab, 1.0, 0.1)
+    for _ in range(150):
+        l1 = tr.step(c8, lab, 1.0, 0.1, want_loss=False)
+    l1 = tr.grad(c8, lab, 1.0, 0.1)[0]
+    assert l1 < 0.2 * l0, (l0, l1)
+
+
+def test_autograd_wrapper_double_backward():
+    """Force matching through torch autograd on the library's wrapper: the
+    gradient of a force-based loss with respect to the parameters equals the
+    oracle's."""
+    import torch
+
+    from paper_2402_12199_gb300.autograd import NNEnergy
+
+    width, B = 64, 40
+    flat, c7, lab, m, tr, c8, l12 = _setup(width, B, 55)
+    f = NNEnergy(width, 3, 256)
+    params = torch.from_numpy(flat).cuda().requires_grad_(True)
+    cfg = c8.clone().requires_grad_(True)
+    E = f(cfg, params)
+    (G,) = torch.autograd.grad(E.sum(), [cfg], create_graph=True)
+    target = torch.from_numpy(np.random.default_rng(1).standard_normal((B, 8))).float().cuda()
+    target[:, 3] = 0.0
+    loss = ((G - target) ** 2).sum() + 0.3 * (E ** 2).sum()
+    (gp,) = torch.autograd.grad(loss, [params])
+    # oracle
+    ft = torch.as_tensor(flat.astype(np.float64)).requires_grad_(True)
+    p = nn.unpack(ft, width)
+    sq = torch.as_tensor(c7.astype(np.float64)).requires_grad_(True)
+    Eo = nn.config_energy(p, sq[:, :3], sq[:, 3:])
+    (Go,) = torch.autograd.grad(Eo.sum(), [sq], create_graph=True)
+    t = target.double().cpu()
+    t7 = torch.cat([t[:, :3], t[:, 4:]], 1)
+    lo = ((Go - t7) ** 2).sum() + 0.3 * (Eo ** 2).sum()
+    (gref,) = torch.autograd.grad(lo, [ft])
+    gref = gref.numpy().copy()
+    gref[:20] = 0.0
+    gref[-2:] = 0.0
+    g = gp.double().cpu().numpy()
+    assert rel_err(g, gref) < 1e-5
