@@ -263,6 +263,59 @@ rb_status rb_train_step(rb_trainer* tr, int64_t batch, const float* cfg, const f
 rb_status rb_nn_weight_vjp(rb_trainer* tr, int64_t n, const float* cfg, const float* u_cfg,
                            const float* c, float* grad_out);
 
+/* ------------------------------------------------------------------ serving */
+
+/* Device bytes rb_create_system would allocate for `desc` (-1 if invalid). */
+int64_t rb_system_footprint(const rb_system_desc* desc);
+
+/* A server runs many independent MD replicas (the paper runs one simulation
+ * per GPU; serving many is this library's extension) with continuous
+ * batching: a scheduler thread admits queued requests whenever a slot is free
+ * and the replica's footprint fits in `hbm_budget_bytes`, runs each resident
+ * replica on its own stream (their work overlaps on the device), advances
+ * every replica by `steps_per_tick` steps per tick, and retires finished ones.
+ * A network-path replica whose forces turn non-finite is rolled back to the
+ * start of its tick and continued on the bead path (rb_result.fell_back). */
+typedef struct rb_server rb_server;
+typedef struct rb_result {
+    int32_t status;      /* RB_OK, or the error that ended the request */
+    int32_t fell_back;   /* 1 if the request switched to the bead path */
+    int64_t n_bodies;
+    int64_t steps_done;
+    int64_t pairs;       /* body pairs in the last step */
+    double e_start;      /* FP64 total energy before the first step */
+    double e_end;        /* FP64 total energy after the last step */
+    double step_ms_p50;  /* device time per step (CUDA events), median */
+    double step_ms_p99;
+    double queue_ms;     /* host time from submission to admission */
+    double run_ms;       /* host time from admission to completion */
+} rb_result;
+typedef struct rb_server_stats_t {
+    int64_t queued, resident, peak_resident, bytes_in_use, steps;
+    double pair_evals;   /* body-pair evaluations completed */
+    double step_ms_p50, step_ms_p99;  /* over every step of every request */
+} rb_server_stats_t;
+
+rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_mlp* mlp,
+                           int32_t steps_per_tick, rb_server** out);
+/* Stops the scheduler; requests still resident end with RB_EINVAL. */
+rb_status rb_server_destroy(rb_server* server);
+/* Queue one replica: `desc` as rb_create_system; pos, quat, vel, angmom are
+ * HOST float4 rows (copied); path RB_PATH_BEADS or RB_PATH_NN (the server's
+ * network) at `precision`; n_steps of size dt.  RB_ENOMEM if the replica
+ * could never fit in the budget.  Never blocks on the device. */
+rb_status rb_submit(rb_server* server, const rb_system_desc* desc, const float* pos,
+                    const float* quat, const float* vel, const float* angmom, int32_t path,
+                    int32_t precision, int64_t n_steps, float dt, uint64_t* ticket);
+/* RB_ENOT_READY until the request has finished; then RB_OK and *out filled. */
+rb_status rb_poll(rb_server* server, uint64_t ticket, rb_result* out);
+/* Block until the request finishes or timeout_ms passes (RB_ETIMEOUT). */
+rb_status rb_wait(rb_server* server, uint64_t ticket, int32_t timeout_ms, rb_result* out);
+/* Final state (HOST float4 rows, any pointer NULL) of a finished request. */
+rb_status rb_fetch_state(rb_server* server, uint64_t ticket, float* pos, float* quat, float* vel,
+                         float* angmom);
+rb_status rb_server_stats(rb_server* server, rb_server_stats_t* out);
+
 /* Wait for the network's stream and report sticky device-side errors of
  * rb_nn_pairs (RB_EFAULT if a tensor-core kernel gave up waiting for an MMA). */
 rb_status rb_mlp_sync(const rb_mlp* mlp);

@@ -678,6 +678,33 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     return RB_OK;
 }
 
+int64_t rb_system_footprint(const rb_system_desc* d) {
+    if (!d || d->n_bodies < 1) return -1;
+    std::string err;
+    std::vector<float> t = make_template(d->body, err);
+    if (t.empty()) return -1;
+    double rmax = 0;
+    for (size_t k = 0; k < t.size() / 3; ++k)
+        rmax = std::max(rmax, std::sqrt((double)t[3 * k] * t[3 * k] + (double)t[3 * k + 1] * t[3 * k + 1] +
+                                        (double)t[3 * k + 2] * t[3 * k + 2]));
+    const double Rc = 2.0 * rmax + d->pot.rcut;
+    int64_t n_cells = 1;
+    for (int a = 0; a < 3; ++a) n_cells *= std::max<int64_t>(1, (int64_t)std::floor(d->box[a] / Rc));
+    const int64_t N = d->n_bodies;
+    const int64_t mn = d->max_neighbors > 0 ? d->max_neighbors : 64;
+    const int64_t cp = std::max<int64_t>(1, N * mn / 2);
+    const int64_t cap = std::max<int64_t>(32, 2 * mn);
+    const int sms = 160;
+    int64_t b = 0;
+    b += 16 * 256;                          // template
+    b += 6 * 16 * N;                        // state + forces
+    b += 4 * n_cells * (1 + cap);           // cells
+    b += 4 * N * (2 + 2 * mn + 2) + 4 * (N / 1024 + 2);  // rows, offsets
+    b += 8 * cp + 3 * 16 * cp;              // pairs + per-pair results
+    b += 8 * 12 * 2 * sms + 8 * 16 + 64;    // reductions, status
+    return b;
+}
+
 rb_status rb_destroy_system(rb_system* s) {
     if (!s) return RB_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
