@@ -210,6 +210,15 @@ rb_status rb_mlp_get_params(const rb_mlp* mlp, float* flat, int64_t n, int32_t t
 rb_status rb_forces_nn(rb_system* sys, const rb_mlp* mlp, int32_t precision, float* force,
                        float* torque, double* energy_host, double* virial9_host);
 
+/* Bead fallback of the network path: listed pairs whose centres are closer
+ * than rho_min (outside the separations the network was trained on) are
+ * evaluated by the bead double sum instead of the network, inside
+ * rb_forces_nn and rb_step.  0 turns it off (default). */
+rb_status rb_set_nn_fallback(rb_system* sys, float rho_min);
+/* Number of pairs that took the bead fallback in the last network evaluation
+ * (synchronises). */
+rb_status rb_nn_fallback_count(rb_system* sys, int64_t* count_host);
+
 /* Network on explicit pair configurations in the frame of body i (q_i = 1):
  * cfg: n x 8 floats (s_x, s_y, s_z, 0, q_s, q_i, q_j, q_k).  out: n x 12 floats
  * (F_j xyz, E, tau_i xyz, 0, tau_j xyz, 0) in the frame of body i.  If

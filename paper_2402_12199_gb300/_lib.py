@@ -43,6 +43,22 @@ class rb_system_desc(ctypes.Structure):
                 ("n_bodies", ctypes.c_int64), ("max_neighbors", ctypes.c_int32)]
 
 
+class rb_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("fell_back", ctypes.c_int32),
+                ("n_bodies", ctypes.c_int64), ("steps_done", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("e_start", ctypes.c_double),
+                ("e_end", ctypes.c_double), ("step_ms_p50", ctypes.c_double),
+                ("step_ms_p99", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double)]
+
+
+class rb_server_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64),
+                ("peak_resident", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("pair_evals", ctypes.c_double),
+                ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double)]
+
+
 P = ctypes.c_void_p
 I32 = ctypes.c_int32
 I64 = ctypes.c_int64
@@ -78,6 +94,17 @@ SIGNATURES = {
     "rb_forces_nn": (I32, [P, P, I32, P, P, DP, DP]),
     "rb_nn_pairs": (I32, [P, I32, I64, P, P, P]),
     "rb_mlp_sync": (I32, [P]),
+    "rb_set_nn_fallback": (I32, [P, F32]),
+    "rb_nn_fallback_count": (I32, [P, I64P]),
+    "rb_system_footprint": (I64, [ctypes.POINTER(rb_system_desc)]),
+    "rb_server_create": (I32, [ctypes.c_size_t, I32, P, I32, ctypes.POINTER(P)]),
+    "rb_server_destroy": (I32, [P]),
+    "rb_submit": (I32, [P, ctypes.POINTER(rb_system_desc), P, P, P, P, I32, I32, I64, F32,
+                        ctypes.POINTER(ctypes.c_uint64)]),
+    "rb_poll": (I32, [P, ctypes.c_uint64, ctypes.POINTER(rb_result)]),
+    "rb_wait": (I32, [P, ctypes.c_uint64, I32, ctypes.POINTER(rb_result)]),
+    "rb_fetch_state": (I32, [P, ctypes.c_uint64, P, P, P, P]),
+    "rb_server_stats": (I32, [P, ctypes.POINTER(rb_server_stats_t)]),
     "rb_sample_pairs": (I32, [P, I64, P, P, P, P]),
     "rb_trainer_create": (I32, [P, I64, F32, F32, F32, F32, ctypes.POINTER(P)]),
     "rb_trainer_destroy": (I32, [P]),

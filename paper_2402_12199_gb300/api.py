@@ -177,6 +177,14 @@ class System:
         check(load().rb_eval_pairs(self._h, path, mlp.handle if mlp is not None else None,
                                    PRECISION[precision]))
 
+    def set_nn_fallback(self, rho_min: float):
+        check(load().rb_set_nn_fallback(self._h, float(rho_min)))
+
+    def nn_fallback_count(self) -> int:
+        n = ctypes.c_int64()
+        check(load().rb_nn_fallback_count(self._h, ctypes.byref(n)))
+        return n.value
+
     def energy(self):
         e, kt, kr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         check(load().rb_energy(self._h, ctypes.byref(e), ctypes.byref(kt), ctypes.byref(kr)))
@@ -309,3 +317,90 @@ def sample_pairs(system: System, uniforms: torch.Tensor):
     check(load().rb_sample_pairs(system.handle, n, uniforms.data_ptr(), cfg.data_ptr(),
                                  lab.data_ptr(), rc.data_ptr()))
     return cfg, lab, rc
+
+
+def _desc(n_bodies: int, box, shape: str = "cube", eps=1.0, sigma=1.0, rcut=2.5,
+          max_neighbors: int = 0):
+    d = _lib.rb_system_desc()
+    d.body.shape = SHAPES[shape]
+    d.body.bead_mass = 1.0
+    d.pot.kind = 0
+    d.pot.eps, d.pot.sigma, d.pot.rcut = eps, sigma, rcut
+    box = np.broadcast_to(np.asarray(box, dtype=np.float32), (3,))
+    for a in range(3):
+        d.box[a] = float(box[a])
+    d.n_bodies = int(n_bodies)
+    d.max_neighbors = int(max_neighbors)
+    return d
+
+
+def footprint(n_bodies: int, box, shape: str = "cube") -> int:
+    """rb_system_footprint: device bytes of one system."""
+    d = _desc(n_bodies, box, shape)
+    return int(load().rb_system_footprint(ctypes.byref(d)))
+
+
+def _result_dict(r) -> dict:
+    return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+class Server:
+    """rb_server_create / rb_submit / rb_poll / rb_wait / rb_fetch_state."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, mlp: MLP = None,
+                 steps_per_tick: int = 8):
+        h = ctypes.c_void_p()
+        check(load().rb_server_create(int(hbm_budget_bytes), int(max_slots),
+                                      mlp.handle if mlp is not None else None,
+                                      int(steps_per_tick), ctypes.byref(h)))
+        self._h = h
+        self.mlp = mlp
+        self._n = {}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().rb_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, state: dict, box, shape: str = "cube", path: int = RB_PATH_BEADS,
+               precision="fp32", n_steps: int = 100, dt: float = 0.002) -> int:
+        n = len(state["pos"])
+        d = _desc(n, box, shape)
+        arrs = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("pos", "quat", "vel", "angmom")]
+        t = ctypes.c_uint64()
+        check(load().rb_submit(self._h, ctypes.byref(d), *[a.ctypes.data for a in arrs], path,
+                               PRECISION[precision], int(n_steps), float(dt), ctypes.byref(t)))
+        self._n[t.value] = n
+        return t.value
+
+    def poll(self, ticket: int):
+        r = _lib.rb_result()
+        st = load().rb_poll(self._h, ticket, ctypes.byref(r))
+        if st == _lib.RB_ENOT_READY:
+            return None
+        check(st)
+        return _result_dict(r)
+
+    def wait(self, ticket: int, timeout_ms: int = 600000):
+        r = _lib.rb_result()
+        check(load().rb_wait(self._h, ticket, int(timeout_ms), ctypes.byref(r)))
+        return _result_dict(r)
+
+    def fetch_state(self, ticket: int) -> dict:
+        n = self._n[ticket]
+        out = {k: np.zeros((n, 4), dtype=np.float32) for k in ("pos", "quat", "vel", "angmom")}
+        check(load().rb_fetch_state(self._h, ticket, *[out[k].ctypes.data for k in
+                                                       ("pos", "quat", "vel", "angmom")]))
+        return out
+
+    def stats(self) -> dict:
+        s = _lib.rb_server_stats_t()
+        check(load().rb_server_stats(self._h, ctypes.byref(s)))
+        return _result_dict(s)

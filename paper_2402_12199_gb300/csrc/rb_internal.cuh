@@ -168,6 +168,10 @@ struct rb_system {
     unsigned* status_dev = nullptr;
     int num_sms = 0;
     rb::GraphCache graph;
+    // network path: pairs closer than this (outside the trained domain) are
+    // evaluated by the bead sum instead (0 = off); count of such pairs
+    float nn_fallback_rho = 0.f;
+    int* fallback_count = nullptr;
 };
 
 namespace rb {
@@ -177,6 +181,7 @@ rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
 rb_status energy_async(rb_system* s);
 // beads.cu
 rb_status bead_pairs_async(rb_system* s);
+rb_status bead_fallback_async(rb_system* s);  // bead sum for pairs with rho < nn_fallback_rho
 // nn.cu
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision);
 rb_status check_mlp(const rb_mlp* m);

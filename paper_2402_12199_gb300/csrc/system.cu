@@ -653,6 +653,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     ALLOC(s->red_partials, sizeof(double) * 12 * s->red_blocks);
     ALLOC(s->red_out, sizeof(double) * 16);
     ALLOC(s->status_dev, sizeof(unsigned));
+    ALLOC(s->fallback_count, sizeof(int));
 #undef ALLOC
     if (e != cudaSuccess) {
         rb_status st = cuda_fail(e, "cudaMalloc (system)");
@@ -666,6 +667,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->pl.n_pairs, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->angmom, 0, sizeof(float4) * N, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->vel, 0, sizeof(float4) * N, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -714,7 +716,8 @@ rb_status rb_destroy_system(rb_system* s) {
                     s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
                     s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
                     s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
-                    s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev};
+                    s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev,
+                    s->fallback_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -838,6 +841,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
     RB_TRY(check_mlp(m));
     RB_TRY(build_pairs_async(s));
     RB_TRY(nn_pairs_system_async(s, m, precision));
+    RB_TRY(bead_fallback_async(s));
     RB_TRY(reduce_forces_async(s, 0.f));
     s->forces_valid = true;
     s->forces_path = RB_PATH_NN;
@@ -850,10 +854,12 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
 static rb_status eval_forces_async(rb_system* s, int path, const rb_mlp* m, int precision,
                                    float kick) {
     RB_TRY(build_pairs_async(s));
-    if (path == RB_PATH_BEADS)
+    if (path == RB_PATH_BEADS) {
         RB_TRY(bead_pairs_async(s));
-    else
+    } else {
         RB_TRY(nn_pairs_system_async(s, m, precision));
+        if (s->nn_fallback_rho > 0.f) RB_TRY(bead_fallback_async(s));
+    }
     return reduce_forces_async(s, kick);
 }
 
@@ -927,6 +933,29 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
         g.dt = dt;
     }
     for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
+    return RB_OK;
+}
+
+rb_status rb_set_nn_fallback(rb_system* s, float rho_min) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (!(rho_min >= 0.f)) return fail(RB_EINVAL, "rho_min must be >= 0");
+    if (rho_min != s->nn_fallback_rho) {
+        s->nn_fallback_rho = rho_min;
+        s->forces_valid = false;
+        if (s->graph.exec) {  // the captured step graph depends on it
+            cudaGraphExecDestroy(s->graph.exec);
+            s->graph.exec = nullptr;
+        }
+    }
+    return RB_OK;
+}
+
+rb_status rb_nn_fallback_count(rb_system* s, int64_t* count_host) {
+    if (!s || !count_host) return fail(RB_EINVAL, "null argument");
+    int c = 0;
+    RB_CUDA(cudaMemcpyAsync(&c, s->fallback_count, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    RB_CUDA(cudaStreamSynchronize(s->stream));
+    *count_host = c;
     return RB_OK;
 }
 

@@ -118,3 +118,37 @@ def test_nn_md_steps_conserve_energy():
     s.step(50, 0.002, path=api.RB_PATH_NN, mlp=m)
     e1 = sum(s.energy())
     assert abs(e1 - e0) < 1e-3 * 512, (e0, e1)
+
+
+def test_bead_fallback_for_close_pairs():
+    """Pairs closer than rho_min take the bead sum inside the network path:
+    rho_min above the cutoff reproduces the bead path exactly; in between, the
+    result is the oracle's bead sum on close pairs plus its network on the rest."""
+    import oracle
+    from oracle import bodies
+    from paper_2402_12199_gb300 import api
+
+    st, L, tmpl = make_state(1500, 0.2, 61)
+    flat = params(128, 8)
+    m = api.MLP(128, 3)
+    m.set_params(flat)
+    s = gpu_system(st, L)
+    ref = s.forces_beads()
+    s.set_nn_fallback(100.0)
+    r = s.forces_nn(m, "fp32")
+    s.sync()
+    assert bool((r["force"] == ref["force"]).all()) and bool((r["torque"] == ref["torque"]).all())
+    rho_min = 8.2
+    s.set_nn_fallback(rho_min)
+    r = s.forces_nn(m, "fp32")
+    n_fb = s.nn_fallback_count()
+    pos = st["pos"][:, :3].astype(np.float64)
+    pairs = oracle.pairs_bruteforce(pos, [L] * 3, bodies.pair_cutoff(tmpl))
+    d = pos[pairs[:, 1]] - pos[pairs[:, 0]]
+    d -= L * np.rint(d / L)
+    close = np.linalg.norm(d, axis=1) < rho_min
+    assert n_fb == int(close.sum()) and 0 < n_fb < len(pairs)
+    Fb, Tb, _, _ = oracle.forces_beads(pos, st["quat"], [L] * 3, tmpl, pairs[close])
+    Fn, Tn, _, _, _ = oracle_nn(st, L, tmpl, flat, 128, pairs=pairs[~close])
+    assert rel_err(r["force"][:, :3].double().cpu().numpy(), Fb + Fn) < TOL_F32
+    assert rel_err(r["torque"][:, :3].double().cpu().numpy(), Tb + Tn) < TOL_F32

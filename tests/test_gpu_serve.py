@@ -1,0 +1,117 @@
+"""Serving: continuous batching of independent MD replicas.  A request's
+result is the same alone and in a mix; admission respects the memory budget;
+waits time out; a network that produces non-finite forces falls back to the
+bead path."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2402_12199_gb300 import inputs
+from tests.helpers import make_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def net(seed=3):
+    from paper_2402_12199_gb300 import api
+
+    mu, isd = inputs.feature_normalisation(5.0, 9.43)
+    m = api.MLP(128, 3)
+    m.set_params(inputs.mlp_params(128, 3, seed, mu=mu, inv_sd=isd))
+    return m
+
+
+def test_result_is_identical_alone_and_in_a_mix():
+    from paper_2402_12199_gb300 import api
+
+    m = net()
+    A = make_state(512, 0.20, 41)
+    B = make_state(900, 0.15, 42, "cylinder")
+    C = make_state(2000, 0.10, 43)
+    s1 = api.Server(4 << 30, 1, m, steps_per_tick=5)
+    ta = s1.submit(A[0], [A[1]] * 3, "cube", api.RB_PATH_NN, "bf16", 30)
+    ra = s1.wait(ta)
+    alone = s1.fetch_state(ta)
+    s1.close()
+    assert ra["status"] == 0 and ra["steps_done"] == 30
+    s2 = api.Server(4 << 30, 4, m, steps_per_tick=3)
+    tb = s2.submit(B[0], [B[1]] * 3, "cylinder", api.RB_PATH_BEADS, "fp32", 25)
+    tc = s2.submit(C[0], [C[1]] * 3, "cube", api.RB_PATH_NN, "fp32", 20)
+    ta2 = s2.submit(A[0], [A[1]] * 3, "cube", api.RB_PATH_NN, "bf16", 30)
+    for t in (tb, tc, ta2):
+        r = s2.wait(t)
+        assert r["status"] == 0, r
+    mixed = s2.fetch_state(ta2)
+    st = s2.stats()
+    s2.close()
+    for k in ("pos", "quat", "vel", "angmom"):
+        assert np.array_equal(alone[k], mixed[k]), k
+    assert st["peak_resident"] >= 2 and st["steps"] == 75
+
+
+def test_admission_respects_memory_budget():
+    from paper_2402_12199_gb300 import api
+
+    st, L, _ = make_state(1000, 0.2, 44)
+    fp = api.footprint(1000, [L] * 3)
+    srv = api.Server(int(2.5 * fp), 8, None, steps_per_tick=4)
+    tickets = [srv.submit(st, [L] * 3, n_steps=12) for _ in range(6)]
+    res = [srv.wait(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert all(r["status"] == 0 and r["steps_done"] == 12 for r in res)
+    assert 1 <= stats["peak_resident"] <= 2
+    # identical requests give identical results whatever their admission order
+    assert len({round(r["e_end"], 12) for r in res}) == 1
+    with pytest.raises(api.RBError) as ei:
+        api.Server(fp // 2, 2).submit(st, [L] * 3)
+    assert ei.value.status == 2
+
+
+def test_wait_times_out_and_poll_is_nonblocking():
+    from paper_2402_12199_gb300 import api
+
+    st, L, _ = make_state(8000, 0.2, 45)
+    srv = api.Server(8 << 30, 2, None, steps_per_tick=8)
+    t = srv.submit(st, [L] * 3, n_steps=3000)
+    t0 = time.perf_counter()
+    assert srv.poll(t) is None
+    with pytest.raises(api.RBError) as ei:
+        srv.wait(t, timeout_ms=5)
+    assert ei.value.status == 6
+    assert time.perf_counter() - t0 < 2.0
+    srv.close()  # the unfinished request is drained, not leaked
+
+
+def test_non_finite_network_falls_back_to_beads():
+    from paper_2402_12199_gb300 import api
+
+    m = api.MLP(128, 3)
+    flat = inputs.mlp_params(128, 3, 9)
+    flat[100] = np.nan
+    m.set_params(flat)
+    st, L, _ = make_state(512, 0.2, 46)
+    srv = api.Server(4 << 30, 2, m, steps_per_tick=4)
+    t = srv.submit(st, [L] * 3, path=api.RB_PATH_NN, precision="bf16", n_steps=16)
+    tb = srv.submit(st, [L] * 3, path=api.RB_PATH_BEADS, n_steps=16)
+    r = srv.wait(t)
+    rb = srv.wait(tb)
+    fin = srv.fetch_state(t)
+    finb = srv.fetch_state(tb)
+    srv.close()
+    assert r["status"] == 0 and r["fell_back"] == 1 and r["steps_done"] == 16
+    assert np.isfinite(fin["pos"]).all()
+    # the fallback replica followed the bead path from its start
+    for k in ("pos", "quat", "vel", "angmom"):
+        assert np.array_equal(fin[k], finb[k]), k
