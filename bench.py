@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
     ap.add_argument("--ref-sample-pairs", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--train-samples", type=int, default=200000)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--skin", type=float, default=0.4)
     return ap.parse_args()
 
 
@@ -57,6 +61,79 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def combine_ranks(ms_step: float, units: float, device=None):
+    """Max of the per-step time and sum of the work units over all ranks (no-op
+    for one process).  Returns (ms_step_max, units_total)."""
+    import torch
+
+    try:
+        import torch.distributed as dist
+
+        active = dist.is_available() and dist.is_initialized()
+    except Exception:
+        active = False
+    if not active:
+        return ms_step, units
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def serving_run(api, inputs, mlp, n_requests=24, steps=200, seed=5, rate_factor=8.0,
+                budget_bytes=2 << 30, slots=8):
+    """Bounded serving workload: cube/cylinder replicas with N log-uniform in
+    [512, 8192], phi in [0.05, 0.25], kT in [0.5, 1.5], Poisson arrivals at about
+    rate_factor / (mean solo run time); cubes on the network (BF16), cylinders on
+    the bead path (the network is a cube model)."""
+    import time as _t
+
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_requests):
+        shape = "cube" if rng.random() < 0.5 else "cylinder"
+        n = int(round(math.exp(rng.uniform(math.log(512), math.log(8192)))))
+        phi = float(rng.uniform(0.05, 0.25))
+        kT = float(rng.uniform(0.5, 1.5))
+        M = 125.0 if shape == "cube" else 152.0
+        I = [500.0] * 3 if shape == "cube" else [1234.2857142857142, 1234.2857142857142, 384.0]
+        while True:
+            try:
+                st, L = inputs.system_state(n, phi, kT, seed * 1000 + k, M, I, shape)
+                break
+            except ValueError:
+                phi -= 0.02
+        path = api.RB_PATH_NN if (shape == "cube" and mlp is not None) else api.RB_PATH_BEADS
+        reqs.append((st, L, shape, path))
+    # calibration: one solo request to set the arrival rate
+    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8)
+    st, L, shape, path = reqs[0]
+    t0 = _t.perf_counter()
+    srv.wait(srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4))
+    t_solo = _t.perf_counter() - t0
+    srv.close()
+    gaps = rng.exponential(t_solo / rate_factor, size=n_requests)
+    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8)
+    t0 = _t.perf_counter()
+    tickets = []
+    for (st, L, shape, path), g in zip(reqs, gaps):
+        tickets.append(srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4))
+        _t.sleep(g)
+    res = [srv.wait(t) for t in tickets]
+    makespan = _t.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    ok = sum(r["status"] == 0 for r in res)
+    return {"requests": n_requests, "completed_ok": ok, "steps_each": steps,
+            "makespan_s": makespan, "pair_evals_per_s": stats["pair_evals"] / makespan,
+            "step_ms_p50": stats["step_ms_p50"], "step_ms_p99": stats["step_ms_p99"],
+            "peak_resident": stats["peak_resident"], "solo_calibration_s": t_solo,
+            "fell_back": sum(r["fell_back"] for r in res),
+            "max_rel_energy_drift": max(abs(r["e_end"] - r["e_start"]) / (r["n_bodies"])
+                                        for r in res)}
 
 
 def make_inputs(rank=0):
@@ -227,12 +304,26 @@ def main():
     paths = [p for p in args.paths.split(",") if p]
     st, L, flat = make_inputs(rank)
     dev_state = {k: torch.from_numpy(st[k]).cuda() for k in ("pos", "quat", "vel", "angmom")}
-    mlp = api.MLP(WIDTH, DEPTH)
-    mlp.set_params(flat)
+    training = None
+    if args.train_steps > 0 and any(p.startswith("nn") for p in paths):
+        from paper_2402_12199_gb300 import train_net
+
+        mlp, rep = train_net.train_network("cube", WIDTH, DEPTH, n_samples=args.train_samples,
+                                           steps=args.train_steps, batch=4096, lr=1e-3,
+                                           time_limit_s=60.0)
+        training = {"samples": rep["samples"], "steps": rep["steps"], "batch": rep["batch"],
+                    "sampler_pairs_per_s": (rep["samples"] + 10000) / rep["t_sample_s"],
+                    "train_samples_per_s": rep["steps"] * rep["batch"] / rep["t_train_s"],
+                    "heldout_e_F": rep["heldout_e_F"], "heldout_e_tau_i": rep["heldout_e_tau_i"],
+                    "heldout_e_tau_j": rep["heldout_e_tau_j"],
+                    "loss": "mean |dF_j|^2 + |dtau_i|^2 + |dtau_j|^2 (FP32, Adam lr 1e-3)"}
+    else:
+        mlp = api.MLP(WIDTH, DEPTH)
+        mlp.set_params(flat)
     stream = torch.cuda.current_stream()
     systems = {}
     for p in paths:
-        s = api.System(N_BODIES, [L] * 3, "cube")
+        s = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
         s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
         systems[p] = s
 
@@ -277,13 +368,10 @@ def main():
     for s in systems.values():
         s.sync()
     per_path_ms = {p: [a.elapsed_time(b) for a, b in ev[p]] for p in paths}
-    ms_step = sum(statistics.mean(v) for v in per_path_ms.values())
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step_local = sum(statistics.mean(v) for v in per_path_ms.values())
     pairs_per_step = sum(n_pairs.values())
-    value = world * pairs_per_step / (ms_step * 1e-3)
+    ms_step, pairs_all = combine_ranks(ms_step_local, pairs_per_step, device="cuda")
+    value = pairs_all / (ms_step * 1e-3)
 
     # ---- dominant kernel: the bead-sum pair kernel, timed alone with events
     roof = None
@@ -357,6 +445,23 @@ def main():
     h2d = len(systems) * 4 * N_BODIES * 16
     d2h = len(systems) * (4 * N_BODIES * 16 + 3 * 8)
 
+    model_error = None
+    if any(p.startswith("nn") for p in paths):
+        from paper_2402_12199_gb300 import train_net
+
+        probe = api.System(N_BODIES, [L] * 3, "cube")
+        probe.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+        model_error = {"vs": "bead path, same state (model error, not parity)",
+                       "trained": training is not None}
+        for p in paths:
+            if p.startswith("nn"):
+                model_error[p] = train_net.force_error(probe, mlp, p.split("_")[1])
+        del probe
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
+                              mlp)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(st, L, flat, args.cpu_sample_pairs)
@@ -381,11 +486,15 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{N_BODIES} cubes (5x5x5 beads, LJ eps=sigma=1 rc=2.5), "
                                    f"phi={PHI}, NVE dt={DT}; one MD step per force path "
-                                   f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU random init",
+                                   f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU "
+                                   f"{'trained on device by force matching' if training else 'random init'}",
                        "parallelism": "replicas" if world > 1 else "single GPU",
+                       "pair_list": f"Verlet skin {args.skin} sigma, rebuilt on the device when a "
+                                    f"centre moves more than skin/2; pairs beyond Rc give exactly zero",
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
             "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "cpu_baseline": cpu,
-            "e2e": {"value": world * pairs_per_step / e2e_t, "unit": UNIT,
+            "nn_model_error": model_error, "training": training, "serving": serving,
+            "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * 7 * len(paths), "clocks": clocks,
             "peaks_source": how, "wall_s": wall}

@@ -99,6 +99,7 @@ typedef struct rb_system_desc {
     float box[3];          /* orthorhombic periodic box; each side >= 2 Rc */
     int64_t n_bodies;      /* N >= 1 */
     int32_t max_neighbors; /* per-body cap of body neighbours within Rc (0: 64) */
+    float skin;            /* Verlet skin of the pair list (0: rebuild every step), see rb_set_skin */
 } rb_system_desc;
 
 /* Create a system with device storage for N bodies on `cuda_stream`.  The
@@ -124,8 +125,15 @@ rb_status rb_get_state(const rb_system* sys, float* pos, float* quat, float* vel
 /* Copy out the forces/torques of the last evaluation (float4 rows). */
 rb_status rb_get_forces(const rb_system* sys, float* force, float* torque, int32_t to_host);
 
+/* Verlet skin (default 0): the pair list then holds every pair within
+ * Rc + skin and is rebuilt only when some centre has moved more than skin / 2
+ * since the last build (decided on the device, so step graphs stay valid).
+ * Pairs listed beyond Rc contribute exactly zero, so forces do not depend on
+ * the skin.  Needs every box side >= 2 (Rc + skin). */
+rb_status rb_set_skin(rb_system* sys, float skin);
+
 /* Build the cell list and the body-pair list for the current positions:
- * all unordered pairs i < j with minimum-image |p_j - p_i| < Rc.  If
+ * all unordered pairs i < j with minimum-image |p_j - p_i| < Rc (+ skin).  If
  * n_pairs_host is not NULL the stream is synchronised and the count (or an
  * RB_EOVERFLOW) returned. */
 rb_status rb_build_pairs(rb_system* sys, int64_t* n_pairs_host);
@@ -251,19 +259,25 @@ typedef struct rb_trainer rb_trainer;
 rb_status rb_trainer_create(rb_mlp* mlp, int64_t max_batch, float lr, float beta1, float beta2,
                             float eps, rb_trainer** out);
 rb_status rb_trainer_destroy(rb_trainer* tr);
+/* Change the Adam learning rate (for schedules); the moments are kept. */
+rb_status rb_trainer_set_lr(rb_trainer* tr, float lr);
 
 /* Force-matching loss over a batch (device cfg n x 8, labels n x 12):
- *   L = mean_b |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
- *       + lam_E (E - E*)^2
- * with the FP32 network's forces/torques (exact energy gradients), and its
+ *   L = mean_b w_b [ |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
+ *       + lam_E (E - E*)^2 ],
+ *   w_b = min(1, exp(-E* / kT_w)) / (1 + (|F_j*|^2 + lam_tau (|tau_i*|^2 +
+ *         |tau_j*|^2)) / f_scale^2)
+ * (each factor is 1 when its parameter is <= 0) with the FP32 network's
+ * forces/torques (exact energy gradients), and its
  * gradient with respect to the flat parameters (zero for mu, inv_sd, e_scale,
  * e_shift, which are not trained).  grad_out: device, n_params (nullable);
  * loss_host (nullable) synchronises. */
 rb_status rb_train_grad(rb_trainer* tr, int64_t batch, const float* cfg, const float* labels,
-                        float lam_tau, float lam_E, float* grad_out, double* loss_host);
+                        float lam_tau, float lam_E, float f_scale, float kT_w, float* grad_out,
+                        double* loss_host);
 /* rb_train_grad followed by one Adam step on the trainable parameters. */
 rb_status rb_train_step(rb_trainer* tr, int64_t batch, const float* cfg, const float* labels,
-                        float lam_tau, float lam_E, double* loss_host);
+                        float lam_tau, float lam_E, float f_scale, float kT_w, double* loss_host);
 /* Weight gradient of sum_b [u_b . dE_hat_b/d(s, q_rel) + c_b E_hat_b] (E_hat:
  * the network output before e_scale/e_shift) for device arrays cfg n x 8,
  * u_cfg n x 8 (du_s xyz, 0, du_q wxyz), c n; grad_out device n_params.  This

@@ -191,9 +191,16 @@ def predict_labels(p: dict, s, q_rel, create_graph: bool = False):
     return E, -gR, -gi, -gj
 
 
-def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E):
-    """L = mean_b( |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
-    + lam_E (E - E*)^2 ).  pair_cfg: (B, 7) = s, q_rel; labels: (B, 10) =
+def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_scale=None,
+                        kT_w=None):
+    """L = mean_b w_b ( |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
+    + lam_E (E - E*)^2 ) with w_b = min(1, exp(-E*/kT_w)) / (1 + (|F_j*|^2 +
+    lam_tau (|tau_i*|^2 + |tau_j*|^2)) / f_scale^2); each factor is 1 when its
+    parameter is None.  (The paper's training pairs are Boltzmann-distributed,
+    coming from simulations at T = 0.2 - 2.0, and it caps large force/torque
+    targets, SI Sec. 6: these weights are their counterparts for uniformly drawn
+    pairs.)
+    pair_cfg: (B, 7) = s, q_rel; labels: (B, 10) =
     E, F_j, tau_i, tau_j (frame of body i).  Returns the loss and dL/dflat
     (zero for mu, inv_sd, e_scale, e_shift, which are not trained).
 
@@ -210,6 +217,12 @@ def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E):
     L = ((Fj - lab[:, 1:4]) ** 2).sum(-1) \
         + lam_tau * (((ti - lab[:, 4:7]) ** 2).sum(-1) + ((tj - lab[:, 7:10]) ** 2).sum(-1)) \
         + lam_E * (E - lab[:, 0]) ** 2
+    if f_scale:
+        mag2 = (lab[:, 1:4] ** 2).sum(-1) + lam_tau * ((lab[:, 4:7] ** 2).sum(-1)
+                                                      + (lab[:, 7:10] ** 2).sum(-1))
+        L = L / (1.0 + mag2 / f_scale ** 2)
+    if kT_w:
+        L = L * torch.exp(-torch.clamp(lab[:, 0], min=0.0) / kT_w)
     L = L.mean()
     (g,) = torch.autograd.grad(L, [flat_t])
     g = g.detach().numpy().copy()

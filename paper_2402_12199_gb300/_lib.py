@@ -40,7 +40,8 @@ class rb_bead_potential(ctypes.Structure):
 
 class rb_system_desc(ctypes.Structure):
     _fields_ = [("body", rb_body_type), ("pot", rb_bead_potential), ("box", ctypes.c_float * 3),
-                ("n_bodies", ctypes.c_int64), ("max_neighbors", ctypes.c_int32)]
+                ("n_bodies", ctypes.c_int64), ("max_neighbors", ctypes.c_int32),
+                ("skin", ctypes.c_float)]
 
 
 class rb_result(ctypes.Structure):
@@ -95,6 +96,7 @@ SIGNATURES = {
     "rb_nn_pairs": (I32, [P, I32, I64, P, P, P]),
     "rb_mlp_sync": (I32, [P]),
     "rb_set_nn_fallback": (I32, [P, F32]),
+    "rb_set_skin": (I32, [P, F32]),
     "rb_nn_fallback_count": (I32, [P, I64P]),
     "rb_system_footprint": (I64, [ctypes.POINTER(rb_system_desc)]),
     "rb_server_create": (I32, [ctypes.c_size_t, I32, P, I32, ctypes.POINTER(P)]),
@@ -108,8 +110,9 @@ SIGNATURES = {
     "rb_sample_pairs": (I32, [P, I64, P, P, P, P]),
     "rb_trainer_create": (I32, [P, I64, F32, F32, F32, F32, ctypes.POINTER(P)]),
     "rb_trainer_destroy": (I32, [P]),
-    "rb_train_grad": (I32, [P, I64, P, P, F32, F32, P, DP]),
-    "rb_train_step": (I32, [P, I64, P, P, F32, F32, DP]),
+    "rb_trainer_set_lr": (I32, [P, F32]),
+    "rb_train_grad": (I32, [P, I64, P, P, F32, F32, F32, F32, P, DP]),
+    "rb_train_step": (I32, [P, I64, P, P, F32, F32, F32, F32, DP]),
     "rb_nn_weight_vjp": (I32, [P, I64, P, P, P, P]),
     "rb_tc_gemm_check": (I32, [I32, I32, P, P, P, P]),
 }

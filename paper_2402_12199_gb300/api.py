@@ -51,7 +51,7 @@ class System:
 
     def __init__(self, n_bodies: int, box, shape: str = "cube", eps: float = 1.0,
                  sigma: float = 1.0, rcut: float = 2.5, max_neighbors: int = 0,
-                 template=None, bead_mass: float = 1.0, stream=None):
+                 template=None, bead_mass: float = 1.0, stream=None, skin: float = 0.0):
         L = load()
         d = _lib.rb_system_desc()
         d.body.shape = SHAPES[shape]
@@ -69,6 +69,7 @@ class System:
             d.box[a] = float(box[a])
         d.n_bodies = int(n_bodies)
         d.max_neighbors = int(max_neighbors)
+        d.skin = float(skin)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         check(L.rb_create_system(ctypes.byref(d), _stream_handle(self.stream), ctypes.byref(h)))
@@ -177,6 +178,9 @@ class System:
         check(load().rb_eval_pairs(self._h, path, mlp.handle if mlp is not None else None,
                                    PRECISION[precision]))
 
+    def set_skin(self, skin: float):
+        check(load().rb_set_skin(self._h, float(skin)))
+
     def set_nn_fallback(self, rho_min: float):
         check(load().rb_set_nn_fallback(self._h, float(rho_min)))
 
@@ -278,23 +282,29 @@ class Trainer:
                 pass
             self._h = None
 
+    def set_lr(self, lr: float):
+        check(load().rb_trainer_set_lr(self._h, float(lr)))
+
     def grad(self, cfg: torch.Tensor, labels: torch.Tensor, lam_tau: float = 1.0,
-             lam_E: float = 0.0):
+             lam_E: float = 0.0, f_scale: float = 0.0, kT_w: float = 0.0):
         _dev(cfg, 8)
         _dev(labels, 12)
         g = torch.empty(self.mlp.n_params, dtype=torch.float32, device="cuda")
         loss = ctypes.c_double()
         check(load().rb_train_grad(self._h, cfg.shape[0], cfg.data_ptr(), labels.data_ptr(),
-                                   lam_tau, lam_E, g.data_ptr(), ctypes.byref(loss)))
+                                   lam_tau, lam_E, f_scale, kT_w, g.data_ptr(),
+                                   ctypes.byref(loss)))
         return loss.value, g
 
     def step(self, cfg: torch.Tensor, labels: torch.Tensor, lam_tau: float = 1.0,
-             lam_E: float = 0.0, want_loss: bool = True):
+             lam_E: float = 0.0, want_loss: bool = True, f_scale: float = 0.0,
+             kT_w: float = 0.0):
         _dev(cfg, 8)
         _dev(labels, 12)
         loss = ctypes.c_double()
         check(load().rb_train_step(self._h, cfg.shape[0], cfg.data_ptr(), labels.data_ptr(),
-                                   lam_tau, lam_E, ctypes.byref(loss) if want_loss else None))
+                                   lam_tau, lam_E, f_scale, kT_w,
+                                   ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
 
     def weight_vjp(self, cfg: torch.Tensor, u_cfg: torch.Tensor, c: torch.Tensor):
@@ -320,7 +330,7 @@ def sample_pairs(system: System, uniforms: torch.Tensor):
 
 
 def _desc(n_bodies: int, box, shape: str = "cube", eps=1.0, sigma=1.0, rcut=2.5,
-          max_neighbors: int = 0):
+          max_neighbors: int = 0, skin: float = 0.0):
     d = _lib.rb_system_desc()
     d.body.shape = SHAPES[shape]
     d.body.bead_mass = 1.0
@@ -331,6 +341,7 @@ def _desc(n_bodies: int, box, shape: str = "cube", eps=1.0, sigma=1.0, rcut=2.5,
         d.box[a] = float(box[a])
     d.n_bodies = int(n_bodies)
     d.max_neighbors = int(max_neighbors)
+    d.skin = float(skin)
     return d
 
 
@@ -370,9 +381,9 @@ class Server:
             pass
 
     def submit(self, state: dict, box, shape: str = "cube", path: int = RB_PATH_BEADS,
-               precision="fp32", n_steps: int = 100, dt: float = 0.002) -> int:
+               precision="fp32", n_steps: int = 100, dt: float = 0.002, skin: float = 0.0) -> int:
         n = len(state["pos"])
-        d = _desc(n, box, shape)
+        d = _desc(n, box, shape, skin=skin)
         arrs = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("pos", "quat", "vel", "angmom")]
         t = ctypes.c_uint64()
         check(load().rb_submit(self._h, ctypes.byref(d), *[a.ctypes.data for a in arrs], path,

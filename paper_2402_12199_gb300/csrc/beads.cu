@@ -20,14 +20,18 @@
 
 namespace rb {
 
-// One warp per listed body pair (persistent grid-stride loop).
+// One warp per listed body pair (persistent grid-stride loop).  Pairs with
+// |R|^2 >= cut2 are skipped: with zero_beyond they get zero results (the bead
+// path, cut2 = Rc^2, pairs listed only because of the skin); without it they
+// keep what is there (the network path's bead fallback, cut2 = rho_min^2,
+// which counts the pairs it evaluates in *count).
 template <int NP>
 __global__ void __launch_bounds__(256)
     k_bead_pairs(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
                  const float4* __restrict__ pos, const float4* __restrict__ quat,
                  const float4* __restrict__ tmpl, int n_beads, float3 L, float3 invL, BeadPot pot,
-                 float4* __restrict__ out_F, float4* __restrict__ out_ti,
-                 float4* __restrict__ out_tj) {
+                 float cut2, int zero_beyond, float4* __restrict__ out_F,
+                 float4* __restrict__ out_ti, float4* __restrict__ out_tj, int* count) {
     __shared__ float4 sT[kMaxBeads];
     __shared__ float4 sN[2 * kMaxBeads];
     load_template(tmpl, n_beads, sT, sN);
@@ -42,6 +46,14 @@ __global__ void __launch_bounds__(256)
         const float4 pi = pos[ij.x], pj = pos[ij.y];
         const float4 qi = quat[ij.x], qj = quat[ij.y];
         const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), L, invL);
+        if (R.x * R.x + R.y * R.y + R.z * R.z >= cut2) {
+            if (zero_beyond && lane == 0) {
+                out_F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                out_ti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                out_tj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            continue;
+        }
         const Mat3 Ri = qmat(qi);
         const Mat3 Rr = qmat(qmul(qconj(qi), qj));
         const float3 s = mulT(Ri, R);
@@ -60,52 +72,8 @@ __global__ void __launch_bounds__(256)
                 const float3 sxF = cross3(s, F);
                 const float3 tj = mul(Ri, make_float3(T.x - sxF.x, T.y - sxF.y, T.z - sxF.z));
                 out_tj[p] = make_float4(tj.x, tj.y, tj.z, 0.f);
+                if (count) atomicAdd(count, 1);
             }
-        }
-    }
-}
-
-// Bead fallback of the network path: the same warp-per-pair bead sum, applied
-// only to listed pairs with |R_ij| < rho_min (a warp-uniform test), which
-// overwrites the network's per-pair results.
-template <int NP>
-__global__ void __launch_bounds__(256)
-    k_bead_fallback(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
-                    const float4* __restrict__ pos, const float4* __restrict__ quat,
-                    const float4* __restrict__ tmpl, int n_beads, float3 L, float3 invL,
-                    BeadPot pot, float rho_min2, float4* __restrict__ out_F,
-                    float4* __restrict__ out_ti, float4* __restrict__ out_tj, int* count) {
-    __shared__ float4 sT[kMaxBeads];
-    __shared__ float4 sN[2 * kMaxBeads];
-    load_template(tmpl, n_beads, sT, sN);
-    __syncthreads();
-    const int n_pairs = *n_pairs_ptr;
-    const int lane = threadIdx.x & 31;
-    const int warps_per_block = blockDim.x >> 5;
-    const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
-    const int nw = gridDim.x * warps_per_block;
-    for (int p = gw; p < n_pairs; p += nw) {
-        const int2 ij = pairs[p];
-        const float4 pi = pos[ij.x], pj = pos[ij.y];
-        const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), L, invL);
-        if (R.x * R.x + R.y * R.y + R.z * R.z >= rho_min2) continue;
-        const float4 qi = quat[ij.x], qj = quat[ij.y];
-        const Mat3 Ri = qmat(qi);
-        const Mat3 Rr = qmat(qmul(qconj(qi), qj));
-        const float3 s = mulT(Ri, R);
-        float v[7];
-        bead_pair_warp<NP>(s, Rr, sT, sN, n_beads, pot, lane, v);
-        if (lane == 0) {
-            const float3 F = make_float3(v[0], v[1], v[2]);
-            const float3 T = make_float3(v[3], v[4], v[5]);
-            const float3 Fs = mul(Ri, F);
-            const float3 ti = mul(Ri, make_float3(-T.x, -T.y, -T.z));
-            const float3 sxF = cross3(s, F);
-            const float3 tj = mul(Ri, make_float3(T.x - sxF.x, T.y - sxF.y, T.z - sxF.z));
-            out_F[p] = make_float4(Fs.x, Fs.y, Fs.z, v[6]);
-            out_ti[p] = make_float4(ti.x, ti.y, ti.z, 0.f);
-            out_tj[p] = make_float4(tj.x, tj.y, tj.z, 0.f);
-            atomicAdd(count, 1);
         }
     }
 }
@@ -121,7 +89,7 @@ BeadPot bead_pot(const rb_system* s) {
 }
 
 template <int NP>
-static rb_status launch_beads(rb_system* s) {
+static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, int* count) {
     static int occ = 0;
     if (occ == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP>, 256, 0);
@@ -132,24 +100,7 @@ static rb_status launch_beads(rb_system* s) {
     const int grid = s->num_sms * occ;
     k_bead_pairs<NP><<<grid, 256, 0, s->stream>>>(
         s->pl.pairs, s->pl.n_pairs, s->pos, s->quat, s->tmpl_dev, s->n_beads, L, invL,
-        bead_pot(s), s->pair_F, s->pair_ti, s->pair_tj);
-    RB_CUDA(cudaGetLastError());
-    return RB_OK;
-}
-
-template <int NP>
-static rb_status launch_fallback(rb_system* s) {
-    static int occ = 0;
-    if (occ == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_fallback<NP>, 256, 0);
-        if (occ <= 0) occ = 1;
-    }
-    const float3 L = make_float3(s->box[0], s->box[1], s->box[2]);
-    const float3 invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
-    k_bead_fallback<NP><<<s->num_sms * occ, 256, 0, s->stream>>>(
-        s->pl.pairs, s->pl.n_pairs, s->pos, s->quat, s->tmpl_dev, s->n_beads, L, invL,
-        bead_pot(s), s->nn_fallback_rho * s->nn_fallback_rho, s->pair_F, s->pair_ti, s->pair_tj,
-        s->fallback_count);
+        bead_pot(s), cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, count);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -157,17 +108,19 @@ static rb_status launch_fallback(rb_system* s) {
 rb_status bead_fallback_async(rb_system* s) {
     RB_CUDA(cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream));
     if (!(s->nn_fallback_rho > 0.f)) return RB_OK;
+    const float r = std::min(s->nn_fallback_rho, s->Rc);
     const int np = (s->n_beads + 63) / 64;
-    if (np <= 2) return launch_fallback<2>(s);
-    if (np <= 3) return launch_fallback<3>(s);
-    return launch_fallback<4>(s);
+    if (np <= 2) return launch_beads<2>(s, r * r, 0, s->fallback_count);
+    if (np <= 3) return launch_beads<3>(s, r * r, 0, s->fallback_count);
+    return launch_beads<4>(s, r * r, 0, s->fallback_count);
 }
 
 rb_status bead_pairs_async(rb_system* s) {
+    const float c2 = s->Rc * s->Rc;
     const int np = (s->n_beads + 63) / 64;
-    if (np <= 2) return launch_beads<2>(s);
-    if (np <= 3) return launch_beads<3>(s);
-    return launch_beads<4>(s);
+    if (np <= 2) return launch_beads<2>(s, c2, 1, nullptr);
+    if (np <= 3) return launch_beads<3>(s, c2, 1, nullptr);
+    return launch_beads<4>(s, c2, 1, nullptr);
 }
 
 }  // namespace rb

@@ -344,6 +344,7 @@ rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     src.quat = s->quat;
     src.L = make_float3(s->box[0], s->box[1], s->box[2]);
     src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
+    src.Rc2 = s->Rc * s->Rc;
     PairDst dst{};
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;

@@ -51,6 +51,7 @@ struct PairSrc {
     const float4* pos;
     const float4* quat;
     float3 L, invL;
+    float Rc2;  // pairs with |R|^2 >= Rc2 (listed within the skin only) give zero
     // explicit mode: configurations in the frame of body i, 2 float4 per pair
     const float4* cfg;
     int64_t n_explicit;
@@ -70,6 +71,7 @@ struct PairGeom {
     float4 qi;  // orientation of body i (identity in explicit mode)
     float sgn;
     float rho;
+    bool beyond;  // system mode: pair outside the cutoff, outputs are zero
 };
 
 template <bool SYSTEM>
@@ -79,6 +81,7 @@ __device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid)
     g.qc = make_float4(1.f, 0.f, 0.f, 0.f);
     g.qi = make_float4(1.f, 0.f, 0.f, 0.f);
     g.sgn = 1.f;
+    g.beyond = false;
     float4 qr = g.qc;
     if (valid) {
         if (SYSTEM) {
@@ -88,6 +91,7 @@ __device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid)
             const float4 qj = src.quat[ij.y];
             const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), src.L,
                                        src.invL);
+            g.beyond = R.x * R.x + R.y * R.y + R.z * R.z >= src.Rc2;
             g.s = mulT(qmat(g.qi), R);
             qr = qmul(qconj(g.qi), qj);
         } else {
@@ -140,6 +144,12 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
     const float3 ti = make_float3(sxG.x - tj.x, sxG.y - tj.y, sxG.z - tj.z);
     const float3 Fj = make_float3(-Gs.x, -Gs.y, -Gs.z);
     if (SYSTEM) {
+        if (g.beyond) {
+            dst.F[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+            dst.ti[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+            dst.tj[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
         const Mat3 Ri = qmat(g.qi);
         const float3 a = mul(Ri, Fj), b = mul(Ri, ti), c = mul(Ri, tj);
         dst.F[gp] = make_float4(a.x, a.y, a.z, E);

@@ -5,9 +5,10 @@
 // (Methods), forces/torques as its gradients (SI Sec. 6), here with the layer
 // GEMMs of the forward and of the reverse pass on tcgen05.mma.
 //
-// One CTA (4 warps, 128 threads) per SM, persistent over tiles of 128 pairs;
-// thread r owns pair r of the tile (TMEM lane r) for the features, every
-// epilogue and the geometric adjoint.  Shared memory (BF16, K-major, 128-byte
+// One CTA (8 warps) per SM, persistent over tiles of 128 pairs.  Warp w reads
+// TMEM lanes 32 (w % 4) .. + 31 (pairs of the tile) and, in every epilogue,
+// columns 64 (w / 4) .. + 63; the first warpgroup also computes the features
+// and the geometric adjoint of its pair.  Shared memory (BF16, K-major, 128-byte
 // swizzle) holds all weights for the whole launch:
 //   W1f [128 x 64]  (layer-1 weights, input features padded from 10 to 64)
 //   W2f, W3f [128 x 128]           forward B operands (W[out][in])
@@ -38,7 +39,8 @@ constexpr int kM = 128;          // pairs per tile (MMA M, TMEM lanes)
 constexpr int kW = 128;          // hidden width handled by this kernel
 constexpr int kK1 = 64;          // layer-1 K (10 features padded)
 constexpr int kNX = 16;          // reverse output columns (10 padded)
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;         // two warpgroups: TMEM lane group = warp % 4, column half = warp / 4
+constexpr int kCheckThreads = 128;
 
 // Byte offset of element (row r, col c) in a K-major, 128-byte-swizzled BF16
 // tile of `rows` rows: 64-column atoms stacked along K, 8-row groups of
@@ -208,7 +210,7 @@ __host__ __device__ inline Layout layout(int D) {
     L.h = o;
     o += kM * kW * 2;
     L.f32 = o;              // b_1..b_D, w_o, mu, inv_sd
-    o += (D * kW + kW + 32) * 4;
+    o += (D * kW + kW + 32 + kM) * 4;  // + per-row energy partials of warpgroup 1
     L.bar = (o + 15) & ~15u;
     L.total = L.bar + 64;
     return L;
@@ -270,11 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const Layout Ly = layout(D);
     const FlatLayout fl = flat_layout(kW, D);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = (warp & 3) * 32 + (tid & 31);   // TMEM lane = pair of the tile
+    const int half = warp >> 2;                      // column half of every epilogue
+    const int cbeg = half * (kW / 2);
     float* f32 = reinterpret_cast<float*>(sm + Ly.f32);
     float* bias = f32;               // D x 128
     float* wo = f32 + D * kW;        // 128
     float* mu = wo + kW;             // 16
     float* isd = mu + 16;            // 16
+    float* epart = isd + 16;         // 128 energy partials (column half 1)
     uint64_t* bar_ptr = reinterpret_cast<uint64_t*>(sm + Ly.bar);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Ly.bar + 16);
     const uint32_t bar = smem_u32(bar_ptr);
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_field = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_field = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t rev_col = (uint32_t)(D * kW);  // reverse accumulators
     const float b_o = flat[fl.bo], e_scale = flat[fl.escale], e_shift = flat[fl.eshift];
     const uint32_t idesc_w = idesc_bf16(kM, kW);
@@ -335,10 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     } while (0)
 
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t gp = tile * kM + tid;
+        const int64_t gp = tile * kM + row;
         const bool valid = gp < n_total;
-        const PairGeom geo = load_pair<SYSTEM>(src, gp, valid);
-        {
+        const PairGeom geo = load_pair<SYSTEM>(src, gp, valid && half == 0);
+        if (half == 0) {
             float x[kIn];
             raw_features(geo, x);
             float xr[16];
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 w.y = pack_bf16(xr[8 * q + 2], xr[8 * q + 3]);
                 w.z = pack_bf16(xr[8 * q + 4], xr[8 * q + 5]);
                 w.w = pack_bf16(xr[8 * q + 6], xr[8 * q + 7]);
-                *reinterpret_cast<uint4*>(Xt + sw128_offset(kM, tid, 8 * q)) = w;
+                *reinterpret_cast<uint4*>(Xt + sw128_offset(kM, row, 8 * q)) = w;
             }
         }
         float E = 0.f;
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* b = bias + (l - 1) * kW;
             float e_acc = 0.f;
 #pragma unroll 1
-            for (int c = 0; c < kW; c += 32) {
+            for (int c = cbeg; c < cbeg + kW / 2; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + lane_field + dcol + c, v);
 #pragma unroll
@@ -380,9 +386,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         v[i] = wo[c + i] * sg * (1.f + z * (1.f - sg));  // g_D
                     }
                 }
-                store_row32(Ht, kM, tid, c, v);
+                store_row32(Ht, kM, row, c, v);
             }
-            if (l == D) E = e_scale * (e_acc + b_o) + e_shift;
+            if (l == D) {
+                if (half == 1) epart[row] = e_acc;
+                __syncthreads();
+                if (half == 0) E = e_scale * (e_acc + epart[row] + b_o) + e_shift;
+            }
         }
         // ---------------- reverse: g_{l-1} = (g_l W_l) * silu'(z_{l-1})
         for (int l = D; l >= 2 && ok; --l) {
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t zcol = (uint32_t)((l - 2) * kW);
             const float* b = bias + (l - 2) * kW;
 #pragma unroll 1
-            for (int c = 0; c < kW; c += 32) {
+            for (int c = cbeg; c < cbeg + kW / 2; c += 32) {
                 float v[32], z[32];
                 tmem_ld32(tmem + lane_field + rev_col + c, v);
                 tmem_ld32(tmem + lane_field + zcol + c, z);
@@ -401,14 +411,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float sg = sigm(zz);
                     v[i] *= sg * (1.f + zz * (1.f - sg));
                 }
-                store_row32(Ht, kM, tid, c, v);
+                store_row32(Ht, kM, row, c, v);
             }
         }
         // ---------------- dE/dx_hat = g_1 W_1 (16 padded columns)
         if (ok) {
             TC_STAGE(tmem + rev_col, s_base + Ly.h, s_base + Ly.w1b, kW, kNX, idesc_x);
         }
-        if (ok) {
+        if (ok && half == 0) {
             float v[16];
             tmem_ld16(tmem + lane_field + rev_col, v);  // warp-collective: all lanes
             if (valid) {
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Single-GEMM check of the tensor-core path (test hook): D[128 x N] =
 // A[128 x K] B[N x K]^T with BF16 operands staged through the same swizzled
 // layouts, descriptors and TMEM read-back as the network kernel.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kCheckThreads, 1)
     k_tc_gemm_check(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ Dout,
                     int N, int K, unsigned* status) {
     extern __shared__ unsigned char smem_raw[];
@@ -444,11 +454,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* bar_ptr = reinterpret_cast<uint64_t*>(Bt + N * K * 2);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(Bt + N * K * 2 + 16);
     const uint32_t bar = smem_u32(bar_ptr);
-    for (int t = tid; t < kM * K; t += kThreads) {
+    for (int t = tid; t < kM * K; t += kCheckThreads) {
         const int r = t / K, c = t % K;
         *reinterpret_cast<__nv_bfloat16*>(At + sw128_offset(kM, r, c)) = __float2bfloat16_rn(A[t]);
     }
-    for (int t = tid; t < N * K; t += kThreads) {
+    for (int t = tid; t < N * K; t += kCheckThreads) {
         const int r = t / K, c = t % K;
         *reinterpret_cast<__nv_bfloat16*>(Bt + sw128_offset(N, r, c)) = __float2bfloat16_rn(B[t]);
     }
@@ -535,6 +545,7 @@ rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m) {
     src.quat = s->quat;
     src.L = make_float3(s->box[0], s->box[1], s->box[2]);
     src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
+    src.Rc2 = s->Rc * s->Rc;
     PairDst dst{};
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;
@@ -570,7 +581,7 @@ extern "C" rb_status rb_tc_gemm_check(int32_t N, int32_t K, const float* A, cons
     const size_t smem = (size_t)(tc::kM + N) * K * 2 + 64 + 1024;
     RB_CUDA(cudaFuncSetAttribute(tc::k_tc_gemm_check, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    tc::k_tc_gemm_check<<<1, tc::kThreads, smem, st>>>(A, B, D, N, K, status);
+    tc::k_tc_gemm_check<<<1, tc::kCheckThreads, smem, st>>>(A, B, D, N, K, status);
     RB_CUDA(cudaGetLastError());
     unsigned h = 0;
     RB_CUDA(cudaMemcpyAsync(&h, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

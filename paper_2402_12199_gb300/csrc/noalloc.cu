@@ -52,7 +52,9 @@ constexpr size_t kOffPairs = kOffBlockSum + align256(sizeof(int) * (kNoAllocMaxB
 constexpr size_t kOffPairF = kOffPairs + align256(sizeof(int2) * kNoAllocMaxPairs);
 constexpr size_t kOffPairTi = kOffPairF + align256(sizeof(float4) * kNoAllocMaxPairs);
 constexpr size_t kOffPairTj = kOffPairTi + align256(sizeof(float4) * kNoAllocMaxPairs);
-constexpr size_t kNoAllocScratchBytes = kOffPairTj + align256(sizeof(float4) * kNoAllocMaxPairs);
+constexpr size_t kOffPosRef = kOffPairTj + align256(sizeof(float4) * kNoAllocMaxPairs);
+constexpr size_t kOffRebuild = kOffPosRef + align256(sizeof(float4) * kNoAllocMaxBodies);
+constexpr size_t kNoAllocScratchBytes = kOffRebuild + 256;
 
 // The scratch array.  Host code must not use its name as an address: it only
 // names a host-side shadow.  The device address comes from
@@ -172,6 +174,8 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     s.pl.lower_nbr = reinterpret_cast<int*>(base + kOffLowerNbr);
     s.pl.half_off = reinterpret_cast<int*>(base + kOffHalfOff);
     s.pl.local_off = reinterpret_cast<int*>(base + kOffLocalOff);
+    s.pos_ref = reinterpret_cast<float4*>(base + kOffPosRef);
+    s.rebuild_flag = reinterpret_cast<int*>(base + kOffRebuild);
     s.pl.block_sum = reinterpret_cast<int*>(base + kOffBlockSum);
     s.pl.pairs = reinterpret_cast<int2*>(base + kOffPairs);
     s.pair_F = reinterpret_cast<float4*>(base + kOffPairF);
@@ -187,10 +191,11 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     RB_CUDA(cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev));
 
     // The scratch keeps the previous call's contents: clear the status word
-    // (cell counts are cleared by the pair-list build itself).
+    // and the cell counts (this call's cell grid may differ from the last).
     RB_CUDA(cudaMemcpyAsync(s.tmpl_dev, tmpl, sizeof(float4) * nb, cudaMemcpyHostToDevice, s.stream));
     RB_CUDA(cudaMemsetAsync(s.status_dev, 0, sizeof(unsigned), s.stream));
-    RB_TRY(build_pairs_async(&s));
+    RB_CUDA(cudaMemsetAsync(s.cells.count, 0, sizeof(int) * n_cells, s.stream));
+    RB_TRY(build_pairs_async(&s, true));
     RB_TRY(bead_pairs_async(&s));
     RB_TRY(reduce_forces_async(&s, 0.f));
     unsigned st = 0;

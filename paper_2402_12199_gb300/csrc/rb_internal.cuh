@@ -172,11 +172,17 @@ struct rb_system {
     // evaluated by the bead sum instead (0 = off); count of such pairs
     float nn_fallback_rho = 0.f;
     int* fallback_count = nullptr;
+    // Verlet skin: the list holds pairs within Rc + skin and is rebuilt only
+    // when a centre has moved more than skin / 2 since the last build
+    // (decided on the device: rebuild_flag); pair kernels skip |R| >= Rc.
+    float skin = 0.f;
+    float4* pos_ref = nullptr;
+    int* rebuild_flag = nullptr;
 };
 
 namespace rb {
 // system.cu
-rb_status build_pairs_async(rb_system* s);
+rb_status build_pairs_async(rb_system* s, bool force);  // force: rebuild regardless of the skin
 rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
 rb_status energy_async(rb_system* s);
 // beads.cu

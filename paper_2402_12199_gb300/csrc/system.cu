@@ -40,7 +40,9 @@ __device__ inline float wrap1(float x, float L, float invL) {
 
 __global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, float3 invL,
                               float3 invw, int3 nc, int* __restrict__ count,
-                              int* __restrict__ bodies, int cap, unsigned* status) {
+                              int* __restrict__ bodies, int cap, unsigned* status,
+                              const int* __restrict__ rebuild) {
+    if (!*rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float4 p = pos[i];
@@ -80,7 +82,8 @@ __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, fl
                              const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
                              int* __restrict__ half_count, int* __restrict__ half_nbr,
                              int* __restrict__ lower_count, int* __restrict__ lower_nbr,
-                             unsigned* status) {
+                             unsigned* status, const int* __restrict__ rebuild) {
+    if (!*rebuild) return;
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
@@ -152,7 +155,8 @@ __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, fl
 constexpr int kScanBlock = 1024;
 
 __global__ void k_scan_local(const int* __restrict__ cnt, int N, int* __restrict__ local_off,
-                             int* __restrict__ block_sum) {
+                             int* __restrict__ block_sum, const int* __restrict__ rebuild) {
+    if (!*rebuild) return;
     __shared__ int warp_tot[32];
     const int i = blockIdx.x * kScanBlock + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -179,7 +183,9 @@ __global__ void k_scan_local(const int* __restrict__ cnt, int N, int* __restrict
 }
 
 __global__ void k_scan_top(int* __restrict__ block_sum, int nb, int N, int* __restrict__ half_off,
-                           int* total, int64_t cap_pairs, unsigned* status) {
+                           int* total, int64_t cap_pairs, unsigned* status,
+                           const int* __restrict__ rebuild) {
+    if (!*rebuild) return;
     __shared__ int sh[1024];
     const int t = threadIdx.x;
     const int chunk = (nb + 1023) / 1024;
@@ -217,7 +223,9 @@ __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_cou
                             const int* __restrict__ half_nbr, const int* __restrict__ local_off,
                             const int* __restrict__ block_prefix, int* __restrict__ half_off,
                             const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
-                            int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status) {
+                            int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status,
+                            const int* __restrict__ rebuild) {
+    if (!*rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int off = local_off[i] + block_prefix[i / kScanBlock];
@@ -246,6 +254,35 @@ __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_cou
             lrow[m] = offj + found;
         }
     }
+}
+
+// After a rebuild: remember the positions the list was built for, clear the
+// cell counts for the next rebuild, and lower the flag.
+__global__ void k_pair_finish(int N, int n_cells, const float4* __restrict__ pos,
+                              float4* __restrict__ pos_ref, int* __restrict__ cell_count,
+                              int* rebuild) {
+    if (!*rebuild) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) pos_ref[t] = pos[t];
+    if (t < n_cells) cell_count[t] = 0;
+    __syncthreads();
+    // the flag is read by every CTA above; it is cleared by the last kernel of
+    // the build in stream order, so clear it in a separate one-thread kernel
+}
+
+__global__ void k_flag_clear(int* rebuild) { *rebuild = 0; }
+__global__ void k_flag_set(int* rebuild) { *rebuild = 1; }
+
+// Raise the rebuild flag if any centre moved more than half the skin since the
+// positions the list was built for (minimum image).
+__global__ void k_skin_check(int N, float half_skin2, float3 L, float3 invL,
+                             const float4* __restrict__ pos, const float4* __restrict__ pos_ref,
+                             int* rebuild) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 a = pos[i], b = pos_ref[i];
+    const float3 d = min_image(make_float3(a.x - b.x, a.y - b.y, a.z - b.z), L, invL);
+    if (d.x * d.x + d.y * d.y + d.z * d.z > half_skin2) *rebuild = 1;
 }
 
 // Per-body reduction of the per-pair results in a fixed order (own half row by
@@ -434,28 +471,38 @@ static inline int blocks_for(int64_t n, int t) { return (int)std::max<int64_t>(1
 static inline float3 f3(const float* a) { return make_float3(a[0], a[1], a[2]); }
 static inline float3 inv3(const float* a) { return make_float3(1.f / a[0], 1.f / a[1], 1.f / a[2]); }
 
-rb_status build_pairs_async(rb_system* s) {
+rb_status build_pairs_async(rb_system* s, bool force) {
     const int N = (int)s->N;
     const float3 L = f3(s->box), invL = inv3(s->box);
     const float3 invw = inv3(s->cells.width);
     const int3 nc = make_int3(s->cells.nc[0], s->cells.nc[1], s->cells.nc[2]);
-    RB_CUDA(cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream));
+    const float Rl = s->Rc + s->skin;
+    if (force || !(s->skin > 0.f)) {
+        k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+    } else {
+        k_skin_check<<<blocks_for(N, 256), 256, 0, s->stream>>>(
+            N, 0.25f * s->skin * s->skin, L, invL, s->pos, s->pos_ref, s->rebuild_flag);
+    }
     k_cell_assign<<<blocks_for(N, 256), 256, 0, s->stream>>>(s->pos, N, L, invL, invw, nc,
                                                              s->cells.count, s->cells.bodies,
-                                                             s->cells.cap, s->status_dev);
+                                                             s->cells.cap, s->status_dev,
+                                                             s->rebuild_flag);
     k_pair_build<<<blocks_for((int64_t)N * 32, 256), 256, 0, s->stream>>>(
-        s->pos, N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap,
-        s->Rc * s->Rc, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.lower_count,
-        s->pl.lower_nbr, s->status_dev);
+        s->pos, N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap, Rl * Rl,
+        s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.lower_count, s->pl.lower_nbr,
+        s->status_dev, s->rebuild_flag);
     const int nb = (N + kScanBlock - 1) / kScanBlock;
     k_scan_local<<<nb, kScanBlock, 0, s->stream>>>(s->pl.half_count, N, s->pl.local_off,
-                                                   s->pl.block_sum);
+                                                   s->pl.block_sum, s->rebuild_flag);
     k_scan_top<<<1, 1024, 0, s->stream>>>(s->pl.block_sum, nb, N, s->pl.half_off, s->pl.n_pairs,
-                                          s->pl.cap_pairs, s->status_dev);
+                                          s->pl.cap_pairs, s->status_dev, s->rebuild_flag);
     k_pair_emit<<<blocks_for(N, 256), 256, 0, s->stream>>>(
         N, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.local_off, s->pl.block_sum,
         s->pl.half_off, s->pl.lower_count, s->pl.lower_nbr, s->pl.pairs, s->pl.cap_pairs,
-        s->status_dev);
+        s->status_dev, s->rebuild_flag);
+    k_pair_finish<<<blocks_for(std::max(N, s->cells.n_cells), 256), 256, 0, s->stream>>>(
+        N, s->cells.n_cells, s->pos, s->pos_ref, s->cells.count, s->rebuild_flag);
+    k_flag_clear<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -606,6 +653,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
         s->u_shift = (float)(4.0 * s->eps * (sr6 * sr6 - sr6));
     }
     s->Rc = (float)(2.0 * rmax + s->rcut);
+    s->skin = 0.f;
     for (int a = 0; a < 3; ++a) {
         s->box[a] = d->box[a];
         if (!(d->box[a] >= 2.f * s->Rc)) {
@@ -654,6 +702,8 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     ALLOC(s->red_out, sizeof(double) * 16);
     ALLOC(s->status_dev, sizeof(unsigned));
     ALLOC(s->fallback_count, sizeof(int));
+    ALLOC(s->pos_ref, sizeof(float4) * N);
+    ALLOC(s->rebuild_flag, sizeof(int));
 #undef ALLOC
     if (e != cudaSuccess) {
         rb_status st = cuda_fail(e, "cudaMalloc (system)");
@@ -668,6 +718,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     if (e == cudaSuccess) e = cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->pl.n_pairs, 0, sizeof(int), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->angmom, 0, sizeof(float4) * N, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->vel, 0, sizeof(float4) * N, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -675,6 +726,13 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
         rb_status st = cuda_fail(e, "system initialisation");
         rb_destroy_system(s);
         return st;
+    }
+    if (d->skin > 0.f) {
+        rb_status st = rb_set_skin(s, d->skin);
+        if (st != RB_OK) {
+            rb_destroy_system(s);
+            return st;
+        }
     }
     *out = s;
     return RB_OK;
@@ -717,7 +775,7 @@ rb_status rb_destroy_system(rb_system* s) {
                     s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
                     s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
                     s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev,
-                    s->fallback_count};
+                    s->fallback_count, s->pos_ref, s->rebuild_flag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -751,6 +809,7 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
     if (quat) RB_CUDA(cudaMemcpyAsync(s->quat, quat, b, k, s->stream));
     if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
     if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
+    if (pos) k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
     s->forces_valid = false;
     return RB_OK;
 }
@@ -780,7 +839,7 @@ rb_status rb_get_forces(const rb_system* s, float* force, float* torque, int32_t
 
 rb_status rb_build_pairs(rb_system* s, int64_t* n_pairs) {
     if (!s) return fail(RB_EINVAL, "null system");
-    RB_TRY(build_pairs_async(s));
+    RB_TRY(build_pairs_async(s, true));
     if (n_pairs) {
         RB_TRY(check_status(s));
         int n = 0;
@@ -825,7 +884,7 @@ static rb_status finish_forces(rb_system* s, float* force, float* torque, double
 rb_status rb_forces_beads(rb_system* s, float* force, float* torque, double* energy,
                           double* virial9) {
     if (!s) return fail(RB_EINVAL, "null system");
-    RB_TRY(build_pairs_async(s));
+    RB_TRY(build_pairs_async(s, false));
     RB_TRY(bead_pairs_async(s));
     RB_TRY(reduce_forces_async(s, 0.f));
     s->forces_valid = true;
@@ -839,7 +898,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
                        float* torque, double* energy, double* virial9) {
     if (!s) return fail(RB_EINVAL, "null system");
     RB_TRY(check_mlp(m));
-    RB_TRY(build_pairs_async(s));
+    RB_TRY(build_pairs_async(s, false));
     RB_TRY(nn_pairs_system_async(s, m, precision));
     RB_TRY(bead_fallback_async(s));
     RB_TRY(reduce_forces_async(s, 0.f));
@@ -853,7 +912,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
 
 static rb_status eval_forces_async(rb_system* s, int path, const rb_mlp* m, int precision,
                                    float kick) {
-    RB_TRY(build_pairs_async(s));
+    RB_TRY(build_pairs_async(s, false));
     if (path == RB_PATH_BEADS) {
         RB_TRY(bead_pairs_async(s));
     } else {
@@ -933,6 +992,32 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
         g.dt = dt;
     }
     for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
+    return RB_OK;
+}
+
+rb_status rb_set_skin(rb_system* s, float skin) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (!(skin >= 0.f)) return fail(RB_EINVAL, "skin must be >= 0");
+    for (int a = 0; a < 3; ++a)
+        if (!(s->box[a] >= 2.f * (s->Rc + skin)))
+            return fail(RB_EINVAL, "every box side must be at least twice Rc + skin");
+    if (skin != s->skin) {
+        s->skin = skin;
+        for (int a = 0; a < 3; ++a) {
+            const int nc = std::max(1, (int)std::floor(s->box[a] / (s->Rc + skin)));
+            if (nc > s->cells.nc[a]) return fail(RB_EINVAL, "internal: cell grid grew");
+            s->cells.nc[a] = nc;
+            s->cells.width[a] = s->box[a] / nc;
+        }
+        s->cells.n_cells = s->cells.nc[0] * s->cells.nc[1] * s->cells.nc[2];
+        RB_CUDA(cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream));
+        k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+        s->forces_valid = false;
+        if (s->graph.exec) {
+            cudaGraphExecDestroy(s->graph.exec);
+            s->graph.exec = nullptr;
+        }
+    }
     return RB_OK;
 }
 

@@ -12,8 +12,14 @@
 // energy) with a loss whose weight gradient needs the derivative of the
 // network's input gradient:
 //
-//   l_b  = |F_j - F*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
-//          + lam_E (E - E*)^2,           L = mean_b l_b
+//   l_b  = w_b [ |F_j - F*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
+//          + lam_E (E - E*)^2 ],         L = mean_b l_b,
+//   w_b  = min(1, exp(-E* / kT_w)) / (1 + (|F*|^2 + lam_tau (|tau_i*|^2 +
+//          |tau_j*|^2)) / f_scale^2)
+//   (each factor 1 when its parameter is 0).  The paper's training pairs come
+//   from simulations at T = 0.2 - 2.0, i.e. Boltzmann-weighted, and it caps
+//   large force/torque targets (SI Sec. 6); pairs drawn uniformly here get the
+//   Boltzmann factor and a smooth force cap as importance weights instead.
 //   With G = dE/d(s, q) the outputs are linear in G, so dl/dG = v (7 numbers)
 //   and dL/dW = d/dW sum_b [u_b . grad_(s,q) E_hat_b + c_b E_hat_b]
 //   (u = e_scale v / B, c = e_scale dl/dE / B): a forward pass carrying the
@@ -259,7 +265,8 @@ __global__ void k_tr_w1(int W, const float* __restrict__ G16, float* __restrict_
 // the per-block FP64 loss partial sums.
 __global__ void k_tr_residual(int64_t n, const float4* __restrict__ cfg, const float4* __restrict__ pred,
                               const float4* __restrict__ lab, float lam_tau, float lam_E,
-                              const float* __restrict__ escale, float inv_n,
+                              float inv_f2, float inv_kTw, const float* __restrict__ escale,
+                              float inv_n,
                               float4* __restrict__ ucfg, float* __restrict__ c,
                               double* __restrict__ part) {
     __shared__ double sh[256];
@@ -275,14 +282,22 @@ __global__ void k_tr_residual(int64_t n, const float4* __restrict__ cfg, const f
         const float3 di = make_float3(p1.x - l1.x, p1.y - l1.y, p1.z - l1.z);
         const float3 dj = make_float3(p2.x - l2.x, p2.y - l2.y, p2.z - l2.z);
         const float dE = p0.w - l0.w;
-        l = (double)(dF.x * dF.x + dF.y * dF.y + dF.z * dF.z) +
-            lam_tau * (double)(di.x * di.x + di.y * di.y + di.z * di.z + dj.x * dj.x + dj.y * dj.y +
-                               dj.z * dj.z) +
-            lam_E * (double)dE * dE;
-        // dl/dF = 2 dF, dl/dtau_i = 2 lam di, dl/dtau_j = 2 lam dj
-        const float3 rF = make_float3(2.f * dF.x, 2.f * dF.y, 2.f * dF.z);
-        const float3 ri = make_float3(2.f * lam_tau * di.x, 2.f * lam_tau * di.y, 2.f * lam_tau * di.z);
-        const float3 rj = make_float3(2.f * lam_tau * dj.x, 2.f * lam_tau * dj.y, 2.f * lam_tau * dj.z);
+        // per-sample weight 1 / (1 + |label|^2 / f_scale^2): relative error for
+        // large forces, absolute for small ones (1 when inv_f2 = 0)
+        const float mag2 = l0.x * l0.x + l0.y * l0.y + l0.z * l0.z +
+                           lam_tau * (l1.x * l1.x + l1.y * l1.y + l1.z * l1.z + l2.x * l2.x +
+                                      l2.y * l2.y + l2.z * l2.z);
+        // Boltzmann importance weight min(1, exp(-E* / kT_w)) (1 when inv_kTw = 0)
+        const float wgt = __expf(-fmaxf(l0.w, 0.f) * inv_kTw) / (1.f + mag2 * inv_f2);
+        l = wgt * ((double)(dF.x * dF.x + dF.y * dF.y + dF.z * dF.z) +
+                   lam_tau * (double)(di.x * di.x + di.y * di.y + di.z * di.z + dj.x * dj.x +
+                                      dj.y * dj.y + dj.z * dj.z) +
+                   lam_E * (double)dE * dE);
+        // dl/dF = 2 w dF, dl/dtau_i = 2 w lam di, dl/dtau_j = 2 w lam dj
+        const float a2 = 2.f * wgt, b2 = 2.f * wgt * lam_tau;
+        const float3 rF = make_float3(a2 * dF.x, a2 * dF.y, a2 * dF.z);
+        const float3 ri = make_float3(b2 * di.x, b2 * di.y, b2 * di.z);
+        const float3 rj = make_float3(b2 * dj.x, b2 * dj.y, b2 * dj.z);
         // F_j = -G_s, tau_i = s x G_s - tau_j, tau_j = -1/2 (-G_w v + w G_v + v x G_v)
         const float3 rixs = cross3(ri, s);
         const float3 us = make_float3(-rF.x + rixs.x, -rF.y + rixs.y, -rF.z + rixs.z);
@@ -295,7 +310,7 @@ __global__ void k_tr_residual(int64_t n, const float4* __restrict__ cfg, const f
                                       -0.5f * (w * rv.z + rvxv.z));
         ucfg[2 * b] = make_float4(scale * us.x, scale * us.y, scale * us.z, 0.f);
         ucfg[2 * b + 1] = make_float4(scale * uw, scale * uv.x, scale * uv.y, scale * uv.z);
-        c[b] = scale * 2.f * lam_E * dE;
+        c[b] = scale * 2.f * wgt * lam_E * dE;
     }
     sh[threadIdx.x] = l;
     __syncthreads();
@@ -423,7 +438,8 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
 }
 
 static rb_status train_grad(rb_trainer* tr, int64_t B, const float* cfg, const float* labels,
-                            float lam_tau, float lam_E, double* loss_host) {
+                            float lam_tau, float lam_E, float f_scale, float kT_w,
+                            double* loss_host) {
     rb_mlp* m = tr->mlp;
     const int W = m->width, D = m->depth;
     TrWork w = tr_work(tr->work, tr->max_batch, W, D);
@@ -436,7 +452,9 @@ static rb_status train_grad(rb_trainer* tr, int64_t B, const float* cfg, const f
     k_tr_residual<<<nb, 256, 0, st>>>(B, reinterpret_cast<const float4*>(cfg),
                                       reinterpret_cast<const float4*>(w.pred),
                                       reinterpret_cast<const float4*>(labels), lam_tau, lam_E,
-                                      m->params + fl.escale, 1.f / (float)B,
+                                      f_scale > 0.f ? 1.f / (f_scale * f_scale) : 0.f,
+                                      kT_w > 0.f ? 1.f / kT_w : 0.f, m->params + fl.escale,
+                                      1.f / (float)B,
                                       reinterpret_cast<float4*>(w.ucfg), w.c, tr->loss_part);
     k_sum_partials<<<1, 32, 0, st>>>(tr->loss_part, (int)nb, 1.0 / (double)B, tr->loss_out);
     RB_TRY(weight_vjp(tr, B, reinterpret_cast<const float4*>(cfg),
@@ -509,6 +527,12 @@ rb_status rb_trainer_create(rb_mlp* mlp, int64_t max_batch, float lr, float beta
     return RB_OK;
 }
 
+rb_status rb_trainer_set_lr(rb_trainer* t, float lr) {
+    if (!t || !(lr > 0.f)) return fail(RB_EINVAL, "need a trainer and lr > 0");
+    t->lr = lr;
+    return RB_OK;
+}
+
 rb_status rb_trainer_destroy(rb_trainer* t) {
     if (!t) return RB_OK;
     if (t->mlp && t->mlp->stream) cudaStreamSynchronize(t->mlp->stream);
@@ -520,10 +544,11 @@ rb_status rb_trainer_destroy(rb_trainer* t) {
 }
 
 rb_status rb_train_grad(rb_trainer* t, int64_t batch, const float* cfg, const float* labels,
-                        float lam_tau, float lam_E, float* grad_out, double* loss_host) {
+                        float lam_tau, float lam_E, float f_scale, float kT_w, float* grad_out,
+                        double* loss_host) {
     if (!t || !cfg || !labels) return fail(RB_EINVAL, "null argument");
     if (batch < 1 || batch > t->max_batch) return fail(RB_EINVAL, "batch out of range");
-    RB_TRY(train_grad(t, batch, cfg, labels, lam_tau, lam_E, loss_host));
+    RB_TRY(train_grad(t, batch, cfg, labels, lam_tau, lam_E, f_scale, kT_w, loss_host));
     if (grad_out)
         RB_CUDA(cudaMemcpyAsync(grad_out, t->grad, sizeof(float) * t->mlp->n_params,
                                 cudaMemcpyDeviceToDevice, t->mlp->stream));
@@ -531,10 +556,11 @@ rb_status rb_train_grad(rb_trainer* t, int64_t batch, const float* cfg, const fl
 }
 
 rb_status rb_train_step(rb_trainer* t, int64_t batch, const float* cfg, const float* labels,
-                        float lam_tau, float lam_E, double* loss_host) {
+                        float lam_tau, float lam_E, float f_scale, float kT_w,
+                        double* loss_host) {
     if (!t || !cfg || !labels) return fail(RB_EINVAL, "null argument");
     if (batch < 1 || batch > t->max_batch) return fail(RB_EINVAL, "batch out of range");
-    RB_TRY(train_grad(t, batch, cfg, labels, lam_tau, lam_E, loss_host));
+    RB_TRY(train_grad(t, batch, cfg, labels, lam_tau, lam_E, f_scale, kT_w, loss_host));
     rb_mlp* m = t->mlp;
     t->t += 1;
     const float c1 = 1.f - std::pow(t->beta1, (float)t->t);

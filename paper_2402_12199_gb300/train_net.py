@@ -1,0 +1,81 @@
+"""Fit the pair energy network to bead-sum forces and torques on the device.
+
+Every numerical step runs in the library: rb_sample_pairs draws and labels the
+training pairs (bead sum), rb_train_step computes the force-matching loss
+gradient and applies Adam, rb_nn_pairs evaluates held-out pairs.  This module
+only sequences those calls (and picks the energy scale from label statistics
+read back once).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import api, inputs
+
+
+def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_samples: int = 200_000,
+                  steps: int = 3000, batch: int = 4096, lr: float = 1e-3, lam_tau: float = 1.0,
+                  lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
+                  log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0):
+    """Returns (mlp, report).  The network's feature normalisation spans the
+    separations contact..Rc; e_scale and e_shift come from the label energies."""
+    box = 60.0 if shape == "cube" else 70.0
+    sysobj = api.System(8, [box] * 3, shape)
+    Rc = sysobj.pair_cutoff
+    u = torch.from_numpy(inputs.sampler_uniforms(n_samples + 10000, seed)).cuda()
+    t0 = time.perf_counter()
+    cfg, lab, rho_c = api.sample_pairs(sysobj, u)
+    torch.cuda.synchronize()
+    t_sample = time.perf_counter() - t0
+    cfg_tr, lab_tr = cfg[:n_samples], lab[:n_samples]
+    cfg_te, lab_te = cfg[n_samples:], lab[n_samples:]
+    E = lab_tr[:, 3].double().cpu().numpy()
+    rmin = float(rho_c.min().item())
+    mu, isd = inputs.feature_normalisation(rmin, Rc)
+    e_scale = float(np.std(np.clip(E, np.percentile(E, 1), np.percentile(E, 99)))) or 1.0
+    e_shift = float(np.median(E))
+    flat = inputs.mlp_params(width, depth, seed + 1, mu=mu, inv_sd=isd, e_scale=e_scale,
+                             e_shift=e_shift)
+    mlp = api.MLP(width, depth)
+    mlp.set_params(flat)
+    tr = api.Trainer(mlp, batch, lr=lr)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    t0 = time.perf_counter()
+    losses = []
+    k = 0
+    for k in range(steps):
+        # cosine learning-rate decay to lr / 20
+        tr.set_lr(lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps)))))
+        idx = torch.randint(0, n_samples, (batch,), device="cuda", generator=g)
+        want = log_every and (k % log_every == 0)
+        loss = tr.step(cfg_tr[idx].contiguous(), lab_tr[idx].contiguous(), lam_tau, lam_E,
+                       want_loss=bool(want), f_scale=f_scale, kT_w=kT_w)
+        if want:
+            losses.append((k, loss))
+        if time_limit_s is not None and time.perf_counter() - t0 > time_limit_s:
+            break
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = mlp.pairs(cfg_te.contiguous(), "fp32")
+    err = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    report = {"shape": shape, "width": width, "depth": depth, "samples": n_samples,
+              "steps": k + 1, "batch": batch, "lr": lr, "f_scale": f_scale, "kT_w": kT_w, "t_sample_s": t_sample,
+              "t_train_s": t_train, "rho_contact_min": rmin, "Rc": Rc,
+              "heldout_e_F": err(out[:, 0:3], lab_te[:, 0:3]),
+              "heldout_e_tau_i": err(out[:, 4:7], lab_te[:, 4:7]),
+              "heldout_e_tau_j": err(out[:, 8:11], lab_te[:, 8:11]),
+              "losses": losses}
+    return mlp, report
+
+
+def force_error(system: api.System, mlp: api.MLP, precision: str = "bf16"):
+    """NN-versus-bead error of whole-system forces and torques (model error)."""
+    ref = system.forces_beads()
+    r = system.forces_nn(mlp, precision)
+    system.sync()
+    err = lambda a, b: float(torch.linalg.norm(a[:, :3] - b[:, :3]) / torch.linalg.norm(b[:, :3]))
+    return {"e_F": err(r["force"], ref["force"]), "e_tau": err(r["torque"], ref["torque"])}

@@ -101,3 +101,18 @@ def test_nn_bf16_md_steps_run_and_conserve():
     e1 = sum(s.energy())
     s.sync()
     assert abs(e1 - e0) < 1e-2 * 512, (e0, e1)
+
+
+def test_nn_skin_identical_forces_bf16():
+    from paper_2402_12199_gb300 import api
+
+    st, L, tmpl = make_state(3000, 0.2, 72)
+    m = api.MLP(128, 3)
+    m.set_params(params(11))
+    a = gpu_system(st, L)
+    b = gpu_system(st, L)
+    b.set_skin(0.4)
+    ra = a.forces_nn(m, "bf16")
+    rb = b.forces_nn(m, "bf16")
+    b.sync()
+    assert bool((ra["force"] == rb["force"]).all()) and bool((ra["torque"] == rb["torque"]).all())

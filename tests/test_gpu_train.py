@@ -92,12 +92,13 @@ def _setup(width, B, seed, lam_tau=0.5, lam_E=0.1):
     return flat, c7, lab.astype(np.float32), m, tr, torch.from_numpy(c8).cuda(), torch.from_numpy(l12).cuda()
 
 
-@pytest.mark.parametrize("width,B", [(64, 200), (128, 96), (128, 1)])
-def test_force_matching_gradient_parity(width, B):
+@pytest.mark.parametrize("width,B,fs,kt", [(64, 200, 0.0, 0.0), (128, 96, 0.0, 0.0),
+                                           (128, 1, 0.0, 0.0), (128, 150, 1.5, 0.7)])
+def test_force_matching_gradient_parity(width, B, fs, kt):
     flat, c7, lab, m, tr, c8, l12 = _setup(width, B, width + B)
-    loss, g = tr.grad(c8, l12, 0.5, 0.1)
+    loss, g = tr.grad(c8, l12, 0.5, 0.1, fs, kt)
     L_ref, g_ref = nn.force_matching_loss(flat.astype(np.float64), width, 3, c7.astype(np.float64),
-                                          lab.astype(np.float64), 0.5, 0.1)
+                                          lab.astype(np.float64), 0.5, 0.1, fs or None, kt or None)
     assert loss == pytest.approx(L_ref, rel=1e-5)
     assert rel_err(g.double().cpu().numpy(), g_ref) < 1e-5
 

@@ -358,22 +358,33 @@ def test_flat_layout_size():
 
 # ------------------------------------------------------------------ training
 
-def test_force_matching_gradient_matches_finite_differences():
+@pytest.mark.parametrize("fs", [None, 0.7])
+def test_force_matching_gradient_matches_finite_differences(fs):
     w = 8
     mu, isd = inputs.feature_normalisation(5.0, 9.4)
     flat = inputs.mlp_params(w, 3, 3, mu=mu, inv_sd=isd).astype(np.float64)
     cfg = inputs.pair_configs(5, 13, 5.5, 9.0).astype(np.float64)
     rng = np.random.default_rng(14)
     lab = rng.standard_normal((5, 10))
-    L0, g = nn.force_matching_loss(flat, w, 3, cfg, lab, 0.5, 0.1)
+    L0, g = nn.force_matching_loss(flat, w, 3, cfg, lab, 0.5, 0.1, fs)
     idx = rng.choice(np.arange(20, len(flat) - 2), 20, replace=False)
     h = 1e-6
     for k in idx:
         fp = flat.copy(); fp[k] += h
         fm = flat.copy(); fm[k] -= h
-        fd = (nn.force_matching_loss(fp, w, 3, cfg, lab, 0.5, 0.1)[0]
-              - nn.force_matching_loss(fm, w, 3, cfg, lab, 0.5, 0.1)[0]) / (2 * h)
+        fd = (nn.force_matching_loss(fp, w, 3, cfg, lab, 0.5, 0.1, fs)[0]
+              - nn.force_matching_loss(fm, w, 3, cfg, lab, 0.5, 0.1, fs)[0]) / (2 * h)
         assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+    if fs:
+        # the weight divides each sample's loss by 1 + |label|^2 / fs^2
+        L1, _ = nn.force_matching_loss(flat, w, 3, cfg, lab, 0.5, 0.1, None)
+        assert L0 < L1
+        # Boltzmann weight: samples with E* <= 0 are untouched, E* > 0 damped by exp(-E*/kT)
+        lab2 = lab.copy()
+        lab2[:, 0] = -np.abs(lab2[:, 0])
+        La, _ = nn.force_matching_loss(flat, w, 3, cfg, lab2, 0.5, 0.1, None, 0.3)
+        Lb, _ = nn.force_matching_loss(flat, w, 3, cfg, lab2, 0.5, 0.1, None, None)
+        assert La == pytest.approx(Lb, rel=1e-14)
 
 
 def test_teacher_equals_student_has_zero_gradient():
