@@ -496,7 +496,9 @@ def main():
             "nn_model_error": model_error, "training": training, "serving": serving,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * 7 * len(paths), "clocks": clocks,
+            # per MD step and path: integrate, skin check, cell assign, pair build,
+            # two scan kernels, emit, finish, flag clear, pair kernel, reduce
+            "gpu_launches": args.steps * 11 * len(paths), "clocks": clocks,
             "peaks_source": how, "wall_s": wall}
     if rank == 0:
         print(json.dumps(line))

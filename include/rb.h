@@ -168,6 +168,16 @@ rb_status rb_step(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t preci
 rb_status rb_energy(rb_system* sys, double* e_pot_host, double* ke_trans_host,
                     double* ke_rot_host);
 
+/* Checkpoint / resume.  rb_checkpoint writes the state, step counter, box,
+ * skin and body template to `path` (versioned binary, synchronises);
+ * rb_restore reads it into a system created with the same N, body and box
+ * (RB_EINVAL otherwise).  Every kernel is deterministic, so a restored run
+ * continues bit for bit like the uninterrupted one. */
+rb_status rb_checkpoint(rb_system* sys, const char* path);
+rb_status rb_restore(rb_system* sys, const char* path);
+/* MD steps taken by rb_step since creation (or as restored). */
+rb_status rb_get_step(const rb_system* sys, int64_t* step_host);
+
 /* Wait for the system's stream and report any sticky device-side error
  * (capacity overflow, non-finite values). */
 rb_status rb_sync(rb_system* sys);

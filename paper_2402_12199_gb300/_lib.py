@@ -87,6 +87,9 @@ SIGNATURES = {
     "rb_eval_pairs": (I32, [P, I32, P, I32]),
     "rb_energy": (I32, [P, DP, DP, DP]),
     "rb_sync": (I32, [P]),
+    "rb_checkpoint": (I32, [P, ctypes.c_char_p]),
+    "rb_restore": (I32, [P, ctypes.c_char_p]),
+    "rb_get_step": (I32, [P, I64P]),
     "rb_mlp_n_params": (I64, [I32, I32]),
     "rb_mlp_create": (I32, [I32, I32, P, ctypes.POINTER(P)]),
     "rb_mlp_destroy": (I32, [P]),

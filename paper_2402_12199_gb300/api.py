@@ -178,6 +178,18 @@ class System:
         check(load().rb_eval_pairs(self._h, path, mlp.handle if mlp is not None else None,
                                    PRECISION[precision]))
 
+    def checkpoint(self, path: str):
+        check(load().rb_checkpoint(self._h, str(path).encode()))
+
+    def restore(self, path: str):
+        check(load().rb_restore(self._h, str(path).encode()))
+
+    @property
+    def step_count(self) -> int:
+        n = ctypes.c_int64()
+        check(load().rb_get_step(self._h, ctypes.byref(n)))
+        return n.value
+
     def set_skin(self, skin: float):
         check(load().rb_set_skin(self._h, float(skin)))
 

@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(256)
                  const float4* __restrict__ tmpl, int n_beads, float3 L, float3 invL, BeadPot pot,
                  float cut2, int zero_beyond, float4* __restrict__ out_F,
                  float4* __restrict__ out_ti, float4* __restrict__ out_tj, int* count) {
-    __shared__ float4 sT[kMaxBeads];
-    __shared__ float4 sN[2 * kMaxBeads];
+    __shared__ float4 sT[kMaxBeads + 1];
+    __shared__ float4 sN[2 * kMaxBeads + 2];
     load_template(tmpl, n_beads, sT, sN);
     __syncthreads();
     const int n_pairs = *n_pairs_ptr;
@@ -85,6 +85,10 @@ BeadPot bead_pot(const rb_system* s) {
     p.eps4 = 4.f * s->eps;
     p.eps24 = 24.f * s->eps;
     p.u_shift = s->u_shift;
+    // |r^2_expanded - r^2| <= a few roundings of values up to (Rc + r_circ)^2
+    // + r_circ^2 (b within Rc + r_circ of body i's centre, d within r_circ)
+    const float big = (s->Rc + s->r_circ) * (s->Rc + s->r_circ) + s->r_circ * s->r_circ;
+    p.rc2_test = p.rc2 + 4e-6f * big;
     return p;
 }
 

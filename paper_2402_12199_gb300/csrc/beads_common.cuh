@@ -14,27 +14,39 @@ namespace rb {
 
 struct BeadPot {
     float rc2, sig2, eps4, eps24, u_shift;
+    float rc2_test;  // rc2 + a bound on the rounding of the expanded distance test
 };
 
 BeadPot bead_pot(const rb_system* s);
 
-// Per-CTA shared template: sT[k] = (x, y, z, 0); sN[2k], sN[2k+1] = negated
-// coordinates duplicated for packed FP32x2 arithmetic.
+// Per-CTA shared template: sT[k] = (x, y, z, 0); sN[2k], sN[2k+1] =
+// (-2x, -2x, -2y, -2y), (-2z, -2z, |d|^2, |d|^2): duplicated for packed FP32x2
+// arithmetic (0.5 * (-2x) = -x exactly).
+// An odd template gets one padding entry far away (never within any cutoff),
+// so the distance loop can take two template beads per iteration.
 __device__ inline void load_template(const float4* __restrict__ tmpl, int n_beads, float4* sT,
                                      float4* sN) {
-    for (int t = threadIdx.x; t < n_beads; t += blockDim.x) {
-        const float4 d = tmpl[t];
-        sT[t] = d;
-        sN[2 * t] = make_float4(-d.x, -d.x, -d.y, -d.y);
-        sN[2 * t + 1] = make_float4(-d.z, -d.z, 0.f, 0.f);
+    for (int t = threadIdx.x; t < n_beads + 1; t += blockDim.x) {
+        if (t < n_beads) {
+            const float4 d = tmpl[t];
+            sT[t] = d;
+            const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
+            sN[2 * t] = make_float4(-2.f * d.x, -2.f * d.x, -2.f * d.y, -2.f * d.y);
+            sN[2 * t + 1] = make_float4(-2.f * d.z, -2.f * d.z, dd, dd);
+        } else {  // padding bead at 1e18 sigma
+            sN[2 * t] = make_float4(-2e18f, -2e18f, 0.f, 0.f);
+            sN[2 * t + 1] = make_float4(0.f, 0.f, 1e36f, 1e36f);
+        }
     }
 }
 
 // Whole-warp bead double sum of one body pair in the frame of body i.
 // NP = packed slot pairs per lane: the lane owns beads l = lane + 32 m,
 // m = 0 .. 2 NP - 1, of body j.  Returns, reduced over the warp (every lane):
-// v[0..2] = F_j, v[3..5] = T = sum_l b_l x f_l, v[6] = E.  The cutoff decision
-// is one warp vote per template bead; the Lennard-Jones body is masked.
+// v[0..2] = F_j, v[3..5] = T = sum_l b_l x f_l, v[6] = E.  Every bead-pair
+// distance is tested (expanded form, with a rounding margin); one warp vote
+// per template bead decides whether any slot may be inside r_c, and then the
+// exact separations, the strict cutoff and the masked Lennard-Jones body run.
 template <int NP>
 __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const float4* sT,
                                       const float4* sN, int n_beads, const BeadPot& pot,
@@ -67,41 +79,66 @@ __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const floa
         Bz[q] = make_float2(bz[2 * q], bz[2 * q + 1]);
         Fx[q] = Fy[q] = Fz[q] = make_float2(0.f, 0.f);
     }
+    // |b_l|^2 per slot for the expanded distance test
+    float2 BB[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        BB[q] = __ffma2_rn(Bz[q], Bz[q], __ffma2_rn(By[q], By[q], __fmul2_rn(Bx[q], Bx[q])));
+    const float2 half2 = make_float2(0.5f, 0.5f);
     float2 acc = make_float2(0.f, 0.f);  // sum of (s^12 - s^6) over inside pairs
     float2 cnt = make_float2(0.f, 0.f);  // number of inside pairs
-#pragma unroll 2
-    for (int k = 0; k < n_beads; ++k) {
-        const float4 n0 = sN[2 * k], n1 = sN[2 * k + 1];
-        const float2 ndx = make_float2(n0.x, n0.y), ndy = make_float2(n0.z, n0.w);
-        const float2 ndz = make_float2(n1.x, n1.y);
-        float2 rx[NP], ry[NP], rz[NP], r2[NP];
+    // two template beads per iteration: independent test chains, one vote
+    for (int k = 0; k < n_beads; k += 2) {
+        float2 md[2][3], dd[2];
         float mn = 3.0e38f;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            rx[q] = __fadd2_rn(Bx[q], ndx);
-            ry[q] = __fadd2_rn(By[q], ndy);
-            rz[q] = __fadd2_rn(Bz[q], ndz);
-            r2[q] = __fmul2_rn(rx[q], rx[q]);
-            r2[q] = __ffma2_rn(ry[q], ry[q], r2[q]);
-            r2[q] = __ffma2_rn(rz[q], rz[q], r2[q]);
-            mn = fminf(mn, fminf(r2[q].x, r2[q].y));
+        for (int u = 0; u < 2; ++u) {
+            const float4 n0 = sN[2 * (k + u)], n1 = sN[2 * (k + u) + 1];
+            md[u][0] = make_float2(n0.x, n0.y);
+            md[u][1] = make_float2(n0.z, n0.w);
+            md[u][2] = make_float2(n1.x, n1.y);
+            dd[u] = make_float2(n1.z, n1.w);
         }
-        if (__any_sync(0xffffffffu, mn < rc2)) {
+        // test: r^2 ~ |b|^2 + |d|^2 - 2 b.d (4 packed ops per 2 slots); the
+        // rounding bound is folded into rc2_test, so no pair inside r_c is missed
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const bool inx = r2[q].x < rc2, iny = r2[q].y < rc2;
-                const float2 inv2 = make_float2(inx ? __fdividef(1.f, r2[q].x) : 0.f,
-                                                iny ? __fdividef(1.f, r2[q].y) : 0.f);
-                const float2 s2 = __fmul2_rn(sig2v, inv2);
-                const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
-                const float2 s12 = __fmul2_rn(s6, s6);
-                acc = __fadd2_rn(acc, __ffma2_rn(s6, m1, s12));
-                cnt = __fadd2_rn(cnt, make_float2(inx ? 1.f : 0.f, iny ? 1.f : 0.f));
-                const float2 fr = __fmul2_rn(inv2, __ffma2_rn(s12, e48, __fmul2_rn(s6, me24)));
-                Fx[q] = __ffma2_rn(fr, rx[q], Fx[q]);
-                Fy[q] = __ffma2_rn(fr, ry[q], Fy[q]);
-                Fz[q] = __ffma2_rn(fr, rz[q], Fz[q]);
+                float2 t = __fadd2_rn(BB[q], dd[u]);
+                t = __ffma2_rn(Bx[q], md[u][0], t);
+                t = __ffma2_rn(By[q], md[u][1], t);
+                t = __ffma2_rn(Bz[q], md[u][2], t);
+                mn = fminf(mn, fminf(t.x, t.y));
             }
+        if (__any_sync(0xffffffffu, mn < pot.rc2_test)) {
+            // exact separations and the strict cutoff r^2 < r_c^2; the masked
+            // Lennard-Jones body runs only for slot pairs with an inside pair
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const float2 rx = __ffma2_rn(half2, md[u][0], Bx[q]);
+                    const float2 ry = __ffma2_rn(half2, md[u][1], By[q]);
+                    const float2 rz = __ffma2_rn(half2, md[u][2], Bz[q]);
+                    float2 r2 = __fmul2_rn(rx, rx);
+                    r2 = __ffma2_rn(ry, ry, r2);
+                    r2 = __ffma2_rn(rz, rz, r2);
+                    const bool inx = r2.x < rc2, iny = r2.y < rc2;
+                    if (!__any_sync(0xffffffffu, inx || iny)) continue;
+                    const float2 inv2 = make_float2(inx ? __fdividef(1.f, r2.x) : 0.f,
+                                                    iny ? __fdividef(1.f, r2.y) : 0.f);
+                    const float2 s2 = __fmul2_rn(sig2v, inv2);
+                    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+                    const float2 s12 = __fmul2_rn(s6, s6);
+                    acc = __fadd2_rn(acc, __ffma2_rn(s6, m1, s12));
+                    cnt = __fadd2_rn(cnt, make_float2(inx ? 1.f : 0.f, iny ? 1.f : 0.f));
+                    const float2 fr =
+                        __fmul2_rn(inv2, __ffma2_rn(s12, e48, __fmul2_rn(s6, me24)));
+                    Fx[q] = __ffma2_rn(fr, rx, Fx[q]);
+                    Fy[q] = __ffma2_rn(fr, ry, Fy[q]);
+                    Fz[q] = __ffma2_rn(fr, rz, Fz[q]);
+                }
         }
     }
 #pragma unroll

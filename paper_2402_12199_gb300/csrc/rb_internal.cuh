@@ -178,6 +178,8 @@ struct rb_system {
     float skin = 0.f;
     float4* pos_ref = nullptr;
     int* rebuild_flag = nullptr;
+    int64_t step = 0;  // MD steps taken (checkpointed)
+    int shape = 0;
 };
 
 namespace rb {

@@ -620,6 +620,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     rb_system* s = new (std::nothrow) rb_system();
     if (!s) return fail(RB_ENOMEM, "host allocation");
     s->stream = (cudaStream_t)stream;
+    s->shape = d->body.shape;
     cudaGetDevice(&s->device);
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     s->tmpl = t;
@@ -992,6 +993,7 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
         g.dt = dt;
     }
     for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
+    s->step += n_steps;
     return RB_OK;
 }
 
@@ -1054,6 +1056,69 @@ rb_status rb_energy(rb_system* s, double* e_pot, double* ke_t, double* ke_r) {
     if (e_pot) *e_pot = h[0];
     if (ke_t) *ke_t = h[1];
     if (ke_r) *ke_r = h[2];
+    return RB_OK;
+}
+
+// Checkpoint file: magic "RBCK", version 1, then int64 N, int64 step, int32
+// shape, int32 n_beads, float box[3], float skin, the template (n_beads x 3
+// floats), and the four state arrays (N x 4 floats each).  Little-endian, as
+// written by the host.
+static const char kMagic[4] = {'R', 'B', 'C', 'K'};
+
+rb_status rb_checkpoint(rb_system* s, const char* path) {
+    if (!s || !path) return fail(RB_EINVAL, "null argument");
+    const size_t n4 = 4 * (size_t)s->N;
+    std::vector<float> buf(4 * n4);
+    RB_TRY(rb_get_state(s, buf.data(), buf.data() + n4, buf.data() + 2 * n4, buf.data() + 3 * n4, 1));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(RB_EINVAL, std::string("cannot open ") + path + " for writing");
+    const int32_t version = 1, shape = s->shape, nb = s->n_beads;
+    const int64_t N = s->N, step = s->step;
+    bool ok = std::fwrite(kMagic, 1, 4, f) == 4 && std::fwrite(&version, 4, 1, f) == 1 &&
+              std::fwrite(&N, 8, 1, f) == 1 && std::fwrite(&step, 8, 1, f) == 1 &&
+              std::fwrite(&shape, 4, 1, f) == 1 && std::fwrite(&nb, 4, 1, f) == 1 &&
+              std::fwrite(s->box, 4, 3, f) == 3 && std::fwrite(&s->skin, 4, 1, f) == 1 &&
+              std::fwrite(s->tmpl.data(), 4, s->tmpl.size(), f) == s->tmpl.size() &&
+              std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(RB_EINVAL, std::string("write failed: ") + path);
+    return RB_OK;
+}
+
+rb_status rb_restore(rb_system* s, const char* path) {
+    if (!s || !path) return fail(RB_EINVAL, "null argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(RB_EINVAL, std::string("cannot open ") + path);
+    char magic[4];
+    int32_t version = 0, shape = 0, nb = 0;
+    int64_t N = 0, step = 0;
+    float box[3], skin = 0.f;
+    bool ok = std::fread(magic, 1, 4, f) == 4 && std::memcmp(magic, kMagic, 4) == 0 &&
+              std::fread(&version, 4, 1, f) == 1 && version == 1 &&
+              std::fread(&N, 8, 1, f) == 1 && std::fread(&step, 8, 1, f) == 1 &&
+              std::fread(&shape, 4, 1, f) == 1 && std::fread(&nb, 4, 1, f) == 1 &&
+              std::fread(box, 4, 3, f) == 3 && std::fread(&skin, 4, 1, f) == 1;
+    if (!ok || N != s->N || nb != s->n_beads || shape != s->shape ||
+        std::memcmp(box, s->box, sizeof(box)) != 0) {
+        std::fclose(f);
+        return fail(RB_EINVAL, "checkpoint does not match this system (N, body or box)");
+    }
+    std::vector<float> t(3 * (size_t)nb);
+    const size_t n4 = 4 * (size_t)N;
+    std::vector<float> buf(4 * n4);
+    ok = std::fread(t.data(), 4, t.size(), f) == t.size() &&
+         std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok || t != s->tmpl) return fail(RB_EINVAL, "truncated checkpoint or different template");
+    RB_TRY(rb_set_state(s, buf.data(), buf.data() + n4, buf.data() + 2 * n4, buf.data() + 3 * n4, 1));
+    RB_TRY(rb_set_skin(s, skin));
+    s->step = step;
+    return RB_OK;
+}
+
+rb_status rb_get_step(const rb_system* s, int64_t* step_host) {
+    if (!s || !step_host) return fail(RB_EINVAL, "null argument");
+    *step_host = s->step;
     return RB_OK;
 }
 

@@ -58,8 +58,8 @@ __global__ void __launch_bounds__(256)
     k_sample_pairs(int64_t n, const float* __restrict__ u, const float4* __restrict__ tmpl,
                    int n_beads, float Rc, float sigma, BeadPot pot, int n_bisect,
                    float4* __restrict__ cfg, float4* __restrict__ lab, float* __restrict__ rho_c) {
-    __shared__ float4 sT[kMaxBeads];
-    __shared__ float4 sN[2 * kMaxBeads];
+    __shared__ float4 sT[kMaxBeads + 1];
+    __shared__ float4 sN[2 * kMaxBeads + 2];
     load_template(tmpl, n_beads, sT, sN);
     __syncthreads();
     const int lane = threadIdx.x & 31;

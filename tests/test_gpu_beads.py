@@ -229,3 +229,27 @@ def test_verlet_skin_gives_identical_forces_and_trajectories():
             assert np.array_equal(sa[k], sb[k]), k
     a.sync()
     b.sync()
+
+
+def test_checkpoint_restore_continues_bit_for_bit(tmp_path):
+    from paper_2402_12199_gb300 import api
+
+    st, L, tmpl = make_state(1000, 0.15, 81)
+    a = gpu_system(st, L)
+    a.set_skin(0.3)
+    a.step(20, 0.002)
+    path = tmp_path / "ck.rbck"
+    a.checkpoint(path)
+    a.step(30, 0.002)
+    ref = a.get_state(to_host=True)
+    b = api.System(1000, [L] * 3, "cube")
+    b.restore(path)
+    assert b.step_count == 20
+    b.step(30, 0.002)
+    got = b.get_state(to_host=True)
+    for k in ("pos", "quat", "vel", "angmom"):
+        assert np.array_equal(ref[k], got[k]), k
+    assert b.step_count == 50
+    c = api.System(999, [L] * 3, "cube")
+    with pytest.raises(api.RBError):
+        c.restore(path)
