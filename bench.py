@@ -300,6 +300,7 @@ def main():
 
     __graft_entry__.build()
     from paper_2402_12199_gb300 import api
+    from paper_2402_12199_gb300 import inputs as inputs_mod
 
     paths = [p for p in args.paths.split(",") if p]
     st, L, flat = make_inputs(rank)
@@ -427,6 +428,46 @@ def main():
                    "peak_source": f"bf16_tflops_sustained ({how})", "flops_per_launch": flops,
                    "mufu_per_pair": 6 * WIDTH, "note": "one tanh.approx per SiLU evaluation"}
 
+    # ---- network width 256 (BF16, streamed weights), same workload, timed alone
+    width256 = None
+    if "nn_bf16" in paths:
+        m256 = api.MLP(256, DEPTH)
+        mu, isd = inputs_mod.feature_normalisation(5.0, 4 * math.sqrt(3) + 2.5)
+        m256.set_params(inputs_mod.mlp_params(256, DEPTH, 6, mu=mu, inv_sd=isd))
+        s256 = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
+        s256.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+        s256.forces_nn(m256, "bf16")
+        ev256 = []
+        for it in range(max(3, args.warmup) + 200):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s256.step(1, DT, path=api.RB_PATH_NN, mlp=m256, precision="bf16")
+            b.record(stream)
+            if it >= max(3, args.warmup):
+                ev256.append((a, b))
+        torch.cuda.synchronize()
+        s256.sync()
+        ms256 = statistics.mean(a.elapsed_time(b) for a, b in ev256)
+        s256.build_pairs()
+        ka = torch.cuda.Event(enable_timing=True)
+        kb = torch.cuda.Event(enable_timing=True)
+        ka.record(stream)
+        for _ in range(10):
+            s256.eval_pairs(api.RB_PATH_NN, m256, "bf16")
+        kb.record(stream)
+        torch.cuda.synchronize()
+        k256 = ka.elapsed_time(kb) / 10
+        tc256 = 2.0 * 128 * (256 * 64 + 4 * 256 * 256 + 256 * 16) / 128 * n_pairs["nn_bf16"]
+        width256 = {"ms_per_md_step": ms256, "md_steps_per_s": 1e3 / ms256,
+                    "speedup_vs_beads": (statistics.mean(per_path_ms["beads"]) / ms256)
+                    if "beads" in per_path_ms else None,
+                    "kernel": "k_nn_tc256", "kernel_ms": k256,
+                    "tensor_tflops": tc256 / (k256 * 1e-3) / 1e12,
+                    "frac_of_bf16_sustained": tc256 / (k256 * 1e-3) / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
+                    "steps_timed": 200}
+        del s256, m256
+
     # ---- end to end through the public API with host buffers
     pinned = {k: torch.from_numpy(st[k]).pin_memory() for k in ("pos", "quat", "vel", "angmom")}
     outs = {k: torch.empty((N_BODIES, 4), dtype=torch.float32).pin_memory()
@@ -494,6 +535,7 @@ def main():
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
             "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
+            "nn_bf16_width256": width256,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per MD step and path: integrate, skin check, cell assign, pair build,

@@ -223,8 +223,9 @@ rb_status rb_mlp_get_params(const rb_mlp* mlp, float* flat, int64_t n, int32_t t
 
 /* Network forces and torques for the whole system (same outputs and pair
  * list as rb_forces_beads).  Each unordered pair i < j is evaluated once with
- * i as the reference body.  RB_FP32: SIMT FP32 arithmetic; RB_BF16: BF16
- * tensor-core GEMMs with FP32 accumulation. */
+ * i as the reference body.  RB_FP32: SIMT FP32 arithmetic (widths 64, 128,
+ * 256); RB_BF16: BF16 tensor-core GEMMs (tcgen05) with FP32 accumulation
+ * (widths 128 and 256, depth 1..3; RB_ENOTSUP otherwise). */
 rb_status rb_forces_nn(rb_system* sys, const rb_mlp* mlp, int32_t precision, float* force,
                        float* torque, double* energy_host, double* virial9_host);
 

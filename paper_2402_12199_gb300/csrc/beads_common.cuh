@@ -112,8 +112,8 @@ __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const floa
                 mn = fminf(mn, fminf(t.x, t.y));
             }
         if (__any_sync(0xffffffffu, mn < pot.rc2_test)) {
-            // exact separations and the strict cutoff r^2 < r_c^2; the masked
-            // Lennard-Jones body runs only for slot pairs with an inside pair
+            // exact separations, the strict cutoff r^2 < r_c^2 and the masked
+            // Lennard-Jones body for every slot
 #pragma unroll
             for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -125,7 +125,6 @@ __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const floa
                     r2 = __ffma2_rn(ry, ry, r2);
                     r2 = __ffma2_rn(rz, rz, r2);
                     const bool inx = r2.x < rc2, iny = r2.y < rc2;
-                    if (!__any_sync(0xffffffffu, inx || iny)) continue;
                     const float2 inv2 = make_float2(inx ? __fdividef(1.f, r2.x) : 0.f,
                                                     iny ? __fdividef(1.f, r2.y) : 0.f);
                     const float2 s2 = __fmul2_rn(sig2v, inv2);

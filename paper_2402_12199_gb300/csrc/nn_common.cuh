@@ -74,8 +74,35 @@ struct PairGeom {
     bool beyond;  // system mode: pair outside the cutoff, outputs are zero
 };
 
+// Raw pair data (the global loads), separated from the geometry so a kernel
+// can fetch the next pair while it works on the current one.
+struct PairRaw {
+    float4 a, b, c, d;  // system: p_i, p_j, q_i, q_j; explicit: cfg[0], cfg[1]
+    bool valid;
+};
+
 template <bool SYSTEM>
-__device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid) {
+__device__ inline PairRaw fetch_pair(const PairSrc& src, int64_t gp, bool valid) {
+    PairRaw r;
+    r.valid = valid;
+    r.a = r.b = r.c = r.d = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        if (SYSTEM) {
+            const int2 ij = src.pairs[gp];
+            r.a = src.pos[ij.x];
+            r.b = src.pos[ij.y];
+            r.c = src.quat[ij.x];
+            r.d = src.quat[ij.y];
+        } else {
+            r.a = src.cfg[2 * gp];
+            r.b = src.cfg[2 * gp + 1];
+        }
+    }
+    return r;
+}
+
+template <bool SYSTEM>
+__device__ inline PairGeom pair_geometry(const PairSrc& src, const PairRaw& r) {
     PairGeom g;
     g.s = make_float3(5.f, 0.f, 0.f);
     g.qc = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -83,21 +110,17 @@ __device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid)
     g.sgn = 1.f;
     g.beyond = false;
     float4 qr = g.qc;
-    if (valid) {
+    if (r.valid) {
         if (SYSTEM) {
-            const int2 ij = src.pairs[gp];
-            const float4 pi = src.pos[ij.x], pj = src.pos[ij.y];
-            g.qi = src.quat[ij.x];
-            const float4 qj = src.quat[ij.y];
-            const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), src.L,
-                                       src.invL);
+            g.qi = r.c;
+            const float3 R = min_image(make_float3(r.b.x - r.a.x, r.b.y - r.a.y, r.b.z - r.a.z),
+                                       src.L, src.invL);
             g.beyond = R.x * R.x + R.y * R.y + R.z * R.z >= src.Rc2;
             g.s = mulT(qmat(g.qi), R);
-            qr = qmul(qconj(g.qi), qj);
+            qr = qmul(qconj(g.qi), r.d);
         } else {
-            const float4 c0 = src.cfg[2 * gp], c1 = src.cfg[2 * gp + 1];
-            g.s = make_float3(c0.x, c0.y, c0.z);
-            qr = c1;
+            g.s = make_float3(r.a.x, r.a.y, r.a.z);
+            qr = r.b;
         }
         if (qr.x < 0.f) {
             g.sgn = -1.f;
@@ -109,6 +132,11 @@ __device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid)
     }
     g.rho = sqrtf(g.s.x * g.s.x + g.s.y * g.s.y + g.s.z * g.s.z);
     return g;
+}
+
+template <bool SYSTEM>
+__device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid) {
+    return pair_geometry<SYSTEM>(src, fetch_pair<SYSTEM>(src, gp, valid));
 }
 
 __device__ inline void raw_features(const PairGeom& g, float (&x)[kIn]) {

@@ -39,9 +39,9 @@ def test_tc_gemm_tile(N, K):
     assert torch.allclose(D, ref, rtol=1e-5, atol=1e-4), (D - ref).abs().max()
 
 
-def params(seed, depth=3):
+def params(seed, depth=3, width=128):
     mu, isd = inputs.feature_normalisation(5.0, 9.43)
-    return inputs.mlp_params(128, depth, seed, mu=mu, inv_sd=isd, e_scale=1.5, e_shift=-0.2)
+    return inputs.mlp_params(width, depth, seed, mu=mu, inv_sd=isd, e_scale=1.5, e_shift=-0.2)
 
 
 def cfg8(cfg7):
@@ -51,18 +51,20 @@ def cfg8(cfg7):
     return c
 
 
-@pytest.mark.parametrize("n,depth", [(4096, 3), (1000, 3), (1, 3), (777, 2), (300, 1)])
-def test_nn_pairs_bf16_parity(n, depth):
+@pytest.mark.parametrize("n,depth,width", [(4096, 3, 128), (1000, 3, 128), (1, 3, 128), (777, 2, 128),
+                                           (300, 1, 128), (4096, 3, 256), (1000, 3, 256),
+                                           (777, 2, 256), (300, 1, 256), (1, 3, 256)])
+def test_nn_pairs_bf16_parity(n, depth, width):
     import torch
 
     from paper_2402_12199_gb300 import api
 
-    flat = params(7 + n, depth)
-    m = api.MLP(128, depth)
+    flat = params(7 + n, depth, width)
+    m = api.MLP(width, depth)
     m.set_params(flat)
     cfg7 = inputs.pair_configs(n, 31 + n, 5.0, 9.4)
     out = m.pairs(torch.from_numpy(cfg8(cfg7)).cuda(), "bf16").double().cpu().numpy()
-    p = nn.unpack(flat.astype(np.float64), 128, depth)
+    p = nn.unpack(flat.astype(np.float64), width, depth)
     c = torch.as_tensor(cfg7.astype(np.float64))
     E, Fj, ti, tj = nn.predict_labels(p, c[:, :3], c[:, 3:])
     assert rel_err(out[:, 0:3], Fj.numpy()) < TOL_BF16
@@ -71,29 +73,31 @@ def test_nn_pairs_bf16_parity(n, depth):
     assert rel_err(out[:, 3], E.detach().numpy()) < TOL_BF16
 
 
-def test_nn_system_forces_bf16_parity():
+@pytest.mark.parametrize("width", [128, 256])
+def test_nn_system_forces_bf16_parity(width):
     from paper_2402_12199_gb300 import api
 
     st, L, tmpl = make_state(2000, 0.20, 12)
-    flat = params(3)
-    m = api.MLP(128, 3)
+    flat = params(3, 3, width)
+    m = api.MLP(width, 3)
     m.set_params(flat)
     s = gpu_system(st, L)
     r = s.forces_nn(m, "bf16", energy=True)
     s.sync()
-    F, T, E, per, pairs = oracle_nn(st, L, tmpl, flat, 128)
+    F, T, E, per, pairs = oracle_nn(st, L, tmpl, flat, width)
     assert canonical_margin(st, pairs) > 1e-5
     assert rel_err(r["force"][:, :3].double().cpu().numpy(), F) < TOL_BF16
     assert rel_err(r["torque"][:, :3].double().cpu().numpy(), T) < TOL_BF16
     assert abs(r["energy"] - E) < TOL_BF16 * np.abs(per).sum()
 
 
-def test_nn_bf16_md_steps_run_and_conserve():
+@pytest.mark.parametrize("width", [128, 256])
+def test_nn_bf16_md_steps_run_and_conserve(width):
     from paper_2402_12199_gb300 import api
 
     st, L, tmpl = make_state(512, 0.2, 6)
-    m = api.MLP(128, 3)
-    m.set_params(params(4))
+    m = api.MLP(width, 3)
+    m.set_params(params(4, 3, width))
     s = gpu_system(st, L)
     s.forces_nn(m, "bf16")
     e0 = sum(s.energy())
