@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--paths", default="beads,nn_fp32,nn_bf16")
-    ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
+    ap.add_argument("--cpu-sample-pairs", type=int, default=100000)
     ap.add_argument("--ref-sample-pairs", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=1500)

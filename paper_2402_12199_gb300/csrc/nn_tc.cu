@@ -27,6 +27,7 @@
 // SiLU uses sigma(z) = 0.5 + 0.5 tanh(z/2) with the hardware tanh.approx
 // (one MUFU operation per element), ample for BF16 operands.
 #include <cstdint>
+#include <cstdlib>
 
 #include "tc_common.cuh"
 
@@ -366,6 +367,17 @@ static int sm_count_tc() {
 
 static bool tc_supported(const rb_mlp* m) { return m->width == tc::kW && m->depth >= 1 && m->depth <= 3; }
 
+// Width 128 runs the two-pipeline kernel (nn_tc2p.cu); RB_TC_SINGLE_PIPELINE=1
+// selects the single-pipeline kernel below (same results, for comparison).
+static bool tc_two_pipelines() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("RB_TC_SINGLE_PIPELINE");
+        v = (e && e[0] == '1') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 rb_status nn_tc_prepare(rb_mlp* m) {
     if (nn_tc256_supported(m)) return nn_tc256_prepare(m);
     if (!tc_supported(m)) return RB_OK;  // FP32 path only for other shapes
@@ -383,6 +395,7 @@ static rb_status launch_tc(const rb_mlp* m, cudaStream_t stream, int grid, const
     if (nn_tc256_supported(m)) return launch_tc256<SYSTEM>(m, stream, grid, src, dst, status);
     if (!tc_supported(m) || !m->bf16_img)
         return fail(RB_ENOTSUP, "BF16 tensor-core network needs width 128 or 256 and depth 1..3");
+    if (tc_two_pipelines()) return launch_tc2p<SYSTEM>(m, stream, grid, src, dst, status);
     const tc::Layout L = tc::layout(m->depth);
     const size_t smem = L.total + 1024;
     static bool attr[2] = {false, false};

@@ -1,0 +1,293 @@
+// Pair-network forces and torques on the tensor cores, width 128: two
+// independent tile pipelines per CTA.
+//
+// Paper mapping as in nn.cu / nn_tc.cu (energy network, Methods; forces and
+// torques as its gradients, SI Sec. 6).  Each 128-pair tile runs 2D dependent
+// stages (D forward layers, D-1 reverse layers, the input gradient); a single
+// pipeline leaves the tensor cores idle during every epilogue.  Here the two
+// warpgroups of the CTA are independent pipelines on different tiles: while
+// one waits for its MMAs, the other runs its epilogue.
+//   * Shared memory: all weights once (BF16, K-major, 128-byte swizzle, as in
+//     nn_tc.cu) plus, per warpgroup, one 128 x 128 activation tile whose first
+//     64-column atom also serves as the 64-column feature tile of layer 1.
+//   * Tensor memory: warpgroup g owns columns 256 g .. 256 g + 255: the
+//     accumulator of every stage (128 columns) and z_1, z_2 as packed BF16
+//     pairs (64 columns each) for the reverse pass.
+//   * Synchronisation per warpgroup: a named barrier (128 threads), its own
+//     mbarrier for MMA completion, a bounded wait with a failure flag.
+// Thread r of a warpgroup owns pair r of its tile (TMEM lane r) for the
+// features, all 128 columns of every epilogue, and the geometric adjoint.
+#include <cstdint>
+
+#include "tc_common.cuh"
+
+namespace rb {
+namespace tc2p {
+
+using namespace tc;
+
+constexpr int kThreads = 256;
+
+struct Layout {
+    uint32_t w1f, wf[4], wb[4], w1b, weights, h[2], f32, bar, total;
+};
+
+__host__ __device__ inline Layout layout(int D) {
+    Layout L{};
+    uint32_t o = 0;
+    L.w1f = o;
+    o += kW * kK1 * 2;
+    for (int l = 2; l <= D; ++l) {
+        L.wf[l] = o;
+        o += kW * kW * 2;
+    }
+    for (int l = 2; l <= D; ++l) {
+        L.wb[l] = o;
+        o += kW * kW * 2;
+    }
+    L.w1b = o;
+    o += kNX * kW * 2;
+    L.weights = o;  // identical to the width-128 image of nn_tc.cu
+    for (int g = 0; g < 2; ++g) {
+        L.h[g] = o;
+        o += kM * kW * 2;
+    }
+    L.f32 = o;
+    o += (D * kW + kW + 32) * 4;
+    L.bar = (o + 15) & ~15u;
+    L.total = L.bar + 64;
+    return L;
+}
+
+__device__ inline void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+// Named-barrier reduction: true if any thread of the warpgroup passes `flag`.
+__device__ inline bool wg_any(int g, bool flag) {
+    uint32_t res;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(res)
+        : "r"((uint32_t)flag), "r"(1 + g)
+        : "memory");
+    return res != 0;
+}
+
+template <bool SYSTEM>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_nn_tc2p(const float* __restrict__ flat, const uint4* __restrict__ img, int D, PairSrc src,
+              PairDst dst, unsigned* status) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const Layout Ly = layout(D);
+    const FlatLayout fl = flat_layout(kW, D);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = warp >> 2;                          // pipeline (warpgroup)
+    const int row = (warp & 3) * 32 + (tid & 31);     // TMEM lane = pair of the tile
+    const bool leader = (tid & 127) == 0;
+    float* bias = reinterpret_cast<float*>(sm + Ly.f32);  // D x 128
+    float* wo = bias + D * kW;
+    float* mu = wo + kW;
+    float* isd = mu + 16;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Ly.bar + 16);
+    const uint32_t bar = smem_u32(sm + Ly.bar + 8 * g);
+    const uint32_t s_base = smem_u32(sm);
+
+    {
+        uint4* dstw = reinterpret_cast<uint4*>(sm);
+        for (uint32_t t = tid; t < Ly.weights / 16; t += kThreads) dstw[t] = __ldg(img + t);
+        for (int t = tid; t < D * kW; t += kThreads) bias[t] = flat[fl.b_(1 + t / kW, kW) + t % kW];
+        for (int t = tid; t < kW; t += kThreads) wo[t] = flat[fl.wo + t];
+        for (int t = tid; t < 16; t += kThreads) {
+            mu[t] = t < kIn ? flat[fl.mu + t] : 0.f;
+            isd[t] = t < kIn ? flat[fl.inv_sd + t] : 0.f;
+        }
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(sm + Ly.bar), 1);
+        mbar_init(smem_u32(sm + Ly.bar + 8), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot + (uint32_t)(256 * g);  // this pipeline's columns
+    const uint32_t lane_field = (uint32_t)((warp & 3) * 32) << 16;
+    const float b_o = flat[fl.bo], e_scale = flat[fl.escale], e_shift = flat[fl.eshift];
+    const uint32_t idesc_w = idesc_bf16(kM, kW);
+    const uint32_t idesc_x = idesc_bf16(kM, kNX);
+    unsigned char* Ht = sm + Ly.h[g];
+    const uint32_t h_addr = s_base + Ly.h[g];
+
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t n_total = SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
+    const int64_t n_tiles = (n_total + kM - 1) / kM;
+    const int64_t stride = 2 * (int64_t)gridDim.x;
+    const int64_t first = (int64_t)blockIdx.x + (int64_t)g * gridDim.x;
+
+    // one GEMM stage of this pipeline: publish the A tile, issue, wait (bounded)
+    auto stage = [&](uint32_t a_base, uint32_t b_base, int K, int rows_b, uint32_t idesc) {
+        fence_proxy_async();
+        fence_before();
+        wg_sync(g);
+        if (leader) issue_gemm(tmem, a_base, b_base, K, rows_b, idesc, bar);
+        const bool got = mbar_wait(bar, phase, kWaitCycles);
+        phase ^= 1u;
+        if (wg_any(g, !got)) ok = false;
+        fence_after();
+    };
+
+    PairRaw raw = fetch_pair<SYSTEM>(src, first * kM + row, first * kM + row < n_total);
+    for (int64_t tile = first; tile < n_tiles && ok; tile += stride) {
+        const int64_t gp = tile * kM + row;
+        const bool valid = gp < n_total;
+        const PairGeom geo = pair_geometry<SYSTEM>(src, raw);
+        {
+            // features into the first atom of the activation tile (64 columns,
+            // 10 used): the zero columns are rewritten every tile because the
+            // previous tile's activations occupied them
+            float x[kIn];
+            raw_features(geo, x);
+            float xr[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) xr[k] = k < kIn ? (x[k] - mu[k]) * isd[k] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint4 w = make_uint4(0, 0, 0, 0);
+                if (q < 2) {
+                    w.x = pack_bf16(xr[8 * q + 0], xr[8 * q + 1]);
+                    w.y = pack_bf16(xr[8 * q + 2], xr[8 * q + 3]);
+                    w.z = pack_bf16(xr[8 * q + 4], xr[8 * q + 5]);
+                    w.w = pack_bf16(xr[8 * q + 6], xr[8 * q + 7]);
+                }
+                *reinterpret_cast<uint4*>(Ht + sw128_offset(kM, row, 8 * q)) = w;
+            }
+        }
+        float E = 0.f;
+        // ---------------- forward
+        for (int l = 1; l <= D && ok; ++l) {
+            if (l == 1)
+                stage(h_addr, s_base + Ly.w1f, kK1, kW, idesc_w);
+            else
+                stage(h_addr, s_base + Ly.wf[l], kW, kW, idesc_w);
+            if (!ok) break;
+            if (l == 1) {  // fetch the next tile's pair data while this one runs
+                const int64_t gn = (tile + stride) * kM + row;
+                raw = fetch_pair<SYSTEM>(src, gn, gn < n_total);
+            }
+            const float* b = bias + (l - 1) * kW;
+            float e_acc = 0.f;
+#pragma unroll 1
+            for (int c = 0; c < kW; c += 64) {
+                uint32_t u0[32], u1[32];
+                tmem_ld32_issue(tmem + lane_field + c, u0);
+                tmem_ld32_issue(tmem + lane_field + c + 32, u1);
+                tmem_wait32(u0);
+                tmem_wait32(u1);
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int cc = c + 32 * h2;
+                    float v[32];
+                    uint32_t zp[16];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(h2 == 0 ? u0[i] : u1[i]);
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const float z0 = v[i] + b[cc + i], z1 = v[i + 1] + b[cc + i + 1];
+                        zp[i / 2] = pack_bf16(z0, z1);
+                        const float s0 = sigm(z0), s1 = sigm(z1);
+                        if (l < D) {
+                            v[i] = z0 * s0;
+                            v[i + 1] = z1 * s1;
+                        } else {
+                            e_acc = fmaf(wo[cc + i], z0 * s0, e_acc);
+                            e_acc = fmaf(wo[cc + i + 1], z1 * s1, e_acc);
+                            v[i] = wo[cc + i] * s0 * (1.f + z0 * (1.f - s0));
+                            v[i + 1] = wo[cc + i + 1] * s1 * (1.f + z1 * (1.f - s1));
+                        }
+                    }
+                    if (l < D) tmem_st16(tmem + lane_field + kW + (l - 1) * 64 + cc / 2, zp);
+                    store_row32(Ht, kM, row, cc, v);
+                }
+            }
+            if (l == D) E = e_scale * (e_acc + b_o) + e_shift;
+        }
+        // ---------------- reverse: g_{l-1} = (g_l W_l) * silu'(z_{l-1})
+        for (int l = D; l >= 2 && ok; --l) {
+            stage(h_addr, s_base + Ly.wb[l], kW, kW, idesc_w);
+            if (!ok) break;
+            const uint32_t zcol = kW + (uint32_t)(l - 2) * 64;
+#pragma unroll 1
+            for (int c = 0; c < kW; c += 32) {
+                uint32_t uv[32], zp[16];
+                tmem_ld32_issue(tmem + lane_field + c, uv);
+                tmem_wait32(uv);
+                tmem_ld16u(tmem + lane_field + zcol + c / 2, zp);
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float2 z = unpack_bf16(zp[i]);
+                    const float s0 = sigm(z.x), s1 = sigm(z.y);
+                    v[2 * i] = __uint_as_float(uv[2 * i]) * s0 * (1.f + z.x * (1.f - s0));
+                    v[2 * i + 1] = __uint_as_float(uv[2 * i + 1]) * s1 * (1.f + z.y * (1.f - s1));
+                }
+                store_row32(Ht, kM, row, c, v);
+            }
+        }
+        // ---------------- dE/dx_hat = g_1 W_1 (16 padded columns) and the adjoint
+        if (ok) stage(h_addr, s_base + Ly.w1b, kW, kNX, idesc_x);
+        if (ok) {
+            float v[16];
+            tmem_ld16(tmem + lane_field, v);
+            if (valid) {
+                float gx[kIn];
+#pragma unroll
+                for (int k = 0; k < kIn; ++k) gx[k] = e_scale * v[k] * isd[k];
+                write_pair_outputs<SYSTEM>(dst, gp, geo, gx, E);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot),
+                     "r"(512));
+    }
+    if (!ok && leader) atomicOr(status, ST_TC_TIMEOUT);
+}
+
+}  // namespace tc2p
+
+template <bool SYSTEM>
+rb_status launch_tc2p(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
+                      const PairDst& dst, unsigned* status) {
+    const tc2p::Layout L = tc2p::layout(m->depth);
+    const size_t smem = L.total + 1024;
+    static bool attr[2] = {false, false};
+    if (!attr[SYSTEM ? 1 : 0]) {
+        RB_CUDA(cudaFuncSetAttribute(tc2p::k_nn_tc2p<SYSTEM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr[SYSTEM ? 1 : 0] = true;
+    }
+    tc2p::k_nn_tc2p<SYSTEM><<<grid, tc2p::kThreads, smem, stream>>>(
+        m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+template rb_status launch_tc2p<true>(const rb_mlp*, cudaStream_t, int, const PairSrc&,
+                                     const PairDst&, unsigned*);
+template rb_status launch_tc2p<false>(const rb_mlp*, cudaStream_t, int, const PairSrc&,
+                                      const PairDst&, unsigned*);
+
+}  // namespace rb

@@ -195,7 +195,7 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     RB_CUDA(cudaMemcpyAsync(s.tmpl_dev, tmpl, sizeof(float4) * nb, cudaMemcpyHostToDevice, s.stream));
     RB_CUDA(cudaMemsetAsync(s.status_dev, 0, sizeof(unsigned), s.stream));
     RB_CUDA(cudaMemsetAsync(s.cells.count, 0, sizeof(int) * n_cells, s.stream));
-    RB_TRY(build_pairs_async(&s, true));
+    RB_TRY(build_pairs_async(&s, true, false));
     RB_TRY(bead_pairs_async(&s));
     RB_TRY(reduce_forces_async(&s, 0.f));
     unsigned st = 0;

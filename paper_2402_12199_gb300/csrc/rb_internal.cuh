@@ -184,7 +184,7 @@ struct rb_system {
 
 namespace rb {
 // system.cu
-rb_status build_pairs_async(rb_system* s, bool force);  // force: rebuild regardless of the skin
+rb_status build_pairs_async(rb_system* s, bool force, bool checked);  // force: rebuild regardless of the skin; checked: skin already checked (by the integrator)
 rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
 rb_status energy_async(rb_system* s);
 // beads.cu

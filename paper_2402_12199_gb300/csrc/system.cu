@@ -285,9 +285,11 @@ __global__ void k_skin_check(int N, float half_skin2, float3 L, float3 invL,
     if (d.x * d.x + d.y * d.y + d.z * d.z > half_skin2) *rebuild = 1;
 }
 
-// Per-body reduction of the per-pair results in a fixed order (own half row by
-// ascending j, then mirrored pairs by ascending j): no atomics, so results are
-// bit-reproducible.  Optionally applies the second velocity-Verlet half kick.
+// Per-body reduction of the per-pair results in a fixed order, no atomics, so
+// results are bit-reproducible: four threads per body take every fourth entry
+// of the body's list (own half row by ascending j, then mirrored pairs by
+// ascending j) and combine with two fixed xor shuffles.  Optionally applies
+// the second velocity-Verlet half kick.
 __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
                          const int* __restrict__ half_count, const int* __restrict__ lower_count,
                          const int* __restrict__ lower_pair, const float4* __restrict__ pF,
@@ -295,41 +297,55 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
                          float4* __restrict__ force, float4* __restrict__ torque, float kick,
                          float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
                          const float4* __restrict__ quat, unsigned* status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t >> 2, sub = t & 3;
+    const bool live = i < N;
     float3 F = make_float3(0.f, 0.f, 0.f), T = make_float3(0.f, 0.f, 0.f);
     float e = 0.f;
-    const int off = half_off[i];
-    const int n = (int)min((int64_t)half_count[i], cap_pairs - off);
-    for (int k = 0; k < n; ++k) {
-        float4 f = pF[off + k];
-        float4 t = pti[off + k];
-        F.x -= f.x; F.y -= f.y; F.z -= f.z;
-        T.x += t.x; T.y += t.y; T.z += t.z;
-        e += 0.5f * f.w;
+    if (live) {
+        const int off = half_off[i];
+        const int n = (int)min((int64_t)half_count[i], cap_pairs - off);
+        const int nl = lower_count[i];
+        const int* lrow = lower_pair + (size_t)i * max_nbr;
+        for (int k = sub; k < n + nl; k += 4) {
+            if (k < n) {
+                const float4 f = pF[off + k];
+                const float4 q = pti[off + k];
+                F.x -= f.x; F.y -= f.y; F.z -= f.z;
+                T.x += q.x; T.y += q.y; T.z += q.z;
+                e += 0.5f * f.w;
+            } else {
+                const int p = lrow[k - n];
+                if (p < 0) continue;
+                const float4 f = pF[p];
+                const float4 q = ptj[p];
+                F.x += f.x; F.y += f.y; F.z += f.z;
+                T.x += q.x; T.y += q.y; T.z += q.z;
+                e += 0.5f * f.w;
+            }
+        }
     }
-    const int nl = lower_count[i];
-    const int* lrow = lower_pair + (size_t)i * max_nbr;
-    for (int m = 0; m < nl; ++m) {
-        int p = lrow[m];
-        if (p < 0) continue;
-        float4 f = pF[p];
-        float4 t = ptj[p];
-        F.x += f.x; F.y += f.y; F.z += f.z;
-        T.x += t.x; T.y += t.y; T.z += t.z;
-        e += 0.5f * f.w;
+    float v[7] = {F.x, F.y, F.z, T.x, T.y, T.z, e};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2);
     }
+    if (!live || sub != 0) return;
+    F = make_float3(v[0], v[1], v[2]);
+    T = make_float3(v[3], v[4], v[5]);
+    e = v[6];
     if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
           isfinite(T.z) && isfinite(e)))
         atomicOr(status, ST_NONFINITE);
     force[i] = make_float4(F.x, F.y, F.z, e);
     torque[i] = make_float4(T.x, T.y, T.z, 0.f);
     if (kick != 0.f) {
-        float4 v = vel[i];
-        v.x += kick * F.x * inv_mass;
-        v.y += kick * F.y * inv_mass;
-        v.z += kick * F.z * inv_mass;
-        vel[i] = v;
+        float4 vv = vel[i];
+        vv.x += kick * F.x * inv_mass;
+        vv.y += kick * F.y * inv_mass;
+        vv.z += kick * F.z * inv_mass;
+        vel[i] = vv;
         Mat3 R = qmat(quat[i]);
         float3 tb = mulT(R, T);
         float4 Lb = angmom[i];
@@ -347,7 +363,9 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
                                   float3 invL, float4* __restrict__ pos, float4* __restrict__ quat,
                                   float4* __restrict__ vel, float4* __restrict__ angmom,
                                   const float4* __restrict__ force,
-                                  const float4* __restrict__ torque) {
+                                  const float4* __restrict__ torque,
+                                  const float4* __restrict__ pos_ref, float half_skin2,
+                                  int* rebuild) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float h = 0.5f * dt;
@@ -389,6 +407,11 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
     quat[i] = q;
     vel[i] = v;
     angmom[i] = make_float4(Lb[0], Lb[1], Lb[2], Lw.w);
+    if (half_skin2 > 0.f) {  // the skin check of the pair list, fused here
+        const float4 r = pos_ref[i];
+        const float3 d = min_image(make_float3(p.x - r.x, p.y - r.y, p.z - r.z), L, invL);
+        if (d.x * d.x + d.y * d.y + d.z * d.z > half_skin2) *rebuild = 1;
+    }
 }
 
 // Deterministic block reduction of NV doubles; thread 0 writes the block sums.
@@ -471,7 +494,7 @@ static inline int blocks_for(int64_t n, int t) { return (int)std::max<int64_t>(1
 static inline float3 f3(const float* a) { return make_float3(a[0], a[1], a[2]); }
 static inline float3 inv3(const float* a) { return make_float3(1.f / a[0], 1.f / a[1], 1.f / a[2]); }
 
-rb_status build_pairs_async(rb_system* s, bool force) {
+rb_status build_pairs_async(rb_system* s, bool force, bool checked) {
     const int N = (int)s->N;
     const float3 L = f3(s->box), invL = inv3(s->box);
     const float3 invw = inv3(s->cells.width);
@@ -479,7 +502,7 @@ rb_status build_pairs_async(rb_system* s, bool force) {
     const float Rl = s->Rc + s->skin;
     if (force || !(s->skin > 0.f)) {
         k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
-    } else {
+    } else if (!checked) {
         k_skin_check<<<blocks_for(N, 256), 256, 0, s->stream>>>(
             N, 0.25f * s->skin * s->skin, L, invL, s->pos, s->pos_ref, s->rebuild_flag);
     }
@@ -509,7 +532,7 @@ rb_status build_pairs_async(rb_system* s, bool force) {
 
 rb_status reduce_forces_async(rb_system* s, float kick) {
     const int N = (int)s->N;
-    k_reduce<<<blocks_for(N, 256), 256, 0, s->stream>>>(
+    k_reduce<<<blocks_for((int64_t)N * 4, 256), 256, 0, s->stream>>>(
         N, s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count, s->pl.lower_count,
         s->pl.lower_nbr,
         s->pair_F, s->pair_ti, s->pair_tj, s->force, s->torque, kick, 1.f / s->mass, s->vel,
@@ -840,7 +863,7 @@ rb_status rb_get_forces(const rb_system* s, float* force, float* torque, int32_t
 
 rb_status rb_build_pairs(rb_system* s, int64_t* n_pairs) {
     if (!s) return fail(RB_EINVAL, "null system");
-    RB_TRY(build_pairs_async(s, true));
+    RB_TRY(build_pairs_async(s, true, false));
     if (n_pairs) {
         RB_TRY(check_status(s));
         int n = 0;
@@ -885,7 +908,7 @@ static rb_status finish_forces(rb_system* s, float* force, float* torque, double
 rb_status rb_forces_beads(rb_system* s, float* force, float* torque, double* energy,
                           double* virial9) {
     if (!s) return fail(RB_EINVAL, "null system");
-    RB_TRY(build_pairs_async(s, false));
+    RB_TRY(build_pairs_async(s, false, false));
     RB_TRY(bead_pairs_async(s));
     RB_TRY(reduce_forces_async(s, 0.f));
     s->forces_valid = true;
@@ -899,7 +922,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
                        float* torque, double* energy, double* virial9) {
     if (!s) return fail(RB_EINVAL, "null system");
     RB_TRY(check_mlp(m));
-    RB_TRY(build_pairs_async(s, false));
+    RB_TRY(build_pairs_async(s, false, false));
     RB_TRY(nn_pairs_system_async(s, m, precision));
     RB_TRY(bead_fallback_async(s));
     RB_TRY(reduce_forces_async(s, 0.f));
@@ -912,8 +935,8 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
 }
 
 static rb_status eval_forces_async(rb_system* s, int path, const rb_mlp* m, int precision,
-                                   float kick) {
-    RB_TRY(build_pairs_async(s, false));
+                                   float kick, bool checked = false) {
+    RB_TRY(build_pairs_async(s, false, checked));
     if (path == RB_PATH_BEADS) {
         RB_TRY(bead_pairs_async(s));
     } else {
@@ -974,8 +997,9 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
         k_integrate_first<<<blocks_for(N, 256), 256, 0, s->stream>>>(
             N, dt, 1.f / s->mass,
             make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
-            f3(s->box), inv3(s->box), s->pos, s->quat, s->vel, s->angmom, s->force, s->torque);
-        rb_status st = eval_forces_async(s, path, m, precision, 0.5f * dt);
+            f3(s->box), inv3(s->box), s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
+            s->pos_ref, s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f, s->rebuild_flag);
+        rb_status st = eval_forces_async(s, path, m, precision, 0.5f * dt, true);
         cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
         s->stream = user;
         if (st != RB_OK) {

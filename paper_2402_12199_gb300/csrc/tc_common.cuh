@@ -241,6 +241,10 @@ __device__ inline void issue_gemm(uint32_t tmem_d, uint32_t a_base, uint32_t b_b
 
 }  // namespace tc
 
+// nn_tc2p.cu (width 128, two tile pipelines per CTA; same weight image)
+template <bool SYSTEM>
+rb_status launch_tc2p(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
+                      const PairDst& dst, unsigned* status);
 // nn_tc256.cu (width 256, streamed weights)
 bool nn_tc256_supported(const rb_mlp* m);
 rb_status nn_tc256_prepare(rb_mlp* m);
