@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--train-samples", type=int, default=200000)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--skin", type=float, default=0.4)
+    ap.add_argument("--drift-steps", type=int, default=10000)
+    ap.add_argument("--drift-every", type=int, default=500)
     return ap.parse_args()
 
 
@@ -423,10 +425,34 @@ def main():
         flops = tc_flops / 128 * n_pairs["nn_bf16"]
         achieved = flops / (d_ms * 1e-3) / 1e12
         peak = pk.get("bf16_tflops_sustained", 1700.0)
-        roof_nn = {"kernel": "k_nn_tc", "bound": "tensor", "achieved": achieved, "peak": peak,
+        roof_nn = {"kernel": "k_nn_tc2p", "bound": "tensor", "achieved": achieved, "peak": peak,
                    "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
                    "peak_source": f"bf16_tflops_sustained ({how})", "flops_per_launch": flops,
                    "mufu_per_pair": 6 * WIDTH, "note": "one tanh.approx per SiLU evaluation"}
+
+    roof_f32 = None
+    if "nn_fp32" in systems:
+        s = systems["nn_fp32"]
+        s.build_pairs()
+        for _ in range(3):
+            s.eval_pairs(api.RB_PATH_NN, mlp, "fp32")
+        durs = []
+        for _ in range(10):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.eval_pairs(api.RB_PATH_NN, mlp, "fp32")
+            b.record(stream)
+            durs.append((a, b))
+        torch.cuda.synchronize()
+        d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
+        flops = nn_flops_per_pair(WIDTH, DEPTH) * n_pairs["nn_fp32"]
+        achieved = flops / (d_ms * 1e-3) / 1e12
+        peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
+        roof_f32 = {"kernel": "k_nn_f32", "bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+                    "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
+                    "flops_per_launch": flops}
 
     # ---- network width 256 (BF16, streamed weights), same workload, timed alone
     width256 = None
@@ -467,6 +493,40 @@ def main():
                     "frac_of_bf16_sustained": tc256 / (k256 * 1e-3) / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
                     "steps_timed": 200}
         del s256, m256
+
+    # ---- NVE energy conservation: a fresh copy of the workload per path, run
+    # for --drift-steps steps with the FP64 total energy read every
+    # --drift-every steps (outside every timed region)
+    drift = None
+    if args.drift_steps > 0:
+        drift = {"steps": args.drift_steps, "dt": DT, "sample_every": args.drift_every,
+                 "measure": "max_t |E_tot(t) - E_tot(0)| / (N kT) and the least-squares slope "
+                            "per 1000 steps; E_tot = E_pot + KE_trans + KE_rot in FP64"}
+        for p in paths:
+            s = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
+            s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+            if p == "beads":
+                s.forces_beads()
+            else:
+                s.forces_nn(mlp, pcfg(p)["precision"])
+            t_series, e_series = [0], [sum(s.energy())]
+            done = 0
+            while done < args.drift_steps:
+                k = min(args.drift_every, args.drift_steps - done)
+                s.step(k, DT, **pcfg(p))
+                done += k
+                t_series.append(done)
+                e_series.append(sum(s.energy()))
+            e = np.array(e_series)
+            dev = np.abs(e - e[0]) / (N_BODIES * KT)
+            finite = bool(np.all(np.isfinite(e)))
+            drift[p] = {"max_abs_drift_per_body_kT": float(dev.max()) if finite else None,
+                        "slope_per_body_kT_per_1k_steps":
+                            float(np.polyfit(np.array(t_series) / 1000.0, e / (N_BODIES * KT), 1)[0])
+                            if finite else None,
+                        "E0_per_body_kT": float(e[0] / (N_BODIES * KT)) if finite else None,
+                        "finite": finite}
+            del s
 
     # ---- end to end through the public API with host buffers
     pinned = {k: torch.from_numpy(st[k]).pin_memory() for k in ("pos", "quat", "vel", "angmom")}
@@ -533,9 +593,9 @@ def main():
                        "pair_list": f"Verlet skin {args.skin} sigma, rebuilt on the device when a "
                                     f"centre moves more than skin/2; pairs beyond Rc give exactly zero",
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
-            "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "cpu_baseline": cpu,
+            "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_fp32": roof_f32, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
-            "nn_bf16_width256": width256,
+            "nn_bf16_width256": width256, "nve_drift": drift,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per MD step and path: integrate, skin check, cell assign, pair build,

@@ -16,12 +16,18 @@
 //   tau_i = s x G_s - tau_j
 // and finally a rotation by R(q_i) into the space frame.
 //
-// Kernel layout: one CTA of 256 threads processes tiles of P pairs.  Layer
-// activations live in shared memory as [unit][pair]; each thread owns a 4-pair
-// x 8-unit register block of every layer GEMM (SIMT FFMA), weights streamed
-// from global memory (L2-resident) in 32-row chunks.  Pre-activations of every
-// layer stay in shared memory for the backward pass, which overwrites them in
-// place with the back-propagated signals.
+// Kernel layout: one CTA of 256 threads per SM, persistent over tiles of P
+// pairs.  Layer activations live in shared memory as [unit][pair]; each thread
+// owns a 4-pair x 8-unit register block of every layer GEMM, accumulated with
+// packed FP32x2 FMAs.  The GEMM weights (transposed copies for the forward
+// pass, plain copies for the reverse pass) stream from L2 in 16 KB chunks
+// through a two-buffer cp.async ring: the copy of chunk c+1 runs while chunk c
+// is multiplied, one barrier per chunk.  The forward pass keeps silu'(z_l) of
+// every layer (not z_l) for the reverse pass, which then needs no
+// transcendental and overwrites those values in place with the
+// back-propagated signals.  The energy and dE/dx are reduced over all threads
+// in a fixed order, and the next tile's pair data is fetched during the
+// current tile.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,21 +38,25 @@
 
 namespace rb {
 
-constexpr int kKC = 32;
+constexpr int kF32Threads = 256;
+constexpr int kChunkBytes = 16384;  // one weight chunk in shared memory
 
 // Prepared FP32 weights (device), built from the flat parameters:
-//   WT1p [16][W]      W1 transposed, rows 10..15 zero
-//   WT_l [W][W]       W_l transposed, l = 2..D
-//   W1p  [W][16]      W1 with columns 10..15 zero
+//   WT1p [16][W]      W1 transposed, rows 10..15 zero          (forward, layer 1)
+//   WT_l [W][W]       W_l transposed, l = 2..D                 (forward)
+//   W1p  [W][16]      W1 with columns 10..15 zero              (dE/dx)
+//   WR_l [W][W]       W_l as stored ([out][in]), l = 2..D      (reverse)
+// Every block starts on a 64-byte boundary (W is a multiple of 64).
 struct F32Layout {
-    int64_t wt1 = 0, wt = 0, w1p = 0, total = 0;
+    int64_t wt1 = 0, wt = 0, w1p = 0, wr = 0, total = 0;
 };
 __host__ __device__ inline F32Layout f32_layout(int W, int D) {
     F32Layout L;
     L.wt1 = 0;
     L.wt = L.wt1 + (int64_t)kInPad * W;
     L.w1p = L.wt + (int64_t)(D - 1) * W * W;
-    L.total = L.w1p + (int64_t)W * kInPad;
+    L.wr = L.w1p + (int64_t)W * kInPad;
+    L.total = L.wr + (int64_t)(D - 1) * W * W;
     return L;
 }
 __global__ void k_prepare_f32(const float* __restrict__ flat, int W, int D, float* __restrict__ out) {
@@ -65,10 +75,14 @@ __global__ void k_prepare_f32(const float* __restrict__ flat, int W, int D, floa
             int64_t e = r % ((int64_t)W * W);
             int k = (int)(e / W), o = (int)(e % W);
             v = flat[f.W_(l, W) + (int64_t)o * W + k];
-        } else {  // W1p[o][k] = W1[o][k]
+        } else if (t < L.wr) {  // W1p[o][k] = W1[o][k]
             int64_t r = t - L.w1p;
             int o = (int)(r / kInPad), k = (int)(r % kInPad);
             v = k < kIn ? flat[f.W1 + (int64_t)o * kIn + k] : 0.f;
+        } else {  // WR_l[o][k] = W_l[o][k]
+            int64_t r = t - L.wr;
+            int l = 2 + (int)(r / ((int64_t)W * W));
+            v = flat[f.W_(l, W) + r % ((int64_t)W * W)];
         }
         out[t] = v;
     }
@@ -85,73 +99,157 @@ struct NetArgs {
 
 __device__ inline float sigmoidf_(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 
-// acc[a][b] += sum_k A[k][p0 + a] * B[k][o0 + b], A in shared [K][P], B in
-// global [K][W] streamed through shared Bs in kKC-row chunks.
+__device__ inline void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The weight chunks one tile consumes, in order: layer-1 (16 rows), the
+// forward chunks of W_2..W_D, the reverse chunks of W_D..W_2.  A CTA consumes
+// this sequence once per tile; chunk c lives in buffer c % 2.
+template <int W>
+struct ChunkFeed {
+    static constexpr int KC = kChunkBytes / (4 * W);  // weight rows per chunk
+    static constexpr int NK = W / KC;                 // chunks per hidden matrix
+    const float* prep;
+    F32Layout pl;
+    int D;
+    int n_chunks;
+    int64_t c, total;
+    float* buf;
+
+    __device__ void source(int ci, const float*& p, int& rows) const {
+        if (ci == 0) {
+            p = prep + pl.wt1;
+            rows = kInPad;
+            return;
+        }
+        int r = ci - 1;
+        rows = KC;
+        const int nf = (D - 1) * NK;
+        if (r < nf) {
+            p = prep + pl.wt + (int64_t)(r / NK) * W * W + (int64_t)(r % NK) * KC * W;
+            return;
+        }
+        r -= nf;
+        const int l = D - r / NK;
+        p = prep + pl.wr + (int64_t)(l - 2) * W * W + (int64_t)(r % NK) * KC * W;
+    }
+    // All threads: start the copy of chunk cc into its buffer.
+    __device__ void issue(int64_t cc) {
+        if (cc >= total) return;
+        const float* p;
+        int rows;
+        source((int)(cc % n_chunks), p, rows);
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(buf + (cc & 1) * KC * W));
+        const int pieces = rows * W / 4;
+        for (int t = threadIdx.x; t < pieces; t += kF32Threads) cp_async16(dst + 16u * t, p + 4 * t);
+        cp_async_commit();
+    }
+    // Wait for chunk c (this thread's copies, then everyone's via the
+    // barrier, which also retires every read of chunk c-1's buffer), start
+    // chunk c+1 into that buffer and return chunk c.
+    __device__ const float* acquire() {
+        cp_async_wait_all();
+        __syncthreads();
+        issue(c + 1);
+        return buf + (c & 1) * KC * W;
+    }
+    __device__ void release() { ++c; }
+};
+
+// acc[i/2][j].{x,y} += sum_k A[k][p0 + i] * B[k][o0 + j] for i = 0..3 and
+// j = 0..7: A in shared memory as [K][P], B the next K/KC weight chunks.
 template <int W, int P>
-__device__ inline void gemm_block(const float* __restrict__ As, int K, const float* __restrict__ Bg,
-                                  float* __restrict__ Bs, int p0, int o0, float (&acc)[4][8]) {
-    for (int kc = 0; kc < K; kc += kKC) {
-        const int kn = min(kKC, K - kc);
-        __syncthreads();
-        const float4* src = reinterpret_cast<const float4*>(Bg + (size_t)kc * W);
-        float4* dst = reinterpret_cast<float4*>(Bs);
-        for (int t = threadIdx.x; t < kn * W / 4; t += blockDim.x) dst[t] = __ldg(src + t);
-        __syncthreads();
+__device__ inline void gemm_tile(const float* __restrict__ As, int K, ChunkFeed<W>& feed, int p0,
+                                 int o0, float2 (&acc)[2][8]) {
+    constexpr int KC = ChunkFeed<W>::KC;
+    for (int kc = 0; kc < K; kc += KC) {
+        const float* Bs = feed.acquire();
+        const int kn = min(KC, K - kc);
 #pragma unroll 4
         for (int k = 0; k < kn; ++k) {
             const float4 a = *reinterpret_cast<const float4*>(As + (size_t)(kc + k) * P + p0);
             const float4 b0 = *reinterpret_cast<const float4*>(Bs + (size_t)k * W + o0);
             const float4 b1 = *reinterpret_cast<const float4*>(Bs + (size_t)k * W + o0 + 4);
-            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float2 a01 = make_float2(a.x, a.y), a23 = make_float2(a.z, a.w);
             const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            for (int j = 0; j < 8; ++j) {
+                const float2 bb = make_float2(bv[j], bv[j]);
+                acc[0][j] = __ffma2_rn(a01, bb, acc[0][j]);
+                acc[1][j] = __ffma2_rn(a23, bb, acc[1][j]);
+            }
         }
+        feed.release();
     }
 }
 
+__device__ inline float acc_at(const float2 (&acc)[2][8], int i, int j) {
+    return (i & 1) ? acc[i >> 1][j].y : acc[i >> 1][j].x;
+}
+
 template <int W, int P, bool SYSTEM>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kF32Threads, 1)
     k_nn_f32(NetArgs net, PairSrc src, PairDst dst) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
+    constexpr int KC = ChunkFeed<W>::KC;
+    constexpr int NTP = P / 4;              // threads along pairs
+    constexpr int NG = kF32Threads / NTP;   // thread groups along units
+    constexpr int NS = kF32Threads / P;     // unit slices of the dE/dx reduction
+    static_assert(NG * 8 == W, "register blocks must tile the layer width");
+    static_assert(NS * kIn * P <= W * P, "dE/dx partial sums must fit in the activation buffer");
     const int D = net.D;
-    float* Zs = smem;                          // D x [W][P]
-    float* Hs = Zs + (size_t)D * W * P;        // [W][P]
-    float* Bs = Hs + (size_t)W * P;            // [kKC][W]
-    float* Xs = Bs + (size_t)kKC * W;          // [16][P]
-    float* misc = Xs + (size_t)kInPad * P;     // mu, inv_sd (16 + 16)
+    float* Zs = smem;                          // D x [W][P]: silu'(z_l), then G_l
+    float* Hs = Zs + (size_t)D * W * P;        // [W][P]: h_l; dE/dx partial sums at the end
+    float* Bs = Hs + (size_t)W * P;            // 2 x [KC][W] weight chunks
+    float* Xs = Bs + (size_t)2 * KC * W;       // [16][P] normalised features
+    float* Red = Xs + (size_t)kInPad * P;      // [NG][P] energy partial sums
+    float* misc = Red + (size_t)NG * P;        // mu, inv_sd (16 + 16)
     float* bias = misc + 32;                   // D x W
     float* wo = bias + (size_t)D * W;          // W
 
-    // pairs vary fastest across a warp: the [unit][pair] stores of a warp hit
-    // consecutive addresses and the weight loads are broadcasts
-    constexpr int NTP = P / 4;
+    // pairs vary fastest across a warp: the [unit][pair] accesses of a warp
+    // hit consecutive addresses and the weight loads are broadcasts
     const int tp = threadIdx.x % NTP, to = threadIdx.x / NTP;
     const int p0 = tp * 4, o0 = to * 8;
     const float* flat = net.flat;
-    for (int t = threadIdx.x; t < kIn; t += blockDim.x) {
+    for (int t = threadIdx.x; t < kIn; t += kF32Threads) {
         misc[t] = flat[net.fl.mu + t];
         misc[16 + t] = flat[net.fl.inv_sd + t];
     }
-    for (int t = threadIdx.x; t < D * W; t += blockDim.x) {
+    for (int t = threadIdx.x; t < D * W; t += kF32Threads) {
         const int l = 1 + t / W, o = t % W;
         bias[t] = flat[net.fl.b_(l, W) + o];
     }
-    for (int t = threadIdx.x; t < W; t += blockDim.x) wo[t] = flat[net.fl.wo + t];
+    for (int t = threadIdx.x; t < W; t += kF32Threads) wo[t] = flat[net.fl.wo + t];
     const float b_o = flat[net.fl.bo], e_scale = flat[net.fl.escale], e_shift = flat[net.fl.eshift];
-    __syncthreads();
 
     const int64_t n_total = SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
     const int64_t n_tiles = (n_total + P - 1) / P;
+    const int64_t my_tiles =
+        n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    ChunkFeed<W> feed;
+    feed.prep = net.prep;
+    feed.pl = net.pl;
+    feed.D = D;
+    feed.n_chunks = 1 + 2 * (D - 1) * ChunkFeed<W>::NK;
+    feed.c = 0;
+    feed.total = my_tiles * feed.n_chunks;
+    feed.buf = Bs;
+    feed.issue(0);
+    __syncthreads();
+
+    const int p = threadIdx.x;
+    PairRaw raw = fetch_pair<SYSTEM>(src, (int64_t)blockIdx.x * P + p,
+                                     p < P && (int64_t)blockIdx.x * P + p < n_total);
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         // ---------------- prologue: features of pair p (threads 0..P-1)
-        const int p = threadIdx.x;
         const int64_t gp = tile * P + p;
         const bool valid = p < P && gp < n_total;
-        const PairGeom geo = load_pair<SYSTEM>(src, gp, valid);
+        const PairGeom geo = pair_geometry<SYSTEM>(src, raw);
         if (p < P) {
             float x[kIn];
             raw_features(geo, x);
@@ -160,106 +258,131 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int k = kIn; k < kInPad; ++k) Xs[k * P + p] = 0.f;
         }
-        // ---------------- forward
-        for (int l = 1; l <= D; ++l) {
-            float acc[4][8];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-            const float* A = l == 1 ? Xs : Hs;
-            const int K = l == 1 ? kInPad : W;
-            const float* B = l == 1 ? net.prep + net.pl.wt1 : net.prep + net.pl.wt + (size_t)(l - 2) * W * W;
-            gemm_block<W, P>(A, K, B, Bs, p0, o0, acc);
-            __syncthreads();  // all reads of Hs done
-            float* Z = Zs + (size_t)(l - 1) * W * P;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float b = bias[(l - 1) * W + o0 + j];
-                float4 z4, h4;
-                float* zz = &z4.x;
-                float* hh = &h4.x;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float z = acc[i][j] + b;
-                    zz[i] = z;
-                    hh[i] = z * sigmoidf_(z);
-                }
-                *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = z4;
-                *reinterpret_cast<float4*>(Hs + (size_t)(o0 + j) * P + p0) = h4;
-            }
-        }
-        __syncthreads();
-        // ---------------- energy (threads 0..P-1) and G_D = w_o * silu'(z_D) in place
-        float E = 0.f;
-        if (p < P) {
-            float e = b_o;
-            for (int o = 0; o < W; ++o) e = fmaf(wo[o], Hs[(size_t)o * P + p], e);
-            E = e_scale * e + e_shift;
-        }
         {
-            float* Z = Zs + (size_t)(D - 1) * W * P;
+            const int64_t nt = tile + gridDim.x, ngp = nt * P + p;
+            raw = fetch_pair<SYSTEM>(src, ngp, p < P && nt < n_tiles && ngp < n_total);
+        }
+        // ---------------- forward; the last layer also forms the energy
+        // partial sums and G_D = w_o * silu'(z_D)
+        for (int l = 1; l <= D; ++l) {
+            float2 acc[2][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float4 z4 = *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0);
-                float* zz = &z4.x;
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float sg = sigmoidf_(zz[i]);
-                    zz[i] = wo[o0 + j] * sg * (1.f + zz[i] * (1.f - sg));
+                for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+            gemm_tile<W, P>(l == 1 ? Xs : Hs, l == 1 ? kInPad : W, feed, p0, o0, acc);
+            float* Z = Zs + (size_t)(l - 1) * W * P;
+            if (l < D) {
+                if (l > 1) __syncthreads();  // every read of Hs by this GEMM is done
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float b = bias[(l - 1) * W + o0 + j];
+                    float4 d4, h4;
+                    float* dd = &d4.x;
+                    float* hh = &h4.x;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float z = acc_at(acc, i, j) + b;
+                        const float sg = sigmoidf_(z);
+                        hh[i] = z * sg;
+                        dd[i] = sg * (1.f + z * (1.f - sg));
+                    }
+                    *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = d4;
+                    *reinterpret_cast<float4*>(Hs + (size_t)(o0 + j) * P + p0) = h4;
                 }
-                *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = z4;
+            } else {
+                float e4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float b = bias[(l - 1) * W + o0 + j], w = wo[o0 + j];
+                    float4 g4;
+                    float* gg = &g4.x;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float z = acc_at(acc, i, j) + b;
+                        const float sg = sigmoidf_(z);
+                        e4[i] = fmaf(w, z * sg, e4[i]);
+                        gg[i] = w * (sg * (1.f + z * (1.f - sg)));
+                    }
+                    *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = g4;
+                }
+                *reinterpret_cast<float4*>(Red + (size_t)to * P + p0) =
+                    make_float4(e4[0], e4[1], e4[2], e4[3]);
             }
         }
-        // ---------------- backward: G_{l-1} = (G_l W_l) * silu'(z_{l-1})
+        // ---------------- reverse: G_{l-1} = (G_l W_l) * silu'(z_{l-1}), in place
         for (int l = D; l >= 2; --l) {
-            float acc[4][8];
+            float2 acc[2][8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-            const float* A = Zs + (size_t)(l - 1) * W * P;        // G_l as [o][p]
-            const float* B = net.flat + net.fl.W_(l, W);          // W_l as [o][i]
-            gemm_block<W, P>(A, W, B, Bs, p0, o0, acc);
+                for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+            gemm_tile<W, P>(Zs + (size_t)(l - 1) * W * P, W, feed, p0, o0, acc);
             float* Z = Zs + (size_t)(l - 2) * W * P;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float4 z4 = *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0);
-                float* zz = &z4.x;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float sg = sigmoidf_(zz[i]);
-                    zz[i] = acc[i][j] * sg * (1.f + zz[i] * (1.f - sg));
-                }
-                *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = z4;
+                float4 g4 = *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0);
+                g4.x *= acc[0][j].x;
+                g4.y *= acc[0][j].y;
+                g4.z *= acc[1][j].x;
+                g4.w *= acc[1][j].y;
+                *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = g4;
             }
         }
         __syncthreads();
-        // ---------------- dE/dx_hat = G_1 W_1 (16 padded outputs per pair)
-        for (int t = threadIdx.x; t < P * kInPad; t += blockDim.x) {
-            const int pp = t % P, k = t / P;
-            const float* G1 = Zs;
-            const float* W1p = net.prep + net.pl.w1p;
-            float a = 0.f;
-            for (int o = 0; o < W; ++o) a = fmaf(G1[(size_t)o * P + pp], __ldg(W1p + (size_t)o * kInPad + k), a);
-            Xs[k * P + pp] = a;
+        // ---------------- dE/dx_hat = G_1 W_1: NS unit slices per pair
+        {
+            const int pp = threadIdx.x % P, ks = threadIdx.x / P;
+            constexpr int SL = W / NS;
+            const float4* W1p = reinterpret_cast<const float4*>(net.prep + net.pl.w1p);
+            float g[kIn];
+#pragma unroll
+            for (int k = 0; k < kIn; ++k) g[k] = 0.f;
+#pragma unroll 4
+            for (int o = ks * SL; o < (ks + 1) * SL; ++o) {
+                const float gv = Zs[(size_t)o * P + pp];
+                const float4 w0 = __ldg(W1p + 4 * o), w1 = __ldg(W1p + 4 * o + 1),
+                             w2 = __ldg(W1p + 4 * o + 2);
+                g[0] = fmaf(gv, w0.x, g[0]);
+                g[1] = fmaf(gv, w0.y, g[1]);
+                g[2] = fmaf(gv, w0.z, g[2]);
+                g[3] = fmaf(gv, w0.w, g[3]);
+                g[4] = fmaf(gv, w1.x, g[4]);
+                g[5] = fmaf(gv, w1.y, g[5]);
+                g[6] = fmaf(gv, w1.z, g[6]);
+                g[7] = fmaf(gv, w1.w, g[7]);
+                g[8] = fmaf(gv, w2.x, g[8]);
+                g[9] = fmaf(gv, w2.y, g[9]);
+            }
+#pragma unroll
+            for (int k = 0; k < kIn; ++k) Hs[(size_t)(ks * kIn + k) * P + pp] = g[k];
         }
         __syncthreads();
-        // ---------------- geometric adjoint (threads 0..P-1)
+        // ---------------- energy and geometric adjoint (threads 0..P-1)
         if (valid) {
+            float e = 0.f;
+#pragma unroll 8
+            for (int g = 0; g < NG; ++g) e += Red[(size_t)g * P + p];
+            const float E = e_scale * (e + b_o) + e_shift;
             float gx[kIn];
 #pragma unroll
-            for (int k = 0; k < kIn; ++k) gx[k] = e_scale * Xs[k * P + p] * misc[16 + k];
+            for (int k = 0; k < kIn; ++k) {
+                float a = 0.f;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) a += Hs[(size_t)(s * kIn + k) * P + p];
+                gx[k] = e_scale * a * misc[16 + k];
+            }
             write_pair_outputs<SYSTEM>(dst, gp, geo, gx, E);
         }
-        __syncthreads();
     }
 }
 
 template <int W, int P>
 static size_t f32_smem_bytes(int D) {
-    return sizeof(float) * ((size_t)D * W * P + (size_t)W * P + (size_t)kKC * W +
-                            (size_t)kInPad * P + 32 + (size_t)D * W + W);
+    constexpr int KC = ChunkFeed<W>::KC;
+    constexpr int NG = kF32Threads / (P / 4);
+    return sizeof(float) * ((size_t)D * W * P + (size_t)W * P + (size_t)2 * KC * W +
+                            (size_t)kInPad * P + (size_t)NG * P + 32 + (size_t)D * W + W);
 }
 
 template <int W, int P, bool SYSTEM>
@@ -280,7 +403,7 @@ static rb_status launch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms, c
     net.pl = f32_layout(m->width, m->depth);
     net.W = m->width;
     net.D = m->depth;
-    k_nn_f32<W, P, SYSTEM><<<num_sms, 256, smem, stream>>>(net, src, dst);
+    k_nn_f32<W, P, SYSTEM><<<num_sms, kF32Threads, smem, stream>>>(net, src, dst);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
