@@ -19,10 +19,12 @@
 // Kernel layout: one CTA of 256 threads per SM, persistent over tiles of P
 // pairs.  Layer activations live in shared memory as [unit][pair]; each thread
 // owns a 4-pair x 8-unit register block of every layer GEMM, accumulated with
-// packed FP32x2 FMAs.  The GEMM weights (transposed copies for the forward
-// pass, plain copies for the reverse pass) stream from L2 in 16 KB chunks
-// through a two-buffer cp.async ring: the copy of chunk c+1 runs while chunk c
-// is multiplied, one barrier per chunk.  The forward pass keeps silu'(z_l) of
+// packed FP32x2 FMAs over pairs of units (the pair value is the broadcast
+// operand).  The GEMM weights (transposed copies for the forward
+// pass, plain copies for the reverse pass) stream from L2 in chunks of KC
+// rows (32 KB where shared memory allows, else 16 KB) through a two-buffer
+// cp.async ring: the copy of chunk c+1 runs while chunk c is multiplied, one
+// barrier per chunk.  The forward pass keeps silu'(z_l) of
 // every layer (not z_l) for the reverse pass, which then needs no
 // transcendental and overwrites those values in place with the
 // back-propagated signals.  The energy and dE/dx are reduced over all threads
@@ -39,7 +41,6 @@
 namespace rb {
 
 constexpr int kF32Threads = 256;
-constexpr int kChunkBytes = 16384;  // one weight chunk in shared memory
 
 // Prepared FP32 weights (device), built from the flat parameters:
 //   WT1p [16][W]      W1 transposed, rows 10..15 zero          (forward, layer 1)
@@ -108,10 +109,10 @@ __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0
 // The weight chunks one tile consumes, in order: layer-1 (16 rows), the
 // forward chunks of W_2..W_D, the reverse chunks of W_D..W_2.  A CTA consumes
 // this sequence once per tile; chunk c lives in buffer c % 2.
-template <int W>
+template <int W, int KC>
 struct ChunkFeed {
-    static constexpr int KC = kChunkBytes / (4 * W);  // weight rows per chunk
-    static constexpr int NK = W / KC;                 // chunks per hidden matrix
+    static_assert(KC >= kInPad && W % KC == 0, "chunk rows must divide the width");
+    static constexpr int NK = W / KC;  // chunks per hidden matrix
     const float* prep;
     F32Layout pl;
     int D;
@@ -159,27 +160,29 @@ struct ChunkFeed {
     __device__ void release() { ++c; }
 };
 
-// acc[i/2][j].{x,y} += sum_k A[k][p0 + i] * B[k][o0 + j] for i = 0..3 and
+// acc_at(acc, i, j) += sum_k A[k][p0 + i] * B[k][o0 + j] for i = 0..3 and
 // j = 0..7: A in shared memory as [K][P], B the next K/KC weight chunks.
-template <int W, int P>
-__device__ inline void gemm_tile(const float* __restrict__ As, int K, ChunkFeed<W>& feed, int p0,
-                                 int o0, float2 (&acc)[2][8]) {
-    constexpr int KC = ChunkFeed<W>::KC;
+// Units (j, j+1) of pair i share one FP32x2 accumulator.
+template <int W, int P, int KC>
+__device__ inline void gemm_tile(const float* __restrict__ As, int K, ChunkFeed<W, KC>& feed,
+                                 int p0, int o0, float2 (&acc)[2][8]) {
     for (int kc = 0; kc < K; kc += KC) {
         const float* Bs = feed.acquire();
         const int kn = min(KC, K - kc);
-#pragma unroll 4
+#pragma unroll 16
         for (int k = 0; k < kn; ++k) {
             const float4 a = *reinterpret_cast<const float4*>(As + (size_t)(kc + k) * P + p0);
             const float4 b0 = *reinterpret_cast<const float4*>(Bs + (size_t)k * W + o0);
             const float4 b1 = *reinterpret_cast<const float4*>(Bs + (size_t)k * W + o0 + 4);
-            const float2 a01 = make_float2(a.x, a.y), a23 = make_float2(a.z, a.w);
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float2 b2[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                                  make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float2 bb = make_float2(bv[j], bv[j]);
-                acc[0][j] = __ffma2_rn(a01, bb, acc[0][j]);
-                acc[1][j] = __ffma2_rn(a23, bb, acc[1][j]);
+            for (int i = 0; i < 4; ++i) {
+                const float2 aa = make_float2(av[i], av[i]);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    acc[i >> 1][(i & 1) * 4 + jj] = __ffma2_rn(aa, b2[jj], acc[i >> 1][(i & 1) * 4 + jj]);
             }
         }
         feed.release();
@@ -187,21 +190,22 @@ __device__ inline void gemm_tile(const float* __restrict__ As, int K, ChunkFeed<
 }
 
 __device__ inline float acc_at(const float2 (&acc)[2][8], int i, int j) {
-    return (i & 1) ? acc[i >> 1][j].y : acc[i >> 1][j].x;
+    const float2 v = acc[i >> 1][(i & 1) * 4 + (j >> 1)];
+    return (j & 1) ? v.y : v.x;
 }
 
-template <int W, int P, bool SYSTEM>
+template <int W, int P, int KC, bool SYSTEM>
 __global__ void __launch_bounds__(kF32Threads, 1)
     k_nn_f32(NetArgs net, PairSrc src, PairDst dst) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    constexpr int KC = ChunkFeed<W>::KC;
     constexpr int NTP = P / 4;              // threads along pairs
     constexpr int NG = kF32Threads / NTP;   // thread groups along units
     constexpr int NS = kF32Threads / P;     // unit slices of the dE/dx reduction
     static_assert(NG * 8 == W, "register blocks must tile the layer width");
     static_assert(NS * kIn * P <= W * P, "dE/dx partial sums must fit in the activation buffer");
     const int D = net.D;
+    using Feed = ChunkFeed<W, KC>;
     float* Zs = smem;                          // D x [W][P]: silu'(z_l), then G_l
     float* Hs = Zs + (size_t)D * W * P;        // [W][P]: h_l; dE/dx partial sums at the end
     float* Bs = Hs + (size_t)W * P;            // 2 x [KC][W] weight chunks
@@ -231,11 +235,11 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     const int64_t n_tiles = (n_total + P - 1) / P;
     const int64_t my_tiles =
         n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    ChunkFeed<W> feed;
+    Feed feed;
     feed.prep = net.prep;
     feed.pl = net.pl;
     feed.D = D;
-    feed.n_chunks = 1 + 2 * (D - 1) * ChunkFeed<W>::NK;
+    feed.n_chunks = 1 + 2 * (D - 1) * Feed::NK;
     feed.c = 0;
     feed.total = my_tiles * feed.n_chunks;
     feed.buf = Bs;
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
-            gemm_tile<W, P>(l == 1 ? Xs : Hs, l == 1 ? kInPad : W, feed, p0, o0, acc);
+            gemm_tile<W, P, KC>(l == 1 ? Xs : Hs, l == 1 ? kInPad : W, feed, p0, o0, acc);
             float* Z = Zs + (size_t)(l - 1) * W * P;
             if (l < D) {
                 if (l > 1) __syncthreads();  // every read of Hs by this GEMM is done
@@ -317,15 +321,15 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
-            gemm_tile<W, P>(Zs + (size_t)(l - 1) * W * P, W, feed, p0, o0, acc);
+            gemm_tile<W, P, KC>(Zs + (size_t)(l - 1) * W * P, W, feed, p0, o0, acc);
             float* Z = Zs + (size_t)(l - 2) * W * P;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 float4 g4 = *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0);
-                g4.x *= acc[0][j].x;
-                g4.y *= acc[0][j].y;
-                g4.z *= acc[1][j].x;
-                g4.w *= acc[1][j].y;
+                g4.x *= acc_at(acc, 0, j);
+                g4.y *= acc_at(acc, 1, j);
+                g4.z *= acc_at(acc, 2, j);
+                g4.w *= acc_at(acc, 3, j);
                 *reinterpret_cast<float4*>(Z + (size_t)(o0 + j) * P + p0) = g4;
             }
         }
@@ -377,25 +381,26 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     }
 }
 
-template <int W, int P>
+constexpr size_t kSmemMax = 227 * 1024;
+
+template <int W, int P, int KC>
 static size_t f32_smem_bytes(int D) {
-    constexpr int KC = ChunkFeed<W>::KC;
     constexpr int NG = kF32Threads / (P / 4);
     return sizeof(float) * ((size_t)D * W * P + (size_t)W * P + (size_t)2 * KC * W +
                             (size_t)kInPad * P + (size_t)NG * P + 32 + (size_t)D * W + W);
 }
 
-template <int W, int P, bool SYSTEM>
+template <int W, int P, int KC, bool SYSTEM>
 static rb_status launch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms, const PairSrc& src,
                             const PairDst& dst) {
-    const size_t smem = f32_smem_bytes<W, P>(m->depth);
+    const size_t smem = f32_smem_bytes<W, P, KC>(m->depth);
     static bool attr_set = false;
     if (!attr_set) {
-        RB_CUDA(cudaFuncSetAttribute(k_nn_f32<W, P, SYSTEM>,
+        RB_CUDA(cudaFuncSetAttribute(k_nn_f32<W, P, KC, SYSTEM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr_set = true;
     }
-    if (smem > 227 * 1024) return fail(RB_ENOTSUP, "network too deep for the FP32 kernel");
+    if (smem > kSmemMax) return fail(RB_ENOTSUP, "network too deep for the FP32 kernel");
     NetArgs net;
     net.flat = m->params;
     net.prep = m->f32_prep;
@@ -403,18 +408,28 @@ static rb_status launch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms, c
     net.pl = f32_layout(m->width, m->depth);
     net.W = m->width;
     net.D = m->depth;
-    k_nn_f32<W, P, SYSTEM><<<num_sms, kF32Threads, smem, stream>>>(net, src, dst);
+    k_nn_f32<W, P, KC, SYSTEM><<<num_sms, kF32Threads, smem, stream>>>(net, src, dst);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
+}
+
+// Widest weight chunk (32 KB) whose shared-memory footprint fits the depth,
+// else 16 KB chunks.
+template <int W, int P, int KC_BIG, int KC_SMALL, bool SYSTEM>
+static rb_status launch_f32_fit(const rb_mlp* m, cudaStream_t stream, int num_sms,
+                                const PairSrc& src, const PairDst& dst) {
+    if (f32_smem_bytes<W, P, KC_BIG>(m->depth) <= kSmemMax)
+        return launch_f32<W, P, KC_BIG, SYSTEM>(m, stream, num_sms, src, dst);
+    return launch_f32<W, P, KC_SMALL, SYSTEM>(m, stream, num_sms, src, dst);
 }
 
 template <bool SYSTEM>
 static rb_status dispatch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms,
                               const PairSrc& src, const PairDst& dst) {
     switch (m->width) {
-        case 64: return launch_f32<64, 128, SYSTEM>(m, stream, num_sms, src, dst);
-        case 128: return launch_f32<128, 64, SYSTEM>(m, stream, num_sms, src, dst);
-        case 256: return launch_f32<256, 32, SYSTEM>(m, stream, num_sms, src, dst);
+        case 64: return launch_f32<64, 128, 64, SYSTEM>(m, stream, num_sms, src, dst);
+        case 128: return launch_f32_fit<128, 64, 64, 32, SYSTEM>(m, stream, num_sms, src, dst);
+        case 256: return launch_f32_fit<256, 32, 32, 16, SYSTEM>(m, stream, num_sms, src, dst);
         default: return fail(RB_ENOTSUP, "FP32 network kernel supports widths 64, 128, 256");
     }
 }

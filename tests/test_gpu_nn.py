@@ -78,15 +78,18 @@ def test_nn_pairs_empty_and_depths():
     m.set_params(params(128, 1))
     out = m.pairs(torch.zeros((0, 8), device="cuda"))
     assert out.shape == (0, 12)
-    for depth in (1, 2, 4):
-        flat = params(64, depth, depth)
-        m = api.MLP(64, depth)
+    # depth 4 at widths 128 and 256 takes the kernel's smaller weight chunks
+    for width, depth in ((64, 1), (64, 2), (64, 4), (128, 1), (128, 4), (256, 4)):
+        flat = params(width, depth, depth)
+        m = api.MLP(width, depth)
         m.set_params(flat)
         cfg7 = inputs.pair_configs(300, depth, 5.0, 9.4)
         out = m.pairs(torch.from_numpy(cfg8(cfg7)).cuda()).double().cpu().numpy()
-        E, Fj, ti, tj = oracle_labels(flat, 64, cfg7, depth)
-        assert rel_err(out[:, 0:3], Fj) < TOL_F32
-        assert rel_err(out[:, 8:11], tj) < TOL_F32
+        E, Fj, ti, tj = oracle_labels(flat, width, cfg7, depth)
+        assert rel_err(out[:, 0:3], Fj) < TOL_F32, (width, depth)
+        assert rel_err(out[:, 4:7], ti) < TOL_F32, (width, depth)
+        assert rel_err(out[:, 8:11], tj) < TOL_F32, (width, depth)
+        assert rel_err(out[:, 3], E) < TOL_F32, (width, depth)
 
 
 def test_nn_system_forces_parity_64_cubes():
