@@ -1,20 +1,25 @@
 // Bead-sum kernel: the traditional composite-body interaction (paper, Methods:
-// U = sum_i sum_j u_bead(r_ij) over the beads of two bodies; "all the
-// inter-body distances between the beads" are computed, abstract).
+// U = sum_i sum_j u_bead(r_ij) over the beads of two bodies; the abstract
+// names the evaluation of every bead-bead distance between two bodies as the
+// cost of this form).
 //
 // One warp per body pair.  The computation runs in the frame of body i: its
 // beads are the template d_k itself, body j's beads are b_l = s + R_rel d_l
 // with s = R(q_i)^T R_ij and R_rel = R(q_i^* q_j).  Each lane owns up to 2 NP
 // beads of body j in registers (as NP packed FP32x2 pairs) and loops over all
 // beads k of body i (template broadcast from shared memory), so every one of
-// the n_i x n_j distances is evaluated.  The cutoff decision is taken once per
-// template bead for the whole warp (vote); the Lennard-Jones body is masked.  Per lane it accumulates the force f_l on each owned bead; then
+// the n_i x n_j distances is evaluated.  For templates made of columns of
+// beads with equal (x, y) (the cube and the cylinder) the expanded distance
+// test shares its x-y part along a column; the cutoff decision is taken once
+// per column (or per pair of template beads for other templates) for the
+// whole warp (vote); the Lennard-Jones body is masked.  Per lane it accumulates the force f_l on each owned bead; then
 //   F_j = sum_l f_l,   T = sum_l b_l x f_l,
 //   tau_i = -T (central bead forces: sum_kl d_k x f_kl = sum_kl b_l x f_kl),
 //   tau_j = T - s x F_j,
 // reduced over the warp with xor shuffles (fixed order, deterministic) and
 // rotated back to the space frame with R(q_i).
 #include <algorithm>
+#include <utility>
 
 #include "beads_common.cuh"
 
@@ -25,16 +30,28 @@ namespace rb {
 // path, cut2 = Rc^2, pairs listed only because of the skin); without it they
 // keep what is there (the network path's bead fallback, cut2 = rho_min^2,
 // which counts the pairs it evaluates in *count).
-template <int NP>
-__global__ void __launch_bounds__(256)
+// C = 0: any template (bead_pair_warp); C = 5 or 8: a column-structured
+// template stored column by column (bead_pair_warp_cols), held to three CTAs
+// of 256 threads per SM (at most 85 registers).
+template <int NP, int C>
+__global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
     k_bead_pairs(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
                  const float4* __restrict__ pos, const float4* __restrict__ quat,
-                 const float4* __restrict__ tmpl, int n_beads, float3 L, float3 invL, BeadPot pot,
-                 float cut2, int zero_beyond, float4* __restrict__ out_F,
-                 float4* __restrict__ out_ti, float4* __restrict__ out_tj, int* count) {
+                 const float4* __restrict__ tmpl, int n_beads, BeadCols cols, float3 L,
+                 float3 invL, BeadPot pot, float cut2, int zero_beyond,
+                 float4* __restrict__ out_F, float4* __restrict__ out_ti,
+                 float4* __restrict__ out_tj, int* count) {
     __shared__ float4 sT[kMaxBeads + 1];
-    __shared__ float4 sN[2 * kMaxBeads + 2];
-    load_template(tmpl, n_beads, sT, sN);
+    // generic: 2 float4 per template bead; columns: 1 float4 per column, then
+    // 8 floats per column and 8 more (at most kMaxBeads / 5 columns)
+    constexpr int kSN = C == 0 ? 2 * (kMaxBeads + kPadBeads) : kMaxBeads / 5 + 1 + 2 * (kMaxBeads / 5 + 2);
+    __shared__ float4 sN[kSN];
+    if (C == 0) {
+        load_template(tmpl, n_beads, pot.rc2_test, sT, sN);
+    } else {
+        for (int t = threadIdx.x; t < n_beads; t += blockDim.x) sT[t] = tmpl[t];
+        load_columns(tmpl, cols, pot.rc2_test, sN, reinterpret_cast<float*>(sN + kMaxBeads / 5 + 1));
+    }
     __syncthreads();
     const int n_pairs = *n_pairs_ptr;
     const int lane = threadIdx.x & 31;
@@ -58,7 +75,13 @@ __global__ void __launch_bounds__(256)
         const Mat3 Rr = qmat(qmul(qconj(qi), qj));
         const float3 s = mulT(Ri, R);
         float v[7];
-        bead_pair_warp<NP>(s, Rr, sT, sN, n_beads, pot, lane, v);
+        if constexpr (C == 0) {
+            bead_pair_warp<NP>(s, Rr, sT, sN, n_beads, pot, lane, v);
+        } else {
+            bead_pair_warp_cols<NP, C>(s, Rr, sT, sN,
+                                       reinterpret_cast<const float*>(sN + kMaxBeads / 5 + 1),
+                                       cols, n_beads, pot, lane, v);
+        }
         if (lane < 3) {
             const float3 F = make_float3(v[0], v[1], v[2]);
             const float3 T = make_float3(v[3], v[4], v[5]);
@@ -92,39 +115,85 @@ BeadPot bead_pot(const rb_system* s) {
     return p;
 }
 
-template <int NP>
+template <int NP, int C>
 static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, int* count) {
     static int occ = 0;
     if (occ == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP, C>, 256, 0);
         if (occ <= 0) occ = 1;
     }
     const float3 L = make_float3(s->box[0], s->box[1], s->box[2]);
     const float3 invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
     const int grid = s->num_sms * occ;
-    k_bead_pairs<NP><<<grid, 256, 0, s->stream>>>(
-        s->pl.pairs, s->pl.n_pairs, s->pos, s->quat, s->tmpl_dev, s->n_beads, L, invL,
+    k_bead_pairs<NP, C><<<grid, 256, 0, s->stream>>>(
+        s->pl.pairs, s->pl.n_pairs, s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL,
         bead_pot(s), cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, count);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
+}
+
+template <int NP>
+static rb_status launch_beads_np(rb_system* s, float cut2, int zero_beyond, int* count) {
+    if (s->cols.len == 5) return launch_beads<NP, 5>(s, cut2, zero_beyond, count);
+    if (s->cols.len == 8) return launch_beads<NP, 8>(s, cut2, zero_beyond, count);
+    return launch_beads<NP, 0>(s, cut2, zero_beyond, count);
+}
+
+static rb_status launch_beads_any(rb_system* s, float cut2, int zero_beyond, int* count) {
+    const int np = (s->n_beads + 63) / 64;
+    if (np <= 2) return launch_beads_np<2>(s, cut2, zero_beyond, count);
+    if (np <= 3) return launch_beads_np<3>(s, cut2, zero_beyond, count);
+    return launch_beads_np<4>(s, cut2, zero_beyond, count);
 }
 
 rb_status bead_fallback_async(rb_system* s) {
     RB_CUDA(cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream));
     if (!(s->nn_fallback_rho > 0.f)) return RB_OK;
     const float r = std::min(s->nn_fallback_rho, s->Rc);
-    const int np = (s->n_beads + 63) / 64;
-    if (np <= 2) return launch_beads<2>(s, r * r, 0, s->fallback_count);
-    if (np <= 3) return launch_beads<3>(s, r * r, 0, s->fallback_count);
-    return launch_beads<4>(s, r * r, 0, s->fallback_count);
+    return launch_beads_any(s, r * r, 0, s->fallback_count);
 }
 
-rb_status bead_pairs_async(rb_system* s) {
-    const float c2 = s->Rc * s->Rc;
-    const int np = (s->n_beads + 63) / 64;
-    if (np <= 2) return launch_beads<2>(s, c2, 1, nullptr);
-    if (np <= 3) return launch_beads<3>(s, c2, 1, nullptr);
-    return launch_beads<4>(s, c2, 1, nullptr);
+rb_status bead_pairs_async(rb_system* s) { return launch_beads_any(s, s->Rc * s->Rc, 1, nullptr); }
+
+void bead_columns(float4* t, int n, BeadCols* c) {
+    *c = BeadCols();
+    if (n < 1 || n > kMaxBeads) return;
+    // group by exact (x, y), in order of first appearance (fixed-size arrays:
+    // no allocation, so the allocation-free entry point can call this)
+    float gx[kMaxBeads], gy[kMaxBeads];
+    int gid[kMaxBeads], gsize[kMaxBeads];
+    int ng = 0;
+    for (int k = 0; k < n; ++k) {
+        int g = 0;
+        while (g < ng && !(gx[g] == t[k].x && gy[g] == t[k].y)) ++g;
+        if (g == ng) {
+            gx[ng] = t[k].x;
+            gy[ng] = t[k].y;
+            gsize[ng++] = 0;
+        }
+        gid[k] = g;
+        ++gsize[g];
+    }
+    const int len = gsize[0];
+    if ((len != 5 && len != 8) || ng * len != n || ng > kMaxBeads / 5) return;
+    float4 out[kMaxBeads];
+    for (int g = 0; g < ng; ++g) {
+        if (gsize[g] != len) return;
+        float4* col = out + g * len;
+        int m = 0;
+        for (int k = 0; k < n; ++k)
+            if (gid[k] == g) col[m++] = t[k];
+        for (int i = 1; i < len; ++i)  // z ascending
+            for (int j = i; j > 0 && col[j].z < col[j - 1].z; --j) std::swap(col[j], col[j - 1]);
+        for (int i = 0; i < len; ++i) {
+            if (col[i].z != out[i].z) return;            // same z values in every column
+            if (i > 0 && col[i].z == col[i - 1].z) return;
+        }
+    }
+    c->n_cols = ng;
+    c->len = len;
+    for (int m = 0; m < len; ++m) c->z[m] = out[m].z;
+    for (int k = 0; k < n; ++k) t[k] = out[k];
 }
 
 }  // namespace rb

@@ -12,6 +12,8 @@
 
 namespace rb {
 
+constexpr int kPadBeads = 3;  // far-away template entries after the last bead
+
 struct BeadPot {
     float rc2, sig2, eps4, eps24, u_shift;
     float rc2_test;  // rc2 + a bound on the rounding of the expanded distance test
@@ -20,46 +22,45 @@ struct BeadPot {
 BeadPot bead_pot(const rb_system* s);
 
 // Per-CTA shared template: sT[k] = (x, y, z, 0); sN[2k], sN[2k+1] =
-// (-2x, -2x, -2y, -2y), (-2z, -2z, |d|^2, |d|^2): duplicated for packed FP32x2
-// arithmetic (0.5 * (-2x) = -x exactly).
-// An odd template gets one padding entry far away (never within any cutoff),
-// so the distance loop can take two template beads per iteration.
-__device__ inline void load_template(const float4* __restrict__ tmpl, int n_beads, float4* sT,
-                                     float4* sN) {
-    for (int t = threadIdx.x; t < n_beads + 1; t += blockDim.x) {
+// (-2x, -2x, -2y, -2y), (-2z, -2z, thr - |d|^2, thr - |d|^2): duplicated for
+// packed FP32x2 arithmetic (0.5 * (-2x) = -x exactly); thr is the distance
+// test's threshold: |b|^2 - 2 b.d < thr - |d|^2 flags a possible hit.
+// The template is padded with kPadBeads entries far away (never within any
+// cutoff), so the distance loop can take up to kPadBeads + 1 template beads
+// per iteration.
+__device__ inline void load_template(const float4* __restrict__ tmpl, int n_beads, float thr,
+                                     float4* sT, float4* sN) {
+    for (int t = threadIdx.x; t < n_beads + kPadBeads; t += blockDim.x) {
         if (t < n_beads) {
             const float4 d = tmpl[t];
             sT[t] = d;
-            const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float dd = thr - (d.x * d.x + d.y * d.y + d.z * d.z);
             sN[2 * t] = make_float4(-2.f * d.x, -2.f * d.x, -2.f * d.y, -2.f * d.y);
             sN[2 * t + 1] = make_float4(-2.f * d.z, -2.f * d.z, dd, dd);
         } else {  // padding bead at 1e18 sigma
             sN[2 * t] = make_float4(-2e18f, -2e18f, 0.f, 0.f);
-            sN[2 * t + 1] = make_float4(0.f, 0.f, 1e36f, 1e36f);
+            sN[2 * t + 1] = make_float4(0.f, 0.f, -1e36f, -1e36f);
         }
     }
 }
 
-// Whole-warp bead double sum of one body pair in the frame of body i.
-// NP = packed slot pairs per lane: the lane owns beads l = lane + 32 m,
-// m = 0 .. 2 NP - 1, of body j.  Returns, reduced over the warp (every lane):
-// v[0..2] = F_j, v[3..5] = T = sum_l b_l x f_l, v[6] = E.  Every bead-pair
-// distance is tested (expanded form, with a rounding margin); one warp vote
-// per template bead decides whether any slot may be inside r_c, and then the
-// exact separations, the strict cutoff and the masked Lennard-Jones body run.
+// Three-input minimum (one instruction on sm_100 and later).
+__device__ inline float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Body j's beads owned by this lane, b_l = s + R_rel d_l for l = lane + 32 m
+// (m < 2 NP), as scalars and as packed pairs, with |b_l|^2; unused slots sit
+// far away (never within any cutoff).
 template <int NP>
-__device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const float4* sT,
-                                      const float4* sN, int n_beads, const BeadPot& pot,
-                                      int lane, float (&v)[7]) {
-    constexpr int MB = 2 * NP;
-    const float2 sig2v = make_float2(pot.sig2, pot.sig2);
-    const float2 e48 = make_float2(2.f * pot.eps24, 2.f * pot.eps24);
-    const float2 me24 = make_float2(-pot.eps24, -pot.eps24);
-    const float2 m1 = make_float2(-1.f, -1.f);
-    const float rc2 = pot.rc2;
-    float bx[MB], by[MB], bz[MB];
+__device__ inline void slots_setup(const float3 s, const Mat3& Rr, const float4* sT, int n_beads,
+                                   int lane, float (&bx)[2 * NP], float (&by)[2 * NP],
+                                   float (&bz)[2 * NP], float2 (&Bx)[NP], float2 (&By)[NP],
+                                   float2 (&Bz)[NP], float2 (&BB)[NP]) {
 #pragma unroll
-    for (int m = 0; m < MB; ++m) {
+    for (int m = 0; m < 2 * NP; ++m) {
         const int l = lane + 32 * m;
         if (l < n_beads) {
             const float4 d = sT[l];
@@ -68,84 +69,78 @@ __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const floa
             by[m] = s.y + b.y;
             bz[m] = s.z + b.z;
         } else {
-            bx[m] = by[m] = bz[m] = 1e18f;  // never within the cutoff
+            bx[m] = by[m] = bz[m] = 1e18f;
         }
     }
-    float2 Bx[NP], By[NP], Bz[NP], Fx[NP], Fy[NP], Fz[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         Bx[q] = make_float2(bx[2 * q], bx[2 * q + 1]);
         By[q] = make_float2(by[2 * q], by[2 * q + 1]);
         Bz[q] = make_float2(bz[2 * q], bz[2 * q + 1]);
-        Fx[q] = Fy[q] = Fz[q] = make_float2(0.f, 0.f);
-    }
-    // |b_l|^2 per slot for the expanded distance test
-    float2 BB[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q)
         BB[q] = __ffma2_rn(Bz[q], Bz[q], __ffma2_rn(By[q], By[q], __fmul2_rn(Bx[q], Bx[q])));
-    const float2 half2 = make_float2(0.5f, 0.5f);
-    float2 acc = make_float2(0.f, 0.f);  // sum of (s^12 - s^6) over inside pairs
-    float2 cnt = make_float2(0.f, 0.f);  // number of inside pairs
-    // two template beads per iteration: independent test chains, one vote
-    for (int k = 0; k < n_beads; k += 2) {
-        float2 md[2][3], dd[2];
-        float mn = 3.0e38f;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float4 n0 = sN[2 * (k + u)], n1 = sN[2 * (k + u) + 1];
-            md[u][0] = make_float2(n0.x, n0.y);
-            md[u][1] = make_float2(n0.z, n0.w);
-            md[u][2] = make_float2(n1.x, n1.y);
-            dd[u] = make_float2(n1.z, n1.w);
-        }
-        // test: r^2 ~ |b|^2 + |d|^2 - 2 b.d (4 packed ops per 2 slots); the
-        // rounding bound is folded into rc2_test, so no pair inside r_c is missed
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                float2 t = __fadd2_rn(BB[q], dd[u]);
-                t = __ffma2_rn(Bx[q], md[u][0], t);
-                t = __ffma2_rn(By[q], md[u][1], t);
-                t = __ffma2_rn(Bz[q], md[u][2], t);
-                mn = fminf(mn, fminf(t.x, t.y));
-            }
-        if (__any_sync(0xffffffffu, mn < pot.rc2_test)) {
-            // exact separations, the strict cutoff r^2 < r_c^2 and the masked
-            // Lennard-Jones body for every slot
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    const float2 rx = __ffma2_rn(half2, md[u][0], Bx[q]);
-                    const float2 ry = __ffma2_rn(half2, md[u][1], By[q]);
-                    const float2 rz = __ffma2_rn(half2, md[u][2], Bz[q]);
-                    float2 r2 = __fmul2_rn(rx, rx);
-                    r2 = __ffma2_rn(ry, ry, r2);
-                    r2 = __ffma2_rn(rz, rz, r2);
-                    const bool inx = r2.x < rc2, iny = r2.y < rc2;
-                    const float2 inv2 = make_float2(inx ? __fdividef(1.f, r2.x) : 0.f,
-                                                    iny ? __fdividef(1.f, r2.y) : 0.f);
-                    const float2 s2 = __fmul2_rn(sig2v, inv2);
-                    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
-                    const float2 s12 = __fmul2_rn(s6, s6);
-                    acc = __fadd2_rn(acc, __ffma2_rn(s6, m1, s12));
-                    cnt = __fadd2_rn(cnt, make_float2(inx ? 1.f : 0.f, iny ? 1.f : 0.f));
-                    const float2 fr =
-                        __fmul2_rn(inv2, __ffma2_rn(s12, e48, __fmul2_rn(s6, me24)));
-                    Fx[q] = __ffma2_rn(fr, rx, Fx[q]);
-                    Fy[q] = __ffma2_rn(fr, ry, Fy[q]);
-                    Fz[q] = __ffma2_rn(fr, rz, Fz[q]);
-                }
-        }
     }
+}
+
+// Lennard-Jones accumulators of one lane: force on each owned bead (packed),
+// sum of (s^12 - s^6) and number of pairs inside r_c.
+template <int NP>
+struct LJAcc {
+    float2 Fx[NP], Fy[NP], Fz[NP];
+    float2 acc, cnt;
+    __device__ void zero() {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) Fx[q] = Fy[q] = Fz[q] = make_float2(0.f, 0.f);
+        acc = cnt = make_float2(0.f, 0.f);
+    }
+};
+
+// One template bead d (given as md = -2 d, duplicated) against every owned
+// slot: exact separations r = b - d, the strict cutoff r^2 < r_c^2 and the
+// masked Lennard-Jones body.
+template <int NP>
+__device__ inline void lj_bead(const float2 md0, const float2 md1, const float2 md2,
+                               const float2 (&Bx)[NP], const float2 (&By)[NP],
+                               const float2 (&Bz)[NP], const BeadPot& pot, LJAcc<NP>& a) {
+    const float2 half2 = make_float2(0.5f, 0.5f);
+    const float2 sig2v = make_float2(pot.sig2, pot.sig2);
+    const float2 e48 = make_float2(2.f * pot.eps24, 2.f * pot.eps24);
+    const float2 me24 = make_float2(-pot.eps24, -pot.eps24);
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const float2 rx = __ffma2_rn(half2, md0, Bx[q]);
+        const float2 ry = __ffma2_rn(half2, md1, By[q]);
+        const float2 rz = __ffma2_rn(half2, md2, Bz[q]);
+        float2 r2 = __fmul2_rn(rx, rx);
+        r2 = __ffma2_rn(ry, ry, r2);
+        r2 = __ffma2_rn(rz, rz, r2);
+        const bool inx = r2.x < pot.rc2, iny = r2.y < pot.rc2;
+        const float2 inv2 = make_float2(inx ? __fdividef(1.f, r2.x) : 0.f,
+                                        iny ? __fdividef(1.f, r2.y) : 0.f);
+        const float2 s2 = __fmul2_rn(sig2v, inv2);
+        const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+        const float2 s12 = __fmul2_rn(s6, s6);
+        a.acc = __fadd2_rn(a.acc, __ffma2_rn(s6, m1, s12));
+        a.cnt = __fadd2_rn(a.cnt, make_float2(inx ? 1.f : 0.f, iny ? 1.f : 0.f));
+        const float2 fr = __fmul2_rn(inv2, __ffma2_rn(s12, e48, __fmul2_rn(s6, me24)));
+        a.Fx[q] = __ffma2_rn(fr, rx, a.Fx[q]);
+        a.Fy[q] = __ffma2_rn(fr, ry, a.Fy[q]);
+        a.Fz[q] = __ffma2_rn(fr, rz, a.Fz[q]);
+    }
+}
+
+// v[0..2] = F_j, v[3..5] = T = sum_l b_l x f_l, v[6] = E, reduced over the
+// warp with xor shuffles (every lane gets the sums).
+template <int NP>
+__device__ inline void warp_finish(const float (&bx)[2 * NP], const float (&by)[2 * NP],
+                                   const float (&bz)[2 * NP], const LJAcc<NP>& a,
+                                   const BeadPot& pot, float (&v)[7]) {
 #pragma unroll
     for (int k = 0; k < 7; ++k) v[k] = 0.f;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        const float fx[2] = {Fx[q].x, Fx[q].y}, fy[2] = {Fy[q].x, Fy[q].y},
-                    fz[2] = {Fz[q].x, Fz[q].y};
+        const float fx[2] = {a.Fx[q].x, a.Fx[q].y}, fy[2] = {a.Fy[q].x, a.Fy[q].y},
+                    fz[2] = {a.Fz[q].x, a.Fz[q].y};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * q + h;
@@ -157,11 +152,130 @@ __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const floa
             v[5] += bx[m] * fy[h] - by[m] * fx[h];
         }
     }
-    v[6] = pot.eps4 * (acc.x + acc.y) - pot.u_shift * (cnt.x + cnt.y);
+    v[6] = pot.eps4 * (a.acc.x + a.acc.y) - pot.u_shift * (a.cnt.x + a.cnt.y);
 #pragma unroll
     for (int k = 0; k < 7; ++k)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+// Whole-warp bead double sum of one body pair in the frame of body i, any
+// template.  NP = packed slot pairs per lane: the lane owns beads
+// l = lane + 32 m, m = 0 .. 2 NP - 1, of body j.  Every bead-pair distance is
+// tested (expanded form, with a rounding margin); one warp vote per U
+// template beads decides whether any slot may be inside r_c, and then the
+// exact separations, the strict cutoff and the masked Lennard-Jones body run
+// for those U beads.  Result as in warp_finish.
+template <int NP, int U = 2>
+__device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const float4* sT,
+                                      const float4* sN, int n_beads, const BeadPot& pot,
+                                      int lane, float (&v)[7]) {
+    float bx[2 * NP], by[2 * NP], bz[2 * NP];
+    float2 Bx[NP], By[NP], Bz[NP], BB[NP];
+    slots_setup<NP>(s, Rr, sT, n_beads, lane, bx, by, bz, Bx, By, Bz, BB);
+    LJAcc<NP> a;
+    a.zero();
+    static_assert(U >= 1 && U <= kPadBeads + 1, "template padding");
+    for (int k = 0; k < n_beads; k += U) {
+        float2 md[U][3];
+        float th[U], mn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float4 n0 = sN[2 * (k + u)], n1 = sN[2 * (k + u) + 1];
+            md[u][0] = make_float2(n0.x, n0.y);
+            md[u][1] = make_float2(n0.z, n0.w);
+            md[u][2] = make_float2(n1.x, n1.y);
+            th[u] = n1.z;
+            mn[u] = 3.0e38f;
+        }
+        // test: |b|^2 - 2 b.d < thr - |d|^2, i.e. r^2 < thr in expanded form
+        // (3 packed FMAs per 2 slots, one three-input min per 2 slots, one
+        // compare per template bead); the rounding bound is folded into thr,
+        // so no pair inside r_c is missed
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float2 t = __ffma2_rn(Bx[q], md[u][0], BB[q]);
+                t = __ffma2_rn(By[q], md[u][1], t);
+                t = __ffma2_rn(Bz[q], md[u][2], t);
+                mn[u] = fmin3(mn[u], t.x, t.y);
+            }
+        bool hit = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) hit |= mn[u] < th[u];
+        if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) lj_bead<NP>(md[u][0], md[u][1], md[u][2], Bx, By, Bz, pot, a);
+        }
+    }
+    warp_finish<NP>(bx, by, bz, a, pot, v);
+}
+
+// Shared-memory form of a column-structured template (see BeadCols): per
+// column c, sC[c] = (-2x, -2x, -2y, -2y) and sTh[8c + m] = thr - |d|^2 for its
+// m-th bead (z = cols.z[m]); thr as in load_template; after the last column,
+// sTh[8 n_cols + m] = -2 z_m.
+__device__ inline void load_columns(const float4* __restrict__ tmpl, const BeadCols& cols,
+                                    float thr, float4* sC, float* sTh) {
+    for (int t = threadIdx.x; t < cols.n_cols * cols.len; t += blockDim.x) {
+        const int c = t / cols.len, m = t % cols.len;
+        const float4 d = tmpl[t];
+        if (m == 0) sC[c] = make_float4(-2.f * d.x, -2.f * d.x, -2.f * d.y, -2.f * d.y);
+        sTh[8 * c + m] = thr - (d.x * d.x + d.y * d.y + d.z * d.z);
+    }
+    for (int m = threadIdx.x; m < cols.len; m += blockDim.x) sTh[8 * cols.n_cols + m] = -2.f * cols.z[m];
+}
+
+// Whole-warp bead double sum for a column-structured template of columns of
+// C beads.  The same distances and the same test as bead_pair_warp, with the
+// column's share of the expanded form computed once per slot pair:
+//   P = |b|^2 - 2 (b_x x + b_y y),   |b|^2 - 2 b.d = P - 2 b_z z_m,
+// i.e. (2 + C) packed FMAs per C distances of a slot pair instead of 3 C.
+// One warp vote per column; result as in warp_finish.
+template <int NP, int C>
+__device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const float4* sT,
+                                           const float4* sC, const float* sTh,
+                                           const BeadCols& cols, int n_beads, const BeadPot& pot,
+                                           int lane, float (&v)[7]) {
+    float bx[2 * NP], by[2 * NP], bz[2 * NP];
+    float2 Bx[NP], By[NP], Bz[NP], BB[NP];
+    slots_setup<NP>(s, Rr, sT, n_beads, lane, bx, by, bz, Bx, By, Bz, BB);
+    LJAcc<NP> a;
+    a.zero();
+    float2 mz[C];  // -2 z_m, duplicated
+#pragma unroll
+    for (int m = 0; m < C; ++m) mz[m] = make_float2(-2.f * cols.z[m], -2.f * cols.z[m]);
+    for (int c = 0; c < cols.n_cols; ++c) {
+        const float4 cxy = sC[c];
+        const float2 mx = make_float2(cxy.x, cxy.y), my = make_float2(cxy.z, cxy.w);
+        float th[C], mn[C];
+#pragma unroll
+        for (int m = 0; m < C; ++m) {
+            th[m] = sTh[8 * c + m];
+            mn[m] = 3.0e38f;
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float2 P = __ffma2_rn(By[q], my, __ffma2_rn(Bx[q], mx, BB[q]));
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                const float2 t = __ffma2_rn(Bz[q], mz[m], P);
+                mn[m] = fmin3(mn[m], t.x, t.y);
+            }
+        }
+        bool hit = false;
+#pragma unroll
+        for (int m = 0; m < C; ++m) hit |= mn[m] < th[m];
+        if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll 1
+            for (int m = 0; m < C; ++m) {
+                const float z2 = sTh[8 * cols.n_cols + m];  // -2 z_m
+                lj_bead<NP>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
+            }
+        }
+    }
+    warp_finish<NP>(bx, by, bz, a, pot, v);
 }
 
 // Smallest squared bead-bead distance between the two bodies (warp min).

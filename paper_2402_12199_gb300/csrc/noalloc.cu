@@ -125,6 +125,8 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
 
     float4 tmpl[kMaxBeads];
     const int nb = noalloc_template(shape, tmpl);
+    BeadCols cols;
+    bead_columns(tmpl, nb, &cols);
     double rmax = 0.0;
     for (int k = 0; k < nb; ++k)
         rmax = std::fmax(rmax, std::sqrt((double)tmpl[k].x * tmpl[k].x +
@@ -145,6 +147,7 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     }
     s.Rc = (float)(2.0 * rmax + rcut);
     s.N = n_bodies;
+    s.cols = cols;
     int n_cells = 1;
     for (int a = 0; a < 3; ++a) {
         s.box[a] = box_host[a];

@@ -38,6 +38,20 @@ enum : unsigned {
 
 constexpr int kMaxBeads = 256;
 
+// Column structure of a bead template: the beads fall into n_cols groups of
+// len beads with equal (x, y), and every group holds the same z values z[0..len)
+// (cube 5x5x5: 25 columns of 5; cylinder: 19 hexagonal sites x 8 layers).
+// The device template is then stored column by column, z ascending.
+constexpr int kMaxColLen = 8;
+struct BeadCols {
+    int n_cols = 0, len = 0;  // len == 0: no usable column structure
+    float z[kMaxColLen] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+// Detects the structure for column lengths the bead kernel is built for
+// (5 and 8) and, if found, reorders t[0..n) column by column; c->len = 0
+// otherwise (t unchanged).  Allocates nothing.
+void bead_columns(float4* t, int n, BeadCols* c);
+
 // ------------------------------------------------------------- device math
 __host__ __device__ inline float4 qmul(float4 a, float4 b) {
     // Hamilton product, (w, x, y, z) stored as (x=w, y=x, z=y, w=z) of float4
@@ -143,8 +157,9 @@ struct rb_system {
     // body type
     int n_beads = 0;
     float bead_mass = 1.f, mass = 0.f, inertia[3] = {0, 0, 0}, r_circ = 0.f, Rc = 0.f;
-    std::vector<float> tmpl;  // n_beads x 3
+    std::vector<float> tmpl;  // n_beads x 3 (same order as tmpl_dev)
     float4* tmpl_dev = nullptr;
+    rb::BeadCols cols;        // column structure of the template (len 0: none)
     // potential
     float eps = 1.f, sigma = 1.f, rcut = 2.5f, u_shift = 0.f;
     float box[3] = {0, 0, 0};

@@ -736,6 +736,12 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     }
     std::vector<float4> t4(s->n_beads);
     for (int k = 0; k < s->n_beads; ++k) t4[k] = make_float4(t[3 * k], t[3 * k + 1], t[3 * k + 2], 0.f);
+    bead_columns(t4.data(), s->n_beads, &s->cols);  // column by column where the template allows
+    for (int k = 0; k < s->n_beads; ++k) {
+        s->tmpl[3 * k] = t4[k].x;
+        s->tmpl[3 * k + 1] = t4[k].y;
+        s->tmpl[3 * k + 2] = t4[k].z;
+    }
     e = cudaMemcpyAsync(s->tmpl_dev, t4.data(), sizeof(float4) * s->n_beads,
                         cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(256)
                    int n_beads, float Rc, float sigma, BeadPot pot, int n_bisect,
                    float4* __restrict__ cfg, float4* __restrict__ lab, float* __restrict__ rho_c) {
     __shared__ float4 sT[kMaxBeads + 1];
-    __shared__ float4 sN[2 * kMaxBeads + 2];
-    load_template(tmpl, n_beads, sT, sN);
+    __shared__ float4 sN[2 * (kMaxBeads + kPadBeads)];
+    load_template(tmpl, n_beads, pot.rc2_test, sT, sN);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
