@@ -89,6 +89,28 @@ def test_bead_forces_parity_cylinders():
     _parity(st, L, tmpl, "cylinder")
 
 
+def test_bead_forces_parity_custom_template():
+    """A 3 x 4 x 6 box of beads: its (x, y) columns hold 6 beads, so the pair
+    kernel takes its any-template path (the cube and cylinder take the
+    column-shared test)."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    g = np.stack(np.meshgrid(np.arange(3) - 1.0, np.arange(4) - 1.5, np.arange(6) - 2.5,
+                             indexing="ij"), -1).reshape(-1, 3)
+    st, L, _ = make_state(300, 0.20, 31)
+    s = api.System(300, [L] * 3, "custom", template=g)
+    s.set_state(*(torch.from_numpy(np.ascontiguousarray(st[k])).cuda()
+                  for k in ("pos", "quat", "vel", "angmom")))
+    res = s.forces_beads(energy=True)
+    s.sync()
+    F, T, E, _, pairs = oracle_beads(st, L, g)
+    assert len(pairs) > 50
+    assert rel_err(res["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
+    assert rel_err(res["torque"][:, :3].double().cpu().numpy(), T) < TOL_F32
+
+
 def test_bead_forces_sampled_32768_cubes():
     """Full bench size (32768 cubes, phi = 0.20): every pair of 40 sampled
     bodies recomputed by the oracle; forces/torques on those bodies compared."""
