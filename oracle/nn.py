@@ -41,8 +41,10 @@ def n_params(width: int, depth: int = 3, n_in: int = N_IN) -> int:
     return 2 * n_in + width * n_in + width + (depth - 1) * (width * width + width) + width + 3
 
 
-def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN) -> dict:
-    """Split the flat parameter vector into named FP64 tensors (views)."""
+def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None) -> dict:
+    """Split the flat parameter vector into named FP64 tensors (views).
+    sym: optional point group (symmetry.point_group) -- the network then sees
+    every pair configuration in its canonical form (symmetry.py)."""
     t = flat if isinstance(flat, torch.Tensor) else torch.as_tensor(np.asarray(flat))
     t = t.to(DT)
     assert t.numel() == n_params(width, depth, n_in), (t.numel(), n_params(width, depth, n_in))
@@ -66,6 +68,7 @@ def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN) -> dict:
     p["e_scale"] = take(1)[0]
     p["e_shift"] = take(1)[0]
     assert o == t.numel()
+    p["sym"] = sym
     return p
 
 
@@ -121,7 +124,12 @@ def mlp_energy(p: dict, x):
 
 
 def config_energy(p: dict, s, q_rel):
-    """Pair energy from the pair configuration in the frame of body i."""
+    """Pair energy from the pair configuration in the frame of body i (in its
+    canonical form under the point group when the network has one)."""
+    if p.get("sym") is not None:
+        from . import symmetry
+
+        s, q_rel = symmetry.canonical_torch(s, q_rel, p["sym"])
     return mlp_energy(p, features(s, q_rel))
 
 
@@ -192,7 +200,7 @@ def predict_labels(p: dict, s, q_rel, create_graph: bool = False):
 
 
 def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_scale=None,
-                        kT_w=None):
+                        kT_w=None, sym=None):
     """L = mean_b w_b ( |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
     + lam_E (E - E*)^2 ) with w_b = min(1, exp(-E*/kT_w)) / (1 + (|F_j*|^2 +
     lam_tau (|tau_i*|^2 + |tau_j*|^2)) / f_scale^2); each factor is 1 when its
@@ -210,7 +218,7 @@ def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_
     pinned by central differences in the tests.
     """
     flat_t = torch.as_tensor(np.asarray(flat, dtype=np.float64)).clone().requires_grad_(True)
-    p = unpack(flat_t, width, depth)
+    p = unpack(flat_t, width, depth, sym=sym)
     cfg = torch.as_tensor(np.asarray(pair_cfg, dtype=np.float64))
     lab = torch.as_tensor(np.asarray(labels, dtype=np.float64))
     E, Fj, ti, tj = predict_labels(p, cfg[:, :3], cfg[:, 3:7], create_graph=True)
