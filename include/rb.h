@@ -221,6 +221,47 @@ rb_status rb_mlp_destroy(rb_mlp* mlp);
 rb_status rb_mlp_set_params(rb_mlp* mlp, const float* flat, int64_t n, int32_t from_host);
 rb_status rb_mlp_get_params(const rb_mlp* mlp, float* flat, int64_t n, int32_t to_host);
 
+/* --- symmetry-reduced pair configurations (paper, SI Sec. 1: a cube pair is
+ * expressed in the one of cube 1's equivalent face frames that puts cube 2's
+ * centre in a fixed octant, reflected across y = z where needed, and cube 2's
+ * orientation is taken relative to its face closest to cube 1; configurations
+ * related by a symmetry of either body share one description).
+ *
+ * Point group of a bead template (host only, needs no GPU): the proper
+ * rotations, among the octahedral group's 24 and the hexagonal prism's 12
+ * (symmetry axes along x, y, z), that map the beads onto themselves
+ * (tolerance 1e-4 sigma), and whether d -> -d does.  xyz: host n x 3.
+ * quats_out: host, room for 24 x 4 floats, unit quaternions (s, i, j, k) with
+ * the first non-zero component positive, in decreasing lexicographic order
+ * of (s, i, j, k) rounded to 1e-9; *n_out their number (>= 1: the identity);
+ * *inversion_out 1 or 0.  RB_EINVAL for null pointers or n < 1. */
+rb_status rb_template_symmetry(const float* xyz, int32_t n, float* quats_out, int32_t* n_out,
+                               int32_t* inversion_out);
+
+/* Attach a point group to a network (n = 0 detaches it; quats: host n x 4 as
+ * rb_template_symmetry writes them, n <= 24).  With a group attached, every
+ * evaluation of the network (rb_forces_nn, rb_step on the network path,
+ * rb_nn_pairs, rb_train_grad, rb_train_step, rb_nn_weight_vjp) first maps
+ * each pair configuration (s, q_rel) in the frame of body i to its canonical
+ * representative
+ *   k = argmax_k sigma (R(Q_k) s) . u,  u = (3, 2, 1) / sqrt(14)
+ *       (sigma = sign of the product when the inversion is in the group, else
+ *        1; the first maximum in group order wins),
+ *   j = argmax_j |scalar part of (Q_k q_rel Q_j)|,
+ *   (s', q') = (sigma R(Q_k) s, Q_k q_rel Q_j),
+ * evaluates the network there, and maps forces and torques back
+ * (F_j = sigma R(Q_k)^T F_j', tau = R(Q_k)^T tau').  The group must be one the
+ * bodies have: the energy is then invariant under it.  Training labels and
+ * the direction u_cfg of rb_nn_weight_vjp are given for the configurations as
+ * passed (they are mapped with them). */
+rb_status rb_mlp_set_symmetry(rb_mlp* mlp, const float* quats_host, int32_t n, int32_t inversion);
+
+/* The canonical representatives themselves (device arrays, in place): cfg
+ * n x 8 as rb_nn_pairs' input; labels n x 12 as its output (nullable), mapped
+ * as the forces and torques.  Runs on the network's stream; a network without
+ * a group leaves the arrays unchanged. */
+rb_status rb_nn_canonical(const rb_mlp* mlp, int64_t n, float* cfg, float* labels);
+
 /* Network forces and torques for the whole system (same outputs and pair
  * list as rb_forces_beads).  Each unordered pair i < j is evaluated once with
  * i as the reference body.  RB_FP32: SIMT FP32 arithmetic (widths 64, 128,

@@ -249,6 +249,23 @@ class MLP:
         check(load().rb_mlp_get_params(self._h, a.ctypes.data, a.size, 1))
         return a
 
+    def set_symmetry(self, quats, inversion: bool):
+        """rb_mlp_set_symmetry: evaluate on canonical configurations under this
+        point group ((n, 4) unit quaternions as template_symmetry returns them;
+        n = 0 detaches)."""
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        check(load().rb_mlp_set_symmetry(self._h, q.ctypes.data if len(q) else None, len(q),
+                                         int(bool(inversion))))
+
+    def canonical(self, cfg: torch.Tensor, labels: torch.Tensor = None):
+        """rb_nn_canonical in place on (n, 8) configurations [and (n, 12) labels]."""
+        _dev(cfg, 8)
+        if labels is not None:
+            _dev(labels, 12)
+        check(load().rb_nn_canonical(self._h, cfg.shape[0], cfg.data_ptr(),
+                                     labels.data_ptr() if labels is not None else None))
+        check(load().rb_mlp_sync(self._h))
+
     def pairs(self, cfg: torch.Tensor, precision="fp32", grad: bool = False):
         """rb_nn_pairs on (n, 8) configurations; returns (n, 12) [and (n, 8)]."""
         n = cfg.shape[0]
@@ -259,6 +276,17 @@ class MLP:
                                  out.data_ptr(), g.data_ptr() if grad else None))
         check(load().rb_mlp_sync(self._h))
         return (out, g) if grad else out
+
+
+def template_symmetry(xyz):
+    """rb_template_symmetry: (quats (n, 4) float32, inversion bool) of the point
+    group of a bead template (n_beads, 3); host only."""
+    t = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+    q = np.zeros((24, 4), dtype=np.float32)
+    n, inv = ctypes.c_int32(), ctypes.c_int32()
+    check(load().rb_template_symmetry(t.ctypes.data, len(t), q.ctypes.data, ctypes.byref(n),
+                                      ctypes.byref(inv)))
+    return q[:n.value].copy(), bool(inv.value)
 
 
 def tc_gemm_check(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:

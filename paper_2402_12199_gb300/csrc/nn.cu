@@ -445,6 +445,7 @@ static int sm_count();
 rb_status nn_pairs_f32_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
                              float4* grad) {
     PairSrc src{};
+    set_symmetry(src, m);
     src.cfg = cfg;
     src.n_explicit = n;
     PairDst dst{};
@@ -476,6 +477,7 @@ rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     if (precision == RB_BF16) return nn_tc_system_async(s, m);
     if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
+    set_symmetry(src, m);
     src.pairs = s->pl.pairs;
     src.n_pairs_ptr = s->pl.n_pairs;
     src.pos = s->pos;
@@ -531,6 +533,7 @@ rb_status rb_mlp_destroy(rb_mlp* m) {
     if (m->params) cudaFree(m->params);
     if (m->f32_prep) cudaFree(m->f32_prep);
     if (m->bf16_img) cudaFree(m->bf16_img);
+    if (m->sym_dev) cudaFree(m->sym_dev);
     if (m->status_dev) cudaFree(m->status_dev);
     delete m;
     return RB_OK;
@@ -564,6 +567,7 @@ rb_status rb_nn_pairs(const rb_mlp* m, int32_t precision, int64_t n, const float
                                  reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(grad_out));
     if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
+    set_symmetry(src, m);
     src.cfg = reinterpret_cast<const float4*>(cfg);
     src.n_explicit = n;
     PairDst dst{};

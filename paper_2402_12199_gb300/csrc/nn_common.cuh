@@ -55,6 +55,10 @@ struct PairSrc {
     // explicit mode: configurations in the frame of body i, 2 float4 per pair
     const float4* cfg;
     int64_t n_explicit;
+    // point group of the bodies (n_sym = 0: none), table as in SymTable
+    const float4* sym;
+    int n_sym;
+    int sym_inv;
 };
 
 struct PairDst {
@@ -72,7 +76,53 @@ struct PairGeom {
     float sgn;
     float rho;
     bool beyond;  // system mode: pair outside the cutoff, outputs are zero
+    // symmetry reduction applied to (s, q_rel): (sym_sg R(Qk) s, Qk q_rel Qj)
+    bool sym;
+    float sym_sg;
+    float4 sym_qk, sym_qj;
 };
+
+// Symmetry-reduced pair configurations (the paper's reduction of a cube pair
+// to one description per class of symmetric configurations, SI Sec. 1).
+// Table of a point group of n proper rotations Q_k, 3 float4 per element:
+//   [3k]     u_k = R(Q_k)^T u_ref, u_ref = (3, 2, 1) / sqrt(14)
+//   [3k + 1] Q_k = (s, i, j, k)
+//   [3k + 2] (Q_k.s, -Q_k.i, -Q_k.j, -Q_k.k)  (so scalar(q Q_k) = q . this)
+// canon_config maps (s, q) to (sg R(Q_k) s, Q_k q Q_j) with k maximising
+// sg (R(Q_k) s) . u_ref (sg = +-1 from the sign when the inversion is in the
+// group, else 1) and j maximising |scalar(Q_k q Q_j)|; first maximum wins.
+__device__ inline void canon_config(const float4* __restrict__ tab, int n, int inv, float3& s,
+                                    float4& q, float4& qk, float4& qj, float& sg) {
+    float best = -3.0e38f;
+    int kb = 0;
+    sg = 1.f;
+    for (int k = 0; k < n; ++k) {
+        const float4 u = tab[3 * k];
+        const float d = s.x * u.x + s.y * u.y + s.z * u.z;
+        const float a = inv ? fabsf(d) : d;
+        if (a > best) {
+            best = a;
+            kb = k;
+            sg = (inv && d < 0.f) ? -1.f : 1.f;
+        }
+    }
+    qk = tab[3 * kb + 1];
+    const float3 r = mul(qmat(qk), s);
+    s = make_float3(sg * r.x, sg * r.y, sg * r.z);
+    const float4 q1 = qmul(qk, q);
+    float bj = -1.f;
+    int jb = 0;
+    for (int j = 0; j < n; ++j) {
+        const float4 c = tab[3 * j + 2];
+        const float a = fabsf(q1.x * c.x + q1.y * c.y + q1.z * c.z + q1.w * c.w);
+        if (a > bj) {
+            bj = a;
+            jb = j;
+        }
+    }
+    qj = tab[3 * jb + 1];
+    q = qmul(q1, qj);
+}
 
 // Raw pair data (the global loads), separated from the geometry so a kernel
 // can fetch the next pair while it works on the current one.
@@ -109,6 +159,9 @@ __device__ inline PairGeom pair_geometry(const PairSrc& src, const PairRaw& r) {
     g.qi = make_float4(1.f, 0.f, 0.f, 0.f);
     g.sgn = 1.f;
     g.beyond = false;
+    g.sym = false;
+    g.sym_sg = 1.f;
+    g.sym_qk = g.sym_qj = g.qc;
     float4 qr = g.qc;
     if (r.valid) {
         if (SYSTEM) {
@@ -121,6 +174,10 @@ __device__ inline PairGeom pair_geometry(const PairSrc& src, const PairRaw& r) {
         } else {
             g.s = make_float3(r.a.x, r.a.y, r.a.z);
             qr = r.b;
+        }
+        if (src.n_sym > 0) {
+            canon_config(src.sym, src.n_sym, src.sym_inv, g.s, qr, g.sym_qk, g.sym_qj, g.sym_sg);
+            g.sym = true;
         }
         if (qr.x < 0.f) {
             g.sgn = -1.f;
@@ -169,8 +226,21 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
                                   -0.5f * (-Gw * v.y + w * Gv.y + vxG.y),
                                   -0.5f * (-Gw * v.z + w * Gv.z + vxG.z));
     const float3 sxG = cross3(s, Gs);
-    const float3 ti = make_float3(sxG.x - tj.x, sxG.y - tj.y, sxG.z - tj.z);
-    const float3 Fj = make_float3(-Gs.x, -Gs.y, -Gs.z);
+    float3 ti = make_float3(sxG.x - tj.x, sxG.y - tj.y, sxG.z - tj.z);
+    float3 Fj = make_float3(-Gs.x, -Gs.y, -Gs.z);
+    float3 tjb = tj;
+    float3 Gsb = Gs;
+    float4 Gq = make_float4(g.sgn * Gw, g.sgn * Gv.x, g.sgn * Gv.y, g.sgn * Gv.z);  // dE/dq (raw sign)
+    if (g.sym) {  // back from the canonical configuration: F = sg R^T F', tau = R^T tau'
+        const Mat3 Rk = qmat(g.sym_qk);
+        Fj = mulT(Rk, Fj);
+        Fj = make_float3(g.sym_sg * Fj.x, g.sym_sg * Fj.y, g.sym_sg * Fj.z);
+        ti = mulT(Rk, ti);
+        tjb = mulT(Rk, tj);
+        Gsb = mulT(Rk, Gs);
+        Gsb = make_float3(g.sym_sg * Gsb.x, g.sym_sg * Gsb.y, g.sym_sg * Gsb.z);
+        Gq = qmul(qmul(qconj(g.sym_qk), Gq), qconj(g.sym_qj));
+    }
     if (SYSTEM) {
         if (g.beyond) {
             dst.F[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -179,20 +249,32 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
             return;
         }
         const Mat3 Ri = qmat(g.qi);
-        const float3 a = mul(Ri, Fj), b = mul(Ri, ti), c = mul(Ri, tj);
+        const float3 a = mul(Ri, Fj), b = mul(Ri, ti), c = mul(Ri, tjb);
         dst.F[gp] = make_float4(a.x, a.y, a.z, E);
         dst.ti[gp] = make_float4(b.x, b.y, b.z, 0.f);
         dst.tj[gp] = make_float4(c.x, c.y, c.z, 0.f);
     } else {
         dst.out[3 * gp] = make_float4(Fj.x, Fj.y, Fj.z, E);
         dst.out[3 * gp + 1] = make_float4(ti.x, ti.y, ti.z, 0.f);
-        dst.out[3 * gp + 2] = make_float4(tj.x, tj.y, tj.z, 0.f);
+        dst.out[3 * gp + 2] = make_float4(tjb.x, tjb.y, tjb.z, 0.f);
         if (dst.grad) {
-            const float sg = g.sgn;
-            dst.grad[2 * gp] = make_float4(Gs.x, Gs.y, Gs.z, 0.f);
-            dst.grad[2 * gp + 1] = make_float4(sg * Gw, sg * Gv.x, sg * Gv.y, sg * Gv.z);
+            dst.grad[2 * gp] = make_float4(Gsb.x, Gsb.y, Gsb.z, 0.f);
+            dst.grad[2 * gp + 1] = Gq;
         }
     }
+}
+
+// symmetry.cu: canonical configurations and a tangent mapped with them
+// (cfg, ucfg: n x 2 float4 as rb_nn_weight_vjp takes them).
+__global__ void k_canon_tangent(int64_t n, const float4* __restrict__ tab, int n_sym, int inv,
+                                const float4* __restrict__ cfg, const float4* __restrict__ ucfg,
+                                float4* __restrict__ cfg_out, float4* __restrict__ u_out);
+
+// The network's point group into a pair source.
+inline void set_symmetry(PairSrc& src, const rb_mlp* m) {
+    src.sym = m->sym_dev;
+    src.n_sym = m->n_sym;
+    src.sym_inv = m->sym_inv;
 }
 
 // nn.cu

@@ -412,6 +412,7 @@ static rb_status launch_tc(const rb_mlp* m, cudaStream_t stream, int grid, const
 
 rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m) {
     PairSrc src{};
+    set_symmetry(src, m);
     src.pairs = s->pl.pairs;
     src.n_pairs_ptr = s->pl.n_pairs;
     src.pos = s->pos;
@@ -429,6 +430,7 @@ rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m) {
 rb_status nn_tc_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
                             float4* grad) {
     PairSrc src{};
+    set_symmetry(src, m);
     src.cfg = cfg;
     src.n_explicit = n;
     PairDst dst{};

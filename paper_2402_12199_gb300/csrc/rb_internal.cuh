@@ -148,6 +148,10 @@ struct rb_mlp {
     void* bf16_img = nullptr;     // BF16 shared-memory image for the tensor-core kernel
     unsigned* status_dev = nullptr;  // sticky device-side error bits of pair-level calls
     uint64_t version = 1;         // bumped on every set_params
+    // point group of the bodies (symmetry-reduced configurations): device
+    // table of 3 float4 per rotation (see canon_config), n_sym = 0: none
+    float4* sym_dev = nullptr;
+    int n_sym = 0, sym_inv = 0;
 };
 
 struct rb_system {

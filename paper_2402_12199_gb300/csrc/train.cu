@@ -347,13 +347,15 @@ static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<
 
 // Workspace layout for batch B, width W, depth D (floats):
 //   X, U [B x 16]; per layer Z, Zd, H, Hd [B x W]; Ah0, Ahd0, Ah1, Ahd1 [B x W];
-//   T [B x W]; c [B]; ucfg, pred [B x 8], [B x 12]; G16 [W x 16]
+//   T [B x W]; c [B]; ucfg, pred [B x 8], [B x 12]; G16 [W x 16];
+//   cfg_c, ucfg_c [B x 8] (canonical configurations and tangents)
 struct TrWork {
     float *X, *U, *Z[4], *Zd[4], *H[4], *Hd[4], *Ah[2], *Ahd[2], *T, *c, *ucfg, *pred, *G16;
+    float *cfg_c, *ucfg_c;
 };
 static size_t tr_work_floats(int64_t B, int W, int D) {
     return (size_t)B * 32 + (size_t)D * 4 * B * W + 5 * (size_t)B * W + B + 8 * B + 12 * B +
-           (size_t)W * 16 + 64;
+           (size_t)W * 16 + 16 * (size_t)B + 16 * 48;  // + rounding of every buffer to 16
 }
 static TrWork tr_work(float* base, int64_t B, int W, int D) {
     TrWork w{};
@@ -380,6 +382,8 @@ static TrWork tr_work(float* base, int64_t B, int W, int D) {
     w.ucfg = take(8 * B);
     w.pred = take(12 * B);
     w.G16 = take((size_t)W * 16);
+    w.cfg_c = take(8 * B);
+    w.ucfg_c = take(8 * B);
     return w;
 }
 
@@ -394,6 +398,13 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
     TrWork w = tr_work(tr->work, tr->max_batch, W, D);
     const float* flat = m->params;
     RB_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * m->n_params, st));
+    if (m->n_sym > 0) {  // the network sees canonical configurations: map cfg and u
+        k_canon_tangent<<<nblk(B), 256, 0, st>>>(B, m->sym_dev, m->n_sym, m->sym_inv, cfg, ucfg,
+                                                 reinterpret_cast<float4*>(w.cfg_c),
+                                                 reinterpret_cast<float4*>(w.ucfg_c));
+        cfg = reinterpret_cast<const float4*>(w.cfg_c);
+        ucfg = reinterpret_cast<const float4*>(w.ucfg_c);
+    }
     k_tr_inputs<<<nblk(B), 256, 0, st>>>(B, cfg, ucfg, flat, fl, w.X, w.U);
     // forward with tangent
     const float* W1p = m->f32_prep + (int64_t)kInPad * W + (int64_t)(D - 1) * W * W;  // [W][16]

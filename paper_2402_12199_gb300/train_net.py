@@ -20,9 +20,14 @@ from . import api, inputs
 def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_samples: int = 200_000,
                   steps: int = 3000, batch: int = 4096, lr: float = 1e-3, lam_tau: float = 1.0,
                   lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
-                  log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0):
-    """Returns (mlp, report).  The network's feature normalisation spans the
-    separations contact..Rc; e_scale and e_shift come from the label energies."""
+                  log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0,
+                  symmetric: bool = True):
+    """Returns (mlp, report).  With `symmetric` the body's point group is
+    attached to the network (rb_mlp_set_symmetry), so it learns one copy of
+    every class of symmetry-related configurations, and the feature
+    normalisation is the mean and spread of the features of the canonical
+    training configurations; otherwise it spans the separations contact..Rc
+    isotropically.  e_scale and e_shift come from the label energies."""
     box = 60.0 if shape == "cube" else 70.0
     sysobj = api.System(8, [box] * 3, shape)
     Rc = sysobj.pair_cutoff
@@ -36,12 +41,22 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     E = lab_tr[:, 3].double().cpu().numpy()
     rmin = float(rho_c.min().item())
     mu, isd = inputs.feature_normalisation(rmin, Rc)
+    group = api.template_symmetry(sysobj.template()) if symmetric else None
+    if group is not None:
+        probe = api.MLP(width, depth)
+        probe.set_params(inputs.mlp_params(width, depth, seed))
+        probe.set_symmetry(*group)
+        cc = cfg_tr[:50000].clone()
+        probe.canonical(cc)
+        mu, isd = _feature_stats(cc)
     e_scale = float(np.std(np.clip(E, np.percentile(E, 1), np.percentile(E, 99)))) or 1.0
     e_shift = float(np.median(E))
     flat = inputs.mlp_params(width, depth, seed + 1, mu=mu, inv_sd=isd, e_scale=e_scale,
                              e_shift=e_shift)
     mlp = api.MLP(width, depth)
     mlp.set_params(flat)
+    if group is not None:
+        mlp.set_symmetry(*group)
     tr = api.Trainer(mlp, batch, lr=lr)
     g = torch.Generator(device="cuda").manual_seed(seed)
     t0 = time.perf_counter()
@@ -63,6 +78,8 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     out = mlp.pairs(cfg_te.contiguous(), "fp32")
     err = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
     report = {"shape": shape, "width": width, "depth": depth, "samples": n_samples,
+              "symmetry": (f"{len(group[0])} rotations" + (" + inversion" if group[1] else ""))
+              if group is not None else None,
               "steps": k + 1, "batch": batch, "lr": lr, "f_scale": f_scale, "kT_w": kT_w, "t_sample_s": t_sample,
               "t_train_s": t_train, "rho_contact_min": rmin, "Rc": Rc,
               "heldout_e_F": err(out[:, 0:3], lab_te[:, 0:3]),
@@ -70,6 +87,20 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
               "heldout_e_tau_j": err(out[:, 8:11], lab_te[:, 8:11]),
               "losses": losses}
     return mlp, report
+
+
+def _feature_stats(cfg):
+    """Mean and inverse spread of the network's 10 input features over
+    configurations (n, 8): s, q_rel with a non-negative scalar part, rho,
+    1/rho, rho^2."""
+    s = cfg[:, :3].double()
+    q = cfg[:, 4:8].double()
+    q = torch.where(q[:, :1] < 0, -q, q)
+    rho = torch.linalg.norm(s, dim=1, keepdim=True)
+    x = torch.cat([s, q, rho, 1.0 / rho, rho * rho], 1)
+    mu = x.mean(0).cpu().numpy()
+    sd = x.std(0).cpu().numpy()
+    return mu, 1.0 / np.maximum(sd, 1e-3)
 
 
 def force_error(system: api.System, mlp: api.MLP, precision: str = "bf16"):

@@ -54,3 +54,23 @@ def test_library_reports_version_without_gpu(lib):
     lib.rb_mlp_n_params.argtypes = [ctypes.c_int32, ctypes.c_int32]
     assert lib.rb_mlp_n_params(128, 3) == 2 * 10 + 128 * 10 + 128 + 2 * (128 * 128 + 128) + 128 + 3
     assert lib.rb_mlp_n_params(0, 3) < 0
+
+
+@pytest.mark.parametrize("shape", ["cube", "cylinder", "box", "cut cube"])
+def test_template_symmetry_matches_the_oracle_without_gpu(lib, shape):
+    """rb_template_symmetry (host code) finds the same point group, in the same
+    order, as the oracle's independent search."""
+    import numpy as np
+
+    from oracle import bodies, symmetry
+    from paper_2402_12199_gb300 import api
+
+    tmpl = {"cube": bodies.cube_template(), "cylinder": bodies.cylinder_template(),
+            "box": np.stack(np.meshgrid(np.arange(3) - 1.0, np.arange(4) - 1.5,
+                                        np.arange(6) - 2.5, indexing="ij"), -1).reshape(-1, 3),
+            "cut cube": bodies.cube_template()[:-1]}[shape]
+    q, inv = api.template_symmetry(tmpl)
+    qo, invo = symmetry.point_group(tmpl)
+    assert inv == invo
+    assert q.shape == qo.shape
+    np.testing.assert_allclose(q, qo, atol=1e-7)
