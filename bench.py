@@ -49,8 +49,12 @@ def parse():
     ap.add_argument("--cpu-sample-pairs", type=int, default=100000)
     ap.add_argument("--ref-sample-pairs", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=1500)
-    ap.add_argument("--train-samples", type=int, default=200000)
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--train-samples", type=int, default=1000000)
+    ap.add_argument("--train-lr", type=float, default=3e-3)
+    ap.add_argument("--train-f-scale", type=float, default=2.0)
+    ap.add_argument("--no-symmetry", action="store_true")
+    ap.add_argument("--train-contact", type=float, default=0.85)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--skin", type=float, default=0.4)
     ap.add_argument("--drift-steps", type=int, default=10000)
@@ -312,22 +316,37 @@ def main():
         from paper_2402_12199_gb300 import train_net
 
         mlp, rep = train_net.train_network("cube", WIDTH, DEPTH, n_samples=args.train_samples,
-                                           steps=args.train_steps, batch=4096, lr=1e-3,
-                                           time_limit_s=60.0)
+                                           steps=args.train_steps, batch=4096, lr=args.train_lr,
+                                           f_scale=args.train_f_scale,
+                                           symmetric=not args.no_symmetry,
+                                           contact=args.train_contact, time_limit_s=60.0)
+        rho_fallback = rep["rho_contact_min"]
         training = {"samples": rep["samples"], "steps": rep["steps"], "batch": rep["batch"],
+                    "symmetry": rep["symmetry"],
                     "sampler_pairs_per_s": (rep["samples"] + 10000) / rep["t_sample_s"],
                     "train_samples_per_s": rep["steps"] * rep["batch"] / rep["t_train_s"],
+                    "train_s": rep["t_train_s"],
                     "heldout_e_F": rep["heldout_e_F"], "heldout_e_tau_i": rep["heldout_e_tau_i"],
                     "heldout_e_tau_j": rep["heldout_e_tau_j"],
-                    "loss": "mean |dF_j|^2 + |dtau_i|^2 + |dtau_j|^2 (FP32, Adam lr 1e-3)"}
+                    "heldout": "10000 pairs drawn like the training set (separation uniform "
+                               "from contact to Rc: dominated by contact forces)",
+                    "contact": f"smallest bead-bead distance {args.train_contact} sigma "
+                               "(separations reach into the repulsive wall)",
+                    "loss": f"mean w (|dF_j|^2 + |dtau_i|^2 + |dtau_j|^2), w = 1 / (1 + "
+                            f"|label|^2 / {args.train_f_scale}^2); FP32, Adam, lr "
+                            f"{args.train_lr} with cosine decay",
+                    "nn_bead_fallback_rho": rho_fallback}
     else:
         mlp = api.MLP(WIDTH, DEPTH)
         mlp.set_params(flat)
+        rho_fallback = 0.0
     stream = torch.cuda.current_stream()
     systems = {}
     for p in paths:
         s = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
         s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+        if p.startswith("nn"):
+            s.set_nn_fallback(rho_fallback)
         systems[p] = s
 
     def pcfg(p):
@@ -368,8 +387,12 @@ def main():
             one_step(ev)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    for s in systems.values():
-        s.sync()
+    path_errors = {}
+    for p, s in systems.items():
+        try:
+            s.sync()
+        except api.RBError as ex:  # reported with the path, not hidden
+            path_errors[p] = str(ex)
     per_path_ms = {p: [a.elapsed_time(b) for a, b in ev[p]] for p in paths}
     ms_step_local = sum(statistics.mean(v) for v in per_path_ms.values())
     pairs_per_step = sum(n_pairs.values())
@@ -505,18 +528,24 @@ def main():
         for p in paths:
             s = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
             s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+            if p.startswith("nn"):
+                s.set_nn_fallback(rho_fallback)
             if p == "beads":
                 s.forces_beads()
             else:
                 s.forces_nn(mlp, pcfg(p)["precision"])
             t_series, e_series = [0], [sum(s.energy())]
             done = 0
-            while done < args.drift_steps:
-                k = min(args.drift_every, args.drift_steps - done)
-                s.step(k, DT, **pcfg(p))
-                done += k
-                t_series.append(done)
-                e_series.append(sum(s.energy()))
+            err = None
+            try:
+                while done < args.drift_steps:
+                    k = min(args.drift_every, args.drift_steps - done)
+                    s.step(k, DT, **pcfg(p))
+                    done += k
+                    t_series.append(done)
+                    e_series.append(sum(s.energy()))
+            except api.RBError as ex:  # e.g. bodies collapsing into one cell
+                err = f"stopped after at most {done + args.drift_every} steps: {ex}"
             e = np.array(e_series)
             dev = np.abs(e - e[0]) / (N_BODIES * KT)
             finite = bool(np.all(np.isfinite(e)))
@@ -525,7 +554,7 @@ def main():
                             float(np.polyfit(np.array(t_series) / 1000.0, e / (N_BODIES * KT), 1)[0])
                             if finite else None,
                         "E0_per_body_kT": float(e[0] / (N_BODIES * KT)) if finite else None,
-                        "finite": finite}
+                        "finite": finite, "steps_done": done, "error": err}
             del s
 
     # ---- end to end through the public API with host buffers
@@ -552,6 +581,7 @@ def main():
 
         probe = api.System(N_BODIES, [L] * 3, "cube")
         probe.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+        probe.set_nn_fallback(rho_fallback)
         model_error = {"vs": "bead path, same state (model error, not parity)",
                        "trained": training is not None}
         for p in paths:
@@ -578,6 +608,8 @@ def main():
         ms = statistics.mean(per_path_ms[p])
         path_info[p] = {"ms_per_md_step": ms, "md_steps_per_s": 1e3 / ms,
                         "pair_evals_per_s": n_pairs[p] / (ms * 1e-3), "pairs": n_pairs[p]}
+        if p in path_errors:
+            path_info[p]["error"] = path_errors[p]
     if "beads" in path_info:
         for p in paths:
             if p != "beads":
@@ -588,7 +620,9 @@ def main():
             "config": {"workload": f"{N_BODIES} cubes (5x5x5 beads, LJ eps=sigma=1 rc=2.5), "
                                    f"phi={PHI}, NVE dt={DT}; one MD step per force path "
                                    f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU "
-                                   f"{'trained on device by force matching' if training else 'random init'}",
+                                   f"{'trained on device by force matching on symmetry-reduced configurations' if training else 'random init'}"
+                                   + (f"; network pairs closer than {rho_fallback:.3f} sigma (the training set's "
+                                      f"smallest contact separation) take the bead sum" if rho_fallback > 0 else ""),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "pair_list": f"Verlet skin {args.skin} sigma, rebuilt on the device when a "
                                     f"centre moves more than skin/2; pairs beyond Rc give exactly zero",
@@ -598,9 +632,12 @@ def main():
             "nn_bf16_width256": width256, "nve_drift": drift,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            # per MD step and path: integrate, skin check, cell assign, pair build,
-            # two scan kernels, emit, finish, flag clear, pair kernel, reduce
-            "gpu_launches": args.steps * 11 * len(paths), "clocks": clocks,
+            # per MD step and path: integrate (with the skin check), cell assign,
+            # pair build, two scan kernels, emit, finish, flag clear, pair kernel,
+            # reduce; plus the bead fallback kernel on the network paths
+            "gpu_launches": args.steps * (11 * len(paths) + (sum(p.startswith("nn") for p in paths)
+                                                            if rho_fallback > 0 else 0)),
+            "clocks": clocks,
             "peaks_source": how, "wall_s": wall}
     if rank == 0:
         print(json.dumps(line))

@@ -304,6 +304,12 @@ rb_status rb_nn_pairs(const rb_mlp* mlp, int32_t precision, int64_t n, const flo
  * potential of `sys`; runs on its stream. */
 rb_status rb_sample_pairs(const rb_system* sys, int64_t n, const float* uniforms, float* cfg,
                           float* labels, float* rho_contact);
+/* rb_sample_pairs with contact defined at a smallest bead-bead distance of
+ * `contact` (sigma units of the potential, > 0) instead of sigma: a value
+ * below sigma draws the separations from slightly inside the repulsive wall
+ * up to Rc, so a network fitted to them has seen the wall. */
+rb_status rb_sample_pairs_at(const rb_system* sys, int64_t n, const float* uniforms, float contact,
+                             float* cfg, float* labels, float* rho_contact);
 
 /* Trainer for `mlp`: Adam state and a workspace for batches of up to
  * max_batch pairs.  Runs on the network's stream. */

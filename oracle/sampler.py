@@ -63,9 +63,12 @@ def contact_distance(direction, q_j, tmpl, Rc, sigma=1.0, n_iter=N_BISECT):
     return 0.5 * (lo + hi)
 
 
-def sample_pairs(u, tmpl, Rc, eps=1.0, sigma=1.0, rc=2.5):
+def sample_pairs(u, tmpl, Rc, eps=1.0, sigma=1.0, rc=2.5, contact=None):
     """Pair configurations (B, 7) = (s, q_rel) and bead-sum labels (B, 10) =
-    (E, F_j, tau_i, tau_j), all in the frame of body i; also rho_c (B,)."""
+    (E, F_j, tau_i, tau_j), all in the frame of body i; also rho_c (B,).
+    `contact` (default sigma) is the smallest bead-bead distance that defines
+    contact: below sigma the draws reach into the repulsive wall."""
+    contact = sigma if contact is None else contact
     u = np.asarray(u, dtype=np.float64)
     d, q = draws_to_config(u)
     B = len(u)
@@ -75,7 +78,7 @@ def sample_pairs(u, tmpl, Rc, eps=1.0, sigma=1.0, rc=2.5):
     zero = np.zeros(3)
     one = np.array([1.0, 0.0, 0.0, 0.0])
     for b in range(B):
-        rho_c[b] = contact_distance(d[b], q[b], tmpl, Rc, sigma)
+        rho_c[b] = contact_distance(d[b], q[b], tmpl, Rc, contact)
         rho = rho_c[b] + u[b, 5] * (Rc - rho_c[b])
         s = rho * d[b]
         r = bead_pair(zero, one, s, q[b], np.zeros(3), tmpl, tmpl, eps, sigma, rc)

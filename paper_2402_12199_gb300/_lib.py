@@ -114,6 +114,7 @@ SIGNATURES = {
     "rb_fetch_state": (I32, [P, ctypes.c_uint64, P, P, P, P]),
     "rb_server_stats": (I32, [P, ctypes.POINTER(rb_server_stats_t)]),
     "rb_sample_pairs": (I32, [P, I64, P, P, P, P]),
+    "rb_sample_pairs_at": (I32, [P, I64, P, F32, P, P, P]),
     "rb_trainer_create": (I32, [P, I64, F32, F32, F32, F32, ctypes.POINTER(P)]),
     "rb_trainer_destroy": (I32, [P]),
     "rb_trainer_set_lr": (I32, [P, F32]),

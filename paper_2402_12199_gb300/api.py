@@ -357,15 +357,20 @@ class Trainer:
         return g
 
 
-def sample_pairs(system: System, uniforms: torch.Tensor):
-    """rb_sample_pairs: (cfg n x 8, labels n x 12, rho_contact n) on the device."""
+def sample_pairs(system: System, uniforms: torch.Tensor, contact: float = None):
+    """rb_sample_pairs (rb_sample_pairs_at when `contact` is given): (cfg n x 8,
+    labels n x 12, rho_contact n) on the device."""
     _dev(uniforms, 6)
     n = uniforms.shape[0]
     cfg = torch.empty((n, 8), dtype=torch.float32, device="cuda")
     lab = torch.empty((n, 12), dtype=torch.float32, device="cuda")
     rc = torch.empty((n,), dtype=torch.float32, device="cuda")
-    check(load().rb_sample_pairs(system.handle, n, uniforms.data_ptr(), cfg.data_ptr(),
-                                 lab.data_ptr(), rc.data_ptr()))
+    if contact is None:
+        check(load().rb_sample_pairs(system.handle, n, uniforms.data_ptr(), cfg.data_ptr(),
+                                     lab.data_ptr(), rc.data_ptr()))
+    else:
+        check(load().rb_sample_pairs_at(system.handle, n, uniforms.data_ptr(), float(contact),
+                                        cfg.data_ptr(), lab.data_ptr(), rc.data_ptr()))
     return cfg, lab, rc
 
 

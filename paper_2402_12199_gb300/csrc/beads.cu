@@ -28,8 +28,9 @@ namespace rb {
 // One warp per listed body pair (persistent grid-stride loop).  Pairs with
 // |R|^2 >= cut2 are skipped: with zero_beyond they get zero results (the bead
 // path, cut2 = Rc^2, pairs listed only because of the skin); without it they
-// keep what is there (the network path's bead fallback, cut2 = rho_min^2,
-// which counts the pairs it evaluates in *count).
+// keep what is there.  With sel (the network path's bead fallback, cut2 =
+// rho_min^2) only the pairs sel[0 .. *sel_count) are visited: the network
+// kernel listed those closer than rho_min.
 // C = 0: any template (bead_pair_warp); C = 5 or 8: a column-structured
 // template stored column by column (bead_pair_warp_cols), held to three CTAs
 // of 256 threads per SM (at most 85 registers).
@@ -40,7 +41,8 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
                  const float4* __restrict__ tmpl, int n_beads, BeadCols cols, float3 L,
                  float3 invL, BeadPot pot, float cut2, int zero_beyond,
                  float4* __restrict__ out_F, float4* __restrict__ out_ti,
-                 float4* __restrict__ out_tj, int* count) {
+                 float4* __restrict__ out_tj, const int* __restrict__ sel,
+                 const int* __restrict__ sel_count) {
     __shared__ float4 sT[kMaxBeads + 1];
     // generic: 2 float4 per template bead; columns: 1 float4 per column, then
     // 8 floats per column and 8 more (at most kMaxBeads / 5 columns)
@@ -53,12 +55,13 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
         load_columns(tmpl, cols, pot.rc2_test, sN, reinterpret_cast<float*>(sN + kMaxBeads / 5 + 1));
     }
     __syncthreads();
-    const int n_pairs = *n_pairs_ptr;
+    const int n_pairs = sel ? *sel_count : *n_pairs_ptr;
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const int nw = gridDim.x * warps_per_block;
-    for (int p = gw; p < n_pairs; p += nw) {
+    for (int t = gw; t < n_pairs; t += nw) {
+        const int p = sel ? sel[t] : t;
         const int2 ij = pairs[p];
         const float4 pi = pos[ij.x], pj = pos[ij.y];
         const float4 qi = quat[ij.x], qj = quat[ij.y];
@@ -95,7 +98,6 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
                 const float3 sxF = cross3(s, F);
                 const float3 tj = mul(Ri, make_float3(T.x - sxF.x, T.y - sxF.y, T.z - sxF.z));
                 out_tj[p] = make_float4(tj.x, tj.y, tj.z, 0.f);
-                if (count) atomicAdd(count, 1);
             }
         }
     }
@@ -116,7 +118,7 @@ BeadPot bead_pot(const rb_system* s) {
 }
 
 template <int NP, int C>
-static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, int* count) {
+static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, const int* sel) {
     static int occ = 0;
     if (occ == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP, C>, 256, 0);
@@ -127,30 +129,33 @@ static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, int* co
     const int grid = s->num_sms * occ;
     k_bead_pairs<NP, C><<<grid, 256, 0, s->stream>>>(
         s->pl.pairs, s->pl.n_pairs, s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL,
-        bead_pot(s), cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, count);
+        bead_pot(s), cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, sel, s->fallback_count);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
 
 template <int NP>
-static rb_status launch_beads_np(rb_system* s, float cut2, int zero_beyond, int* count) {
-    if (s->cols.len == 5) return launch_beads<NP, 5>(s, cut2, zero_beyond, count);
-    if (s->cols.len == 8) return launch_beads<NP, 8>(s, cut2, zero_beyond, count);
-    return launch_beads<NP, 0>(s, cut2, zero_beyond, count);
+static rb_status launch_beads_np(rb_system* s, float cut2, int zero_beyond, const int* sel) {
+    if (s->cols.len == 5) return launch_beads<NP, 5>(s, cut2, zero_beyond, sel);
+    if (s->cols.len == 8) return launch_beads<NP, 8>(s, cut2, zero_beyond, sel);
+    return launch_beads<NP, 0>(s, cut2, zero_beyond, sel);
 }
 
-static rb_status launch_beads_any(rb_system* s, float cut2, int zero_beyond, int* count) {
+static rb_status launch_beads_any(rb_system* s, float cut2, int zero_beyond, const int* sel) {
     const int np = (s->n_beads + 63) / 64;
-    if (np <= 2) return launch_beads_np<2>(s, cut2, zero_beyond, count);
-    if (np <= 3) return launch_beads_np<3>(s, cut2, zero_beyond, count);
-    return launch_beads_np<4>(s, cut2, zero_beyond, count);
+    if (np <= 2) return launch_beads_np<2>(s, cut2, zero_beyond, sel);
+    if (np <= 3) return launch_beads_np<3>(s, cut2, zero_beyond, sel);
+    return launch_beads_np<4>(s, cut2, zero_beyond, sel);
 }
 
+// The pairs the network kernel listed (closer than rho_min) by the bead sum.
 rb_status bead_fallback_async(rb_system* s) {
-    RB_CUDA(cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream));
-    if (!(s->nn_fallback_rho > 0.f)) return RB_OK;
+    if (!(s->nn_fallback_rho > 0.f)) {
+        RB_CUDA(cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream));
+        return RB_OK;
+    }
     const float r = std::min(s->nn_fallback_rho, s->Rc);
-    return launch_beads_any(s, r * r, 0, s->fallback_count);
+    return launch_beads_any(s, r * r, 0, s->fb_list);
 }
 
 rb_status bead_pairs_async(rb_system* s) { return launch_beads_any(s, s->Rc * s->Rc, 1, nullptr); }

@@ -489,6 +489,7 @@ rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;
     dst.tj = s->pair_tj;
+    RB_TRY(set_fallback(dst, s));
     return dispatch_f32<true>(m, s->stream, s->num_sms, src, dst);
 }
 

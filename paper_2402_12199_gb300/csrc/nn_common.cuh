@@ -67,6 +67,11 @@ struct PairDst {
     float4* tj;    // system: (tau_j, 0)
     float4* out;   // explicit: n x 3 float4 (F_j, E), (tau_i, 0), (tau_j, 0), body-i frame
     float4* grad;  // explicit (nullable): n x 2 float4 (dE/ds, 0), dE/dq_rel (raw sign)
+    // system mode, bead fallback (nullable): pairs with |R|^2 < fb_rho2 are
+    // appended to fb_list (count in *fb_count) for the bead kernel to redo
+    int* fb_list;
+    int* fb_count;
+    float fb_rho2;
 };
 
 struct PairGeom {
@@ -248,6 +253,7 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
             dst.tj[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
             return;
         }
+        if (dst.fb_list && g.rho * g.rho < dst.fb_rho2) dst.fb_list[atomicAdd(dst.fb_count, 1)] = (int)gp;
         const Mat3 Ri = qmat(g.qi);
         const float3 a = mul(Ri, Fj), b = mul(Ri, ti), c = mul(Ri, tjb);
         dst.F[gp] = make_float4(a.x, a.y, a.z, E);
@@ -269,6 +275,21 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
 __global__ void k_canon_tangent(int64_t n, const float4* __restrict__ tab, int n_sym, int inv,
                                 const float4* __restrict__ cfg, const float4* __restrict__ ucfg,
                                 float4* __restrict__ cfg_out, float4* __restrict__ u_out);
+
+// The bead-fallback list of a system into a pair destination (and its count
+// reset), when the system has a fallback separation.
+inline rb_status set_fallback(PairDst& dst, rb_system* s) {
+    dst.fb_list = nullptr;
+    dst.fb_count = nullptr;
+    dst.fb_rho2 = 0.f;
+    if (!(s->nn_fallback_rho > 0.f)) return RB_OK;
+    const float r = s->nn_fallback_rho < s->Rc ? s->nn_fallback_rho : s->Rc;
+    dst.fb_list = s->fb_list;
+    dst.fb_count = s->fallback_count;
+    dst.fb_rho2 = r * r;
+    RB_CUDA(cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream));
+    return RB_OK;
+}
 
 // The network's point group into a pair source.
 inline void set_symmetry(PairSrc& src, const rb_mlp* m) {

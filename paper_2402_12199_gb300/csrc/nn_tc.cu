@@ -424,6 +424,7 @@ rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m) {
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;
     dst.tj = s->pair_tj;
+    RB_TRY(set_fallback(dst, s));
     return launch_tc<true>(m, s->stream, s->num_sms, src, dst, s->status_dev);
 }
 

@@ -191,6 +191,7 @@ struct rb_system {
     // evaluated by the bead sum instead (0 = off); count of such pairs
     float nn_fallback_rho = 0.f;
     int* fallback_count = nullptr;
+    int* fb_list = nullptr;  // pair indices the network kernel hands to the bead fallback
     // Verlet skin: the list holds pairs within Rc + skin and is rebuilt only
     // when a centre has moved more than skin / 2 since the last build
     // (decided on the device: rebuild_flag); pair kernels skip |R| >= Rc.

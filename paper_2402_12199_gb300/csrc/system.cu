@@ -726,6 +726,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     ALLOC(s->red_out, sizeof(double) * 16);
     ALLOC(s->status_dev, sizeof(unsigned));
     ALLOC(s->fallback_count, sizeof(int));
+    ALLOC(s->fb_list, sizeof(int) * cp);
     ALLOC(s->pos_ref, sizeof(float4) * N);
     ALLOC(s->rebuild_flag, sizeof(int));
 #undef ALLOC
@@ -790,7 +791,7 @@ int64_t rb_system_footprint(const rb_system_desc* d) {
     b += 6 * 16 * N;                        // state + forces
     b += 4 * n_cells * (1 + cap);           // cells
     b += 4 * N * (2 + 2 * mn + 2) + 4 * (N / 1024 + 2);  // rows, offsets
-    b += 8 * cp + 3 * 16 * cp;              // pairs + per-pair results
+    b += 8 * cp + 3 * 16 * cp + 4 * cp;     // pairs + per-pair results + fallback list
     b += 8 * 12 * 2 * sms + 8 * 16 + 64;    // reductions, status
     return b;
 }
@@ -805,7 +806,7 @@ rb_status rb_destroy_system(rb_system* s) {
                     s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
                     s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
                     s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev,
-                    s->fallback_count, s->pos_ref, s->rebuild_flag};
+                    s->fallback_count, s->fb_list, s->pos_ref, s->rebuild_flag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;

@@ -486,6 +486,13 @@ extern "C" {
 rb_status rb_sample_pairs(const rb_system* s, int64_t n, const float* uniforms, float* cfg,
                           float* labels, float* rho_contact) {
     if (!s) return fail(RB_EINVAL, "null system");
+    return rb_sample_pairs_at(s, n, uniforms, s->sigma, cfg, labels, rho_contact);
+}
+
+rb_status rb_sample_pairs_at(const rb_system* s, int64_t n, const float* uniforms, float contact,
+                             float* cfg, float* labels, float* rho_contact) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (!(contact > 0.f)) return fail(RB_EINVAL, "contact distance must be positive");
     if (n < 0 || (n > 0 && (!uniforms || !cfg || !labels))) return fail(RB_EINVAL, "bad arrays");
     if (n == 0) return RB_OK;
     const int np = (s->n_beads + 63) / 64;
@@ -493,7 +500,7 @@ rb_status rb_sample_pairs(const rb_system* s, int64_t n, const float* uniforms, 
     const int grid = s->num_sms * 4;
 #define RB_SAMPLE(NP)                                                                           \
     k_sample_pairs<NP><<<grid, 256, 0, s->stream>>>(n, uniforms, s->tmpl_dev, s->n_beads, s->Rc, \
-                                                    s->sigma, pot, 40,                          \
+                                                    contact, pot, 40,                           \
                                                     reinterpret_cast<float4*>(cfg),             \
                                                     reinterpret_cast<float4*>(labels), rho_contact)
     if (np <= 2)

@@ -21,19 +21,21 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
                   steps: int = 3000, batch: int = 4096, lr: float = 1e-3, lam_tau: float = 1.0,
                   lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
                   log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0,
-                  symmetric: bool = True):
+                  symmetric: bool = True, contact: float = 1.0):
     """Returns (mlp, report).  With `symmetric` the body's point group is
     attached to the network (rb_mlp_set_symmetry), so it learns one copy of
     every class of symmetry-related configurations, and the feature
     normalisation is the mean and spread of the features of the canonical
     training configurations; otherwise it spans the separations contact..Rc
-    isotropically.  e_scale and e_shift come from the label energies."""
+    isotropically.  e_scale and e_shift come from the label energies.
+    `contact`: smallest bead-bead distance (sigma units) that defines contact
+    for the sampled separations (rb_sample_pairs_at)."""
     box = 60.0 if shape == "cube" else 70.0
     sysobj = api.System(8, [box] * 3, shape)
     Rc = sysobj.pair_cutoff
     u = torch.from_numpy(inputs.sampler_uniforms(n_samples + 10000, seed)).cuda()
     t0 = time.perf_counter()
-    cfg, lab, rho_c = api.sample_pairs(sysobj, u)
+    cfg, lab, rho_c = api.sample_pairs(sysobj, u, contact)
     torch.cuda.synchronize()
     t_sample = time.perf_counter() - t0
     cfg_tr, lab_tr = cfg[:n_samples], lab[:n_samples]

@@ -39,8 +39,8 @@ def cfg7(cfg8):
     return np.concatenate([cfg8[:, :3], cfg8[:, 4:8]], 1)
 
 
-@pytest.mark.parametrize("shape", ["cube", "cylinder"])
-def test_sampler_matches_oracle(shape):
+@pytest.mark.parametrize("shape,contact", [("cube", None), ("cylinder", None), ("cube", 0.85)])
+def test_sampler_matches_oracle(shape, contact):
     import torch
 
     from paper_2402_12199_gb300 import api
@@ -48,14 +48,14 @@ def test_sampler_matches_oracle(shape):
     tmpl = bodies.cube_template() if shape == "cube" else bodies.cylinder_template()
     s = api.System(8, [60.0] * 3, shape)
     u = inputs.sampler_uniforms(48, 5)
-    cfg, lab, rc = api.sample_pairs(s, torch.from_numpy(u).cuda())
+    cfg, lab, rc = api.sample_pairs(s, torch.from_numpy(u).cuda(), contact)
     torch.cuda.synchronize()
     cfg, lab, rc = cfg.cpu().numpy(), lab.cpu().numpy(), rc.cpu().numpy()
     d, q = sampler.draws_to_config(u.astype(np.float64))
     np.testing.assert_allclose(cfg[:, 4:8], q, atol=2e-6)
     Rc = bodies.pair_cutoff(tmpl)
     for b in range(0, 48, 6):
-        rc_ref = sampler.contact_distance(d[b], q[b], tmpl, Rc)
+        rc_ref = sampler.contact_distance(d[b], q[b], tmpl, Rc, contact or 1.0)
         assert rc[b] == pytest.approx(rc_ref, abs=2e-5)
     rho = np.linalg.norm(cfg[:, :3], axis=1)
     assert np.all(rho >= rc - 1e-4) and np.all(rho <= Rc + 1e-4)

@@ -513,3 +513,17 @@ def test_contact_bisection_finds_sigma():
     # aligned cubes along a face normal touch when the face planes are 1 sigma apart
     rc = sampler.contact_distance(np.array([1.0, 0, 0]), ID, CUBE, Rc)
     assert rc == pytest.approx(5.0, abs=1e-9)
+
+
+def test_contact_bisection_at_a_smaller_distance():
+    """Contact defined at 0.85 sigma: the bisection lands on that smallest bead
+    distance, and aligned cubes touch at 4 + 0.85 sigma."""
+    u = inputs.sampler_uniforms(4, 19).astype(np.float64)
+    d, q = sampler.draws_to_config(u)
+    Rc = bodies.pair_cutoff(CUBE)
+    for b in range(4):
+        rc = sampler.contact_distance(d[b], q[b], CUBE, Rc, 0.85)
+        md_ = oracle.min_bead_distance(np.zeros(3), ID, rc * d[b], q[b], NOBOX, CUBE)
+        assert md_ == pytest.approx(0.85, abs=1e-9)
+    rc = sampler.contact_distance(np.array([1.0, 0, 0]), ID, CUBE, Rc, 0.85)
+    assert rc == pytest.approx(4.85, abs=1e-9)
