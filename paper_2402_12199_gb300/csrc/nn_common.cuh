@@ -55,10 +55,12 @@ struct PairSrc {
     // explicit mode: configurations in the frame of body i, 2 float4 per pair
     const float4* cfg;
     int64_t n_explicit;
-    // point group of the bodies (n_sym = 0: none), table as in SymTable
+    // point group of the bodies (n_sym = 0: none), table as in canon_config;
+    // sym_cube: the group is the cube's (see canon_cube)
     const float4* sym;
     int n_sym;
     int sym_inv;
+    int sym_cube;
 };
 
 struct PairDst {
@@ -96,6 +98,68 @@ struct PairGeom {
 // canon_config maps (s, q) to (sg R(Q_k) s, Q_k q Q_j) with k maximising
 // sg (R(Q_k) s) . u_ref (sg = +-1 from the sign when the inversion is in the
 // group, else 1) and j maximising |scalar(Q_k q Q_j)|; first maximum wins.
+// The same choice in closed form for the cube's group (the 24 rotations that
+// permute the axes with signs, and the inversion: all 48 signed axis
+// permutations M = sg R(Q_k)).  (M s) . u is largest for the M that sends
+// |s| sorted in decreasing order to (x, y, z) with signs that make them
+// non-negative; tab[8 perm + signs] holds Q_k of that M (perm: the axis
+// order, signs: bit a set when component perm[a] is negative).  Over the 24
+// rotations, |scalar(q1 Q_j)| takes the values |q_a|, (|q_a| + |q_b|)/sqrt 2
+// and (|q_0| + |q_1| + |q_2| + |q_3|)/2, so the best Q_j follows from the
+// sorted magnitudes of q1's components.  Where the maximum is unique this is
+// the element canon_config's scan finds.
+__device__ inline void canon_cube(const float4* __restrict__ tab, float3& s, float4& q, float4& qk,
+                                  float4& qj, float& sg) {
+    // stable sort of the axes by decreasing |s| (scalars and selects only)
+    float a0 = fabsf(s.x), a1 = fabsf(s.y), a2 = fabsf(s.z);
+    float v0 = s.x, v1 = s.y, v2 = s.z;
+    int i0 = 0, i1 = 1, i2 = 2;
+#define RB_CSWAP(A, B, VA, VB, IA, IB)                      \
+    if (B > A) {                                            \
+        const float ta = A, tv = VA;                        \
+        const int ti = IA;                                  \
+        A = B; VA = VB; IA = IB;                            \
+        B = ta; VB = tv; IB = ti;                           \
+    }
+    RB_CSWAP(a0, a1, v0, v1, i0, i1)
+    RB_CSWAP(a1, a2, v1, v2, i1, i2)
+    RB_CSWAP(a0, a1, v0, v1, i0, i1)
+    const int perm = i0 == 0 ? (i1 == 1 ? 0 : 1) : i0 == 1 ? (i1 == 0 ? 2 : 3) : (i1 == 0 ? 4 : 5);
+    const int signs = (v0 < 0.f ? 1 : 0) | (v1 < 0.f ? 2 : 0) | (v2 < 0.f ? 4 : 0);
+    // det M: parity of the permutation times the product of the signs
+    const int odd = (perm == 1 || perm == 2 || perm == 5) ? 1 : 0;
+    sg = ((odd + __popc(signs)) & 1) ? -1.f : 1.f;
+    qk = tab[8 * perm + signs];
+    s = make_float3(a0, a1, a2);
+    const float4 q1 = qmul(qk, q);
+    // the two largest |components| of q1 (indices o0, o1)
+    float m0 = fabsf(q1.x), m1 = fabsf(q1.y), m2 = fabsf(q1.z), m3 = fabsf(q1.w);
+    const float msum = m0 + m1 + m2 + m3;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;  // unused payloads of the sort
+    int o0 = 0, o1 = 1, o2 = 2, o3 = 3;
+    RB_CSWAP(m0, m1, d0, d1, o0, o1)
+    RB_CSWAP(m2, m3, d2, d3, o2, o3)
+    RB_CSWAP(m0, m2, d0, d2, o0, o2)
+    RB_CSWAP(m1, m3, d1, d3, o1, o3)
+    RB_CSWAP(m1, m2, d1, d2, o1, o2)
+#undef RB_CSWAP
+    const float sA = m0, sB = (m0 + m1) * 0.70710678f, sC = 0.5f * msum;
+    // conj(Q_j): the group element with the largest |q1 . e|, with the signs
+    // of q1's components on the positions it uses
+    const int type = (sA >= sB && sA >= sC) ? 0 : (sB >= sC ? 1 : 2);
+    const float mag = type == 0 ? 1.f : (type == 1 ? 0.70710678f : 0.5f);
+    auto comp = [&](int t, float c) {
+        const bool on = type == 2 || t == o0 || (type == 1 && t == o1);
+        return on ? (c < 0.f ? -mag : mag) : 0.f;
+    };
+    const float e0 = comp(0, q1.x), e1 = comp(1, q1.y), e2 = comp(2, q1.z), e3 = comp(3, q1.w);
+    qj = make_float4(e0, -e1, -e2, -e3);
+    // the group's sign convention: first non-zero component positive
+    const float lead = qj.x != 0.f ? qj.x : (qj.y != 0.f ? qj.y : (qj.z != 0.f ? qj.z : qj.w));
+    if (lead < 0.f) qj = make_float4(-qj.x, -qj.y, -qj.z, -qj.w);
+    q = qmul(q1, qj);
+}
+
 __device__ inline void canon_config(const float4* __restrict__ tab, int n, int inv, float3& s,
                                     float4& q, float4& qk, float4& qj, float& sg) {
     float best = -3.0e38f;
@@ -127,6 +191,15 @@ __device__ inline void canon_config(const float4* __restrict__ tab, int n, int i
     }
     qj = tab[3 * jb + 1];
     q = qmul(q1, qj);
+}
+
+// The canonical representative under the point group of a pair source.
+__device__ inline void canon_pair(const PairSrc& src, float3& s, float4& q, float4& qk, float4& qj,
+                                  float& sg) {
+    if (src.sym_cube)
+        canon_cube(src.sym, s, q, qk, qj, sg);
+    else
+        canon_config(src.sym, src.n_sym, src.sym_inv, s, q, qk, qj, sg);
 }
 
 // Raw pair data (the global loads), separated from the geometry so a kernel
@@ -181,7 +254,7 @@ __device__ inline PairGeom pair_geometry(const PairSrc& src, const PairRaw& r) {
             qr = r.b;
         }
         if (src.n_sym > 0) {
-            canon_config(src.sym, src.n_sym, src.sym_inv, g.s, qr, g.sym_qk, g.sym_qj, g.sym_sg);
+            canon_pair(src, g.s, qr, g.sym_qk, g.sym_qj, g.sym_sg);
             g.sym = true;
         }
         if (qr.x < 0.f) {
@@ -272,9 +345,9 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
 
 // symmetry.cu: canonical configurations and a tangent mapped with them
 // (cfg, ucfg: n x 2 float4 as rb_nn_weight_vjp takes them).
-__global__ void k_canon_tangent(int64_t n, const float4* __restrict__ tab, int n_sym, int inv,
-                                const float4* __restrict__ cfg, const float4* __restrict__ ucfg,
-                                float4* __restrict__ cfg_out, float4* __restrict__ u_out);
+__global__ void k_canon_tangent(int64_t n, PairSrc sym, const float4* __restrict__ cfg,
+                                const float4* __restrict__ ucfg, float4* __restrict__ cfg_out,
+                                float4* __restrict__ u_out);
 
 // The bead-fallback list of a system into a pair destination (and its count
 // reset), when the system has a fallback separation.
@@ -293,9 +366,10 @@ inline rb_status set_fallback(PairDst& dst, rb_system* s) {
 
 // The network's point group into a pair source.
 inline void set_symmetry(PairSrc& src, const rb_mlp* m) {
-    src.sym = m->sym_dev;
+    src.sym = m->sym_cube ? m->sym_dev + 3 * 24 : m->sym_dev;
     src.n_sym = m->n_sym;
     src.sym_inv = m->sym_inv;
+    src.sym_cube = m->sym_cube;
 }
 
 // nn.cu

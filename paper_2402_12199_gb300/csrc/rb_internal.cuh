@@ -150,8 +150,9 @@ struct rb_mlp {
     uint64_t version = 1;         // bumped on every set_params
     // point group of the bodies (symmetry-reduced configurations): device
     // table of 3 float4 per rotation (see canon_config), n_sym = 0: none
-    float4* sym_dev = nullptr;
+    float4* sym_dev = nullptr;     // 3 x 24 float4 (generic table) + 48 float4 (cube table)
     int n_sym = 0, sym_inv = 0;
+    int sym_cube = 0;              // the group is the cube's: closed-form choice
 };
 
 struct rb_system {

@@ -131,8 +131,8 @@ bool maps_onto(const float* xyz, int n, const Rot* r, bool invert) {
     return true;
 }
 
-__global__ void k_nn_canonical(int64_t n, const float4* __restrict__ tab, int n_sym, int inv,
-                               float4* __restrict__ cfg, float4* __restrict__ lab) {
+__global__ void k_nn_canonical(int64_t n, PairSrc sym, float4* __restrict__ cfg,
+                               float4* __restrict__ lab) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= n) return;
     const float4 c0 = cfg[2 * b];
@@ -140,7 +140,7 @@ __global__ void k_nn_canonical(int64_t n, const float4* __restrict__ tab, int n_
     float4 q = cfg[2 * b + 1];
     float4 qk, qj;
     float sg;
-    canon_config(tab, n_sym, inv, s, q, qk, qj, sg);
+    canon_pair(sym, s, q, qk, qj, sg);
     cfg[2 * b] = make_float4(s.x, s.y, s.z, c0.w);
     cfg[2 * b + 1] = q;
     if (lab) {  // F_j' = sg R F_j, tau' = R tau
@@ -159,9 +159,9 @@ __global__ void k_nn_canonical(int64_t n, const float4* __restrict__ tab, int n_
 
 // (cfg', u') = canonical configurations and the tangent u mapped with them:
 // u_s' = sg R(Q_k) u_s, u_q' = Q_k u_q Q_j (the map is linear in (s, q)).
-__global__ void k_canon_tangent(int64_t n, const float4* __restrict__ tab, int n_sym, int inv,
-                                const float4* __restrict__ cfg, const float4* __restrict__ ucfg,
-                                float4* __restrict__ cfg_out, float4* __restrict__ u_out) {
+__global__ void k_canon_tangent(int64_t n, PairSrc sym, const float4* __restrict__ cfg,
+                                const float4* __restrict__ ucfg, float4* __restrict__ cfg_out,
+                                float4* __restrict__ u_out) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= n) return;
     const float4 c0 = cfg[2 * b];
@@ -169,7 +169,7 @@ __global__ void k_canon_tangent(int64_t n, const float4* __restrict__ tab, int n
     float4 q = cfg[2 * b + 1];
     float4 qk, qj;
     float sg;
-    canon_config(tab, n_sym, inv, s, q, qk, qj, sg);
+    canon_pair(sym, s, q, qk, qj, sg);
     cfg_out[2 * b] = make_float4(s.x, s.y, s.z, 0.f);
     cfg_out[2 * b + 1] = q;
     const float4 u0 = ucfg[2 * b];
@@ -215,6 +215,7 @@ rb_status rb_mlp_set_symmetry(rb_mlp* m, const float* quats, int32_t n, int32_t 
     if (n == 0) {
         m->n_sym = 0;
         m->sym_inv = 0;
+        m->sym_cube = 0;
         m->version++;
         return RB_OK;
     }
@@ -236,12 +237,47 @@ rb_status rb_mlp_set_symmetry(rb_mlp* m, const float* quats, int32_t n, int32_t 
         tab[3 * k + 1] = make_float4((float)w, (float)x, (float)y, (float)z);
         tab[3 * k + 2] = make_float4((float)w, (float)-x, (float)-y, (float)-z);
     }
-    if (!m->sym_dev) RB_CUDA(cudaMalloc(&m->sym_dev, sizeof(float4) * 3 * 24));
+    // The cube's group (the 24 signed axis permutations of determinant +1, with
+    // the inversion) takes the closed-form choice: table of Q_k for every
+    // signed permutation M = sg R(Q_k), indexed 8 perm + signs as in canon_cube.
+    bool cube = inversion && n == 24;
+    std::vector<Rot> rots = candidates();
+    for (int k = 0; k < n && cube; ++k) {
+        bool found = false;
+        for (int r = 0; r < 24 && !found; ++r) {
+            double qc[4];
+            to_quat(rots[r], qc);
+            double d = 0.0;
+            for (int c = 0; c < 4; ++c) d += qc[c] * quats[4 * k + c];
+            found = std::fabs(std::fabs(d) - 1.0) < 1e-5;
+        }
+        cube = found;
+    }
+    std::vector<float4> cube_tab(48);
+    if (cube) {
+        const int orders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+        for (int p = 0; p < 6; ++p)
+            for (int sgn = 0; sgn < 8; ++sgn) {
+                Rot M{};
+                for (int r = 0; r < 3; ++r) M.m[3 * r + orders[p][r]] = (sgn >> r) & 1 ? -1.0 : 1.0;
+                const double det = M.m[0] * (M.m[4] * M.m[8] - M.m[5] * M.m[7]) -
+                                   M.m[1] * (M.m[3] * M.m[8] - M.m[5] * M.m[6]) +
+                                   M.m[2] * (M.m[3] * M.m[7] - M.m[4] * M.m[6]);
+                for (double& x : M.m) x *= det;  // the proper rotation sg M
+                double q[4];
+                to_quat(M, q);
+                cube_tab[8 * p + sgn] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+            }
+    }
+    if (!m->sym_dev) RB_CUDA(cudaMalloc(&m->sym_dev, sizeof(float4) * (3 * 24 + 48)));
     RB_CUDA(cudaMemcpyAsync(m->sym_dev, tab.data(), sizeof(float4) * 3 * n, cudaMemcpyHostToDevice,
                             m->stream));
-    RB_CUDA(cudaStreamSynchronize(m->stream));  // tab is a host temporary
+    RB_CUDA(cudaMemcpyAsync(m->sym_dev + 3 * 24, cube_tab.data(), sizeof(float4) * 48,
+                            cudaMemcpyHostToDevice, m->stream));
+    RB_CUDA(cudaStreamSynchronize(m->stream));  // the tables are host temporaries
     m->n_sym = n;
     m->sym_inv = inversion ? 1 : 0;
+    m->sym_cube = cube ? 1 : 0;
     m->version++;  // captured step graphs hold the old table arguments
     return RB_OK;
 }
@@ -252,8 +288,9 @@ rb_status rb_nn_canonical(const rb_mlp* m, int64_t n, float* cfg, float* labels)
     if (n == 0 || m->n_sym == 0) return RB_OK;
     const int threads = 256;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-    k_nn_canonical<<<blocks, threads, 0, m->stream>>>(n, m->sym_dev, m->n_sym, m->sym_inv,
-                                                      reinterpret_cast<float4*>(cfg),
+    PairSrc sym{};
+    set_symmetry(sym, m);
+    k_nn_canonical<<<blocks, threads, 0, m->stream>>>(n, sym, reinterpret_cast<float4*>(cfg),
                                                       reinterpret_cast<float4*>(labels));
     RB_CUDA(cudaGetLastError());
     return RB_OK;

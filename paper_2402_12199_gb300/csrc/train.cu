@@ -399,7 +399,9 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
     const float* flat = m->params;
     RB_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * m->n_params, st));
     if (m->n_sym > 0) {  // the network sees canonical configurations: map cfg and u
-        k_canon_tangent<<<nblk(B), 256, 0, st>>>(B, m->sym_dev, m->n_sym, m->sym_inv, cfg, ucfg,
+        PairSrc sym{};
+        set_symmetry(sym, m);
+        k_canon_tangent<<<nblk(B), 256, 0, st>>>(B, sym, cfg, ucfg,
                                                  reinterpret_cast<float4*>(w.cfg_c),
                                                  reinterpret_cast<float4*>(w.ucfg_c));
         cfg = reinterpret_cast<const float4*>(w.cfg_c);

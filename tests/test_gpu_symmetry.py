@@ -59,13 +59,18 @@ def _safe_configs(n, seed, group, rho=(5.0, 9.4)):
     return c7, c8
 
 
-@pytest.mark.parametrize("shape", ["cube", "cylinder"])
+@pytest.mark.parametrize("shape", ["cube", "cylinder", "cube rotations only"])
 def test_canonical_matches_oracle(shape):
+    """The cube's full group takes the library's closed-form choice; the
+    cylinder's group and the cube's rotations without the inversion take the
+    scan over the group's table."""
     import torch
 
     from paper_2402_12199_gb300 import api
 
-    group = _group(shape)
+    group = _group("cylinder" if shape == "cylinder" else "cube")
+    if shape == "cube rotations only":
+        group = (group[0], False)
     m = api.MLP(64, 3)
     m.set_params(inputs.mlp_params(64, 3, 1))
     m.set_symmetry(group[0].astype(np.float32), group[1])
