@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
     // 8 floats per column and 8 more (at most kMaxBeads / 5 columns)
     constexpr int kSN = C == 0 ? 2 * (kMaxBeads + kPadBeads) : kMaxBeads / 5 + 1 + 2 * (kMaxBeads / 5 + 2);
     __shared__ float4 sN[kSN];
+    pdl_wait();
     if (C == 0) {
         load_template(tmpl, n_beads, pot.rc2_test, sT, sN);
     } else {
@@ -127,10 +128,10 @@ static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, const i
     const float3 L = make_float3(s->box[0], s->box[1], s->box[2]);
     const float3 invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
     const int grid = s->num_sms * occ;
-    k_bead_pairs<NP, C><<<grid, 256, 0, s->stream>>>(
-        s->pl.pairs, s->pl.n_pairs, s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL,
-        bead_pot(s), cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, sel, s->fallback_count);
-    RB_CUDA(cudaGetLastError());
+    RB_CUDA(launch_pdl(k_bead_pairs<NP, C>, grid, 256, 0, s->stream, s->pl.pairs, s->pl.n_pairs,
+                       s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL, bead_pot(s),
+                       cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, sel,
+                       s->fallback_count));
     return RB_OK;
 }
 

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     constexpr int NS = kF32Threads / P;     // unit slices of the dE/dx reduction
     static_assert(NG * 8 == W, "register blocks must tile the layer width");
     static_assert(NS * kIn * P <= W * P, "dE/dx partial sums must fit in the activation buffer");
+    pdl_wait();
     const int D = net.D;
     using Feed = ChunkFeed<W, KC>;
     float* Zs = smem;                          // D x [W][P]: silu'(z_l), then G_l
@@ -408,7 +409,11 @@ static rb_status launch_f32(const rb_mlp* m, cudaStream_t stream, int num_sms, c
     net.pl = f32_layout(m->width, m->depth);
     net.W = m->width;
     net.D = m->depth;
-    k_nn_f32<W, P, KC, SYSTEM><<<num_sms, kF32Threads, smem, stream>>>(net, src, dst);
+    if (SYSTEM)  // inside an MD step: may start while the list kernels drain
+        RB_CUDA(launch_pdl(k_nn_f32<W, P, KC, SYSTEM>, num_sms, kF32Threads, smem, stream, net,
+                           src, dst));
+    else
+        k_nn_f32<W, P, KC, SYSTEM><<<num_sms, kF32Threads, smem, stream>>>(net, src, dst);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }

@@ -360,7 +360,7 @@ inline rb_status set_fallback(PairDst& dst, rb_system* s) {
     dst.fb_list = s->fb_list;
     dst.fb_count = s->fallback_count;
     dst.fb_rho2 = r * r;
-    RB_CUDA(cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream));
+    RB_CUDA(launch_pdl(k_zero_count, 1, 1, 0, s->stream, s->fallback_count));
     return RB_OK;
 }
 

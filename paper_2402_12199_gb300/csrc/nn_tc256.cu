@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    pdl_wait();  // weights staged; pair data below may come from the kernels just before
     fence_proxy_async();
     fence_before();
     __syncthreads();
@@ -344,8 +345,14 @@ rb_status launch_tc256(const rb_mlp* m, cudaStream_t stream, int grid, const Pai
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr[SYSTEM ? 1 : 0] = true;
     }
-    tc256::k_nn_tc256<SYSTEM><<<grid, tc256::kThreads, smem, stream>>>(
-        m->params, static_cast<const unsigned char*>(m->bf16_img), m->depth, src, dst, status);
+    if (SYSTEM)  // inside an MD step: may start while the list kernels drain
+        RB_CUDA(launch_pdl(tc256::k_nn_tc256<SYSTEM>, grid, tc256::kThreads, smem, stream,
+                           m->params, static_cast<const unsigned char*>(m->bf16_img), m->depth,
+                           src, dst, status));
+    else
+        tc256::k_nn_tc256<SYSTEM><<<grid, tc256::kThreads, smem, stream>>>(
+            m->params, static_cast<const unsigned char*>(m->bf16_img), m->depth, src, dst,
+            status);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }

@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    pdl_wait();  // weights staged; pair data below may come from the kernels just before
     fence_proxy_async();
     fence_before();
     __syncthreads();
@@ -279,8 +280,12 @@ rb_status launch_tc2p(const rb_mlp* m, cudaStream_t stream, int grid, const Pair
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr[SYSTEM ? 1 : 0] = true;
     }
-    tc2p::k_nn_tc2p<SYSTEM><<<grid, tc2p::kThreads, smem, stream>>>(
-        m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status);
+    if (SYSTEM)  // inside an MD step: may start while the list kernels drain
+        RB_CUDA(launch_pdl(tc2p::k_nn_tc2p<SYSTEM>, grid, tc2p::kThreads, smem, stream, m->params,
+                           static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status));
+    else
+        tc2p::k_nn_tc2p<SYSTEM><<<grid, tc2p::kThreads, smem, stream>>>(
+            m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }

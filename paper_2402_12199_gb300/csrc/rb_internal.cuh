@@ -38,6 +38,29 @@ enum : unsigned {
 
 constexpr int kMaxBeads = 256;
 
+// Programmatic dependent launch: the kernels of an MD step are launched so
+// that each may start while its predecessor drains (launch_pdl); every such
+// kernel calls pdl_wait() before it touches anything an earlier kernel wrote,
+// which returns once the preceding grids have completed and their writes are
+// visible.  Without the launch attribute the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Column structure of a bead template: the beads fall into n_cols groups of
 // len beads with equal (x, y), and every group holds the same z values z[0..len)
 // (cube 5x5x5: 25 columns of 5; cylinder: 19 hexagonal sites x 8 layers).
@@ -210,6 +233,7 @@ rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
 rb_status energy_async(rb_system* s);
 // beads.cu
 rb_status bead_pairs_async(rb_system* s);
+__global__ void k_zero_count(int* count);  // *count = 0 after pdl_wait (system.cu)
 rb_status bead_fallback_async(rb_system* s);  // bead sum for pairs with rho < nn_fallback_rho
 // nn.cu
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision);

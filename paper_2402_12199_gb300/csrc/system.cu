@@ -42,6 +42,7 @@ __global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, f
                               float3 invw, int3 nc, int* __restrict__ count,
                               int* __restrict__ bodies, int cap, unsigned* status,
                               const int* __restrict__ rebuild) {
+    pdl_wait();
     if (!*rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -83,68 +84,71 @@ __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, fl
                              int* __restrict__ half_count, int* __restrict__ half_nbr,
                              int* __restrict__ lower_count, int* __restrict__ lower_nbr,
                              unsigned* status, const int* __restrict__ rebuild) {
+    pdl_wait();
     if (!*rebuild) return;
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= N) return;
-    const float4 p = pos[i];
-    const float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
-    const int c[3] = {min(max(int(x * invw.x), 0), nc.x - 1), min(max(int(y * invw.y), 0), nc.y - 1),
-                      min(max(int(z * invw.z), 0), nc.z - 1)};
-    const int n_[3] = {nc.x, nc.y, nc.z};
-    const int off[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-    bool active = lane < 27;
-    int cell = 0;
-    for (int a = 2; a >= 0; --a) {
-        const int o = off[a];
-        if (n_[a] == 1 && o != 0) active = false;
-        if (n_[a] == 2 && o == -1) active = false;
-        cell = cell * n_[a] + (c[a] + o + n_[a]) % n_[a];
-    }
-    const int n = active ? min(count[cell], cap) : 0;
-    int nmax = n;
-    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-    int* hrow = half_nbr + (size_t)i * max_nbr;
-    int* lrow = lower_nbr + (size_t)i * max_nbr;
-    int nh = 0, nl = 0;
-    const unsigned lt = (1u << lane) - 1u;
-    const int* cb = bodies + (size_t)cell * cap;
-    for (int s = 0; s < nmax; ++s) {
-        int j = -1;
-        bool hit = false;
-        if (s < n) {
-            j = cb[s];
-            if (j != i) {
-                const float4 q = pos[j];
-                const float3 d = min_image(make_float3(q.x - p.x, q.y - p.y, q.z - p.z), L, invL);
-                hit = d.x * d.x + d.y * d.y + d.z * d.z < Rc2;
+    // a warp per body, grid-stride (one wave of CTAs: cheap when no rebuild is due)
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
+        const float4 p = pos[i];
+        const float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
+        const int c[3] = {min(max(int(x * invw.x), 0), nc.x - 1), min(max(int(y * invw.y), 0), nc.y - 1),
+                          min(max(int(z * invw.z), 0), nc.z - 1)};
+        const int n_[3] = {nc.x, nc.y, nc.z};
+        const int off[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        bool active = lane < 27;
+        int cell = 0;
+        for (int a = 2; a >= 0; --a) {
+            const int o = off[a];
+            if (n_[a] == 1 && o != 0) active = false;
+            if (n_[a] == 2 && o == -1) active = false;
+            cell = cell * n_[a] + (c[a] + o + n_[a]) % n_[a];
+        }
+        const int n = active ? min(count[cell], cap) : 0;
+        int nmax = n;
+        for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        int* hrow = half_nbr + (size_t)i * max_nbr;
+        int* lrow = lower_nbr + (size_t)i * max_nbr;
+        int nh = 0, nl = 0;
+        const unsigned lt = (1u << lane) - 1u;
+        const int* cb = bodies + (size_t)cell * cap;
+        for (int s = 0; s < nmax; ++s) {
+            int j = -1;
+            bool hit = false;
+            if (s < n) {
+                j = cb[s];
+                if (j != i) {
+                    const float4 q = pos[j];
+                    const float3 d = min_image(make_float3(q.x - p.x, q.y - p.y, q.z - p.z), L, invL);
+                    hit = d.x * d.x + d.y * d.y + d.z * d.z < Rc2;
+                }
             }
+            const unsigned bh = __ballot_sync(0xffffffffu, hit && j > i);
+            const unsigned bl = __ballot_sync(0xffffffffu, hit && j < i);
+            if (hit && j > i) {
+                const int k = nh + __popc(bh & lt);
+                if (k < max_nbr) hrow[k] = j;
+            }
+            if (hit && j < i) {
+                const int k = nl + __popc(bl & lt);
+                if (k < max_nbr) lrow[k] = j;
+            }
+            nh += __popc(bh);
+            nl += __popc(bl);
         }
-        const unsigned bh = __ballot_sync(0xffffffffu, hit && j > i);
-        const unsigned bl = __ballot_sync(0xffffffffu, hit && j < i);
-        if (hit && j > i) {
-            const int k = nh + __popc(bh & lt);
-            if (k < max_nbr) hrow[k] = j;
+        if (nh + nl > max_nbr) {
+            if (lane == 0) atomicOr(status, ST_NBR_OVERFLOW);
+            nh = min(nh, max_nbr);
+            nl = min(nl, max_nbr);
         }
-        if (hit && j < i) {
-            const int k = nl + __popc(bl & lt);
-            if (k < max_nbr) lrow[k] = j;
+        __syncwarp();
+        if (lane == 0) {
+            sort_row(hrow, nh);
+            half_count[i] = nh;
+        } else if (lane == 1) {
+            sort_row(lrow, nl);
+            lower_count[i] = nl;
         }
-        nh += __popc(bh);
-        nl += __popc(bl);
-    }
-    if (nh + nl > max_nbr) {
-        if (lane == 0) atomicOr(status, ST_NBR_OVERFLOW);
-        nh = min(nh, max_nbr);
-        nl = min(nl, max_nbr);
-    }
-    __syncwarp();
-    if (lane == 0) {
-        sort_row(hrow, nh);
-        half_count[i] = nh;
-    } else if (lane == 1) {
-        sort_row(lrow, nl);
-        lower_count[i] = nl;
     }
 }
 
@@ -156,6 +160,7 @@ constexpr int kScanBlock = 1024;
 
 __global__ void k_scan_local(const int* __restrict__ cnt, int N, int* __restrict__ local_off,
                              int* __restrict__ block_sum, const int* __restrict__ rebuild) {
+    pdl_wait();
     if (!*rebuild) return;
     __shared__ int warp_tot[32];
     const int i = blockIdx.x * kScanBlock + threadIdx.x;
@@ -185,6 +190,7 @@ __global__ void k_scan_local(const int* __restrict__ cnt, int N, int* __restrict
 __global__ void k_scan_top(int* __restrict__ block_sum, int nb, int N, int* __restrict__ half_off,
                            int* total, int64_t cap_pairs, unsigned* status,
                            const int* __restrict__ rebuild) {
+    pdl_wait();
     if (!*rebuild) return;
     __shared__ int sh[1024];
     const int t = threadIdx.x;
@@ -225,6 +231,7 @@ __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_cou
                             const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
                             int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status,
                             const int* __restrict__ rebuild) {
+    pdl_wait();
     if (!*rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -261,6 +268,7 @@ __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_cou
 __global__ void k_pair_finish(int N, int n_cells, const float4* __restrict__ pos,
                               float4* __restrict__ pos_ref, int* __restrict__ cell_count,
                               int* rebuild) {
+    pdl_wait();
     if (!*rebuild) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < N) pos_ref[t] = pos[t];
@@ -270,8 +278,15 @@ __global__ void k_pair_finish(int N, int n_cells, const float4* __restrict__ pos
     // the build in stream order, so clear it in a separate one-thread kernel
 }
 
-__global__ void k_flag_clear(int* rebuild) { *rebuild = 0; }
+__global__ void k_flag_clear(int* rebuild) {
+    pdl_wait();
+    *rebuild = 0;
+}
 __global__ void k_flag_set(int* rebuild) { *rebuild = 1; }
+__global__ void k_zero_count(int* count) {
+    pdl_wait();
+    *count = 0;
+}
 
 // Raise the rebuild flag if any centre moved more than half the skin since the
 // positions the list was built for (minimum image).
@@ -297,6 +312,7 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
                          float4* __restrict__ force, float4* __restrict__ torque, float kick,
                          float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
                          const float4* __restrict__ quat, unsigned* status) {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t >> 2, sub = t & 3;
     const bool live = i < N;
@@ -366,6 +382,7 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
                                   const float4* __restrict__ torque,
                                   const float4* __restrict__ pos_ref, float half_skin2,
                                   int* rebuild) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float h = 0.5f * dt;
@@ -506,37 +523,38 @@ rb_status build_pairs_async(rb_system* s, bool force, bool checked) {
         k_skin_check<<<blocks_for(N, 256), 256, 0, s->stream>>>(
             N, 0.25f * s->skin * s->skin, L, invL, s->pos, s->pos_ref, s->rebuild_flag);
     }
-    k_cell_assign<<<blocks_for(N, 256), 256, 0, s->stream>>>(s->pos, N, L, invL, invw, nc,
-                                                             s->cells.count, s->cells.bodies,
-                                                             s->cells.cap, s->status_dev,
-                                                             s->rebuild_flag);
-    k_pair_build<<<blocks_for((int64_t)N * 32, 256), 256, 0, s->stream>>>(
-        s->pos, N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap, Rl * Rl,
-        s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.lower_count, s->pl.lower_nbr,
-        s->status_dev, s->rebuild_flag);
+    RB_CUDA(launch_pdl(k_cell_assign, blocks_for(N, 256), 256, 0, s->stream, s->pos, N, L, invL,
+                       invw, nc, s->cells.count, s->cells.bodies, s->cells.cap, s->status_dev,
+                       s->rebuild_flag));
+    RB_CUDA(launch_pdl(k_pair_build, std::min(blocks_for((int64_t)N * 32, 256), s->num_sms * 8),
+                       256, 0, s->stream, s->pos,
+                       N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap,
+                       Rl * Rl, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr,
+                       s->pl.lower_count, s->pl.lower_nbr, s->status_dev, s->rebuild_flag));
     const int nb = (N + kScanBlock - 1) / kScanBlock;
-    k_scan_local<<<nb, kScanBlock, 0, s->stream>>>(s->pl.half_count, N, s->pl.local_off,
-                                                   s->pl.block_sum, s->rebuild_flag);
-    k_scan_top<<<1, 1024, 0, s->stream>>>(s->pl.block_sum, nb, N, s->pl.half_off, s->pl.n_pairs,
-                                          s->pl.cap_pairs, s->status_dev, s->rebuild_flag);
-    k_pair_emit<<<blocks_for(N, 256), 256, 0, s->stream>>>(
-        N, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr, s->pl.local_off, s->pl.block_sum,
-        s->pl.half_off, s->pl.lower_count, s->pl.lower_nbr, s->pl.pairs, s->pl.cap_pairs,
-        s->status_dev, s->rebuild_flag);
-    k_pair_finish<<<blocks_for(std::max(N, s->cells.n_cells), 256), 256, 0, s->stream>>>(
-        N, s->cells.n_cells, s->pos, s->pos_ref, s->cells.count, s->rebuild_flag);
-    k_flag_clear<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+    RB_CUDA(launch_pdl(k_scan_local, nb, kScanBlock, 0, s->stream, s->pl.half_count, N,
+                       s->pl.local_off, s->pl.block_sum, s->rebuild_flag));
+    RB_CUDA(launch_pdl(k_scan_top, 1, 1024, 0, s->stream, s->pl.block_sum, nb, N, s->pl.half_off,
+                       s->pl.n_pairs, s->pl.cap_pairs, s->status_dev, s->rebuild_flag));
+    RB_CUDA(launch_pdl(k_pair_emit, blocks_for(N, 256), 256, 0, s->stream, N, s->pl.max_nbr,
+                       s->pl.half_count, s->pl.half_nbr, s->pl.local_off, s->pl.block_sum,
+                       s->pl.half_off, s->pl.lower_count, s->pl.lower_nbr, s->pl.pairs,
+                       s->pl.cap_pairs, s->status_dev, s->rebuild_flag));
+    RB_CUDA(launch_pdl(k_pair_finish, blocks_for(std::max(N, s->cells.n_cells), 256), 256, 0,
+                       s->stream, N, s->cells.n_cells, s->pos, s->pos_ref, s->cells.count,
+                       s->rebuild_flag));
+    RB_CUDA(launch_pdl(k_flag_clear, 1, 1, 0, s->stream, s->rebuild_flag));
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
 
 rb_status reduce_forces_async(rb_system* s, float kick) {
     const int N = (int)s->N;
-    k_reduce<<<blocks_for((int64_t)N * 4, 256), 256, 0, s->stream>>>(
-        N, s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count, s->pl.lower_count,
-        s->pl.lower_nbr,
-        s->pair_F, s->pair_ti, s->pair_tj, s->force, s->torque, kick, 1.f / s->mass, s->vel,
-        s->angmom, s->quat, s->status_dev);
+    RB_CUDA(launch_pdl(k_reduce, blocks_for((int64_t)N * 4, 256), 256, 0, s->stream, N,
+                       s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count,
+                       s->pl.lower_count, s->pl.lower_nbr, s->pair_F, s->pair_ti, s->pair_tj,
+                       s->force, s->torque, kick, 1.f / s->mass, s->vel, s->angmom, s->quat,
+                       s->status_dev));
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -1001,12 +1019,13 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
             return cuda_fail(be, "cudaStreamBeginCapture");
         }
         const int N = (int)s->N;
-        k_integrate_first<<<blocks_for(N, 256), 256, 0, s->stream>>>(
-            N, dt, 1.f / s->mass,
+        const cudaError_t le = launch_pdl(
+            k_integrate_first, blocks_for(N, 256), 256, 0, s->stream, N, dt, 1.f / s->mass,
             make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
             f3(s->box), inv3(s->box), s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
             s->pos_ref, s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f, s->rebuild_flag);
-        rb_status st = eval_forces_async(s, path, m, precision, 0.5f * dt, true);
+        rb_status st = le == cudaSuccess ? eval_forces_async(s, path, m, precision, 0.5f * dt, true)
+                                         : cuda_fail(le, "k_integrate_first");
         cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
         s->stream = user;
         if (st != RB_OK) {
