@@ -262,6 +262,56 @@ def cpu_baseline(st, L, flat, n_sample):
             "pairs": int(len(pairs)), "t_bead_s": t_bead, "t_nn_s": t_nn}
 
 
+_CPU_STATE = {}
+
+
+def _cpu_worker_init(pos, quat, box, flat):
+    import torch
+
+    from oracle import bodies, nn
+
+    torch.set_num_threads(1)
+    _CPU_STATE.update(pos=pos, quat=quat, box=box, tmpl=bodies.cube_template(),
+                      p=nn.unpack(np.asarray(flat, np.float64), WIDTH, DEPTH))
+
+
+def _cpu_worker_ping(_):
+    return os.getpid()
+
+
+def _cpu_worker_pairs(pairs):
+    import oracle
+    from oracle import nn
+
+    c = _CPU_STATE
+    oracle.forces_beads(c["pos"], c["quat"], c["box"], c["tmpl"], pairs)
+    nn.forces_nn(c["p"], c["pos"], c["quat"], c["box"], pairs)
+    return len(pairs)
+
+
+def cpu_baseline_parallel(st, L, flat, n_sample, workers):
+    """The same oracle calls on the same sample, split into chunks over a pool
+    of `workers` processes (started with spawn, after the GPU work): a timing
+    wrapper only, the oracle code is unchanged."""
+    import multiprocessing as mp
+
+    cpu_baseline(st, L, flat, n_sample)  # fills the sample cache
+    pairs = _PAIR_CACHE[(id(st), n_sample)]
+    pos = st["pos"][:, :3].astype(np.float64)
+    quat = st["quat"].astype(np.float64)
+    chunks = np.array_split(pairs, 4 * workers)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_cpu_worker_init,
+                  initargs=(pos, quat, np.array([L] * 3), flat)) as pool:
+        pool.map(_cpu_worker_ping, range(4 * workers))  # workers up and initialised
+        t0 = time.perf_counter()
+        done = sum(pool.map(_cpu_worker_pairs, chunks, chunksize=1))
+        t = time.perf_counter() - t0
+    return {"value": 2 * done / t, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"the same {done} body pairs, bead sum and network, in {len(chunks)} "
+                      f"chunks over {workers} spawned processes (one thread each)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -601,6 +651,11 @@ def main():
                "sample": f"{cb['pairs']} body pairs of the workload, bead sum and network "
                          f"(FP64, single thread)", "bead_pairs_per_s": cb["bead_pairs_per_s"],
                "nn_pairs_per_s": cb["nn_pairs_per_s"]}
+        try:
+            cpu["all_cores"] = cpu_baseline_parallel(st, L, flat, args.cpu_sample_pairs,
+                                                     os.cpu_count() or 1)
+        except Exception as ex:  # reported, not fatal: the single-thread number stands
+            cpu["all_cores"] = {"error": repr(ex)}
 
     clocks = clk.summary()
     path_info = {}
