@@ -119,7 +119,10 @@ rb_status rb_body_template(const rb_system* sys, float* xyz_host);
  * are host memory.  Invalidates cached forces. */
 rb_status rb_set_state(rb_system* sys, const float* pos, const float* quat, const float* vel,
                        const float* angmom, int32_t from_host);
-/* Copy the state out; any pointer may be NULL. */
+/* Copy the state out; any pointer may be NULL.  to_host: 0 device pointers;
+ * 1 host pointers, returns after the copies completed; 2 host pointers (page-
+ * locked for overlap), returns after queueing the copies on the system's
+ * stream: the caller synchronises that stream before reading them. */
 rb_status rb_get_state(const rb_system* sys, float* pos, float* quat, float* vel, float* angmom,
                        int32_t to_host);
 /* Copy out the forces/torques of the last evaluation (float4 rows). */

@@ -111,15 +111,21 @@ class System:
         ptrs = [(a.ctypes.data if host else a) if a is not None else None for a, _ in arrs]
         check(load().rb_set_state(self._h, *ptrs, host))
 
-    def get_state(self, to_host: bool = False):
-        if to_host:
-            out = {k: np.zeros((self.N, 4), dtype=np.float32) for k in ("pos", "quat", "vel", "angmom")}
-            ptrs = [out[k].ctypes.data for k in ("pos", "quat", "vel", "angmom")]
+    def get_state(self, to_host: bool = False, out: dict = None, sync: bool = True):
+        """rb_get_state.  `out`: preallocated tensors (page-locked host tensors
+        with to_host) to fill; with to_host and sync=False the copies are only
+        queued on the system's stream (rb_get_state's to_host = 2)."""
+        keys = ("pos", "quat", "vel", "angmom")
+        if out is not None:
+            ptrs = [out[k].data_ptr() for k in keys]
+        elif to_host:
+            out = {k: np.zeros((self.N, 4), dtype=np.float32) for k in keys}
+            ptrs = [out[k].ctypes.data for k in keys]
         else:
-            out = {k: torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
-                   for k in ("pos", "quat", "vel", "angmom")}
-            ptrs = [out[k].data_ptr() for k in ("pos", "quat", "vel", "angmom")]
-        check(load().rb_get_state(self._h, *ptrs, 1 if to_host else 0))
+            out = {k: torch.empty((self.N, 4), dtype=torch.float32, device="cuda") for k in keys}
+            ptrs = [out[k].data_ptr() for k in keys]
+        mode = (1 if sync else 2) if to_host else 0
+        check(load().rb_get_state(self._h, *ptrs, mode))
         return out
 
     def get_forces(self):

@@ -872,7 +872,7 @@ rb_status rb_get_state(const rb_system* s, float* pos, float* quat, float* vel, 
     if (quat) RB_CUDA(cudaMemcpyAsync(quat, s->quat, b, k, s->stream));
     if (vel) RB_CUDA(cudaMemcpyAsync(vel, s->vel, b, k, s->stream));
     if (angmom) RB_CUDA(cudaMemcpyAsync(angmom, s->angmom, b, k, s->stream));
-    if (to_host) RB_CUDA(cudaStreamSynchronize(s->stream));
+    if (to_host == 1) RB_CUDA(cudaStreamSynchronize(s->stream));
     return RB_OK;
 }
 

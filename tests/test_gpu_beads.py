@@ -275,3 +275,23 @@ def test_checkpoint_restore_continues_bit_for_bit(tmp_path):
     c = api.System(999, [L] * 3, "cube")
     with pytest.raises(api.RBError):
         c.restore(path)
+
+
+def test_state_read_back_asynchronously_into_pinned_memory():
+    """rb_get_state with to_host = 2 queues the copies; after a stream
+    synchronisation the page-locked buffers hold the same state as a
+    synchronous read."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    st, L, tmpl = make_state(300, 0.15, 61)
+    s = gpu_system(st, L)
+    s.forces_beads()
+    s.step(3, 0.002, path=api.RB_PATH_BEADS)
+    out = {k: torch.full((300, 4), float("nan")).pin_memory() for k in ("pos", "quat", "vel", "angmom")}
+    s.get_state(to_host=True, out=out, sync=False)
+    torch.cuda.synchronize()
+    ref = s.get_state(to_host=True)
+    for k in out:
+        np.testing.assert_array_equal(out[k].numpy(), ref[k])
