@@ -185,10 +185,9 @@ rb_status rb_get_step(const rb_system* sys, int64_t* step_host);
  * (capacity overflow, non-finite values). */
 rb_status rb_sync(rb_system* sys);
 
-/* Bead-sum forces for callers that cannot allocate device memory (code running
- * where cudaMalloc is forbidden or unsafe, such as inside a stream capture
- * that must not allocate, host programs that own the whole device memory
- * pool, or real-time loops that cannot risk an allocation stall).  The paper
+/* Bead-sum forces for callers that cannot allocate device memory (plug-ins of
+ * host programs that own the whole device memory pool, or real-time loops
+ * that cannot risk an allocation stall or failure mid-run).  The paper
  * has no counterpart: this is the same computation as rb_forces_beads without
  * an rb_system object and without any allocation.
  *   shape: RB_SHAPE_CUBE or RB_SHAPE_CYLINDER (built-in templates, unit bead
@@ -199,9 +198,10 @@ rb_status rb_sync(rb_system* sys);
  * Working memory is a fixed ~3.4 MB device array inside the library, held by
  * every GPU that loads it until the process exits; at most 32 neighbours per
  * body (RB_EOVERFLOW beyond).  Sizes beyond these limits return RB_EINVAL.
- * The first call on each device looks up that array's device address.  All
- * calls share the array, so calls that overlap on the GPU race: order them on
- * one stream.  Synchronises `cuda_stream` before returning. */
+ * The first call on each device (with that device current) looks up that
+ * array's device address; make it before any stream capture begins.  All calls
+ * share the array, so calls that overlap on the GPU race: order them on one
+ * stream.  Synchronises `cuda_stream` before returning. */
 rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, const float* box_host,
                                   float eps, float sigma, float rcut, const float* pos,
                                   const float* quat, float* force, float* torque,

@@ -1,7 +1,6 @@
 // Bead-sum forces for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA-graph
-// capture that forbids allocation, plug-ins of host programs that own the
+// Some callers cannot call cudaMalloc: plug-ins of host programs that own the
 // device memory pool and hand out only the tensors they manage, and real-time
 // loops where an allocation could stall or fail mid-run.  For them this file
 // provides one extra entry point, rb_forces_beads_noalloc, that evaluates the
@@ -16,9 +15,13 @@
 // with at most kNoAllocMaxNeighbors neighbours each, and at most
 // kNoAllocMaxCells cells.  Larger requests are rejected with RB_EINVAL.
 //
-// All calls share the array.  Calls whose work overlaps on the GPU (different
-// streams, or different host threads without ordering) race on it and give
-// wrong results; serialise them (one stream is enough).
+// All calls share the array and find the previous call's contents in it (the
+// status word and the cell counts are cleared at the start of every call).
+// Calls whose work overlaps on the GPU (different streams, or different host
+// threads without ordering) race on it and give wrong results; serialise them
+// (one stream is enough).  The first call on a device, with that device
+// current, looks up the array's device address (cudaGetSymbolAddress); make
+// that first call before any stream capture begins.
 #include <cmath>
 #include <mutex>
 
