@@ -41,10 +41,11 @@ def n_params(width: int, depth: int = 3, n_in: int = N_IN) -> int:
     return 2 * n_in + width * n_in + width + (depth - 1) * (width * width + width) + width + 3
 
 
-def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None) -> dict:
+def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None, cutoff=None) -> dict:
     """Split the flat parameter vector into named FP64 tensors (views).
     sym: optional point group (symmetry.point_group) -- the network then sees
-    every pair configuration in its canonical form (symmetry.py)."""
+    every pair configuration in its canonical form (symmetry.py).
+    cutoff: optional (r_on, r_off) -- the energy is multiplied by switch()."""
     t = flat if isinstance(flat, torch.Tensor) else torch.as_tensor(np.asarray(flat))
     t = t.to(DT)
     assert t.numel() == n_params(width, depth, n_in), (t.numel(), n_params(width, depth, n_in))
@@ -69,6 +70,7 @@ def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None) -> dict
     p["e_shift"] = take(1)[0]
     assert o == t.numel()
     p["sym"] = sym
+    p["cutoff"] = cutoff
     return p
 
 
@@ -123,14 +125,29 @@ def mlp_energy(p: dict, x):
     return p["e_scale"] * e_hat + p["e_shift"]
 
 
+def switch(rho, r_on: float, r_off: float):
+    """Smooth cutoff factor of the network energy (reading: the paper leaves the
+    network energy at the pair cutoff open; the bead potential itself is
+    shifted to zero at r_c).  1 for rho <= r_on, 0 for rho >= r_off, and in
+    between the quintic 1 - t^3 (10 - 15 t + 6 t^2), t = (rho - r_on) /
+    (r_off - r_on), whose first and second derivatives vanish at both ends."""
+    t = torch.clamp((rho - r_on) / (r_off - r_on), 0.0, 1.0)
+    return 1.0 - t ** 3 * (10.0 - 15.0 * t + 6.0 * t * t)
+
+
 def config_energy(p: dict, s, q_rel):
     """Pair energy from the pair configuration in the frame of body i (in its
-    canonical form under the point group when the network has one)."""
+    canonical form under the point group when the network has one; times the
+    smooth cutoff factor when the network has one)."""
+    rho = torch.sqrt((s * s).sum(-1))
     if p.get("sym") is not None:
         from . import symmetry
 
         s, q_rel = symmetry.canonical_torch(s, q_rel, p["sym"])
-    return mlp_energy(p, features(s, q_rel))
+    E = mlp_energy(p, features(s, q_rel))
+    if p.get("cutoff") is not None:
+        E = E * switch(rho, *p["cutoff"])
+    return E
 
 
 def pair_forces(p: dict, R_ij, q_i, q_j):
@@ -200,7 +217,7 @@ def predict_labels(p: dict, s, q_rel, create_graph: bool = False):
 
 
 def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_scale=None,
-                        kT_w=None, sym=None):
+                        kT_w=None, sym=None, cutoff=None):
     """L = mean_b w_b ( |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
     + lam_E (E - E*)^2 ) with w_b = min(1, exp(-E*/kT_w)) / (1 + (|F_j*|^2 +
     lam_tau (|tau_i*|^2 + |tau_j*|^2)) / f_scale^2); each factor is 1 when its
@@ -218,7 +235,7 @@ def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_
     pinned by central differences in the tests.
     """
     flat_t = torch.as_tensor(np.asarray(flat, dtype=np.float64)).clone().requires_grad_(True)
-    p = unpack(flat_t, width, depth, sym=sym)
+    p = unpack(flat_t, width, depth, sym=sym, cutoff=cutoff)
     cfg = torch.as_tensor(np.asarray(pair_cfg, dtype=np.float64))
     lab = torch.as_tensor(np.asarray(labels, dtype=np.float64))
     E, Fj, ti, tj = predict_labels(p, cfg[:, :3], cfg[:, 3:7], create_graph=True)

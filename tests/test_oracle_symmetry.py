@@ -148,3 +148,53 @@ def test_symmetric_network_is_invariant_and_differentiable():
         fdi = -(energy(bodies.qrotate(rm, s), bodies.qmul(rm, q))
                 - energy(bodies.qrotate(rp, s), bodies.qmul(rp, q))) / (2 * h)
         np.testing.assert_allclose(ti.numpy()[:, a], fdi, rtol=1e-6, atol=1e-8)
+
+
+def test_cutoff_switch_is_smooth_and_exact_at_its_ends():
+    """The network's cutoff factor: 1 up to r_on, 0 from r_off, continuous
+    with its first two derivatives (central differences), and a network with
+    it has forces and torques that are central differences of its energy in
+    the switching region, and exactly zero energy beyond r_off."""
+    r_on, r_off = 8.4, 9.4
+    rho = torch.linspace(7.0, 10.0, 3001, dtype=torch.float64)
+    S = nn.switch(rho, r_on, r_off).numpy()
+    r = rho.numpy()
+    assert np.all(S[r <= r_on] == 1.0) and np.all(S[r >= r_off] == 0.0)
+    assert np.all(np.diff(S) <= 1e-15)
+    h = 1e-4
+    for x in (r_on, r_off):
+        for side in (-1, 1):
+            xs = torch.tensor([x + side * 2 * h, x + side * h, x], dtype=torch.float64)
+            v = nn.switch(xs, r_on, r_off).numpy()
+            # first derivative 0 at the end; second derivative 0 at the end,
+            # so the one-sided second difference (centred one step in) is O(h)
+            assert abs(v[1] - v[2]) / h < 1e-6
+            assert abs(v[0] - 2 * v[1] + v[2]) / h ** 2 < 100 * h
+    mid = nn.switch(torch.tensor([0.5 * (r_on + r_off)], dtype=torch.float64), r_on, r_off)
+    assert float(mid[0]) == pytest.approx(0.5)
+
+    group = symmetry.point_group(CUBE)
+    mu, isd = inputs.feature_normalisation(5.0, 9.4)
+    flat = inputs.mlp_params(16, 3, 7, mu=mu, inv_sd=isd, e_scale=2.0, e_shift=-0.3)
+    p = nn.unpack(flat.astype(np.float64), 16, sym=group, cutoff=(r_on, r_off))
+    c7 = inputs.pair_configs(40, 8, 8.3, 9.6).astype(np.float64)
+    s, q = c7[:, :3], c7[:, 3:]
+    _, _, _, mk, mj = symmetry.choose(s, q, group)
+    keep = (mk > 1e-3) & (mj > 1e-3) & (np.abs(symmetry.canonical(s, q, group)[1][:, 0]) > 1e-3)
+    s, q = s[keep], q[keep]
+    E, Fj, ti, tj = nn.predict_labels(p, torch.as_tensor(s), torch.as_tensor(q))
+    rho = np.linalg.norm(s, axis=1)
+    assert np.all(E.detach().numpy()[rho >= r_off] == 0.0)
+    assert np.all(Fj.numpy()[rho >= r_off] == 0.0)
+
+    def energy(s_, q_):
+        return nn.config_energy(p, torch.as_tensor(s_), torch.as_tensor(q_)).detach().numpy()
+
+    for a in range(3):
+        e = np.eye(3)[a] * h
+        fd = -(energy(s + e, q) - energy(s - e, q)) / (2 * h)
+        np.testing.assert_allclose(Fj.numpy()[:, a], fd, rtol=1e-6, atol=1e-8)
+        rp = np.broadcast_to(bodies.qexp(e), q.shape)
+        rm = np.broadcast_to(bodies.qexp(-e), q.shape)
+        fdj = -(energy(s, bodies.qmul(rp, q)) - energy(s, bodies.qmul(rm, q))) / (2 * h)
+        np.testing.assert_allclose(tj.numpy()[:, a], fdj, rtol=1e-6, atol=1e-8)
