@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--train-f-scale", type=float, default=2.0)
     ap.add_argument("--no-symmetry", action="store_true")
     ap.add_argument("--train-contact", type=float, default=0.85)
+    ap.add_argument("--train-cutoff-width", type=float, default=1.0)
+    ap.add_argument("--train-lam-e", type=float, default=0.1)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--skin", type=float, default=0.4)
     ap.add_argument("--drift-steps", type=int, default=10000)
@@ -369,7 +371,9 @@ def main():
                                            steps=args.train_steps, batch=4096, lr=args.train_lr,
                                            f_scale=args.train_f_scale,
                                            symmetric=not args.no_symmetry,
-                                           contact=args.train_contact, time_limit_s=60.0)
+                                           contact=args.train_contact,
+                                           cutoff_width=args.train_cutoff_width,
+                                           lam_E=args.train_lam_e, time_limit_s=60.0)
         rho_fallback = rep["rho_contact_min"]
         training = {"samples": rep["samples"], "steps": rep["steps"], "batch": rep["batch"],
                     "symmetry": rep["symmetry"],
@@ -382,9 +386,10 @@ def main():
                                "from contact to Rc: dominated by contact forces)",
                     "contact": f"smallest bead-bead distance {args.train_contact} sigma "
                                "(separations reach into the repulsive wall)",
-                    "loss": f"mean w (|dF_j|^2 + |dtau_i|^2 + |dtau_j|^2), w = 1 / (1 + "
-                            f"|label|^2 / {args.train_f_scale}^2); FP32, Adam, lr "
+                    "loss": f"mean w (|dF_j|^2 + |dtau_i|^2 + |dtau_j|^2 + {args.train_lam_e} dE^2), "
+                            f"w = 1 / (1 + |label|^2 / {args.train_f_scale}^2); FP32, Adam, lr "
                             f"{args.train_lr} with cosine decay",
+                    "energy_cutoff": rep["cutoff"],
                     "nn_bead_fallback_rho": rho_fallback}
     else:
         mlp = api.MLP(WIDTH, DEPTH)

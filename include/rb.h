@@ -259,6 +259,17 @@ rb_status rb_template_symmetry(const float* xyz, int32_t n, float* quats_out, in
  * passed (they are mapped with them). */
 rb_status rb_mlp_set_symmetry(rb_mlp* mlp, const float* quats_host, int32_t n, int32_t inversion);
 
+/* Smooth cutoff of the network energy.  The paper leaves the network's energy
+ * at the body-pair cutoff open; without a cutoff every pair that crosses Rc
+ * makes the energy jump by the network's value there.  With r_off > r_on > 0
+ * the energy becomes E = S(rho) E_net, S = 1 for rho <= r_on, S = 0 for
+ * rho >= r_off, S = 1 - t^3 (10 - 15 t + 6 t^2) with t = (rho - r_on) /
+ * (r_off - r_on) in between (S' and S'' vanish at both ends), rho = |s|; forces
+ * and torques are the gradients of E, and training and rb_nn_weight_vjp use
+ * it as well (rb_nn_weight_vjp's E_hat becomes S E_hat).  r_off = 0 removes
+ * it; RB_EINVAL unless r_off = 0 or r_off > r_on >= 0. */
+rb_status rb_mlp_set_cutoff(rb_mlp* mlp, float r_on, float r_off);
+
 /* The canonical representatives themselves (device arrays, in place): cfg
  * n x 8 as rb_nn_pairs' input; labels n x 12 as its output (nullable), mapped
  * as the forces and torques.  Runs on the network's stream; a network without

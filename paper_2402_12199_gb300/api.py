@@ -263,6 +263,11 @@ class MLP:
         check(load().rb_mlp_set_symmetry(self._h, q.ctypes.data if len(q) else None, len(q),
                                          int(bool(inversion))))
 
+    def set_cutoff(self, r_on: float, r_off: float):
+        """rb_mlp_set_cutoff: energy times a smooth switch from 1 at r_on to 0 at
+        r_off (r_off = 0 removes it)."""
+        check(load().rb_mlp_set_cutoff(self._h, float(r_on), float(r_off)))
+
     def canonical(self, cfg: torch.Tensor, labels: torch.Tensor = None):
         """rb_nn_canonical in place on (n, 8) configurations [and (n, 12) labels]."""
         _dev(cfg, 8)

@@ -454,6 +454,7 @@ rb_status nn_pairs_f32_async(const rb_mlp* m, int64_t n, const float4* cfg, floa
     src.cfg = cfg;
     src.n_explicit = n;
     PairDst dst{};
+    set_cutoff(dst, m);
     dst.out = out;
     dst.grad = grad;
     return dispatch_f32<false>(m, m->stream, sm_count(), src, dst);
@@ -491,6 +492,7 @@ rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
     src.Rc2 = s->Rc * s->Rc;
     PairDst dst{};
+    set_cutoff(dst, m);
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;
     dst.tj = s->pair_tj;
@@ -554,6 +556,16 @@ rb_status rb_mlp_set_params(rb_mlp* m, const float* flat, int64_t n, int32_t fro
     return mlp_refresh(m);
 }
 
+rb_status rb_mlp_set_cutoff(rb_mlp* m, float r_on, float r_off) {
+    if (!m) return fail(RB_EINVAL, "null network");
+    if (!(r_off == 0.f || (r_off > r_on && r_on >= 0.f)))
+        return fail(RB_EINVAL, "need r_off = 0 (no cutoff) or r_off > r_on >= 0");
+    m->sw_on = r_off > 0.f ? r_on : 0.f;
+    m->sw_off = r_off;
+    m->version++;  // captured step graphs hold the old values
+    return RB_OK;
+}
+
 rb_status rb_mlp_get_params(const rb_mlp* m, float* flat, int64_t n, int32_t to_host) {
     if (!m || !flat) return fail(RB_EINVAL, "null argument");
     if (n != m->n_params) return fail(RB_EINVAL, "parameter count does not match the layout");
@@ -577,6 +589,7 @@ rb_status rb_nn_pairs(const rb_mlp* m, int32_t precision, int64_t n, const float
     src.cfg = reinterpret_cast<const float4*>(cfg);
     src.n_explicit = n;
     PairDst dst{};
+    set_cutoff(dst, m);
     dst.out = reinterpret_cast<float4*>(out);
     dst.grad = reinterpret_cast<float4*>(grad_out);
     return dispatch_f32<false>(m, m->stream, sm_count(), src, dst);

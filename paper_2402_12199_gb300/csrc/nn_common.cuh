@@ -74,7 +74,17 @@ struct PairDst {
     int* fb_list;
     int* fb_count;
     float fb_rho2;
+    // smooth cutoff of the energy: sw_inv = 1 / (r_off - r_on), 0 = none
+    float sw_on, sw_inv;
 };
+
+// Smooth cutoff factor S(rho) and dS/drho (1 below r_on, 0 beyond r_off, the
+// quintic 1 - t^3 (10 - 15 t + 6 t^2) between, t = (rho - r_on) / (r_off - r_on)).
+__device__ inline void cutoff_switch(float rho, float on, float inv, float& S, float& dS) {
+    const float t = fminf(fmaxf((rho - on) * inv, 0.f), 1.f);
+    S = 1.f - t * t * t * (10.f + t * (-15.f + 6.f * t));
+    dS = -30.f * t * t * (1.f - t) * (1.f - t) * inv;
+}
 
 struct PairGeom {
     float3 s;
@@ -290,7 +300,18 @@ __device__ inline void raw_features(const PairGeom& g, float (&x)[kIn]) {
 // gx = dE/dx (raw features).  Writes the outputs of pair gp.
 template <bool SYSTEM>
 __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const PairGeom& g,
-                                          const float (&gx)[kIn], float E) {
+                                          const float (&gx_in)[kIn], float E) {
+    float gx[kIn];
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) gx[k] = gx_in[k];
+    if (dst.sw_inv > 0.f) {  // E S(rho): every gradient scaled by S, plus E S' along rho
+        float S, dS;
+        cutoff_switch(g.rho, dst.sw_on, dst.sw_inv, S, dS);
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) gx[k] *= S;
+        gx[7] += E * dS;  // feature 7 is rho itself
+        E *= S;
+    }
     const float3 s = g.s;
     const float inv_rho = 1.f / g.rho;
     const float gr = (gx[7] - gx[8] * inv_rho * inv_rho + 2.f * g.rho * gx[9]) * inv_rho;
@@ -362,6 +383,12 @@ inline rb_status set_fallback(PairDst& dst, rb_system* s) {
     dst.fb_rho2 = r * r;
     RB_CUDA(launch_pdl(k_zero_count, 1, 1, 0, s->stream, s->fallback_count));
     return RB_OK;
+}
+
+// The network's smooth energy cutoff into a pair destination.
+inline void set_cutoff(PairDst& dst, const rb_mlp* m) {
+    dst.sw_on = m->sw_on;
+    dst.sw_inv = m->sw_off > m->sw_on ? 1.f / (m->sw_off - m->sw_on) : 0.f;
 }
 
 // The network's point group into a pair source.

@@ -426,6 +426,7 @@ rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m) {
     src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
     src.Rc2 = s->Rc * s->Rc;
     PairDst dst{};
+    set_cutoff(dst, m);
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;
     dst.tj = s->pair_tj;
@@ -440,6 +441,7 @@ rb_status nn_tc_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float
     src.cfg = cfg;
     src.n_explicit = n;
     PairDst dst{};
+    set_cutoff(dst, m);
     dst.out = out;
     dst.grad = grad;
     const int grid = (int)std::min<int64_t>(sm_count_tc(), (n + tc::kM - 1) / tc::kM);

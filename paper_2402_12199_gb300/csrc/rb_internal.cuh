@@ -176,6 +176,7 @@ struct rb_mlp {
     float4* sym_dev = nullptr;     // 3 x 24 float4 (generic table) + 48 float4 (cube table)
     int n_sym = 0, sym_inv = 0;
     int sym_cube = 0;              // the group is the cube's: closed-form choice
+    float sw_on = 0.f, sw_off = 0.f;  // smooth cutoff of the energy (sw_off = 0: none)
 };
 
 struct rb_system {

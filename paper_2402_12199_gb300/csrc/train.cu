@@ -348,14 +348,15 @@ static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<
 // Workspace layout for batch B, width W, depth D (floats):
 //   X, U [B x 16]; per layer Z, Zd, H, Hd [B x W]; Ah0, Ahd0, Ah1, Ahd1 [B x W];
 //   T [B x W]; c [B]; ucfg, pred [B x 8], [B x 12]; G16 [W x 16];
-//   cfg_c, ucfg_c [B x 8] (canonical configurations and tangents)
+//   cfg_c, ucfg_c [B x 8] (canonical configurations and tangents);
+//   u_sw [B x 8], c_sw [B] (tangents and coefficients of the switched energy)
 struct TrWork {
     float *X, *U, *Z[4], *Zd[4], *H[4], *Hd[4], *Ah[2], *Ahd[2], *T, *c, *ucfg, *pred, *G16;
-    float *cfg_c, *ucfg_c;
+    float *cfg_c, *ucfg_c, *u_sw, *c_sw;
 };
 static size_t tr_work_floats(int64_t B, int W, int D) {
     return (size_t)B * 32 + (size_t)D * 4 * B * W + 5 * (size_t)B * W + B + 8 * B + 12 * B +
-           (size_t)W * 16 + 16 * (size_t)B + 16 * 48;  // + rounding of every buffer to 16
+           (size_t)W * 16 + 25 * (size_t)B + 16 * 48;  // + rounding of every buffer to 16
 }
 static TrWork tr_work(float* base, int64_t B, int W, int D) {
     TrWork w{};
@@ -384,7 +385,29 @@ static TrWork tr_work(float* base, int64_t B, int W, int D) {
     w.G16 = take((size_t)W * 16);
     w.cfg_c = take(8 * B);
     w.ucfg_c = take(8 * B);
+    w.u_sw = take(8 * B);
+    w.c_sw = take(B);
     return w;
+}
+
+// With the smooth cutoff the output is S(rho) E_hat: d/dW [u . grad(S E_hat) +
+// c S E_hat] = d/dW [u' . grad E_hat + c' E_hat] with u' = S u and
+// c' = S c + S' (u_s . s / rho), since grad(S E_hat) = S grad E_hat + E_hat S'
+// grad rho and rho = |s|.
+__global__ void k_switch_tangent(int64_t n, const float4* __restrict__ cfg,
+                                 const float4* __restrict__ ucfg, const float* __restrict__ c,
+                                 float on, float inv, float4* __restrict__ u_out,
+                                 float* __restrict__ c_out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const float4 c0 = cfg[2 * b];
+    const float rho = sqrtf(c0.x * c0.x + c0.y * c0.y + c0.z * c0.z);
+    float S, dS;
+    cutoff_switch(rho, on, inv, S, dS);
+    const float4 u0 = ucfg[2 * b], u1 = ucfg[2 * b + 1];
+    c_out[b] = S * c[b] + dS * (u0.x * c0.x + u0.y * c0.y + u0.z * c0.z) / rho;
+    u_out[2 * b] = make_float4(S * u0.x, S * u0.y, S * u0.z, 0.f);
+    u_out[2 * b + 1] = make_float4(S * u1.x, S * u1.y, S * u1.z, S * u1.w);
 }
 
 // grad = d/dW sum_b [u_b . grad_(s,q) E_hat_b + c_b E_hat_b] (flat layout; the
@@ -398,6 +421,13 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
     TrWork w = tr_work(tr->work, tr->max_batch, W, D);
     const float* flat = m->params;
     RB_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * m->n_params, st));
+    if (m->sw_off > m->sw_on) {  // switched output S E_hat (see k_switch_tangent)
+        k_switch_tangent<<<nblk(B), 256, 0, st>>>(B, cfg, ucfg, c, m->sw_on,
+                                                  1.f / (m->sw_off - m->sw_on),
+                                                  reinterpret_cast<float4*>(w.u_sw), w.c_sw);
+        ucfg = reinterpret_cast<const float4*>(w.u_sw);
+        c = w.c_sw;
+    }
     if (m->n_sym > 0) {  // the network sees canonical configurations: map cfg and u
         PairSrc sym{};
         set_symmetry(sym, m);

@@ -21,7 +21,7 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
                   steps: int = 3000, batch: int = 4096, lr: float = 1e-3, lam_tau: float = 1.0,
                   lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
                   log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0,
-                  symmetric: bool = True, contact: float = 1.0):
+                  symmetric: bool = True, contact: float = 1.0, cutoff_width: float = 0.0):
     """Returns (mlp, report).  With `symmetric` the body's point group is
     attached to the network (rb_mlp_set_symmetry), so it learns one copy of
     every class of symmetry-related configurations, and the feature
@@ -29,7 +29,9 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     training configurations; otherwise it spans the separations contact..Rc
     isotropically.  e_scale and e_shift come from the label energies.
     `contact`: smallest bead-bead distance (sigma units) that defines contact
-    for the sampled separations (rb_sample_pairs_at)."""
+    for the sampled separations (rb_sample_pairs_at).  `cutoff_width` > 0:
+    the energy is switched smoothly to zero between Rc - cutoff_width and Rc
+    (rb_mlp_set_cutoff) during training and afterwards."""
     box = 60.0 if shape == "cube" else 70.0
     sysobj = api.System(8, [box] * 3, shape)
     Rc = sysobj.pair_cutoff
@@ -59,6 +61,8 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     mlp.set_params(flat)
     if group is not None:
         mlp.set_symmetry(*group)
+    if cutoff_width > 0.0:
+        mlp.set_cutoff(Rc - cutoff_width, Rc)
     tr = api.Trainer(mlp, batch, lr=lr)
     g = torch.Generator(device="cuda").manual_seed(seed)
     t0 = time.perf_counter()
@@ -82,6 +86,7 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     report = {"shape": shape, "width": width, "depth": depth, "samples": n_samples,
               "symmetry": (f"{len(group[0])} rotations" + (" + inversion" if group[1] else ""))
               if group is not None else None,
+              "cutoff": [Rc - cutoff_width, Rc] if cutoff_width > 0.0 else None,
               "steps": k + 1, "batch": batch, "lr": lr, "f_scale": f_scale, "kT_w": kT_w, "t_sample_s": t_sample,
               "t_train_s": t_train, "rho_contact_min": rmin, "Rc": Rc,
               "heldout_e_F": err(out[:, 0:3], lab_te[:, 0:3]),
