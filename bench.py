@@ -57,7 +57,11 @@ def parse():
     ap.add_argument("--train-contact", type=float, default=0.85)
     ap.add_argument("--train-cutoff-width", type=float, default=1.0)
     ap.add_argument("--train-lam-e", type=float, default=0.1)
+    ap.add_argument("--cyl-train-steps", type=int, default=300)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=256)
+    ap.add_argument("--serving-steps", type=int, default=1000)
+    ap.add_argument("--serving-nmax", type=int, default=65536)
     ap.add_argument("--skin", type=float, default=0.4)
     ap.add_argument("--drift-steps", type=int, default=10000)
     ap.add_argument("--drift-every", type=int, default=500)
@@ -91,19 +95,20 @@ def combine_ranks(ms_step: float, units: float, device=None):
     return float(t.item()), float(u.item())
 
 
-def serving_run(api, inputs, mlp, n_requests=24, steps=200, seed=5, rate_factor=8.0,
-                budget_bytes=2 << 30, slots=8):
-    """Bounded serving workload: cube/cylinder replicas with N log-uniform in
-    [512, 8192], phi in [0.05, 0.25], kT in [0.5, 1.5], Poisson arrivals at about
-    rate_factor / (mean solo run time); cubes on the network (BF16), cylinders on
-    the bead path (the network is a cube model)."""
+def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=5,
+                rate_factor=8.0, budget_bytes=2 << 30, slots=8):
+    """Serving workload: cube/cylinder replicas with N log-uniform in
+    [512, n_max], phi in [0.05, 0.25], kT in [0.5, 1.5], `steps` MD steps each,
+    Poisson arrivals at rate_factor / (solo run time of the first request), so
+    about rate_factor replicas are in flight; cubes on the network (BF16),
+    cylinders on the bead path (the network is a cube model)."""
     import time as _t
 
     rng = np.random.default_rng(seed)
     reqs = []
     for k in range(n_requests):
         shape = "cube" if rng.random() < 0.5 else "cylinder"
-        n = int(round(math.exp(rng.uniform(math.log(512), math.log(8192)))))
+        n = int(round(math.exp(rng.uniform(math.log(512), math.log(n_max)))))
         phi = float(rng.uniform(0.05, 0.25))
         kT = float(rng.uniform(0.5, 1.5))
         M = 125.0 if shape == "cube" else 152.0
@@ -136,6 +141,10 @@ def serving_run(api, inputs, mlp, n_requests=24, steps=200, seed=5, rate_factor=
     srv.close()
     ok = sum(r["status"] == 0 for r in res)
     return {"requests": n_requests, "completed_ok": ok, "steps_each": steps,
+            "workload": f"cube or cylinder with probability 1/2, N log-uniform in [512, {n_max}], "
+                        f"phi in [0.05, 0.25], kT in [0.5, 1.5]; Poisson arrivals, about "
+                        f"{rate_factor:g} replicas in flight; HBM budget {budget_bytes >> 20} MiB, "
+                        f"{slots} slots",
             "makespan_s": makespan, "pair_evals_per_s": stats["pair_evals"] / makespan,
             "step_ms_p50": stats["step_ms_p50"], "step_ms_p99": stats["step_ms_p99"],
             "peak_resident": stats["peak_resident"], "solo_calibration_s": t_solo,
@@ -532,6 +541,23 @@ def main():
                     "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
                     "flops_per_launch": flops}
 
+    # ---- cylinder training throughput at width 256: 1M pairs drawn and
+    # labelled on the device, then Adam steps on batches of 4096
+    train_cyl = None
+    if args.train_steps > 0 and any(p.startswith("nn") for p in paths):
+        from paper_2402_12199_gb300 import train_net
+
+        _, rc = train_net.train_network("cylinder", 256, DEPTH, n_samples=1_000_000,
+                                        steps=args.cyl_train_steps, batch=4096, lr=args.train_lr,
+                                        f_scale=args.train_f_scale, contact=args.train_contact,
+                                        lam_E=args.train_lam_e,
+                                        cutoff_width=args.train_cutoff_width, seed=4)
+        train_cyl = {"workload": "cylinders (8 x 19 beads), network 10-256x3-1, 1M training pairs",
+                     "symmetry": rc["symmetry"],
+                     "sampler_pairs_per_s": (rc["samples"] + 10000) / rc["t_sample_s"],
+                     "train_samples_per_s": rc["steps"] * rc["batch"] / rc["t_train_s"],
+                     "steps": rc["steps"], "heldout_e_F_after_these_steps": rc["heldout_e_F"]}
+
     # ---- network width 256 (BF16, streamed weights), same workload, timed alone
     width256 = None
     if "nn_bf16" in paths:
@@ -649,7 +675,8 @@ def main():
     serving = None
     if not args.no_serving and world == 1:
         serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
-                              mlp)
+                              mlp, n_requests=args.serving_requests, steps=args.serving_steps,
+                              n_max=args.serving_nmax)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -692,7 +719,7 @@ def main():
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
             "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_fp32": roof_f32, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
-            "nn_bf16_width256": width256, "nve_drift": drift,
+            "nn_bf16_width256": width256, "nve_drift": drift, "training_cylinders_w256": train_cyl,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "results_finite": e2e_ok,
