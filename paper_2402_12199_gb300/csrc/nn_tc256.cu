@@ -11,10 +11,11 @@
 //     shared buffer with bulk asynchronous copies completing on an mbarrier;
 //     the copy for stage s+1 is issued as soon as stage s's MMAs have retired,
 //     so it overlaps stage s's epilogue;
-//   * the pre-activations z_1, z_2 needed by the reverse pass are kept in
-//     tensor memory as packed BF16 pairs (tcgen05.st), 128 columns each.
-// Tensor memory: cols 0..255 accumulator of every stage, 256..383 z_1 packed,
-// 384..511 z_2 packed.  Shared memory: X [128 x 64], H [128 x 256] and the
+//   * the derivatives silu'(z_1), silu'(z_2) needed by the reverse pass are
+//     written by the forward epilogue into tensor memory as packed BF16 pairs
+//     (tcgen05.st), 128 columns each.
+// Tensor memory: cols 0..255 accumulator of every stage, 256..383 silu'(z_1)
+// packed, 384..511 silu'(z_2) packed.  Shared memory: X [128 x 64], H [128 x 256] and the
 // weight buffer, all BF16, K-major, 128-byte swizzle.  One CTA of 8 warps per
 // SM: warp w reads TMEM lanes 32 (w % 4).. and columns 128 (w / 4)..+127 of
 // every accumulator.  Waits are bounded; TMEM is freed on every exit path.
@@ -106,8 +107,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = (warp & 3) * 32 + (tid & 31);
     const int half = warp >> 2;
     const int cbeg = half * (kW / 2);
-    float* bias = reinterpret_cast<float*>(sm + Ly.s_f32);  // D x 256
-    float* wo = bias + D * kW;                               // 256
+    float* hbias = reinterpret_cast<float*>(sm + Ly.s_f32);  // D x 256, b_l / 2
+    float* wo = hbias + D * kW;                               // 256
     float* mu = wo + kW;                                     // 16
     float* isd = mu + 16;                                    // 16
     float* epart = isd + 16;                                 // 128
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     {
         uint4* xz = reinterpret_cast<uint4*>(sm + Ly.s_x);
         for (uint32_t t = tid; t < (kM * kK1 * 2) / 16; t += kThreads) xz[t] = make_uint4(0, 0, 0, 0);
-        for (int t = tid; t < D * kW; t += kThreads) bias[t] = flat[fl.b_(1 + t / kW, kW) + t % kW];
+        for (int t = tid; t < D * kW; t += kThreads)  // half biases: silu2 works on z / 2
+            hbias[t] = 0.5f * flat[fl.b_(1 + t / kW, kW) + t % kW];
         for (int t = tid; t < kW; t += kThreads) wo[t] = flat[fl.wo + t];
         for (int t = tid; t < 16; t += kThreads) {
             mu[t] = t < kIn ? flat[fl.mu + t] : 0.f;
@@ -241,32 +243,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---- epilogue of stage s
             if (s < D) {  // forward layer l = s + 1
                 const int l = s + 1;
-                const float* b = bias + (l - 1) * kW;
-                float e_acc = 0.f;
+                const float* hb = hbias + (l - 1) * kW;
+                float2 e2 = make_float2(0.f, 0.f);
 #pragma unroll 1
                 for (int c = cbeg; c < cbeg + kW / 2; c += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + lane_field + c, v);
-                    uint32_t zp[16];
+                    uint32_t u[32];
+                    tmem_ld32_issue(tmem + lane_field + c, u);
+                    tmem_wait32(u);
+                    uint32_t yp[16], dp[16];
 #pragma unroll
-                    for (int i = 0; i < 32; i += 2) {
-                        const float z0 = v[i] + b[c + i], z1 = v[i + 1] + b[c + i + 1];
-                        zp[i / 2] = pack_bf16(z0, z1);
-                        const float s0 = sigm(z0), s1 = sigm(z1);
+                    for (int i = 0; i < 16; i += 2) {
+                        const float4 b4 = *reinterpret_cast<const float4*>(hb + c + 2 * i);
+                        float2 y0, d0, y1, d1;
+                        silu2(make_float2(__uint_as_float(u[2 * i]), __uint_as_float(u[2 * i + 1])),
+                              make_float2(b4.x, b4.y), y0, d0);
+                        silu2(make_float2(__uint_as_float(u[2 * i + 2]),
+                                          __uint_as_float(u[2 * i + 3])),
+                              make_float2(b4.z, b4.w), y1, d1);
                         if (l < D) {
-                            v[i] = z0 * s0;
-                            v[i + 1] = z1 * s1;
-                        } else {
-                            e_acc = fmaf(wo[c + i], z0 * s0, e_acc);
-                            e_acc = fmaf(wo[c + i + 1], z1 * s1, e_acc);
-                            v[i] = wo[c + i] * s0 * (1.f + z0 * (1.f - s0));
-                            v[i + 1] = wo[c + i + 1] * s1 * (1.f + z1 * (1.f - s1));
+                            yp[i] = pack_bf16(y0);
+                            yp[i + 1] = pack_bf16(y1);
+                            dp[i] = pack_bf16(d0);
+                            dp[i + 1] = pack_bf16(d1);
+                        } else {  // output layer: E += w_o . y, seed g_D = w_o * silu'(z_D)
+                            const float4 w4 = *reinterpret_cast<const float4*>(wo + c + 2 * i);
+                            const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+                            e2 = __ffma2_rn(wa, y0, e2);
+                            e2 = __ffma2_rn(wb, y1, e2);
+                            yp[i] = pack_bf16(__fmul2_rn(wa, d0));
+                            yp[i + 1] = pack_bf16(__fmul2_rn(wb, d1));
                         }
                     }
-                    if (l < D) tmem_st16(tmem + lane_field + 256 + (l - 1) * 128 + c / 2, zp);
-                    store_row32(Ht, kM, row, c, v);
+                    if (l < D) tmem_st16(tmem + lane_field + 256 + (l - 1) * 128 + c / 2, dp);
+                    store_row32p(Ht, kM, row, c, yp);
                 }
                 if (l == D) {
+                    const float e_acc = e2.x + e2.y;
                     if (half == 1) epart[row] = e_acc;
                     __syncthreads();
                     if (half == 0) E = e_scale * (e_acc + epart[row] + b_o) + e_shift;
@@ -275,18 +287,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int l = 2 * D - s;      // s = D -> l = D, ..., s = 2D-2 -> l = 2
 #pragma unroll 1
                 for (int c = cbeg; c < cbeg + kW / 2; c += 32) {
-                    float v[32];
-                    uint32_t zp[16];
-                    tmem_ld32(tmem + lane_field + c, v);
-                    tmem_ld16u(tmem + lane_field + 256 + (l - 2) * 128 + c / 2, zp);
+                    uint32_t u[32], d[16];
+                    tmem_ld32_issue(tmem + lane_field + c, u);
+                    tmem_ld16_issue(tmem + lane_field + 256 + (l - 2) * 128 + c / 2, d);
+                    tmem_wait32(u);
+                    tmem_wait16(d);
+                    uint32_t gp[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float2 z = unpack_bf16(zp[i]);
-                        const float s0 = sigm(z.x), s1 = sigm(z.y);
-                        v[2 * i] *= s0 * (1.f + z.x * (1.f - s0));
-                        v[2 * i + 1] *= s1 * (1.f + z.y * (1.f - s1));
-                    }
-                    store_row32(Ht, kM, row, c, v);
+                    for (int i = 0; i < 16; ++i)
+                        gp[i] = pack_bf16(__fmul2_rn(
+                            make_float2(__uint_as_float(u[2 * i]), __uint_as_float(u[2 * i + 1])),
+                            widen_bf16x2(d[i])));
+                    store_row32p(Ht, kM, row, c, gp);
                 }
             } else if (half == 0) {  // dE/dx_hat (16 columns) and the adjoint
                 float v[16];

@@ -11,10 +11,12 @@
 //     nn_tc.cu) plus, per warpgroup, one 128 x 128 activation tile whose first
 //     64-column atom also serves as the 64-column feature tile of layer 1.
 //   * Tensor memory: warpgroup g owns columns 256 g .. 256 g + 255: the
-//     accumulator of every stage (128 columns) and z_1, z_2 as packed BF16
-//     pairs (64 columns each) for the reverse pass.
-//   * Synchronisation per warpgroup: a named barrier (128 threads), its own
-//     mbarrier for MMA completion, a bounded wait with a failure flag.
+//     accumulator of every stage (128 columns) and silu'(z_1), silu'(z_2) as
+//     packed BF16 pairs (64 columns each), written by the forward epilogue so
+//     that a reverse epilogue is one product per element.
+//   * Synchronisation per warpgroup: one named barrier per stage (128
+//     threads, also OR-ing earlier failed waits), its own mbarrier for MMA
+//     completion, a bounded wait with a failure flag.
 // Thread r of a warpgroup owns pair r of its tile (TMEM lane r) for the
 // features, all 128 columns of every epilogue, and the geometric adjoint.
 #include <cstdint>
@@ -59,8 +61,6 @@ __host__ __device__ inline Layout layout(int D) {
     return L;
 }
 
-__device__ inline void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
-
 // Named-barrier reduction: true if any thread of the warpgroup passes `flag`.
 __device__ inline bool wg_any(int g, bool flag) {
     uint32_t res;
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int g = warp >> 2;                          // pipeline (warpgroup)
     const int row = (warp & 3) * 32 + (tid & 31);     // TMEM lane = pair of the tile
     const bool leader = (tid & 127) == 0;
-    float* bias = reinterpret_cast<float*>(sm + Ly.f32);  // D x 128
-    float* wo = bias + D * kW;
+    float* hbias = reinterpret_cast<float*>(sm + Ly.f32);  // D x 128, b_l / 2
+    float* wo = hbias + D * kW;
     float* mu = wo + kW;
     float* isd = mu + 16;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Ly.bar + 16);
@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     {
         uint4* dstw = reinterpret_cast<uint4*>(sm);
         for (uint32_t t = tid; t < Ly.weights / 16; t += kThreads) dstw[t] = __ldg(img + t);
-        for (int t = tid; t < D * kW; t += kThreads) bias[t] = flat[fl.b_(1 + t / kW, kW) + t % kW];
+        for (int t = tid; t < D * kW; t += kThreads)  // half biases: silu2 works on z / 2
+            hbias[t] = 0.5f * flat[fl.b_(1 + t / kW, kW) + t % kW];
         for (int t = tid; t < kW; t += kThreads) wo[t] = flat[fl.wo + t];
         for (int t = tid; t < 16; t += kThreads) {
             mu[t] = t < kIn ? flat[fl.mu + t] : 0.f;
@@ -129,21 +130,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t h_addr = s_base + Ly.h[g];
 
     uint32_t phase = 0;
-    bool ok = true;
+    bool ok = true;       // the same in every thread of the warpgroup
+    bool waited = true;   // this thread's last MMA wait completed
     const int64_t n_total = SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
     const int64_t n_tiles = (n_total + kM - 1) / kM;
     const int64_t stride = 2 * (int64_t)gridDim.x;
     const int64_t first = (int64_t)blockIdx.x + (int64_t)g * gridDim.x;
 
-    // one GEMM stage of this pipeline: publish the A tile, issue, wait (bounded)
+    // one GEMM stage of this pipeline: publish the A tile, issue, wait
+    // (bounded).  The publishing barrier also ORs the previous stage's failed
+    // waits, so every thread leaves through the same stage.
     auto stage = [&](uint32_t a_base, uint32_t b_base, int K, int rows_b, uint32_t idesc) {
         fence_proxy_async();
         fence_before();
-        wg_sync(g);
+        if (wg_any(g, !waited)) {
+            ok = false;
+            return;
+        }
         if (leader) issue_gemm(tmem, a_base, b_base, K, rows_b, idesc, bar);
-        const bool got = mbar_wait(bar, phase, kWaitCycles);
+        waited = mbar_wait(bar, phase, kWaitCycles);
         phase ^= 1u;
-        if (wg_any(g, !got)) ok = false;
         fence_after();
     };
 
@@ -185,8 +191,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t gn = (tile + stride) * kM + row;
                 raw = fetch_pair<SYSTEM>(src, gn, gn < n_total);
             }
-            const float* b = bias + (l - 1) * kW;
-            float e_acc = 0.f;
+            const float* hb = hbias + (l - 1) * kW;
+            float2 e2 = make_float2(0.f, 0.f);
 #pragma unroll 1
             for (int c = 0; c < kW; c += 64) {
                 uint32_t u0[32], u1[32];
@@ -197,51 +203,66 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int h2 = 0; h2 < 2; ++h2) {
                     const int cc = c + 32 * h2;
-                    float v[32];
-                    uint32_t zp[16];
+                    uint32_t yp[16], dp[16];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(h2 == 0 ? u0[i] : u1[i]);
-#pragma unroll
-                    for (int i = 0; i < 32; i += 2) {
-                        const float z0 = v[i] + b[cc + i], z1 = v[i + 1] + b[cc + i + 1];
-                        zp[i / 2] = pack_bf16(z0, z1);
-                        const float s0 = sigm(z0), s1 = sigm(z1);
+                    for (int i = 0; i < 16; i += 2) {
+                        const float4 b4 = *reinterpret_cast<const float4*>(hb + cc + 2 * i);
+                        const uint32_t* u = h2 == 0 ? u0 : u1;
+                        float2 y0, d0, y1, d1;
+                        silu2(make_float2(__uint_as_float(u[2 * i]), __uint_as_float(u[2 * i + 1])),
+                              make_float2(b4.x, b4.y), y0, d0);
+                        silu2(make_float2(__uint_as_float(u[2 * i + 2]),
+                                          __uint_as_float(u[2 * i + 3])),
+                              make_float2(b4.z, b4.w), y1, d1);
                         if (l < D) {
-                            v[i] = z0 * s0;
-                            v[i + 1] = z1 * s1;
-                        } else {
-                            e_acc = fmaf(wo[cc + i], z0 * s0, e_acc);
-                            e_acc = fmaf(wo[cc + i + 1], z1 * s1, e_acc);
-                            v[i] = wo[cc + i] * s0 * (1.f + z0 * (1.f - s0));
-                            v[i + 1] = wo[cc + i + 1] * s1 * (1.f + z1 * (1.f - s1));
+                            yp[i] = pack_bf16(y0);
+                            yp[i + 1] = pack_bf16(y1);
+                            dp[i] = pack_bf16(d0);
+                            dp[i + 1] = pack_bf16(d1);
+                        } else {  // output layer: E += w_o . y, seed g_D = w_o * silu'(z_D)
+                            const float4 w4 = *reinterpret_cast<const float4*>(wo + cc + 2 * i);
+                            const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+                            e2 = __ffma2_rn(wa, y0, e2);
+                            e2 = __ffma2_rn(wb, y1, e2);
+                            yp[i] = pack_bf16(__fmul2_rn(wa, d0));
+                            yp[i + 1] = pack_bf16(__fmul2_rn(wb, d1));
                         }
                     }
-                    if (l < D) tmem_st16(tmem + lane_field + kW + (l - 1) * 64 + cc / 2, zp);
-                    store_row32(Ht, kM, row, cc, v);
+                    if (l < D) tmem_st16(tmem + lane_field + kW + (l - 1) * 64 + cc / 2, dp);
+                    store_row32p(Ht, kM, row, cc, yp);
                 }
             }
-            if (l == D) E = e_scale * (e_acc + b_o) + e_shift;
+            if (l == D) E = e_scale * (e2.x + e2.y + b_o) + e_shift;
         }
-        // ---------------- reverse: g_{l-1} = (g_l W_l) * silu'(z_{l-1})
+        // ---------------- reverse: g_{l-1} = (g_l W_l) * silu'(z_{l-1}), the
+        // derivative read back from TMEM where the forward pass left it
         for (int l = D; l >= 2 && ok; --l) {
             stage(h_addr, s_base + Ly.wb[l], kW, kW, idesc_w);
             if (!ok) break;
-            const uint32_t zcol = kW + (uint32_t)(l - 2) * 64;
+            const uint32_t dcol = kW + (uint32_t)(l - 2) * 64;
 #pragma unroll 1
-            for (int c = 0; c < kW; c += 32) {
-                uint32_t uv[32], zp[16];
-                tmem_ld32_issue(tmem + lane_field + c, uv);
-                tmem_wait32(uv);
-                tmem_ld16u(tmem + lane_field + zcol + c / 2, zp);
-                float v[32];
+            for (int c = 0; c < kW; c += 64) {
+                uint32_t u0[32], u1[32], d0[16], d1[16];
+                tmem_ld32_issue(tmem + lane_field + c, u0);
+                tmem_ld32_issue(tmem + lane_field + c + 32, u1);
+                tmem_ld16_issue(tmem + lane_field + dcol + c / 2, d0);
+                tmem_ld16_issue(tmem + lane_field + dcol + c / 2 + 16, d1);
+                tmem_wait32(u0);
+                tmem_wait32(u1);
+                tmem_wait16(d0);
+                tmem_wait16(d1);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float2 z = unpack_bf16(zp[i]);
-                    const float s0 = sigm(z.x), s1 = sigm(z.y);
-                    v[2 * i] = __uint_as_float(uv[2 * i]) * s0 * (1.f + z.x * (1.f - s0));
-                    v[2 * i + 1] = __uint_as_float(uv[2 * i + 1]) * s1 * (1.f + z.y * (1.f - s1));
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const uint32_t* u = h2 == 0 ? u0 : u1;
+                    const uint32_t* d = h2 == 0 ? d0 : d1;
+                    uint32_t gp[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        gp[i] = pack_bf16(__fmul2_rn(
+                            make_float2(__uint_as_float(u[2 * i]), __uint_as_float(u[2 * i + 1])),
+                            widen_bf16x2(d[i])));
+                    store_row32p(Ht, kM, row, c + 32 * h2, gp);
                 }
-                store_row32(Ht, kM, row, c, v);
             }
         }
         // ---------------- dE/dx_hat = g_1 W_1 (16 padded columns) and the adjoint
@@ -249,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ok) {
             float v[16];
             tmem_ld16(tmem + lane_field, v);
-            if (valid) {
+            if (valid && waited) {
                 float gx[kIn];
 #pragma unroll
                 for (int k = 0; k < kIn; ++k) gx[k] = e_scale * v[k] * isd[k];
@@ -257,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     }
+    if (wg_any(g, !waited)) ok = false;  // the last stage's wait
     fence_before();
     __syncthreads();
     if (warp == 0) {

@@ -166,6 +166,38 @@ __device__ inline uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
 }
+__device__ inline uint32_t pack_bf16(float2 a) { return pack_bf16(a.x, a.y); }
+
+// Two BF16 values (low half first) widened to FP32: a BF16 is the upper
+// 16 bits of the FP32 with the same value.
+__device__ inline float2 widen_bf16x2(uint32_t u) {
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+
+// SiLU and its derivative for two pre-activations z = acc + b, given half
+// the bias hb = b / 2, in packed FP32x2 arithmetic.  With h = z / 2 and
+// t = tanh(h) the logistic function is s = (1 + t) / 2, so
+//   silu(z)  = z s = h + h t,
+//   silu'(z) = s (1 + z (1 - s)) = s + s h (1 - t).
+__device__ inline void silu2(float2 acc, float2 hb, float2& y, float2& dy) {
+    const float2 half2 = make_float2(0.5f, 0.5f);
+    const float2 h = __ffma2_rn(acc, half2, hb);
+    const float2 t = make_float2(tanh_approx(h.x), tanh_approx(h.y));
+    y = __ffma2_rn(h, t, h);
+    const float2 s = __ffma2_rn(t, half2, half2);
+    const float2 a = __fmul2_rn(h, __ffma2_rn(t, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+    dy = __ffma2_rn(s, a, s);
+}
+
+// Store 32 columns (c0..c0+31 of row r) given as 16 packed BF16 pairs into
+// a swizzled tile of `rows` rows.
+__device__ inline void store_row32p(unsigned char* tile, int rows, int r, int c0,
+                                    const uint32_t (&p)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(tile + sw128_offset(rows, r, c0 + 8 * q)) =
+            make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+}
 
 // Store 32 FP32 values (columns c0..c0+31 of row r) as BF16 into a swizzled
 // tile of `rows` rows.
@@ -218,6 +250,24 @@ __device__ inline void tmem_ld16u(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Split form of tmem_ld16u (see tmem_ld32_issue / tmem_wait32).
+__device__ inline void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ inline void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
 }
 __device__ inline float2 unpack_bf16(uint32_t u) {
     __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
