@@ -6,8 +6,9 @@ package.  The product library never calls it, and it never calls the product
 library: the two share no code.
 
 Layout:
-  bead_sum.c   bead-bead Lennard-Jones double sum, brute-force body-pair
-               search, minimum bead distance (plain C, FP64, single thread)
+  bead_sum.c   bead-bead double sum (Lennard-Jones or the half-power
+               half-cosine of Eq. 1), brute-force body-pair search, minimum
+               bead distance (plain C, FP64, single thread)
   bodies.py    bead templates, mass, inertia, quaternion algebra (numpy FP64)
   nn.py        pair MLP energy, features, forces/torques as exact gradients
                (PyTorch CPU FP64 with autograd), force-matching loss gradient
@@ -73,6 +74,18 @@ def lib() -> ctypes.CDLL:
             L.orc_min_bead_distance.argtypes = [dp, dp, dp, dp, dp, ctypes.c_int64, dp,
                                                 ctypes.c_int64, dp]
             L.orc_min_bead_distance.restype = ctypes.c_double
+            L.orc_hphc.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, dp, dp]
+            L.orc_hphc.restype = ctypes.c_int
+            L.orc_hphc_cutoff.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+            L.orc_hphc_cutoff.restype = ctypes.c_double
+            L.orc_pot_cutoff.argtypes = [dp]
+            L.orc_pot_cutoff.restype = ctypes.c_double
+            L.orc_bead_pair_pot.argtypes = [dp, dp, dp, dp, dp, ctypes.c_int64, dp,
+                                            ctypes.c_int64, dp, dp, dp]
+            L.orc_bead_pair_pot.restype = None
+            L.orc_forces_beads_pot.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int64, dp, dp,
+                                               ctypes.c_int64, i64p, dp, dp, dp, dp, dp]
+            L.orc_forces_beads_pot.restype = None
             _lib = L
     return _lib
 
@@ -97,16 +110,52 @@ def lj(r: float, eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5):
     return u.value, f.value
 
 
-def bead_pair(p_i, q_i, p_j, q_j, box, tmpl_i, tmpl_j=None, eps=1.0, sigma=1.0, rc=2.5):
+def hphc(r: float, A: float, b: float, c: float, p: float, printed: bool = False):
+    """Half-power half-cosine bead potential (paper, Eq. 1): u(r) and -u'(r)/r.
+
+    printed=False: the continuous reading (half cosine -A (1 + cos c(r - b))
+    from -2A at r = b to 0 at b + pi/c); printed=True: the printed cosine
+    -A cos c(r - b), cut at its first zero b + pi/(2c), with the jump at b."""
+    u = ctypes.c_double()
+    f = ctypes.c_double()
+    lib().orc_hphc(float(r) ** 2, A, b, c, p, int(bool(printed)), ctypes.byref(u), ctypes.byref(f))
+    return u.value, f.value
+
+
+def hphc_cutoff(b: float, c: float, printed: bool = False) -> float:
+    return float(lib().orc_hphc_cutoff(b, c, int(bool(printed))))
+
+
+def pot_lj(eps: float = 1.0, sigma: float = 1.0, rc: float = 2.5) -> np.ndarray:
+    """Potential descriptor of the Lennard-Jones bead potential."""
+    return np.array([0.0, eps, sigma, rc, 0.0])
+
+
+def pot_hphc(A: float, b: float, c: float, p: float, printed: bool = False) -> np.ndarray:
+    """Potential descriptor of the half-power half-cosine bead potential."""
+    return np.array([2.0 if printed else 1.0, A, b, c, p])
+
+
+def pot_cutoff(pot) -> float:
+    return float(lib().orc_pot_cutoff(_p(_d(pot))))
+
+
+def bead_pair(p_i, q_i, p_j, q_j, box, tmpl_i, tmpl_j=None, eps=1.0, sigma=1.0, rc=2.5,
+              pot=None):
     """Bead double sum for one body pair (paper, Methods: U = sum_i sum_j u_bead).
 
-    Returns dict with E, F_i, F_j, tau_i, tau_j (space frame), the bead-level
-    virial (3x3) and the number of bead pairs inside the cutoff."""
+    The bead potential is Lennard-Jones (eps, sigma, rc) unless a descriptor
+    `pot` (pot_lj / pot_hphc) is given.  Returns dict with E, F_i, F_j,
+    tau_i, tau_j (space frame), the bead-level virial (3x3) and the number of
+    bead pairs inside the cutoff."""
     tmpl_i = _d(tmpl_i)
     tmpl_j = tmpl_i if tmpl_j is None else _d(tmpl_j)
     out = np.zeros(23)
-    lib().orc_bead_pair(_p(_d(p_i)), _p(_d(q_i)), _p(_d(p_j)), _p(_d(q_j)), _p(_d(box)),
-                        len(tmpl_i), _p(tmpl_i), len(tmpl_j), _p(tmpl_j), eps, sigma, rc, _p(out))
+    if pot is None:
+        pot = pot_lj(eps, sigma, rc)
+    lib().orc_bead_pair_pot(_p(_d(p_i)), _p(_d(q_i)), _p(_d(p_j)), _p(_d(q_j)), _p(_d(box)),
+                            len(tmpl_i), _p(tmpl_i), len(tmpl_j), _p(tmpl_j), _p(_d(pot)),
+                            _p(out))
     return {"E": out[0], "F_i": out[1:4].copy(), "F_j": out[4:7].copy(),
             "tau_i": out[7:10].copy(), "tau_j": out[10:13].copy(),
             "virial": out[13:22].reshape(3, 3).copy(), "n_in": int(out[22])}
@@ -125,8 +174,10 @@ def pairs_bruteforce(pos, box, Rc) -> np.ndarray:
         cap = int(m)
 
 
-def forces_beads(pos, quat, box, tmpl, pairs, eps=1.0, sigma=1.0, rc=2.5, per_pair=False):
-    """Per-body bead-sum forces and torques over the given body pairs.
+def forces_beads(pos, quat, box, tmpl, pairs, eps=1.0, sigma=1.0, rc=2.5, per_pair=False,
+                 pot=None):
+    """Per-body bead-sum forces and torques over the given body pairs, with the
+    Lennard-Jones bead potential (eps, sigma, rc) or the descriptor `pot`.
 
     Returns (F [N,3], tau [N,3], E, virial9 (COM virial sum R_ij (x) F_j)
     [, per-pair array (M, 23)])."""
@@ -140,9 +191,11 @@ def forces_beads(pos, quat, box, tmpl, pairs, eps=1.0, sigma=1.0, rc=2.5, per_pa
     E = np.zeros(1)
     vir = np.zeros(9)
     pp = np.zeros((len(pairs), 23)) if per_pair else None
-    lib().orc_forces_beads(N, _p(pos), _p(quat), _p(_d(box)), len(tmpl), _p(tmpl), eps, sigma, rc,
-                           len(pairs), _pi(pairs), _p(F), _p(tau), _p(E), _p(vir),
-                           _p(pp) if pp is not None else None)
+    if pot is None:
+        pot = pot_lj(eps, sigma, rc)
+    lib().orc_forces_beads_pot(N, _p(pos), _p(quat), _p(_d(box)), len(tmpl), _p(tmpl),
+                               _p(_d(pot)), len(pairs), _pi(pairs), _p(F), _p(tau), _p(E),
+                               _p(vir), _p(pp) if pp is not None else None)
     if per_pair:
         return F, tau, float(E[0]), vir.reshape(3, 3), pp
     return F, tau, float(E[0]), vir.reshape(3, 3)

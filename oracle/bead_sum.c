@@ -13,7 +13,8 @@
  *     and translated by its centre of mass p (SI Sec. 1 lists p and q as the
  *     raw pair configuration);
  *   - u_bead: Lennard-Jones 12-6, energy shifted to zero at the cutoff r_c,
- *     force truncated (not shifted) at r_c; r < r_c strictly;
+ *     force truncated (not shifted) at r_c; r < r_c strictly; or the
+ *     half-power half-cosine of Eq. 1 (orc_hphc);
  *   - every bead pair (k of body i, l of body j) is visited; no cell list, no
  *     culling.  Force on bead l is f = -u'(r) r_hat with r = b_l - a_k.
  *   - forces and torques are accumulated on BOTH bodies directly:
@@ -29,6 +30,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+
+/* pi to double precision (C11 does not define M_PI) */
+static const double kPi = 3.14159265358979323846;
 
 /* Rotation matrix of a unit quaternion q = (w, x, y, z), scalar first,
  * active rotation v' = q v q^*.  Row-major R[3*a + b]. */
@@ -83,15 +87,69 @@ int orc_lj(double r2, double eps, double sigma, double rc, double* u, double* f_
 }
 
 /*
+ * Half-power half-cosine bead potential (paper, Eq. 1, with A, b, c, p; the
+ * paper's cube and cylinder workload uses A = 0.00035, b = 1.46375,
+ * c = 3.3833, p = 2.5).  As printed, the repulsive branch (b - r)^p - 2A ends
+ * at -2A for r = b while the cosine branch -A cos(c (r - b)) starts at -A,
+ * and the cosine branch has no stated end.  Two readings:
+ *   printed = 0 (default): the attractive branch is the half cosine from the
+ *     minimum -2A at r = b up to 0 at r = b + pi/c,
+ *       u = -A (1 + cos(c (r - b)))  for b < r < b + pi/c,  0 beyond;
+ *     u and u' are continuous everywhere (u'(b) = u'(b + pi/c) = 0);
+ *   printed = 1: the printed cosine, cut where it first reaches zero,
+ *       u = -A cos(c (r - b))        for b < r < b + pi/(2c), 0 beyond,
+ *     which keeps the jump of A at r = b.
+ * Repulsive branch in both: u = (b - r)^p - 2A for r <= b.
+ * Returns 1 and fills u, f_over_r (= -u'(r)/r) when r is inside the
+ * cutoff (strict), else 0.
+ */
+double orc_hphc_cutoff(double b, double c, int printed) {
+    return printed ? b + 0.5 * kPi / c : b + kPi / c;
+}
+
+int orc_hphc(double r2, double A, double b, double c, double p, int printed, double* u,
+             double* f_over_r) {
+    const double r = sqrt(r2);
+    if (!(r < orc_hphc_cutoff(b, c, printed))) { *u = 0.0; *f_over_r = 0.0; return 0; }
+    if (r <= b) {
+        const double x = b - r;
+        *u = pow(x, p) - 2.0 * A;
+        /* u'(r) = -p (b - r)^(p - 1) */
+        *f_over_r = p * pow(x, p - 1.0) / r;
+    } else {
+        const double t = c * (r - b);
+        *u = printed ? -A * cos(t) : -A * (1.0 + cos(t));
+        /* u'(r) = A c sin(c (r - b)) in both readings */
+        *f_over_r = -A * c * sin(t) / r;
+    }
+    return 1;
+}
+
+/* Bead potential descriptor used by the _pot entry points:
+ *   pot[0] = 0: Lennard-Jones, pot[1..3] = eps, sigma, rc (as orc_lj);
+ *   pot[0] = 1 or 2: half-power half-cosine, pot[1..4] = A, b, c, p; 1 is
+ *   the continuous reading, 2 the printed one (see orc_hphc). */
+static int bead_u(const double* pot, double r2, double* u, double* f_over_r) {
+    if (pot[0] == 0.0) return orc_lj(r2, pot[1], pot[2], pot[3], u, f_over_r);
+    return orc_hphc(r2, pot[1], pot[2], pot[3], pot[4], pot[0] == 2.0, u, f_over_r);
+}
+
+/* Cutoff radius of a potential descriptor. */
+double orc_pot_cutoff(const double* pot) {
+    if (pot[0] == 0.0) return pot[3];
+    return orc_hphc_cutoff(pot[2], pot[3], pot[0] == 2.0);
+}
+
+/*
  * One body pair.  out[0] = E; out[1..3] = F_i; out[4..6] = F_j;
  * out[7..9] = tau_i; out[10..12] = tau_j; out[13..21] = bead-level pair
  * virial W_ab = sum over bead pairs of r_a f_b (r = b_l - a_k, f on bead l);
  * out[22] = number of bead pairs with r < rc.
  */
-void orc_bead_pair(const double p_i[3], const double q_i[4], const double p_j[3],
-                   const double q_j[4], const double box[3], int64_t n_i,
-                   const double* tmpl_i, int64_t n_j, const double* tmpl_j, double eps,
-                   double sigma, double rc, double out[23]) {
+void orc_bead_pair_pot(const double p_i[3], const double q_i[4], const double p_j[3],
+                       const double q_j[4], const double box[3], int64_t n_i,
+                       const double* tmpl_i, int64_t n_j, const double* tmpl_j,
+                       const double* pot, double out[23]) {
     double Ri[9], Rj[9], Rij[3];
     quat_matrix(q_i, Ri);
     quat_matrix(q_j, Rj);
@@ -110,7 +168,7 @@ void orc_bead_pair(const double p_i[3], const double q_i[4], const double p_j[3]
             }
             const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
             double u, fr;
-            if (!orc_lj(r2, eps, sigma, rc, &u, &fr)) continue;
+            if (!bead_u(pot, r2, &u, &fr)) continue;
             double f[3] = {fr * r[0], fr * r[1], fr * r[2]};
             double mf[3] = {-f[0], -f[1], -f[2]};
             double ti[3], tj[3];
@@ -128,6 +186,15 @@ void orc_bead_pair(const double p_i[3], const double q_i[4], const double p_j[3]
             out[22] += 1.0;
         }
     }
+}
+
+/* The same with the Lennard-Jones potential (eps, sigma, rc). */
+void orc_bead_pair(const double p_i[3], const double q_i[4], const double p_j[3],
+                   const double q_j[4], const double box[3], int64_t n_i,
+                   const double* tmpl_i, int64_t n_j, const double* tmpl_j, double eps,
+                   double sigma, double rc, double out[23]) {
+    const double pot[4] = {0.0, eps, sigma, rc};
+    orc_bead_pair_pot(p_i, q_i, p_j, q_j, box, n_i, tmpl_i, n_j, tmpl_j, pot, out);
 }
 
 /* Brute-force body-pair search: all i < j with |R_ij| < Rc (minimum image).
@@ -159,10 +226,10 @@ int64_t orc_pairs_bruteforce(int64_t N, const double* pos, const double box[3], 
  * (from orc_pairs_bruteforce) so that a sample of the list can be evaluated.
  * per_pair (nullable): n_pairs x 23 of the orc_bead_pair outputs.
  */
-void orc_forces_beads(int64_t N, const double* pos, const double* quat, const double box[3],
-                      int64_t n_beads, const double* tmpl, double eps, double sigma, double rc,
-                      int64_t n_pairs, const int64_t* pairs, double* F, double* tau,
-                      double* energy, double* virial9, double* per_pair) {
+void orc_forces_beads_pot(int64_t N, const double* pos, const double* quat, const double box[3],
+                          int64_t n_beads, const double* tmpl, const double* pot,
+                          int64_t n_pairs, const int64_t* pairs, double* F, double* tau,
+                          double* energy, double* virial9, double* per_pair) {
     memset(F, 0, 3 * N * sizeof(double));
     memset(tau, 0, 3 * N * sizeof(double));
     *energy = 0.0;
@@ -170,8 +237,8 @@ void orc_forces_beads(int64_t N, const double* pos, const double* quat, const do
     for (int64_t m = 0; m < n_pairs; ++m) {
         const int64_t i = pairs[2 * m], j = pairs[2 * m + 1];
         double out[23];
-        orc_bead_pair(&pos[3 * i], &quat[4 * i], &pos[3 * j], &quat[4 * j], box, n_beads, tmpl,
-                      n_beads, tmpl, eps, sigma, rc, out);
+        orc_bead_pair_pot(&pos[3 * i], &quat[4 * i], &pos[3 * j], &quat[4 * j], box, n_beads,
+                          tmpl, n_beads, tmpl, pot, out);
         double Rij[3];
         min_image(&pos[3 * i], &pos[3 * j], box, Rij);
         *energy += out[0];
@@ -185,6 +252,16 @@ void orc_forces_beads(int64_t N, const double* pos, const double* quat, const do
             for (int y = 0; y < 3; ++y) virial9[3 * x + y] += Rij[x] * out[4 + y];
         if (per_pair) memcpy(&per_pair[23 * m], out, sizeof(out));
     }
+}
+
+/* The same with the Lennard-Jones potential (eps, sigma, rc). */
+void orc_forces_beads(int64_t N, const double* pos, const double* quat, const double box[3],
+                      int64_t n_beads, const double* tmpl, double eps, double sigma, double rc,
+                      int64_t n_pairs, const int64_t* pairs, double* F, double* tau,
+                      double* energy, double* virial9, double* per_pair) {
+    const double pot[4] = {0.0, eps, sigma, rc};
+    orc_forces_beads_pot(N, pos, quat, box, n_beads, tmpl, pot, n_pairs, pairs, F, tau, energy,
+                         virial9, per_pair);
 }
 
 /* Smallest bead-bead distance between two bodies (minimum image on the COMs). */

@@ -17,6 +17,22 @@ the body frame, principal axes along the template axes:
      L_b <- Rot_k(-phi) L_b;  then q <- q/|q|
   4. F, tau at the new configuration
   5. v += dt/2 F/M;  L_b += dt/2 R(q)^T tau
+
+Nose-Hoover NVT (paper, Results: the bead-form runs keep the temperature with
+a Nose-Hoover thermostat at dt = 0.005; no equations are given).  Reading:
+one thermostat variable xi acts on every translational and rotational
+degree of freedom,
+  dv/dt = F/M - xi v,   dL_b/dt = tau_b - w x L_b - xi L_b,
+  dxi/dt = (2K - g kT) / Q,   d eta/dt = xi,
+with K the total (translational + rotational) kinetic energy, g = 6N - 3
+(the centre-of-mass momentum stays zero), Q = g kT tau_T^2 for a thermostat
+period tau_T.  H' = E_pot + K + Q xi^2/2 + g kT eta is conserved.  The step
+is the time-reversible Trotter split
+  T(dt/2) . [steps 1-5 above] . T(dt/2),
+  T(h): xi += h/2 G(K);  s = exp(-xi h);  v, L_b *= s;  K *= s^2;
+        eta += xi h;  xi += h/2 G(K),       G(K) = (2K - g kT) / Q.
+Image counters (whole box lengths crossed, for unwrapped positions) are kept
+when the state carries them.
 """
 from __future__ import annotations
 
@@ -61,17 +77,72 @@ def kinetic(vel, Lb, mass, inertia):
 
 
 def step(state, force_fn, mass, inertia, box, dt):
-    """One velocity-Verlet step.  state = dict(pos, quat, vel, angmom, F, tau);
-    force_fn(pos, quat) -> (F, tau, E_pot).  Returns the new state and E_pot."""
+    """One velocity-Verlet step.  state = dict(pos, quat, vel, angmom, F, tau
+    [, image]); force_fn(pos, quat) -> (F, tau, E_pot).  Returns the new state
+    and E_pot."""
     box = np.asarray(box, dtype=np.float64)
     vel, Lb = half_kick(state["vel"], state["angmom"], state["quat"], state["F"], state["tau"],
                         mass, dt)
     pos = state["pos"] + dt * vel
-    pos = pos - box * np.floor(pos / box)
+    shift = np.floor(pos / box)
+    pos = pos - box * shift
     quat, Lb = rotate_free(state["quat"], Lb, inertia, dt)
     F, tau, E = force_fn(pos, quat)
     vel, Lb = half_kick(vel, Lb, quat, F, tau, mass, dt)
-    return {"pos": pos, "quat": quat, "vel": vel, "angmom": Lb, "F": F, "tau": tau}, E
+    out = {"pos": pos, "quat": quat, "vel": vel, "angmom": Lb, "F": F, "tau": tau}
+    if "image" in state:
+        out["image"] = state["image"] + shift
+    return out, E
+
+
+def thermostat_half(vel, Lb, thermo, K, h):
+    """T(h) of the Nose-Hoover split: returns scaled vel, L_b, the new
+    thermostat dict and the scaled kinetic energy."""
+    g_kT = thermo["g"] * thermo["kT"]
+    Q = thermo["Q"]
+    xi = thermo["xi"] + 0.5 * h * (2.0 * K - g_kT) / Q
+    s = np.exp(-xi * h)
+    K = K * s * s
+    eta = thermo["eta"] + xi * h
+    xi = xi + 0.5 * h * (2.0 * K - g_kT) / Q
+    return vel * s, Lb * s, dict(thermo, xi=xi, eta=eta), K
+
+
+def step_nvt(state, force_fn, mass, inertia, box, dt, thermo):
+    """One Nose-Hoover NVT step: T(dt/2), the velocity-Verlet step, T(dt/2).
+    thermo = dict(xi, eta, kT, Q, g).  Returns the new state, E_pot and the
+    new thermostat dict."""
+    kt, kr = kinetic(state["vel"], state["angmom"], mass, inertia)
+    vel, Lb, thermo, _ = thermostat_half(state["vel"], state["angmom"], thermo, kt + kr, 0.5 * dt)
+    st, E = step(dict(state, vel=vel, angmom=Lb), force_fn, mass, inertia, box, dt)
+    kt, kr = kinetic(st["vel"], st["angmom"], mass, inertia)
+    vel, Lb, thermo, _ = thermostat_half(st["vel"], st["angmom"], thermo, kt + kr, 0.5 * dt)
+    return dict(st, vel=vel, angmom=Lb), E, thermo
+
+
+def thermostat(n_bodies: int, kT: float, tau: float, xi: float = 0.0, eta: float = 0.0):
+    """Thermostat dict for n_bodies rigid bodies: g = 6N - 3, Q = g kT tau^2."""
+    g = 6.0 * n_bodies - 3.0
+    return {"xi": xi, "eta": eta, "kT": kT, "g": g, "Q": g * kT * tau * tau}
+
+
+def conserved_nvt(E_pot, K, thermo):
+    """H' = E_pot + K + Q xi^2 / 2 + g kT eta."""
+    return E_pot + K + 0.5 * thermo["Q"] * thermo["xi"] ** 2 + thermo["g"] * thermo["kT"] * thermo["eta"]
+
+
+def run_nvt(state, force_fn, mass, inertia, box, dt, n_steps, thermo):
+    """n_steps of NVT; returns the final state, the thermostat dict and H'
+    after each step (index 0 = before the first step)."""
+    F, tau, E = force_fn(state["pos"], state["quat"])
+    st = dict(state, F=F, tau=tau)
+    kt, kr = kinetic(st["vel"], st["angmom"], mass, inertia)
+    h = [conserved_nvt(E, kt + kr, thermo)]
+    for _ in range(n_steps):
+        st, E, thermo = step_nvt(st, force_fn, mass, inertia, box, dt, thermo)
+        kt, kr = kinetic(st["vel"], st["angmom"], mass, inertia)
+        h.append(conserved_nvt(E, kt + kr, thermo))
+    return st, thermo, np.array(h)
 
 
 def run(state, force_fn, mass, inertia, box, dt, n_steps):

@@ -34,6 +34,13 @@ SHAPES = {
 }
 
 
+# The paper's half-power half-cosine bead parameters (Eq. 1 and the text
+# after it; units eps, sigma): well depth 2A, minimum at b, cosine rate c,
+# repulsive power p.  Its cube workload runs at phi = 0.16 with a
+# Nose-Hoover thermostat and dt = 0.005.
+HPHC_PAPER = {"A": 0.00035, "b": 1.46375, "c": 3.3833, "p": 2.5}
+
+
 def box_length(n_bodies: int, phi: float, shape: str = "cube") -> float:
     return (n_bodies * SHAPES[shape]["v_particle"] / phi) ** (1.0 / 3.0)
 
