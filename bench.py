@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--train-lam-e", type=float, default=0.1)
     ap.add_argument("--cyl-train-steps", type=int, default=300)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-paper-workload", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--serving-steps", type=int, default=1000)
     ap.add_argument("--serving-nmax", type=int, default=65536)
@@ -598,6 +599,76 @@ def main():
                     "steps_timed": 200}
         del s256, m256
 
+    # ---- the paper's own workload shape: half-power half-cosine bead
+    # potential (Eq. 1, continuous reading) between cubes at phi = 0.16 under
+    # the Nose-Hoover thermostat (kT = 0.6, period 0.5) with dt = 0.005, bead
+    # path; then the cost of one g(r) / MSD / MSR frame
+    paper_wl = None
+    if "beads" in paths and not args.no_paper_workload:
+        KT_P, DT_P, PHI_P = 0.6, 0.005, 0.16
+        stp, Lp = inputs_mod.system_state(N_BODIES, PHI_P, KT_P, SEED + 7, 125.0, [500.0] * 3, "cube")
+        sp = api.System(N_BODIES, [Lp] * 3, "cube", skin=args.skin, potential="hphc",
+                        hphc=inputs_mod.HPHC_PAPER)
+        sp.set_state(*(torch.from_numpy(stp[k]).cuda() for k in ("pos", "quat", "vel", "angmom")))
+        sp.set_thermostat(KT_P, 0.5)
+        sp.forces_beads()
+        sp.step(200, DT_P)  # warm-up: graph capture, list rebuilds settle
+        n_pairs_p = sp.build_pairs()
+        sp.set_reference()
+        ev_p = []
+        for _ in range(300):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sp.step(1, DT_P)
+            b.record(stream)
+            ev_p.append((a, b))
+        torch.cuda.synchronize()
+        ms_p = statistics.mean(a.elapsed_time(b) for a, b in ev_p)
+        _, kt_p, kr_p = sp.energy()
+        # the pair kernel alone (k_bead_pairs with the half-power half-cosine body)
+        sp.build_pairs()
+        kp = []
+        for _ in range(10):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sp.eval_pairs(api.RB_PATH_BEADS)
+            b.record(stream)
+            kp.append((a, b))
+        torch.cuda.synchronize()
+        kms_p = statistics.mean(a.elapsed_time(b) for a, b in kp)
+        flops_p = bead_flops_per_pair(125) * n_pairs_p
+        # analyses: one g(r) frame (pair list current) and one MSD / MSR read
+        r_max_p = 0.95 * sp.pair_cutoff
+        counts = sp.gr_counts(r_max_p, 200)
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        for _ in range(10):
+            sp.gr_counts(r_max_p, 200, counts)
+        gb.record(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        msd_p, msr_p = sp.msd_msr()
+        t_msd = time.perf_counter() - t0
+        g_p = sp.gr_normalise(counts.cpu().numpy(), r_max_p, 11)
+        paper_wl = {
+            "workload": f"{N_BODIES} cubes (5x5x5 beads), half-power half-cosine beads of Eq. 1 "
+                        f"(A=0.00035, b=1.46375, c=3.3833, p=2.5; continuous reading, cutoff "
+                        f"b + pi/c), phi={PHI_P}, Nose-Hoover NVT kT={KT_P} (period 0.5), "
+                        f"dt={DT_P}, skin {args.skin}",
+            "ms_per_md_step": ms_p, "md_steps_per_s": 1e3 / ms_p,
+            "pair_evals_per_s": n_pairs_p / (ms_p * 1e-3), "pairs": n_pairs_p,
+            "steps_timed": 300, "temperature_2K_over_g": 2 * (kt_p + kr_p) / (6 * N_BODIES - 3),
+            "kernel": "k_bead_pairs (half-power half-cosine)", "kernel_ms": kms_p,
+            "kernel_tflops": flops_p / (kms_p * 1e-3) / 1e12,
+            "frac_of_fp32_peak": flops_p / (kms_p * 1e-3) / 1e12
+                                 / fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0)),
+            "gr_frame_ms": ga.elapsed_time(gb) / 10, "msd_msr_read_ms": t_msd * 1e3,
+            "msd_after_300_steps": msd_p, "msr_after_300_steps": msr_p,
+            "g_r_first_peak": {"r": float((np.argmax(g_p) + 0.5) * r_max_p / 200), "g": float(g_p.max())}}
+        del sp
+
     # ---- NVE energy conservation: a fresh copy of the workload per path, run
     # for --drift-steps steps with the FP64 total energy read every
     # --drift-every steps (outside every timed region)
@@ -720,6 +791,7 @@ def main():
             "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_fp32": roof_f32, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
             "nn_bf16_width256": width256, "nve_drift": drift, "training_cylinders_w256": train_cyl,
+            "paper_workload_hphc_nvt": paper_wl,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "results_finite": e2e_ok,

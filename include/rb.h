@@ -56,7 +56,7 @@ typedef enum rb_status {
 } rb_status;
 
 enum { RB_SHAPE_CUBE = 0, RB_SHAPE_CYLINDER = 1, RB_SHAPE_CUSTOM = 2 };
-enum { RB_POT_LJ = 0 };
+enum { RB_POT_LJ = 0, RB_POT_HPHC = 1, RB_POT_HPHC_PRINTED = 2 };
 enum { RB_PATH_BEADS = 0, RB_PATH_NN = 1 };
 enum { RB_FP32 = 0, RB_BF16 = 1 };
 
@@ -84,13 +84,29 @@ typedef struct rb_body_type {
     float bead_mass;
 } rb_body_type;
 
-/* Bead-bead potential.  RB_POT_LJ: 4 eps ((sigma/r)^12 - (sigma/r)^6) for
- * r < rcut, shifted to zero energy at rcut (force not shifted). */
+/* Bead-bead potential.
+ *   RB_POT_LJ: 4 eps ((sigma/r)^12 - (sigma/r)^6) for r < rcut, shifted to
+ *     zero energy at rcut (force not shifted).  A, b, c, p unused.
+ *   RB_POT_HPHC: the half-power half-cosine of the paper's Eq. 1 with
+ *     parameters A, b, c, p (the paper's workload: A = 0.00035 eps,
+ *     b = 1.46375 sigma, c = 3.3833 / sigma, p = 2.5; required A >= 0,
+ *     b > 0, c > 0, p > 1), in the continuous reading:
+ *       u = (b - r)^p - 2A             for r <= b,
+ *       u = -A (1 + cos(c (r - b)))    for b < r < b + pi/c,   0 beyond.
+ *     The printed equation jumps from -2A to -A at r = b and gives the
+ *     cosine branch no end; this reading keeps its repulsive branch, its
+ *     minimum -2A at b and its rate c, and makes u and u' continuous.
+ *   RB_POT_HPHC_PRINTED: the equation as printed, -A cos(c (r - b)) for
+ *     b < r < b + pi/(2c) (its first zero), 0 beyond; jump of A at r = b.
+ * For the HPHC kinds rcut and eps are ignored (the cutoff follows from b and
+ * c, the energy scale is A); sigma stays the length unit of the training
+ * sampler's contact distance. */
 typedef struct rb_bead_potential {
     int32_t kind;
     float eps;
     float sigma;
     float rcut;
+    float A, b, c, p; /* RB_POT_HPHC* only */
 } rb_bead_potential;
 
 typedef struct rb_system_desc {
@@ -160,11 +176,69 @@ rb_status rb_forces_beads(rb_system* sys, float* force, float* torque, double* e
 typedef struct rb_mlp rb_mlp;
 rb_status rb_eval_pairs(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision);
 
-/* Integrate n_steps of NVE velocity Verlet (NO_SQUISH free-rotor split for
- * the orientation) with forces from `path` (RB_PATH_BEADS, or RB_PATH_NN with
- * `mlp` at `precision`).  Each step is one CUDA-graph launch; asynchronous. */
+/* Integrate n_steps of velocity Verlet (NO_SQUISH free-rotor split for the
+ * orientation) with forces from `path` (RB_PATH_BEADS, or RB_PATH_NN with
+ * `mlp` at `precision`): NVE, or NVT when a thermostat is set.  Each step is
+ * one CUDA-graph launch; asynchronous.  The integrator also counts, per body,
+ * the box lengths crossed (unwrapped positions, see rb_msd_msr). */
 rb_status rb_step(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
                   int64_t n_steps, float dt);
+
+/* Nose-Hoover thermostat for rb_step (the paper's bead-form runs keep the
+ * temperature with one, Results, with no equations given).  Reading: one
+ * thermostat variable xi on all translational and rotational degrees of
+ * freedom, dv/dt = F/M - xi v, dL_b/dt = tau_b - w x L_b - xi L_b,
+ * dxi/dt = (2K - g kT)/Q, deta/dt = xi, with K the total kinetic energy,
+ * g = 6N - 3 and Q = g kT tau^2 (tau: thermostat period).  Each step is the
+ * time-reversible split T(dt/2) . velocity Verlet . T(dt/2), where T(h)
+ * moves xi by h/2 G(K), scales v and L_b by exp(-xi h), advances eta by
+ * xi h and moves xi by h/2 G(K) again (G = (2K - g kT)/Q, FP64 on the
+ * device).  H' = E_pot + K + Q xi^2/2 + g kT eta is conserved.
+ * rb_set_thermostat: tau > 0 turns it on with xi = eta = 0 at the current
+ * state (kT > 0 required, else RB_EINVAL); tau <= 0 turns it off (NVE).
+ * Synchronises.  rb_set_state keeps xi and eta and re-reads K.
+ * rb_get_thermostat: out4 = {xi, eta, Q, g kT} between steps (all zero when
+ * off); host array; synchronises. */
+rb_status rb_set_thermostat(rb_system* sys, float kT, float tau);
+rb_status rb_get_thermostat(const rb_system* sys, double* out4_host);
+
+/* ---------------------------------------------------------------- analyses
+ * Structure and kinetics of a run (paper, Results: the pair correlation
+ * function g(r) of the centres of mass, the mean square displacement (MSD)
+ * and the mean square rotation (MSR, SI Sec. 5)).
+ *
+ * rb_set_reference: store the current positions, image counters and
+ * orientations as the reference frame of rb_msd_msr (device copy,
+ * asynchronous; the first call allocates 36 N bytes + a few KB).
+ * rb_msd_msr: MSD = (1/N) sum_i |r_i - r_i(ref)|^2 over the unwrapped centres
+ * (pos + image x box) and MSR = (1/N) sum_i d(q_i(ref), q_i) with the
+ * orientational distance d(q1, q2) = 1 - <q1, q2>^2 (SI Sec. 5; q and -q
+ * give the same d).  FP64 on the device, fixed summation order; host
+ * outputs (nullable); synchronises; RB_EINVAL before rb_set_reference.
+ * rb_get_images: the image counters (N x 4 int32, host; the fourth lane is
+ * unused), synchronises.  They are zeroed by rb_set_state(pos) and moved by
+ * every rb_step when a centre is wrapped into the box.
+ *
+ * rb_gr_counts: adds one to counts[k] for every body pair i < j whose
+ * minimum-image centre distance r satisfies r^2 < r_max^2, with
+ * k = min(trunc(r * (n_bins / r_max)), n_bins - 1).  counts: caller's device
+ * array of n_bins uint32, accumulated over calls (zero it first).  The
+ * distance is formed in FP32 with round-to-nearest operations in this order:
+ * d = p_j - p_i; d = d - L rint(d invL) (invL = 1/L rounded to FP32, each
+ * product and difference rounded); r^2 = (dx dx + dy dy) + dz dz; r =
+ * sqrt(r^2); the scale n_bins / r_max is rounded to FP32 first.  Requires
+ * 0 < r_max <= Rc (the pair list holds every pair within Rc) and
+ * 1 <= n_bins <= 4096 (RB_EINVAL otherwise).  Brings the pair list up to
+ * date first; asynchronous.
+ * rb_gr_normalise: g_k = counts_k / (n_frames * ideal_k), ideal_k =
+ * N (N - 1)/2 * (4 pi/3)(r_{k+1}^3 - r_k^3) / V with r_k = k r_max / n_bins
+ * (host arrays, FP64). */
+rb_status rb_set_reference(rb_system* sys);
+rb_status rb_msd_msr(rb_system* sys, double* msd_host, double* msr_host);
+rb_status rb_get_images(const rb_system* sys, int32_t* images_host);
+rb_status rb_gr_counts(rb_system* sys, float r_max, int32_t n_bins, uint32_t* counts);
+rb_status rb_gr_normalise(const rb_system* sys, const uint32_t* counts_host, int32_t n_bins,
+                          float r_max, int64_t n_frames, double* g_host);
 
 /* FP64 potential, translational and rotational kinetic energy of the current
  * state (forces of the last evaluation).  Synchronises. */
@@ -172,7 +246,8 @@ rb_status rb_energy(rb_system* sys, double* e_pot_host, double* ke_trans_host,
                     double* ke_rot_host);
 
 /* Checkpoint / resume.  rb_checkpoint writes the state, step counter, box,
- * skin and body template to `path` (versioned binary, synchronises);
+ * skin, body template, image counters and thermostat (xi, eta, K, kT, tau)
+ * to `path` (versioned binary, version 2; synchronises);
  * rb_restore reads it into a system created with the same N, body and box
  * (RB_EINVAL otherwise).  Every kernel is deterministic, so a restored run
  * continues bit for bit like the uninterrupted one. */

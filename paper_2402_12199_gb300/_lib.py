@@ -17,7 +17,7 @@ STATUS = {0: "RB_OK", 1: "RB_EINVAL", 2: "RB_ENOMEM", 3: "RB_ECUDA", 4: "RB_EOVE
 RB_OK, RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_EOVERFLOW = 0, 1, 2, 3, 4
 RB_ENOT_READY, RB_ETIMEOUT, RB_EFAULT, RB_EBUSY, RB_ENOTSUP = 5, 6, 7, 8, 9
 RB_SHAPE_CUBE, RB_SHAPE_CYLINDER, RB_SHAPE_CUSTOM = 0, 1, 2
-RB_POT_LJ = 0
+RB_POT_LJ, RB_POT_HPHC, RB_POT_HPHC_PRINTED = 0, 1, 2
 RB_PATH_BEADS, RB_PATH_NN = 0, 1
 RB_FP32, RB_BF16 = 0, 1
 
@@ -35,7 +35,8 @@ class rb_body_type(ctypes.Structure):
 
 class rb_bead_potential(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("eps", ctypes.c_float), ("sigma", ctypes.c_float),
-                ("rcut", ctypes.c_float)]
+                ("rcut", ctypes.c_float), ("A", ctypes.c_float), ("b", ctypes.c_float),
+                ("c", ctypes.c_float), ("p", ctypes.c_float)]
 
 
 class rb_system_desc(ctypes.Structure):
@@ -90,6 +91,13 @@ SIGNATURES = {
     "rb_checkpoint": (I32, [P, ctypes.c_char_p]),
     "rb_restore": (I32, [P, ctypes.c_char_p]),
     "rb_get_step": (I32, [P, I64P]),
+    "rb_set_thermostat": (I32, [P, F32, F32]),
+    "rb_get_thermostat": (I32, [P, DP]),
+    "rb_set_reference": (I32, [P]),
+    "rb_msd_msr": (I32, [P, DP, DP]),
+    "rb_get_images": (I32, [P, I32P]),
+    "rb_gr_counts": (I32, [P, F32, I32, P]),
+    "rb_gr_normalise": (I32, [P, ctypes.POINTER(ctypes.c_uint32), I32, F32, I64, DP]),
     "rb_mlp_n_params": (I64, [I32, I32]),
     "rb_mlp_create": (I32, [I32, I32, P, ctypes.POINTER(P)]),
     "rb_mlp_destroy": (I32, [P]),

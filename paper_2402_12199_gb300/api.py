@@ -15,6 +15,8 @@ from ._lib import (RB_BF16, RB_FP32, RB_PATH_BEADS, RB_PATH_NN, RB_SHAPE_CUBE, R
                    RB_SHAPE_CYLINDER, RBError, check, load)
 
 SHAPES = {"cube": RB_SHAPE_CUBE, "cylinder": RB_SHAPE_CYLINDER, "custom": RB_SHAPE_CUSTOM}
+POTENTIALS = {"lj": _lib.RB_POT_LJ, "hphc": _lib.RB_POT_HPHC,
+              "hphc_printed": _lib.RB_POT_HPHC_PRINTED}
 PRECISION = {"fp32": RB_FP32, "bf16": RB_BF16, RB_FP32: RB_FP32, RB_BF16: RB_BF16}
 
 __all__ = ["System", "MLP", "RBError", "RB_PATH_BEADS", "RB_PATH_NN", "RB_FP32", "RB_BF16"]
@@ -51,7 +53,11 @@ class System:
 
     def __init__(self, n_bodies: int, box, shape: str = "cube", eps: float = 1.0,
                  sigma: float = 1.0, rcut: float = 2.5, max_neighbors: int = 0,
-                 template=None, bead_mass: float = 1.0, stream=None, skin: float = 0.0):
+                 template=None, bead_mass: float = 1.0, stream=None, skin: float = 0.0,
+                 potential: str = "lj", hphc=None):
+        """potential: "lj" (eps, sigma, rcut), "hphc" (the continuous reading
+        of Eq. 1) or "hphc_printed"; hphc = dict(A=, b=, c=, p=) for the two
+        half-power half-cosine kinds."""
         L = load()
         d = _lib.rb_system_desc()
         d.body.shape = SHAPES[shape]
@@ -62,8 +68,10 @@ class System:
             d.body.n_beads = len(t)
             d.body.bead_xyz_host = t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         d.body.bead_mass = bead_mass
-        d.pot.kind = 0
+        d.pot.kind = POTENTIALS[potential]
         d.pot.eps, d.pot.sigma, d.pot.rcut = eps, sigma, rcut
+        if potential != "lj":
+            d.pot.A, d.pot.b, d.pot.c, d.pot.p = (float(hphc[k]) for k in ("A", "b", "c", "p"))
         box = np.broadcast_to(np.asarray(box, dtype=np.float32), (3,))
         for a in range(3):
             d.box[a] = float(box[a])
@@ -214,6 +222,44 @@ class System:
 
     def sync(self):
         check(load().rb_sync(self._h))
+
+    def set_thermostat(self, kT: float, tau: float):
+        """Nose-Hoover NVT for step() (tau <= 0: off, NVE)."""
+        check(load().rb_set_thermostat(self._h, float(kT), float(tau)))
+
+    def thermostat(self) -> dict:
+        out = (ctypes.c_double * 4)()
+        check(load().rb_get_thermostat(self._h, out))
+        return {"xi": out[0], "eta": out[1], "Q": out[2], "g_kT": out[3]}
+
+    def set_reference(self):
+        check(load().rb_set_reference(self._h))
+
+    def msd_msr(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        check(load().rb_msd_msr(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def images(self) -> np.ndarray:
+        out = np.zeros((self.N, 4), dtype=np.int32)
+        check(load().rb_get_images(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
+
+    def gr_counts(self, r_max: float, n_bins: int, counts: torch.Tensor = None) -> torch.Tensor:
+        """Adds this frame's pair-distance counts into `counts` (device int32
+        tensor of n_bins, zero-initialised when None)."""
+        if counts is None:
+            counts = torch.zeros(n_bins, dtype=torch.int32, device="cuda")
+        check(load().rb_gr_counts(self._h, float(r_max), int(n_bins), counts.data_ptr()))
+        return counts
+
+    def gr_normalise(self, counts, r_max: float, n_frames: int) -> np.ndarray:
+        c = np.ascontiguousarray(np.asarray(counts, dtype=np.uint32))
+        g = np.zeros(len(c))
+        check(load().rb_gr_normalise(self._h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                     len(c), float(r_max), int(n_frames),
+                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return g
 
 
 class MLP:

@@ -33,8 +33,9 @@ namespace rb {
 // kernel listed those closer than rho_min.
 // C = 0: any template (bead_pair_warp); C = 5 or 8: a column-structured
 // template stored column by column (bead_pair_warp_cols), held to three CTAs
-// of 256 threads per SM (at most 85 registers).
-template <int NP, int C>
+// of 256 threads per SM (at most 85 registers).  POT = 0: Lennard-Jones beads;
+// POT = 1: the half-power half-cosine beads of Eq. 1 (either reading).
+template <int NP, int C, int POT>
 __global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
     k_bead_pairs(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
                  const float4* __restrict__ pos, const float4* __restrict__ quat,
@@ -80,9 +81,9 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
         const float3 s = mulT(Ri, R);
         float v[7];
         if constexpr (C == 0) {
-            bead_pair_warp<NP>(s, Rr, sT, sN, n_beads, pot, lane, v);
+            bead_pair_warp<NP, POT>(s, Rr, sT, sN, n_beads, pot, lane, v);
         } else {
-            bead_pair_warp_cols<NP, C>(s, Rr, sT, sN,
+            bead_pair_warp_cols<NP, C, POT>(s, Rr, sT, sN,
                                        reinterpret_cast<const float*>(sN + kMaxBeads / 5 + 1),
                                        cols, n_beads, pot, lane, v);
         }
@@ -111,6 +112,15 @@ BeadPot bead_pot(const rb_system* s) {
     p.eps4 = 4.f * s->eps;
     p.eps24 = 24.f * s->eps;
     p.u_shift = s->u_shift;
+    p.kind = s->pot_kind;
+    p.hA = s->hphc[0];
+    p.hb = s->hphc[1];
+    p.hc = s->hphc[2];
+    p.hp = s->hphc[3];
+    if (s->pot_kind != RB_POT_LJ) {  // the sum of u itself is the energy
+        p.eps4 = 1.f;
+        p.u_shift = 0.f;
+    }
     // |r^2_expanded - r^2| <= a few roundings of values up to (Rc + r_circ)^2
     // + r_circ^2 (b within Rc + r_circ of body i's centre, d within r_circ)
     const float big = (s->Rc + s->r_circ) * (s->Rc + s->r_circ) + s->r_circ * s->r_circ;
@@ -118,35 +128,41 @@ BeadPot bead_pot(const rb_system* s) {
     return p;
 }
 
-template <int NP, int C>
+template <int NP, int C, int POT>
 static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, const int* sel) {
     static int occ = 0;
     if (occ == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP, C>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP, C, POT>, 256, 0);
         if (occ <= 0) occ = 1;
     }
     const float3 L = make_float3(s->box[0], s->box[1], s->box[2]);
     const float3 invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
     const int grid = s->num_sms * occ;
-    RB_CUDA(launch_pdl(k_bead_pairs<NP, C>, grid, 256, 0, s->stream, s->pl.pairs, s->pl.n_pairs,
+    RB_CUDA(launch_pdl(k_bead_pairs<NP, C, POT>, grid, 256, 0, s->stream, s->pl.pairs, s->pl.n_pairs,
                        s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL, bead_pot(s),
                        cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, sel,
                        s->fallback_count));
     return RB_OK;
 }
 
-template <int NP>
+template <int NP, int POT>
 static rb_status launch_beads_np(rb_system* s, float cut2, int zero_beyond, const int* sel) {
-    if (s->cols.len == 5) return launch_beads<NP, 5>(s, cut2, zero_beyond, sel);
-    if (s->cols.len == 8) return launch_beads<NP, 8>(s, cut2, zero_beyond, sel);
-    return launch_beads<NP, 0>(s, cut2, zero_beyond, sel);
+    if (s->cols.len == 5) return launch_beads<NP, 5, POT>(s, cut2, zero_beyond, sel);
+    if (s->cols.len == 8) return launch_beads<NP, 8, POT>(s, cut2, zero_beyond, sel);
+    return launch_beads<NP, 0, POT>(s, cut2, zero_beyond, sel);
+}
+
+template <int POT>
+static rb_status launch_beads_pot(rb_system* s, float cut2, int zero_beyond, const int* sel) {
+    const int np = (s->n_beads + 63) / 64;
+    if (np <= 2) return launch_beads_np<2, POT>(s, cut2, zero_beyond, sel);
+    if (np <= 3) return launch_beads_np<3, POT>(s, cut2, zero_beyond, sel);
+    return launch_beads_np<4, POT>(s, cut2, zero_beyond, sel);
 }
 
 static rb_status launch_beads_any(rb_system* s, float cut2, int zero_beyond, const int* sel) {
-    const int np = (s->n_beads + 63) / 64;
-    if (np <= 2) return launch_beads_np<2>(s, cut2, zero_beyond, sel);
-    if (np <= 3) return launch_beads_np<3>(s, cut2, zero_beyond, sel);
-    return launch_beads_np<4>(s, cut2, zero_beyond, sel);
+    if (s->pot_kind == RB_POT_LJ) return launch_beads_pot<0>(s, cut2, zero_beyond, sel);
+    return launch_beads_pot<1>(s, cut2, zero_beyond, sel);
 }
 
 // The pairs the network kernel listed (closer than rho_min) by the bead sum.

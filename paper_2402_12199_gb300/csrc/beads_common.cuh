@@ -14,9 +14,15 @@ namespace rb {
 
 constexpr int kPadBeads = 3;  // far-away template entries after the last bead
 
+// Bead potential.  Lennard-Jones (kind 0): rc2, sig2, eps4, eps24, u_shift.
+// Half-power half-cosine of Eq. 1 (kind 1: the continuous reading, kind 2:
+// as printed): A, b, c, p; eps4 = 1 and u_shift = 0 so that the accumulated
+// sum is the energy itself.  rc2 is the squared cutoff in every kind.
 struct BeadPot {
     float rc2, sig2, eps4, eps24, u_shift;
     float rc2_test;  // rc2 + a bound on the rounding of the expanded distance test
+    int kind;
+    float hA, hb, hc, hp;
 };
 
 BeadPot bead_pot(const rb_system* s);
@@ -129,6 +135,65 @@ __device__ inline void lj_bead(const float2 md0, const float2 md1, const float2 
     }
 }
 
+// The half-power half-cosine (paper, Eq. 1) counterpart of lj_bead, per
+// slot: x = b - r; r <= b: u = x^p - 2A, -u'/r = p x^(p-1) / r; b < r < r_c:
+// u = -A (1 + cos t) (kind 1) or -A cos t (kind 2) with t = c (r - b),
+// -u'/r = -A c sin t / r; nothing from r_c on.  Both branches are evaluated
+// and one selected (no divergence inside the warp).
+template <int NP>
+__device__ inline void hphc_bead(const float2 md0, const float2 md1, const float2 md2,
+                                 const float2 (&Bx)[NP], const float2 (&By)[NP],
+                                 const float2 (&Bz)[NP], const BeadPot& pot, LJAcc<NP>& a) {
+    const float2 half2 = make_float2(0.5f, 0.5f);
+    const float u_base = pot.kind == 2 ? 0.f : -pot.hA;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const float2 rx = __ffma2_rn(half2, md0, Bx[q]);
+        const float2 ry = __ffma2_rn(half2, md1, By[q]);
+        const float2 rz = __ffma2_rn(half2, md2, Bz[q]);
+        float2 r2 = __fmul2_rn(rx, rx);
+        r2 = __ffma2_rn(ry, ry, r2);
+        r2 = __ffma2_rn(rz, rz, r2);
+        const float r2s[2] = {r2.x, r2.y};
+        float us[2], fs[2], ns[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool in = r2s[h] < pot.rc2;
+            const float ir = rsqrtf(r2s[h]);
+            const float r = r2s[h] * ir;
+            const float x = pot.hb - r;
+            const float xp = fmaxf(x, 0.f);
+            const float xp1 = __powf(xp, pot.hp - 1.f);  // 0 at x = 0 (p > 1)
+            float sn, cs;
+            __sincosf(pot.hc * (r - pot.hb), &sn, &cs);
+            const bool rep = x >= 0.f;
+            const float u = rep ? fmaf(xp1, xp, -2.f * pot.hA) : fmaf(-pot.hA, cs, u_base);
+            const float f = rep ? pot.hp * xp1 * ir : -pot.hA * pot.hc * sn * ir;
+            us[h] = in ? u : 0.f;
+            fs[h] = in ? f : 0.f;
+            ns[h] = in ? 1.f : 0.f;
+        }
+        a.acc = __fadd2_rn(a.acc, make_float2(us[0], us[1]));
+        a.cnt = __fadd2_rn(a.cnt, make_float2(ns[0], ns[1]));
+        const float2 fr = make_float2(fs[0], fs[1]);
+        a.Fx[q] = __ffma2_rn(fr, rx, a.Fx[q]);
+        a.Fy[q] = __ffma2_rn(fr, ry, a.Fy[q]);
+        a.Fz[q] = __ffma2_rn(fr, rz, a.Fz[q]);
+    }
+}
+
+// One template bead against every owned slot with the potential POT
+// (0: Lennard-Jones, 1: half-power half-cosine, either reading).
+template <int NP, int POT>
+__device__ inline void bead_terms(const float2 md0, const float2 md1, const float2 md2,
+                                  const float2 (&Bx)[NP], const float2 (&By)[NP],
+                                  const float2 (&Bz)[NP], const BeadPot& pot, LJAcc<NP>& a) {
+    if constexpr (POT == 0)
+        lj_bead<NP>(md0, md1, md2, Bx, By, Bz, pot, a);
+    else
+        hphc_bead<NP>(md0, md1, md2, Bx, By, Bz, pot, a);
+}
+
 // v[0..2] = F_j, v[3..5] = T = sum_l b_l x f_l, v[6] = E, reduced over the
 // warp with xor shuffles (every lane gets the sums).
 template <int NP>
@@ -166,7 +231,7 @@ __device__ inline void warp_finish(const float (&bx)[2 * NP], const float (&by)[
 // template beads decides whether any slot may be inside r_c, and then the
 // exact separations, the strict cutoff and the masked Lennard-Jones body run
 // for those U beads.  Result as in warp_finish.
-template <int NP, int U = 2>
+template <int NP, int POT = 0, int U = 2>
 __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const float4* sT,
                                       const float4* sN, int n_beads, const BeadPot& pot,
                                       int lane, float (&v)[7]) {
@@ -206,7 +271,8 @@ __device__ inline void bead_pair_warp(const float3 s, const Mat3& Rr, const floa
         for (int u = 0; u < U; ++u) hit |= mn[u] < th[u];
         if (__any_sync(0xffffffffu, hit)) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) lj_bead<NP>(md[u][0], md[u][1], md[u][2], Bx, By, Bz, pot, a);
+            for (int u = 0; u < U; ++u)
+                bead_terms<NP, POT>(md[u][0], md[u][1], md[u][2], Bx, By, Bz, pot, a);
         }
     }
     warp_finish<NP>(bx, by, bz, a, pot, v);
@@ -233,7 +299,7 @@ __device__ inline void load_columns(const float4* __restrict__ tmpl, const BeadC
 //   P = |b|^2 - 2 (b_x x + b_y y),   |b|^2 - 2 b.d = P - 2 b_z z_m,
 // i.e. (2 + C) packed FMAs per C distances of a slot pair instead of 3 C.
 // One warp vote per column; result as in warp_finish.
-template <int NP, int C>
+template <int NP, int C, int POT = 0>
 __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const float4* sT,
                                            const float4* sC, const float* sTh,
                                            const BeadCols& cols, int n_beads, const BeadPot& pot,
@@ -271,7 +337,7 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
 #pragma unroll 1
             for (int m = 0; m < C; ++m) {
                 const float z2 = sTh[8 * cols.n_cols + m];  // -2 z_m
-                lj_bead<NP>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
+                bead_terms<NP, POT>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
             }
         }
     }

@@ -274,9 +274,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                             yp[i + 1] = pack_bf16(__fmul2_rn(wb, d1));
                         }
                     }
-                    if (l < D) tmem_st16(tmem + lane_field + 256 + (l - 1) * 128 + c / 2, dp);
+                    if (l < D) tmem_st16_issue(tmem + lane_field + 256 + (l - 1) * 128 + c / 2, dp);
                     store_row32p(Ht, kM, row, c, yp);
                 }
+                if (l < D) tmem_wait_st();  // silu'(z_l) in place before the reverse pass
                 if (l == D) {
                     const float e_acc = e2.x + e2.y;
                     if (half == 1) epart[row] = e_acc;

@@ -228,10 +228,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             yp[i + 1] = pack_bf16(__fmul2_rn(wb, d1));
                         }
                     }
-                    if (l < D) tmem_st16(tmem + lane_field + kW + (l - 1) * 64 + cc / 2, dp);
+                    if (l < D) tmem_st16_issue(tmem + lane_field + kW + (l - 1) * 64 + cc / 2, dp);
                     store_row32p(Ht, kM, row, cc, yp);
                 }
             }
+            if (l < D) tmem_wait_st();  // silu'(z_l) in place before the reverse pass
             if (l == D) E = e_scale * (e2.x + e2.y + b_o) + e_shift;
         }
         // ---------------- reverse: g_{l-1} = (g_l W_l) * silu'(z_{l-1}), the

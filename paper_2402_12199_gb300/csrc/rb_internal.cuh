@@ -157,6 +157,17 @@ struct GraphCache {
     const void* mlp = nullptr;
     uint64_t mlp_version = 0;
     float dt = 0.f;
+    bool nvt = false;
+};
+
+// Nose-Hoover thermostat state on the device (FP64).  The step's first
+// thermostat half reads *_b and writes *_a; the second half reads *_a and
+// writes *_b, so no kernel reads what another block of it writes.  *_b is
+// the state between steps; K is the total kinetic energy after the half.
+struct NHDev {
+    double xi_a, eta_a, K_a, pad_a;
+    double xi_b, eta_b, K_b, pad_b;
+    double kT, Q, g;
 };
 
 }  // namespace rb
@@ -191,6 +202,8 @@ struct rb_system {
     rb::BeadCols cols;        // column structure of the template (len 0: none)
     // potential
     float eps = 1.f, sigma = 1.f, rcut = 2.5f, u_shift = 0.f;
+    int pot_kind = 0;                         // RB_POT_*
+    float hphc[4] = {0.f, 0.f, 0.f, 0.f};    // A, b, c, p (half-power half-cosine)
     float box[3] = {0, 0, 0};
     int64_t N = 0;
     // state
@@ -225,6 +238,19 @@ struct rb_system {
     int* rebuild_flag = nullptr;
     int64_t step = 0;  // MD steps taken (checkpointed)
     int shape = 0;
+    // Nose-Hoover NVT (off: nh == nullptr) and the per-block kinetic-energy
+    // partial sums (2K per reduction block) of the step's force reduction
+    rb::NHDev* nh = nullptr;
+    double* ke_part = nullptr;
+    int ke_blocks = 0;
+    float nvt_kT = 0.f, nvt_tau = 0.f;
+    // image counters: box lengths each centre has crossed since the state was
+    // set (unwrapped position = pos + image * box), and the reference frame of
+    // the displacement analyses (allocated on first use)
+    int4* image = nullptr;
+    float4 *ref_pos = nullptr, *ref_quat = nullptr;
+    int4* ref_image = nullptr;
+    double* ana_part = nullptr;
 };
 
 namespace rb {

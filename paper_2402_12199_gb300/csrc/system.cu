@@ -38,6 +38,32 @@ __device__ inline float wrap1(float x, float L, float invL) {
     return x;
 }
 
+// wrap1 that also counts the box lengths removed (for unwrapped positions).
+__device__ inline float wrap1_count(float x, float L, float invL, int& shift) {
+    const float k = floorf(x * invL);
+    x -= L * k;
+    shift = (int)k;
+    if (x >= L) {
+        x -= L;
+        ++shift;
+    }
+    if (x < 0.f) x = 0.f;
+    return x;
+}
+
+// One Nose-Hoover thermostat half T(h) (see k_integrate_first), FP64:
+// xi += h/2 G(K); s = exp(-xi h); K *= s^2; eta += xi h; xi += h/2 G(K),
+// G(K) = (2K - g kT) / Q.  Returns s.
+__device__ inline double nh_half(double& xi, double& eta, double& K, double h, const NHDev* nh) {
+    const double gkT = nh->g * nh->kT, Q = nh->Q;
+    xi += 0.5 * h * (2.0 * K - gkT) / Q;
+    const double sc = exp(-xi * h);
+    K *= sc * sc;
+    eta += xi * h;
+    xi += 0.5 * h * (2.0 * K - gkT) / Q;
+    return sc;
+}
+
 __global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, float3 invL,
                               float3 invw, int3 nc, int* __restrict__ count,
                               int* __restrict__ bodies, int cap, unsigned* status,
@@ -311,7 +337,8 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
                          const float4* __restrict__ pti, const float4* __restrict__ ptj,
                          float4* __restrict__ force, float4* __restrict__ torque, float kick,
                          float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
-                         const float4* __restrict__ quat, unsigned* status) {
+                         const float4* __restrict__ quat, unsigned* status, float mass,
+                         float3 invI, double* __restrict__ ke_part) {
     pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t >> 2, sub = t & 3;
@@ -347,28 +374,107 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
         v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
         v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2);
     }
-    if (!live || sub != 0) return;
-    F = make_float3(v[0], v[1], v[2]);
-    T = make_float3(v[3], v[4], v[5]);
-    e = v[6];
-    if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
-          isfinite(T.z) && isfinite(e)))
-        atomicOr(status, ST_NONFINITE);
-    force[i] = make_float4(F.x, F.y, F.z, e);
-    torque[i] = make_float4(T.x, T.y, T.z, 0.f);
-    if (kick != 0.f) {
-        float4 vv = vel[i];
-        vv.x += kick * F.x * inv_mass;
-        vv.y += kick * F.y * inv_mass;
-        vv.z += kick * F.z * inv_mass;
-        vel[i] = vv;
-        Mat3 R = qmat(quat[i]);
-        float3 tb = mulT(R, T);
-        float4 Lb = angmom[i];
-        Lb.x += kick * tb.x;
-        Lb.y += kick * tb.y;
-        Lb.z += kick * tb.z;
-        angmom[i] = Lb;
+    double ke2 = 0.0;  // 2 x kinetic energy of body i after the kick (thermostat)
+    if (live && sub == 0) {
+        F = make_float3(v[0], v[1], v[2]);
+        T = make_float3(v[3], v[4], v[5]);
+        e = v[6];
+        if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
+              isfinite(T.z) && isfinite(e)))
+            atomicOr(status, ST_NONFINITE);
+        force[i] = make_float4(F.x, F.y, F.z, e);
+        torque[i] = make_float4(T.x, T.y, T.z, 0.f);
+        if (kick != 0.f) {
+            float4 vv = vel[i];
+            vv.x += kick * F.x * inv_mass;
+            vv.y += kick * F.y * inv_mass;
+            vv.z += kick * F.z * inv_mass;
+            vel[i] = vv;
+            Mat3 R = qmat(quat[i]);
+            float3 tb = mulT(R, T);
+            float4 Lb = angmom[i];
+            Lb.x += kick * tb.x;
+            Lb.y += kick * tb.y;
+            Lb.z += kick * tb.z;
+            angmom[i] = Lb;
+            if (ke_part)
+                ke2 = (double)mass * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z) +
+                      (double)Lb.x * Lb.x * invI.x + (double)Lb.y * Lb.y * invI.y +
+                      (double)Lb.z * Lb.z * invI.z;
+        }
+    }
+    if (ke_part) {  // fixed-order block sum (deterministic)
+        __shared__ double s_ke[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ke2 += __shfl_xor_sync(0xffffffffu, ke2, o);
+        if ((threadIdx.x & 31) == 0) s_ke[threadIdx.x >> 5] = ke2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_ke[w];
+            ke_part[blockIdx.x] = a;
+        }
+    }
+}
+
+// Second thermostat half of an NVT step, after the force reduction: every
+// block sums the reduction's kinetic-energy partials in the same fixed order
+// (so all blocks agree bit for bit), applies T(dt/2) to the state left by
+// the first half (*_a) and scales its bodies' v and L_b; block 0 stores the
+// thermostat state between steps (*_b).
+__global__ void k_thermo_end(int N, float dt, const double* __restrict__ ke_part, int n_part,
+                             NHDev* nh, float4* __restrict__ vel, float4* __restrict__ angmom) {
+    pdl_wait();
+    __shared__ float s_scale;
+    if (threadIdx.x < 32) {
+        double a = 0.0;
+        for (int k = threadIdx.x; k < n_part; k += 32) a += ke_part[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) {
+            double xi = nh->xi_a, eta = nh->eta_a, K = 0.5 * a;
+            s_scale = (float)nh_half(xi, eta, K, 0.5 * (double)dt, nh);
+            if (blockIdx.x == 0) {
+                nh->xi_b = xi;
+                nh->eta_b = eta;
+                nh->K_b = K;
+            }
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float sc = s_scale;
+    float4 v = vel[i], L = angmom[i];
+    v.x *= sc; v.y *= sc; v.z *= sc;
+    L.x *= sc; L.y *= sc; L.z *= sc;
+    vel[i] = v;
+    angmom[i] = L;
+}
+
+// Thermostat start: K of the current state (one block, fixed order), xi and
+// eta kept or reset.
+__global__ void k_thermo_init(int N, float mass, float3 invI, const float4* __restrict__ vel,
+                              const float4* __restrict__ angmom, NHDev* nh, int reset) {
+    __shared__ double s_k[32];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float4 v = vel[i], L = angmom[i];
+        a += (double)mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z) +
+             (double)L.x * L.x * invI.x + (double)L.y * L.y * invI.y + (double)L.z * L.z * invI.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) s_k[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_k[w];
+        nh->K_b = 0.5 * t;
+        if (reset) {
+            nh->xi_b = 0.0;
+            nh->eta_b = 0.0;
+        }
     }
 }
 
@@ -381,25 +487,54 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
                                   const float4* __restrict__ force,
                                   const float4* __restrict__ torque,
                                   const float4* __restrict__ pos_ref, float half_skin2,
-                                  int* rebuild) {
+                                  int* rebuild, NHDev* nh, int4* __restrict__ image) {
     pdl_wait();
+    // NVT: first thermostat half T(dt/2) from the state between steps; one
+    // thread per block computes it (FP64, identical in every block), block 0
+    // stores it for the second half
+    __shared__ float s_scale;
+    if (nh) {
+        if (threadIdx.x == 0) {
+            double xi = nh->xi_b, eta = nh->eta_b, K = nh->K_b;
+            s_scale = (float)nh_half(xi, eta, K, 0.5 * (double)dt, nh);
+            if (blockIdx.x == 0) {
+                nh->xi_a = xi;
+                nh->eta_a = eta;
+                nh->K_a = K;
+            }
+        }
+        __syncthreads();
+    }
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float h = 0.5f * dt;
     float4 f = force[i], t = torque[i];
     float4 v = vel[i];
+    float4 Lw = angmom[i];
+    if (nh) {
+        const float sc = s_scale;
+        v.x *= sc; v.y *= sc; v.z *= sc;
+        Lw.x *= sc; Lw.y *= sc; Lw.z *= sc;
+    }
     v.x += h * f.x * inv_mass;
     v.y += h * f.y * inv_mass;
     v.z += h * f.z * inv_mass;
     float4 q = quat[i];
     Mat3 R = qmat(q);
     float3 tb = mulT(R, make_float3(t.x, t.y, t.z));
-    float4 Lw = angmom[i];
     float Lb[3] = {Lw.x + h * tb.x, Lw.y + h * tb.y, Lw.z + h * tb.z};
     float4 p = pos[i];
-    p.x = wrap1(p.x + dt * v.x, L.x, invL.x);
-    p.y = wrap1(p.y + dt * v.y, L.y, invL.y);
-    p.z = wrap1(p.z + dt * v.z, L.z, invL.z);
+    int kx, ky, kz;
+    p.x = wrap1_count(p.x + dt * v.x, L.x, invL.x, kx);
+    p.y = wrap1_count(p.y + dt * v.y, L.y, invL.y, ky);
+    p.z = wrap1_count(p.z + dt * v.z, L.z, invL.z, kz);
+    if ((kx | ky | kz) != 0) {  // crossed a face: count it (rare, so no traffic otherwise)
+        int4 im = image[i];
+        im.x += kx;
+        im.y += ky;
+        im.z += kz;
+        image[i] = im;
+    }
     const float invIk[3] = {invI.x, invI.y, invI.z};
     const int axes[5] = {2, 1, 0, 1, 2};
     const float frac[5] = {0.5f, 0.5f, 1.f, 0.5f, 0.5f};
@@ -550,11 +685,17 @@ rb_status build_pairs_async(rb_system* s, bool force, bool checked) {
 
 rb_status reduce_forces_async(rb_system* s, float kick) {
     const int N = (int)s->N;
+    const bool nvt = s->nh && kick != 0.f;  // kinetic-energy partials for the thermostat
     RB_CUDA(launch_pdl(k_reduce, blocks_for((int64_t)N * 4, 256), 256, 0, s->stream, N,
                        s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count,
                        s->pl.lower_count, s->pl.lower_nbr, s->pair_F, s->pair_ti, s->pair_tj,
                        s->force, s->torque, kick, 1.f / s->mass, s->vel, s->angmom, s->quat,
-                       s->status_dev));
+                       s->status_dev, s->mass,
+                       make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
+                       nvt ? s->ke_part : (double*)nullptr));
+    if (nvt)
+        RB_CUDA(launch_pdl(k_thermo_end, blocks_for(N, 256), 256, 0, s->stream, N, 2.f * kick,
+                           (const double*)s->ke_part, s->ke_blocks, s->nh, s->vel, s->angmom));
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -645,16 +786,21 @@ using namespace rb;
 extern "C" {
 
 const char* rb_last_error(void) { return rb::g_err.c_str(); }
-int32_t rb_abi_version(void) { return 1; }
+int32_t rb_abi_version(void) { return 2; }
 
 rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** out) {
     if (!d || !out) return fail(RB_EINVAL, "null argument");
     *out = nullptr;
     if (d->n_bodies < 1 || d->n_bodies > (int64_t)1 << 26)
         return fail(RB_EINVAL, "n_bodies out of range [1, 2^26]");
-    if (d->pot.kind != RB_POT_LJ) return fail(RB_ENOTSUP, "only the LJ bead potential is built");
-    if (!(d->pot.eps > 0 && d->pot.sigma > 0 && d->pot.rcut > 0))
+    const int kind = d->pot.kind;
+    if (kind != RB_POT_LJ && kind != RB_POT_HPHC && kind != RB_POT_HPHC_PRINTED)
+        return fail(RB_EINVAL, "unknown bead potential");
+    if (kind == RB_POT_LJ && !(d->pot.eps > 0 && d->pot.sigma > 0 && d->pot.rcut > 0))
         return fail(RB_EINVAL, "potential parameters must be positive");
+    if (kind != RB_POT_LJ && !(d->pot.A >= 0 && d->pot.b > 0 && d->pot.c > 0 && d->pot.p > 1 &&
+                               d->pot.sigma > 0))
+        return fail(RB_EINVAL, "half-power half-cosine needs A >= 0, b > 0, c > 0, p > 1, sigma > 0");
     std::string err;
     std::vector<float> t = make_template(d->body, err);
     if (t.empty()) return fail(RB_EINVAL, err);
@@ -686,13 +832,23 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     s->inertia[1] = (float)I[4];
     s->inertia[2] = (float)I[8];
     s->r_circ = (float)rmax;
-    s->eps = d->pot.eps;
+    s->pot_kind = kind;
     s->sigma = d->pot.sigma;
-    s->rcut = d->pot.rcut;
-    {
+    if (kind == RB_POT_LJ) {
+        s->eps = d->pot.eps;
+        s->rcut = d->pot.rcut;
         double sr2 = (double)s->sigma * s->sigma / ((double)s->rcut * s->rcut);
         double sr6 = sr2 * sr2 * sr2;
         s->u_shift = (float)(4.0 * s->eps * (sr6 * sr6 - sr6));
+    } else {  // cutoff where the cosine branch ends: b + pi/c (b + pi/(2c) as printed)
+        const double kPi = 3.14159265358979323846;
+        s->eps = 1.f;
+        s->u_shift = 0.f;
+        s->hphc[0] = d->pot.A;
+        s->hphc[1] = d->pot.b;
+        s->hphc[2] = d->pot.c;
+        s->hphc[3] = d->pot.p;
+        s->rcut = (float)((double)d->pot.b + (kind == RB_POT_HPHC ? kPi : 0.5 * kPi) / d->pot.c);
     }
     s->Rc = (float)(2.0 * rmax + s->rcut);
     s->skin = 0.f;
@@ -747,6 +903,9 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     ALLOC(s->fb_list, sizeof(int) * cp);
     ALLOC(s->pos_ref, sizeof(float4) * N);
     ALLOC(s->rebuild_flag, sizeof(int));
+    s->ke_blocks = blocks_for((int64_t)N * 4, 256);
+    ALLOC(s->ke_part, sizeof(double) * s->ke_blocks);
+    ALLOC(s->image, sizeof(int4) * N);
 #undef ALLOC
     if (e != cudaSuccess) {
         rb_status st = cuda_fail(e, "cudaMalloc (system)");
@@ -770,6 +929,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     if (e == cudaSuccess) e = cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->angmom, 0, sizeof(float4) * N, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->vel, 0, sizeof(float4) * N, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->image, 0, sizeof(int4) * N, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         rb_status st = cuda_fail(e, "system initialisation");
@@ -796,7 +956,11 @@ int64_t rb_system_footprint(const rb_system_desc* d) {
     for (size_t k = 0; k < t.size() / 3; ++k)
         rmax = std::max(rmax, std::sqrt((double)t[3 * k] * t[3 * k] + (double)t[3 * k + 1] * t[3 * k + 1] +
                                         (double)t[3 * k + 2] * t[3 * k + 2]));
-    const double Rc = 2.0 * rmax + d->pot.rcut;
+    const double kPi = 3.14159265358979323846;
+    const double rcut = d->pot.kind == RB_POT_HPHC         ? d->pot.b + kPi / d->pot.c
+                        : d->pot.kind == RB_POT_HPHC_PRINTED ? d->pot.b + 0.5 * kPi / d->pot.c
+                                                             : d->pot.rcut;
+    const double Rc = 2.0 * rmax + rcut;
     int64_t n_cells = 1;
     for (int a = 0; a < 3; ++a) n_cells *= std::max<int64_t>(1, (int64_t)std::floor(d->box[a] / Rc));
     const int64_t N = d->n_bodies;
@@ -824,7 +988,8 @@ rb_status rb_destroy_system(rb_system* s) {
                     s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
                     s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
                     s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev,
-                    s->fallback_count, s->fb_list, s->pos_ref, s->rebuild_flag};
+                    s->fallback_count, s->fb_list, s->pos_ref, s->rebuild_flag, s->nh,
+                    s->ke_part, s->image, s->ref_pos, s->ref_quat, s->ref_image, s->ana_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -858,8 +1023,71 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
     if (quat) RB_CUDA(cudaMemcpyAsync(s->quat, quat, b, k, s->stream));
     if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
     if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
-    if (pos) k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+    if (pos) {
+        k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+        RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
+    }
+    if (s->nh && (vel || angmom))
+        k_thermo_init<<<1, 1024, 0, s->stream>>>(
+            (int)s->N, s->mass,
+            make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]), s->vel,
+            s->angmom, s->nh, 0);
     s->forces_valid = false;
+    return RB_OK;
+}
+
+rb_status rb_set_thermostat(rb_system* s, float kT, float tau) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    auto drop_graph = [&] {  // the captured step graph holds the thermostat pointer
+        if (s->graph.exec) {
+            cudaGraphExecDestroy(s->graph.exec);
+            s->graph.exec = nullptr;
+        }
+    };
+    if (!(tau > 0.f)) {  // off
+        if (s->nh) {
+            RB_CUDA(cudaStreamSynchronize(s->stream));
+            drop_graph();
+            cudaFree(s->nh);
+            s->nh = nullptr;
+        }
+        s->nvt_kT = s->nvt_tau = 0.f;
+        return RB_OK;
+    }
+    if (!(kT > 0.f)) return fail(RB_EINVAL, "kT must be positive");
+    if (!s->nh) {
+        RB_CUDA(cudaStreamSynchronize(s->stream));
+        drop_graph();
+        RB_CUDA(cudaMalloc((void**)&s->nh, sizeof(NHDev)));
+    }
+    NHDev h{};
+    h.kT = kT;
+    h.g = 6.0 * (double)s->N - 3.0;
+    h.Q = h.g * (double)kT * (double)tau * (double)tau;
+    RB_CUDA(cudaMemcpyAsync(s->nh, &h, sizeof(NHDev), cudaMemcpyHostToDevice, s->stream));
+    k_thermo_init<<<1, 1024, 0, s->stream>>>(
+        (int)s->N, s->mass, make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
+        s->vel, s->angmom, s->nh, 1);
+    RB_CUDA(cudaGetLastError());
+    RB_CUDA(cudaStreamSynchronize(s->stream));  // h lives on this stack frame
+    s->nvt_kT = kT;
+    s->nvt_tau = tau;
+    return RB_OK;
+}
+
+rb_status rb_get_thermostat(const rb_system* s, double* out4) {
+    if (!s || !out4) return fail(RB_EINVAL, "null argument");
+    if (!s->nh) {
+        for (int k = 0; k < 4; ++k) out4[k] = 0.0;
+        return RB_OK;
+    }
+    NHDev h;
+    RB_CUDA(cudaMemcpyAsync(&h, s->nh, sizeof(NHDev), cudaMemcpyDeviceToHost, s->stream));
+    RB_CUDA(cudaStreamSynchronize(s->stream));
+    out4[0] = h.xi_b;
+    out4[1] = h.eta_b;
+    out4[2] = h.Q;
+    out4[3] = h.g * h.kT;
     return RB_OK;
 }
 
@@ -1003,7 +1231,7 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
     if (n_steps == 0) return RB_OK;
     GraphCache& g = s->graph;
     if (!g.exec || g.path != path || g.precision != precision || g.mlp != m || g.dt != dt ||
-        (m && g.mlp_version != m->version)) {
+        (m && g.mlp_version != m->version) || g.nvt != (s->nh != nullptr)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1023,7 +1251,8 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
             k_integrate_first, blocks_for(N, 256), 256, 0, s->stream, N, dt, 1.f / s->mass,
             make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
             f3(s->box), inv3(s->box), s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
-            s->pos_ref, s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f, s->rebuild_flag);
+            s->pos_ref, s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f, s->rebuild_flag, s->nh,
+            s->image);
         rb_status st = le == cudaSuccess ? eval_forces_async(s, path, m, precision, 0.5f * dt, true)
                                          : cuda_fail(le, "k_integrate_first");
         cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
@@ -1041,6 +1270,7 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
         g.mlp = m;
         g.mlp_version = m ? m->version : 0;
         g.dt = dt;
+        g.nvt = s->nh != nullptr;
     }
     for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
     s->step += n_steps;
@@ -1120,16 +1350,30 @@ rb_status rb_checkpoint(rb_system* s, const char* path) {
     const size_t n4 = 4 * (size_t)s->N;
     std::vector<float> buf(4 * n4);
     RB_TRY(rb_get_state(s, buf.data(), buf.data() + n4, buf.data() + 2 * n4, buf.data() + 3 * n4, 1));
+    // version 2 adds the image counters and the thermostat
+    std::vector<int32_t> img(n4);
+    RB_TRY(rb_get_images(s, img.data()));
+    NHDev h{};
+    const int32_t nvt = s->nh ? 1 : 0;
+    if (nvt) {
+        RB_CUDA(cudaMemcpyAsync(&h, s->nh, sizeof(NHDev), cudaMemcpyDeviceToHost, s->stream));
+        RB_CUDA(cudaStreamSynchronize(s->stream));
+    }
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(RB_EINVAL, std::string("cannot open ") + path + " for writing");
-    const int32_t version = 1, shape = s->shape, nb = s->n_beads;
+    const int32_t version = 2, shape = s->shape, nb = s->n_beads;
     const int64_t N = s->N, step = s->step;
+    const double th[3] = {h.xi_b, h.eta_b, h.K_b};
+    const float thp[2] = {s->nvt_kT, s->nvt_tau};
     bool ok = std::fwrite(kMagic, 1, 4, f) == 4 && std::fwrite(&version, 4, 1, f) == 1 &&
               std::fwrite(&N, 8, 1, f) == 1 && std::fwrite(&step, 8, 1, f) == 1 &&
               std::fwrite(&shape, 4, 1, f) == 1 && std::fwrite(&nb, 4, 1, f) == 1 &&
               std::fwrite(s->box, 4, 3, f) == 3 && std::fwrite(&s->skin, 4, 1, f) == 1 &&
               std::fwrite(s->tmpl.data(), 4, s->tmpl.size(), f) == s->tmpl.size() &&
-              std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+              std::fwrite(buf.data(), 4, buf.size(), f) == buf.size() &&
+              std::fwrite(img.data(), 4, img.size(), f) == img.size() &&
+              std::fwrite(&nvt, 4, 1, f) == 1 && std::fwrite(thp, 4, 2, f) == 2 &&
+              std::fwrite(th, 8, 3, f) == 3;
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) return fail(RB_EINVAL, std::string("write failed: ") + path);
     return RB_OK;
@@ -1144,7 +1388,7 @@ rb_status rb_restore(rb_system* s, const char* path) {
     int64_t N = 0, step = 0;
     float box[3], skin = 0.f;
     bool ok = std::fread(magic, 1, 4, f) == 4 && std::memcmp(magic, kMagic, 4) == 0 &&
-              std::fread(&version, 4, 1, f) == 1 && version == 1 &&
+              std::fread(&version, 4, 1, f) == 1 && (version == 1 || version == 2) &&
               std::fread(&N, 8, 1, f) == 1 && std::fread(&step, 8, 1, f) == 1 &&
               std::fread(&shape, 4, 1, f) == 1 && std::fread(&nb, 4, 1, f) == 1 &&
               std::fread(box, 4, 3, f) == 3 && std::fread(&skin, 4, 1, f) == 1;
@@ -1156,12 +1400,29 @@ rb_status rb_restore(rb_system* s, const char* path) {
     std::vector<float> t(3 * (size_t)nb);
     const size_t n4 = 4 * (size_t)N;
     std::vector<float> buf(4 * n4);
+    std::vector<int32_t> img(n4, 0);
+    int32_t nvt = 0;
+    float thp[2] = {0.f, 0.f};
+    double th[3] = {0.0, 0.0, 0.0};
     ok = std::fread(t.data(), 4, t.size(), f) == t.size() &&
          std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+    if (ok && version >= 2)
+        ok = std::fread(img.data(), 4, img.size(), f) == img.size() &&
+             std::fread(&nvt, 4, 1, f) == 1 && std::fread(thp, 4, 2, f) == 2 &&
+             std::fread(th, 8, 3, f) == 3;
     std::fclose(f);
     if (!ok || t != s->tmpl) return fail(RB_EINVAL, "truncated checkpoint or different template");
     RB_TRY(rb_set_state(s, buf.data(), buf.data() + n4, buf.data() + 2 * n4, buf.data() + 3 * n4, 1));
+    RB_CUDA(cudaMemcpyAsync(s->image, img.data(), sizeof(int4) * s->N, cudaMemcpyHostToDevice,
+                            s->stream));
     RB_TRY(rb_set_skin(s, skin));
+    // the thermostat exactly as saved (its stored K included, so the run
+    // continues bit for bit)
+    RB_TRY(rb_set_thermostat(s, thp[0], nvt ? thp[1] : 0.f));
+    if (nvt) {
+        RB_CUDA(cudaMemcpyAsync(&s->nh->xi_b, th, sizeof(th), cudaMemcpyHostToDevice, s->stream));
+    }
+    RB_CUDA(cudaStreamSynchronize(s->stream));
     s->step = step;
     return RB_OK;
 }

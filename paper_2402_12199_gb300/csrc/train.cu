@@ -53,7 +53,7 @@ struct rb_trainer {
 namespace rb {
 
 // ------------------------------------------------------------- sampler
-template <int NP>
+template <int NP, int POT>
 __global__ void __launch_bounds__(256)
     k_sample_pairs(int64_t n, const float* __restrict__ u, const float4* __restrict__ tmpl,
                    int n_beads, float Rc, float sigma, BeadPot pot, int n_bisect,
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256)
         const float rho = rc + ub[5] * (Rc - rc);
         const float3 s = make_float3(rho * dir.x, rho * dir.y, rho * dir.z);
         float v[7];
-        bead_pair_warp<NP>(s, Rr, sT, sN, n_beads, pot, lane, v);
+        bead_pair_warp<NP, POT>(s, Rr, sT, sN, n_beads, pot, lane, v);
         if (lane == 0) {
             cfg[2 * b] = make_float4(s.x, s.y, s.z, 0.f);
             cfg[2 * b + 1] = q;
@@ -530,17 +530,18 @@ rb_status rb_sample_pairs_at(const rb_system* s, int64_t n, const float* uniform
     const int np = (s->n_beads + 63) / 64;
     BeadPot pot = bead_pot(s);
     const int grid = s->num_sms * 4;
-#define RB_SAMPLE(NP)                                                                           \
-    k_sample_pairs<NP><<<grid, 256, 0, s->stream>>>(n, uniforms, s->tmpl_dev, s->n_beads, s->Rc, \
-                                                    contact, pot, 40,                           \
-                                                    reinterpret_cast<float4*>(cfg),             \
-                                                    reinterpret_cast<float4*>(labels), rho_contact)
-    if (np <= 2)
-        RB_SAMPLE(2);
-    else if (np <= 3)
-        RB_SAMPLE(3);
-    else
-        RB_SAMPLE(4);
+#define RB_SAMPLE(NP, POT)                                                                   \
+    k_sample_pairs<NP, POT><<<grid, 256, 0, s->stream>>>(                                    \
+        n, uniforms, s->tmpl_dev, s->n_beads, s->Rc, contact, pot, 40,                       \
+        reinterpret_cast<float4*>(cfg), reinterpret_cast<float4*>(labels), rho_contact)
+    const bool lj = s->pot_kind == RB_POT_LJ;
+    if (np <= 2) {
+        if (lj) RB_SAMPLE(2, 0); else RB_SAMPLE(2, 1);
+    } else if (np <= 3) {
+        if (lj) RB_SAMPLE(3, 0); else RB_SAMPLE(3, 1);
+    } else {
+        if (lj) RB_SAMPLE(4, 0); else RB_SAMPLE(4, 1);
+    }
 #undef RB_SAMPLE
     RB_CUDA(cudaGetLastError());
     return RB_OK;
