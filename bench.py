@@ -38,6 +38,15 @@ UNIT = "pair evals/s"
 N_BODIES, PHI, SEED, KT, DT = 32768, 0.20, 3, 1.0, 0.002
 WIDTH, DEPTH = 128, 3
 
+# DRAM bytes (read + write) per launch of each pair kernel at this workload,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, one launch each, the
+# same kernel code) on
+#   python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-serving
+#                   --train-steps 0 --drift-steps 0 [--no-paper-workload]
+# None would mark a kernel changed since its capture.
+NCU_DRAM_BYTES = {"k_bead_pairs": 1.855e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 3.588e6,
+                  "k_nn_tc256": 2.458e6}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -487,7 +496,8 @@ def main():
         achieved = flops / (d_ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
         roof = {"kernel": "k_bead_pairs", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NCU_DRAM_BYTES["k_bead_pairs"], "traffic_unit": "bytes per launch (ncu)",
                 "kernel_ms": d_ms, "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
                 "flops_per_launch": flops}
 
@@ -515,6 +525,7 @@ def main():
         peak = pk.get("bf16_tflops_sustained", 1700.0)
         roof_nn = {"kernel": "k_nn_tc2p", "bound": "tensor", "achieved": achieved, "peak": peak,
                    "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+                   "traffic": NCU_DRAM_BYTES["k_nn_tc2p"], "traffic_unit": "bytes per launch (ncu)",
                    "peak_source": f"bf16_tflops_sustained ({how})", "flops_per_launch": flops,
                    "mufu_per_pair": 6 * WIDTH, "note": "one tanh.approx per SiLU evaluation"}
 
@@ -539,6 +550,7 @@ def main():
         peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
         roof_f32 = {"kernel": "k_nn_f32", "bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+                    "traffic": NCU_DRAM_BYTES["k_nn_f32"], "traffic_unit": "bytes per launch (ncu)",
                     "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
                     "flops_per_launch": flops}
 
@@ -594,6 +606,7 @@ def main():
                     "speedup_vs_beads": (statistics.mean(per_path_ms["beads"]) / ms256)
                     if "beads" in per_path_ms else None,
                     "kernel": "k_nn_tc256", "kernel_ms": k256,
+                    "traffic": NCU_DRAM_BYTES["k_nn_tc256"], "traffic_unit": "bytes per launch (ncu)",
                     "tensor_tflops": tc256 / (k256 * 1e-3) / 1e12,
                     "frac_of_bf16_sustained": tc256 / (k256 * 1e-3) / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
                     "steps_timed": 200}
