@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--cyl-train-steps", type=int, default=300)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-paper-workload", action="store_true")
+    ap.add_argument("--fnet-train-steps", type=int, default=4000)
+    ap.add_argument("--paper-nn-train-steps", type=int, default=10000)
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--serving-steps", type=int, default=1000)
     ap.add_argument("--serving-nmax", type=int, default=65536)
@@ -681,6 +683,99 @@ def main():
             "msd_after_300_steps": msd_p, "msr_after_300_steps": msr_p,
             "g_r_first_peak": {"r": float((np.argmax(g_p) + 0.5) * r_max_p / 200), "g": float(g_p.max())}}
         del sp
+        # the network on the same workload: trained on half-power half-cosine
+        # labels, BF16, same thermostat; model error against the bead sum
+        if any(p.startswith("nn") for p in paths) and args.paper_nn_train_steps > 0:
+            from paper_2402_12199_gb300 import train_net
+
+            mlp_p, rep_p = train_net.train_network(
+                "cube", WIDTH, DEPTH, n_samples=args.train_samples, steps=args.paper_nn_train_steps,
+                batch=4096, lr=args.train_lr, lam_E=args.train_lam_e, f_scale=0.05, seed=9,
+                contact=0.7, cutoff_width=args.train_cutoff_width, potential="hphc",
+                hphc=inputs_mod.HPHC_PAPER, time_limit_s=40.0)
+            sn = api.System(N_BODIES, [Lp] * 3, "cube", skin=args.skin, potential="hphc",
+                            hphc=inputs_mod.HPHC_PAPER)
+            sn.set_state(*(torch.from_numpy(stp[k]).cuda() for k in ("pos", "quat", "vel", "angmom")))
+            sn.set_nn_fallback(rep_p["rho_contact_min"])
+            err_p = train_net.force_error(sn, mlp_p, "bf16")
+            sn.set_thermostat(KT_P, 0.5)
+            sn.forces_nn(mlp_p, "bf16")
+            sn.step(200, DT_P, path=api.RB_PATH_NN, mlp=mlp_p, precision="bf16")
+            ev_n = []
+            for _ in range(300):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sn.step(1, DT_P, path=api.RB_PATH_NN, mlp=mlp_p, precision="bf16")
+                b.record(stream)
+                ev_n.append((a, b))
+            torch.cuda.synchronize()
+            sn.sync()
+            ms_n = statistics.mean(a.elapsed_time(b) for a, b in ev_n)
+            _, kt_n, kr_n = sn.energy()
+            paper_wl["nn_bf16"] = {
+                "ms_per_md_step": ms_n, "md_steps_per_s": 1e3 / ms_n,
+                "speedup_vs_beads": ms_p / ms_n,
+                "temperature_2K_over_g": 2 * (kt_n + kr_n) / (6 * N_BODIES - 3),
+                "model_error": dict(err_p, vs="bead path (half-power half-cosine), same state"),
+                "training": {k: rep_p.get(k) for k in ("samples", "steps", "heldout_e_F", "t_train_s")},
+                "net": f"10-{WIDTH}x{DEPTH}-1 SiLU, cube point group, trained on half-power "
+                       f"half-cosine labels (contact 0.7 sigma, force scale 0.05)"}
+            del sn, mlp_p
+
+    # ---- per-component networks for cylinders (the paper's cylinder method):
+    # 32768 cylinders at phi = 0.15, five networks (width 32, depth 3) trained
+    # on the device on 1M bead-labelled pairs (capped, force-scale weighted
+    # targets), then one MD
+    # step per path timed on the same state, and the model error
+    fnet_leg = None
+    if "beads" in paths and args.fnet_train_steps > 0 and world == 1:
+        from paper_2402_12199_gb300 import train_net
+
+        Nc, PHI_C, CAP, WF, DF = 32768, 0.15, 5.0, 32, 3
+        fn, rep_fn = train_net.train_fnet("cylinder", WF, DF, n_samples=1_000_000,
+                                          steps=args.fnet_train_steps, batch=4096, lr=2e-3,
+                                          cap=CAP, seed=8, f_scale=1.0)
+        probe = api.System(8, [80.0] * 3, "cylinder")
+        stc, Lc = inputs_mod.system_state(Nc, PHI_C, KT, SEED + 11, probe.mass, probe.inertia,
+                                          "cylinder")
+        del probe
+        sysc = {}
+        for pth in ("beads", "fnet"):
+            sc = api.System(Nc, [Lc] * 3, "cylinder", skin=args.skin)
+            sc.set_state(*(torch.from_numpy(stc[k]).cuda() for k in ("pos", "quat", "vel", "angmom")))
+            sysc[pth] = sc
+        err_fn = train_net.fnet_force_error(sysc["fnet"], fn)
+        n_pairs_c = sysc["beads"].build_pairs()
+        tc = {}
+        for pth, sc in sysc.items():
+            run = (lambda k, sc=sc: sc.step(k, DT)) if pth == "beads" else (lambda k, sc=sc: sc.step_fnet(fn, k, DT))
+            run(20)
+            evs = []
+            for _ in range(100):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                run(1)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            sc.sync()
+            tc[pth] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        # the network pair kernel alone: whole-system forces minus nothing else
+        # is not separable, so time rb_forces_fnet and rb_forces_beads (list
+        # current, reduction included)
+        fl = 2.0 * 5 * (4 * WF + (DF - 1) * WF * WF + WF) * n_pairs_c
+        fnet_leg = {"workload": f"{Nc} cylinders (8 x 19 beads), phi={PHI_C}, NVE dt={DT}, skin "
+                                f"{args.skin}; five per-component networks 4-{WF}x{DF}-1 SiLU",
+                    "pairs": n_pairs_c,
+                    "ms_per_md_step": {"beads": tc["beads"], "fnet": tc["fnet"]},
+                    "speedup_vs_beads": tc["beads"] / tc["fnet"],
+                    "fnet_pair_evals_per_s": n_pairs_c / (tc["fnet"] * 1e-3),
+                    "fnet_flop_per_pair": fl / max(1, n_pairs_c),
+                    "model_error": dict(err_fn, vs="bead path, same state (model error, not parity)"),
+                    "training": rep_fn}
+        del sysc, fn
 
     # ---- NVE energy conservation: a fresh copy of the workload per path, run
     # for --drift-steps steps with the FP64 total energy read every
@@ -804,7 +899,7 @@ def main():
             "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_fp32": roof_f32, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
             "nn_bf16_width256": width256, "nve_drift": drift, "training_cylinders_w256": train_cyl,
-            "paper_workload_hphc_nvt": paper_wl,
+            "paper_workload_hphc_nvt": paper_wl, "cylinders_per_component_networks": fnet_leg,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "results_finite": e2e_ok,

@@ -57,7 +57,7 @@ typedef enum rb_status {
 
 enum { RB_SHAPE_CUBE = 0, RB_SHAPE_CYLINDER = 1, RB_SHAPE_CUSTOM = 2 };
 enum { RB_POT_LJ = 0, RB_POT_HPHC = 1, RB_POT_HPHC_PRINTED = 2 };
-enum { RB_PATH_BEADS = 0, RB_PATH_NN = 1 };
+enum { RB_PATH_BEADS = 0, RB_PATH_NN = 1, RB_PATH_FNET = 2 };
 enum { RB_FP32 = 0, RB_BF16 = 1 };
 
 /* Thread-local message describing the most recent failure on this thread. */
@@ -497,6 +497,75 @@ rb_status rb_mlp_sync(const rb_mlp* mlp);
  * K in {64, 128}.  Synchronises the stream. */
 rb_status rb_tc_gemm_check(int32_t N, int32_t K, const float* A, const float* B, float* D,
                            void* cuda_stream);
+
+/* ------------------------------------------------ per-component networks
+ * The paper's cylinder method (Methods; SI Sec. 2): five separate networks
+ * predict the force components f_1, f_2, f_3 and the torque components
+ * tau_1, tau_2 directly (tau_3, about the cylinder's axis, is not needed),
+ * from four numbers describing the pair.  Pair (i = cylinder 1,
+ * j = cylinder 2), in body i's frame (s = R(q_i)^T R_ij, q_rel = q_i^* q_j;
+ * a cylinder's axis is its body z axis):
+ *   z_hat = sign(s_z) e_z (+e_z for s_z = 0), p_z = |s_z|;
+ *   x_hat = (s_x, s_y, 0)/p_r with p_r = |(s_x, s_y)| (e_x when p_r = 0);
+ *   y_hat = z_hat x x_hat;
+ *   u = R(q_rel) e_z (cylinder 2's axis) in (x_hat, y_hat, z_hat), turned end
+ *   over end when u_z < 0 (a cylinder is unchanged by that; for u_z = 0 the
+ *   first non-zero of u_x, u_y is made positive);
+ *   inputs (p_r, p_z, theta = atan2(|(u_x, u_y)|, u_z), phi = atan2(u_y, u_x)).
+ * Each network: (x - mu) * inv_sd -> depth SiLU layers of width W (16, 32 or
+ * 64) -> y = y_scale (w_o . h + b_o) + y_shift.  Outputs: the force on j and
+ * the torque on i in (x_hat, y_hat, z_hat) (tau_i has no z_hat part);
+ * F_i = -F_j, tau_j = -tau_i - s x F_j.  No pair energy is modelled.
+ * Flat parameters (FP32), one network after the other (f_1, f_2, f_3, tau_1,
+ * tau_2), each: mu[4], inv_sd[4], W_1[W][4], b_1[W], {W_l[W][W], b_l[W]} for
+ * l = 2..depth, w_o[W], b_o, y_scale, y_shift.
+ *
+ * rb_fnet_n_params: 5 x that size (-1 for a bad width or depth).
+ * rb_fnet_create: width 16, 32 or 64 (else RB_ENOTSUP), depth 1..8 (else
+ *   RB_EINVAL); parameters start at zero; all work goes to `stream`.
+ * rb_fnet_set_params / _get_params: n = rb_fnet_n_params; host or device
+ *   array (flag); a host copy synchronises.
+ * rb_fnet_pairs: n explicit pairs, cfg = (s, 0), (q_rel) as 2 float4 per
+ *   pair (device); out = (F_j, 0), (tau_i, 0), (tau_j, 0) as 3 float4 per pair
+ *   in body i's frame (device).  Asynchronous.
+ * rb_forces_fnet: the system's per-body forces and torques from the networks
+ *   (pairs of the list within Rc; i < j, i taken as cylinder 1), like
+ *   rb_forces_beads without an energy.
+ * rb_step_fnet: rb_step with these forces (NVE or NVT).
+ * Training (regression of the five components on bead-sum labels):
+ *   L = (1/B) sum_b sum_c (y_c - t_c)^2 with t = (F_j . x_hat, F_j . y_hat,
+ *   F_j . z_hat, tau_i . x_hat, tau_i . y_hat) from the labels of
+ *   rb_sample_pairs (cfg: 2 float4, labels: 3 float4 per pair, device).
+ *   rb_fnet_train_grad: L (host, synchronises when given) and optionally
+ *   dL/dparams into grad_out (device, flat layout; zero for mu, inv_sd,
+ *   y_scale, y_shift).  rb_fnet_train_step: the same, then one Adam step
+ *   (beta1, beta2, eps of the trainer).  batch <= max_batch (RB_EINVAL
+ *   otherwise).  Every sum runs in a fixed order (deterministic).
+ *   rb_fnet_trainer_set_cap: clamp every target to [-cap, cap] (cap >= 0,
+ *   0 = no cap; the paper caps its force and torque training values,
+ *   SI Sec. 6) and weight each sample's loss by w_b = 1 / (1 + |t_b|^2 /
+ *   f_scale^2) over its five capped targets (f_scale >= 0, 0 = weight 1):
+ *   L = (1/B) sum_b w_b sum_c (y_c - t_c)^2. */
+typedef struct rb_fnet rb_fnet;
+typedef struct rb_fnet_trainer rb_fnet_trainer;
+int64_t rb_fnet_n_params(int32_t width, int32_t depth);
+rb_status rb_fnet_create(int32_t width, int32_t depth, void* cuda_stream, rb_fnet** out);
+rb_status rb_fnet_destroy(rb_fnet* fnet);
+rb_status rb_fnet_set_params(rb_fnet* fnet, const float* flat, int64_t n, int32_t from_host);
+rb_status rb_fnet_get_params(const rb_fnet* fnet, float* flat, int64_t n, int32_t to_host);
+rb_status rb_fnet_pairs(const rb_fnet* fnet, int64_t n, const float* cfg, float* out);
+rb_status rb_forces_fnet(rb_system* sys, const rb_fnet* fnet, float* force, float* torque,
+                         double* virial9_host);
+rb_status rb_step_fnet(rb_system* sys, const rb_fnet* fnet, int64_t n_steps, float dt);
+rb_status rb_fnet_trainer_create(rb_fnet* fnet, int64_t max_batch, float lr, float beta1,
+                                 float beta2, float eps, rb_fnet_trainer** out);
+rb_status rb_fnet_trainer_destroy(rb_fnet_trainer* trainer);
+rb_status rb_fnet_trainer_set_lr(rb_fnet_trainer* trainer, float lr);
+rb_status rb_fnet_trainer_set_cap(rb_fnet_trainer* trainer, float cap, float f_scale);
+rb_status rb_fnet_train_grad(rb_fnet_trainer* trainer, int64_t batch, const float* cfg,
+                             const float* labels, float* grad_out, double* loss_host);
+rb_status rb_fnet_train_step(rb_fnet_trainer* trainer, int64_t batch, const float* cfg,
+                             const float* labels, double* loss_host);
 
 #ifdef __cplusplus
 }

@@ -123,26 +123,32 @@ def predict(nets, s, q_rel):
     return Fj, ti, tj, y
 
 
-def targets(s, q_rel, F_j, tau_i):
+def targets(s, q_rel, F_j, tau_i, cap=None):
     """Training targets: the bead-sum force on body j and torque on body i
-    (frame of body i) in the descriptor frame, (f_1, f_2, f_3, tau_1, tau_2)."""
+    (frame of body i) in the descriptor frame, (f_1, f_2, f_3, tau_1, tau_2),
+    optionally clamped to [-cap, cap] (the paper caps the wide range of its
+    force and torque training values, SI Sec. 6)."""
     xh, yh, zh, d = frame(s, q_rel)
     F_j = np.atleast_2d(F_j)
     tau_i = np.atleast_2d(tau_i)
     t = np.stack([(F_j * xh).sum(1), (F_j * yh).sum(1), (F_j * zh).sum(1),
                   (tau_i * xh).sum(1), (tau_i * yh).sum(1)], 1)
+    if cap:
+        t = np.clip(t, -cap, cap)
     return d, t
 
 
-def loss_and_grad(flat, width, depth, d, t):
-    """L = mean_b sum_c (y_c(d_b) - t_bc)^2 and dL/dflat (FP64 autograd);
-    mu, inv_sd, y_scale and y_shift are held fixed (zero gradient)."""
+def loss_and_grad(flat, width, depth, d, t, f_scale=None):
+    """L = mean_b w_b sum_c (y_c(d_b) - t_bc)^2 and dL/dflat (FP64 autograd),
+    w_b = 1 / (1 + |t_b|^2 / f_scale^2) when f_scale is given, else 1; mu,
+    inv_sd, y_scale and y_shift are held fixed (zero gradient)."""
     ft = torch.as_tensor(np.asarray(flat, dtype=np.float64)).clone().requires_grad_(True)
     nets = unpack(ft, width, depth)
     dt = torch.as_tensor(np.asarray(d, dtype=np.float64))
     tt = torch.as_tensor(np.asarray(t, dtype=np.float64))
     y = torch.stack([net_forward(p, dt) for p in nets], 1)
-    L = ((y - tt) ** 2).sum(1).mean()
+    w = 1.0 / (1.0 + (tt ** 2).sum(1) / f_scale ** 2) if f_scale else torch.ones(len(tt), dtype=tt.dtype)
+    L = (w * ((y - tt) ** 2).sum(1)).mean()
     (g,) = torch.autograd.grad(L, [ft])
     g = g.numpy().copy()
     n = net_size(width, depth)

@@ -18,7 +18,7 @@ RB_OK, RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_EOVERFLOW = 0, 1, 2, 3, 4
 RB_ENOT_READY, RB_ETIMEOUT, RB_EFAULT, RB_EBUSY, RB_ENOTSUP = 5, 6, 7, 8, 9
 RB_SHAPE_CUBE, RB_SHAPE_CYLINDER, RB_SHAPE_CUSTOM = 0, 1, 2
 RB_POT_LJ, RB_POT_HPHC, RB_POT_HPHC_PRINTED = 0, 1, 2
-RB_PATH_BEADS, RB_PATH_NN = 0, 1
+RB_PATH_BEADS, RB_PATH_NN, RB_PATH_FNET = 0, 1, 2
 RB_FP32, RB_BF16 = 0, 1
 
 
@@ -91,6 +91,20 @@ SIGNATURES = {
     "rb_checkpoint": (I32, [P, ctypes.c_char_p]),
     "rb_restore": (I32, [P, ctypes.c_char_p]),
     "rb_get_step": (I32, [P, I64P]),
+    "rb_fnet_n_params": (I64, [I32, I32]),
+    "rb_fnet_create": (I32, [I32, I32, P, ctypes.POINTER(P)]),
+    "rb_fnet_destroy": (I32, [P]),
+    "rb_fnet_set_params": (I32, [P, P, I64, I32]),
+    "rb_fnet_get_params": (I32, [P, P, I64, I32]),
+    "rb_fnet_pairs": (I32, [P, I64, P, P]),
+    "rb_forces_fnet": (I32, [P, P, P, P, DP]),
+    "rb_step_fnet": (I32, [P, P, I64, F32]),
+    "rb_fnet_trainer_create": (I32, [P, I64, F32, F32, F32, F32, ctypes.POINTER(P)]),
+    "rb_fnet_trainer_destroy": (I32, [P]),
+    "rb_fnet_trainer_set_lr": (I32, [P, F32]),
+    "rb_fnet_trainer_set_cap": (I32, [P, F32, F32]),
+    "rb_fnet_train_grad": (I32, [P, I64, P, P, P, DP]),
+    "rb_fnet_train_step": (I32, [P, I64, P, P, DP]),
     "rb_set_thermostat": (I32, [P, F32, F32]),
     "rb_get_thermostat": (I32, [P, DP]),
     "rb_set_reference": (I32, [P]),

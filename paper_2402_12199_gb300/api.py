@@ -19,7 +19,8 @@ POTENTIALS = {"lj": _lib.RB_POT_LJ, "hphc": _lib.RB_POT_HPHC,
               "hphc_printed": _lib.RB_POT_HPHC_PRINTED}
 PRECISION = {"fp32": RB_FP32, "bf16": RB_BF16, RB_FP32: RB_FP32, RB_BF16: RB_BF16}
 
-__all__ = ["System", "MLP", "RBError", "RB_PATH_BEADS", "RB_PATH_NN", "RB_FP32", "RB_BF16"]
+__all__ = ["System", "MLP", "FNet", "FNetTrainer", "RBError", "RB_PATH_BEADS", "RB_PATH_NN",
+           "RB_FP32", "RB_BF16"]
 
 
 def _stream_handle(stream=None) -> int:
@@ -187,6 +188,17 @@ class System:
              precision="fp32"):
         check(load().rb_step(self._h, path, mlp.handle if mlp is not None else None,
                              PRECISION[precision], int(n_steps), float(dt)))
+
+    def forces_fnet(self, fnet: "FNet", virial: bool = False):
+        F = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        T = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        v = (ctypes.c_double * 9)()
+        st = load().rb_forces_fnet(self._h, fnet.handle, F.data_ptr(), T.data_ptr(),
+                                   v if virial else None)
+        return self._finish(st, F, T, None, v, False, virial)
+
+    def step_fnet(self, fnet: "FNet", n_steps: int, dt: float):
+        check(load().rb_step_fnet(self._h, fnet.handle, int(n_steps), float(dt)))
 
     def eval_pairs(self, path: int = RB_PATH_BEADS, mlp: "MLP" = None, precision="fp32"):
         check(load().rb_eval_pairs(self._h, path, mlp.handle if mlp is not None else None,
@@ -356,6 +368,97 @@ def tc_gemm_check(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     check(load().rb_tc_gemm_check(N, K, A.data_ptr(), B.data_ptr(), D.data_ptr(),
                                   torch.cuda.current_stream().cuda_stream))
     return D
+
+
+class FNet:
+    """rb_fnet_*: the five per-component force/torque networks of cylinders."""
+
+    def __init__(self, width: int, depth: int = 3, stream=None):
+        L = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(L.rb_fnet_create(int(width), int(depth), _stream_handle(self.stream), ctypes.byref(h)))
+        self._h = h
+        self.width, self.depth = int(width), int(depth)
+        self.n_params = int(L.rb_fnet_n_params(int(width), int(depth)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().rb_fnet_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, flat):
+        if isinstance(flat, torch.Tensor) and flat.is_cuda:
+            t = flat.contiguous().float()
+            check(load().rb_fnet_set_params(self._h, t.data_ptr(), t.numel(), 0))
+            self._keep = t
+        else:
+            a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32).ravel())
+            check(load().rb_fnet_set_params(self._h, a.ctypes.data, a.size, 1))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(self.n_params, dtype=np.float32)
+        check(load().rb_fnet_get_params(self._h, a.ctypes.data, a.size, 1))
+        return a
+
+    def pairs(self, cfg: torch.Tensor) -> torch.Tensor:
+        """rb_fnet_pairs: cfg (n x 8: s, 0, q_rel) -> (n x 12: F_j, 0, tau_i, 0, tau_j, 0)."""
+        _dev(cfg, 8)
+        out = torch.empty((cfg.shape[0], 12), dtype=torch.float32, device="cuda")
+        check(load().rb_fnet_pairs(self._h, cfg.shape[0], cfg.data_ptr(), out.data_ptr()))
+        return out
+
+
+class FNetTrainer:
+    """rb_fnet_trainer_*: regression of the five components on bead labels."""
+
+    def __init__(self, fnet: FNet, max_batch: int, lr: float = 1e-3, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8):
+        h = ctypes.c_void_p()
+        check(load().rb_fnet_trainer_create(fnet.handle, int(max_batch), lr, beta1, beta2, eps,
+                                            ctypes.byref(h)))
+        self._h = h
+        self.fnet = fnet
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().rb_fnet_trainer_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def set_lr(self, lr: float):
+        check(load().rb_fnet_trainer_set_lr(self._h, float(lr)))
+
+    def set_cap(self, cap: float, f_scale: float = 0.0):
+        check(load().rb_fnet_trainer_set_cap(self._h, float(cap), float(f_scale)))
+
+    def grad(self, cfg: torch.Tensor, labels: torch.Tensor):
+        _dev(cfg, 8)
+        _dev(labels, 12)
+        g = torch.empty(self.fnet.n_params, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        check(load().rb_fnet_train_grad(self._h, cfg.shape[0], cfg.data_ptr(), labels.data_ptr(),
+                                        g.data_ptr(), ctypes.byref(loss)))
+        return loss.value, g
+
+    def step(self, cfg: torch.Tensor, labels: torch.Tensor, loss: bool = False):
+        _dev(cfg, 8)
+        _dev(labels, 12)
+        out = ctypes.c_double()
+        check(load().rb_fnet_train_step(self._h, cfg.shape[0], cfg.data_ptr(), labels.data_ptr(),
+                                        ctypes.byref(out) if loss else None))
+        return out.value if loss else None
 
 
 class Trainer:

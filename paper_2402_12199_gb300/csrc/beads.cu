@@ -33,10 +33,12 @@ namespace rb {
 // kernel listed those closer than rho_min.
 // C = 0: any template (bead_pair_warp); C = 5 or 8: a column-structured
 // template stored column by column (bead_pair_warp_cols), held to three CTAs
-// of 256 threads per SM (at most 85 registers).  POT = 0: Lennard-Jones beads;
-// POT = 1: the half-power half-cosine beads of Eq. 1 (either reading).
+// of 256 threads per SM (at most 85 registers) for up to 128 beads and to two
+// (no spills) for larger templates such as the 152-bead cylinder.  POT = 0:
+// Lennard-Jones beads; POT = 1: the half-power half-cosine beads of Eq. 1
+// (either reading).
 template <int NP, int C, int POT>
-__global__ void __launch_bounds__(256, C == 0 ? 1 : 3)
+__global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
     k_bead_pairs(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
                  const float4* __restrict__ pos, const float4* __restrict__ quat,
                  const float4* __restrict__ tmpl, int n_beads, BeadCols cols, float3 L,

@@ -211,7 +211,7 @@ struct rb_system {
     float4 *force = nullptr, *torque = nullptr;
     bool forces_valid = false;
     int forces_path = -1, forces_precision = -1;
-    const rb_mlp* forces_mlp = nullptr;
+    const void* forces_mlp = nullptr;     // rb_mlp or rb_fnet of the cached forces
     uint64_t forces_mlp_version = 0;
     // neighbour structures
     rb::CellList cells;
@@ -264,5 +264,20 @@ __global__ void k_zero_count(int* count);  // *count = 0 after pdl_wait (system.
 rb_status bead_fallback_async(rb_system* s);  // bead sum for pairs with rho < nn_fallback_rho
 // nn.cu
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision);
+// fnet.cu (per-component cylinder networks)
+rb_status fnet_pairs_system_async(rb_system* s, const rb_fnet* f);
+rb_status check_fnet(const rb_fnet* f);
+uint64_t fnet_version(const rb_fnet* f);  // bumped whenever its parameters change
+// train.cu: fixed-order GEMM C = beta C + alpha A B with strided operands
+// (A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn], C row-major), the
+// fixed-order column sum and Adam, shared with the per-component trainer
+rb_status sgemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak,
+                const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha,
+                float beta);
+__global__ void k_colsum(int M, int N, const float* __restrict__ A, int64_t lda,
+                         float* __restrict__ out, int accumulate);
+__global__ void k_adam(int64_t n, int64_t lo, int64_t hi, float* __restrict__ p,
+                       const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       float lr, float b1, float b2, float eps, float c1, float c2);
 rb_status check_mlp(const rb_mlp* m);
 }  // namespace rb

@@ -1187,13 +1187,16 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
     return finish_forces(s, force, torque, energy, virial9);
 }
 
-static rb_status eval_forces_async(rb_system* s, int path, const rb_mlp* m, int precision,
+// model: the rb_mlp of RB_PATH_NN or the rb_fnet of RB_PATH_FNET (unused for beads)
+static rb_status eval_forces_async(rb_system* s, int path, const void* model, int precision,
                                    float kick, bool checked = false) {
     RB_TRY(build_pairs_async(s, false, checked));
     if (path == RB_PATH_BEADS) {
         RB_TRY(bead_pairs_async(s));
+    } else if (path == RB_PATH_FNET) {
+        RB_TRY(fnet_pairs_system_async(s, static_cast<const rb_fnet*>(model)));
     } else {
-        RB_TRY(nn_pairs_system_async(s, m, precision));
+        RB_TRY(nn_pairs_system_async(s, static_cast<const rb_mlp*>(model), precision));
         if (s->nn_fallback_rho > 0.f) RB_TRY(bead_fallback_async(s));
     }
     return reduce_forces_async(s, kick);
@@ -1209,29 +1212,27 @@ rb_status rb_eval_pairs(rb_system* s, int32_t path, const rb_mlp* m, int32_t pre
     return fail(RB_EINVAL, "unknown path");
 }
 
-rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
-                  int64_t n_steps, float dt) {
-    if (!s) return fail(RB_EINVAL, "null system");
-    if (path != RB_PATH_BEADS && path != RB_PATH_NN) return fail(RB_EINVAL, "unknown path");
-    if (path == RB_PATH_NN) RB_TRY(check_mlp(m));
-    if (path == RB_PATH_BEADS) { m = nullptr; precision = RB_FP32; }
+// The MD step of every force path: `model` is null (beads), an rb_mlp (NN) or
+// an rb_fnet (FNET) whose parameter version is `version`.
+static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t version,
+                           int32_t precision, int64_t n_steps, float dt) {
     if (precision != RB_FP32 && precision != RB_BF16) return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
     const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
                       s->forces_precision == precision &&
-                      (!m || s->forces_mlp_version == m->version);
+                      (!m || s->forces_mlp_version == version);
     if (!same) {
         RB_TRY(eval_forces_async(s, path, m, precision, 0.f));
         s->forces_valid = true;
         s->forces_path = path;
         s->forces_precision = precision;
         s->forces_mlp = m;
-        s->forces_mlp_version = m ? m->version : 0;
+        s->forces_mlp_version = m ? version : 0;
     }
     if (n_steps == 0) return RB_OK;
     GraphCache& g = s->graph;
     if (!g.exec || g.path != path || g.precision != precision || g.mlp != m || g.dt != dt ||
-        (m && g.mlp_version != m->version) || g.nvt != (s->nh != nullptr)) {
+        (m && g.mlp_version != version) || g.nvt != (s->nh != nullptr)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1268,13 +1269,47 @@ rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision
         g.path = path;
         g.precision = precision;
         g.mlp = m;
-        g.mlp_version = m ? m->version : 0;
+        g.mlp_version = m ? version : 0;
         g.dt = dt;
         g.nvt = s->nh != nullptr;
     }
     for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
     s->step += n_steps;
     return RB_OK;
+}
+
+rb_status rb_step(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
+                  int64_t n_steps, float dt) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    if (path != RB_PATH_BEADS && path != RB_PATH_NN)
+        return fail(RB_EINVAL, "unknown path (per-component networks: rb_step_fnet)");
+    if (path == RB_PATH_NN) RB_TRY(check_mlp(m));
+    if (path == RB_PATH_BEADS) {
+        m = nullptr;
+        precision = RB_FP32;
+    }
+    return step_impl(s, path, m, m ? m->version : 0, precision, n_steps, dt);
+}
+
+rb_status rb_step_fnet(rb_system* s, const rb_fnet* f, int64_t n_steps, float dt) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    RB_TRY(check_fnet(f));
+    return step_impl(s, RB_PATH_FNET, f, fnet_version(f), RB_FP32, n_steps, dt);
+}
+
+rb_status rb_forces_fnet(rb_system* s, const rb_fnet* f, float* force, float* torque,
+                         double* virial9) {
+    if (!s) return fail(RB_EINVAL, "null system");
+    RB_TRY(check_fnet(f));
+    RB_TRY(build_pairs_async(s, false, false));
+    RB_TRY(fnet_pairs_system_async(s, f));
+    RB_TRY(reduce_forces_async(s, 0.f));
+    s->forces_valid = true;
+    s->forces_path = RB_PATH_FNET;
+    s->forces_precision = RB_FP32;
+    s->forces_mlp = f;
+    s->forces_mlp_version = fnet_version(f);
+    return finish_forces(s, force, torque, nullptr, virial9);
 }
 
 rb_status rb_set_skin(rb_system* s, float skin) {

@@ -160,9 +160,9 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-static rb_status sgemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam,
-                       int64_t sak, const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc,
-                       float alpha, float beta) {
+rb_status sgemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak,
+                const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha,
+                float beta) {
     dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
     k_sgemm<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta);
     RB_CUDA(cudaGetLastError());

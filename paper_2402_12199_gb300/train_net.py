@@ -21,7 +21,8 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
                   steps: int = 3000, batch: int = 4096, lr: float = 1e-3, lam_tau: float = 1.0,
                   lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
                   log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0,
-                  symmetric: bool = True, contact: float = 1.0, cutoff_width: float = 0.0):
+                  symmetric: bool = True, contact: float = 1.0, cutoff_width: float = 0.0,
+                  potential: str = "lj", hphc=None):
     """Returns (mlp, report).  With `symmetric` the body's point group is
     attached to the network (rb_mlp_set_symmetry), so it learns one copy of
     every class of symmetry-related configurations, and the feature
@@ -31,9 +32,10 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     `contact`: smallest bead-bead distance (sigma units) that defines contact
     for the sampled separations (rb_sample_pairs_at).  `cutoff_width` > 0:
     the energy is switched smoothly to zero between Rc - cutoff_width and Rc
-    (rb_mlp_set_cutoff) during training and afterwards."""
+    (rb_mlp_set_cutoff) during training and afterwards.  `potential`, `hphc`:
+    the bead potential that labels the samples (as api.System)."""
     box = 60.0 if shape == "cube" else 70.0
-    sysobj = api.System(8, [box] * 3, shape)
+    sysobj = api.System(8, [box] * 3, shape, potential=potential, hphc=hphc)
     Rc = sysobj.pair_cutoff
     u = torch.from_numpy(inputs.sampler_uniforms(n_samples + 10000, seed)).cuda()
     t0 = time.perf_counter()
@@ -114,6 +116,69 @@ def force_error(system: api.System, mlp: api.MLP, precision: str = "bf16"):
     """NN-versus-bead error of whole-system forces and torques (model error)."""
     ref = system.forces_beads()
     r = system.forces_nn(mlp, precision)
+    system.sync()
+    err = lambda a, b: float(torch.linalg.norm(a[:, :3] - b[:, :3]) / torch.linalg.norm(b[:, :3]))
+    return {"e_F": err(r["force"], ref["force"]), "e_tau": err(r["torque"], ref["torque"])}
+
+
+def fnet_init(width: int, depth: int, Rc: float, cap: float, seed: int = 0) -> np.ndarray:
+    """Initial parameters of the five per-component networks: weights
+    N(0, 1/fan_in), zero biases, input normalisation from the ranges of the
+    four numbers (p_r, p_z in [0, Rc], theta in [0, pi/2], phi in [-pi, pi]),
+    output scale cap / 4 (targets are capped to [-cap, cap])."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(5):
+        p = [np.array([Rc / 2, Rc / 2, np.pi / 4, 0.0]), np.array([2 / Rc, 2 / Rc, 4 / np.pi, 1 / np.pi])]
+        fan = 4
+        for _l in range(depth):
+            p.append(rng.standard_normal(width * fan) / np.sqrt(fan))
+            p.append(np.zeros(width))
+            fan = width
+        p.append(rng.standard_normal(width) / np.sqrt(width))
+        p.append(np.array([0.0, cap / 4.0, 0.0]))
+        parts.append(np.concatenate(p))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train_fnet(shape: str, width: int, depth: int, n_samples: int, steps: int, batch: int,
+               lr: float, cap: float, contact: float = 1.0, seed: int = 0, f_scale: float = 0.0):
+    """Per-component networks (rb_fnet) trained on the device: n_samples pairs
+    drawn and labelled by the bead sum, capped regression, Adam with cosine
+    decay.  Returns (fnet, report)."""
+    s = api.System(8, [80.0] * 3, shape)
+    u = torch.from_numpy(inputs.sampler_uniforms(n_samples, seed + 101)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cfg, lab, _ = api.sample_pairs(s, u, contact)
+    torch.cuda.synchronize()
+    t_sample = time.perf_counter() - t0
+    f = api.FNet(width, depth)
+    f.set_params(fnet_init(width, depth, s.pair_cutoff, cap, seed))
+    tr = api.FNetTrainer(f, batch, lr=lr)
+    tr.set_cap(cap, f_scale)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    t0 = time.perf_counter()
+    first = None
+    for k in range(steps):
+        idx = torch.randint(0, n_samples, (batch,), device="cuda", generator=g)
+        tr.set_lr(lr * 0.5 * (1.0 + np.cos(np.pi * k / max(1, steps))))
+        loss = tr.step(cfg[idx].contiguous(), lab[idx].contiguous(), loss=(k == 0))
+        if k == 0:
+            first = loss
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    last = tr.grad(cfg[:batch].contiguous(), lab[:batch].contiguous())[0]
+    return f, {"samples": n_samples, "steps": steps, "batch": batch, "cap": cap, "f_scale": f_scale,
+               "contact": contact,
+               "t_sample_s": t_sample, "t_train_s": t_train, "loss_first": first, "loss_last": last}
+
+
+def fnet_force_error(system: api.System, f: api.FNet):
+    """Per-component-network-versus-bead error of whole-system forces and torques."""
+    ref = system.forces_beads()
+    r = system.forces_fnet(f)
     system.sync()
     err = lambda a, b: float(torch.linalg.norm(a[:, :3] - b[:, :3]) / torch.linalg.norm(b[:, :3]))
     return {"e_F": err(r["force"], ref["force"]), "e_tau": err(r["torque"], ref["torque"])}

@@ -10,7 +10,8 @@
     third law and angular-momentum balance, give no torque on cylinder 1
     about its axis, and map back to the same five numbers;
   * a width-1 network is the hand-written scalar composition;
-  * the regression loss gradient equals central differences.
+  * the regression loss gradient (plain and force-scale weighted) equals
+    central differences.
 No GPU.
 """
 import math
@@ -145,21 +146,22 @@ def test_width_one_network_closed_form():
         assert got == pytest.approx(expect, rel=1e-14)
 
 
-def test_regression_gradient_matches_central_differences():
+@pytest.mark.parametrize("f_scale", [None, 1.5])
+def test_regression_gradient_matches_central_differences(f_scale):
     width, depth = 6, 2
     flat = _rand_flat(width, depth, 6)
     rng = np.random.default_rng(7)
     d = np.column_stack([rng.uniform(2, 8, 20), rng.uniform(0, 5, 20), rng.uniform(0, 1.5, 20),
                          rng.uniform(-3, 3, 20)])
     t = rng.standard_normal((20, 5))
-    L, g = fnet.loss_and_grad(flat, width, depth, d, t)
+    L, g = fnet.loss_and_grad(flat, width, depth, d, t, f_scale=f_scale)
     n = fnet.net_size(width, depth)
     h = 1e-6
     for k in rng.choice(len(flat), 40, replace=False):
         e = np.zeros_like(flat)
         e[k] = h
-        fd = (fnet.loss_and_grad(flat + e, width, depth, d, t)[0]
-              - fnet.loss_and_grad(flat - e, width, depth, d, t)[0]) / (2 * h)
+        fd = (fnet.loss_and_grad(flat + e, width, depth, d, t, f_scale=f_scale)[0]
+              - fnet.loss_and_grad(flat - e, width, depth, d, t, f_scale=f_scale)[0]) / (2 * h)
         if k % n < 8 or k % n >= n - 2:
             assert g[k] == 0.0  # held fixed
         else:
