@@ -118,11 +118,10 @@ static rb_status start_replica(rb_server* sv, Request* r) {
 
 static rb_status launch_chunk(rb_server* sv, Request* r) {
     const int64_t n = std::min<int64_t>(sv->chunk, r->n_steps - r->done);
-    const size_t b = sizeof(float4) * r->desc.n_bodies;
-    RB_CUDA(cudaMemcpyAsync(r->backup, r->sys->pos, b, cudaMemcpyDeviceToDevice, r->stream));
-    RB_CUDA(cudaMemcpyAsync(r->backup + r->desc.n_bodies, r->sys->quat, b, cudaMemcpyDeviceToDevice, r->stream));
-    RB_CUDA(cudaMemcpyAsync(r->backup + 2 * r->desc.n_bodies, r->sys->vel, b, cudaMemcpyDeviceToDevice, r->stream));
-    RB_CUDA(cudaMemcpyAsync(r->backup + 3 * r->desc.n_bodies, r->sys->angmom, b, cudaMemcpyDeviceToDevice, r->stream));
+    // the backup block has the state's layout (pos | quat | vel | angmom): one copy
+    float* bk = (float*)r->backup;
+    const int64_t n4 = 4 * r->desc.n_bodies;
+    RB_TRY(rb_get_state(r->sys, bk, bk + n4, bk + 2 * n4, bk + 3 * n4, 0));
     while ((int64_t)r->ev.size() < n + 1) {
         cudaEvent_t e;
         RB_CUDA(cudaEventCreate(&e));
@@ -145,12 +144,10 @@ static bool harvest_chunk(rb_server* sv, Request* r) {
     rb_status st = rb_sync(r->sys);
     if (st == RB_EFAULT && r->path == RB_PATH_NN) {
         // roll back to the chunk start and continue on the bead path
-        const size_t b = sizeof(float4) * r->desc.n_bodies;
         const float4* bk = r->backup;
         rb_set_state(r->sys, (const float*)bk, (const float*)(bk + r->desc.n_bodies),
                      (const float*)(bk + 2 * r->desc.n_bodies),
                      (const float*)(bk + 3 * r->desc.n_bodies), 0);
-        (void)b;
         r->fell_back = true;
         r->path = RB_PATH_BEADS;
         r->chunk_n = 0;

@@ -876,10 +876,14 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
 #define ALLOC(ptr, bytes) \
     if (e == cudaSuccess) e = A((void**)&(ptr), (bytes))
     ALLOC(s->tmpl_dev, sizeof(float4) * s->n_beads);
-    ALLOC(s->pos, sizeof(float4) * N);
-    ALLOC(s->quat, sizeof(float4) * N);
-    ALLOC(s->vel, sizeof(float4) * N);
-    ALLOC(s->angmom, sizeof(float4) * N);
+    // the four state arrays as one block (pos | quat | vel | angmom), so that a
+    // caller's contiguous state moves in one copy
+    ALLOC(s->pos, sizeof(float4) * 4 * N);
+    if (e == cudaSuccess) {
+        s->quat = s->pos + N;
+        s->vel = s->pos + 2 * N;
+        s->angmom = s->pos + 3 * N;
+    }
     ALLOC(s->force, sizeof(float4) * N);
     ALLOC(s->torque, sizeof(float4) * N);
     ALLOC(s->cells.count, sizeof(int) * s->cells.n_cells);
@@ -983,7 +987,7 @@ rb_status rb_destroy_system(rb_system* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-    void* ptrs[] = {s->tmpl_dev, s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
+    void* ptrs[] = {s->tmpl_dev, s->pos, s->force, s->torque,
                     s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
                     s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
                     s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
@@ -1019,10 +1023,15 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
     if (!s) return fail(RB_EINVAL, "null system");
     const size_t b = sizeof(float4) * s->N;
     const cudaMemcpyKind k = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    if (pos) RB_CUDA(cudaMemcpyAsync(s->pos, pos, b, k, s->stream));
-    if (quat) RB_CUDA(cudaMemcpyAsync(s->quat, quat, b, k, s->stream));
-    if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
-    if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
+    const size_t n4 = 4 * (size_t)s->N;  // floats per array
+    if (pos && quat == pos + n4 && vel == pos + 2 * n4 && angmom == pos + 3 * n4) {
+        RB_CUDA(cudaMemcpyAsync(s->pos, pos, 4 * b, k, s->stream));  // one block, one copy
+    } else {
+        if (pos) RB_CUDA(cudaMemcpyAsync(s->pos, pos, b, k, s->stream));
+        if (quat) RB_CUDA(cudaMemcpyAsync(s->quat, quat, b, k, s->stream));
+        if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
+        if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
+    }
     if (pos) {
         k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
         RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
@@ -1096,10 +1105,15 @@ rb_status rb_get_state(const rb_system* s, float* pos, float* quat, float* vel, 
     if (!s) return fail(RB_EINVAL, "null system");
     const size_t b = sizeof(float4) * s->N;
     const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    if (pos) RB_CUDA(cudaMemcpyAsync(pos, s->pos, b, k, s->stream));
-    if (quat) RB_CUDA(cudaMemcpyAsync(quat, s->quat, b, k, s->stream));
-    if (vel) RB_CUDA(cudaMemcpyAsync(vel, s->vel, b, k, s->stream));
-    if (angmom) RB_CUDA(cudaMemcpyAsync(angmom, s->angmom, b, k, s->stream));
+    const size_t n4 = 4 * (size_t)s->N;
+    if (pos && quat == pos + n4 && vel == pos + 2 * n4 && angmom == pos + 3 * n4) {
+        RB_CUDA(cudaMemcpyAsync(pos, s->pos, 4 * b, k, s->stream));  // one block, one copy
+    } else {
+        if (pos) RB_CUDA(cudaMemcpyAsync(pos, s->pos, b, k, s->stream));
+        if (quat) RB_CUDA(cudaMemcpyAsync(quat, s->quat, b, k, s->stream));
+        if (vel) RB_CUDA(cudaMemcpyAsync(vel, s->vel, b, k, s->stream));
+        if (angmom) RB_CUDA(cudaMemcpyAsync(angmom, s->angmom, b, k, s->stream));
+    }
     if (to_host == 1) RB_CUDA(cudaStreamSynchronize(s->stream));
     return RB_OK;
 }
@@ -1216,7 +1230,8 @@ rb_status rb_eval_pairs(rb_system* s, int32_t path, const rb_mlp* m, int32_t pre
 // an rb_fnet (FNET) whose parameter version is `version`.
 static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t version,
                            int32_t precision, int64_t n_steps, float dt) {
-    if (precision != RB_FP32 && precision != RB_BF16) return fail(RB_EINVAL, "unknown precision");
+    if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
+        return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
     const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
                       s->forces_precision == precision &&

@@ -295,3 +295,25 @@ def test_state_read_back_asynchronously_into_pinned_memory():
     ref = s.get_state(to_host=True)
     for k in out:
         np.testing.assert_array_equal(out[k].numpy(), ref[k])
+
+
+def test_contiguous_state_block_moves_in_one_copy_and_round_trips():
+    """State given as one page-locked block (pos | quat | vel | angmom) takes the
+    single-copy path in and out and round-trips exactly; separate arrays and
+    the block give the same state."""
+    import torch
+
+    st, L, tmpl = make_state(777, 0.1, 91)
+    a = gpu_system(st, L)
+    blk = torch.from_numpy(np.stack([st[k] for k in ("pos", "quat", "vel", "angmom")])).pin_memory()
+    b = gpu_system(st, L)
+    b.set_state(blk[0], blk[1], blk[2], blk[3])
+    out = torch.empty((4, 777, 4), dtype=torch.float32).pin_memory()
+    b.get_state(to_host=True, out={k: out[i] for i, k in enumerate(("pos", "quat", "vel", "angmom"))})
+    for i, k in enumerate(("pos", "quat", "vel", "angmom")):
+        assert np.array_equal(out[i].numpy(), st[k]), k
+    a.step(10, 0.002)
+    b.step(10, 0.002)
+    ra, rb = a.get_state(to_host=True), b.get_state(to_host=True)
+    for k in ("pos", "quat", "vel", "angmom"):
+        assert np.array_equal(ra[k], rb[k]), k
