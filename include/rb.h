@@ -58,7 +58,11 @@ typedef enum rb_status {
 enum { RB_SHAPE_CUBE = 0, RB_SHAPE_CYLINDER = 1, RB_SHAPE_CUSTOM = 2 };
 enum { RB_POT_LJ = 0, RB_POT_HPHC = 1, RB_POT_HPHC_PRINTED = 2 };
 enum { RB_PATH_BEADS = 0, RB_PATH_NN = 1, RB_PATH_FNET = 2 };
-enum { RB_FP32 = 0, RB_BF16 = 1 };
+/* Network arithmetic.  RB_FP32: SIMT FP32.  RB_BF16: BF16 tensor-core GEMMs
+ * with FP32 accumulation.  RB_F16X3: FP32-accurate tensor-core GEMMs, each
+ * operand split into two power-of-two-scaled FP16 parts, three products
+ * accumulated in FP32 (width 128, depth 1..3). */
+enum { RB_FP32 = 0, RB_BF16 = 1, RB_F16X3 = 2 };
 
 /* Thread-local message describing the most recent failure on this thread. */
 const char* rb_last_error(void);
@@ -132,7 +136,9 @@ rb_status rb_body_info(const rb_system* sys, float* mass_host, float* inertia3_h
 rb_status rb_body_template(const rb_system* sys, float* xyz_host);
 
 /* Copy the state in (float4 rows, see above).  from_host != 0: the pointers
- * are host memory.  Invalidates cached forces. */
+ * are host memory.  Invalidates cached forces.  When the four arrays are one
+ * contiguous block (quat = pos + 4N floats, vel = pos + 8N, angmom =
+ * pos + 12N) they move in a single copy (the same holds for rb_get_state). */
 rb_status rb_set_state(rb_system* sys, const float* pos, const float* quat, const float* vel,
                        const float* angmom, int32_t from_host);
 /* Copy the state out; any pointer may be NULL.  to_host: 0 device pointers;
@@ -355,7 +361,9 @@ rb_status rb_nn_canonical(const rb_mlp* mlp, int64_t n, float* cfg, float* label
  * list as rb_forces_beads).  Each unordered pair i < j is evaluated once with
  * i as the reference body.  RB_FP32: SIMT FP32 arithmetic (widths 64, 128,
  * 256); RB_BF16: BF16 tensor-core GEMMs (tcgen05) with FP32 accumulation
- * (widths 128 and 256, depth 1..3; RB_ENOTSUP otherwise). */
+ * (widths 128 and 256, depth 1..3); RB_F16X3: the same GEMMs at FP32
+ * accuracy from split FP16 operands (width 128, depth 1..3); RB_ENOTSUP for
+ * other shapes. */
 rb_status rb_forces_nn(rb_system* sys, const rb_mlp* mlp, int32_t precision, float* force,
                        float* torque, double* energy_host, double* virial9_host);
 

@@ -19,7 +19,7 @@ RB_ENOT_READY, RB_ETIMEOUT, RB_EFAULT, RB_EBUSY, RB_ENOTSUP = 5, 6, 7, 8, 9
 RB_SHAPE_CUBE, RB_SHAPE_CYLINDER, RB_SHAPE_CUSTOM = 0, 1, 2
 RB_POT_LJ, RB_POT_HPHC, RB_POT_HPHC_PRINTED = 0, 1, 2
 RB_PATH_BEADS, RB_PATH_NN, RB_PATH_FNET = 0, 1, 2
-RB_FP32, RB_BF16 = 0, 1
+RB_FP32, RB_BF16, RB_F16X3 = 0, 1, 2
 
 
 class RBError(RuntimeError):

@@ -11,16 +11,18 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (RB_BF16, RB_FP32, RB_PATH_BEADS, RB_PATH_NN, RB_SHAPE_CUBE, RB_SHAPE_CUSTOM,
+from ._lib import (RB_BF16, RB_F16X3, RB_FP32, RB_PATH_BEADS, RB_PATH_NN, RB_SHAPE_CUBE, RB_SHAPE_CUSTOM,
                    RB_SHAPE_CYLINDER, RBError, check, load)
 
 SHAPES = {"cube": RB_SHAPE_CUBE, "cylinder": RB_SHAPE_CYLINDER, "custom": RB_SHAPE_CUSTOM}
 POTENTIALS = {"lj": _lib.RB_POT_LJ, "hphc": _lib.RB_POT_HPHC,
               "hphc_printed": _lib.RB_POT_HPHC_PRINTED}
-PRECISION = {"fp32": RB_FP32, "bf16": RB_BF16, RB_FP32: RB_FP32, RB_BF16: RB_BF16}
+# "f16x3": FP32 accuracy on the tensor cores (split FP16 operands)
+PRECISION = {"fp32": RB_FP32, "bf16": RB_BF16, "f16x3": RB_F16X3, RB_FP32: RB_FP32,
+             RB_BF16: RB_BF16, RB_F16X3: RB_F16X3}
 
 __all__ = ["System", "MLP", "FNet", "FNetTrainer", "RBError", "RB_PATH_BEADS", "RB_PATH_NN",
-           "RB_FP32", "RB_BF16"]
+           "RB_FP32", "RB_BF16", "RB_F16X3"]
 
 
 def _stream_handle(stream=None) -> int:

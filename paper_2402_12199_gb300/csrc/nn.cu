@@ -467,6 +467,7 @@ rb_status mlp_refresh(rb_mlp* m) {
                                                          m->f32_prep);
     RB_CUDA(cudaGetLastError());
     RB_TRY(nn_tc_prepare(m));
+    RB_TRY(nn_f16x3_prepare(m));
     m->version++;
     return RB_OK;
 }
@@ -481,6 +482,7 @@ static int sm_count() {
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     RB_TRY(check_mlp(m));
     if (precision == RB_BF16) return nn_tc_system_async(s, m);
+    if (precision == RB_F16X3) return nn_f16x3_system_async(s, m);
     if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
     set_symmetry(src, m);
@@ -541,6 +543,7 @@ rb_status rb_mlp_destroy(rb_mlp* m) {
     if (m->params) cudaFree(m->params);
     if (m->f32_prep) cudaFree(m->f32_prep);
     if (m->bf16_img) cudaFree(m->bf16_img);
+    if (m->f16x3_img) cudaFree(m->f16x3_img);
     if (m->sym_dev) cudaFree(m->sym_dev);
     if (m->status_dev) cudaFree(m->status_dev);
     delete m;
@@ -583,6 +586,10 @@ rb_status rb_nn_pairs(const rb_mlp* m, int32_t precision, int64_t n, const float
     if (precision == RB_BF16)
         return nn_tc_pairs_async(m, n, reinterpret_cast<const float4*>(cfg),
                                  reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(grad_out));
+    if (precision == RB_F16X3)
+        return nn_f16x3_pairs_async(m, n, reinterpret_cast<const float4*>(cfg),
+                                    reinterpret_cast<float4*>(out),
+                                    reinterpret_cast<float4*>(grad_out));
     if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
     set_symmetry(src, m);

@@ -405,6 +405,12 @@ rb_status nn_pairs_f32_async(const rb_mlp* m, int64_t n, const float4* cfg, floa
 rb_status mlp_refresh(rb_mlp* m);  // rebuild the derived weight copies after params change
 // nn_tc.cu
 rb_status nn_tc_prepare(rb_mlp* m);
+// nn_f16x3.cu (FP32 accuracy from split FP16 operands on the tensor cores)
+bool nn_f16x3_supported(const rb_mlp* m);
+rb_status nn_f16x3_prepare(rb_mlp* m);
+rb_status nn_f16x3_system_async(rb_system* s, const rb_mlp* m);
+rb_status nn_f16x3_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
+                               float4* grad);
 rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m);
 rb_status nn_tc_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
                             float4* grad);

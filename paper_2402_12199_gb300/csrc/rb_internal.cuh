@@ -180,6 +180,7 @@ struct rb_mlp {
     float* params = nullptr;      // flat FP32 (device)
     float* f32_prep = nullptr;    // transposed/padded FP32 copies for the SIMT kernel
     void* bf16_img = nullptr;     // BF16 shared-memory image for the tensor-core kernel
+    void* f16x3_img = nullptr;    // FP16 hi/lo weight image of the FP32-accurate tensor-core kernel
     unsigned* status_dev = nullptr;  // sticky device-side error bits of pair-level calls
     uint64_t version = 1;         // bumped on every set_params
     // point group of the bodies (symmetry-reduced configurations): device

@@ -53,7 +53,7 @@ def _configs(n, seed, group, rho=(R_ON - 0.4, R_OFF + 0.3)):
 
 
 @pytest.mark.parametrize("width,precision,tol", [(128, "fp32", TOL_F32), (128, "bf16", TOL_BF16),
-                                                 (256, "bf16", TOL_BF16)])
+                                                 (256, "bf16", TOL_BF16), (128, "f16x3", TOL_F32)])
 def test_switched_pairs_parity(width, precision, tol):
     import torch
 

@@ -97,7 +97,7 @@ def test_canonical_matches_oracle(shape):
 
 @pytest.mark.parametrize("width,precision,tol", [(64, "fp32", TOL_F32), (128, "fp32", TOL_F32),
                                                  (256, "fp32", TOL_F32), (128, "bf16", TOL_BF16),
-                                                 (256, "bf16", TOL_BF16)])
+                                                 (256, "bf16", TOL_BF16), (128, "f16x3", TOL_F32)])
 def test_symmetric_pairs_parity(width, precision, tol):
     import torch
 
@@ -158,7 +158,8 @@ def _pair_margins(st, L, pairs, group):
     return np.minimum(np.minimum(mk, mj), np.abs(cq[:, 0]))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", TOL_F32), ("bf16", TOL_BF16)])
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_F32), ("bf16", TOL_BF16),
+                                           ("f16x3", TOL_F32)])
 def test_symmetric_system_forces_parity(precision, tol):
     import oracle
 
