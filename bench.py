@@ -7,10 +7,11 @@ velocities at kT = 1, NVE velocity Verlet at dt = 0.002.
 
 One bench step = one full MD step (integrate, cell list, pair list, pair
 force/torque evaluation, per-body reduction and half kick) of the same system
-on each force path: the bead double sum (FP32) and the pair network (FP32
-SIMT; BF16 tensor cores where built).  `value` = body-pair force+torque
-evaluations per second over both paths.  Per-path MD steps/s are reported in
-`paths`.
+on each force path: the bead double sum (FP32), the pair network at FP32
+accuracy (tensor cores, split FP16 operands: RB_F16X3) and the pair network in
+BF16 (tensor cores).  `value` = body-pair force+torque evaluations per second
+over all paths.  Per-path MD steps/s are reported in `paths`; the SIMT FP32
+network kernel is timed beside them (`nn_fp32_simt`).
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 system stream; a 256 MiB buffer is written between steps (outside the events)
@@ -45,7 +46,7 @@ WIDTH, DEPTH = 128, 3
 #                   --train-steps 0 --drift-steps 0 [--no-paper-workload]
 # None would mark a kernel changed since its capture.
 NCU_DRAM_BYTES = {"k_bead_pairs": 1.855e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 3.588e6,
-                  "k_nn_tc256": 2.458e6}
+                  "k_nn_tc256": 2.458e6, "k_nn_f16x3": None}
 
 
 def parse():
@@ -54,7 +55,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="beads,nn_fp32,nn_bf16")
+    ap.add_argument("--paths", default="beads,nn_f16x3,nn_bf16")
     ap.add_argument("--cpu-sample-pairs", type=int, default=100000)
     ap.add_argument("--ref-sample-pairs", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -531,23 +532,71 @@ def main():
                    "peak_source": f"bf16_tflops_sustained ({how})", "flops_per_launch": flops,
                    "mufu_per_pair": 6 * WIDTH, "note": "one tanh.approx per SiLU evaluation"}
 
-    roof_f32 = None
-    if "nn_fp32" in systems:
-        s = systems["nn_fp32"]
+    def kernel_ms(s, prec):
         s.build_pairs()
         for _ in range(3):
-            s.eval_pairs(api.RB_PATH_NN, mlp, "fp32")
+            s.eval_pairs(api.RB_PATH_NN, mlp, prec)
         durs = []
         for _ in range(10):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            s.eval_pairs(api.RB_PATH_NN, mlp, "fp32")
+            s.eval_pairs(api.RB_PATH_NN, mlp, prec)
             b.record(stream)
             durs.append((a, b))
         torch.cuda.synchronize()
-        d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
-        flops = nn_flops_per_pair(WIDTH, DEPTH) * n_pairs["nn_fp32"]
+        return statistics.mean(a.elapsed_time(b) for a, b in durs)
+
+    roof_x3 = None
+    if "nn_f16x3" in systems:
+        d_ms = kernel_ms(systems["nn_f16x3"], "f16x3")
+        # three FP16 products per layer GEMM (hi.hi, hi.lo, lo.hi), the same
+        # padded shapes as the BF16 kernel
+        tc_flops = 3 * 2.0 * 128 * (128 * 64 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
+        flops = tc_flops / 128 * n_pairs["nn_f16x3"]
+        achieved = flops / (d_ms * 1e-3) / 1e12
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        alg = nn_flops_per_pair(WIDTH, DEPTH) * n_pairs["nn_f16x3"] / (d_ms * 1e-3) / 1e12
+        roof_x3 = {"kernel": "k_nn_f16x3", "bound": "tensor", "achieved": achieved, "peak": peak,
+                   "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+                   "traffic": NCU_DRAM_BYTES["k_nn_f16x3"], "traffic_unit": "bytes per launch (ncu)",
+                   "peak_source": f"bf16_tflops_sustained ({how}); FP16 and BF16 share the "
+                                  "dense tensor rate",
+                   "flops_per_launch": flops,
+                   "fp32_network_tflops": alg,
+                   "note": "FP32-accurate: operands split into two scaled FP16 parts, three "
+                           "tensor-core products per GEMM; fp32_network_tflops counts the "
+                           "network's own FP32 flops (2 x 2 (10w + 2w^2 + w) per pair)"}
+
+    # the SIMT FP32 network kernel, timed beside the step (a system of its own
+    # when the step does not run it)
+    roof_f32 = None
+    simt = None
+    if any(p.startswith("nn") for p in paths):
+        if "nn_fp32" in systems:
+            s = systems["nn_fp32"]
+        else:
+            s = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
+            s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+            s.set_nn_fallback(rho_fallback)
+            s.forces_nn(mlp, "fp32")
+            md = []
+            for _ in range(3):
+                s.step(1, DT, path=api.RB_PATH_NN, mlp=mlp, precision="fp32")
+            for _ in range(20):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.step(1, DT, path=api.RB_PATH_NN, mlp=mlp, precision="fp32")
+                b.record(stream)
+                md.append((a, b))
+            torch.cuda.synchronize()
+            s.sync()
+            simt = {"ms_per_md_step": statistics.mean(a.elapsed_time(b) for a, b in md),
+                    "md_steps": 20, "note": "SIMT FP32 network path, same state, not in the step"}
+        d_ms = kernel_ms(s, "fp32")
+        n_f32 = s.build_pairs()
+        flops = nn_flops_per_pair(WIDTH, DEPTH) * n_f32
         achieved = flops / (d_ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
         roof_f32 = {"kernel": "k_nn_f32", "bound": "alu", "achieved": achieved, "peak": peak,
@@ -555,6 +604,10 @@ def main():
                     "traffic": NCU_DRAM_BYTES["k_nn_f32"], "traffic_unit": "bytes per launch (ncu)",
                     "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
                     "flops_per_launch": flops}
+        if simt is not None:
+            simt["kernel_ms"] = d_ms
+            simt["f16x3_kernel_speedup"] = d_ms / roof_x3["kernel_ms"] if roof_x3 else None
+            del s
 
     # ---- cylinder training throughput at width 256: 1M pairs drawn and
     # labelled on the device, then Adam steps on batches of 4096
@@ -890,6 +943,10 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "path_dtypes": {"beads": "f32", "nn_fp32": "f32 (SIMT)",
+                            "nn_f16x3": "f16 x3 split products, f32 accumulation (FP32 accuracy, "
+                                        "parity-tested at the FP32 tolerance)",
+                            "nn_bf16": "bf16 products, f32 accumulation"},
             "config": {"workload": f"{N_BODIES} cubes (5x5x5 beads, LJ eps=sigma=1 rc=2.5), "
                                    f"phi={PHI}, NVE dt={DT}; one MD step per force path "
                                    f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU "
@@ -900,7 +957,8 @@ def main():
                        "pair_list": f"Verlet skin {args.skin} sigma, rebuilt on the device when a "
                                     f"centre moves more than skin/2; pairs beyond Rc give exactly zero",
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
-            "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_fp32": roof_f32, "cpu_baseline": cpu,
+            "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_f16x3": roof_x3,
+            "roofline_nn_fp32": roof_f32, "nn_fp32_simt": simt, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
             "nn_bf16_width256": width256, "nve_drift": drift, "training_cylinders_w256": train_cyl,
             "paper_workload_hphc_nvt": paper_wl, "cylinders_per_component_networks": fnet_leg,

@@ -139,20 +139,21 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 
 // The three products of one stage (small terms first), committed to `bar`;
 // mma_bf16 issues kind::f16, whose operand type comes from the descriptor.
-__device__ inline void issue_gemm3(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                   uint32_t b_lo, int K, int rows_b, uint32_t idesc, uint32_t bar) {
+// K and the B rows are compile-time, so the loop unrolls into the MMAs alone
+// with constant descriptor offsets (see sdesc_at).
+template <int K, int ROWS_B>
+__device__ inline void issue_gemm3(uint32_t tmem_d, uint64_t da_hi, uint64_t da_lo, uint64_t db_hi,
+                                   uint64_t db_lo, uint32_t idesc, uint32_t bar) {
     fence_after();
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-        const uint32_t a = p == 0 ? a_lo : a_hi;
-        const uint32_t b = p == 1 ? b_lo : b_hi;
-        for (int k = 0; k < K / 16; ++k) {
-            const uint32_t koff_a = (uint32_t)(k >> 2) * (kM * 128) + (uint32_t)(k & 3) * 32;
-            const uint32_t koff_b =
-                (uint32_t)(k >> 2) * (uint32_t)(rows_b * 128) + (uint32_t)(k & 3) * 32;
-            mma_bf16(tmem_d, sdesc(a + koff_a), sdesc(b + koff_b), idesc,
+        const uint64_t da = p == 0 ? da_lo : da_hi;
+        const uint64_t db = p == 1 ? db_lo : db_hi;
+#pragma unroll
+        for (int k = 0; k < K / 16; ++k)
+            mma_bf16(tmem_d, sdesc_at(da, (k >> 2) * (kM * 128) + (k & 3) * 32),
+                     sdesc_at(db, (k >> 2) * (ROWS_B * 128) + (k & 3) * 32), idesc,
                      (p > 0 || k > 0) ? 1u : 0u);
-        }
     }
     mma_commit(bar);
 }
@@ -162,19 +163,44 @@ __device__ inline void pair_sync(int g) {
     asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
 }
 
-__device__ inline float sigmoid_f32(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+__device__ inline float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ inline float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// SiLU and its derivative for two pre-activations, packed FP32x2: the
+// logistic function s = 1 / (1 + e^-z) with e^-z = 2^(-z log2 e) (hardware
+// base-2 exponential and reciprocal approximations, the accuracy class of
+// the SIMT kernel's exp and division), y = z s, y' = s (1 + z (1 - s)).
+__device__ inline void silu_pair(float2 z, float2& y, float2& d) {
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 t = __fmul2_rn(z, make_float2(-kLog2e, -kLog2e));
+    const float2 den = __fadd2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), one);
+    const float2 sg = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+    y = __fmul2_rn(z, sg);
+    const float2 om = __ffma2_rn(sg, make_float2(-1.f, -1.f), one);
+    d = __fmul2_rn(sg, __ffma2_rn(z, om, one));
+}
 
 // Scale 8 values by s, split into hi and lo FP16 parts, store them as one
 // 16-byte chunk of each tile (columns c .. c+7 of row r).
 __device__ inline void split_store8(unsigned char* thi, unsigned char* tlo, int r, int c,
                                     const float* v, float s) {
     uint32_t h[4], l[4];
+    const float2 s2 = make_float2(s, s);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float x0 = v[2 * i] * s, x1 = v[2 * i + 1] * s;
-        const __half2 hh = __floats2half2_rn(x0, x1);
-        const float2 hf = __half22float2(hh);
-        const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+        const float2 x = __fmul2_rn(make_float2(v[2 * i], v[2 * i + 1]), s2);
+        const __half2 hh = __float22half2_rn(x);
+        const float2 r2 = __ffma2_rn(__half22float2(hh), make_float2(-1.f, -1.f), x);  // exact
+        const __half2 ll = __float22half2_rn(r2);
         h[i] = *reinterpret_cast<const uint32_t*>(&hh);
         l[i] = *reinterpret_cast<const uint32_t*>(&ll);
     }
@@ -325,10 +351,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             ld_pending = false;
             if (s == 0) a_inv = rinv[row];
             if (tid == 0) {
-                const bool last = s == n_stages - 1;
-                issue_gemm3(tmem, s_base + Sl.a_hi, s_base + Sl.a_lo, s_base + Sl.b,
-                            s_base + Sl.b + kPart, (int)stage_K(s), last ? kNX : kW,
-                            last ? idesc_x : idesc_w, bar_mma);
+                const uint64_t dah = sdesc(s_base + Sl.a_hi), dal = sdesc(s_base + Sl.a_lo);
+                const uint64_t dbh = sdesc(s_base + Sl.b), dbl = sdesc(s_base + Sl.b + kPart);
+                if (s == 0)
+                    issue_gemm3<kK1, kW>(tmem, dah, dal, dbh, dbl, idesc_w, bar_mma);
+                else if (s == n_stages - 1)
+                    issue_gemm3<kW, kNX>(tmem, dah, dal, dbh, dbl, idesc_x, bar_mma);
+                else
+                    issue_gemm3<kW, kW>(tmem, dah, dal, dbh, dbl, idesc_w, bar_mma);
             }
             if (s == 0) {  // the next tile's pair data, while this tile's MMAs run
                 const int64_t gn = (tile + gridDim.x) * kM + row;
@@ -351,7 +381,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int l = s + 1;
                 const float* b = bias + (l - 1) * kW + cbeg;
                 float v[64];
-                float m = 0.f, e = 0.f;
+                float m = 0.f;
+                float2 e2 = make_float2(0.f, 0.f);
+                const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     uint32_t u[32];
@@ -361,22 +393,31 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 32; i += 4) {
                         const float4 b4 = *reinterpret_cast<const float4*>(b + 32 * q + i);
-                        const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+                        float2 y[2], d[2];
+                        silu_pair(__ffma2_rn(make_float2(__uint_as_float(u[i]), __uint_as_float(u[i + 1])),
+                                             sc2, make_float2(b4.x, b4.y)),
+                                  y[0], d[0]);
+                        silu_pair(__ffma2_rn(make_float2(__uint_as_float(u[i + 2]),
+                                                         __uint_as_float(u[i + 3])),
+                                             sc2, make_float2(b4.z, b4.w)),
+                                  y[1], d[1]);
+                        if (l == D) {  // output layer: E += w_o . y, seed g_D = w_o * silu'(z_D)
+                            const float4 w4 = *reinterpret_cast<const float4*>(wo + cbeg + 32 * q + i);
+                            const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+                            e2 = __ffma2_rn(wa, y[0], e2);
+                            e2 = __ffma2_rn(wb, y[1], e2);
+                            y[0] = __fmul2_rn(wa, d[0]);
+                            y[1] = __fmul2_rn(wb, d[1]);
+                        }
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float z = fmaf(__uint_as_float(u[i + k]), sc, bb[k]);
-                            const float sg = sigmoid_f32(z);
-                            const float y = z * sg;
-                            const float d = sg * fmaf(z, 1.f - sg, 1.f);
+                        for (int k = 0; k < 2; ++k) {
+                            v[32 * q + i + 2 * k] = y[k].x;
+                            v[32 * q + i + 2 * k + 1] = y[k].y;
+                            m = fmaxf(m, fmaxf(fabsf(y[k].x), fabsf(y[k].y)));
                             if (l < D) {
-                                v[32 * q + i + k] = y;
-                                dv[(i + k) >> 4][(i + k) & 15] = __float_as_uint(d);
-                            } else {  // output layer: E += w_o . y, seed g_D = w_o * silu'(z_D)
-                                const float w = wo[cbeg + 32 * q + i + k];
-                                e = fmaf(w, y, e);
-                                v[32 * q + i + k] = w * d;
+                                dv[(i + 2 * k) >> 4][(i + 2 * k) & 15] = __float_as_uint(d[k].x);
+                                dv[(i + 2 * k + 1) >> 4][(i + 2 * k + 1) & 15] = __float_as_uint(d[k].y);
                             }
-                            m = fmaxf(m, fabsf(v[32 * q + i + k]));
                         }
                     }
                     if (l < D) {
@@ -386,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 rmax[half * kM + row] = m;
+                const float e = e2.x + e2.y;
                 if (l == D && half == 1) epart[row] = e;
                 pair_sync(warp & 3);
                 m = fmaxf(rmax[row], rmax[kM + row]);
@@ -407,10 +449,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_wait32(u);
                     tmem_wait32(d);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float g = __uint_as_float(u[i]) * sc * __uint_as_float(d[i]);
-                        v[32 * q + i] = g;
-                        m = fmaxf(m, fabsf(g));
+                    for (int i = 0; i < 32; i += 2) {
+                        const float2 g = __fmul2_rn(
+                            __fmul2_rn(make_float2(__uint_as_float(u[i]), __uint_as_float(u[i + 1])),
+                                       make_float2(sc, sc)),
+                            make_float2(__uint_as_float(d[i]), __uint_as_float(d[i + 1])));
+                        v[32 * q + i] = g.x;
+                        v[32 * q + i + 1] = g.y;
+                        m = fmaxf(m, fmaxf(fabsf(g.x), fabsf(g.y)));
                     }
                 }
                 rmax[half * kM + row] = m;

@@ -43,6 +43,13 @@ __device__ inline uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
+// Descriptor of the tile `off` bytes (a multiple of 16) after the one that
+// `d` describes, same layout: the start address field (bits 0..13, in 16-byte
+// units) takes the offset.  Shared-memory addresses stay below 2^18 bytes, so
+// the field never carries into the next one; with `off` a compile-time
+// constant this is a single add.
+__device__ inline uint64_t sdesc_at(uint64_t d, uint32_t off) { return d + (uint64_t)(off >> 4); }
+
 // Instruction descriptor, kind::f16: BF16 A and B, FP32 D, K-major A and B.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -291,9 +298,32 @@ __device__ inline float2 unpack_bf16(uint32_t u) {
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // Issue the MMAs of one layer GEMM (K in steps of 16) and commit to `bar`.
-// A: [128 x K] tile, B: [N x K] tile, both swizzled K-major, `rows_b` rows.
+// A: [128 x K] tile, B: [N x K] tile, both swizzled K-major, ROWS_B rows.
+// With K and ROWS_B compile-time the loop unrolls into the MMAs alone, with
+// constant descriptor offsets: a single thread issues them, so per-MMA
+// address arithmetic would otherwise delay the tensor pipe.
+template <int K, int ROWS_B>
+__device__ inline void issue_gemm_k(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                    uint32_t bar) {
+    fence_after();
+#pragma unroll
+    for (int k = 0; k < K / 16; ++k)
+        mma_bf16(tmem_d, sdesc_at(da, (k >> 2) * (kM * 128) + (k & 3) * 32),
+                 sdesc_at(db, (k >> 2) * (ROWS_B * 128) + (k & 3) * 32), idesc, k > 0 ? 1u : 0u);
+    mma_commit(bar);
+}
+
+// Runtime shape: the network kernels' shapes take the unrolled form, others
+// (the single-tile GEMM check) the loop.
 __device__ inline void issue_gemm(uint32_t tmem_d, uint32_t a_base, uint32_t b_base, int K,
                                   int rows_b, uint32_t idesc, uint32_t bar) {
+    const uint64_t da = sdesc(a_base), db = sdesc(b_base);
+    if (K == 128 && rows_b == 128) return issue_gemm_k<128, 128>(tmem_d, da, db, idesc, bar);
+    if (K == 64 && rows_b == 128) return issue_gemm_k<64, 128>(tmem_d, da, db, idesc, bar);
+    if (K == 128 && rows_b == 16) return issue_gemm_k<128, 16>(tmem_d, da, db, idesc, bar);
+    if (K == 256 && rows_b == 256) return issue_gemm_k<256, 256>(tmem_d, da, db, idesc, bar);
+    if (K == 64 && rows_b == 256) return issue_gemm_k<64, 256>(tmem_d, da, db, idesc, bar);
+    if (K == 256 && rows_b == 16) return issue_gemm_k<256, 16>(tmem_d, da, db, idesc, bar);
     fence_after();
     for (int k = 0; k < K / 16; ++k) {
         const uint32_t koff_a = (uint32_t)(k >> 2) * (kM * 128) + (uint32_t)(k & 3) * 32;
