@@ -45,8 +45,8 @@ WIDTH, DEPTH = 128, 3
 #   python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-serving
 #                   --train-steps 0 --drift-steps 0 [--no-paper-workload]
 # None would mark a kernel changed since its capture.
-NCU_DRAM_BYTES = {"k_bead_pairs": 1.855e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 3.588e6,
-                  "k_nn_tc256": 2.458e6, "k_nn_f16x3": None}
+NCU_DRAM_BYTES = {"k_bead_pairs": 1.855e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 2.052e6,
+                  "k_nn_tc256": None, "k_nn_f16x3": 2.211e6}
 
 
 def parse():
@@ -520,9 +520,9 @@ def main():
             durs.append((a, b))
         torch.cuda.synchronize()
         d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
-        # tensor-core work actually issued per 128-pair tile: layer-1 K padded to 64,
-        # reverse output N padded to 16
-        tc_flops = 2.0 * 128 * (128 * 64 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
+        # tensor-core work actually issued per 128-pair tile: layer 1 one K step of
+        # 16 (10 features), the input gradient's N padded to 16
+        tc_flops = 2.0 * 128 * (128 * 16 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
         flops = tc_flops / 128 * n_pairs["nn_bf16"]
         achieved = flops / (d_ms * 1e-3) / 1e12
         peak = pk.get("bf16_tflops_sustained", 1700.0)
@@ -552,7 +552,7 @@ def main():
         d_ms = kernel_ms(systems["nn_f16x3"], "f16x3")
         # three FP16 products per layer GEMM (hi.hi, hi.lo, lo.hi), the same
         # padded shapes as the BF16 kernel
-        tc_flops = 3 * 2.0 * 128 * (128 * 64 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
+        tc_flops = 3 * 2.0 * 128 * (128 * 16 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
         flops = tc_flops / 128 * n_pairs["nn_f16x3"]
         achieved = flops / (d_ms * 1e-3) / 1e12
         peak = pk.get("bf16_tflops_sustained", 1700.0)
@@ -656,7 +656,7 @@ def main():
         kb.record(stream)
         torch.cuda.synchronize()
         k256 = ka.elapsed_time(kb) / 10
-        tc256 = 2.0 * 128 * (256 * 64 + 4 * 256 * 256 + 256 * 16) / 128 * n_pairs["nn_bf16"]
+        tc256 = 2.0 * 128 * (256 * 16 + 4 * 256 * 256 + 256 * 16) / 128 * n_pairs["nn_bf16"]
         width256 = {"ms_per_md_step": ms256, "md_steps_per_s": 1e3 / ms256,
                     "speedup_vs_beads": (statistics.mean(per_path_ms["beads"]) / ms256)
                     if "beads" in per_path_ms else None,

@@ -17,7 +17,8 @@
 // work (SiLU from exp and a reciprocal, silu', products with silu') is plain
 // FP32, as in the SIMT kernel.
 //   * Shared memory: A_hi, A_lo [128 x 128] FP16 (K-major, 128-byte swizzle;
-//     the first 64-column atom also holds the layer-1 features), one weight
+//     the first 16 columns also hold the layer-1 features, so layer 1 is one
+//     K step), one weight
 //     buffer with B_hi and B_lo of one stage, streamed from a pre-swizzled
 //     global image by bulk asynchronous copies completing on an mbarrier; the
 //     copy for stage s + 1 is issued as soon as stage s's MMAs retire, so it
@@ -311,8 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool valid = gp < n_total;
         const PairGeom geo = pair_geometry<SYSTEM>(src, raw);
         if (half == 0) {
-            // standardised features (10 of the first 64 columns; the zero
-            // columns are rewritten because the previous tile used them)
+            // standardised features in the first 16 columns (10 used), the
+            // only ones layer 1's single K step reads
             float x[kIn];
             raw_features(geo, x);
             float xr[16];
@@ -327,12 +328,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             rinv[row] = inv;
             split_store8(Ahi, Alo, row, 0, xr, s);
             split_store8(Ahi, Alo, row, 8, xr + 8, s);
-#pragma unroll
-            for (int q = 2; q < 8; ++q) {
-                const uint32_t o = sw128_offset(kM, row, 8 * q);
-                *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(0, 0, 0, 0);
-                *reinterpret_cast<uint4*>(Alo + o) = make_uint4(0, 0, 0, 0);
-            }
         }
         float E = 0.f;
         float a_inv = 1.f;  // 1/s_A of this thread's row of the current A tile
@@ -353,8 +348,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (tid == 0) {
                 const uint64_t dah = sdesc(s_base + Sl.a_hi), dal = sdesc(s_base + Sl.a_lo);
                 const uint64_t dbh = sdesc(s_base + Sl.b), dbl = sdesc(s_base + Sl.b + kPart);
-                if (s == 0)
-                    issue_gemm3<kK1, kW>(tmem, dah, dal, dbh, dbl, idesc_w, bar_mma);
+                if (s == 0)  // the features fill the first 16 columns: one K step
+                    issue_gemm3<16, kW>(tmem, dah, dal, dbh, dbl, idesc_w, bar_mma);
                 else if (s == n_stages - 1)
                     issue_gemm3<kW, kNX>(tmem, dah, dal, dbh, dbl, idesc_x, bar_mma);
                 else

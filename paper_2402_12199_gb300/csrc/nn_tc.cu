@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int l = 1; l <= D && ok; ++l) {
             const uint32_t dcol = (uint32_t)((l - 1) * kW);
             if (l == 1)
-                TC_STAGE(tmem + dcol, s_base + Ly.x, s_base + Ly.w1f, kK1, kW, idesc_w);
+                TC_STAGE(tmem + dcol, s_base + Ly.x, s_base + Ly.w1f, 16, kW, idesc_w);
             else
                 TC_STAGE(tmem + dcol, s_base + Ly.h, s_base + Ly.wf[l], kW, kW, idesc_w);
             if (!ok) break;

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (tid == 0) {
                 const bool last = s == n_stages - 1;
                 issue_gemm(tmem, s == 0 ? s_base + Ly.s_x : s_base + Ly.s_h, s_base + Ly.s_b,
-                           s == 0 ? kK1 : kW, last ? kNX : kW, last ? idesc_x : idesc_w, bar_mma);
+                           s == 0 ? 16 : kW, last ? kNX : kW, last ? idesc_x : idesc_w, bar_mma);
             }
             got = mbar_wait(bar_mma, ph_mma, kWaitCycles);
             ph_mma ^= 1u;

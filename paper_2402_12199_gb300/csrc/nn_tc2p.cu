@@ -9,7 +9,7 @@
 // one waits for its MMAs, the other runs its epilogue.
 //   * Shared memory: all weights once (BF16, K-major, 128-byte swizzle, as in
 //     nn_tc.cu) plus, per warpgroup, one 128 x 128 activation tile whose first
-//     64-column atom also serves as the 64-column feature tile of layer 1.
+//     16 columns also hold the layer-1 features (layer 1 is one K step).
 //   * Tensor memory: warpgroup g owns columns 256 g .. 256 g + 255: the
 //     accumulator of every stage (128 columns) and silu'(z_1), silu'(z_2) as
 //     packed BF16 pairs (64 columns each), written by the forward epilogue so
@@ -159,23 +159,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool valid = gp < n_total;
         const PairGeom geo = pair_geometry<SYSTEM>(src, raw);
         {
-            // features into the first atom of the activation tile (64 columns,
-            // 10 used): the zero columns are rewritten every tile because the
-            // previous tile's activations occupied them
+            // features in the first 16 columns of the activation tile (10
+            // used), the only ones layer 1's single K step reads
             float x[kIn];
             raw_features(geo, x);
             float xr[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) xr[k] = k < kIn ? (x[k] - mu[k]) * isd[k] : 0.f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                uint4 w = make_uint4(0, 0, 0, 0);
-                if (q < 2) {
-                    w.x = pack_bf16(xr[8 * q + 0], xr[8 * q + 1]);
-                    w.y = pack_bf16(xr[8 * q + 2], xr[8 * q + 3]);
-                    w.z = pack_bf16(xr[8 * q + 4], xr[8 * q + 5]);
-                    w.w = pack_bf16(xr[8 * q + 6], xr[8 * q + 7]);
-                }
+            for (int q = 0; q < 2; ++q) {
+                uint4 w;
+                w.x = pack_bf16(xr[8 * q + 0], xr[8 * q + 1]);
+                w.y = pack_bf16(xr[8 * q + 2], xr[8 * q + 3]);
+                w.z = pack_bf16(xr[8 * q + 4], xr[8 * q + 5]);
+                w.w = pack_bf16(xr[8 * q + 6], xr[8 * q + 7]);
                 *reinterpret_cast<uint4*>(Ht + sw128_offset(kM, row, 8 * q)) = w;
             }
         }
@@ -183,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- forward
         for (int l = 1; l <= D && ok; ++l) {
             if (l == 1)
-                stage(h_addr, s_base + Ly.w1f, kK1, kW, idesc_w);
+                stage(h_addr, s_base + Ly.w1f, 16, kW, idesc_w);  // features: columns 0..15
             else
                 stage(h_addr, s_base + Ly.wf[l], kW, kW, idesc_w);
             if (!ok) break;

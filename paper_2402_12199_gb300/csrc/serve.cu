@@ -327,6 +327,8 @@ rb_status rb_submit(rb_server* sv, const rb_system_desc* desc, const float* pos,
         return fail(RB_EINVAL, "null argument");
     if (path != RB_PATH_BEADS && path != RB_PATH_NN) return fail(RB_EINVAL, "unknown path");
     if (path == RB_PATH_NN && !sv->mlp) return fail(RB_EINVAL, "server has no network");
+    if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
+        return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
     const int64_t fp = rb_system_footprint(desc);
     if (fp < 0) return fail(RB_EINVAL, "invalid system description");

@@ -319,10 +319,11 @@ __device__ inline void issue_gemm(uint32_t tmem_d, uint32_t a_base, uint32_t b_b
                                   int rows_b, uint32_t idesc, uint32_t bar) {
     const uint64_t da = sdesc(a_base), db = sdesc(b_base);
     if (K == 128 && rows_b == 128) return issue_gemm_k<128, 128>(tmem_d, da, db, idesc, bar);
+    if (K == 16 && rows_b == 128) return issue_gemm_k<16, 128>(tmem_d, da, db, idesc, bar);
     if (K == 64 && rows_b == 128) return issue_gemm_k<64, 128>(tmem_d, da, db, idesc, bar);
     if (K == 128 && rows_b == 16) return issue_gemm_k<128, 16>(tmem_d, da, db, idesc, bar);
     if (K == 256 && rows_b == 256) return issue_gemm_k<256, 256>(tmem_d, da, db, idesc, bar);
-    if (K == 64 && rows_b == 256) return issue_gemm_k<64, 256>(tmem_d, da, db, idesc, bar);
+    if (K == 16 && rows_b == 256) return issue_gemm_k<16, 256>(tmem_d, da, db, idesc, bar);
     if (K == 256 && rows_b == 16) return issue_gemm_k<256, 16>(tmem_d, da, db, idesc, bar);
     fence_after();
     for (int k = 0; k < K / 16; ++k) {
