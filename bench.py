@@ -45,8 +45,8 @@ WIDTH, DEPTH = 128, 3
 #   python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-serving
 #                   --train-steps 0 --drift-steps 0 [--no-paper-workload]
 # None would mark a kernel changed since its capture.
-NCU_DRAM_BYTES = {"k_bead_pairs": 1.855e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 2.052e6,
-                  "k_nn_tc256": None, "k_nn_f16x3": 2.211e6}
+NCU_DRAM_BYTES = {"k_bead_pairs": 1.864e6, "k_nn_f32": None, "k_nn_tc2p": 2.054e6,
+                  "k_nn_tc256": None, "k_nn_f16x3": 2.220e6}
 
 
 def parse():
@@ -907,6 +907,46 @@ def main():
         for p in paths:
             if p.startswith("nn"):
                 model_error[p] = train_net.force_error(probe, mlp, p.split("_")[1])
+        # the pair-symmetrised evaluation (each pair's energy averaged over both
+        # choices of reference body): its error against the bead sum, how far
+        # it is from the plain evaluation (the network's i <-> j asymmetry), and
+        # its MD step time, outside the timed step
+        sym_prec = "f16x3" if "nn_f16x3" in paths else "fp32"
+        plain = probe.forces_nn(mlp, sym_prec)
+        plain_F = plain["force"][:, :3].clone()
+        mlp.set_pair_symmetrised(True)
+        try:
+            err_sym = train_net.force_error(probe, mlp, sym_prec)
+            symF = probe.forces_nn(mlp, sym_prec)["force"][:, :3]
+            probe.sync()
+            asym = float(torch.linalg.norm(symF - plain_F) / torch.linalg.norm(plain_F))
+            sym_ms = {}
+            for prec in sorted({sym_prec, "bf16"}):
+                ss = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
+                ss.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+                ss.set_nn_fallback(rho_fallback)
+                ss.forces_nn(mlp, prec)
+                for _ in range(3):
+                    ss.step(1, DT, path=api.RB_PATH_NN, mlp=mlp, precision=prec)
+                evs = []
+                for _ in range(20):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    ss.step(1, DT, path=api.RB_PATH_NN, mlp=mlp, precision=prec)
+                    b.record(stream)
+                    evs.append((a, b))
+                torch.cuda.synchronize()
+                ss.sync()
+                sym_ms[prec] = statistics.mean(x.elapsed_time(y) for x, y in evs)
+                del ss
+            model_error["pair_symmetrised"] = {
+                "precision": sym_prec, **err_sym, "asymmetry_e_F_vs_plain": asym,
+                "ms_per_md_step": sym_ms,
+                "note": "energy of every pair averaged over both choices of reference body "
+                        "(two network passes); not in the timed step"}
+        finally:
+            mlp.set_pair_symmetrised(False)
         del probe
     serving = None
     if not args.no_serving and world == 1:

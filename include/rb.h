@@ -351,6 +351,19 @@ rb_status rb_mlp_set_symmetry(rb_mlp* mlp, const float* quats_host, int32_t n, i
  * it; RB_EINVAL unless r_off = 0 or r_off > r_on >= 0. */
 rb_status rb_mlp_set_cutoff(rb_mlp* mlp, float r_on, float r_off);
 
+/* Pair-symmetrised evaluation (on != 0).  The network describes a pair from
+ * the frame of one body, so its energy depends on which body of the pair is
+ * the reference; the library evaluates each unordered pair i < j with i as
+ * the reference.  With this switch on, the system-level calls (rb_forces_nn,
+ * rb_eval_pairs, rb_step, the server) use instead
+ * E_s(i, j) = (E(x_ij) + E(x_ji)) / 2, the network evaluated with each body
+ * as the reference and averaged: independent of how the bodies are labelled,
+ * with forces and torques its exact gradients, at twice the network work.
+ * A system's first such evaluation allocates three more pair arrays
+ * (48 bytes per pair of its capacity, outside rb_system_footprint).
+ * rb_nn_pairs and training evaluate the network as it is (one reference). */
+rb_status rb_mlp_set_pair_symmetrised(rb_mlp* mlp, int32_t on);
+
 /* The canonical representatives themselves (device arrays, in place): cfg
  * n x 8 as rb_nn_pairs' input; labels n x 12 as its output (nullable), mapped
  * as the forces and torques.  Runs on the network's stream; a network without

@@ -196,6 +196,18 @@ def forces_nn(p: dict, pos, quat, box, pairs):
     return F, tau, float(r["E"].sum()), r["E"]
 
 
+def forces_nn_symmetrised(p: dict, pos, quat, box, pairs):
+    """Pair energy averaged over both choices of reference body,
+    E_s(i, j) = (E(x_ij) + E(x_ji)) / 2, so that it does not depend on how
+    the bodies are labelled; forces and torques are its gradients, i.e. the
+    mean of forces_nn over the listed pairs and over the same pairs with the
+    roles swapped.  Returns F, tau, E_total, per-pair E_s."""
+    pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    F1, T1, E1, e1 = forces_nn(p, pos, quat, box, pairs)
+    F2, T2, E2, e2 = forces_nn(p, pos, quat, box, pairs[:, ::-1])
+    return 0.5 * (F1 + F2), 0.5 * (T1 + T2), 0.5 * (E1 + E2), 0.5 * (e1 + e2)
+
+
 # ------------------------------------------------------------------ training
 
 def predict_labels(p: dict, s, q_rel, create_graph: bool = False):

@@ -328,6 +328,11 @@ class MLP:
         r_off (r_off = 0 removes it)."""
         check(load().rb_mlp_set_cutoff(self._h, float(r_on), float(r_off)))
 
+    def set_pair_symmetrised(self, on: bool = True):
+        """rb_mlp_set_pair_symmetrised: system-level evaluations use the energy
+        averaged over both choices of reference body of every pair."""
+        check(load().rb_mlp_set_pair_symmetrised(self._h, int(bool(on))))
+
     def canonical(self, cfg: torch.Tensor, labels: torch.Tensor = None):
         """rb_nn_canonical in place on (n, 8) configurations [and (n, 12) labels]."""
         _dev(cfg, 8)

@@ -479,27 +479,59 @@ static int sm_count() {
     return n > 0 ? n : 1;
 }
 
-rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
-    RB_TRY(check_mlp(m));
-    if (precision == RB_BF16) return nn_tc_system_async(s, m);
-    if (precision == RB_F16X3) return nn_f16x3_system_async(s, m);
+// One network pass over the system's pair list (swap: second body as the
+// reference, into the secondary arrays).
+static rb_status nn_system_pass(rb_system* s, const rb_mlp* m, int precision, bool swap) {
+    if (precision == RB_BF16) return nn_tc_system_async(s, m, swap);
+    if (precision == RB_F16X3) return nn_f16x3_system_async(s, m, swap);
     if (precision != RB_FP32) return fail(RB_EINVAL, "unknown precision");
     PairSrc src{};
     set_symmetry(src, m);
-    src.pairs = s->pl.pairs;
-    src.n_pairs_ptr = s->pl.n_pairs;
-    src.pos = s->pos;
-    src.quat = s->quat;
-    src.L = make_float3(s->box[0], s->box[1], s->box[2]);
-    src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
-    src.Rc2 = s->Rc * s->Rc;
     PairDst dst{};
     set_cutoff(dst, m);
-    dst.F = s->pair_F;
-    dst.ti = s->pair_ti;
-    dst.tj = s->pair_tj;
-    RB_TRY(set_fallback(dst, s));
+    RB_TRY(system_pass_io(s, swap, src, dst));
     return dispatch_f32<true>(m, s->stream, s->num_sms, src, dst);
+}
+
+// Pair-symmetrised energy E_s = (E(x_ij) + E(x_ji)) / 2 from the two passes.
+// The swapped pass wrote, per pair, (F_i, E_ji) with j as the reference, the
+// torque on j and the torque on i; the gradients of E_s are the averages
+//   F_j = (F_j - F'_i) / 2,  tau_i = (tau_i + tau'_other) / 2,
+//   tau_j = (tau_j + tau'_ref) / 2,  E = (E_ij + E_ji) / 2.
+__global__ void k_pair_sym_combine(const int* __restrict__ n_pairs, float4* __restrict__ F,
+                                   float4* __restrict__ ti, float4* __restrict__ tj,
+                                   const float4* __restrict__ F2, const float4* __restrict__ ti2,
+                                   const float4* __restrict__ tj2) {
+    pdl_wait();
+    const int n = *n_pairs;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const float4 a = F[p], b = F2[p];
+        F[p] = make_float4(0.5f * (a.x - b.x), 0.5f * (a.y - b.y), 0.5f * (a.z - b.z), 0.5f * (a.w + b.w));
+        const float4 ci = ti[p], cj = tj[p], r = ti2[p], o = tj2[p];
+        ti[p] = make_float4(0.5f * (ci.x + o.x), 0.5f * (ci.y + o.y), 0.5f * (ci.z + o.z), 0.f);
+        tj[p] = make_float4(0.5f * (cj.x + r.x), 0.5f * (cj.y + r.y), 0.5f * (cj.z + r.z), 0.f);
+    }
+}
+
+rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
+    RB_TRY(check_mlp(m));
+    RB_TRY(nn_system_pass(s, m, precision, false));
+    if (!m->pair_sym) return RB_OK;
+    RB_TRY(nn_system_pass(s, m, precision, true));
+    RB_CUDA(launch_pdl(k_pair_sym_combine, s->num_sms * 4, 256, 0, s->stream,
+                       (const int*)s->pl.n_pairs, s->pair_F, s->pair_ti, s->pair_tj,
+                       (const float4*)s->pair_F2, (const float4*)s->pair_ti2,
+                       (const float4*)s->pair_tj2));
+    return RB_OK;
+}
+
+rb_status ensure_pair_sym_arrays(rb_system* s, const rb_mlp* m) {
+    if (!m || !m->pair_sym || s->pair_F2) return RB_OK;
+    const size_t b = sizeof(float4) * (size_t)s->pl.cap_pairs;
+    RB_CUDA(cudaMalloc(&s->pair_F2, b));
+    RB_CUDA(cudaMalloc(&s->pair_ti2, b));
+    RB_CUDA(cudaMalloc(&s->pair_tj2, b));
+    return RB_OK;
 }
 
 }  // namespace rb
@@ -566,6 +598,13 @@ rb_status rb_mlp_set_cutoff(rb_mlp* m, float r_on, float r_off) {
     m->sw_on = r_off > 0.f ? r_on : 0.f;
     m->sw_off = r_off;
     m->version++;  // captured step graphs hold the old values
+    return RB_OK;
+}
+
+rb_status rb_mlp_set_pair_symmetrised(rb_mlp* m, int32_t on) {
+    if (!m) return fail(RB_EINVAL, "null network");
+    m->pair_sym = on ? 1 : 0;
+    m->version++;  // captured step graphs hold the old evaluation
     return RB_OK;
 }
 

@@ -61,6 +61,9 @@ struct PairSrc {
     int n_sym;
     int sym_inv;
     int sym_cube;
+    // system mode: evaluate every listed pair (i, j) with j as the reference
+    // body (the second half of the pair-symmetrised energy)
+    int swap;
 };
 
 struct PairDst {
@@ -226,11 +229,12 @@ __device__ inline PairRaw fetch_pair(const PairSrc& src, int64_t gp, bool valid)
     r.a = r.b = r.c = r.d = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
         if (SYSTEM) {
-            const int2 ij = src.pairs[gp];
-            r.a = src.pos[ij.x];
-            r.b = src.pos[ij.y];
-            r.c = src.quat[ij.x];
-            r.d = src.quat[ij.y];
+            const int2 p = src.pairs[gp];
+            const int i = src.swap ? p.y : p.x, j = src.swap ? p.x : p.y;
+            r.a = src.pos[i];
+            r.b = src.pos[j];
+            r.c = src.quat[i];
+            r.d = src.quat[j];
         } else {
             r.a = src.cfg[2 * gp];
             r.b = src.cfg[2 * gp + 1];
@@ -385,6 +389,35 @@ inline rb_status set_fallback(PairDst& dst, rb_system* s) {
     return RB_OK;
 }
 
+// Pair source and destination of a system-mode network pass.  swap: every
+// listed pair is evaluated with its second body as the reference, into the
+// secondary pair arrays, without bead-fallback listing (the first pass lists
+// the pairs).
+inline rb_status system_pass_io(rb_system* s, bool swap, PairSrc& src, PairDst& dst) {
+    src.pairs = s->pl.pairs;
+    src.n_pairs_ptr = s->pl.n_pairs;
+    src.pos = s->pos;
+    src.quat = s->quat;
+    src.L = make_float3(s->box[0], s->box[1], s->box[2]);
+    src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
+    src.Rc2 = s->Rc * s->Rc;
+    src.swap = swap ? 1 : 0;
+    if (swap) {
+        if (!s->pair_F2) return fail(RB_EINVAL, "pair-symmetrised network: pair arrays not prepared");
+        dst.F = s->pair_F2;
+        dst.ti = s->pair_ti2;
+        dst.tj = s->pair_tj2;
+        dst.fb_list = nullptr;
+        dst.fb_count = nullptr;
+        dst.fb_rho2 = 0.f;
+        return RB_OK;
+    }
+    dst.F = s->pair_F;
+    dst.ti = s->pair_ti;
+    dst.tj = s->pair_tj;
+    return set_fallback(dst, s);
+}
+
 // The network's smooth energy cutoff into a pair destination.
 inline void set_cutoff(PairDst& dst, const rb_mlp* m) {
     dst.sw_on = m->sw_on;
@@ -408,10 +441,10 @@ rb_status nn_tc_prepare(rb_mlp* m);
 // nn_f16x3.cu (FP32 accuracy from split FP16 operands on the tensor cores)
 bool nn_f16x3_supported(const rb_mlp* m);
 rb_status nn_f16x3_prepare(rb_mlp* m);
-rb_status nn_f16x3_system_async(rb_system* s, const rb_mlp* m);
+rb_status nn_f16x3_system_async(rb_system* s, const rb_mlp* m, bool swap);
 rb_status nn_f16x3_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
                                float4* grad);
-rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m);
+rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m, bool swap);
 rb_status nn_tc_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,
                             float4* grad);
 

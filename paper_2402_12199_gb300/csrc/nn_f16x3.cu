@@ -529,22 +529,12 @@ static rb_status launch_f16x3(const rb_mlp* m, cudaStream_t stream, int grid, co
     return RB_OK;
 }
 
-rb_status nn_f16x3_system_async(rb_system* s, const rb_mlp* m) {
+rb_status nn_f16x3_system_async(rb_system* s, const rb_mlp* m, bool swap) {
     PairSrc src{};
     set_symmetry(src, m);
-    src.pairs = s->pl.pairs;
-    src.n_pairs_ptr = s->pl.n_pairs;
-    src.pos = s->pos;
-    src.quat = s->quat;
-    src.L = make_float3(s->box[0], s->box[1], s->box[2]);
-    src.invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
-    src.Rc2 = s->Rc * s->Rc;
     PairDst dst{};
     set_cutoff(dst, m);
-    dst.F = s->pair_F;
-    dst.ti = s->pair_ti;
-    dst.tj = s->pair_tj;
-    RB_TRY(set_fallback(dst, s));
+    RB_TRY(system_pass_io(s, swap, src, dst));
     return launch_f16x3<true>(m, s->stream, s->num_sms, src, dst, s->status_dev);
 }
 

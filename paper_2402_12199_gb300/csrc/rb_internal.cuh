@@ -189,6 +189,7 @@ struct rb_mlp {
     int n_sym = 0, sym_inv = 0;
     int sym_cube = 0;              // the group is the cube's: closed-form choice
     float sw_on = 0.f, sw_off = 0.f;  // smooth cutoff of the energy (sw_off = 0: none)
+    int pair_sym = 0;  // pair energy averaged over both choices of reference body
 };
 
 struct rb_system {
@@ -219,6 +220,9 @@ struct rb_system {
     rb::PairList pl;
     // per-pair results: (F_j, E), (tau_i, 0), (tau_j, 0)
     float4 *pair_F = nullptr, *pair_ti = nullptr, *pair_tj = nullptr;
+    // outputs of the reference-swapped pass of a pair-symmetrised network
+    // (allocated on first use, cap_pairs each)
+    float4 *pair_F2 = nullptr, *pair_ti2 = nullptr, *pair_tj2 = nullptr;
     // energies / status
     double* red_partials = nullptr;  // reduction scratch
     int red_blocks = 0;
@@ -265,6 +269,9 @@ __global__ void k_zero_count(int* count);  // *count = 0 after pdl_wait (system.
 rb_status bead_fallback_async(rb_system* s);  // bead sum for pairs with rho < nn_fallback_rho
 // nn.cu
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision);
+// the secondary pair arrays a pair-symmetrised network needs (no-op otherwise);
+// call outside stream capture
+rb_status ensure_pair_sym_arrays(rb_system* s, const rb_mlp* m);
 // fnet.cu (per-component cylinder networks)
 rb_status fnet_pairs_system_async(rb_system* s, const rb_fnet* f);
 rb_status check_fnet(const rb_fnet* f);

@@ -993,7 +993,8 @@ rb_status rb_destroy_system(rb_system* s) {
                     s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
                     s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev,
                     s->fallback_count, s->fb_list, s->pos_ref, s->rebuild_flag, s->nh,
-                    s->ke_part, s->image, s->ref_pos, s->ref_quat, s->ref_image, s->ana_part};
+                    s->ke_part, s->image, s->ref_pos, s->ref_quat, s->ref_image, s->ana_part,
+                    s->pair_F2, s->pair_ti2, s->pair_tj2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -1189,6 +1190,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
                        float* torque, double* energy, double* virial9) {
     if (!s) return fail(RB_EINVAL, "null system");
     RB_TRY(check_mlp(m));
+    RB_TRY(ensure_pair_sym_arrays(s, m));
     RB_TRY(build_pairs_async(s, false, false));
     RB_TRY(nn_pairs_system_async(s, m, precision));
     RB_TRY(bead_fallback_async(s));
@@ -1221,6 +1223,7 @@ rb_status rb_eval_pairs(rb_system* s, int32_t path, const rb_mlp* m, int32_t pre
     if (path == RB_PATH_BEADS) return bead_pairs_async(s);
     if (path == RB_PATH_NN) {
         RB_TRY(check_mlp(m));
+        RB_TRY(ensure_pair_sym_arrays(s, m));
         return nn_pairs_system_async(s, m, precision);
     }
     return fail(RB_EINVAL, "unknown path");
@@ -1233,6 +1236,7 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
     if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
         return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
+    if (path == RB_PATH_NN) RB_TRY(ensure_pair_sym_arrays(s, static_cast<const rb_mlp*>(m)));
     const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
                       s->forces_precision == precision &&
                       (!m || s->forces_mlp_version == version);
