@@ -45,7 +45,7 @@ WIDTH, DEPTH = 128, 3
 #   python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-serving
 #                   --train-steps 0 --drift-steps 0 [--no-paper-workload]
 # None would mark a kernel changed since its capture.
-NCU_DRAM_BYTES = {"k_bead_pairs": 1.864e6, "k_nn_f32": None, "k_nn_tc2p": 2.054e6,
+NCU_DRAM_BYTES = {"k_bead_pairs": 1.864e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 2.054e6,
                   "k_nn_tc256": None, "k_nn_f16x3": 2.220e6}
 
 
@@ -873,25 +873,37 @@ def main():
     # ---- end to end through the public API with host buffers: every step
     # copies each path's inputs from page-locked host memory, runs the step
     # and reads the new state back into page-locked host memory; one
-    # synchronisation per step (all paths share the stream)
-    # one page-locked block per direction (pos | quat | vel | angmom), so the
-    # state moves in one copy each way
+    # synchronisation per step.  Each path is its own system on its own
+    # stream (independent systems, as a user would run them), so one path's
+    # copies and list rebuild overlap another's pair kernel.  One page-locked
+    # block per direction (pos | quat | vel | angmom): one copy each way.
     keys4 = ("pos", "quat", "vel", "angmom")
     blk_in = torch.from_numpy(np.stack([st[k] for k in keys4])).pin_memory()
     pinned = {k: blk_in[i] for i, k in enumerate(keys4)}
     blk_out = {p: torch.empty((4, N_BODIES, 4), dtype=torch.float32).pin_memory() for p in systems}
     outs = {p: {k: blk_out[p][i] for i, k in enumerate(keys4)} for p in systems}
+    e2e_sys = {}
+    for p in systems:
+        se = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin, stream=torch.cuda.Stream())
+        se.set_state(*(dev_state[k] for k in keys4))
+        if p.startswith("nn"):
+            se.set_nn_fallback(rho_fallback)
+        se.step(1, DT, **pcfg(p))  # forces and the step graph, before the timed loop
+        e2e_sys[p] = se
     e2e_steps = max(3, min(args.steps, 50))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for p, s in systems.items():
-            s.set_state(*(pinned[k] for k in ("pos", "quat", "vel", "angmom")))
-            s.step(1, DT, **pcfg(p))
-            s.get_state(to_host=True, out=outs[p], sync=False)
+        for p, se in e2e_sys.items():
+            se.set_state(*(pinned[k] for k in keys4))
+            se.step(1, DT, **pcfg(p))
+            se.get_state(to_host=True, out=outs[p], sync=False)
         torch.cuda.synchronize()
     e2e_t = (time.perf_counter() - t0) / e2e_steps
     e2e_ok = all(bool(torch.isfinite(outs[p]["pos"]).all()) for p in systems)
+    for se in e2e_sys.values():
+        se.sync()
+    del e2e_sys
     h2d = len(systems) * 4 * N_BODIES * 16
     d2h = len(systems) * 4 * N_BODIES * 16
 
@@ -1007,7 +1019,8 @@ def main():
                     "results_finite": e2e_ok,
                     "note": "per step and path: state in from page-locked host memory (one "
                             "block, one copy), one MD step, new state out to page-locked host "
-                            "memory (one copy); one host synchronisation per step"},
+                            "memory (one copy); one host synchronisation per step; each path "
+                            "a system on its own stream"},
             # per MD step and path: integrate (with the skin check), cell assign,
             # pair build, two scan kernels, emit, finish, flag clear, pair kernel,
             # reduce; plus the bead fallback kernel on the network paths
