@@ -299,19 +299,23 @@ __device__ inline void load_columns(const float4* __restrict__ tmpl, const BeadC
 //   P = |b|^2 - 2 (b_x x + b_y y),   |b|^2 - 2 b.d = P - 2 b_z z_m,
 // i.e. (2 + C) packed FMAs per C distances of a slot pair instead of 3 C.
 // One warp vote per column; result as in warp_finish.
-template <int NP, int C, int POT = 0>
-__device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const float4* sT,
-                                           const float4* sC, const float* sTh,
-                                           const BeadCols& cols, int n_beads, const BeadPot& pot,
-                                           int lane, float (&v)[7]) {
-    float bx[2 * NP], by[2 * NP], bz[2 * NP];
-    float2 Bx[NP], By[NP], Bz[NP], BB[NP];
-    slots_setup<NP>(s, Rr, sT, n_beads, lane, bx, by, bz, Bx, By, Bz, BB);
-    LJAcc<NP> a;
-    a.zero();
+// The column loop of bead_pair_warp_cols: for every column of the fixed
+// template, the expanded distance test of all slots against its C beads
+// (running minimum per bead, one vote), and the exact terms on a hit.
+// ZINT: the column z values are -2, -1, 0, 1, 2 (see bead_pair_warp_cols).
+template <int NP, int C, int POT, bool ZINT>
+__device__ inline void cols_scan(const float4* sC, const float* sTh, const BeadCols& cols,
+                                 const BeadPot& pot, const float2 (&Bx)[NP], const float2 (&By)[NP],
+                                 const float2 (&Bz)[NP], const float2 (&BB)[NP], LJAcc<NP>& a) {
     float2 mz[C];  // -2 z_m, duplicated
 #pragma unroll
     for (int m = 0; m < C; ++m) mz[m] = make_float2(-2.f * cols.z[m], -2.f * cols.z[m]);
+    float2 U[NP], W[NP];  // ZINT: 2 B_z and 4 B_z (exact)
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        U[q] = __fmul2_rn(Bz[q], make_float2(2.f, 2.f));
+        W[q] = __fmul2_rn(Bz[q], make_float2(4.f, 4.f));
+    }
     for (int c = 0; c < cols.n_cols; ++c) {
         const float4 cxy = sC[c];
         const float2 mx = make_float2(cxy.x, cxy.y), my = make_float2(cxy.z, cxy.w);
@@ -324,10 +328,21 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             const float2 P = __ffma2_rn(By[q], my, __ffma2_rn(Bx[q], mx, BB[q]));
+            if constexpr (ZINT) {
+                float2 t[5];
+                t[0] = __fadd2_rn(P, W[q]);
+                t[1] = __fadd2_rn(P, U[q]);
+                t[2] = P;
+                t[3] = __fadd2_rn(P, make_float2(-U[q].x, -U[q].y));
+                t[4] = __fadd2_rn(P, make_float2(-W[q].x, -W[q].y));
 #pragma unroll
-            for (int m = 0; m < C; ++m) {
-                const float2 t = __ffma2_rn(Bz[q], mz[m], P);
-                mn[m] = fmin3(mn[m], t.x, t.y);
+                for (int m = 0; m < C; ++m) mn[m] = fmin3(mn[m], t[m].x, t[m].y);
+            } else {
+#pragma unroll
+                for (int m = 0; m < C; ++m) {
+                    const float2 t = __ffma2_rn(Bz[q], mz[m], P);
+                    mn[m] = fmin3(mn[m], t.x, t.y);
+                }
             }
         }
         bool hit = false;
@@ -341,6 +356,31 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
             }
         }
     }
+}
+
+template <int NP, int C, int POT = 0>
+__device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const float4* sT,
+                                           const float4* sC, const float* sTh,
+                                           const BeadCols& cols, int n_beads, const BeadPot& pot,
+                                           int lane, float (&v)[7]) {
+    float bx[2 * NP], by[2 * NP], bz[2 * NP];
+    float2 Bx[NP], By[NP], Bz[NP], BB[NP];
+    slots_setup<NP>(s, Rr, sT, n_beads, lane, bx, by, bz, Bx, By, Bz, BB);
+    LJAcc<NP> a;
+    a.zero();
+    // The cube's columns have z = -2, -1, 0, 1, 2 (bead spacing 1): then
+    // -2 z_m B_z is 4 B_z, 2 B_z, 0, -2 B_z, -4 B_z, exact multiples, and
+    // P + (-2 z_m) B_z is formed with one add (or none for z = 0) from U = 2 B_z
+    // and W = 4 B_z kept per slot, rounding exactly as the fused multiply-add
+    // of the general form would.
+    bool zint = false;
+    if constexpr (C == 5)
+        zint = cols.z[0] == -2.f && cols.z[1] == -1.f && cols.z[2] == 0.f && cols.z[3] == 1.f &&
+               cols.z[4] == 2.f;
+    if (zint)
+        cols_scan<NP, C, POT, true>(sC, sTh, cols, pot, Bx, By, Bz, BB, a);
+    else
+        cols_scan<NP, C, POT, false>(sC, sTh, cols, pot, Bx, By, Bz, BB, a);
     warp_finish<NP>(bx, by, bz, a, pot, v);
 }
 
