@@ -184,7 +184,8 @@ rb_status rb_eval_pairs(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t
 
 /* Integrate n_steps of velocity Verlet (NO_SQUISH free-rotor split for the
  * orientation) with forces from `path` (RB_PATH_BEADS, or RB_PATH_NN with
- * `mlp` at `precision`): NVE, or NVT when a thermostat is set.  Each step is
+ * `mlp` at `precision`, RB_FP32, RB_BF16 or RB_F16X3; RB_EINVAL for another
+ * value): NVE, or NVT when a thermostat is set.  Each step is
  * one CUDA-graph launch; asynchronous.  The integrator also counts, per body,
  * the box lengths crossed (unwrapped positions, see rb_msd_msr). */
 rb_status rb_step(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
@@ -393,7 +394,8 @@ rb_status rb_nn_fallback_count(rb_system* sys, int64_t* count_host);
  * cfg: n x 8 floats (s_x, s_y, s_z, 0, q_s, q_i, q_j, q_k).  out: n x 12 floats
  * (F_j xyz, E, tau_i xyz, 0, tau_j xyz, 0) in the frame of body i.  If
  * grad_out is not NULL it receives n x 8 floats (dE/ds xyz, 0, dE/dq wxyz) of
- * the raw (non-canonical) q_rel.  Runs on the mlp's stream. */
+ * the raw (non-canonical) q_rel.  Runs on the mlp's stream.  precision as in
+ * rb_forces_nn; the pair-symmetrised switch does not apply here. */
 rb_status rb_nn_pairs(const rb_mlp* mlp, int32_t precision, int64_t n, const float* cfg,
                       float* out, float* grad_out);
 
