@@ -423,6 +423,16 @@ rb_status rb_sample_pairs(const rb_system* sys, int64_t n, const float* uniforms
 rb_status rb_sample_pairs_at(const rb_system* sys, int64_t n, const float* uniforms, float contact,
                              float* cfg, float* labels, float* rho_contact);
 
+/* The same pair configurations and labels described from the other body
+ * (in place, device arrays, on `stream`): cfg rows (s, q) of rb_nn_pairs'
+ * input become (R(q)^T (-s), q^*), the first body seen from the second;
+ * labels rows (F_j, E), tau_i, tau_j (nullable) become (R(q)^T (-F_j), E),
+ * R(q)^T tau_j, R(q)^T tau_i.  The bead sum of two identical bodies is
+ * symmetric, so swapped bead labels are the labels of the swapped
+ * configurations: a training set doubled this way shows the network both
+ * descriptions of every pair. */
+rb_status rb_pairs_swap_reference(int64_t n, float* cfg, float* labels, void* stream);
+
 /* Trainer for `mlp`: Adam state and a workspace for batches of up to
  * max_batch pairs.  Runs on the network's stream. */
 typedef struct rb_trainer rb_trainer;

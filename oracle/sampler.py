@@ -98,3 +98,24 @@ def label_pairs(cfg, tmpl, eps=1.0, sigma=1.0, rc=2.5):
         r = bead_pair(zero, one, cfg[b, :3], cfg[b, 3:7], np.zeros(3), tmpl, tmpl, eps, sigma, rc)
         out[b] = np.concatenate([[r["E"]], r["F_j"], r["tau_i"], r["tau_j"]])
     return out
+
+
+def swap_reference(cfg, labels):
+    """The same pairs described from the other body.  A pair configuration
+    is given in the frame of its first body (SI Sec. 1): separation s and
+    relative orientation q of the second body, the first at the origin with
+    the identity orientation.  Taking the second body as the reference puts
+    the first at s' = R(q)^T (-s) with orientation q' = q^*, and the labels
+    (E, F on the second body, tau on the first, tau on the second) become
+    E' = E, F' = R(q)^T (-F), tau'_1 = R(q)^T tau_2, tau'_2 = R(q)^T tau_1.
+    cfg (B, 7) = (s, q); labels (B, 10) = (E, F_j, tau_i, tau_j)."""
+    from . import bodies
+
+    cfg = np.asarray(cfg, dtype=np.float64)
+    lab = np.asarray(labels, dtype=np.float64)
+    s, q = cfg[:, :3], cfg[:, 3:7]
+    qc = bodies.qconj(q)
+    out_cfg = np.concatenate([bodies.qrotate(qc, -s), qc], axis=1)
+    out_lab = np.concatenate([lab[:, :1], bodies.qrotate(qc, -lab[:, 1:4]),
+                              bodies.qrotate(qc, lab[:, 7:10]), bodies.qrotate(qc, lab[:, 4:7])], axis=1)
+    return out_cfg, out_lab

@@ -124,6 +124,7 @@ SIGNATURES = {
     "rb_mlp_set_symmetry": (I32, [P, P, I32, I32]),
     "rb_mlp_set_cutoff": (I32, [P, F32, F32]),
     "rb_mlp_set_pair_symmetrised": (I32, [P, I32]),
+    "rb_pairs_swap_reference": (I32, [I64, P, P, P]),
     "rb_nn_canonical": (I32, [P, I64, P, P]),
     "rb_set_nn_fallback": (I32, [P, F32]),
     "rb_set_skin": (I32, [P, F32]),

@@ -541,6 +541,17 @@ def sample_pairs(system: System, uniforms: torch.Tensor, contact: float = None):
     return cfg, lab, rc
 
 
+def pairs_swap_reference(cfg: torch.Tensor, labels: torch.Tensor = None, stream=None):
+    """rb_pairs_swap_reference in place on (n, 8) configurations [and (n, 12)
+    labels]: the same pairs described from the other body."""
+    _dev(cfg, 8)
+    if labels is not None:
+        _dev(labels, 12)
+    check(load().rb_pairs_swap_reference(cfg.shape[0], cfg.data_ptr(),
+                                         labels.data_ptr() if labels is not None else None,
+                                         _stream_handle(stream)))
+
+
 def _desc(n_bodies: int, box, shape: str = "cube", eps=1.0, sigma=1.0, rcut=2.5,
           max_neighbors: int = 0, skin: float = 0.0):
     d = _lib.rb_system_desc()

@@ -509,11 +509,47 @@ static rb_status train_grad(rb_trainer* tr, int64_t B, const float* cfg, const f
     return RB_OK;
 }
 
+// The same pairs with the other body as the reference, in place: cfg
+// (s, 0 | q) -> (R(q)^T (-s), 0 | q^*), labels (F, E | tau_i | tau_j) ->
+// (R(q)^T (-F), E | R(q)^T tau_j | R(q)^T tau_i).
+__global__ void k_swap_reference(int64_t n, float4* __restrict__ cfg, float4* __restrict__ lab) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const float4 s = cfg[2 * p], q = cfg[2 * p + 1];
+        const Mat3 R = qmat(q);
+        const float3 s2 = mulT(R, make_float3(-s.x, -s.y, -s.z));
+        cfg[2 * p] = make_float4(s2.x, s2.y, s2.z, 0.f);
+        cfg[2 * p + 1] = make_float4(q.x, -q.y, -q.z, -q.w);
+        if (lab) {
+            const float4 F = lab[3 * p], ti = lab[3 * p + 1], tj = lab[3 * p + 2];
+            const float3 F2 = mulT(R, make_float3(-F.x, -F.y, -F.z));
+            const float3 a = mulT(R, make_float3(tj.x, tj.y, tj.z));
+            const float3 b = mulT(R, make_float3(ti.x, ti.y, ti.z));
+            lab[3 * p] = make_float4(F2.x, F2.y, F2.z, F.w);
+            lab[3 * p + 1] = make_float4(a.x, a.y, a.z, 0.f);
+            lab[3 * p + 2] = make_float4(b.x, b.y, b.z, 0.f);
+        }
+    }
+}
+
 }  // namespace rb
 
 using namespace rb;
 
 extern "C" {
+
+rb_status rb_pairs_swap_reference(int64_t n, float* cfg, float* labels, void* stream) {
+    if (n < 0 || (n > 0 && !cfg)) return fail(RB_EINVAL, "bad pair arrays");
+    if (n == 0) return RB_OK;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    k_swap_reference<<<grid, 256, 0, (cudaStream_t)stream>>>(n, reinterpret_cast<float4*>(cfg),
+                                                            reinterpret_cast<float4*>(labels));
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
 
 rb_status rb_sample_pairs(const rb_system* s, int64_t n, const float* uniforms, float* cfg,
                           float* labels, float* rho_contact) {

@@ -22,7 +22,7 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
                   lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
                   log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0,
                   symmetric: bool = True, contact: float = 1.0, cutoff_width: float = 0.0,
-                  potential: str = "lj", hphc=None):
+                  potential: str = "lj", hphc=None, swap_augment: bool = False):
     """Returns (mlp, report).  With `symmetric` the body's point group is
     attached to the network (rb_mlp_set_symmetry), so it learns one copy of
     every class of symmetry-related configurations, and the feature
@@ -33,7 +33,10 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     for the sampled separations (rb_sample_pairs_at).  `cutoff_width` > 0:
     the energy is switched smoothly to zero between Rc - cutoff_width and Rc
     (rb_mlp_set_cutoff) during training and afterwards.  `potential`, `hphc`:
-    the bead potential that labels the samples (as api.System)."""
+    the bead potential that labels the samples (as api.System).  `swap_augment`:
+    the training set is doubled with every sample described from its other
+    body (rb_pairs_swap_reference; the bead labels of two identical bodies
+    are symmetric, so the swapped samples are exact)."""
     box = 60.0 if shape == "cube" else 70.0
     sysobj = api.System(8, [box] * 3, shape, potential=potential, hphc=hphc)
     Rc = sysobj.pair_cutoff
@@ -44,6 +47,10 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     t_sample = time.perf_counter() - t0
     cfg_tr, lab_tr = cfg[:n_samples], lab[:n_samples]
     cfg_te, lab_te = cfg[n_samples:], lab[n_samples:]
+    if swap_augment:
+        cfg_sw, lab_sw = cfg_tr.clone(), lab_tr.clone()
+        api.pairs_swap_reference(cfg_sw, lab_sw)
+        cfg_tr, lab_tr = torch.cat([cfg_tr, cfg_sw]), torch.cat([lab_tr, lab_sw])
     E = lab_tr[:, 3].double().cpu().numpy()
     rmin = float(rho_c.min().item())
     mu, isd = inputs.feature_normalisation(rmin, Rc)
@@ -73,7 +80,7 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     for k in range(steps):
         # cosine learning-rate decay to lr / 20
         tr.set_lr(lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps)))))
-        idx = torch.randint(0, n_samples, (batch,), device="cuda", generator=g)
+        idx = torch.randint(0, cfg_tr.shape[0], (batch,), device="cuda", generator=g)
         want = log_every and (k % log_every == 0)
         loss = tr.step(cfg_tr[idx].contiguous(), lab_tr[idx].contiguous(), lam_tau, lam_E,
                        want_loss=bool(want), f_scale=f_scale, kT_w=kT_w)
@@ -86,6 +93,7 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     out = mlp.pairs(cfg_te.contiguous(), "fp32")
     err = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
     report = {"shape": shape, "width": width, "depth": depth, "samples": n_samples,
+              "swap_augment": swap_augment,
               "symmetry": (f"{len(group[0])} rotations" + (" + inversion" if group[1] else ""))
               if group is not None else None,
               "cutoff": [Rc - cutoff_width, Rc] if cutoff_width > 0.0 else None,

@@ -112,3 +112,37 @@ def test_forces_and_torques_are_finite_differences_of_the_symmetrised_energy():
             qm[b] = bodies.qmul(bodies.qexp(-h * e), q[b])
             assert T[b, k] == pytest.approx(-(energy(pos, qp) - energy(pos, qm)) / (2 * h), rel=1e-6,
                                             abs=1e-9)
+
+
+# ------------------------------------------------- swapped reference body
+
+def _sampled(n, seed, tmpl):
+    from oracle import sampler
+
+    u = inputs.sampler_uniforms(n, seed)
+    cfg, lab, _ = sampler.sample_pairs(u, tmpl, bodies.pair_cutoff(tmpl))
+    return cfg, lab
+
+
+def test_swapping_the_reference_twice_is_the_identity():
+    from oracle import sampler
+
+    cfg, lab = _sampled(6, 51, bodies.cube_template())
+    c2, l2 = sampler.swap_reference(*sampler.swap_reference(cfg, lab))
+    np.testing.assert_allclose(c2, cfg, atol=1e-13)
+    np.testing.assert_allclose(l2, lab, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", ["cube", "cylinder"])
+def test_swapped_labels_are_the_bead_sum_of_the_swapped_configuration(shape):
+    """The bead sum is symmetric in its two identical bodies, so the labels
+    computed afresh at the swapped configuration must equal the swapped
+    labels: pins the rotation of every component."""
+    from oracle import sampler
+
+    tmpl = bodies.cube_template() if shape == "cube" else bodies.cylinder_template()
+    cfg, lab = _sampled(5, 52, tmpl)
+    sc, sl = sampler.swap_reference(cfg, lab)
+    fresh = sampler.label_pairs(sc, tmpl)
+    scale = np.abs(lab).max()
+    np.testing.assert_allclose(fresh, sl, atol=1e-10 * scale, rtol=1e-10)
