@@ -74,3 +74,32 @@ def test_template_symmetry_matches_the_oracle_without_gpu(lib, shape):
     assert inv == invo
     assert q.shape == qo.shape
     np.testing.assert_allclose(q, qo, atol=1e-7)
+
+
+def test_fnet_parameter_count_matches_the_oracle_layout_without_gpu(lib):
+    from oracle import fnet
+
+    lib.rb_fnet_n_params.restype = ctypes.c_int64
+    lib.rb_fnet_n_params.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    for w, d in ((16, 1), (32, 3), (64, 2)):
+        assert lib.rb_fnet_n_params(w, d) == 5 * fnet.net_size(w, d)
+    assert lib.rb_fnet_n_params(0, 3) == -1
+    assert lib.rb_fnet_n_params(32, 0) == -1
+
+
+def test_system_footprint_without_gpu(lib):
+    from paper_2402_12199_gb300 import api
+
+    lib.rb_system_footprint.restype = ctypes.c_int64
+    lib.rb_system_footprint.argtypes = [ctypes.c_void_p]
+    sizes = []
+    for n in (1000, 2000, 4000):
+        d = api._desc(n, [200.0] * 3, "cube")
+        sizes.append(lib.rb_system_footprint(ctypes.byref(d)))
+    assert all(b > 0 for b in sizes)
+    # linear in the body count at a fixed box: equal increments
+    assert sizes[2] - sizes[1] == 2 * (sizes[1] - sizes[0])
+    bad = api._desc(1, [200.0] * 3, "cube")
+    bad.n_bodies = 0
+    assert lib.rb_system_footprint(ctypes.byref(bad)) == -1
+    assert lib.rb_system_footprint(None) == -1
