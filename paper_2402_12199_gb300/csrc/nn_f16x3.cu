@@ -14,15 +14,16 @@
 // normal range) is about 2^-22 of the row's and the matrix's largest entries,
 // i.e. the GEMM keeps FP32-level accuracy at three FP16 MMAs, without the
 // exponent-range loss an unscaled FP16 split would have.  The elementwise
-// work (SiLU from exp and a reciprocal, silu', products with silu') is plain
-// FP32, as in the SIMT kernel.
+// work (SiLU and silu' from a base-2 exponential and a reciprocal, products
+// with silu', the split) is FP32 in packed FP32x2 arithmetic, the accuracy
+// class of the SIMT kernel's exp and division.  The MMAs of a stage are
+// issued as an unrolled sequence with constant descriptor offsets.
 //   * Shared memory: A_hi, A_lo [128 x 128] FP16 (K-major, 128-byte swizzle;
 //     the first 16 columns also hold the layer-1 features, so layer 1 is one
-//     K step), one weight
-//     buffer with B_hi and B_lo of one stage, streamed from a pre-swizzled
-//     global image by bulk asynchronous copies completing on an mbarrier; the
-//     copy for stage s + 1 is issued as soon as stage s's MMAs retire, so it
-//     overlaps stage s's epilogue.
+//     K step), one weight buffer with B_hi and B_lo of one stage, streamed
+//     from a pre-swizzled global image by bulk asynchronous copies completing
+//     on an mbarrier; the copy for stage s + 1 is issued as soon as stage s's
+//     MMAs retire, so it overlaps stage s's epilogue.
 //   * Tensor memory: columns 0..127 the accumulator of every stage; columns
 //     128 l .. 128 l + 127 silu'(z_l) in FP32 for l = 1 .. D-1, written by the
 //     forward epilogue and read by the reverse one.
