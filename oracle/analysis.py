@@ -9,43 +9,57 @@ unit quaternions as d(q1, q2) = 1 - <q1, q2>^2 (with the 4-D inner product)
 and the MSR as its average over the bodies, taken between a starting
 orientation and the orientation at a later time, like the MSD.
 
-g(r) bin decisions follow the CUDA path's stated FP32 recipe: every
-operation below is one IEEE single-precision operation with
-round-to-nearest (numpy float32), in the stated order, so the integer counts
-can be compared exactly.
+g(r) is taken from its plain definition in FP64: the minimum-image
+distance r of every pair of centres i < j, counted in bin
+k = floor(r n_bins / r_max) when r < r_max.  A single-precision evaluation
+can put a pair whose distance lies within its rounding error of a bin edge
+into the neighbouring bin; gr_edge_counts gives, per edge, how many pairs lie
+that close, so a comparison can allow exactly those moves.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def gr_counts(pos, box, r_max: float, n_bins: int, chunk: int = 2048) -> np.ndarray:
-    """Counts of body pairs i < j by minimum-image centre distance, all in
-    FP32: d = p_j - p_i; d -= L rint(d invL); r2 = (dx dx + dy dy) + dz dz;
-    bin = trunc(sqrt(r2) * (n_bins / r_max)) for r2 < r_max^2, clamped to the
-    last bin.  Brute force over all pairs (no pair list)."""
-    f = np.float32
-    p = np.asarray(pos, dtype=np.float32)[:, :3]
-    L = np.asarray(box, dtype=np.float32).reshape(3)
-    invL = (f(1.0) / L).astype(np.float32)
-    rmax = f(r_max)
-    rmax2 = f(rmax * rmax)
-    scale = f(f(n_bins) / rmax)
-    counts = np.zeros(n_bins, dtype=np.int64)
+def gr_distances(pos, box, r_max: float, chunk: int = 2048) -> np.ndarray:
+    """Minimum-image centre distances (FP64) of all pairs i < j with
+    r < r_max, by brute force over all pairs (no pair list)."""
+    p = np.asarray(pos, dtype=np.float64)[:, :3]
+    L = np.asarray(box, dtype=np.float64).reshape(3)
     N = len(p)
+    out = []
     for i0 in range(0, N, chunk):
         a = p[i0:i0 + chunk]
-        d = (p[None, :, :] - a[:, None, :]).astype(np.float32)
-        d = (d - (L * np.rint((d * invL).astype(np.float32))).astype(np.float32)).astype(np.float32)
-        r2 = ((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]).astype(np.float32)
+        d = p[None, :, :] - a[:, None, :]
+        d -= L * np.rint(d / L)
+        r = np.sqrt(np.sum(d * d, axis=-1))
         ii = np.arange(i0, i0 + len(a))[:, None]
         jj = np.arange(N)[None, :]
-        m = (jj > ii) & (r2 < rmax2)
-        r = np.sqrt(r2[m]).astype(np.float32)
-        k = (r * scale).astype(np.float32).astype(np.int64)
-        np.minimum(k, n_bins - 1, out=k)
-        counts += np.bincount(k, minlength=n_bins)
-    return counts
+        out.append(r[(jj > ii) & (r < r_max)])
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def gr_counts(pos, box, r_max: float, n_bins: int, chunk: int = 2048) -> np.ndarray:
+    """Counts of pairs i < j in the bins [k dr, (k + 1) dr), dr = r_max / n_bins,
+    of their minimum-image centre distance (FP64)."""
+    r = gr_distances(pos, box, r_max, chunk)
+    k = np.floor(r * (n_bins / float(r_max))).astype(np.int64)
+    # r < r_max, so k <= n_bins - 1 in exact arithmetic; the FP64 product can
+    # round up to n_bins for r within an ulp of r_max
+    np.minimum(k, n_bins - 1, out=k)
+    return np.bincount(k, minlength=n_bins)
+
+
+def gr_edge_counts(pos, box, r_max: float, n_bins: int, tol: float,
+                   chunk: int = 2048) -> np.ndarray:
+    """Per bin edge e = 0..n_bins (at r = e dr, the last one r_max): the number
+    of pairs i < j whose FP64 distance lies within `tol` of that edge,
+    including pairs just beyond r_max."""
+    r = gr_distances(pos, box, float(r_max) + tol, chunk)
+    dr = float(r_max) / n_bins
+    e = np.rint(r / dr).astype(np.int64)
+    near = (np.abs(r - e * dr) < tol) & (e <= n_bins)
+    return np.bincount(e[near], minlength=n_bins + 1)
 
 
 def gr_normalise(counts, r_max: float, n_frames: int, n_bodies: int, volume: float) -> np.ndarray:

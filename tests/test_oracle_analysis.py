@@ -36,6 +36,25 @@ def test_gr_counts_simple_cubic_lattice():
     np.testing.assert_array_equal(c, expect)
 
 
+def test_gr_edge_counts_find_shells_on_bin_edges():
+    """dr = 0.5 puts the lattice's first shell (a = 3) and fourth (2a = 6) on
+    bin edges 6 and 12; the second and third (4.24, 5.20) lie 0.24 and 0.20
+    from the nearest edges.  A pair exactly on an edge belongs to the bin
+    above it."""
+    m, a = 6, 3.0
+    g = (np.arange(m) + 0.5) * a
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    N = len(pos)
+    e = analysis.gr_edge_counts(pos, [m * a] * 3, 6.5, 13, 1e-6)
+    expect = np.zeros(14, dtype=np.int64)
+    expect[6] = N * 6 // 2
+    expect[12] = N * 6 // 2
+    np.testing.assert_array_equal(e, expect)
+    assert analysis.gr_edge_counts(pos, [m * a] * 3, 6.5, 13, 0.21)[10] == N * 8 // 2
+    c = analysis.gr_counts(pos, [m * a] * 3, 6.5, 13)
+    assert c[6] == N * 6 // 2 and c[5] == 0 and c[12] == N * 6 // 2
+
+
 def test_gr_of_ideal_gas_is_one():
     rng = np.random.default_rng(2)
     N, L = 3000, 40.0
