@@ -671,7 +671,9 @@ rb_status rb_fnet_train_step(rb_fnet_trainer* t, int64_t batch, const float* cfg
     rb_fnet* f = t->f;
     const int64_t np = kFnNets * f->net_floats;
     ++t->t;
-    const float c1 = 1.f - std::pow(t->beta1, (float)t->t), c2 = 1.f - std::pow(t->beta2, (float)t->t);
+    // bias corrections in FP64 (1 - beta2^t cancels badly in FP32)
+    const float c1 = (float)(1.0 - std::pow((double)t->beta1, (double)t->t));
+    const float c2 = (float)(1.0 - std::pow((double)t->beta2, (double)t->t));
     k_adam<<<nblk(np), 256, 0, f->stream>>>(np, 0, np, f->params, t->grad, t->m, t->v, t->lr, t->beta1,
                                             t->beta2, t->eps, c1, c2);
     RB_CUDA(cudaGetLastError());

@@ -650,8 +650,10 @@ rb_status rb_train_step(rb_trainer* t, int64_t batch, const float* cfg, const fl
     RB_TRY(train_grad(t, batch, cfg, labels, lam_tau, lam_E, f_scale, kT_w, loss_host));
     rb_mlp* m = t->mlp;
     t->t += 1;
-    const float c1 = 1.f - std::pow(t->beta1, (float)t->t);
-    const float c2 = 1.f - std::pow(t->beta2, (float)t->t);
+    // Bias corrections 1 - beta^t in FP64: in FP32, 1 - beta2^t loses about
+    // five digits to cancellation (beta2^t is within 1e-3 of 1 early on).
+    const float c1 = (float)(1.0 - std::pow((double)t->beta1, (double)t->t));
+    const float c2 = (float)(1.0 - std::pow((double)t->beta2, (double)t->t));
     const int64_t np = m->n_params;
     k_adam<<<nblk(np), 256, 0, m->stream>>>(np, 2 * kIn, np - 2, m->params, t->grad, t->m, t->v,
                                             t->lr, t->beta1, t->beta2, t->eps, c1, c2);
