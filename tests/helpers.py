@@ -1,5 +1,7 @@
 """Shared test helpers: build systems from the seeded inputs, run the oracle,
-and compute the error metrics (aggregate relative L2 norm over bodies)."""
+and compute the error metrics: the aggregate relative L2 norm over bodies
+(e_F, e_tau) and the element-wise error max_i |a_i - b_i| / max(rms, |b_i|),
+which a single wrong body cannot hide under."""
 from __future__ import annotations
 
 import numpy as np
@@ -17,6 +19,39 @@ def rel_err(a, b) -> float:
     b = np.asarray(b, dtype=np.float64)
     den = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
+
+
+def max_body_err(a, b) -> float:
+    """max_i |a_i - b_i| / max(rms, |b_i|) over the rows i (bodies or pairs) of
+    (n, k) arrays, rms = sqrt(mean_i |b_i|^2); a 1-D array is taken as n rows
+    of one value.  Rows far larger than the rms (a body in hard contact among
+    many in soft contact: the bead forces and torques are heavy-tailed) are
+    held to their own magnitude, the others to the rms."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.ndim == 1:
+        a, b = a[:, None], b[:, None]
+    if len(a) == 0:
+        return 0.0
+    d = np.sqrt(np.sum((a - b) ** 2, axis=1))
+    nb = np.sqrt(np.sum(b * b, axis=1))
+    rms = float(np.sqrt(np.mean(nb * nb)))
+    if rms == 0.0:
+        return float(d.max())
+    return float(np.max(d / np.maximum(nb, rms)))
+
+
+PER_BODY_FACTOR = 10.0  # element-wise bound: max_i |error_i| / max(rms, |ref_i|) <= 10 x tolerance
+
+
+def assert_parity(got, ref, tol, what=""):
+    """Aggregate relative error below `tol` and no row worse than
+    PER_BODY_FACTOR x tol relative to max(rms of the reference rows, its own
+    reference magnitude)."""
+    e = rel_err(got, ref)
+    m = max_body_err(got, ref)
+    assert e < tol and m < PER_BODY_FACTOR * tol, (what, e, m, tol)
+    return e, m
 
 
 def template(shape: str):

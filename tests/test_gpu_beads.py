@@ -5,7 +5,8 @@ import pytest
 
 import oracle
 from oracle import bodies, md
-from tests.helpers import (TOL_F32, gpu_system, make_state, oracle_beads, rel_err, template)
+from tests.helpers import (TOL_F32, assert_parity, gpu_system, make_state, oracle_beads, rel_err,
+                           template)
 
 pytestmark = pytest.mark.gpu
 
@@ -60,8 +61,8 @@ def _parity(st, L, tmpl, shape, tol=TOL_F32):
     F, T, E, vir, pairs = oracle_beads(st, L, tmpl)
     Fg = res["force"][:, :3].double().cpu().numpy()
     Tg = res["torque"][:, :3].double().cpu().numpy()
-    eF, eT = rel_err(Fg, F), rel_err(Tg, T)
-    assert eF < tol and eT < tol, (eF, eT)
+    eF, _ = assert_parity(Fg, F, tol, "force")
+    eT, _ = assert_parity(Tg, T, tol, "torque")
     # energy: relative to the sum of |pair energies|
     pp = oracle.forces_beads(st["pos"][:, :3], st["quat"], [L] * 3, tmpl, pairs,
                              per_pair=True)[4]
@@ -107,8 +108,8 @@ def test_bead_forces_parity_custom_template():
     s.sync()
     F, T, E, _, pairs = oracle_beads(st, L, g)
     assert len(pairs) > 50
-    assert rel_err(res["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
-    assert rel_err(res["torque"][:, :3].double().cpu().numpy(), T) < TOL_F32
+    assert_parity(res["force"][:, :3].double().cpu().numpy(), F, TOL_F32, "force")
+    assert_parity(res["torque"][:, :3].double().cpu().numpy(), T, TOL_F32, "torque")
 
 
 def test_bead_forces_sampled_32768_cubes():
@@ -133,10 +134,34 @@ def test_bead_forces_sampled_32768_cubes():
     F, T, E, _ = oracle.forces_beads(pos, st["quat"], [L] * 3, tmpl, pairs)
     Fg = res["force"][:, :3].double().cpu().numpy()[idx]
     Tg = res["torque"][:, :3].double().cpu().numpy()[idx]
-    assert rel_err(Fg, F[idx]) < TOL_F32
-    assert rel_err(Tg, T[idx]) < TOL_F32
+    assert_parity(Fg, F[idx], TOL_F32, "force")
+    assert_parity(Tg, T[idx], TOL_F32, "torque")
     n_pairs = s.build_pairs()
     assert 60000 < n_pairs < 200000
+
+
+@pytest.mark.parametrize("shape,n,phi,seed", [("cube", 4096, 0.20, 13), ("cylinder", 1500, 0.15, 14)])
+def test_kinetic_energies_match_oracle(shape, n, phi, seed):
+    """rb_energy's translational and rotational kinetic energies (FP64 sums on
+    the device) equal the oracle's sum(M |v|^2 / 2) and sum(L_b,k^2 / 2 I_k)
+    on the same state, after a few steps so that v and L_b are not the
+    initial draw; FP64 sums in different orders agree to ~N x 1e-16.  The
+    system holds its principal moments in FP32 (the cylinder's are not
+    representable exactly), so the oracle takes the same FP32 values, the
+    moments the dynamics run with."""
+    st, L, tmpl = make_state(n, phi, seed, shape)
+    M, I = bodies.mass_and_inertia(tmpl)
+    s = gpu_system(st, L, shape)
+    s.step(5, 0.002)
+    _, ke_t, ke_r = s.energy()
+    cur = s.get_state(to_host=True)
+    s.sync()
+    I32 = np.diag(I).astype(np.float32).astype(np.float64)
+    ref_t, ref_r = md.kinetic(cur["vel"][:, :3].astype(np.float64),
+                              cur["angmom"][:, :3].astype(np.float64), M, I32)
+    assert ke_t == pytest.approx(ref_t, rel=1e-12)
+    assert ke_r == pytest.approx(ref_r, rel=1e-12)
+    assert ref_t > 0 and ref_r > 0
 
 
 def test_edge_cases():
@@ -164,7 +189,7 @@ def test_edge_cases():
     r = s.forces_beads(energy=True)
     F, T, E, _, pairs = oracle_beads(st2, 30.0, tmpl)
     assert len(pairs) == 1 and E != 0.0
-    assert rel_err(r["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
+    assert_parity(r["force"][:, :3].double().cpu().numpy(), F, TOL_F32)
     assert r["energy"] == pytest.approx(E, rel=TOL_F32)
     # invalid box: smaller than 2 Rc
     with pytest.raises(api.RBError) as ei:

@@ -9,7 +9,7 @@ import pytest
 
 from oracle import bodies, nn, symmetry
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_BF16, TOL_F32, gpu_system, make_state, rel_err
+from tests.helpers import TOL_BF16, TOL_F32, assert_parity, gpu_system, make_state, rel_err
 
 pytestmark = pytest.mark.gpu
 MARGIN = 1e-4
@@ -68,10 +68,10 @@ def test_switched_pairs_parity(width, precision, tol):
     assert beyond.any() and (rho < R_ON).any()
     # beyond r_off: exactly nothing
     assert np.all(out[beyond][:, [0, 1, 2, 3, 4, 5, 6, 8, 9, 10]] == 0.0)
-    assert rel_err(out[:, 0:3], Fj.numpy()) < tol
-    assert rel_err(out[:, 4:7], ti.numpy()) < tol
-    assert rel_err(out[:, 8:11], tj.numpy()) < tol
-    assert rel_err(out[:, 3], E.detach().numpy()) < tol
+    assert_parity(out[:, 0:3], Fj.numpy(), tol)
+    assert_parity(out[:, 4:7], ti.numpy(), tol)
+    assert_parity(out[:, 8:11], tj.numpy(), tol)
+    assert_parity(out[:, 3], E.detach().numpy(), tol)
 
 
 def test_switched_system_forces_parity():
@@ -96,8 +96,8 @@ def test_switched_system_forces_parity():
     bad = np.unique(pairs[np.minimum(np.minimum(mk, mj), np.abs(cq[:, 0])) < MARGIN].ravel())
     keep = np.setdiff1d(np.arange(len(pos)), bad)
     assert len(keep) > 0.95 * len(pos)
-    assert rel_err(r["force"][:, :3].double().cpu().numpy()[keep], F[keep]) < TOL_F32
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy()[keep], T[keep]) < TOL_F32
+    assert_parity(r["force"][:, :3].double().cpu().numpy()[keep], F[keep], TOL_F32)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy()[keep], T[keep], TOL_F32)
 
 
 def test_switched_training_gradient_and_weight_vjp():

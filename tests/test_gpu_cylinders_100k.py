@@ -11,8 +11,8 @@ import pytest
 
 from oracle import bodies, nn, sampler
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import (TOL_BF16, TOL_F32, canonical_margin, gpu_system, make_state,
-                           oracle_beads, oracle_nn, rel_err)
+from tests.helpers import (TOL_BF16, TOL_F32, assert_parity, canonical_margin, gpu_system,
+                           make_state, oracle_beads, oracle_nn, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -60,8 +60,8 @@ def test_bead_forces_sampled_100k_cylinders(system100k):
     s.sync()
     assert len(pairs) > 32
     F, T, _, _, _ = oracle_beads(st, L, tmpl, pairs)
-    assert rel_err(res["force"][:, :3].double().cpu().numpy()[idx], F[idx]) < TOL_F32
-    assert rel_err(res["torque"][:, :3].double().cpu().numpy()[idx], T[idx]) < TOL_F32
+    assert_parity(res["force"][:, :3].double().cpu().numpy()[idx], F[idx], TOL_F32)
+    assert_parity(res["torque"][:, :3].double().cpu().numpy()[idx], T[idx], TOL_F32)
     # about 2.7 half pairs per body at this density
     assert 150_000 < n_pairs < 500_000
 
@@ -79,8 +79,8 @@ def test_nn_width256_sampled_100k_cylinders(system100k, precision, tol):
     s.sync()
     assert canonical_margin(st, pairs) > 1e-6
     F, T, _, _, _ = oracle_nn(st, L, tmpl, flat, WIDTH, pairs=pairs)
-    assert rel_err(r["force"][:, :3].double().cpu().numpy()[idx], F[idx]) < tol
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy()[idx], T[idx]) < tol
+    assert_parity(r["force"][:, :3].double().cpu().numpy()[idx], F[idx], tol)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy()[idx], T[idx], tol)
 
 
 def test_width256_adjoint_matches_central_differences():
@@ -122,9 +122,9 @@ def test_width256_adjoint_matches_central_differences():
         Fj[:, k] = -(energy(R + e, qi, qj) - energy(R - e, qi, qj)) / (2 * h)
         tj[:, k] = -(energy(R, qi, bodies.qmul(rp, qj)) - energy(R, qi, bodies.qmul(rm, qj))) / (2 * h)
         ti[:, k] = -(energy(R, bodies.qmul(rp, qi), qj) - energy(R, bodies.qmul(rm, qi), qj)) / (2 * h)
-    assert rel_err(out[:, 0:3], Fj) < TOL_F32
-    assert rel_err(out[:, 4:7], ti) < TOL_F32
-    assert rel_err(out[:, 8:11], tj) < TOL_F32
+    assert_parity(out[:, 0:3], Fj, TOL_F32)
+    assert_parity(out[:, 4:7], ti, TOL_F32)
+    assert_parity(out[:, 8:11], tj, TOL_F32)
 
 
 def test_sampler_one_million_cylinder_pairs():
@@ -150,9 +150,9 @@ def test_sampler_one_million_cylinder_pairs():
     c = cfg[pick].double().cpu().numpy()
     got = lab[pick].double().cpu().numpy()
     ref = sampler.label_pairs(np.concatenate([c[:, :3], c[:, 4:8]], 1), tmpl)
-    assert rel_err(got[:, 0:3], ref[:, 1:4]) < TOL_F32
-    assert rel_err(got[:, 4:7], ref[:, 4:7]) < TOL_F32
-    assert rel_err(got[:, 8:11], ref[:, 7:10]) < TOL_F32
+    assert_parity(got[:, 0:3], ref[:, 1:4], TOL_F32)
+    assert_parity(got[:, 4:7], ref[:, 4:7], TOL_F32)
+    assert_parity(got[:, 8:11], ref[:, 7:10], TOL_F32)
     d, q = sampler.draws_to_config(u[pick].astype(np.float64))
     for b in range(0, 64, 8):
         assert float(rc[pick[b]]) == pytest.approx(sampler.contact_distance(d[b], q[b], tmpl, Rc),

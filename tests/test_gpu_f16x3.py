@@ -9,7 +9,8 @@ import pytest
 
 from oracle import nn
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_F32, canonical_margin, gpu_system, make_state, oracle_nn, rel_err
+from tests.helpers import (TOL_F32, assert_parity, canonical_margin, gpu_system, make_state,
+                           oracle_nn, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -48,10 +49,10 @@ def _check_pairs(flat, depth, n, seed, tol=TOL_F32):
     p = nn.unpack(flat.astype(np.float64), 128, depth)
     c = torch.as_tensor(cfg7.astype(np.float64))
     E, Fj, ti, tj = nn.predict_labels(p, c[:, :3], c[:, 3:])
-    assert rel_err(out[:, 0:3], Fj.numpy()) < tol
-    assert rel_err(out[:, 4:7], ti.numpy()) < tol
-    assert rel_err(out[:, 8:11], tj.numpy()) < tol
-    assert rel_err(out[:, 3], E.detach().numpy()) < tol
+    assert_parity(out[:, 0:3], Fj.numpy(), tol)
+    assert_parity(out[:, 4:7], ti.numpy(), tol)
+    assert_parity(out[:, 8:11], tj.numpy(), tol)
+    assert_parity(out[:, 3], E.detach().numpy(), tol)
     assert np.all(out[:, [7, 11]] == 0.0)
 
 
@@ -104,8 +105,8 @@ def test_nn_system_forces_f16x3_parity():
     s.sync()
     F, T, E, per, pairs = oracle_nn(st, L, tmpl, flat, 128)
     assert canonical_margin(st, pairs) > 1e-5
-    assert rel_err(r["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy(), T) < TOL_F32
+    assert_parity(r["force"][:, :3].double().cpu().numpy(), F, TOL_F32)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy(), T, TOL_F32)
     assert abs(r["energy"] - E) < TOL_F32 * np.abs(per).sum()
 
 

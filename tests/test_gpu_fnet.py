@@ -14,7 +14,7 @@ import pytest
 
 from oracle import bodies, fnet
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_F32, gpu_system, make_state, rel_err
+from tests.helpers import TOL_F32, assert_parity, gpu_system, make_state, rel_err
 
 pytestmark = pytest.mark.gpu
 MARGIN = 1e-4
@@ -80,9 +80,9 @@ def test_fnet_pair_outputs_parity(width, depth):
     out = f.pairs(torch.from_numpy(cfg).cuda()).double().cpu().numpy()
     nets = fnet.unpack(flat.astype(np.float64), width, depth)
     Fj, ti, tj, _ = fnet.predict(nets, s.astype(np.float64), q.astype(np.float64))
-    assert rel_err(out[:, 0:3], Fj) < TOL_F32
-    assert rel_err(out[:, 4:7], ti) < TOL_F32
-    assert rel_err(out[:, 8:11], tj) < TOL_F32
+    assert_parity(out[:, 0:3], Fj, TOL_F32)
+    assert_parity(out[:, 4:7], ti, TOL_F32)
+    assert_parity(out[:, 8:11], tj, TOL_F32)
     assert np.all(out[:, [3, 7, 11]] == 0.0)
 
 
@@ -110,8 +110,8 @@ def test_fnet_system_forces_parity():
     keep = np.setdiff1d(np.arange(len(pos)), bad)
     assert len(pairs) > 300 and len(keep) > 0.9 * len(pos)
     F, T = fnet.forces_fnet(fnet.unpack(flat.astype(np.float64), width, depth), pos, quat, box, pairs)
-    assert rel_err(r["force"][:, :3].double().cpu().numpy()[keep], F[keep]) < TOL_F32
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy()[keep], T[keep]) < TOL_F32
+    assert_parity(r["force"][:, :3].double().cpu().numpy()[keep], F[keep], TOL_F32)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy()[keep], T[keep], TOL_F32)
     # Newton 3: the total force vanishes (FP32 rounding only)
     tot = r["force"][:, :3].double().sum(0).abs().max().item()
     assert tot < 1e-4 * np.abs(F).sum()

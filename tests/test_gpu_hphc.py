@@ -10,7 +10,7 @@ import pytest
 import oracle
 from oracle import bodies
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_F32, make_state, rel_err
+from tests.helpers import TOL_F32, assert_parity, make_state, rel_err
 
 pytestmark = pytest.mark.gpu
 H = inputs.HPHC_PAPER
@@ -61,8 +61,8 @@ def test_hphc_system_parity(shape, n, printed, phi):
     s.sync()
     F, T, E, vir = _oracle(st, L, tmpl, printed)
     assert np.abs(F).max() > 0
-    assert rel_err(res["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
-    assert rel_err(res["torque"][:, :3].double().cpu().numpy(), T) < TOL_F32
+    assert_parity(res["force"][:, :3].double().cpu().numpy(), F, TOL_F32)
+    assert_parity(res["torque"][:, :3].double().cpu().numpy(), T, TOL_F32)
     assert res["energy"] == pytest.approx(E, rel=TOL_F32)
     assert rel_err(res["virial"], vir) < TOL_F32
 
@@ -85,8 +85,8 @@ def test_hphc_generic_template_parity():
     s.sync()
     F, T, E, _ = _oracle(st, L, box_t, False)
     assert np.abs(F).max() > 0
-    assert rel_err(res["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
-    assert rel_err(res["torque"][:, :3].double().cpu().numpy(), T) < TOL_F32
+    assert_parity(res["force"][:, :3].double().cpu().numpy(), F, TOL_F32)
+    assert_parity(res["torque"][:, :3].double().cpu().numpy(), T, TOL_F32)
     assert res["energy"] == pytest.approx(E, rel=TOL_F32)
 
 

@@ -5,7 +5,8 @@ import pytest
 
 from oracle import bodies, nn
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_F32, canonical_margin, gpu_system, make_state, oracle_nn, rel_err
+from tests.helpers import (TOL_F32, assert_parity, canonical_margin, gpu_system, make_state,
+                           oracle_nn, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -55,9 +56,9 @@ def test_nn_pairs_parity(width, n):
     torch.cuda.synchronize()
     out = out.double().cpu().numpy()
     E, Fj, ti, tj = oracle_labels(flat, width, cfg7)
-    assert rel_err(out[:, 0:3], Fj) < TOL_F32
-    assert rel_err(out[:, 4:7], ti) < TOL_F32
-    assert rel_err(out[:, 8:11], tj) < TOL_F32
+    assert_parity(out[:, 0:3], Fj, TOL_F32)
+    assert_parity(out[:, 4:7], ti, TOL_F32)
+    assert_parity(out[:, 8:11], tj, TOL_F32)
     assert np.abs(out[:, 3] - E).max() < TOL_F32 * max(1.0, np.abs(E).max())
     # gradient of E with respect to the raw inputs (s, q_rel)
     sq = torch.as_tensor(cfg7.astype(np.float64)).requires_grad_(True)
@@ -65,8 +66,8 @@ def test_nn_pairs_parity(width, n):
     Eo = nn.config_energy(p, sq[:, :3], sq[:, 3:])
     (gref,) = torch.autograd.grad(Eo.sum(), [sq])
     g = g.double().cpu().numpy()
-    assert rel_err(g[:, 0:3], gref[:, :3].numpy()) < TOL_F32
-    assert rel_err(g[:, 4:8], gref[:, 3:].numpy()) < TOL_F32
+    assert_parity(g[:, 0:3], gref[:, :3].numpy(), TOL_F32)
+    assert_parity(g[:, 4:8], gref[:, 3:].numpy(), TOL_F32)
 
 
 def test_nn_pairs_empty_and_depths():
@@ -86,10 +87,10 @@ def test_nn_pairs_empty_and_depths():
         cfg7 = inputs.pair_configs(300, depth, 5.0, 9.4)
         out = m.pairs(torch.from_numpy(cfg8(cfg7)).cuda()).double().cpu().numpy()
         E, Fj, ti, tj = oracle_labels(flat, width, cfg7, depth)
-        assert rel_err(out[:, 0:3], Fj) < TOL_F32, (width, depth)
-        assert rel_err(out[:, 4:7], ti) < TOL_F32, (width, depth)
-        assert rel_err(out[:, 8:11], tj) < TOL_F32, (width, depth)
-        assert rel_err(out[:, 3], E) < TOL_F32, (width, depth)
+        assert_parity(out[:, 0:3], Fj, TOL_F32)
+        assert_parity(out[:, 4:7], ti, TOL_F32)
+        assert_parity(out[:, 8:11], tj, TOL_F32)
+        assert_parity(out[:, 3], E, TOL_F32)
 
 
 def test_nn_system_forces_parity_64_cubes():
@@ -104,8 +105,8 @@ def test_nn_system_forces_parity_64_cubes():
     s.sync()
     F, T, E, per, pairs = oracle_nn(st, L, tmpl, flat, 128)
     assert canonical_margin(st, pairs) > 1e-4
-    assert rel_err(r["force"][:, :3].double().cpu().numpy(), F) < TOL_F32
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy(), T) < TOL_F32
+    assert_parity(r["force"][:, :3].double().cpu().numpy(), F, TOL_F32)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy(), T, TOL_F32)
     assert abs(r["energy"] - E) < TOL_F32 * np.abs(per).sum()
 
 
@@ -153,5 +154,5 @@ def test_bead_fallback_for_close_pairs():
     assert n_fb == int(close.sum()) and 0 < n_fb < len(pairs)
     Fb, Tb, _, _ = oracle.forces_beads(pos, st["quat"], [L] * 3, tmpl, pairs[close])
     Fn, Tn, _, _, _ = oracle_nn(st, L, tmpl, flat, 128, pairs=pairs[~close])
-    assert rel_err(r["force"][:, :3].double().cpu().numpy(), Fb + Fn) < TOL_F32
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy(), Tb + Tn) < TOL_F32
+    assert_parity(r["force"][:, :3].double().cpu().numpy(), Fb + Fn, TOL_F32)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy(), Tb + Tn, TOL_F32)

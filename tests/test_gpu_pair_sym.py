@@ -8,7 +8,8 @@ import pytest
 import oracle
 from oracle import bodies, nn
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_BF16, TOL_F32, canonical_margin, gpu_system, make_state, rel_err
+from tests.helpers import (TOL_BF16, TOL_F32, assert_parity, canonical_margin, gpu_system,
+                           make_state, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -52,8 +53,8 @@ def test_pair_symmetrised_forces_parity(precision, tol):
     s.sync()
     F, T, E, per, pairs = oracle_sym(st, L, tmpl, flat)
     assert canonical_margin(st, pairs) > 1e-5
-    assert rel_err(r["force"][:, :3].double().cpu().numpy(), F) < tol
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy(), T) < tol
+    assert_parity(r["force"][:, :3].double().cpu().numpy(), F, tol)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy(), T, tol)
     assert abs(r["energy"] - E) < tol * np.abs(per).sum()
     # switched off again: the plain evaluation (i < j, i the reference)
     m.set_pair_symmetrised(False)
@@ -62,7 +63,7 @@ def test_pair_symmetrised_forces_parity(precision, tol):
     F0, T0, E0, per0 = nn.forces_nn(nn.unpack(flat.astype(np.float64), 128, 3),
                                     st["pos"][:, :3].astype(np.float64), st["quat"].astype(np.float64),
                                     np.array([L] * 3), pairs)
-    assert rel_err(r0["force"][:, :3].double().cpu().numpy(), F0) < tol
+    assert_parity(r0["force"][:, :3].double().cpu().numpy(), F0, tol)
     assert abs(r0["energy"] - E0) < tol * np.abs(per0).sum()
 
 

@@ -13,7 +13,7 @@ import pytest
 
 from oracle import bodies, nn, symmetry
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_BF16, TOL_F32, gpu_system, make_state, rel_err
+from tests.helpers import TOL_BF16, TOL_F32, assert_parity, gpu_system, make_state, rel_err
 
 pytestmark = pytest.mark.gpu
 MARGIN = 1e-4
@@ -110,15 +110,15 @@ def test_symmetric_pairs_parity(width, precision, tol):
     s = torch.as_tensor(c8[:, :3].astype(np.float64))
     q = torch.as_tensor(c8[:, 4:].astype(np.float64))
     E, Fj, ti, tj = nn.predict_labels(p, s, q)
-    assert rel_err(out[:, 0:3], Fj.numpy()) < tol
-    assert rel_err(out[:, 4:7], ti.numpy()) < tol
-    assert rel_err(out[:, 8:11], tj.numpy()) < tol
-    assert rel_err(out[:, 3], E.detach().numpy()) < tol
+    assert_parity(out[:, 0:3], Fj.numpy(), tol)
+    assert_parity(out[:, 4:7], ti.numpy(), tol)
+    assert_parity(out[:, 8:11], tj.numpy(), tol)
+    assert_parity(out[:, 3], E.detach().numpy(), tol)
     # dE/d(s, q_rel) of the raw configuration
     sq = torch.cat([s, q], 1).requires_grad_(True)
     (gref,) = torch.autograd.grad(nn.config_energy(p, sq[:, :3], sq[:, 3:]).sum(), [sq])
-    assert rel_err(g[:, 0:3], gref[:, :3].numpy()) < tol
-    assert rel_err(g[:, 4:8], gref[:, 3:].numpy()) < tol
+    assert_parity(g[:, 0:3], gref[:, :3].numpy(), tol)
+    assert_parity(g[:, 4:8], gref[:, 3:].numpy(), tol)
 
 
 def test_symmetric_network_is_invariant_on_gpu():
@@ -139,10 +139,10 @@ def test_symmetric_network_is_invariant_on_gpu():
         c2[:, 4:] = q2
         out = m.pairs(torch.from_numpy(c2).cuda(), "fp32").double().cpu().numpy()
         R = bodies.qmatrix(quats[k])
-        assert rel_err(out[:, 3], base[:, 3]) < TOL_F32
-        assert rel_err(out[:, 0:3], sg * base[:, 0:3] @ R.T) < TOL_F32
-        assert rel_err(out[:, 4:7], base[:, 4:7] @ R.T) < TOL_F32
-        assert rel_err(out[:, 8:11], base[:, 8:11] @ R.T) < TOL_F32
+        assert_parity(out[:, 3], base[:, 3], TOL_F32)
+        assert_parity(out[:, 0:3], sg * base[:, 0:3] @ R.T, TOL_F32)
+        assert_parity(out[:, 4:7], base[:, 4:7] @ R.T, TOL_F32)
+        assert_parity(out[:, 8:11], base[:, 8:11] @ R.T, TOL_F32)
 
 
 def _pair_margins(st, L, pairs, group):
@@ -176,8 +176,8 @@ def test_symmetric_system_forces_parity(precision, tol):
     bad = np.unique(pairs[_pair_margins(st, L, pairs, group) < MARGIN].ravel())
     keep = np.setdiff1d(np.arange(len(pos)), bad)
     assert len(keep) > 0.95 * len(pos)
-    assert rel_err(r["force"][:, :3].double().cpu().numpy()[keep], F[keep]) < tol
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy()[keep], T[keep]) < tol
+    assert_parity(r["force"][:, :3].double().cpu().numpy()[keep], F[keep], tol)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy()[keep], T[keep], tol)
 
 
 def _train_setup(width, B, seed):

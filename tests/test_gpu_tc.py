@@ -6,7 +6,8 @@ import pytest
 
 from oracle import nn
 from paper_2402_12199_gb300 import inputs
-from tests.helpers import TOL_BF16, canonical_margin, gpu_system, make_state, oracle_nn, rel_err
+from tests.helpers import (TOL_BF16, assert_parity, canonical_margin, gpu_system, make_state,
+                           oracle_nn, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -67,10 +68,10 @@ def test_nn_pairs_bf16_parity(n, depth, width):
     p = nn.unpack(flat.astype(np.float64), width, depth)
     c = torch.as_tensor(cfg7.astype(np.float64))
     E, Fj, ti, tj = nn.predict_labels(p, c[:, :3], c[:, 3:])
-    assert rel_err(out[:, 0:3], Fj.numpy()) < TOL_BF16
-    assert rel_err(out[:, 4:7], ti.numpy()) < TOL_BF16
-    assert rel_err(out[:, 8:11], tj.numpy()) < TOL_BF16
-    assert rel_err(out[:, 3], E.detach().numpy()) < TOL_BF16
+    assert_parity(out[:, 0:3], Fj.numpy(), TOL_BF16)
+    assert_parity(out[:, 4:7], ti.numpy(), TOL_BF16)
+    assert_parity(out[:, 8:11], tj.numpy(), TOL_BF16)
+    assert_parity(out[:, 3], E.detach().numpy(), TOL_BF16)
 
 
 @pytest.mark.parametrize("width", [128, 256])
@@ -86,8 +87,8 @@ def test_nn_system_forces_bf16_parity(width):
     s.sync()
     F, T, E, per, pairs = oracle_nn(st, L, tmpl, flat, width)
     assert canonical_margin(st, pairs) > 1e-5
-    assert rel_err(r["force"][:, :3].double().cpu().numpy(), F) < TOL_BF16
-    assert rel_err(r["torque"][:, :3].double().cpu().numpy(), T) < TOL_BF16
+    assert_parity(r["force"][:, :3].double().cpu().numpy(), F, TOL_BF16)
+    assert_parity(r["torque"][:, :3].double().cpu().numpy(), T, TOL_BF16)
     assert abs(r["energy"] - E) < TOL_BF16 * np.abs(per).sum()
 
 

@@ -7,7 +7,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from tests.helpers import TOL_F32, gpu_system, make_state, rel_err
+from tests.helpers import TOL_F32, assert_parity, gpu_system, make_state, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -46,9 +46,11 @@ def call_noalloc(lib, st, L, shape_id=0):
     return rc, F, T
 
 
-@pytest.mark.parametrize("shape,shape_id", [("cube", 0)])
-def test_noalloc_matches_allocating_entry_point_twice(lib, shape, shape_id):
-    cases = [make_state(1500, 0.20, 21, shape), make_state(700, 0.12, 22, shape)]
+@pytest.mark.parametrize("shape,shape_id,phi", [("cube", 0, (0.20, 0.12)), ("cylinder", 1, (0.15, 0.10))])
+def test_noalloc_matches_allocating_entry_point_twice(lib, shape, shape_id, phi):
+    """The cube (125 beads, five-bead columns) and the cylinder (152 beads,
+    eight-bead columns, the kernel instance for templates above 128 beads)."""
+    cases = [make_state(1500, phi[0], 21, shape), make_state(700, phi[1], 22, shape)]
     for st, L, _ in cases:
         rc, F, T = call_noalloc(lib, st, L, shape_id)
         assert rc == 0, lib.rb_last_error().decode()
@@ -56,8 +58,8 @@ def test_noalloc_matches_allocating_entry_point_twice(lib, shape, shape_id):
         Fr = ref["force"].double().cpu().numpy()
         Tr = ref["torque"].double().cpu().numpy()
         assert np.isfinite(F.cpu().numpy()).all()
-        assert rel_err(F[:, :3].double().cpu().numpy(), Fr[:, :3]) < TOL_F32
-        assert rel_err(T[:, :3].double().cpu().numpy(), Tr[:, :3]) < TOL_F32
+        assert_parity(F[:, :3].double().cpu().numpy(), Fr[:, :3], TOL_F32)
+        assert_parity(T[:, :3].double().cpu().numpy(), Tr[:, :3], TOL_F32)
         assert np.abs(F[:, 3].double().cpu().numpy() - Fr[:, 3]).max() <= TOL_F32 * max(
             1.0, np.abs(Fr[:, 3]).max())
 
