@@ -41,11 +41,14 @@ def n_params(width: int, depth: int = 3, n_in: int = N_IN) -> int:
     return 2 * n_in + width * n_in + width + (depth - 1) * (width * width + width) + width + 3
 
 
-def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None, cutoff=None) -> dict:
+def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None, cutoff=None,
+           desc=None) -> dict:
     """Split the flat parameter vector into named FP64 tensors (views).
     sym: optional point group (symmetry.point_group) -- the network then sees
     every pair configuration in its canonical form (symmetry.py).
-    cutoff: optional (r_on, r_off) -- the energy is multiplied by switch()."""
+    cutoff: optional (r_on, r_off) -- the energy is multiplied by switch().
+    desc: None for the 10 features, "paper6" for the paper's six numbers of a
+    cube pair (descriptor.py) in the first six inputs, the other four zero."""
     t = flat if isinstance(flat, torch.Tensor) else torch.as_tensor(np.asarray(flat))
     t = t.to(DT)
     assert t.numel() == n_params(width, depth, n_in), (t.numel(), n_params(width, depth, n_in))
@@ -71,6 +74,8 @@ def unpack(flat, width: int, depth: int = 3, n_in: int = N_IN, sym=None, cutoff=
     assert o == t.numel()
     p["sym"] = sym
     p["cutoff"] = cutoff
+    p["desc"] = desc
+    assert desc in (None, "paper6")
     return p
 
 
@@ -140,11 +145,18 @@ def config_energy(p: dict, s, q_rel):
     canonical form under the point group when the network has one; times the
     smooth cutoff factor when the network has one)."""
     rho = torch.sqrt((s * s).sum(-1))
-    if p.get("sym") is not None:
-        from . import symmetry
+    if p.get("desc") == "paper6":
+        from . import descriptor
 
-        s, q_rel = symmetry.canonical_torch(s, q_rel, p["sym"])
-    E = mlp_energy(p, features(s, q_rel))
+        d = descriptor.describe(s, q_rel).reshape(s.shape[:-1] + (6,))
+        x = torch.cat([d, torch.zeros(d.shape[:-1] + (N_IN - 6,), dtype=d.dtype)], -1)
+    else:
+        if p.get("sym") is not None:
+            from . import symmetry
+
+            s, q_rel = symmetry.canonical_torch(s, q_rel, p["sym"])
+        x = features(s, q_rel)
+    E = mlp_energy(p, x)
     if p.get("cutoff") is not None:
         E = E * switch(rho, *p["cutoff"])
     return E
@@ -229,7 +241,7 @@ def predict_labels(p: dict, s, q_rel, create_graph: bool = False):
 
 
 def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_scale=None,
-                        kT_w=None, sym=None, cutoff=None):
+                        kT_w=None, sym=None, cutoff=None, desc=None):
     """L = mean_b w_b ( |F_j - F_j*|^2 + lam_tau (|tau_i - tau_i*|^2 + |tau_j - tau_j*|^2)
     + lam_E (E - E*)^2 ) with w_b = min(1, exp(-E*/kT_w)) / (1 + (|F_j*|^2 +
     lam_tau (|tau_i*|^2 + |tau_j*|^2)) / f_scale^2); each factor is 1 when its
@@ -247,7 +259,7 @@ def force_matching_loss(flat, width, depth, pair_cfg, labels, lam_tau, lam_E, f_
     pinned by central differences in the tests.
     """
     flat_t = torch.as_tensor(np.asarray(flat, dtype=np.float64)).clone().requires_grad_(True)
-    p = unpack(flat_t, width, depth, sym=sym, cutoff=cutoff)
+    p = unpack(flat_t, width, depth, sym=sym, cutoff=cutoff, desc=desc)
     cfg = torch.as_tensor(np.asarray(pair_cfg, dtype=np.float64))
     lab = torch.as_tensor(np.asarray(labels, dtype=np.float64))
     E, Fj, ti, tj = predict_labels(p, cfg[:, :3], cfg[:, 3:7], create_graph=True)
