@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--train-lam-e", type=float, default=0.1)
     ap.add_argument("--cyl-train-steps", type=int, default=300)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--descriptor-comparison", type=int, default=1)
     ap.add_argument("--no-paper-workload", action="store_true")
     ap.add_argument("--fnet-train-steps", type=int, default=4000)
     ap.add_argument("--paper-nn-train-steps", type=int, default=10000)
@@ -960,6 +961,71 @@ def main():
         finally:
             mlp.set_pair_symmetrised(False)
         del probe
+    # ---- the paper's six-number cube descriptor (SI Sec. 1) against the 10
+    # features: the same training recipe and budget, then model error against
+    # the bead sum on the MD state and the cost of an MD step and of the
+    # network kernel, both networks timed the same way here
+    desc_cmp = None
+    if training is not None and args.descriptor_comparison:
+        from paper_2402_12199_gb300 import train_net
+
+        mlp6, rep6 = train_net.train_network(
+            "cube", WIDTH, DEPTH, n_samples=args.train_samples, steps=args.train_steps, batch=4096,
+            lr=args.train_lr, f_scale=args.train_f_scale, symmetric=True,
+            contact=args.train_contact, cutoff_width=args.train_cutoff_width,
+            lam_E=args.train_lam_e, time_limit_s=60.0, descriptor="paper6")
+
+        def md_and_kernel_ms(net, prec, fb):
+            sd = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
+            sd.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+            sd.set_nn_fallback(fb)
+            sd.forces_nn(net, prec)
+            for _ in range(3):
+                sd.step(1, DT, path=api.RB_PATH_NN, mlp=net, precision=prec)
+            evs = []
+            for _ in range(50):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sd.step(1, DT, path=api.RB_PATH_NN, mlp=net, precision=prec)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            sd.sync()
+            md = statistics.mean(x.elapsed_time(y) for x, y in evs)
+            sd.build_pairs()
+            kd = []
+            for _ in range(10):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sd.eval_pairs(api.RB_PATH_NN, net, prec)
+                b.record(stream)
+                kd.append((a, b))
+            torch.cuda.synchronize()
+            sd.sync()
+            return md, statistics.mean(x.elapsed_time(y) for x, y in kd)
+
+        probe6 = api.System(N_BODIES, [L] * 3, "cube")
+        probe6.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
+        desc_cmp = {"workload": "the bench state; both networks 10-128x3-1 SiLU trained with the "
+                                "same recipe and time budget; model error against the bead sum",
+                    "paper6": {"inputs": "p_x, p_y, p_z, alpha_1, alpha_2, alpha_3 (SI Sec. 1)",
+                               "training": {k: rep6.get(k) for k in ("samples", "steps", "t_train_s",
+                                                                      "heldout_e_F", "heldout_e_tau_i")}},
+                    "features10": {"inputs": "s, q_rel, rho, 1/rho, rho^2 of the canonical "
+                                             "configuration",
+                                   "training": {k: training.get(k) for k in ("samples", "steps",
+                                                                             "heldout_e_F",
+                                                                             "heldout_e_tau_i")}}}
+        for name, net, fb in (("paper6", mlp6, rep6["rho_contact_min"]), ("features10", mlp, rho_fallback)):
+            probe6.set_nn_fallback(fb)
+            for prec in ("bf16", "f16x3"):
+                e = train_net.force_error(probe6, net, prec)
+                md, kern = md_and_kernel_ms(net, prec, fb)
+                desc_cmp[name][prec] = dict(e, ms_per_md_step=md, kernel_ms=kern)
+        del probe6, mlp6
+
     serving = None
     if not args.no_serving and world == 1:
         serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
@@ -1014,6 +1080,7 @@ def main():
             "nn_model_error": model_error, "training": training, "serving": serving,
             "nn_bf16_width256": width256, "nve_drift": drift, "training_cylinders_w256": train_cyl,
             "paper_workload_hphc_nvt": paper_wl, "cylinders_per_component_networks": fnet_leg,
+            "descriptor_paper6_vs_features10": desc_cmp,
             "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "results_finite": e2e_ok,

@@ -371,6 +371,37 @@ rb_status rb_mlp_set_pair_symmetrised(rb_mlp* mlp, int32_t on);
  * a group leaves the arrays unchanged. */
 rb_status rb_nn_canonical(const rb_mlp* mlp, int64_t n, float* cfg, float* labels);
 
+/* --- network input: the paper's six numbers of a cube pair (SI Sec. 1) ---
+ * RB_DESC_FEATURES10 (default): x = [s, q_c, rho, 1/rho, rho^2] as above.
+ * RB_DESC_PAPER6: x = [p_x, p_y, p_z, alpha_1, alpha_2, alpha_3, 0, 0, 0, 0],
+ * the paper's reduction of a cube pair to six numbers:
+ *   p = cube 2's centre in the one of cube 1's face frames with
+ *       p_x >= p_y >= p_z >= 0 (non-negative octant, cube 1's face towards
+ *       cube 2 along x, reflected across y = z when p_z > p_y);
+ *   w = the face normal of cube 2 opposite its face closest to cube 1's
+ *       centre (largest w . p); alpha_1 = angle between w and x (the
+ *       paper's arccos w_x), alpha_2 = atan2(w_z, w_y);
+ *   alpha_3 in [0, pi/2) = the rotation about x that makes cube 2 coincide
+ *       with cube 1 after the two rotations that take w onto x.
+ * Forces and torques are the exact gradients of the network energy through
+ * these numbers (SI Sec. 6 differentiates them numerically): the torque on
+ * cube 2 from d alpha / d theta, the one on cube 1 from angular-momentum
+ * balance.  alpha_2 is undefined where the interacting faces are parallel
+ * (alpha_1 = 0); there its derivative is taken with sin(alpha_1) clamped at
+ * 1e-4.  The last four inputs are constant zeros (set their mu to 0: their
+ * weights then get zero gradient).  RB_DESC_PAPER6 needs the cube's point
+ * group attached (rb_mlp_set_symmetry with the cube template's group; the
+ * canonical frame is the paper's), else RB_EINVAL; it applies to every
+ * network evaluation and to training. */
+enum { RB_DESC_FEATURES10 = 0, RB_DESC_PAPER6 = 1 };
+rb_status rb_mlp_set_descriptor(rb_mlp* mlp, int32_t kind);
+
+/* The network's raw input features (before normalisation) of n explicit
+ * configurations: cfg device n x 8 as rb_nn_pairs' input, x_out device
+ * n x 10 (FP32), on the network's stream.  With a point group the features
+ * are those of the canonical representative. */
+rb_status rb_nn_features(const rb_mlp* mlp, int64_t n, const float* cfg, float* x_out);
+
 /* Network forces and torques for the whole system (same outputs and pair
  * list as rb_forces_beads).  Each unordered pair i < j is evaluated once with
  * i as the reference body.  RB_FP32: SIMT FP32 arithmetic (widths 64, 128,
@@ -530,6 +561,20 @@ rb_status rb_mlp_sync(const rb_mlp* mlp);
  * K in {64, 128}.  Synchronises the stream. */
 rb_status rb_tc_gemm_check(int32_t N, int32_t K, const float* A, const float* B, float* D,
                            void* cuda_stream);
+
+/* Throughput probe of one arithmetic unit, for the rooflines of the pair
+ * kernels (measured peaks instead of unit counts times clock; the paper
+ * reports no rooflines).  Launches SMs x blocks_per_sm CTAs of 256 threads
+ * on `cuda_stream`; each thread runs 8 independent register-resident chains
+ * of `iters` operations of one kind: 0 fma.rn.f32 (FFMA), 1 fma.rn.f32x2
+ * (FFMA2, two FMAs per instruction), 2 ex2.approx.ftz.f32, 3
+ * rcp.approx.ftz.f32, 4 tanh.approx.f32 (the last three on the
+ * multi-function unit).  Asynchronous: time it with events on the stream.
+ * *ops_out (nullable, host) = operations issued by the launch (FMAs for
+ * kinds 0 and 1).  RB_EINVAL for other kinds, blocks_per_sm outside 1..8 or
+ * iters < 1. */
+rb_status rb_peak_probe(int32_t kind, int32_t blocks_per_sm, int64_t iters, void* cuda_stream,
+                        double* ops_out);
 
 /* ------------------------------------------------ per-component networks
  * The paper's cylinder method (Methods; SI Sec. 2): five separate networks

@@ -20,6 +20,7 @@ RB_SHAPE_CUBE, RB_SHAPE_CYLINDER, RB_SHAPE_CUSTOM = 0, 1, 2
 RB_POT_LJ, RB_POT_HPHC, RB_POT_HPHC_PRINTED = 0, 1, 2
 RB_PATH_BEADS, RB_PATH_NN, RB_PATH_FNET = 0, 1, 2
 RB_FP32, RB_BF16, RB_F16X3 = 0, 1, 2
+RB_DESC_FEATURES10, RB_DESC_PAPER6 = 0, 1
 
 
 class RBError(RuntimeError):
@@ -126,6 +127,8 @@ SIGNATURES = {
     "rb_mlp_set_pair_symmetrised": (I32, [P, I32]),
     "rb_pairs_swap_reference": (I32, [I64, P, P, P]),
     "rb_nn_canonical": (I32, [P, I64, P, P]),
+    "rb_mlp_set_descriptor": (I32, [P, I32]),
+    "rb_nn_features": (I32, [P, I64, P, P]),
     "rb_set_nn_fallback": (I32, [P, F32]),
     "rb_set_skin": (I32, [P, F32]),
     "rb_nn_fallback_count": (I32, [P, I64P]),
@@ -147,6 +150,7 @@ SIGNATURES = {
     "rb_train_step": (I32, [P, I64, P, P, F32, F32, F32, F32, DP]),
     "rb_nn_weight_vjp": (I32, [P, I64, P, P, P, P]),
     "rb_tc_gemm_check": (I32, [I32, I32, P, P, P, P]),
+    "rb_peak_probe": (I32, [I32, I32, I64, P, P]),
 }
 
 _lock = threading.Lock()

@@ -11,8 +11,9 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (RB_BF16, RB_F16X3, RB_FP32, RB_PATH_BEADS, RB_PATH_NN, RB_SHAPE_CUBE, RB_SHAPE_CUSTOM,
-                   RB_SHAPE_CYLINDER, RBError, check, load)
+from ._lib import (RB_BF16, RB_DESC_FEATURES10, RB_DESC_PAPER6, RB_F16X3, RB_FP32, RB_PATH_BEADS,
+                   RB_PATH_NN, RB_SHAPE_CUBE, RB_SHAPE_CUSTOM, RB_SHAPE_CYLINDER, RBError, check,
+                   load)
 
 SHAPES = {"cube": RB_SHAPE_CUBE, "cylinder": RB_SHAPE_CYLINDER, "custom": RB_SHAPE_CUSTOM}
 POTENTIALS = {"lj": _lib.RB_POT_LJ, "hphc": _lib.RB_POT_HPHC,
@@ -328,6 +329,20 @@ class MLP:
         r_off (r_off = 0 removes it)."""
         check(load().rb_mlp_set_cutoff(self._h, float(r_on), float(r_off)))
 
+    def set_descriptor(self, kind: str = "paper6"):
+        """rb_mlp_set_descriptor: "paper6" (the paper's six numbers of a cube
+        pair; the cube's point group must be attached) or "features10"."""
+        k = {"features10": RB_DESC_FEATURES10, "paper6": RB_DESC_PAPER6}[kind]
+        check(load().rb_mlp_set_descriptor(self._h, k))
+
+    def features(self, cfg: torch.Tensor) -> torch.Tensor:
+        """rb_nn_features: (n, 10) raw network inputs of (n, 8) configurations."""
+        _dev(cfg, 8)
+        x = torch.empty((cfg.shape[0], 10), dtype=torch.float32, device="cuda")
+        check(load().rb_nn_features(self._h, cfg.shape[0], cfg.data_ptr(), x.data_ptr()))
+        check(load().rb_mlp_sync(self._h))
+        return x
+
     def set_pair_symmetrised(self, on: bool = True):
         """rb_mlp_set_pair_symmetrised: system-level evaluations use the energy
         averaged over both choices of reference body of every pair."""
@@ -363,6 +378,17 @@ def template_symmetry(xyz):
     check(load().rb_template_symmetry(t.ctypes.data, len(t), q.ctypes.data, ctypes.byref(n),
                                       ctypes.byref(inv)))
     return q[:n.value].copy(), bool(inv.value)
+
+
+def peak_probe(kind: str, blocks_per_sm: int, iters: int, stream=None) -> float:
+    """rb_peak_probe (asynchronous on the stream): one launch of the named
+    probe ("ffma", "ffma2", "ex2", "rcp", "tanh"); returns the operations it
+    issues (FMAs for the FMA probes)."""
+    k = {"ffma": 0, "ffma2": 1, "ex2": 2, "rcp": 3, "tanh": 4}[kind]
+    ops = ctypes.c_double()
+    check(load().rb_peak_probe(k, int(blocks_per_sm), int(iters), _stream_handle(stream),
+                               ctypes.byref(ops)))
+    return ops.value
 
 
 def tc_gemm_check(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:

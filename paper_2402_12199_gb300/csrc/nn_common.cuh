@@ -10,6 +10,10 @@
 //   G_s   = dE/ds + (E_rho - E_{1/rho}/rho^2 + 2 rho E_{rho^2}) s / rho
 //   F_j   = -G_s,  tau_j = -1/2 (-G_w v + w G_v + v x G_v) with q_c = (w, v),
 //   tau_i = s x G_s - tau_j           (all in the frame of body i)
+// With the paper's six numbers of a cube pair as the input (desc = 1, SI
+// Sec. 1) the features are x = [p, alpha_1, alpha_2, alpha_3, 0, 0, 0, 0]
+// and tau_j comes from the derivatives of the angles under rotations of
+// cube 2 (paper6_geometry).
 #pragma once
 
 #include "rb_internal.cuh"
@@ -64,6 +68,9 @@ struct PairSrc {
     // system mode: evaluate every listed pair (i, j) with j as the reference
     // body (the second half of the pair-symmetrised energy)
     int swap;
+    // network input: 0 = the 10 features, 1 = the paper's six numbers of a
+    // cube pair (needs the cube's group, sym_cube)
+    int desc;
 };
 
 struct PairDst {
@@ -100,7 +107,65 @@ struct PairGeom {
     bool sym;
     float sym_sg;
     float4 sym_qk, sym_qj;
+    bool paper6;  // the network takes the paper's six numbers
 };
+
+// The paper's six numbers of a cube pair (SI Sec. 1), from the canonical
+// configuration of the cube's group: s with s_x >= s_y >= s_z >= 0 is the
+// paper's frame of cube 1 (octant, face towards cube 2 along x, the y = z
+// reflection), and R(q) cube 2's orientation in it.
+//   w: of cube 2's face normals +-R(q) e_a, the one with the largest w . s
+//      (opposite its face closest to cube 1's centre);
+//   alpha_1 = angle(w, x) = atan2(|(w_y, w_z)|, w_x)  (the paper's arccos w_x,
+//      in the form that keeps its FP32 rounding bounded near 0);
+//   alpha_2 = atan2(w_z, w_y);
+//   alpha_3 = atan2(e2 . c, e1 . c) mod pi/2 for c another face normal of
+//      cube 2, with e1 = dw/dalpha_1 = (-sin a1, cos a1 cos a2, cos a1 sin a2)
+//      and e2 = (0, -sin a2, cos a2): the frame that the two rotations taking
+//      w onto x carry onto y and z, so alpha_3 is the roll about x left after
+//      them, a quarter turn being a symmetry of the cube.
+// Derivatives under a small rotation theta of cube 2 (w -> w + theta x w,
+// c -> c + theta x c; (w, e1, e2) is right-handed):
+//   d alpha_1 / d theta = e2,  d alpha_2 / d theta = -e1 / sin a1,
+//   d alpha_3 / d theta = w + (cos a1 / sin a1) e1.
+// alpha_2 is undefined where the faces are parallel (sin a1 = 0); the
+// derivatives clamp sin a1 at kPaper6MinSin there.
+constexpr float kPaper6MinSin = 1e-4f;
+struct Paper6 {
+    float a1, a2, a3;
+    float3 w, e1, e2;
+    float inv_sin, cot;
+};
+__device__ inline Paper6 paper6_geometry(const float3& s, const float4& q) {
+    const Mat3 R = qmat(q);
+    const float p0 = R.m[0] * s.x + R.m[3] * s.y + R.m[6] * s.z;
+    const float p1 = R.m[1] * s.x + R.m[4] * s.y + R.m[7] * s.z;
+    const float p2 = R.m[2] * s.x + R.m[5] * s.y + R.m[8] * s.z;
+    int a = 0;
+    float pa = p0;
+    if (fabsf(p1) > fabsf(pa)) { a = 1; pa = p1; }
+    if (fabsf(p2) > fabsf(pa)) { a = 2; pa = p2; }
+    const float sg = pa < 0.f ? -1.f : 1.f;
+    const int b = a == 2 ? 0 : a + 1;
+    Paper6 P;
+    P.w = make_float3(sg * R.m[a], sg * R.m[3 + a], sg * R.m[6 + a]);
+    const float3 c = make_float3(R.m[b], R.m[3 + b], R.m[6 + b]);
+    const float r = sqrtf(P.w.y * P.w.y + P.w.z * P.w.z);
+    P.a1 = atan2f(r, P.w.x);
+    P.a2 = atan2f(P.w.z, P.w.y);
+    const float c2 = r > 0.f ? P.w.y / r : 1.f, s2 = r > 0.f ? P.w.z / r : 0.f;
+    P.e1 = make_float3(-r, P.w.x * c2, P.w.x * s2);
+    P.e2 = make_float3(0.f, -s2, c2);
+    const float y = P.e1.x * c.x + P.e1.y * c.y + P.e1.z * c.z;
+    const float z = P.e2.y * c.y + P.e2.z * c.z;
+    const float quarter = 1.5707963267948966f;
+    float a3 = atan2f(z, y);
+    a3 -= quarter * floorf(a3 * (1.f / quarter));
+    P.a3 = a3 >= quarter ? a3 - quarter : (a3 < 0.f ? 0.f : a3);
+    P.inv_sin = 1.f / fmaxf(r, kPaper6MinSin);
+    P.cot = P.w.x * P.inv_sin;
+    return P;
+}
 
 // Symmetry-reduced pair configurations (the paper's reduction of a cube pair
 // to one description per class of symmetric configurations, SI Sec. 1).
@@ -254,6 +319,7 @@ __device__ inline PairGeom pair_geometry(const PairSrc& src, const PairRaw& r) {
     g.sym = false;
     g.sym_sg = 1.f;
     g.sym_qk = g.sym_qj = g.qc;
+    g.paper6 = src.desc == 1;
     float4 qr = g.qc;
     if (r.valid) {
         if (SYSTEM) {
@@ -289,6 +355,17 @@ __device__ inline PairGeom load_pair(const PairSrc& src, int64_t gp, bool valid)
 }
 
 __device__ inline void raw_features(const PairGeom& g, float (&x)[kIn]) {
+    if (g.paper6) {
+        const Paper6 P = paper6_geometry(g.s, g.qc);
+        x[0] = g.s.x;
+        x[1] = g.s.y;
+        x[2] = g.s.z;
+        x[3] = P.a1;
+        x[4] = P.a2;
+        x[5] = P.a3;
+        x[6] = x[7] = x[8] = x[9] = 0.f;
+        return;
+    }
     x[0] = g.s.x;
     x[1] = g.s.y;
     x[2] = g.s.z;
@@ -308,6 +385,7 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
     float gx[kIn];
 #pragma unroll
     for (int k = 0; k < kIn; ++k) gx[k] = gx_in[k];
+    if (g.paper6) gx[6] = gx[7] = gx[8] = gx[9] = 0.f;  // constant inputs
     if (dst.sw_inv > 0.f) {  // E S(rho): every gradient scaled by S, plus E S' along rho
         float S, dS;
         cutoff_switch(g.rho, dst.sw_on, dst.sw_inv, S, dS);
@@ -325,15 +403,26 @@ __device__ inline void write_pair_outputs(const PairDst& dst, int64_t gp, const 
     const float w = g.qc.x;
     const float3 v = make_float3(g.qc.y, g.qc.z, g.qc.w);
     const float3 vxG = cross3(v, Gv);
-    const float3 tj = make_float3(-0.5f * (-Gw * v.x + w * Gv.x + vxG.x),
-                                  -0.5f * (-Gw * v.y + w * Gv.y + vxG.y),
-                                  -0.5f * (-Gw * v.z + w * Gv.z + vxG.z));
+    float3 tj = make_float3(-0.5f * (-Gw * v.x + w * Gv.x + vxG.x),
+                            -0.5f * (-Gw * v.y + w * Gv.y + vxG.y),
+                            -0.5f * (-Gw * v.z + w * Gv.z + vxG.z));
+    if (g.paper6) {  // tau_j = -(dE/dalpha) . (dalpha/dtheta)
+        const Paper6 P = paper6_geometry(s, g.qc);
+        const float c1 = gx[5] * P.cot - gx[4] * P.inv_sin;
+        tj = make_float3(-(gx[3] * P.e2.x + c1 * P.e1.x + gx[5] * P.w.x),
+                         -(gx[3] * P.e2.y + c1 * P.e1.y + gx[5] * P.w.y),
+                         -(gx[3] * P.e2.z + c1 * P.e1.z + gx[5] * P.w.z));
+    }
     const float3 sxG = cross3(s, Gs);
     float3 ti = make_float3(sxG.x - tj.x, sxG.y - tj.y, sxG.z - tj.z);
     float3 Fj = make_float3(-Gs.x, -Gs.y, -Gs.z);
     float3 tjb = tj;
     float3 Gsb = Gs;
     float4 Gq = make_float4(g.sgn * Gw, g.sgn * Gv.x, g.sgn * Gv.y, g.sgn * Gv.z);  // dE/dq (raw sign)
+    if (g.paper6) {  // the tangent gradient whose rotation derivative is -tau_j
+        const float4 t = qmul(make_float4(0.f, -2.f * tj.x, -2.f * tj.y, -2.f * tj.z), g.qc);
+        Gq = make_float4(g.sgn * t.x, g.sgn * t.y, g.sgn * t.z, g.sgn * t.w);
+    }
     if (g.sym) {  // back from the canonical configuration: F = sg R^T F', tau = R^T tau'
         const Mat3 Rk = qmat(g.sym_qk);
         Fj = mulT(Rk, Fj);
@@ -385,7 +474,10 @@ inline rb_status set_fallback(PairDst& dst, rb_system* s) {
     dst.fb_list = s->fb_list;
     dst.fb_count = s->fallback_count;
     dst.fb_rho2 = r * r;
-    RB_CUDA(launch_pdl(k_zero_count, 1, 1, 0, s->stream, s->fallback_count));
+    if (s->fb_zeroed)  // reset by the list build just before (no launch of its own)
+        s->fb_zeroed = false;
+    else
+        RB_CUDA(launch_pdl(k_zero_count, 1, 1, 0, s->stream, s->fallback_count));
     return RB_OK;
 }
 
@@ -430,6 +522,7 @@ inline void set_symmetry(PairSrc& src, const rb_mlp* m) {
     src.n_sym = m->n_sym;
     src.sym_inv = m->sym_inv;
     src.sym_cube = m->sym_cube;
+    src.desc = m->desc;
 }
 
 // nn.cu

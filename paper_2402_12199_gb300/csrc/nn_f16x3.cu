@@ -227,7 +227,9 @@ __host__ __device__ inline Smem smem_layout(int D) {
     return S;
 }
 
-template <bool SYSTEM>
+// PAPER6: the network takes the paper's six numbers (a compile-time switch:
+// the runtime branch of both descriptors costs this kernel register spills).
+template <bool SYSTEM, bool PAPER6>
 __global__ void __launch_bounds__(kThreads, 1)
     k_nn_f16x3(const float* __restrict__ flat, const unsigned char* __restrict__ img, int D,
                PairSrc src, PairDst dst, unsigned* status) {
@@ -311,7 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int64_t gp = tile * kM + row;
         const bool valid = gp < n_total;
-        const PairGeom geo = pair_geometry<SYSTEM>(src, raw);
+        PairGeom geo = pair_geometry<SYSTEM>(src, raw);
+        geo.paper6 = PAPER6;
         if (half == 0) {
             // standardised features in the first 16 columns (10 used), the
             // only ones layer 1's single K step reads
@@ -506,28 +509,36 @@ rb_status nn_f16x3_prepare(rb_mlp* m) {
     return RB_OK;
 }
 
+template <bool SYSTEM, bool P6>
+static rb_status launch_f16x3_impl(const rb_mlp* m, cudaStream_t stream, int grid,
+                                   const PairSrc& src, const PairDst& dst, unsigned* status) {
+    const f16x3::Smem S = f16x3::smem_layout(m->depth);
+    const size_t smem = S.total + 1024;
+    static bool attr = false;
+    if (!attr) {
+        RB_CUDA(cudaFuncSetAttribute(f16x3::k_nn_f16x3<SYSTEM, P6>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const unsigned char* img = static_cast<const unsigned char*>(m->f16x3_img);
+    if (SYSTEM)  // inside an MD step: may start while the list kernels drain
+        RB_CUDA(launch_pdl(f16x3::k_nn_f16x3<SYSTEM, P6>, grid, f16x3::kThreads, smem, stream,
+                           m->params, img, m->depth, src, dst, status));
+    else
+        f16x3::k_nn_f16x3<SYSTEM, P6><<<grid, f16x3::kThreads, smem, stream>>>(
+            m->params, img, m->depth, src, dst, status);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
 template <bool SYSTEM>
 static rb_status launch_f16x3(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
                               const PairDst& dst, unsigned* status) {
     if (!nn_f16x3_supported(m) || !m->f16x3_img)
         return fail(RB_ENOTSUP, "F16X3 network needs width 128 and depth 1..3");
-    const f16x3::Smem S = f16x3::smem_layout(m->depth);
-    const size_t smem = S.total + 1024;
-    static bool attr[2] = {false, false};
-    if (!attr[SYSTEM ? 1 : 0]) {
-        RB_CUDA(cudaFuncSetAttribute(f16x3::k_nn_f16x3<SYSTEM>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[SYSTEM ? 1 : 0] = true;
-    }
-    const unsigned char* img = static_cast<const unsigned char*>(m->f16x3_img);
-    if (SYSTEM)  // inside an MD step: may start while the list kernels drain
-        RB_CUDA(launch_pdl(f16x3::k_nn_f16x3<SYSTEM>, grid, f16x3::kThreads, smem, stream,
-                           m->params, img, m->depth, src, dst, status));
-    else
-        f16x3::k_nn_f16x3<SYSTEM><<<grid, f16x3::kThreads, smem, stream>>>(m->params, img, m->depth,
-                                                                           src, dst, status);
-    RB_CUDA(cudaGetLastError());
-    return RB_OK;
+    return src.desc == RB_DESC_PAPER6
+               ? launch_f16x3_impl<SYSTEM, true>(m, stream, grid, src, dst, status)
+               : launch_f16x3_impl<SYSTEM, false>(m, stream, grid, src, dst, status);
 }
 
 rb_status nn_f16x3_system_async(rb_system* s, const rb_mlp* m, bool swap) {

@@ -73,7 +73,9 @@ __device__ inline bool wg_any(int g, bool flag) {
     return res != 0;
 }
 
-template <bool SYSTEM>
+// PAPER6: the network takes the paper's six numbers (a compile-time switch:
+// the runtime branch of both descriptors costs this kernel register spills).
+template <bool SYSTEM, bool PAPER6>
 __global__ void __launch_bounds__(kThreads, 1)
     k_nn_tc2p(const float* __restrict__ flat, const uint4* __restrict__ img, int D, PairSrc src,
               PairDst dst, unsigned* status) {
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t tile = first; tile < n_tiles && ok; tile += stride) {
         const int64_t gp = tile * kM + row;
         const bool valid = gp < n_total;
-        const PairGeom geo = pair_geometry<SYSTEM>(src, raw);
+        PairGeom geo = pair_geometry<SYSTEM>(src, raw);
+        geo.paper6 = PAPER6;
         {
             // features in the first 16 columns of the activation tile (10
             // used), the only ones layer 1's single K step reads
@@ -289,25 +292,34 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace tc2p
 
-template <bool SYSTEM>
-rb_status launch_tc2p(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
-                      const PairDst& dst, unsigned* status) {
+template <bool SYSTEM, bool P6>
+static rb_status launch_tc2p_impl(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
+                                  const PairDst& dst, unsigned* status) {
     const tc2p::Layout L = tc2p::layout(m->depth);
     const size_t smem = L.total + 1024;
-    static bool attr[2] = {false, false};
-    if (!attr[SYSTEM ? 1 : 0]) {
-        RB_CUDA(cudaFuncSetAttribute(tc2p::k_nn_tc2p<SYSTEM>,
+    static bool attr = false;
+    if (!attr) {
+        RB_CUDA(cudaFuncSetAttribute(tc2p::k_nn_tc2p<SYSTEM, P6>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[SYSTEM ? 1 : 0] = true;
+        attr = true;
     }
     if (SYSTEM)  // inside an MD step: may start while the list kernels drain
-        RB_CUDA(launch_pdl(tc2p::k_nn_tc2p<SYSTEM>, grid, tc2p::kThreads, smem, stream, m->params,
-                           static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status));
+        RB_CUDA(launch_pdl(tc2p::k_nn_tc2p<SYSTEM, P6>, grid, tc2p::kThreads, smem, stream,
+                           m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst,
+                           status));
     else
-        tc2p::k_nn_tc2p<SYSTEM><<<grid, tc2p::kThreads, smem, stream>>>(
+        tc2p::k_nn_tc2p<SYSTEM, P6><<<grid, tc2p::kThreads, smem, stream>>>(
             m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
+}
+
+template <bool SYSTEM>
+rb_status launch_tc2p(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
+                      const PairDst& dst, unsigned* status) {
+    return src.desc == RB_DESC_PAPER6
+               ? launch_tc2p_impl<SYSTEM, true>(m, stream, grid, src, dst, status)
+               : launch_tc2p_impl<SYSTEM, false>(m, stream, grid, src, dst, status);
 }
 
 template rb_status launch_tc2p<true>(const rb_mlp*, cudaStream_t, int, const PairSrc&,

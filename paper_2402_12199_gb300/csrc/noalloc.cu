@@ -16,7 +16,8 @@
 // kNoAllocMaxCells cells.  Larger requests are rejected with RB_EINVAL.
 //
 // All calls share the array and find the previous call's contents in it (the
-// status word and the cell counts are cleared at the start of every call).
+// status word, the list build's hand-off counters and the cell counts are
+// cleared at the start of every call).
 // Calls whose work overlaps on the GPU (different streams, or different host
 // threads without ordering) race on it and give wrong results; serialise them
 // (one stream is enough).  The first call on a device, with that device
@@ -49,9 +50,8 @@ constexpr size_t kOffLowerNbr =
     kOffHalfNbr + align256(sizeof(int) * kNoAllocMaxBodies * kNoAllocMaxNeighbors);
 constexpr size_t kOffHalfOff =
     kOffLowerNbr + align256(sizeof(int) * kNoAllocMaxBodies * kNoAllocMaxNeighbors);
-constexpr size_t kOffLocalOff = kOffHalfOff + align256(sizeof(int) * (kNoAllocMaxBodies + 1));
-constexpr size_t kOffBlockSum = kOffLocalOff + align256(sizeof(int) * kNoAllocMaxBodies);
-constexpr size_t kOffPairs = kOffBlockSum + align256(sizeof(int) * (kNoAllocMaxBodies / 1024 + 2));
+constexpr size_t kOffDone = kOffHalfOff + align256(sizeof(int) * (kNoAllocMaxBodies + 1));
+constexpr size_t kOffPairs = kOffDone + 256;
 constexpr size_t kOffPairF = kOffPairs + align256(sizeof(int2) * kNoAllocMaxPairs);
 constexpr size_t kOffPairTi = kOffPairF + align256(sizeof(float4) * kNoAllocMaxPairs);
 constexpr size_t kOffPairTj = kOffPairTi + align256(sizeof(float4) * kNoAllocMaxPairs);
@@ -179,10 +179,9 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     s.pl.half_nbr = reinterpret_cast<int*>(base + kOffHalfNbr);
     s.pl.lower_nbr = reinterpret_cast<int*>(base + kOffLowerNbr);
     s.pl.half_off = reinterpret_cast<int*>(base + kOffHalfOff);
-    s.pl.local_off = reinterpret_cast<int*>(base + kOffLocalOff);
     s.pos_ref = reinterpret_cast<float4*>(base + kOffPosRef);
     s.rebuild_flag = reinterpret_cast<int*>(base + kOffRebuild);
-    s.pl.block_sum = reinterpret_cast<int*>(base + kOffBlockSum);
+    s.pl.done = reinterpret_cast<int*>(base + kOffDone);
     s.pl.pairs = reinterpret_cast<int2*>(base + kOffPairs);
     s.pair_F = reinterpret_cast<float4*>(base + kOffPairF);
     s.pair_ti = reinterpret_cast<float4*>(base + kOffPairTi);
@@ -200,6 +199,7 @@ extern "C" rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, co
     // and the cell counts (this call's cell grid may differ from the last).
     RB_CUDA(cudaMemcpyAsync(s.tmpl_dev, tmpl, sizeof(float4) * nb, cudaMemcpyHostToDevice, s.stream));
     RB_CUDA(cudaMemsetAsync(s.status_dev, 0, sizeof(unsigned), s.stream));
+    RB_CUDA(cudaMemsetAsync(s.pl.done, 0, sizeof(int) * 2, s.stream));
     RB_CUDA(cudaMemsetAsync(s.cells.count, 0, sizeof(int) * n_cells, s.stream));
     RB_TRY(build_pairs_async(&s, true, false));
     RB_TRY(bead_pairs_async(&s));

@@ -135,8 +135,7 @@ struct PairList {
     int* lower_count = nullptr; // N
     int* lower_nbr = nullptr;   // N x max_nbr (j < i, sorted), replaced by pair ids
     int* half_off = nullptr;    // N + 1
-    int* local_off = nullptr;   // N (offsets inside 1024-body scan blocks)
-    int* block_sum = nullptr;   // N / 1024 + 1 (block totals, then block prefixes)
+    int* done = nullptr;        // 2 counters of the last-CTA hand-offs of a rebuild (0 between)
     int2* pairs = nullptr;      // cap_pairs
     int* n_pairs = nullptr;     // device scalar
 };
@@ -190,6 +189,7 @@ struct rb_mlp {
     int sym_cube = 0;              // the group is the cube's: closed-form choice
     float sw_on = 0.f, sw_off = 0.f;  // smooth cutoff of the energy (sw_off = 0: none)
     int pair_sym = 0;  // pair energy averaged over both choices of reference body
+    int desc = 0;      // network input: RB_DESC_FEATURES10 or RB_DESC_PAPER6 (cube group set)
 };
 
 struct rb_system {
@@ -234,6 +234,7 @@ struct rb_system {
     // evaluated by the bead sum instead (0 = off); count of such pairs
     float nn_fallback_rho = 0.f;
     int* fallback_count = nullptr;
+    bool fb_zeroed = false;  // the list build has reset fallback_count for the next network pass
     int* fb_list = nullptr;  // pair indices the network kernel hands to the bead fallback
     // Verlet skin: the list holds pairs within Rc + skin and is rebuilt only
     // when a centre has moved more than skin / 2 since the last build
@@ -260,7 +261,7 @@ struct rb_system {
 
 namespace rb {
 // system.cu
-rb_status build_pairs_async(rb_system* s, bool force, bool checked);  // force: rebuild regardless of the skin; checked: skin already checked (by the integrator)
+rb_status build_pairs_async(rb_system* s, bool force, bool checked, int* zero_count = nullptr);  // force: rebuild regardless of the skin; checked: skin already checked (by the integrator)
 rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
 rb_status energy_async(rb_system* s);
 // beads.cu

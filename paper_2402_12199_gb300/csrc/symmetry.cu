@@ -155,6 +155,17 @@ __global__ void k_nn_canonical(int64_t n, PairSrc sym, float4* __restrict__ cfg,
     }
 }
 
+// Raw network inputs of explicit configurations (rb_nn_features).
+__global__ void k_nn_features(int64_t n, PairSrc src, float* __restrict__ x_out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const PairGeom g = load_pair<false>(src, b, true);
+    float x[kIn];
+    raw_features(g, x);
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) x_out[b * kIn + k] = x[k];
+}
+
 }  // namespace
 
 // (cfg', u') = canonical configurations and the tangent u mapped with them:
@@ -212,6 +223,8 @@ rb_status rb_template_symmetry(const float* xyz, int32_t n, float* quats_out, in
 rb_status rb_mlp_set_symmetry(rb_mlp* m, const float* quats, int32_t n, int32_t inversion) {
     if (!m) return fail(RB_EINVAL, "null network");
     if (n < 0 || n > 24 || (n > 0 && !quats)) return fail(RB_EINVAL, "need 0..24 rotations");
+    if (m->desc == RB_DESC_PAPER6 && !(n == 24 && inversion))
+        return fail(RB_EINVAL, "the paper's cube descriptor is set: only the cube's group applies");
     if (n == 0) {
         m->n_sym = 0;
         m->sym_inv = 0;
@@ -253,6 +266,8 @@ rb_status rb_mlp_set_symmetry(rb_mlp* m, const float* quats, int32_t n, int32_t 
         }
         cube = found;
     }
+    if (m->desc == RB_DESC_PAPER6 && !cube)
+        return fail(RB_EINVAL, "the paper's cube descriptor is set: only the cube's group applies");
     std::vector<float4> cube_tab(48);
     if (cube) {
         const int orders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
@@ -279,6 +294,31 @@ rb_status rb_mlp_set_symmetry(rb_mlp* m, const float* quats, int32_t n, int32_t 
     m->sym_inv = inversion ? 1 : 0;
     m->sym_cube = cube ? 1 : 0;
     m->version++;  // captured step graphs hold the old table arguments
+    return RB_OK;
+}
+
+rb_status rb_mlp_set_descriptor(rb_mlp* m, int32_t kind) {
+    if (!m) return fail(RB_EINVAL, "null network");
+    if (kind != RB_DESC_FEATURES10 && kind != RB_DESC_PAPER6)
+        return fail(RB_EINVAL, "descriptor: RB_DESC_FEATURES10 or RB_DESC_PAPER6");
+    if (kind == RB_DESC_PAPER6 && !m->sym_cube)
+        return fail(RB_EINVAL, "the paper's six numbers need the cube's point group attached");
+    m->desc = kind;
+    m->version++;  // captured step graphs hold the old pair source
+    return RB_OK;
+}
+
+rb_status rb_nn_features(const rb_mlp* m, int64_t n, const float* cfg, float* x_out) {
+    if (!m) return fail(RB_EINVAL, "null network");
+    if (n < 0 || (n > 0 && (!cfg || !x_out))) return fail(RB_EINVAL, "bad arrays");
+    if (n == 0) return RB_OK;
+    PairSrc src{};
+    set_symmetry(src, m);
+    src.cfg = reinterpret_cast<const float4*>(cfg);
+    src.n_explicit = n;
+    const int threads = 256;
+    k_nn_features<<<(unsigned)((n + threads - 1) / threads), threads, 0, m->stream>>>(n, src, x_out);
+    RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
 

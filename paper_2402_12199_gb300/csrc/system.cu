@@ -64,11 +64,72 @@ __device__ inline double nh_half(double& xi, double& eta, double& K, double h, c
     return sc;
 }
 
+// Hand-off to the last CTA of a kernel: every CTA calls this after its own
+// work; it returns true in all threads of the CTA that finished last, which
+// then sees every other CTA's writes (each thread fences before the CTA
+// barrier, thread 0 fences and counts; the last CTA fences again before it
+// reads).  That CTA resets the counter for the next launch.  No CTA waits on
+// another, so this needs no co-residency.
+__device__ inline bool last_cta_done(int* done) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int prev = atomicAdd(done, 1);
+        is_last = prev == (int)gridDim.x - 1;
+        if (is_last) *done = 0;
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    return true;
+}
+
+// Exclusive scan of the half-row counts by one CTA (the last of k_pair_build):
+// each thread sums a contiguous chunk, the chunk totals are scanned in shared
+// memory, and each thread writes its chunk's offsets; half_off[N] and *total
+// get the pair count (capped, with the overflow bit raised).  Exact integer
+// sums.  Counts written by other CTAs are read past L1 (__ldcg).
+__device__ inline void scan_counts(const int* __restrict__ cnt, int N, int* __restrict__ half_off,
+                                   int* total, int64_t cap_pairs, unsigned* status) {
+    __shared__ int sh[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int chunk = (N + T - 1) / T;
+    const int b = min(t * chunk, N), e = min(b + chunk, N);
+    int sum = 0;
+    for (int k = b; k < e; ++k) sum += __ldcg(cnt + k);
+    sh[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        const int v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    int run = sh[t] - sum;
+    for (int k = b; k < e; ++k) {
+        half_off[k] = run;
+        run += __ldcg(cnt + k);
+    }
+    if (t == T - 1) {
+        int tot = sh[T - 1];
+        if ((int64_t)tot > cap_pairs) {
+            atomicOr(status, ST_NBR_OVERFLOW);
+            tot = (int)cap_pairs;
+        }
+        half_off[N] = tot;
+        *total = tot;
+    }
+}
+
+// zero_count (nullable): a counter this step's later kernels append to (the
+// bead-fallback list), reset here so that it needs no launch of its own.
 __global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, float3 invL,
                               float3 invw, int3 nc, int* __restrict__ count,
                               int* __restrict__ bodies, int cap, unsigned* status,
-                              const int* __restrict__ rebuild) {
+                              const int* __restrict__ rebuild, int* zero_count) {
     pdl_wait();
+    if (zero_count && blockIdx.x == 0 && threadIdx.x == 0) *zero_count = 0;
     if (!*rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -104,12 +165,15 @@ __device__ inline void sort_row(int* row, int n) {
 // mirrored for the reduction).  Hits are appended with warp ballots, then
 // lane 0 sorts each row by j so the list does not depend on the cell fill
 // order or on the lane interleaving.
+// The CTA that finishes last then scans the half-row counts (k_scan_counts).
 __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, float3 invL,
                              float3 invw, int3 nc, const int* __restrict__ count,
                              const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
                              int* __restrict__ half_count, int* __restrict__ half_nbr,
                              int* __restrict__ lower_count, int* __restrict__ lower_nbr,
-                             unsigned* status, const int* __restrict__ rebuild) {
+                             unsigned* status, const int* __restrict__ rebuild,
+                             int* __restrict__ half_off, int* total, int64_t cap_pairs,
+                             int* done) {
     pdl_wait();
     if (!*rebuild) return;
     const int lane = threadIdx.x & 31;
@@ -176,138 +240,56 @@ __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, fl
             lower_count[i] = nl;
         }
     }
-}
-
-// Exclusive scan of the half-row counts in two levels: k_scan_local scans
-// 1024-body blocks (local offsets + one total per block), k_scan_top scans the
-// block totals (single block) and stores the pair count; k_pair_emit adds the
-// block prefix.  All sums are exact integer sums.
-constexpr int kScanBlock = 1024;
-
-__global__ void k_scan_local(const int* __restrict__ cnt, int N, int* __restrict__ local_off,
-                             int* __restrict__ block_sum, const int* __restrict__ rebuild) {
-    pdl_wait();
-    if (!*rebuild) return;
-    __shared__ int warp_tot[32];
-    const int i = blockIdx.x * kScanBlock + threadIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int v = i < N ? cnt[i] : 0;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int t = warp_tot[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        warp_tot[lane] = t;  // inclusive over warps
-    }
-    __syncthreads();
-    const int before = (w > 0 ? warp_tot[w - 1] : 0) + x - v;
-    if (i < N) local_off[i] = before;
-    if (threadIdx.x == kScanBlock - 1) block_sum[blockIdx.x] = warp_tot[31];
-}
-
-__global__ void k_scan_top(int* __restrict__ block_sum, int nb, int N, int* __restrict__ half_off,
-                           int* total, int64_t cap_pairs, unsigned* status,
-                           const int* __restrict__ rebuild) {
-    pdl_wait();
-    if (!*rebuild) return;
-    __shared__ int sh[1024];
-    const int t = threadIdx.x;
-    const int chunk = (nb + 1023) / 1024;
-    const int b = t * chunk, e = min(b + chunk, nb);
-    int sum = 0;
-    for (int k = b; k < e; ++k) sum += block_sum[k];
-    sh[t] = sum;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int v = t >= o ? sh[t - o] : 0;
-        __syncthreads();
-        sh[t] += v;
-        __syncthreads();
-    }
-    int run = sh[t] - sum;
-    for (int k = b; k < e; ++k) {
-        const int c = block_sum[k];
-        block_sum[k] = run;  // exclusive prefix of block k
-        run += c;
-    }
-    if (t == 1023) {
-        int tot = sh[1023];
-        if ((int64_t)tot > cap_pairs) {
-            atomicOr(status, ST_NBR_OVERFLOW);
-            tot = (int)cap_pairs;
-        }
-        half_off[N] = tot;
-        *total = tot;
-    }
+    if (last_cta_done(done)) scan_counts(half_count, N, half_off, total, cap_pairs, status);
 }
 
 // Emit the compact pair list and turn each lower-row entry j (< i) into the
-// index of pair (j, i) inside j's half row.
+// index of pair (j, i) inside j's half row; then remember the positions the
+// list was built for and clear the cell counts for the next rebuild.  The
+// CTA that finishes last lowers the rebuild flag (every CTA has read it by
+// then).
 __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_count,
-                            const int* __restrict__ half_nbr, const int* __restrict__ local_off,
-                            const int* __restrict__ block_prefix, int* __restrict__ half_off,
+                            const int* __restrict__ half_nbr, const int* __restrict__ half_off,
                             const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
                             int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status,
-                            const int* __restrict__ rebuild) {
+                            int n_cells, const float4* __restrict__ pos,
+                            float4* __restrict__ pos_ref, int* __restrict__ cell_count,
+                            int* rebuild, int* done) {
     pdl_wait();
     if (!*rebuild) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int off = local_off[i] + block_prefix[i / kScanBlock];
-    half_off[i] = off;
-    const int n = half_count[i];
-    const int* hrow = half_nbr + (size_t)i * max_nbr;
-    for (int k = 0; k < n; ++k)
-        if (off + k < cap_pairs) pairs[off + k] = make_int2(i, hrow[k]);
-    int* lrow = lower_nbr + (size_t)i * max_nbr;
-    const int nl = lower_count[i];
-    for (int m = 0; m < nl; ++m) {
-        const int j = lrow[m];
-        const int* jrow = half_nbr + (size_t)j * max_nbr;
-        int a = 0, b = half_count[j] - 1, found = -1;
-        while (a <= b) {
-            int mid = (a + b) >> 1;
-            int v = jrow[mid];
-            if (v == i) { found = mid; break; }
-            if (v < i) a = mid + 1; else b = mid - 1;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const int off = half_off[i];
+        const int n = half_count[i];
+        const int* hrow = half_nbr + (size_t)i * max_nbr;
+        for (int k = 0; k < n; ++k)
+            if (off + k < cap_pairs) pairs[off + k] = make_int2(i, hrow[k]);
+        int* lrow = lower_nbr + (size_t)i * max_nbr;
+        const int nl = lower_count[i];
+        for (int m = 0; m < nl; ++m) {
+            const int j = lrow[m];
+            const int* jrow = half_nbr + (size_t)j * max_nbr;
+            int a = 0, b = half_count[j] - 1, found = -1;
+            while (a <= b) {
+                int mid = (a + b) >> 1;
+                int v = jrow[mid];
+                if (v == i) { found = mid; break; }
+                if (v < i) a = mid + 1; else b = mid - 1;
+            }
+            const int offj = half_off[j];
+            if (found < 0 || offj + found >= cap_pairs) {
+                atomicOr(status, ST_NBR_OVERFLOW);
+                lrow[m] = -1;
+            } else {
+                lrow[m] = offj + found;
+            }
         }
-        const int offj = local_off[j] + block_prefix[j / kScanBlock];
-        if (found < 0 || offj + found >= cap_pairs) {
-            atomicOr(status, ST_NBR_OVERFLOW);
-            lrow[m] = -1;
-        } else {
-            lrow[m] = offj + found;
-        }
+        pos_ref[i] = pos[i];
     }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) cell_count[c] = 0;
+    if (last_cta_done(done) && threadIdx.x == 0) *rebuild = 0;
 }
 
-// After a rebuild: remember the positions the list was built for, clear the
-// cell counts for the next rebuild, and lower the flag.
-__global__ void k_pair_finish(int N, int n_cells, const float4* __restrict__ pos,
-                              float4* __restrict__ pos_ref, int* __restrict__ cell_count,
-                              int* rebuild) {
-    pdl_wait();
-    if (!*rebuild) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < N) pos_ref[t] = pos[t];
-    if (t < n_cells) cell_count[t] = 0;
-    __syncthreads();
-    // the flag is read by every CTA above; it is cleared by the last kernel of
-    // the build in stream order, so clear it in a separate one-thread kernel
-}
-
-__global__ void k_flag_clear(int* rebuild) {
-    pdl_wait();
-    *rebuild = 0;
-}
 __global__ void k_flag_set(int* rebuild) { *rebuild = 1; }
 __global__ void k_zero_count(int* count) {
     pdl_wait();
@@ -646,7 +628,13 @@ static inline int blocks_for(int64_t n, int t) { return (int)std::max<int64_t>(1
 static inline float3 f3(const float* a) { return make_float3(a[0], a[1], a[2]); }
 static inline float3 inv3(const float* a) { return make_float3(1.f / a[0], 1.f / a[1], 1.f / a[2]); }
 
-rb_status build_pairs_async(rb_system* s, bool force, bool checked) {
+// The bead-fallback counter when the network pass that follows the list build
+// uses it (the list build resets it), else null.
+static int* fallback_counter(rb_system* s) { return s->nn_fallback_rho > 0.f ? s->fallback_count : nullptr; }
+
+// zero_count (nullable): reset by the first list kernel (the bead-fallback
+// count of a network pass that follows).
+rb_status build_pairs_async(rb_system* s, bool force, bool checked, int* zero_count) {
     const int N = (int)s->N;
     const float3 L = f3(s->box), invL = inv3(s->box);
     const float3 invw = inv3(s->cells.width);
@@ -660,25 +648,20 @@ rb_status build_pairs_async(rb_system* s, bool force, bool checked) {
     }
     RB_CUDA(launch_pdl(k_cell_assign, blocks_for(N, 256), 256, 0, s->stream, s->pos, N, L, invL,
                        invw, nc, s->cells.count, s->cells.bodies, s->cells.cap, s->status_dev,
-                       s->rebuild_flag));
+                       s->rebuild_flag, zero_count));
+    s->fb_zeroed = zero_count != nullptr;
     RB_CUDA(launch_pdl(k_pair_build, std::min(blocks_for((int64_t)N * 32, 256), s->num_sms * 8),
                        256, 0, s->stream, s->pos,
                        N, L, invL, invw, nc, s->cells.count, s->cells.bodies, s->cells.cap,
                        Rl * Rl, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr,
-                       s->pl.lower_count, s->pl.lower_nbr, s->status_dev, s->rebuild_flag));
-    const int nb = (N + kScanBlock - 1) / kScanBlock;
-    RB_CUDA(launch_pdl(k_scan_local, nb, kScanBlock, 0, s->stream, s->pl.half_count, N,
-                       s->pl.local_off, s->pl.block_sum, s->rebuild_flag));
-    RB_CUDA(launch_pdl(k_scan_top, 1, 1024, 0, s->stream, s->pl.block_sum, nb, N, s->pl.half_off,
-                       s->pl.n_pairs, s->pl.cap_pairs, s->status_dev, s->rebuild_flag));
-    RB_CUDA(launch_pdl(k_pair_emit, blocks_for(N, 256), 256, 0, s->stream, N, s->pl.max_nbr,
-                       s->pl.half_count, s->pl.half_nbr, s->pl.local_off, s->pl.block_sum,
+                       s->pl.lower_count, s->pl.lower_nbr, s->status_dev, s->rebuild_flag,
+                       s->pl.half_off, s->pl.n_pairs, s->pl.cap_pairs, s->pl.done));
+    RB_CUDA(launch_pdl(k_pair_emit, std::min(blocks_for(std::max(N, s->cells.n_cells), 256),
+                                             s->num_sms * 8),
+                       256, 0, s->stream, N, s->pl.max_nbr, s->pl.half_count, s->pl.half_nbr,
                        s->pl.half_off, s->pl.lower_count, s->pl.lower_nbr, s->pl.pairs,
-                       s->pl.cap_pairs, s->status_dev, s->rebuild_flag));
-    RB_CUDA(launch_pdl(k_pair_finish, blocks_for(std::max(N, s->cells.n_cells), 256), 256, 0,
-                       s->stream, N, s->cells.n_cells, s->pos, s->pos_ref, s->cells.count,
-                       s->rebuild_flag));
-    RB_CUDA(launch_pdl(k_flag_clear, 1, 1, 0, s->stream, s->rebuild_flag));
+                       s->pl.cap_pairs, s->status_dev, s->cells.n_cells, s->pos, s->pos_ref,
+                       s->cells.count, s->rebuild_flag, s->pl.done + 1));
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -893,8 +876,7 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     ALLOC(s->pl.half_nbr, sizeof(int) * N * mn);
     ALLOC(s->pl.lower_nbr, sizeof(int) * N * mn);
     ALLOC(s->pl.half_off, sizeof(int) * (N + 1));
-    ALLOC(s->pl.local_off, sizeof(int) * N);
-    ALLOC(s->pl.block_sum, sizeof(int) * ((N + 1023) / 1024 + 1));
+    ALLOC(s->pl.done, sizeof(int) * 2);
     ALLOC(s->pl.pairs, sizeof(int2) * cp);
     ALLOC(s->pl.n_pairs, sizeof(int));
     ALLOC(s->pair_F, sizeof(float4) * cp);
@@ -929,6 +911,8 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->pl.n_pairs, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->pl.done, 0, sizeof(int) * 2, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->rebuild_flag, 1, sizeof(int), s->stream);  // no list yet
     if (e == cudaSuccess) e = cudaMemsetAsync(s->fallback_count, 0, sizeof(int), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->angmom, 0, sizeof(float4) * N, s->stream);
@@ -976,7 +960,7 @@ int64_t rb_system_footprint(const rb_system_desc* d) {
     b += 16 * 256;                          // template
     b += 6 * 16 * N;                        // state + forces
     b += 4 * n_cells * (1 + cap);           // cells
-    b += 4 * N * (2 + 2 * mn + 2) + 4 * (N / 1024 + 2);  // rows, offsets
+    b += 4 * N * (2 + 2 * mn + 1) + 4 + 8;  // rows, offsets, counters
     b += 8 * cp + 3 * 16 * cp + 4 * cp;     // pairs + per-pair results + fallback list
     b += 8 * 12 * 2 * sms + 8 * 16 + 64;    // reductions, status
     return b;
@@ -989,8 +973,8 @@ rb_status rb_destroy_system(rb_system* s) {
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     void* ptrs[] = {s->tmpl_dev, s->pos, s->force, s->torque,
                     s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
-                    s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.local_off,
-                    s->pl.block_sum, s->pl.pairs, s->pl.n_pairs,
+                    s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.done,
+                    s->pl.pairs, s->pl.n_pairs,
                     s->pair_F, s->pair_ti, s->pair_tj, s->red_partials, s->red_out, s->status_dev,
                     s->fallback_count, s->fb_list, s->pos_ref, s->rebuild_flag, s->nh,
                     s->ke_part, s->image, s->ref_pos, s->ref_quat, s->ref_image, s->ana_part,
@@ -1034,7 +1018,11 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
         if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
     }
     if (pos) {
-        k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+        // With a skin the list stays valid while every centre is within skin/2
+        // of the positions it was built for, however the centres got there:
+        // the skin check of the next evaluation decides (a state close to the
+        // previous one, as a caller feeding each step's state back, keeps it).
+        if (!(s->skin > 0.f)) k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
         RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
     }
     if (s->nh && (vel || angmom))
@@ -1191,7 +1179,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
     if (!s) return fail(RB_EINVAL, "null system");
     RB_TRY(check_mlp(m));
     RB_TRY(ensure_pair_sym_arrays(s, m));
-    RB_TRY(build_pairs_async(s, false, false));
+    RB_TRY(build_pairs_async(s, false, false, fallback_counter(s)));
     RB_TRY(nn_pairs_system_async(s, m, precision));
     RB_TRY(bead_fallback_async(s));
     RB_TRY(reduce_forces_async(s, 0.f));
@@ -1206,7 +1194,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
 // model: the rb_mlp of RB_PATH_NN or the rb_fnet of RB_PATH_FNET (unused for beads)
 static rb_status eval_forces_async(rb_system* s, int path, const void* model, int precision,
                                    float kick, bool checked = false) {
-    RB_TRY(build_pairs_async(s, false, checked));
+    RB_TRY(build_pairs_async(s, false, checked, path == RB_PATH_NN ? fallback_counter(s) : nullptr));
     if (path == RB_PATH_BEADS) {
         RB_TRY(bead_pairs_async(s));
     } else if (path == RB_PATH_FNET) {

@@ -188,22 +188,35 @@ __global__ void k_colsum(int M, int N, const float* __restrict__ A, int64_t lda,
 __device__ inline float sig_f(float z) { return 1.f / (1.f + __expf(-z)); }
 
 // Features x_hat and the tangent u_hat (x-hat space) of each pair, padded to 16.
+// desc = 1: the paper's six numbers, whose tangent follows from the rotation
+// delta theta = 2 vec(delta q (x) q^*) of cube 2 (paper6_geometry).
 __global__ void k_tr_inputs(int64_t n, const float4* __restrict__ cfg, const float4* __restrict__ ucfg,
-                            const float* __restrict__ flat, FlatLayout fl, float* __restrict__ X,
-                            float* __restrict__ U) {
+                            const float* __restrict__ flat, FlatLayout fl, int desc,
+                            float* __restrict__ X, float* __restrict__ U) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= n) return;
     PairSrc src{};
     src.cfg = cfg;
     src.n_explicit = n;
+    src.desc = desc;
     const PairGeom g = load_pair<false>(src, b, true);
     float x[kIn];
     raw_features(g, x);
     const float4 u0 = ucfg[2 * b], u1 = ucfg[2 * b + 1];
     const float3 sd = make_float3(u0.x, u0.y, u0.z);
     const float rd = (g.s.x * sd.x + g.s.y * sd.y + g.s.z * sd.z) / g.rho;
-    const float xd[kIn] = {sd.x, sd.y, sd.z, g.sgn * u1.x, g.sgn * u1.y, g.sgn * u1.z,
-                           g.sgn * u1.w, rd, -rd / (g.rho * g.rho), 2.f * g.rho * rd};
+    float xd[kIn] = {sd.x, sd.y, sd.z, g.sgn * u1.x, g.sgn * u1.y, g.sgn * u1.z,
+                     g.sgn * u1.w, rd, -rd / (g.rho * g.rho), 2.f * g.rho * rd};
+    if (g.paper6) {
+        const Paper6 P = paper6_geometry(g.s, g.qc);
+        const float4 t = qmul(make_float4(xd[3], xd[4], xd[5], xd[6]), qconj(g.qc));
+        const float3 th = make_float3(2.f * t.y, 2.f * t.z, 2.f * t.w);
+        const float e1t = P.e1.x * th.x + P.e1.y * th.y + P.e1.z * th.z;
+        xd[3] = P.e2.y * th.y + P.e2.z * th.z;
+        xd[4] = -e1t * P.inv_sin;
+        xd[5] = P.w.x * th.x + P.w.y * th.y + P.w.z * th.z + P.cot * e1t;
+        xd[6] = xd[7] = xd[8] = xd[9] = 0.f;
+    }
     for (int k = 0; k < kInPad; ++k) {
         const float isd = k < kIn ? flat[fl.inv_sd + k] : 0.f;
         X[b * kInPad + k] = k < kIn ? (x[k] - flat[fl.mu + k]) * isd : 0.f;
@@ -437,7 +450,7 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
         cfg = reinterpret_cast<const float4*>(w.cfg_c);
         ucfg = reinterpret_cast<const float4*>(w.ucfg_c);
     }
-    k_tr_inputs<<<nblk(B), 256, 0, st>>>(B, cfg, ucfg, flat, fl, w.X, w.U);
+    k_tr_inputs<<<nblk(B), 256, 0, st>>>(B, cfg, ucfg, flat, fl, m->desc, w.X, w.U);
     // forward with tangent
     const float* W1p = m->f32_prep + (int64_t)kInPad * W + (int64_t)(D - 1) * W * W;  // [W][16]
     for (int l = 1; l <= D; ++l) {

@@ -22,7 +22,8 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
                   lam_E: float = 0.0, seed: int = 2, time_limit_s: float | None = None,
                   log_every: int = 0, f_scale: float = 0.0, kT_w: float = 0.0,
                   symmetric: bool = True, contact: float = 1.0, cutoff_width: float = 0.0,
-                  potential: str = "lj", hphc=None, swap_augment: bool = False):
+                  potential: str = "lj", hphc=None, swap_augment: bool = False,
+                  descriptor: str = "features10"):
     """Returns (mlp, report).  With `symmetric` the body's point group is
     attached to the network (rb_mlp_set_symmetry), so it learns one copy of
     every class of symmetry-related configurations, and the feature
@@ -55,13 +56,23 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     rmin = float(rho_c.min().item())
     mu, isd = inputs.feature_normalisation(rmin, Rc)
     group = api.template_symmetry(sysobj.template()) if symmetric else None
+    if descriptor == "paper6" and (group is None or shape != "cube"):
+        raise ValueError("the paper's six numbers describe cube pairs under the cube's group")
     if group is not None:
         probe = api.MLP(width, depth)
         probe.set_params(inputs.mlp_params(width, depth, seed))
         probe.set_symmetry(*group)
-        cc = cfg_tr[:50000].clone()
-        probe.canonical(cc)
-        mu, isd = _feature_stats(cc)
+        if descriptor == "paper6":
+            probe.set_descriptor("paper6")
+            x = probe.features(cfg_tr[:50000].contiguous()).double()
+            mu = np.zeros(10)
+            isd = np.zeros(10)
+            mu[:6] = x[:, :6].mean(0).cpu().numpy()
+            isd[:6] = 1.0 / np.maximum(x[:, :6].std(0).cpu().numpy(), 1e-3)
+        else:
+            cc = cfg_tr[:50000].clone()
+            probe.canonical(cc)
+            mu, isd = _feature_stats(cc)
     e_scale = float(np.std(np.clip(E, np.percentile(E, 1), np.percentile(E, 99)))) or 1.0
     e_shift = float(np.median(E))
     flat = inputs.mlp_params(width, depth, seed + 1, mu=mu, inv_sd=isd, e_scale=e_scale,
@@ -70,6 +81,8 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     mlp.set_params(flat)
     if group is not None:
         mlp.set_symmetry(*group)
+        if descriptor == "paper6":
+            mlp.set_descriptor("paper6")
     if cutoff_width > 0.0:
         mlp.set_cutoff(Rc - cutoff_width, Rc)
     tr = api.Trainer(mlp, batch, lr=lr)
@@ -93,6 +106,7 @@ def train_network(shape: str = "cube", width: int = 128, depth: int = 3, n_sampl
     out = mlp.pairs(cfg_te.contiguous(), "fp32")
     err = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
     report = {"shape": shape, "width": width, "depth": depth, "samples": n_samples,
+              "descriptor": descriptor,
               "swap_augment": swap_augment,
               "symmetry": (f"{len(group[0])} rotations" + (" + inversion" if group[1] else ""))
               if group is not None else None,
@@ -120,13 +134,28 @@ def _feature_stats(cfg):
     return mu, 1.0 / np.maximum(sd, 1e-3)
 
 
+def _err(a, b):
+    return float(torch.linalg.norm(a[:, :3] - b[:, :3]) / torch.linalg.norm(b[:, :3]))
+
+
+def _max_err(a, b):
+    """max_i |a_i - b_i| / rms_i |b_i| over the bodies (the worst body's error
+    in units of the typical force or torque)."""
+    d = torch.linalg.norm(a[:, :3] - b[:, :3], dim=1)
+    rms = torch.sqrt(torch.mean(torch.sum(b[:, :3].double() ** 2, dim=1)))
+    return float(d.max() / rms)
+
+
 def force_error(system: api.System, mlp: api.MLP, precision: str = "bf16"):
-    """NN-versus-bead error of whole-system forces and torques (model error)."""
+    """NN-versus-bead error of whole-system forces and torques (model error):
+    e_F, e_tau (relative L2 over bodies) and the worst body's error over the
+    rms (max_F_over_rms, max_tau_over_rms)."""
     ref = system.forces_beads()
     r = system.forces_nn(mlp, precision)
     system.sync()
-    err = lambda a, b: float(torch.linalg.norm(a[:, :3] - b[:, :3]) / torch.linalg.norm(b[:, :3]))
-    return {"e_F": err(r["force"], ref["force"]), "e_tau": err(r["torque"], ref["torque"])}
+    return {"e_F": _err(r["force"], ref["force"]), "e_tau": _err(r["torque"], ref["torque"]),
+            "max_F_over_rms": _max_err(r["force"], ref["force"]),
+            "max_tau_over_rms": _max_err(r["torque"], ref["torque"])}
 
 
 def fnet_init(width: int, depth: int, Rc: float, cap: float, seed: int = 0) -> np.ndarray:
@@ -188,5 +217,6 @@ def fnet_force_error(system: api.System, f: api.FNet):
     ref = system.forces_beads()
     r = system.forces_fnet(f)
     system.sync()
-    err = lambda a, b: float(torch.linalg.norm(a[:, :3] - b[:, :3]) / torch.linalg.norm(b[:, :3]))
-    return {"e_F": err(r["force"], ref["force"]), "e_tau": err(r["torque"], ref["torque"])}
+    return {"e_F": _err(r["force"], ref["force"]), "e_tau": _err(r["torque"], ref["torque"]),
+            "max_F_over_rms": _max_err(r["force"], ref["force"]),
+            "max_tau_over_rms": _max_err(r["torque"], ref["torque"])}
