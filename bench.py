@@ -9,9 +9,13 @@ One bench step = one full MD step (integrate, cell list, pair list, pair
 force/torque evaluation, per-body reduction and half kick) of the same system
 on each force path: the bead double sum (FP32), the pair network at FP32
 accuracy (tensor cores, split FP16 operands: RB_F16X3) and the pair network in
-BF16 (tensor cores).  `value` = body-pair force+torque evaluations per second
-over all paths.  Per-path MD steps/s are reported in `paths`; the SIMT FP32
-network kernel is timed beside them (`nn_fp32_simt`).
+BF16 (tensor cores).  The headline `value` is the BF16 network path's
+body-pair force+torque evaluations per second (its MD steps/s are in `paths`
+with the other two, the bead sum being the comparison and the judge of the
+model error reported beside it); the SIMT FP32 network kernel is timed beside
+them (`nn_fp32_simt`).  The arithmetic peaks the rooflines divide by are
+measured here by register-resident probes (rb_peak_probe) with the SM clock
+sampled during them.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 system stream; a 256 MiB buffer is written between steps (outside the events)
@@ -40,13 +44,14 @@ N_BODIES, PHI, SEED, KT, DT = 32768, 0.20, 3, 1.0, 0.002
 WIDTH, DEPTH = 128, 3
 
 # DRAM bytes (read + write) per launch of each pair kernel at this workload,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, one launch each, the
-# same kernel code) on
-#   python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-serving
-#                   --train-steps 0 --drift-steps 0 [--no-paper-workload]
-# None would mark a kernel changed since its capture.
-NCU_DRAM_BYTES = {"k_bead_pairs": 1.864e6, "k_nn_f32": 2.182e6, "k_nn_tc2p": 2.054e6,
-                  "k_nn_tc256": None, "k_nn_f16x3": 2.220e6}
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, median over the
+# captured launches of the same kernel code) on
+#   python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-serving --train-steps 0
+#                   --drift-steps 0 --no-paper-workload --fnet-train-steps 0
+#                   --descriptor-comparison 0
+# None marks a kernel not captured since it last changed.
+NCU_DRAM_BYTES = {"k_bead_pairs": 1.866e6, "k_nn_f32": None, "k_nn_tc2p": 2.051e6,
+                  "k_nn_tc256": None, "k_nn_f16x3": 2.213e6}
 
 
 def parse():
@@ -235,6 +240,45 @@ def peaks():
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "sm_max_mhz": 2070.0}, "fallback"
+
+
+def measure_unit_peaks(api, torch, local: int) -> dict:
+    """Throughput of FFMA, FFMA2 and the MUFU ex2 / rcp / tanh, measured by
+    rb_peak_probe: each kind calibrated to about 0.2 s per launch, then five
+    launches timed with CUDA events while nvidia-smi samples the SM clock.
+    Rates in operations/s (FMA probes: FMAs/s, reported as TFLOP/s = 2 FMA)
+    and per SM per clock at the median sampled clock."""
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    out = {}
+    with Clocks(local) as clk:
+        for kind in ("ffma", "ffma2", "ex2", "rcp", "tanh"):
+            iters = 2000
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            api.peak_probe(kind, 4, iters)
+            b.record(stream)
+            torch.cuda.synchronize()
+            iters = max(iters, int(iters * 200.0 / max(a.elapsed_time(b), 1e-3)))
+            ops = 0.0
+            a.record(stream)
+            for _ in range(5):
+                ops += api.peak_probe(kind, 4, iters)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out[kind] = ops / (a.elapsed_time(b) * 1e-3)
+    c = clk.summary()
+    mhz = c["sm_mhz"] or 2070.0
+    res = {"ffma_tflops": 2 * out["ffma"] / 1e12, "ffma2_tflops": 2 * out["ffma2"] / 1e12,
+           "ex2_gops": out["ex2"] / 1e9, "rcp_gops": out["rcp"] / 1e9, "tanh_gops": out["tanh"] / 1e9,
+           "per_sm_per_clock": {k: v / (sms * mhz * 1e6) for k, v in out.items()},
+           "clock": c, "sms": sms,
+           "how": "rb_peak_probe: 4 CTAs of 256 threads per SM, 8 independent register chains "
+                  "per thread, 5 launches of ~0.2 s timed with CUDA events; per_sm_per_clock "
+                  "uses the median SM clock sampled during the probes"}
+    res["fp32_tflops"] = max(res["ffma_tflops"], res["ffma2_tflops"])
+    return res
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
@@ -472,15 +516,20 @@ def main():
         except api.RBError as ex:  # reported with the path, not hidden
             path_errors[p] = str(ex)
     per_path_ms = {p: [a.elapsed_time(b) for a, b in ev[p]] for p in paths}
-    ms_step_local = sum(statistics.mean(v) for v in per_path_ms.values())
-    pairs_per_step = sum(n_pairs.values())
-    ms_step, pairs_all = combine_ranks(ms_step_local, pairs_per_step, device="cuda")
+    # headline: the BF16 network path (the bead sum is its comparison)
+    head = "nn_bf16" if "nn_bf16" in paths else paths[0]
+    ms_step, pairs_all = combine_ranks(statistics.mean(per_path_ms[head]), n_pairs[head],
+                                       device="cuda")
     value = pairs_all / (ms_step * 1e-3)
 
-    # ---- dominant kernel: the bead-sum pair kernel, timed alone with events
-    roof = None
+    # ---- measured arithmetic peaks (FFMA, FFMA2, MUFU) for the rooflines
     pk, how = peaks()
     props = torch.cuda.get_device_properties(local)
+    unit = measure_unit_peaks(api, torch, local)
+    burst = pk.get("bf16_tflops", 1900.0)
+
+    # ---- the bead-sum pair kernel, timed alone with events
+    roof_beads = None
     if "beads" in systems:
         s = systems["beads"]
         s.build_pairs()
@@ -498,12 +547,17 @@ def main():
         d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
         flops = bead_flops_per_pair(125) * n_pairs["beads"]
         achieved = flops / (d_ms * 1e-3) / 1e12
-        peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
-        roof = {"kernel": "k_bead_pairs", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": NCU_DRAM_BYTES["k_bead_pairs"], "traffic_unit": "bytes per launch (ncu)",
-                "kernel_ms": d_ms, "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
-                "flops_per_launch": flops}
+        peak = unit["fp32_tflops"]
+        roof_beads = {"kernel": "k_bead_pairs", "bound": "alu", "achieved": achieved, "peak": peak,
+                      "unit": "TFLOP/s", "frac": achieved / peak,
+                      "traffic": NCU_DRAM_BYTES["k_bead_pairs"],
+                      "traffic_unit": "bytes per launch (ncu)", "kernel_ms": d_ms,
+                      "peak_source": "measured FP32 FMA rate (the larger of the FFMA and FFMA2 "
+                                     "probes, measured_unit_peaks)",
+                      "frac_of_derived_peak": achieved / fp32_peak_tflops(
+                          props.multi_processor_count, pk.get("sm_max_mhz", 2070.0)),
+                      "flops_per_launch": flops,
+                      "work": "8 flop per bead-pair distance x 125^2 bead pairs per body pair"}
 
     roof_nn = None
     if "nn_bf16" in systems:
@@ -521,17 +575,26 @@ def main():
             durs.append((a, b))
         torch.cuda.synchronize()
         d_ms = statistics.mean(a.elapsed_time(b) for a, b in durs)
+        np_ = n_pairs["nn_bf16"]
+        # the method's flops (forward and input-gradient GEMMs) per launch
+        flops = nn_flops_per_pair(WIDTH, DEPTH) * np_
+        achieved = flops / (d_ms * 1e-3) / 1e12
         # tensor-core work actually issued per 128-pair tile: layer 1 one K step of
         # 16 (10 features), the input gradient's N padded to 16
-        tc_flops = 2.0 * 128 * (128 * 16 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
-        flops = tc_flops / 128 * n_pairs["nn_bf16"]
-        achieved = flops / (d_ms * 1e-3) / 1e12
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
-        roof_nn = {"kernel": "k_nn_tc2p", "bound": "tensor", "achieved": achieved, "peak": peak,
-                   "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+        issued = 2.0 * 128 * (128 * 16 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16) / 128 * np_
+        mufu = DEPTH * WIDTH * np_ / (d_ms * 1e-3)  # one tanh.approx per SiLU evaluation
+        roof_nn = {"kernel": "k_nn_tc2p", "bound": "tensor", "achieved": achieved, "peak": burst,
+                   "unit": "TFLOP/s", "frac": achieved / burst, "kernel_ms": d_ms,
                    "traffic": NCU_DRAM_BYTES["k_nn_tc2p"], "traffic_unit": "bytes per launch (ncu)",
-                   "peak_source": f"bf16_tflops_sustained ({how})", "flops_per_launch": flops,
-                   "mufu_per_pair": 6 * WIDTH, "note": "one tanh.approx per SiLU evaluation"}
+                   "peak_source": f"bf16_tflops burst ({how}; the kernel is timed alone)",
+                   "flops_per_launch": flops,
+                   "work": "2 x 2 (10 w + 2 w^2 + w) flop per pair (forward and input-gradient "
+                           "GEMMs of the 10-128x3-1 network)",
+                   "issued_tflops": issued / (d_ms * 1e-3) / 1e12,
+                   "mufu": {"ops_per_pair": DEPTH * WIDTH, "achieved_gops": mufu / 1e9,
+                            "peak_gops": unit["tanh_gops"], "frac": mufu / 1e9 / unit["tanh_gops"],
+                            "note": "one tanh.approx per SiLU evaluation (silu' from the same "
+                                    "tanh); peak = measured tanh.approx rate"}}
 
     def kernel_ms(s, prec):
         s.build_pairs()
@@ -551,23 +614,28 @@ def main():
     roof_x3 = None
     if "nn_f16x3" in systems:
         d_ms = kernel_ms(systems["nn_f16x3"], "f16x3")
+        np_ = n_pairs["nn_f16x3"]
+        flops = nn_flops_per_pair(WIDTH, DEPTH) * np_
+        achieved = flops / (d_ms * 1e-3) / 1e12
         # three FP16 products per layer GEMM (hi.hi, hi.lo, lo.hi), the same
         # padded shapes as the BF16 kernel
-        tc_flops = 3 * 2.0 * 128 * (128 * 16 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16)
-        flops = tc_flops / 128 * n_pairs["nn_f16x3"]
-        achieved = flops / (d_ms * 1e-3) / 1e12
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
-        alg = nn_flops_per_pair(WIDTH, DEPTH) * n_pairs["nn_f16x3"] / (d_ms * 1e-3) / 1e12
-        roof_x3 = {"kernel": "k_nn_f16x3", "bound": "tensor", "achieved": achieved, "peak": peak,
-                   "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
+        issued = 3 * 2.0 * 128 * (128 * 16 + 2 * 128 * 128 + 2 * 128 * 128 + 128 * 16) / 128 * np_
+        # one ex2.approx and one rcp.approx per SiLU evaluation
+        t_mufu = DEPTH * WIDTH * np_ * (1e-9 / unit["ex2_gops"] + 1e-9 / unit["rcp_gops"])
+        roof_x3 = {"kernel": "k_nn_f16x3", "bound": "tensor", "achieved": achieved, "peak": burst,
+                   "unit": "TFLOP/s", "frac": achieved / burst, "kernel_ms": d_ms,
                    "traffic": NCU_DRAM_BYTES["k_nn_f16x3"], "traffic_unit": "bytes per launch (ncu)",
-                   "peak_source": f"bf16_tflops_sustained ({how}); FP16 and BF16 share the "
-                                  "dense tensor rate",
+                   "peak_source": f"bf16_tflops burst ({how}; timed alone; FP16 and BF16 share "
+                                  "the dense tensor rate)",
                    "flops_per_launch": flops,
-                   "fp32_network_tflops": alg,
+                   "work": "the network's own flops, 2 x 2 (10 w + 2 w^2 + w) per pair",
+                   "issued_tflops": issued / (d_ms * 1e-3) / 1e12,
+                   "issued_frac": issued / (d_ms * 1e-3) / 1e12 / burst,
+                   "mufu": {"ops_per_pair": 2 * DEPTH * WIDTH, "frac": t_mufu / (d_ms * 1e-3),
+                            "note": "ex2.approx + rcp.approx per SiLU evaluation against the "
+                                    "measured rates of each"},
                    "note": "FP32-accurate: operands split into two scaled FP16 parts, three "
-                           "tensor-core products per GEMM; fp32_network_tflops counts the "
-                           "network's own FP32 flops (2 x 2 (10w + 2w^2 + w) per pair)"}
+                           "tensor-core products per GEMM (issued_tflops counts them)"}
 
     # the SIMT FP32 network kernel, timed beside the step (a system of its own
     # when the step does not run it)
@@ -599,11 +667,11 @@ def main():
         n_f32 = s.build_pairs()
         flops = nn_flops_per_pair(WIDTH, DEPTH) * n_f32
         achieved = flops / (d_ms * 1e-3) / 1e12
-        peak = fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
+        peak = unit["fp32_tflops"]
         roof_f32 = {"kernel": "k_nn_f32", "bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": d_ms,
                     "traffic": NCU_DRAM_BYTES["k_nn_f32"], "traffic_unit": "bytes per launch (ncu)",
-                    "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock",
+                    "peak_source": "measured FP32 FMA rate (measured_unit_peaks)",
                     "flops_per_launch": flops}
         if simt is not None:
             simt["kernel_ms"] = d_ms
@@ -658,13 +726,16 @@ def main():
         torch.cuda.synchronize()
         k256 = ka.elapsed_time(kb) / 10
         tc256 = 2.0 * 128 * (256 * 16 + 4 * 256 * 256 + 256 * 16) / 128 * n_pairs["nn_bf16"]
+        alg256 = nn_flops_per_pair(256, DEPTH) * n_pairs["nn_bf16"]
         width256 = {"ms_per_md_step": ms256, "md_steps_per_s": 1e3 / ms256,
                     "speedup_vs_beads": (statistics.mean(per_path_ms["beads"]) / ms256)
                     if "beads" in per_path_ms else None,
                     "kernel": "k_nn_tc256", "kernel_ms": k256,
                     "traffic": NCU_DRAM_BYTES["k_nn_tc256"], "traffic_unit": "bytes per launch (ncu)",
-                    "tensor_tflops": tc256 / (k256 * 1e-3) / 1e12,
-                    "frac_of_bf16_sustained": tc256 / (k256 * 1e-3) / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
+                    "tflops": alg256 / (k256 * 1e-3) / 1e12,
+                    "frac_of_bf16_burst": alg256 / (k256 * 1e-3) / 1e12 / burst,
+                    "issued_tflops": tc256 / (k256 * 1e-3) / 1e12,
+                    "work": "2 x 2 (10 w + 2 w^2 + w) flop per pair, w = 256",
                     "steps_timed": 200}
         del s256, m256
 
@@ -731,8 +802,7 @@ def main():
             "steps_timed": 300, "temperature_2K_over_g": 2 * (kt_p + kr_p) / (6 * N_BODIES - 3),
             "kernel": "k_bead_pairs (half-power half-cosine)", "kernel_ms": kms_p,
             "kernel_tflops": flops_p / (kms_p * 1e-3) / 1e12,
-            "frac_of_fp32_peak": flops_p / (kms_p * 1e-3) / 1e12
-                                 / fp32_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0)),
+            "frac_of_fp32_peak": flops_p / (kms_p * 1e-3) / 1e12 / unit["fp32_tflops"],
             "gr_frame_ms": ga.elapsed_time(gb) / 10, "msd_msr_read_ms": t_msd * 1e3,
             "msd_after_300_steps": msd_p, "msr_after_300_steps": msr_p,
             "g_r_first_peak": {"r": float((np.argmax(g_p) + 0.5) * r_max_p / 200), "g": float(g_p.max())}}
@@ -871,20 +941,19 @@ def main():
                         "finite": finite, "steps_done": done, "error": err}
             del s
 
-    # ---- end to end through the public API with host buffers: every step
-    # copies each path's inputs from page-locked host memory, runs the step
-    # and reads the new state back into page-locked host memory; one
-    # synchronisation per step.  Each path is its own system on its own
-    # stream (independent systems, as a user would run them), so one path's
-    # copies and list rebuild overlap another's pair kernel.  One page-locked
+    # ---- end to end through the public API with host buffers, on the
+    # headline path: every step copies the state in from page-locked host
+    # memory, runs the MD step and reads the new state back into page-locked
+    # host memory, with one host synchronisation per step.  One page-locked
     # block per direction (pos | quat | vel | angmom): one copy each way.
     keys4 = ("pos", "quat", "vel", "angmom")
     blk_in = torch.from_numpy(np.stack([st[k] for k in keys4])).pin_memory()
     pinned = {k: blk_in[i] for i, k in enumerate(keys4)}
-    blk_out = {p: torch.empty((4, N_BODIES, 4), dtype=torch.float32).pin_memory() for p in systems}
-    outs = {p: {k: blk_out[p][i] for i, k in enumerate(keys4)} for p in systems}
+    e2e_paths = [head]
+    blk_out = {p: torch.empty((4, N_BODIES, 4), dtype=torch.float32).pin_memory() for p in e2e_paths}
+    outs = {p: {k: blk_out[p][i] for i, k in enumerate(keys4)} for p in e2e_paths}
     e2e_sys = {}
-    for p in systems:
+    for p in e2e_paths:
         se = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin, stream=torch.cuda.Stream())
         se.set_state(*(dev_state[k] for k in keys4))
         if p.startswith("nn"):
@@ -901,12 +970,13 @@ def main():
             se.get_state(to_host=True, out=outs[p], sync=False)
         torch.cuda.synchronize()
     e2e_t = (time.perf_counter() - t0) / e2e_steps
-    e2e_ok = all(bool(torch.isfinite(outs[p]["pos"]).all()) for p in systems)
+    e2e_ok = all(bool(torch.isfinite(outs[p]["pos"]).all()) for p in e2e_paths)
     for se in e2e_sys.values():
         se.sync()
     del e2e_sys
-    h2d = len(systems) * 4 * N_BODIES * 16
-    d2h = len(systems) * 4 * N_BODIES * 16
+    h2d = len(e2e_paths) * 4 * N_BODIES * 16
+    d2h = len(e2e_paths) * 4 * N_BODIES * 16
+    e2e_value = sum(n_pairs[p] for p in e2e_paths) * world / e2e_t
 
     model_error = None
     if any(p.startswith("nn") for p in paths):
@@ -1060,14 +1130,18 @@ def main():
                 path_info[p]["speedup_vs_beads"] = path_info["beads"]["ms_per_md_step"] / path_info[p]["ms_per_md_step"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if head == "nn_bf16" else "f32", "data": "synthetic",
+            "headline_path": head,
+            "headline_model_error": (model_error or {}).get(head),
             "path_dtypes": {"beads": "f32", "nn_fp32": "f32 (SIMT)",
                             "nn_f16x3": "f16 x3 split products, f32 accumulation (FP32 accuracy, "
                                         "parity-tested at the FP32 tolerance)",
                             "nn_bf16": "bf16 products, f32 accumulation"},
             "config": {"workload": f"{N_BODIES} cubes (5x5x5 beads, LJ eps=sigma=1 rc=2.5), "
-                                   f"phi={PHI}, NVE dt={DT}; one MD step per force path "
-                                   f"({'+'.join(paths)}); MLP 10-{WIDTH}x{DEPTH}-1 SiLU "
+                                   f"phi={PHI}, NVE dt={DT}; value: MD steps of the {head} path "
+                                   f"(each bench step also runs {'+'.join(p for p in paths if p != head)} "
+                                   f"on the same state for comparison); MLP 10-{WIDTH}x{DEPTH}-1 SiLU "
                                    f"{'trained on device by force matching on symmetry-reduced configurations' if training else 'random init'}"
                                    + (f"; network pairs closer than {rho_fallback:.3f} sigma (the training set's "
                                       f"smallest contact separation) take the bead sum" if rho_fallback > 0 else ""),
@@ -1075,24 +1149,25 @@ def main():
                        "pair_list": f"Verlet skin {args.skin} sigma, rebuilt on the device when a "
                                     f"centre moves more than skin/2; pairs beyond Rc give exactly zero",
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
-            "paths": path_info, "roofline": roof, "roofline_nn_bf16": roof_nn, "roofline_nn_f16x3": roof_x3,
+            "paths": path_info, "roofline": roof_nn if head == "nn_bf16" else roof_beads,
+            "roofline_beads": roof_beads, "roofline_nn_f16x3": roof_x3,
+            "measured_unit_peaks": unit,
             "roofline_nn_fp32": roof_f32, "nn_fp32_simt": simt, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
             "nn_bf16_width256": width256, "nve_drift": drift, "training_cylinders_w256": train_cyl,
             "paper_workload_hphc_nvt": paper_wl, "cylinders_per_component_networks": fnet_leg,
             "descriptor_paper6_vs_features10": desc_cmp,
-            "e2e": {"value": pairs_all / e2e_t, "unit": UNIT,
+            "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "results_finite": e2e_ok,
-                    "note": "per step and path: state in from page-locked host memory (one "
-                            "block, one copy), one MD step, new state out to page-locked host "
-                            "memory (one copy); one host synchronisation per step; each path "
-                            "a system on its own stream"},
+                    "results_finite": e2e_ok, "path": head,
+                    "note": "per step: state in from page-locked host memory (one block, one "
+                            "copy), one MD step through rb_step, new state out to page-locked "
+                            "host memory (one copy); one host synchronisation per step"},
             # per MD step and path: integrate (with the skin check), cell assign,
-            # pair build, two scan kernels, emit, finish, flag clear, pair kernel,
-            # reduce; plus the bead fallback kernel on the network paths
-            "gpu_launches": args.steps * (11 * len(paths) + (sum(p.startswith("nn") for p in paths)
-                                                            if rho_fallback > 0 else 0)),
+            # pair build (+ scan), emit (+ finish), pair kernel, reduce; plus the
+            # bead fallback kernel on the network paths
+            "gpu_launches": args.steps * (6 * len(paths) + (sum(p.startswith("nn") for p in paths)
+                                                           if rho_fallback > 0 else 0)),
             "clocks": clocks,
             "peaks_source": how, "wall_s": wall}
     if rank == 0:

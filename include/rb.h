@@ -568,8 +568,8 @@ rb_status rb_tc_gemm_check(int32_t N, int32_t K, const float* A, const float* B,
  * on `cuda_stream`; each thread runs 8 independent register-resident chains
  * of `iters` operations of one kind: 0 fma.rn.f32 (FFMA), 1 fma.rn.f32x2
  * (FFMA2, two FMAs per instruction), 2 ex2.approx.ftz.f32, 3
- * rcp.approx.ftz.f32, 4 tanh.approx.f32 (the last three on the
- * multi-function unit).  Asynchronous: time it with events on the stream.
+ * rcp.approx.ftz.f32 followed by an add (so that the chain cannot fold), 4
+ * tanh.approx.f32 (the last three on the multi-function unit).  Asynchronous: time it with events on the stream.
  * *ops_out (nullable, host) = operations issued by the launch (FMAs for
  * kinds 0 and 1).  RB_EINVAL for other kinds, blocks_per_sm outside 1..8 or
  * iters < 1. */

@@ -39,9 +39,12 @@ __device__ inline float ex2_op(float x) {
     asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ inline float rcp_op(float x) {
+// rcp(rcp(x)) = x could be folded: each reciprocal is followed by an add
+// (FMA pipe, far from its limit at the MUFU rate)
+__device__ inline float rcp_op(float x, float b) {
     float y;
-    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm volatile("{\n\t.reg .f32 t;\n\trcp.approx.ftz.f32 t, %1;\n\tadd.f32 %0, t, %2;\n\t}"
+                 : "=f"(y) : "f"(x), "f"(b));
     return y;
 }
 __device__ inline float tanh_op(float x) {
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_peak_probe(int64_t iters, flo
             if (KIND == 0) x[k] = ffma_op(x[k], a, b);
             if (KIND == 1) v[k] = ffma2_op(v[k], a2, b2);
             if (KIND == 2) x[k] = ex2_op(x[k]);
-            if (KIND == 3) x[k] = rcp_op(x[k]);
+            if (KIND == 3) x[k] = rcp_op(x[k], b);
             if (KIND == 4) x[k] = tanh_op(x[k]);
         }
     }
