@@ -139,7 +139,7 @@ static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, const i
     }
     const float3 L = make_float3(s->box[0], s->box[1], s->box[2]);
     const float3 invL = make_float3(1.f / s->box[0], 1.f / s->box[1], 1.f / s->box[2]);
-    const int grid = s->num_sms * occ;
+    const int grid = pair_grid(s, 8, s->num_sms * occ);  // a warp per pair, 8 per CTA
     RB_CUDA(launch_pdl(k_bead_pairs<NP, C, POT>, grid, 256, 0, s->stream, s->pl.pairs, s->pl.n_pairs,
                        s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL, bead_pot(s),
                        cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, sel,

@@ -340,7 +340,7 @@ rb_status fnet_pairs_system_async(rb_system* s, const rb_fnet* f) {
     dst.F = s->pair_F;
     dst.ti = s->pair_ti;
     dst.tj = s->pair_tj;
-    return launch_fnet<true>(f, s->stream, s->num_sms * 8, src, dst);
+    return launch_fnet<true>(f, s->stream, pair_grid(s, kFnThreads, s->num_sms * 8), src, dst);
 }
 
 // ------------------------------------------------------------- training

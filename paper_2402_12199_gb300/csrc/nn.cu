@@ -490,7 +490,7 @@ static rb_status nn_system_pass(rb_system* s, const rb_mlp* m, int precision, bo
     PairDst dst{};
     set_cutoff(dst, m);
     RB_TRY(system_pass_io(s, swap, src, dst));
-    return dispatch_f32<true>(m, s->stream, s->num_sms, src, dst);
+    return dispatch_f32<true>(m, s->stream, pair_grid(s, 32, s->num_sms), src, dst);
 }
 
 // Pair-symmetrised energy E_s = (E(x_ij) + E(x_ji)) / 2 from the two passes.

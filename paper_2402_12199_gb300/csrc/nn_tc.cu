@@ -421,7 +421,7 @@ rb_status nn_tc_system_async(rb_system* s, const rb_mlp* m, bool swap) {
     PairDst dst{};
     set_cutoff(dst, m);
     RB_TRY(system_pass_io(s, swap, src, dst));
-    return launch_tc<true>(m, s->stream, s->num_sms, src, dst, s->status_dev);
+    return launch_tc<true>(m, s->stream, pair_grid(s, tc::kM, s->num_sms), src, dst, s->status_dev);
 }
 
 rb_status nn_tc_pairs_async(const rb_mlp* m, int64_t n, const float4* cfg, float4* out,

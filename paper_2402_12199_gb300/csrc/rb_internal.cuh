@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -261,7 +262,23 @@ struct rb_system {
 
 namespace rb {
 // system.cu
-rb_status build_pairs_async(rb_system* s, bool force, bool checked, int* zero_count = nullptr);  // force: rebuild regardless of the skin; checked: skin already checked (by the integrator)
+rb_status build_pairs_async(rb_system* s, bool force, bool checked, int* zero_count = nullptr);
+// Grid of a pair kernel of a system: enough CTAs for the pairs the system is
+// expected to list (uniform density within Rc + skin, with twice the mean as
+// margin) at `pairs_per_cta` pairs per CTA and pass, at most `max_ctas`.  Pair
+// kernels loop over their pairs, so an underestimate (clustered bodies) only
+// leaves more pairs per CTA; a small system no longer occupies every SM, so
+// the pair kernels of several small systems (serving replicas on their own
+// streams) run side by side.
+inline int pair_grid(const rb_system* s, int pairs_per_cta, int max_ctas) {
+    const double V = (double)s->box[0] * s->box[1] * s->box[2];
+    const double r = (double)s->Rc + s->skin;
+    const double frac = std::min(1.0, 4.18879020478639 * r * r * r / V);
+    const double est = 0.5 * (double)s->N * (double)(s->N - 1) * frac;
+    const double ctas = 2.0 * est / pairs_per_cta + 1.0;
+    return (int)std::max(1.0, std::min((double)max_ctas, ctas));
+}
+  // force: rebuild regardless of the skin; checked: skin already checked (by the integrator)
 rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
 rb_status energy_async(rb_system* s);
 // beads.cu
