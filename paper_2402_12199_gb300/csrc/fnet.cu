@@ -52,6 +52,8 @@ struct rb_fnet_trainer {
     int64_t t = 0;
     float *m = nullptr, *v = nullptr, *grad = nullptr;
     float* work = nullptr;
+    float* sk = nullptr;          // split-K partial tiles of the weight gradients
+    size_t sk_floats = 0;
     double* loss_part = nullptr;  // per block, 5 networks
     double* loss_out = nullptr;
     int loss_blocks = 0;
@@ -479,7 +481,8 @@ static rb_status fn_train_grad(rb_fnet_trainer* tr, int64_t B, const float4* cfg
         const float* HD = H + (int64_t)(D - 1) * B * W;
         k_fn_out<<<nbo, 256, 0, st>>>(B, W, HD, net, Ly.wo, T, Wb, c, r, tr->loss_part + c * nbo);
         // backward: w_o, b_o
-        RB_TRY(sgemm(st, 1, W, (int)B, r, 0, 1, HD, W, 1, g + Ly.wo, W, 1.f, 0.f));
+        RB_TRY(sgemm(st, 1, W, (int)B, r, 0, 1, HD, W, 1, g + Ly.wo, W, 1.f, 0.f, tr->sk,
+                     tr->sk_floats));
         k_colsum<<<1, 256, 0, st>>>((int)B, 1, r, 1, g + Ly.bo, 0);
         k_fn_seed<<<nblk(B * W), 256, 0, st>>>(B, W, r, net + Ly.wo, S + (int64_t)(D - 1) * B * W, G0);
         float* Gl = G0;
@@ -488,7 +491,8 @@ static rb_status fn_train_grad(rb_fnet_trainer* tr, int64_t B, const float4* cfg
             const int inl = l == 0 ? kFnIn : W;
             const float* Hprev = l == 0 ? Xc : H + (int64_t)(l - 1) * B * W;
             // dW_l[o][k] = sum_b G[b][o] Hprev[b][k]
-            RB_TRY(sgemm(st, W, inl, (int)B, Gl, 1, W, Hprev, inl, 1, g + Ly.w(l), inl, 1.f, 0.f));
+            RB_TRY(sgemm(st, W, inl, (int)B, Gl, 1, W, Hprev, inl, 1, g + Ly.w(l), inl, 1.f, 0.f,
+                         tr->sk, tr->sk_floats));
             k_colsum<<<W, 256, 0, st>>>((int)B, W, Gl, W, g + Ly.b(l), 0);
             if (l > 0) {
                 // G_{l-1} = (G_l W_l) * S_{l-1}
@@ -621,6 +625,8 @@ rb_status rb_fnet_trainer_create(rb_fnet* f, int64_t max_batch, float lr, float 
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->v, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->grad, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->work, sizeof(float) * work);
+    t->sk_floats = (size_t)kSplitMax * W * std::max<int64_t>(W, kFnIn);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->sk, sizeof(float) * t->sk_floats);
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->loss_part, sizeof(double) * t->loss_blocks);
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->loss_out, sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(t->m, 0, sizeof(float) * np, f->stream);
@@ -630,6 +636,7 @@ rb_status rb_fnet_trainer_create(rb_fnet* f, int64_t max_batch, float lr, float 
         cudaFree(t->v);
         cudaFree(t->grad);
         cudaFree(t->work);
+        cudaFree(t->sk);
         cudaFree(t->loss_part);
         cudaFree(t->loss_out);
         delete t;
@@ -646,6 +653,7 @@ rb_status rb_fnet_trainer_destroy(rb_fnet_trainer* t) {
     cudaFree(t->v);
     cudaFree(t->grad);
     cudaFree(t->work);
+    cudaFree(t->sk);
     cudaFree(t->loss_part);
     cudaFree(t->loss_out);
     delete t;

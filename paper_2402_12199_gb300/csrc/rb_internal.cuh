@@ -297,9 +297,13 @@ uint64_t fnet_version(const rb_fnet* f);  // bumped whenever its parameters chan
 // train.cu: fixed-order GEMM C = beta C + alpha A B with strided operands
 // (A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn], C row-major), the
 // fixed-order column sum and Adam, shared with the per-component trainer
+constexpr int kSplitMax = 32;  // most split-K parts of one sgemm (ws: kSplitMax x M x N floats)
+// ws (nullable, ws_floats floats): room for split-K partial tiles; with it a
+// long reduction (K >= 512) onto a small C is split along K over more CTAs and
+// summed in a fixed order.
 rb_status sgemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak,
                 const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha,
-                float beta);
+                float beta, float* ws = nullptr, size_t ws_floats = 0);
 __global__ void k_colsum(int M, int N, const float* __restrict__ A, int64_t lda,
                          float* __restrict__ out, int accumulate);
 __global__ void k_adam(int64_t n, int64_t lo, int64_t hi, float* __restrict__ p,
