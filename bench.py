@@ -72,12 +72,12 @@ def parse():
     ap.add_argument("--train-contact", type=float, default=0.85)
     ap.add_argument("--train-cutoff-width", type=float, default=1.0)
     ap.add_argument("--train-lam-e", type=float, default=0.1)
-    ap.add_argument("--cyl-train-steps", type=int, default=300)
+    ap.add_argument("--cyl-train-steps", type=int, default=3000)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--descriptor-comparison", type=int, default=1)
     ap.add_argument("--no-paper-workload", action="store_true")
-    ap.add_argument("--fnet-train-steps", type=int, default=4000)
-    ap.add_argument("--paper-nn-train-steps", type=int, default=10000)
+    ap.add_argument("--fnet-train-steps", type=int, default=20000)
+    ap.add_argument("--paper-nn-train-steps", type=int, default=30000)
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--serving-steps", type=int, default=1000)
     ap.add_argument("--serving-nmax", type=int, default=65536)
