@@ -115,12 +115,15 @@ def combine_ranks(ms_step: float, units: float, device=None):
 
 
 def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=5,
-                rate_factor=8.0, budget_bytes=2 << 30, slots=8):
+                rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None):
     """Serving workload: cube/cylinder replicas with N log-uniform in
     [512, n_max], phi in [0.05, 0.25], kT in [0.5, 1.5], `steps` MD steps each,
     Poisson arrivals at rate_factor / (solo run time of the first request), so
     about rate_factor replicas are in flight; cubes on the network (BF16),
-    cylinders on the bead path (the network is a cube model)."""
+    cylinders on the bead path (the network is a cube model).  solo_rates
+    (optional): pair evaluations/s of each path on one large system alone,
+    {"nn": ..., "beads": ...}; the mix's reference rate then weights them by
+    each path's share of the pairs evaluated."""
     import time as _t
 
     rng = np.random.default_rng(seed)
@@ -169,6 +172,32 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     sat = srv.stats()
     srv.close()
     ok = sum(r["status"] == 0 for r in res)
+    by_path = {"nn": 0.0, "beads": 0.0}
+    for (_, _, _, path), r in zip(reqs, res):
+        key = "nn" if (path == api.RB_PATH_NN and not r["fell_back"]) else "beads"
+        by_path[key] += float(r["pairs"]) * float(r["steps_done"])
+    mix = None
+    if solo_rates and all(solo_rates.get(k) for k in by_path if by_path[k] > 0):
+        tot = sum(by_path.values())
+        ref = tot / sum(v / solo_rates[k] for k, v in by_path.items() if v > 0)
+        # per request: its median step time over the time its pairs take alone on the GPU
+        slow = []
+        for (_, _, _, path), r in zip(reqs, res):
+            key = "nn" if (path == api.RB_PATH_NN and not r["fell_back"]) else "beads"
+            if r["pairs"] > 0 and solo_rates.get(key):
+                slow.append(r["step_ms_p50"] / (1e3 * r["pairs"] / solo_rates[key]))
+        mix = {"pairs_by_path": by_path, "solo_rates": solo_rates, "reference_rate": ref,
+               "slowdown_p50": float(np.percentile(slow, 50)) if slow else None,
+               "slowdown_p99": float(np.percentile(slow, 99)) if slow else None,
+               "slowdown_note": "per request: median step time / (its pairs at its path's solo "
+                                "rate); the step time of a request grows with its size (N spans "
+                                "a factor 128), so step_ms_p99 / step_ms_p50 is dominated by "
+                                "the size mix; this ratio measures the cost of sharing the GPU",
+               "efficiency_poisson": stats["pair_evals"] / makespan / ref,
+               "efficiency_saturated": sat["pair_evals"] / sat_span / ref,
+               "note": "reference_rate: the same pairs at each path's rate on one large system "
+                       "alone (cubes: BF16 network, 32768-cube bench system; cylinders: bead "
+                       "sum, 32768-cylinder system)"}
     return {"requests": n_requests, "completed_ok": ok, "steps_each": steps,
             "workload": f"cube or cylinder with probability 1/2, N log-uniform in [512, {n_max}], "
                         f"phi in [0.05, 0.25], kT in [0.5, 1.5]; Poisson arrivals, about "
@@ -176,6 +205,7 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
                         f"{slots} slots",
             "makespan_s": makespan, "pair_evals_per_s": stats["pair_evals"] / makespan,
             "step_ms_p50": stats["step_ms_p50"], "step_ms_p99": stats["step_ms_p99"],
+            "mix_reference": mix,
             "saturated": {"note": "all requests submitted at once: the server's capacity",
                           "makespan_s": sat_span, "pair_evals_per_s": sat["pair_evals"] / sat_span,
                           "step_ms_p50": sat["step_ms_p50"], "step_ms_p99": sat["step_ms_p99"]},
@@ -183,6 +213,13 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
             "fell_back": sum(r["fell_back"] for r in res),
             "max_rel_energy_drift": max(abs(r["e_end"] - r["e_start"]) / (r["n_bodies"])
                                         for r in res)}
+
+
+def path_info_rate(per_path_ms, n_pairs, p):
+    """Pair evaluations/s of one timed path of the MD step (None if not run)."""
+    if p not in per_path_ms:
+        return None
+    return n_pairs[p] / (statistics.mean(per_path_ms[p]) * 1e-3)
 
 
 def make_inputs(rank=0):
@@ -1111,9 +1148,12 @@ def main():
 
     serving = None
     if not args.no_serving and world == 1:
+        solo = {"nn": path_info_rate(per_path_ms, n_pairs, "nn_bf16")}
+        if fnet_leg is not None:
+            solo["beads"] = fnet_leg["pairs"] / (fnet_leg["ms_per_md_step"]["beads"] * 1e-3)
         serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
                               mlp, n_requests=args.serving_requests, steps=args.serving_steps,
-                              n_max=args.serving_nmax)
+                              n_max=args.serving_nmax, solo_rates=solo)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
