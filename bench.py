@@ -52,6 +52,14 @@ WIDTH, DEPTH = 128, 3
 # None marks a kernel not captured since it last changed.
 NCU_DRAM_BYTES = {"k_bead_pairs": 1.866e6, "k_nn_f32": None, "k_nn_tc2p": 2.051e6,
                   "k_nn_tc256": None, "k_nn_f16x3": 2.213e6}
+# The MD step's HBM-side kernels from the same captures (median launch, no
+# list rebuild due): DRAM bytes read + written and the ncu duration (cold L2,
+# serialised: the events inside the captured step graph cannot time single
+# kernels).  Algorithmic bytes: the reduction reads 48 B per neighbour entry
+# and 64 B per body and writes 64 B per body; the integrator reads and writes
+# 64 B per body.
+NCU_STEP_KERNELS = {"k_reduce": {"dram_bytes": 10.284e6, "ncu_us": 7.8},
+                    "k_integrate_first": {"dram_bytes": 3.706e6, "ncu_us": 5.4}}
 
 
 def parse():
@@ -1204,6 +1212,14 @@ def main():
                        "l2": "256 MiB buffer written between steps, outside the per-step events"},
             "paths": path_info, "roofline": roof_nn if head == "nn_bf16" else roof_beads,
             "roofline_beads": roof_beads, "roofline_nn_f16x3": roof_x3,
+            "roofline_hbm_step_kernels": {
+                k: {"bound": "hbm", "traffic": v["dram_bytes"], "ncu_us": v["ncu_us"],
+                    "achieved_gbs": v["dram_bytes"] / (v["ncu_us"] * 1e-6) / 1e9,
+                    "peak": pk.get("hbm_gbs", 6800.0),
+                    "frac": v["dram_bytes"] / (v["ncu_us"] * 1e-6) / 1e9 / pk.get("hbm_gbs", 6800.0),
+                    "source": "ncu dram__bytes and gpu__time_duration (profiles/"
+                              "launches_32768_cubes_md_step.md)"}
+                for k, v in NCU_STEP_KERNELS.items()},
             "measured_unit_peaks": unit,
             "roofline_nn_fp32": roof_f32, "nn_fp32_simt": simt, "cpu_baseline": cpu,
             "nn_model_error": model_error, "training": training, "serving": serving,
