@@ -52,6 +52,10 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
     constexpr int kSN = C == 0 ? 2 * (kMaxBeads + kPadBeads) : kMaxBeads / 5 + 1 + 2 * (kMaxBeads / 5 + 2);
     __shared__ float4 sN[kSN];
     pdl_wait();
+    // a CTA with no pair (most of them when only the few fallback pairs are
+    // listed) leaves before staging the template
+    const int n_pairs = sel ? *sel_count : *n_pairs_ptr;
+    if ((int64_t)blockIdx.x * (blockDim.x >> 5) >= n_pairs) return;
     if (C == 0) {
         load_template(tmpl, n_beads, pot.rc2_test, sT, sN);
     } else {
@@ -59,7 +63,6 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
         load_columns(tmpl, cols, pot.rc2_test, sN, reinterpret_cast<float*>(sN + kMaxBeads / 5 + 1));
     }
     __syncthreads();
-    const int n_pairs = sel ? *sel_count : *n_pairs_ptr;
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);

@@ -309,10 +309,13 @@ __global__ void k_skin_check(int N, float half_skin2, float3 L, float3 invL,
 }
 
 // Per-body reduction of the per-pair results in a fixed order, no atomics, so
-// results are bit-reproducible: four threads per body take every fourth entry
-// of the body's list (own half row by ascending j, then mirrored pairs by
-// ascending j) and combine with two fixed xor shuffles.  Optionally applies
-// the second velocity-Verlet half kick.
+// results are bit-reproducible: four threads per body; thread t takes entries
+// t, t + 4, ... of the body's own half row (pairs (i, j > i), ascending j) and
+// of its mirrored row (pairs (j < i, i)), then the four combine with two fixed
+// xor shuffles.  The first two mirrored pair ids of each thread and the
+// state the kick needs are loaded together with the row counts, so the chain
+// of dependent loads is two deep.  Optionally applies the second
+// velocity-Verlet half kick.
 __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
                          const int* __restrict__ half_count, const int* __restrict__ lower_count,
                          const int* __restrict__ lower_pair, const float4* __restrict__ pF,
@@ -327,27 +330,36 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
     const bool live = i < N;
     float3 F = make_float3(0.f, 0.f, 0.f), T = make_float3(0.f, 0.f, 0.f);
     float e = 0.f;
+    float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), Lb = vv, qq = vv;
     if (live) {
-        const int off = half_off[i];
-        const int n = (int)min((int64_t)half_count[i], cap_pairs - off);
-        const int nl = lower_count[i];
         const int* lrow = lower_pair + (size_t)i * max_nbr;
-        for (int k = sub; k < n + nl; k += 4) {
-            if (k < n) {
-                const float4 f = pF[off + k];
-                const float4 q = pti[off + k];
-                F.x -= f.x; F.y -= f.y; F.z -= f.z;
-                T.x += q.x; T.y += q.y; T.z += q.z;
-                e += 0.5f * f.w;
-            } else {
-                const int p = lrow[k - n];
-                if (p < 0) continue;
-                const float4 f = pF[p];
-                const float4 q = ptj[p];
-                F.x += f.x; F.y += f.y; F.z += f.z;
-                T.x += q.x; T.y += q.y; T.z += q.z;
-                e += 0.5f * f.w;
-            }
+        // independent loads first: counts, the first mirrored ids, the kick's state
+        const int off = half_off[i];
+        const int hc = half_count[i];
+        const int nl = lower_count[i];
+        const int m0 = sub < max_nbr ? lrow[sub] : -1;
+        const int m1 = sub + 4 < max_nbr ? lrow[sub + 4] : -1;
+        if (kick != 0.f && sub == 0) {
+            vv = vel[i];
+            Lb = angmom[i];
+            qq = quat[i];
+        }
+        const int n = (int)min((int64_t)hc, cap_pairs - off);
+        for (int k = sub; k < n; k += 4) {
+            const float4 f = pF[off + k];
+            const float4 q = pti[off + k];
+            F.x -= f.x; F.y -= f.y; F.z -= f.z;
+            T.x += q.x; T.y += q.y; T.z += q.z;
+            e += 0.5f * f.w;
+        }
+        for (int k = sub; k < nl; k += 4) {
+            const int p = k == sub ? m0 : k == sub + 4 ? m1 : lrow[k];
+            if (p < 0) continue;  // an entry the list build could not resolve (flagged)
+            const float4 f = pF[p];
+            const float4 q = ptj[p];
+            F.x += f.x; F.y += f.y; F.z += f.z;
+            T.x += q.x; T.y += q.y; T.z += q.z;
+            e += 0.5f * f.w;
         }
     }
     float v[7] = {F.x, F.y, F.z, T.x, T.y, T.z, e};
@@ -367,14 +379,12 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
         force[i] = make_float4(F.x, F.y, F.z, e);
         torque[i] = make_float4(T.x, T.y, T.z, 0.f);
         if (kick != 0.f) {
-            float4 vv = vel[i];
             vv.x += kick * F.x * inv_mass;
             vv.y += kick * F.y * inv_mass;
             vv.z += kick * F.z * inv_mass;
             vel[i] = vv;
-            Mat3 R = qmat(quat[i]);
+            Mat3 R = qmat(qq);
             float3 tb = mulT(R, T);
-            float4 Lb = angmom[i];
             Lb.x += kick * tb.x;
             Lb.y += kick * tb.y;
             Lb.z += kick * tb.z;
