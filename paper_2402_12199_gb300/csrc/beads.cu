@@ -37,6 +37,29 @@ namespace rb {
 // (no spills) for larger templates such as the 152-bead cylinder.  POT = 0:
 // Lennard-Jones beads; POT = 1: the half-power half-cosine beads of Eq. 1
 // (either reading).
+// Lanes 0..2 store the pair's results in the space frame: F_j (with E), tau_i,
+// tau_j = T - s x F (T: the bead torques about body i's centre, in i's frame).
+__device__ __forceinline__ void write_pair_result(int lane, int p, const float3 s, const float4 qi,
+                                                  const float (&v)[7], float4* __restrict__ out_F,
+                                                  float4* __restrict__ out_ti,
+                                                  float4* __restrict__ out_tj) {
+    if (lane >= 3) return;
+    const Mat3 Ri = qmat(qi);
+    const float3 F = make_float3(v[0], v[1], v[2]);
+    const float3 T = make_float3(v[3], v[4], v[5]);
+    if (lane == 0) {
+        const float3 Fs = mul(Ri, F);
+        out_F[p] = make_float4(Fs.x, Fs.y, Fs.z, v[6]);
+    } else if (lane == 1) {
+        const float3 ti = mul(Ri, make_float3(-T.x, -T.y, -T.z));
+        out_ti[p] = make_float4(ti.x, ti.y, ti.z, 0.f);
+    } else {
+        const float3 sxF = cross3(s, F);
+        const float3 tj = mul(Ri, make_float3(T.x - sxF.x, T.y - sxF.y, T.z - sxF.z));
+        out_tj[p] = make_float4(tj.x, tj.y, tj.z, 0.f);
+    }
+}
+
 template <int NP, int C, int POT>
 __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
     k_bead_pairs(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
@@ -55,7 +78,7 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
     // a CTA with no pair (most of them when only the few fallback pairs are
     // listed) leaves before staging the template
     const int n_pairs = sel ? *sel_count : *n_pairs_ptr;
-    if ((int64_t)blockIdx.x * (blockDim.x >> 5) >= n_pairs) return;
+    if ((int64_t)blockIdx.x * (blockDim.x >> 5) * (C > 0 ? 8 : 1) >= n_pairs) return;
     if (C == 0) {
         load_template(tmpl, n_beads, pot.rc2_test, sT, sN);
     } else {
@@ -67,6 +90,65 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
     const int warps_per_block = blockDim.x >> 5;
     const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const int nw = gridDim.x * warps_per_block;
+    if constexpr (C > 0) {
+        // kPB pairs per warp at a time: lane l < kPB loads pair l's bodies, forms
+        // its frame and tests it against the box of body i's columns grown by
+        // r_c + r_circ; pairs that cannot interact get their zeros from that
+        // lane, and the warp then works through the others one by one, taking
+        // each pair's geometry from its lane by shuffles.  The global loads of
+        // kPB pairs are in flight together instead of one pair at a time.
+        constexpr int kPB = 8;
+        // per warp and pair: (s, pair index), q_rel, q_i
+        __shared__ float4 sP[8][kPB][3];
+        float4(*wp)[3] = sP[threadIdx.x >> 5];
+        for (int base = gw * kPB; base < n_pairs; base += nw * kPB) {
+            const int t = base + lane;
+            bool work = false;
+            if (lane < kPB && t < n_pairs) {
+                const int p = sel ? sel[t] : t;
+                const int2 ij = pairs[p];
+                const float4 pi = pos[ij.x], pj = pos[ij.y];
+                const float4 qi = quat[ij.x], qj = quat[ij.y];
+                const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), L, invL);
+                if (R.x * R.x + R.y * R.y + R.z * R.z >= cut2) {
+                    if (zero_beyond) {
+                        out_F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        out_ti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        out_tj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                } else {
+                    const float3 sv = mulT(qmat(qi), R);
+                    const float dx = fmaxf(fmaxf(cols.x_lo - sv.x, sv.x - cols.x_hi), 0.f);
+                    const float dy = fmaxf(fmaxf(cols.y_lo - sv.y, sv.y - cols.y_hi), 0.f);
+                    const float dz = fmaxf(fmaxf(cols.z[0] - sv.z, sv.z - cols.z[C - 1]), 0.f);
+                    work = dx * dx + dy * dy + dz * dz <= pot.cull2;
+                    if (work) {
+                        wp[lane][0] = make_float4(sv.x, sv.y, sv.z, __int_as_float(p));
+                        wp[lane][1] = qmul(qconj(qi), qj);
+                        wp[lane][2] = qi;
+                    } else {  // no bead of j within r_c of a bead of i
+                        out_F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        out_ti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        out_tj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+            __syncwarp();  // the slots written above, visible to the whole warp
+            unsigned todo = __ballot_sync(0xffffffffu, work);
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const float4 a0 = wp[l][0];
+                const float3 s = make_float3(a0.x, a0.y, a0.z);
+                float v[7];
+                bead_pair_warp_cols<NP, C, POT>(s, qmat(wp[l][1]), sT, sN,
+                                                reinterpret_cast<const float*>(sN + kMaxBeads / 5 + 1),
+                                                cols, n_beads, pot, lane, v);
+                write_pair_result(lane, __float_as_int(a0.w), s, wp[l][2], v, out_F, out_ti, out_tj);
+            }
+            __syncwarp();  // the batch's slots are read before the next batch writes them
+        }
+    } else {
     for (int t = gw; t < n_pairs; t += nw) {
         const int p = sel ? sel[t] : t;
         const int2 ij = pairs[p];
@@ -81,32 +163,12 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
             }
             continue;
         }
-        const Mat3 Ri = qmat(qi);
         const Mat3 Rr = qmat(qmul(qconj(qi), qj));
-        const float3 s = mulT(Ri, R);
+        const float3 s = mulT(qmat(qi), R);
         float v[7];
-        if constexpr (C == 0) {
-            bead_pair_warp<NP, POT>(s, Rr, sT, sN, n_beads, pot, lane, v);
-        } else {
-            bead_pair_warp_cols<NP, C, POT>(s, Rr, sT, sN,
-                                       reinterpret_cast<const float*>(sN + kMaxBeads / 5 + 1),
-                                       cols, n_beads, pot, lane, v);
-        }
-        if (lane < 3) {
-            const float3 F = make_float3(v[0], v[1], v[2]);
-            const float3 T = make_float3(v[3], v[4], v[5]);
-            if (lane == 0) {
-                const float3 Fs = mul(Ri, F);
-                out_F[p] = make_float4(Fs.x, Fs.y, Fs.z, v[6]);
-            } else if (lane == 1) {
-                const float3 ti = mul(Ri, make_float3(-T.x, -T.y, -T.z));
-                out_ti[p] = make_float4(ti.x, ti.y, ti.z, 0.f);
-            } else {
-                const float3 sxF = cross3(s, F);
-                const float3 tj = mul(Ri, make_float3(T.x - sxF.x, T.y - sxF.y, T.z - sxF.z));
-                out_tj[p] = make_float4(tj.x, tj.y, tj.z, 0.f);
-            }
-        }
+        bead_pair_warp<NP, POT>(s, Rr, sT, sN, n_beads, pot, lane, v);
+        write_pair_result(lane, p, s, qi, v, out_F, out_ti, out_tj);
+    }
     }
 }
 
@@ -130,6 +192,10 @@ BeadPot bead_pot(const rb_system* s) {
     // + r_circ^2 (b within Rc + r_circ of body i's centre, d within r_circ)
     const float big = (s->Rc + s->r_circ) * (s->Rc + s->r_circ) + s->r_circ * s->r_circ;
     p.rc2_test = p.rc2 + 4e-6f * big;
+    // column cull radius r_c + r_circ, widened well past the FP32 rounding of
+    // the test's squared distance (a few ulps of values below (Rc + r_circ)^2)
+    const float rct = (sqrtf(p.rc2_test) + s->r_circ) * 1.0001f + 1e-3f;
+    p.cull2 = rct * rct;
     return p;
 }
 
@@ -220,6 +286,14 @@ void bead_columns(float4* t, int n, BeadCols* c) {
     c->n_cols = ng;
     c->len = len;
     for (int m = 0; m < len; ++m) c->z[m] = out[m].z;
+    c->x_lo = c->x_hi = gx[0];
+    c->y_lo = c->y_hi = gy[0];
+    for (int g = 1; g < ng; ++g) {
+        c->x_lo = std::min(c->x_lo, gx[g]);
+        c->x_hi = std::max(c->x_hi, gx[g]);
+        c->y_lo = std::min(c->y_lo, gy[g]);
+        c->y_hi = std::max(c->y_hi, gy[g]);
+    }
     for (int k = 0; k < n; ++k) t[k] = out[k];
 }
 

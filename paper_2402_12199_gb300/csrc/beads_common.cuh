@@ -23,6 +23,9 @@ struct BeadPot {
     float rc2_test;  // rc2 + a bound on the rounding of the expanded distance test
     int kind;
     float hA, hb, hc, hp;
+    // (r_c + r_circ)^2 with a rounding margin: a column of body i farther
+    // than this from body j's centre has no bead within r_c of any bead of j
+    float cull2 = 3.0e38f;
 };
 
 BeadPot bead_pot(const rb_system* s);
@@ -298,14 +301,34 @@ __device__ inline void load_columns(const float4* __restrict__ tmpl, const BeadC
 // column's share of the expanded form computed once per slot pair:
 //   P = |b|^2 - 2 (b_x x + b_y y),   |b|^2 - 2 b.d = P - 2 b_z z_m,
 // i.e. (2 + C) packed FMAs per C distances of a slot pair instead of 3 C.
-// One warp vote per column; result as in warp_finish.
+// Columns of body i whose segment lies farther than r_c + r_circ from body
+// j's centre s hold no bead within r_c of any bead of j (every bead of j is
+// within r_circ of s): one test per column, a lane per column, decides which
+// columns are scanned at all.  A skipped column would have had no hit, so the
+// sums are those of the full scan.
+// One warp vote per scanned column; result as in warp_finish.
+
+// Lane's share of the column test: column c (< n_cols) near body j's centre.
+template <int C>
+__device__ inline bool column_near(const float3 s, const float4* sC, const BeadCols& cols, int c,
+                                   float cull2) {
+    if (c >= cols.n_cols) return false;
+    const float4 cxy = sC[c];                  // (-2 x_c, -2 x_c, -2 y_c, -2 y_c)
+    const float dx = fmaf(0.5f, cxy.x, s.x);   // s_x - x_c
+    const float dy = fmaf(0.5f, cxy.z, s.y);
+    const float dz = fmaxf(fmaxf(cols.z[0] - s.z, s.z - cols.z[C - 1]), 0.f);
+    return dx * dx + dy * dy + dz * dz <= cull2;
+}
+
 // The column loop of bead_pair_warp_cols: for every column of the fixed
-// template, the expanded distance test of all slots against its C beads
-// (running minimum per bead, one vote), and the exact terms on a hit.
+// template near body j, the expanded distance test of all slots against its
+// C beads (running minimum per bead, one vote), and the exact terms on a hit.
+// Columns in ascending order, as a full scan takes them.
 // ZINT: the column z values are -2, -1, 0, 1, 2 (see bead_pair_warp_cols).
 template <int NP, int C, int POT, bool ZINT>
-__device__ inline void cols_scan(const float4* sC, const float* sTh, const BeadCols& cols,
-                                 const BeadPot& pot, const float2 (&Bx)[NP], const float2 (&By)[NP],
+__device__ inline bool cols_scan(const float3 s, const float4* sC, const float* sTh,
+                                 const BeadCols& cols, const BeadPot& pot, int lane,
+                                 const float2 (&Bx)[NP], const float2 (&By)[NP],
                                  const float2 (&Bz)[NP], const float2 (&BB)[NP], LJAcc<NP>& a) {
     float2 mz[C];  // -2 z_m, duplicated
 #pragma unroll
@@ -316,46 +339,54 @@ __device__ inline void cols_scan(const float4* sC, const float* sTh, const BeadC
         U[q] = __fmul2_rn(Bz[q], make_float2(2.f, 2.f));
         W[q] = __fmul2_rn(Bz[q], make_float2(4.f, 4.f));
     }
-    for (int c = 0; c < cols.n_cols; ++c) {
-        const float4 cxy = sC[c];
-        const float2 mx = make_float2(cxy.x, cxy.y), my = make_float2(cxy.z, cxy.w);
-        float th[C], mn[C];
+    bool any_hit = false;  // warp-uniform
+    for (int c0 = 0; c0 < cols.n_cols; c0 += 32) {
+        unsigned near = __ballot_sync(0xffffffffu, column_near<C>(s, sC, cols, c0 + lane, pot.cull2));
+        while (near) {
+            const int c = c0 + __ffs(near) - 1;
+            near &= near - 1u;
+            const float4 cxy = sC[c];
+            const float2 mx = make_float2(cxy.x, cxy.y), my = make_float2(cxy.z, cxy.w);
+            float th[C], mn[C];
 #pragma unroll
-        for (int m = 0; m < C; ++m) {
-            th[m] = sTh[8 * c + m];
-            mn[m] = 3.0e38f;
-        }
+            for (int m = 0; m < C; ++m) {
+                th[m] = sTh[8 * c + m];
+                mn[m] = 3.0e38f;
+            }
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const float2 P = __ffma2_rn(By[q], my, __ffma2_rn(Bx[q], mx, BB[q]));
-            if constexpr (ZINT) {
-                float2 t[5];
-                t[0] = __fadd2_rn(P, W[q]);
-                t[1] = __fadd2_rn(P, U[q]);
-                t[2] = P;
-                t[3] = __fadd2_rn(P, make_float2(-U[q].x, -U[q].y));
-                t[4] = __fadd2_rn(P, make_float2(-W[q].x, -W[q].y));
+            for (int q = 0; q < NP; ++q) {
+                const float2 P = __ffma2_rn(By[q], my, __ffma2_rn(Bx[q], mx, BB[q]));
+                if constexpr (ZINT) {
+                    float2 t[5];
+                    t[0] = __fadd2_rn(P, W[q]);
+                    t[1] = __fadd2_rn(P, U[q]);
+                    t[2] = P;
+                    t[3] = __fadd2_rn(P, make_float2(-U[q].x, -U[q].y));
+                    t[4] = __fadd2_rn(P, make_float2(-W[q].x, -W[q].y));
 #pragma unroll
-                for (int m = 0; m < C; ++m) mn[m] = fmin3(mn[m], t[m].x, t[m].y);
-            } else {
+                    for (int m = 0; m < C; ++m) mn[m] = fmin3(mn[m], t[m].x, t[m].y);
+                } else {
 #pragma unroll
+                    for (int m = 0; m < C; ++m) {
+                        const float2 t = __ffma2_rn(Bz[q], mz[m], P);
+                        mn[m] = fmin3(mn[m], t.x, t.y);
+                    }
+                }
+            }
+            bool hit = false;
+#pragma unroll
+            for (int m = 0; m < C; ++m) hit |= mn[m] < th[m];
+            if (__any_sync(0xffffffffu, hit)) {
+                any_hit = true;
+#pragma unroll 1
                 for (int m = 0; m < C; ++m) {
-                    const float2 t = __ffma2_rn(Bz[q], mz[m], P);
-                    mn[m] = fmin3(mn[m], t.x, t.y);
+                    const float z2 = sTh[8 * cols.n_cols + m];  // -2 z_m
+                    bead_terms<NP, POT>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
                 }
             }
         }
-        bool hit = false;
-#pragma unroll
-        for (int m = 0; m < C; ++m) hit |= mn[m] < th[m];
-        if (__any_sync(0xffffffffu, hit)) {
-#pragma unroll 1
-            for (int m = 0; m < C; ++m) {
-                const float z2 = sTh[8 * cols.n_cols + m];  // -2 z_m
-                bead_terms<NP, POT>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
-            }
-        }
     }
+    return any_hit;
 }
 
 template <int NP, int C, int POT = 0>
@@ -363,6 +394,15 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
                                            const float4* sC, const float* sTh,
                                            const BeadCols& cols, int n_beads, const BeadPot& pot,
                                            int lane, float (&v)[7]) {
+    // no column near body j (a third of the listed pairs of a dilute system):
+    // every sum is zero, skip the slots as well
+    bool any = false;
+    for (int c = lane; c < cols.n_cols; c += 32) any |= column_near<C>(s, sC, cols, c, pot.cull2);
+    if (!__any_sync(0xffffffffu, any)) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] = 0.f;
+        return;
+    }
     float bx[2 * NP], by[2 * NP], bz[2 * NP];
     float2 Bx[NP], By[NP], Bz[NP], BB[NP];
     slots_setup<NP>(s, Rr, sT, n_beads, lane, bx, by, bz, Bx, By, Bz, BB);
@@ -377,10 +417,13 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
     if constexpr (C == 5)
         zint = cols.z[0] == -2.f && cols.z[1] == -1.f && cols.z[2] == 0.f && cols.z[3] == 1.f &&
                cols.z[4] == 2.f;
-    if (zint)
-        cols_scan<NP, C, POT, true>(sC, sTh, cols, pot, Bx, By, Bz, BB, a);
-    else
-        cols_scan<NP, C, POT, false>(sC, sTh, cols, pot, Bx, By, Bz, BB, a);
+    const bool hit = zint ? cols_scan<NP, C, POT, true>(s, sC, sTh, cols, pot, lane, Bx, By, Bz, BB, a)
+                          : cols_scan<NP, C, POT, false>(s, sC, sTh, cols, pot, lane, Bx, By, Bz, BB, a);
+    if (!hit) {  // no bead pair within r_c: the sums are zero
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] = 0.f;
+        return;
+    }
     warp_finish<NP>(bx, by, bz, a, pot, v);
 }
 

@@ -70,6 +70,7 @@ constexpr int kMaxColLen = 8;
 struct BeadCols {
     int n_cols = 0, len = 0;  // len == 0: no usable column structure
     float z[kMaxColLen] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float x_lo = 0, x_hi = 0, y_lo = 0, y_hi = 0;  // bounding box of the columns' (x, y)
 };
 // Detects the structure for column lengths the bead kernel is built for
 // (5 and 8) and, if found, reorders t[0..n) column by column; c->len = 0
