@@ -240,6 +240,17 @@ def make_inputs(rank=0):
     return st, L, flat
 
 
+def gpu_uuid(local: int):
+    """NVML name of the CUDA device (GPU-<uuid>), or None."""
+    try:
+        import torch
+
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
 
@@ -247,21 +258,74 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    # NVML clock-event reason bits (nvml.h): the four reported by name
+    NVML_REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+                    0x4: "sw_power_cap"}
+
+    def __init__(self, index: int, uuid: str = None):
         self.index = index
+        self.uuid = uuid
         self.p = None
+        self.nv = []  # (sm MHz, max sm MHz, reason bits) read through NVML
+        self._stop = None
+
+    def _nvml_handle(self):
+        """Read-only NVML handle of this GPU (by UUID, else by index), or None."""
+        import ctypes
+
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None, None
+            h = ctypes.c_void_p()
+            ok = False
+            if self.uuid:
+                ok = lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h)) == 0
+            if not ok:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(h)) == 0
+            return (lib, h) if ok else (None, None)
+        except (OSError, AttributeError):
+            return None, None
+
+    def _poll(self):
+        """Clock samples every half millisecond while the timed region runs
+        (nvidia-smi's own loop cannot sample a region of a few milliseconds)."""
+        import ctypes
+
+        lib, h = self._nvml_handle()
+        if lib is None:
+            return
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        mhz, mx, r = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and  # NVML_CLOCK_SM
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0):
+                bits = r.value if reasons_fn and reasons_fn(h, ctypes.byref(r)) == 0 else 0
+                self.nv.append((float(mhz.value), float(mx.value), int(bits)))
+            time.sleep(0.0005)
 
     def __enter__(self):
+        import threading
+
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._poll, daemon=True)
+        self._t.start()
+        t0 = time.perf_counter()  # the poller is reading before the region starts
+        while not self.nv and self._t.is_alive() and time.perf_counter() - t0 < 2.0:
+            time.sleep(0.0005)
         return self
 
     def __exit__(self, *a):
         self.out = ""
+        self._stop.set()
+        self._t.join(timeout=5)
         if self.p is not None:
             self.p.terminate()
             try:
@@ -272,6 +336,12 @@ class Clocks:
 
     def summary(self):
         sm, smax, reasons = [], [], set()
+        for mhz, mx, bits in self.nv:
+            sm.append(mhz)
+            smax.append(mx)
+            for b, n in self.NVML_REASONS.items():
+                if bits & b:
+                    reasons.add(n)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in (self.out or "").strip().splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -288,7 +358,8 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "sources": {"nvml_polls": len(self.nv), "nvidia_smi": len(sm) - len(self.nv)}}
 
 
 def peaks():
@@ -310,7 +381,7 @@ def measure_unit_peaks(api, torch, local: int) -> dict:
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     out = {}
-    with Clocks(local) as clk:
+    with Clocks(local, gpu_uuid(local)) as clk:
         for kind in ("ffma", "ffma2", "ex2", "rcp", "tanh"):
             iters = 2000
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -615,7 +686,7 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev = {p: [] for p in paths}
-    with Clocks(local) as clk:
+    with Clocks(local, gpu_uuid(local)) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
             one_step(ev)

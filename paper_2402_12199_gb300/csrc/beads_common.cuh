@@ -306,7 +306,7 @@ __device__ inline void load_columns(const float4* __restrict__ tmpl, const BeadC
 // within r_circ of s): one test per column, a lane per column, decides which
 // columns are scanned at all.  A skipped column would have had no hit, so the
 // sums are those of the full scan.
-// One warp vote per scanned column; result as in warp_finish.
+// One warp vote per bead of a scanned column; result as in warp_finish.
 
 // Lane's share of the column test: column c (< n_cols) near body j's centre.
 template <int C>
@@ -322,7 +322,7 @@ __device__ inline bool column_near(const float3 s, const float4* sC, const BeadC
 
 // The column loop of bead_pair_warp_cols: for every column of the fixed
 // template near body j, the expanded distance test of all slots against its
-// C beads (running minimum per bead, one vote), and the exact terms on a hit.
+// C beads (running minimum per bead), and the exact terms for the beads with a hit.
 // Columns in ascending order, as a full scan takes them.
 // ZINT: the column z values are -2, -1, 0, 1, 2 (see bead_pair_warp_cols).
 template <int NP, int C, int POT, bool ZINT>
@@ -373,16 +373,18 @@ __device__ inline bool cols_scan(const float3 s, const float4* sC, const float* 
                     }
                 }
             }
-            bool hit = false;
+            // the column's beads with a slot inside the test radius (one vote
+            // each): only those get the exact terms, which for the others
+            // would add masked zeros
+            unsigned zhit = 0;
 #pragma unroll
-            for (int m = 0; m < C; ++m) hit |= mn[m] < th[m];
-            if (__any_sync(0xffffffffu, hit)) {
-                any_hit = true;
-#pragma unroll 1
-                for (int m = 0; m < C; ++m) {
-                    const float z2 = sTh[8 * cols.n_cols + m];  // -2 z_m
-                    bead_terms<NP, POT>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
-                }
+            for (int m = 0; m < C; ++m) zhit |= __any_sync(0xffffffffu, mn[m] < th[m]) ? 1u << m : 0u;
+            any_hit |= zhit != 0;
+            while (zhit) {
+                const int m = __ffs(zhit) - 1;
+                zhit &= zhit - 1u;
+                const float z2 = sTh[8 * cols.n_cols + m];  // -2 z_m
+                bead_terms<NP, POT>(mx, my, make_float2(z2, z2), Bx, By, Bz, pot, a);
             }
         }
     }
