@@ -562,6 +562,24 @@ rb_status rb_mlp_sync(const rb_mlp* mlp);
 rb_status rb_tc_gemm_check(int32_t N, int32_t K, const float* A, const float* B, float* D,
                            void* cuda_stream);
 
+/* FP32-accurate GEMM on the tensor cores, the product every GEMM of the
+ * force-matching training pass (rb_train_grad / rb_train_step,
+ * rb_fnet_train_*) uses (paper, Methods: training of the pair network):
+ *   C = alpha A B + beta C,  A(m, k) = A[m sam + k sak] (M x K),
+ *   B(k, n) = B[k sbk + n sbn] (K x N), C row-major M x N with leading
+ *   dimension ldc >= N; all device arrays, FP32.
+ * Each operand is split into two TF32 parts (x_hi = tf32(x), x_lo = x - x_hi)
+ * and the product is A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated in FP32:
+ * relative error of the order of 1e-6 of sum |A||B|, like an FP32 dot product.
+ * ws (ws_floats floats, may be null / 0): scratch for splitting a long K
+ * (K >= 512) into up to 32 partial products summed in a fixed order; the
+ * result is deterministic either way.  M, N, K in [0, 2^30].  Runs on
+ * `cuda_stream` and synchronises it; RB_EFAULT if a kernel gave up waiting
+ * for its MMAs (bounded waits). */
+rb_status rb_gemm_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t sam, int64_t sak,
+                      const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc,
+                      float alpha, float beta, float* ws, int64_t ws_floats, void* cuda_stream);
+
 /* Throughput probe of one arithmetic unit, for the rooflines of the pair
  * kernels (measured peaks instead of unit counts times clock; the paper
  * reports no rooflines).  Launches SMs x blocks_per_sm CTAs of 256 threads

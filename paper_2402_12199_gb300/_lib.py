@@ -150,6 +150,7 @@ SIGNATURES = {
     "rb_train_step": (I32, [P, I64, P, P, F32, F32, F32, F32, DP]),
     "rb_nn_weight_vjp": (I32, [P, I64, P, P, P, P]),
     "rb_tc_gemm_check": (I32, [I32, I32, P, P, P, P]),
+    "rb_gemm_f32": (I32, [I64, I64, I64, P, I64, I64, P, I64, I64, P, I64, F32, F32, P, I64, P]),
     "rb_peak_probe": (I32, [I32, I32, I64, P, P]),
 }
 

@@ -403,6 +403,27 @@ def tc_gemm_check(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     return D
 
 
+def gemm_f32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None, alpha: float = 1.0,
+             beta: float = 0.0, split_k: bool = True) -> torch.Tensor:
+    """rb_gemm_f32: C = alpha A B + beta C at FP32 accuracy on the tensor cores.
+    A (M x K) and B (K x N) are FP32 CUDA tensors with any strides (in
+    elements); C (M x N) row-major with unit column stride."""
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    if C.stride(1) != 1 or C.shape != (M, N):
+        raise ValueError("C must be M x N with unit column stride")
+    ws = torch.empty(32 * M * N if split_k else 0, dtype=torch.float32, device="cuda")
+    check(load().rb_gemm_f32(M, N, K, A.data_ptr(), A.stride(0), A.stride(1), B.data_ptr(),
+                             B.stride(0), B.stride(1), C.data_ptr(), C.stride(0), float(alpha),
+                             float(beta), ws.data_ptr() if split_k else None, ws.numel(),
+                             torch.cuda.current_stream().cuda_stream))
+    return C
+
+
 class FNet:
     """rb_fnet_*: the five per-component force/torque networks of cylinders."""
 

@@ -473,7 +473,7 @@ static rb_status fn_train_grad(rb_fnet_trainer* tr, int64_t B, const float4* cfg
             float* Hl = H + (int64_t)l * B * W;
             float* Sl = S + (int64_t)l * B * W;
             // Z = Hin W_l^T  (W_l stored [out][in])
-            RB_TRY(sgemm(st, (int)B, W, in, Hin, in, 1, net + Ly.w(l), 1, in, Hl, W, 1.f, 0.f));
+            RB_TRY(sgemm(st, (int)B, W, in, Hin, in, 1, net + Ly.w(l), 1, in, Hl, W, 1.f, 0.f, nullptr));
             k_fn_act<<<nblk(B * W), 256, 0, st>>>(B, W, net + Ly.b(l), Hl, Hl, Sl);
             Hin = Hl;
             in = W;
@@ -481,7 +481,7 @@ static rb_status fn_train_grad(rb_fnet_trainer* tr, int64_t B, const float4* cfg
         const float* HD = H + (int64_t)(D - 1) * B * W;
         k_fn_out<<<nbo, 256, 0, st>>>(B, W, HD, net, Ly.wo, T, Wb, c, r, tr->loss_part + c * nbo);
         // backward: w_o, b_o
-        RB_TRY(sgemm(st, 1, W, (int)B, r, 0, 1, HD, W, 1, g + Ly.wo, W, 1.f, 0.f, tr->sk,
+        RB_TRY(sgemm(st, 1, W, (int)B, r, 0, 1, HD, W, 1, g + Ly.wo, W, 1.f, 0.f, nullptr, tr->sk,
                      tr->sk_floats));
         k_colsum<<<1, 256, 0, st>>>((int)B, 1, r, 1, g + Ly.bo, 0);
         k_fn_seed<<<nblk(B * W), 256, 0, st>>>(B, W, r, net + Ly.wo, S + (int64_t)(D - 1) * B * W, G0);
@@ -492,11 +492,12 @@ static rb_status fn_train_grad(rb_fnet_trainer* tr, int64_t B, const float4* cfg
             const float* Hprev = l == 0 ? Xc : H + (int64_t)(l - 1) * B * W;
             // dW_l[o][k] = sum_b G[b][o] Hprev[b][k]
             RB_TRY(sgemm(st, W, inl, (int)B, Gl, 1, W, Hprev, inl, 1, g + Ly.w(l), inl, 1.f, 0.f,
-                         tr->sk, tr->sk_floats));
+                         nullptr, tr->sk, tr->sk_floats));
             k_colsum<<<W, 256, 0, st>>>((int)B, W, Gl, W, g + Ly.b(l), 0);
             if (l > 0) {
                 // G_{l-1} = (G_l W_l) * S_{l-1}
-                RB_TRY(sgemm(st, (int)B, W, W, Gl, W, 1, net + Ly.w(l), W, 1, Gn, W, 1.f, 0.f));
+                RB_TRY(sgemm(st, (int)B, W, W, Gl, W, 1, net + Ly.w(l), W, 1, Gn, W, 1.f, 0.f,
+                             nullptr));
                 k_fn_mul<<<nblk(B * W), 256, 0, st>>>(B * W, Gn, S + (int64_t)(l - 1) * B * W);
                 std::swap(Gl, Gn);
             }
@@ -667,6 +668,11 @@ rb_status rb_fnet_train_grad(rb_fnet_trainer* t, int64_t batch, const float* cfg
         return fail(RB_EINVAL, "batch must be in [1, max_batch] with cfg and labels");
     RB_TRY(fn_train_grad(t, batch, reinterpret_cast<const float4*>(cfg),
                          reinterpret_cast<const float4*>(labels), loss_host));
+    if (loss_host) {  // the loss read is a synchronisation point: report a timed-out GEMM
+        bool bad = false;
+        RB_TRY(gemm_status_take(t->f->stream, &bad));
+        if (bad) return fail(RB_EFAULT, "tensor-core GEMM timed out waiting for an MMA");
+    }
     if (grad_out)
         RB_CUDA(cudaMemcpyAsync(grad_out, t->grad, sizeof(float) * kFnNets * t->f->net_floats,
                                 cudaMemcpyDeviceToDevice, t->f->stream));

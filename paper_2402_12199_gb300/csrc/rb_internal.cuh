@@ -302,9 +302,14 @@ constexpr int kSplitMax = 32;  // most split-K parts of one sgemm (ws: kSplitMax
 // ws (nullable, ws_floats floats): room for split-K partial tiles; with it a
 // long reduction (K >= 512) onto a small C is split along K over more CTAs and
 // summed in a fixed order.
+// gemm_tc.cu: FP32-accurate GEMM (split TF32 on the tensor cores), C = alpha A B + beta C
+// with A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]; a timed-out MMA wait
+// sets ST_TC_TIMEOUT in *status (or in the module's own word, read by gemm_status_take).
+// ws (ws_floats floats): partial tiles of a split K reduction (K >= 512), optional.
 rb_status sgemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak,
                 const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha,
-                float beta, float* ws = nullptr, size_t ws_floats = 0);
+                float beta, unsigned* status, float* ws = nullptr, size_t ws_floats = 0);
+rb_status gemm_status_take(cudaStream_t st, bool* timed_out);  // synchronises st
 __global__ void k_colsum(int M, int N, const float* __restrict__ A, int64_t lda,
                          float* __restrict__ out, int accumulate);
 __global__ void k_adam(int64_t n, int64_t lo, int64_t hi, float* __restrict__ p,

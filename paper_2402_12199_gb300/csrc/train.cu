@@ -108,118 +108,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// ------------------------------------------------------------- generic SGEMM
-// C[m][n] = beta C[m][n] + alpha sum_k A(m, k) B(k, n), A(m, k) = A[m sam + k sak],
-// B(k, n) = B[k sbk + n sbn], C row-major with leading dimension ldc.
-// 64 x 64 tiles, 256 threads, 4 x 4 outputs per thread; fixed k order.  The
-// operand tiles are loaded with consecutive threads along the operand's unit
-// stride (coalesced for either layout of A).  Split K (gridDim.z > 1): CTA z
-// sums k in [z kchunk, (z + 1) kchunk) and stores its partial tile at
-// C + z csplit (alpha and beta are then applied by k_splitk_sum).
-constexpr int GT = 64, GK = 16;
-__global__ void __launch_bounds__(256)
-    k_sgemm(int M, int N, int K, const float* __restrict__ A, int64_t sam, int64_t sak,
-            const float* __restrict__ B, int64_t sbk, int64_t sbn, float* __restrict__ C,
-            int64_t ldc, float alpha, float beta, int kchunk, int64_t csplit) {
-    __shared__ float As[GK][GT + 4];
-    __shared__ float Bs[GK][GT + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    const bool a_mfast = sam == 1;
-    float acc[4][4] = {};
-    for (int k0 = kb; k0 < ke; k0 += GK) {
-        for (int t = threadIdx.x; t < GT * GK; t += 256) {
-            const int mm = a_mfast ? t % GT : t / GK, kk = a_mfast ? t / GT : t % GK;
-            const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < ke) ? A[gm * sam + gk * sak] : 0.f;
-            const int nn = t % GT, kbb = t / GT;
-            const int gn = n0 + nn, gk2 = k0 + kbb;
-            Bs[kbb][nn] = (gn < N && gk2 < ke) ? B[gk2 * sbk + gn * sbn] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-    const bool split = gridDim.z > 1;
-    float* Cz = C + blockIdx.z * csplit;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + ty * 4 + i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + tx * 4 + j;
-            if (gn >= N) continue;
-            float* c = Cz + gm * ldc + gn;
-            if (split)
-                *c = acc[i][j];
-            else
-                *c = beta == 0.f ? alpha * acc[i][j] : fmaf(beta, *c, alpha * acc[i][j]);
-        }
-    }
-}
-
-// C = beta C + alpha (sum over the S partial tiles, in order).
-__global__ void k_splitk_sum(int M, int N, int S, const float* __restrict__ P, float* __restrict__ C,
-                             int64_t ldc, float alpha, float beta) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)M * N) return;
-    const int m = (int)(t / N), n = (int)(t % N);
-    float sum = 0.f;
-    for (int z = 0; z < S; ++z) sum += P[(int64_t)z * M * N + t];
-    float* c = C + m * ldc + n;
-    *c = beta == 0.f ? alpha * sum : fmaf(beta, *c, alpha * sum);
-}
-
-static int device_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
-
-rb_status sgemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak,
-                const float* B, int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha,
-                float beta, float* ws, size_t ws_floats) {
-    const int gm = (M + GT - 1) / GT, gn = (N + GT - 1) / GT;
-    int S = 1;
-    if (ws && K >= 512) {  // a long reduction on a small output: split K to fill the GPU
-        const int want = (2 * device_sms() + gm * gn - 1) / (gm * gn);
-        const size_t fit = ws_floats / ((size_t)M * N);
-        S = std::max(1, std::min({want, K / 256, kSplitMax, (int)std::min<size_t>(fit, 1 << 20)}));
-    }
-    if (S == 1) {
-        k_sgemm<<<dim3(gn, gm, 1), 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha,
-                                                  beta, K, 0);
-        RB_CUDA(cudaGetLastError());
-        return RB_OK;
-    }
-    const int kchunk = (((K + S - 1) / S) + GK - 1) / GK * GK;
-    S = (K + kchunk - 1) / kchunk;
-    k_sgemm<<<dim3(gn, gm, S), 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, ws, N, 1.f, 0.f,
-                                              kchunk, (int64_t)M * N);
-    const int64_t mn = (int64_t)M * N;
-    k_splitk_sum<<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(M, N, S, ws, C, ldc, alpha, beta);
-    RB_CUDA(cudaGetLastError());
-    return RB_OK;
-}
-
 // out[n] = accumulate * out[n] + sum_m A[m][n] (fixed-order tree per column).
 __global__ void k_colsum(int M, int N, const float* __restrict__ A, int64_t lda,
                          float* __restrict__ out, int accumulate) {
@@ -513,8 +401,8 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
         const float* Uin = l == 1 ? w.U : w.Hd[l - 2];
         const int K = l == 1 ? kInPad : W;
         const float* Wl = l == 1 ? W1p : flat + fl.W_(l, W);  // [W][K] row-major
-        RB_TRY(sgemm(st, (int)B, W, K, Ain, K, 1, Wl, 1, K, w.Z[l - 1], W, 1.f, 0.f));
-        RB_TRY(sgemm(st, (int)B, W, K, Uin, K, 1, Wl, 1, K, w.Zd[l - 1], W, 1.f, 0.f));
+        RB_TRY(sgemm(st, (int)B, W, K, Ain, K, 1, Wl, 1, K, w.Z[l - 1], W, 1.f, 0.f, m->status_dev));
+        RB_TRY(sgemm(st, (int)B, W, K, Uin, K, 1, Wl, 1, K, w.Zd[l - 1], W, 1.f, 0.f, m->status_dev));
         k_tr_act<<<nblk(B * W), 256, 0, st>>>(B, W, flat + fl.b_(l, W), w.Z[l - 1], w.Zd[l - 1],
                                               w.H[l - 1], w.Hd[l - 1]);
     }
@@ -533,16 +421,18 @@ static rb_status weight_vjp(rb_trainer* tr, int64_t B, const float4* cfg, const 
         const int K = l == 1 ? kInPad : W;
         float* gW = l == 1 ? w.G16 : grad + fl.W_(l, W);
         // gW[o][i] = sum_b Az[b][o] Hp[b][i] + Azd[b][o] Hdp[b][i]
-        RB_TRY(sgemm(st, W, K, (int)B, w.Ah[cur], 1, W, Hp, K, 1, gW, K, 1.f, 0.f, w.SK,
-                     tr_split_floats(W)));
-        RB_TRY(sgemm(st, W, K, (int)B, w.Ahd[cur], 1, W, Hdp, K, 1, gW, K, 1.f, 1.f, w.SK,
-                     tr_split_floats(W)));
+        RB_TRY(sgemm(st, W, K, (int)B, w.Ah[cur], 1, W, Hp, K, 1, gW, K, 1.f, 0.f, m->status_dev,
+                     w.SK, tr_split_floats(W)));
+        RB_TRY(sgemm(st, W, K, (int)B, w.Ahd[cur], 1, W, Hdp, K, 1, gW, K, 1.f, 1.f, m->status_dev,
+                     w.SK, tr_split_floats(W)));
         if (l == 1) {
             k_tr_w1<<<nblk(W * kIn), 256, 0, st>>>(W, w.G16, grad + fl.W1);
         } else {
             const float* Wl = flat + fl.W_(l, W);  // a_{l-1} = a_l W_l: B(k=o, n=i) = W[o][i]
-            RB_TRY(sgemm(st, (int)B, W, W, w.Ah[cur], W, 1, Wl, W, 1, w.Ah[1 - cur], W, 1.f, 0.f));
-            RB_TRY(sgemm(st, (int)B, W, W, w.Ahd[cur], W, 1, Wl, W, 1, w.Ahd[1 - cur], W, 1.f, 0.f));
+            RB_TRY(sgemm(st, (int)B, W, W, w.Ah[cur], W, 1, Wl, W, 1, w.Ah[1 - cur], W, 1.f, 0.f,
+                         m->status_dev));
+            RB_TRY(sgemm(st, (int)B, W, W, w.Ahd[cur], W, 1, Wl, W, 1, w.Ahd[1 - cur], W, 1.f, 0.f,
+                         m->status_dev));
             cur = 1 - cur;
         }
     }
