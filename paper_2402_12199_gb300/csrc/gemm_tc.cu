@@ -12,13 +12,15 @@
 // needed; what is dropped (A_lo B_lo, the truncation of the lo parts to TF32)
 // is about 2^-21 of each product, the accuracy class of an FP32 dot product.
 //
-// CTA tile: 128 rows of A (the TMEM lanes) x BN columns of B; K in chunks of
-// 32 (one 128-byte swizzle row of FP32): each chunk is read from global memory
-// along the operand's unit stride into registers while the previous chunk's
-// MMAs run, split, and stored K-major with the 128-byte swizzle into one of
-// two shared-memory stages.  One thread issues the 12 MMAs of a chunk (three
-// products x four K steps of 8) and commits them to the stage's mbarrier,
-// which the threads wait on (bounded) before they overwrite that stage.
+// CTA tile: 128 rows of A (the TMEM lanes) x BN columns of B, 256 threads; K
+// in chunks of 64 (two 128-byte swizzle atoms of FP32): each chunk is read
+// from global memory along the operand's unit stride into registers while
+// the previous chunk's MMAs run, split, and stored K-major with the 128-byte
+// swizzle into one of two shared-memory stages.  One thread issues the 24
+// MMAs of a chunk (three products x two atoms x four K steps of 8) and
+// commits them to the stage's mbarrier, which the threads wait on (bounded)
+// before they overwrite that stage.  The epilogue splits the tile's columns
+// between the two warps that share each TMEM lane quarter.
 // Split K (gridDim.z > 1): CTA z sums its K range into a partial tile at
 // C + z csplit; k_splitk_sum adds the partials in a fixed order.
 #include <algorithm>
@@ -31,16 +33,18 @@ namespace gemm {
 
 using namespace tc;
 
-constexpr int kTM = 128, kTK = 32, kThreads = 128;
+constexpr int kTM = 128, kTK = 64, kThreads = 256;
 
 // status word for callers that pass none
 __device__ unsigned g_status;
 
-// Byte offset of element (r, k) of a [rows x 32] FP32 tile, K-major,
-// 128-byte swizzle: one 128-byte row per r, 8-row groups of 1024 bytes, the
-// 16-byte chunk index XOR-ed with (r % 8).
+// Byte offset of element (r, k) of a [ROWS x 64] FP32 tile, K-major,
+// 128-byte swizzle: two atoms of 32 columns (ROWS x 128 bytes each), one
+// 128-byte row per r, 8-row groups of 1024 bytes, the 16-byte chunk index
+// XOR-ed with (r % 8).
+template <int ROWS>
 __device__ __forceinline__ uint32_t off32(int r, int k) {
-    return (uint32_t)(r * 128 + ((((k >> 2) ^ r) & 7) << 4) + ((k & 3) << 2));
+    return (uint32_t)((k >> 5) * (ROWS * 128) + r * 128 + ((((k >> 2) ^ r) & 7) << 4) + ((k & 3) << 2));
 }
 
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
@@ -64,7 +68,7 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t 
 
 template <int BN>
 struct Shape {
-    static constexpr uint32_t kA = kTM * kTK * 4;  // one part of the A chunk (16 KB)
+    static constexpr uint32_t kA = kTM * kTK * 4;  // one part of the A chunk (32 KB)
     static constexpr uint32_t kB = BN * kTK * 4;   // one part of the B chunk
     static constexpr uint32_t kStage = 2 * kA + 2 * kB;
     static constexpr uint32_t kBar = 2 * kStage;   // two mbarriers, then the TMEM slot
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(kThreads)
             const int r = a_kfast ? e / kTK : e % kTM, kk = a_kfast ? e % kTK : e / kTM;
             uint32_t hi, lo;
             split_tf32(ra[i], hi, lo);
-            const uint32_t o = off32(r, kk);
+            const uint32_t o = off32<kTM>(r, kk);
             *reinterpret_cast<uint32_t*>(st + o) = hi;
             *reinterpret_cast<uint32_t*>(st + S::kA + o) = lo;
         }
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kThreads)
             const int n = b_kfast ? e / kTK : e % BN, kk = b_kfast ? e % kTK : e / BN;
             uint32_t hi, lo;
             split_tf32(rb[i], hi, lo);
-            const uint32_t o = off32(n, kk);
+            const uint32_t o = off32<BN>(n, kk);
             *reinterpret_cast<uint32_t*>(st + 2 * S::kA + o) = hi;
             *reinterpret_cast<uint32_t*>(st + 2 * S::kA + S::kB + o) = lo;
         }
@@ -173,11 +177,13 @@ __global__ void __launch_bounds__(kThreads)
             const uint64_t dah = sdesc(a), dal = sdesc(a + S::kA);
             const uint64_t dbh = sdesc(a + 2 * S::kA), dbl = sdesc(a + 2 * S::kA + S::kB);
 #pragma unroll
-            for (int k = 0; k < kTK / 8; ++k) {
+            for (int k = 0; k < kTK / 8; ++k) {  // atom k / 4, K step k % 4 of 8
+                const uint32_t oa = (k >> 2) * (kTM * 128) + (k & 3) * 32;
+                const uint32_t ob = (k >> 2) * (BN * 128) + (k & 3) * 32;
                 const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-                mma_tf32(tmem, sdesc_at(dah, 32 * k), sdesc_at(dbh, 32 * k), idesc, acc);
-                mma_tf32(tmem, sdesc_at(dah, 32 * k), sdesc_at(dbl, 32 * k), idesc, 1u);
-                mma_tf32(tmem, sdesc_at(dal, 32 * k), sdesc_at(dbh, 32 * k), idesc, 1u);
+                mma_tf32(tmem, sdesc_at(dah, oa), sdesc_at(dbh, ob), idesc, acc);
+                mma_tf32(tmem, sdesc_at(dah, oa), sdesc_at(dbl, ob), idesc, 1u);
+                mma_tf32(tmem, sdesc_at(dal, oa), sdesc_at(dbh, ob), idesc, 1u);
             }
             mma_commit(s ? bar1 : bar0);
         }
@@ -191,13 +197,17 @@ __global__ void __launch_bounds__(kThreads)
         done = !__syncthreads_or(!mbar_wait((c & 1) ? bar1 : bar0, (c >> 1) & 1, kWaitCycles));
     }
     fence_after();
-    if (ok && done) {
-        const int r = m0 + warp * 32 + lane;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    // warps w and w + 4 read TMEM lanes 32 (w % 4) .. +31: column halves
+    // (BN = 16: the first four warps take all of them)
+    constexpr int kHalf = BN >= 32 ? BN / 2 : BN;
+    const int half = warp >> 2;
+    if (ok && done && half * kHalf < BN) {
+        const int r = m0 + (warp & 3) * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * kHalf;
         const bool split = gridDim.z > 1;
         float* Cz = C + blockIdx.z * csplit;
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        for (int c0 = 0; c0 < kHalf; c0 += 16) {
             float v[16];
             if (nch > 0)
                 tmem_ld16(lane_addr + c0, v);
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(kThreads)
             if (r < M) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c0 + j;
+                    const int n = n0 + half * kHalf + c0 + j;
                     if (n >= N) break;
                     float* cp = Cz + (int64_t)r * ldc + n;
                     *cp = split ? v[j] : (beta == 0.f ? alpha * v[j] : fmaf(beta, *cp, alpha * v[j]));
