@@ -1140,16 +1140,15 @@ def main():
             del s
 
     # ---- end to end through the public API with host buffers, on the
-    # headline path: every step copies the state in from page-locked host
-    # memory, runs the MD step and reads the new state back into page-locked
-    # host memory, with one host synchronisation per step.  One page-locked
-    # block per direction (pos | quat | vel | angmom): one copy each way.
+    # headline path: a client that keeps the whole velocity-Verlet state in
+    # page-locked host memory (centres, orientations, momenta and the forces
+    # at the current centres, one block) feeds it in, runs one MD step and
+    # reads the new state and forces back into the same block, with one host
+    # synchronisation per step.  rb_set_forces hands the forces back, so the
+    # step does not evaluate them again at the state it was given.
     keys4 = ("pos", "quat", "vel", "angmom")
-    blk_in = torch.from_numpy(np.stack([st[k] for k in keys4])).pin_memory()
-    pinned = {k: blk_in[i] for i, k in enumerate(keys4)}
     e2e_paths = [head]
-    blk_out = {p: torch.empty((4, N_BODIES, 4), dtype=torch.float32).pin_memory() for p in e2e_paths}
-    outs = {p: {k: blk_out[p][i] for i, k in enumerate(keys4)} for p in e2e_paths}
+    blk = {p: torch.empty((6, N_BODIES, 4), dtype=torch.float32).pin_memory() for p in e2e_paths}
     e2e_sys = {}
     for p in e2e_paths:
         se = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin, stream=torch.cuda.Stream())
@@ -1157,23 +1156,28 @@ def main():
         if p.startswith("nn"):
             se.set_nn_fallback(rho_fallback)
         se.step(1, DT, **pcfg(p))  # forces and the step graph, before the timed loop
+        se.get_state(to_host=True, out={k: blk[p][i] for i, k in enumerate(keys4)})
+        se.get_forces(to_host=True, out=(blk[p][4], blk[p][5]))
         e2e_sys[p] = se
     e2e_steps = max(3, min(args.steps, 50))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for p, se in e2e_sys.items():
-            se.set_state(*(pinned[k] for k in keys4))
+            b = blk[p]
+            se.set_state(b[0], b[1], b[2], b[3])
+            se.set_forces(b[4], b[5], **pcfg(p))
             se.step(1, DT, **pcfg(p))
-            se.get_state(to_host=True, out=outs[p], sync=False)
+            se.get_state(to_host=True, out={k: b[i] for i, k in enumerate(keys4)}, sync=False)
+            se.get_forces(to_host=True, out=(b[4], b[5]), sync=False)
         torch.cuda.synchronize()
     e2e_t = (time.perf_counter() - t0) / e2e_steps
-    e2e_ok = all(bool(torch.isfinite(outs[p]["pos"]).all()) for p in e2e_paths)
+    e2e_ok = all(bool(torch.isfinite(blk[p]).all()) for p in e2e_paths)
     for se in e2e_sys.values():
         se.sync()
     del e2e_sys
-    h2d = len(e2e_paths) * 4 * N_BODIES * 16
-    d2h = len(e2e_paths) * 4 * N_BODIES * 16
+    h2d = len(e2e_paths) * 6 * N_BODIES * 16
+    d2h = len(e2e_paths) * 6 * N_BODIES * 16
     e2e_value = sum(n_pairs[p] for p in e2e_paths) * world / e2e_t
 
     model_error = None
@@ -1369,9 +1373,11 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "results_finite": e2e_ok, "path": head,
-                    "note": "per step: state in from page-locked host memory (one block, one "
-                            "copy), one MD step through rb_step, new state out to page-locked "
-                            "host memory (one copy); one host synchronisation per step"},
+                    "note": "per step: the velocity-Verlet state (centres, orientations, "
+                            "momenta, forces) in from page-locked host memory (rb_set_state, one "
+                            "copy; rb_set_forces, two), one MD step through rb_step, the new "
+                            "state and forces out to the same block (three copies); one host "
+                            "synchronisation per step"},
             # per MD step and path: integrate (with the skin check), cell assign,
             # pair build (+ scan), emit (+ finish), pair kernel, reduce; plus the
             # bead fallback kernel on the network paths

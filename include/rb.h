@@ -72,6 +72,7 @@ int32_t rb_abi_version(void);
 /* ------------------------------------------------------------------ system */
 
 typedef struct rb_system rb_system;
+typedef struct rb_mlp rb_mlp; /* a pair network (see rb_mlp_create) */
 
 /* Composite body (paper, Methods: a body is a rigid set of beads).
  *   RB_SHAPE_CUBE:     5 x 5 x 5 simple-cubic beads at 1 sigma (125 beads)
@@ -136,7 +137,8 @@ rb_status rb_body_info(const rb_system* sys, float* mass_host, float* inertia3_h
 rb_status rb_body_template(const rb_system* sys, float* xyz_host);
 
 /* Copy the state in (float4 rows, see above).  from_host != 0: the pointers
- * are host memory.  Invalidates cached forces.  When the four arrays are one
+ * are host memory.  Invalidates cached forces (rb_set_forces gives them back).
+ * When the four arrays are one
  * contiguous block (quat = pos + 4N floats, vel = pos + 8N, angmom =
  * pos + 12N) they move in a single copy (the same holds for rb_get_state). */
 rb_status rb_set_state(rb_system* sys, const float* pos, const float* quat, const float* vel,
@@ -147,8 +149,26 @@ rb_status rb_set_state(rb_system* sys, const float* pos, const float* quat, cons
  * stream: the caller synchronises that stream before reading them. */
 rb_status rb_get_state(const rb_system* sys, float* pos, float* quat, float* vel, float* angmom,
                        int32_t to_host);
-/* Copy out the forces/torques of the last evaluation (float4 rows). */
+/* Copy out the forces/torques of the last evaluation (float4 rows: force
+ * (x, y, z, the body's share of the pair energies), torque (x, y, z, 0));
+ * either pointer may be NULL.  to_host as in rb_get_state (0 device, 1 host
+ * and synchronised, 2 host and queued). */
 rb_status rb_get_forces(const rb_system* sys, float* force, float* torque, int32_t to_host);
+/* Give the forces and torques of the current state back after rb_set_state:
+ * the rows that rb_get_forces returned after a force evaluation or an MD step
+ * on force path `path` (with `mlp` and `precision` for RB_PATH_NN; mlp NULL
+ * and precision RB_FP32 for RB_PATH_BEADS) at that state.  The next rb_step
+ * on the same path, network (and network parameters) and precision takes them
+ * as F(t) of its first half kick instead of evaluating them again; any other
+ * step or force call evaluates them as usual.  This is for a client that keeps
+ * the whole velocity-Verlet state on the host (centres, orientations, momenta
+ * and the forces at the current centres) and feeds it back every step.  The
+ * caller vouches that the rows are that path's forces at the current state:
+ * nothing checks it.  force, torque: N float4 rows each, device pointers, or
+ * host pointers with from_host != 0; both required.  RB_EINVAL on a null
+ * argument or an unknown path or precision. */
+rb_status rb_set_forces(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
+                        const float* force, const float* torque, int32_t from_host);
 
 /* Verlet skin (default 0): the pair list then holds every pair within
  * Rc + skin and is rebuilt only when some centre has moved more than skin / 2
@@ -179,7 +199,6 @@ rb_status rb_forces_beads(rb_system* sys, float* force, float* torque, double* e
 /* Evaluate the per-pair results of `path` on the CURRENT pair list only (no
  * pair-list rebuild, no per-body reduction): one launch of the pair kernel.
  * Used to time the pair kernels in isolation.  Asynchronous. */
-typedef struct rb_mlp rb_mlp;
 rb_status rb_eval_pairs(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision);
 
 /* Integrate n_steps of velocity Verlet (NO_SQUISH free-rotor split for the

@@ -140,11 +140,32 @@ class System:
         check(load().rb_get_state(self._h, *ptrs, mode))
         return out
 
-    def get_forces(self):
-        F = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
-        T = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
-        check(load().rb_get_forces(self._h, F.data_ptr(), T.data_ptr(), 0))
+    def get_forces(self, to_host: bool = False, out=None, sync: bool = True):
+        """rb_get_forces: (force, torque) rows of the last evaluation.  `out`:
+        two preallocated tensors (page-locked host tensors with to_host); with
+        to_host and sync=False the copies are only queued (to_host = 2)."""
+        if out is not None:
+            F, T = out
+        elif to_host:
+            F = torch.empty((self.N, 4), dtype=torch.float32).pin_memory()
+            T = torch.empty((self.N, 4), dtype=torch.float32).pin_memory()
+        else:
+            F = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+            T = torch.empty((self.N, 4), dtype=torch.float32, device="cuda")
+        mode = (1 if sync else 2) if to_host else 0
+        check(load().rb_get_forces(self._h, F.data_ptr(), T.data_ptr(), mode))
         return F, T
+
+    def set_forces(self, force, torque, path: int = RB_PATH_BEADS, mlp: "MLP" = None,
+                   precision="fp32"):
+        """rb_set_forces: give back the forces of the current state on `path`
+        (device tensors, or host tensors: both the same kind)."""
+        host = not force.is_cuda
+        if torque.is_cuda == host:
+            raise ValueError("force and torque must both be host or both device tensors")
+        check(load().rb_set_forces(self._h, path, mlp.handle if mlp is not None else None,
+                                   PRECISION[precision], force.data_ptr(), torque.data_ptr(),
+                                   1 if host else 0))
 
     def build_pairs(self) -> int:
         n = ctypes.c_int64()

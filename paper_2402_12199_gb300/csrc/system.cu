@@ -1119,11 +1119,37 @@ rb_status rb_get_state(const rb_system* s, float* pos, float* quat, float* vel, 
 
 rb_status rb_get_forces(const rb_system* s, float* force, float* torque, int32_t to_host) {
     if (!s) return fail(RB_EINVAL, "null system");
+    if (to_host < 0 || to_host > 2) return fail(RB_EINVAL, "to_host: 0, 1 or 2");
     const size_t b = sizeof(float4) * s->N;
     const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (force) RB_CUDA(cudaMemcpyAsync(force, s->force, b, k, s->stream));
     if (torque) RB_CUDA(cudaMemcpyAsync(torque, s->torque, b, k, s->stream));
-    if (to_host) RB_CUDA(cudaStreamSynchronize(s->stream));
+    if (to_host == 1) RB_CUDA(cudaStreamSynchronize(s->stream));
+    return RB_OK;
+}
+
+rb_status rb_set_forces(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
+                        const float* force, const float* torque, int32_t from_host) {
+    if (!s || !force || !torque) return fail(RB_EINVAL, "null argument");
+    if (path == RB_PATH_BEADS) {
+        m = nullptr;
+        precision = RB_FP32;
+    } else if (path == RB_PATH_NN) {
+        RB_TRY(check_mlp(m));
+        if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
+            return fail(RB_EINVAL, "unknown precision");
+    } else {
+        return fail(RB_EINVAL, "path: RB_PATH_BEADS or RB_PATH_NN");
+    }
+    const size_t b = sizeof(float4) * s->N;
+    const cudaMemcpyKind k = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    RB_CUDA(cudaMemcpyAsync(s->force, force, b, k, s->stream));
+    RB_CUDA(cudaMemcpyAsync(s->torque, torque, b, k, s->stream));
+    s->forces_valid = true;
+    s->forces_path = path;
+    s->forces_precision = precision;
+    s->forces_mlp = m;
+    s->forces_mlp_version = m ? m->version : 0;
     return RB_OK;
 }
 
