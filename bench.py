@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--train-contact", type=float, default=0.85)
     ap.add_argument("--train-cutoff-width", type=float, default=1.0)
     ap.add_argument("--train-lam-e", type=float, default=0.1)
-    ap.add_argument("--cyl-train-steps", type=int, default=3000)
+    ap.add_argument("--cyl-train-steps", type=int, default=12000)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--descriptor-comparison", type=int, default=1)
     ap.add_argument("--no-paper-workload", action="store_true")
@@ -877,16 +877,31 @@ def main():
     if args.train_steps > 0 and any(p.startswith("nn") for p in paths):
         from paper_2402_12199_gb300 import train_net
 
-        _, rc = train_net.train_network("cylinder", 256, DEPTH, n_samples=1_000_000,
-                                        steps=args.cyl_train_steps, batch=4096, lr=args.train_lr,
-                                        f_scale=args.train_f_scale, contact=args.train_contact,
-                                        lam_E=args.train_lam_e,
-                                        cutoff_width=args.train_cutoff_width, seed=4)
+        m_cyl, rc = train_net.train_network("cylinder", 256, DEPTH, n_samples=1_000_000,
+                                            steps=args.cyl_train_steps, batch=4096,
+                                            lr=args.train_lr, f_scale=args.train_f_scale,
+                                            contact=args.train_contact, lam_E=args.train_lam_e,
+                                            cutoff_width=args.train_cutoff_width, seed=4)
+        # model error on an MD state of cylinders (the per-component leg's system)
+        probe = api.System(8, [80.0] * 3, "cylinder")
+        st_cy, L_cy = inputs_mod.system_state(32768, 0.15, KT, SEED + 11, probe.mass,
+                                              probe.inertia, "cylinder")
+        del probe
+        s_cy = api.System(32768, [L_cy] * 3, "cylinder", skin=args.skin)
+        s_cy.set_state(*(torch.from_numpy(st_cy[k]).cuda() for k in ("pos", "quat", "vel", "angmom")))
+        s_cy.set_nn_fallback(rc["rho_contact_min"])
+        err_cy = train_net.force_error(s_cy, m_cyl, "bf16")
+        del s_cy, m_cyl
         train_cyl = {"workload": "cylinders (8 x 19 beads), network 10-256x3-1, 1M training pairs",
                      "symmetry": rc["symmetry"],
                      "sampler_pairs_per_s": (rc["samples"] + 10000) / rc["t_sample_s"],
                      "train_samples_per_s": rc["steps"] * rc["batch"] / rc["t_train_s"],
-                     "steps": rc["steps"], "heldout_e_F_after_these_steps": rc["heldout_e_F"]}
+                     "steps": rc["steps"], "heldout_e_F_after_these_steps": rc["heldout_e_F"],
+                     "heldout": "pairs drawn like the training set (separation uniform from "
+                                "contact to Rc: dominated by contact forces)",
+                     "model_error_md_state": dict(err_cy, vs="bead path on 32768 cylinders at "
+                                                  "phi 0.15 (model error, not parity), BF16, "
+                                                  "bead fallback below the contact separation")}
 
     # ---- network width 256 (BF16, streamed weights), same workload, timed alone
     width256 = None
