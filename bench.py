@@ -1159,8 +1159,9 @@ def main():
     # page-locked host memory (centres, orientations, momenta and the forces
     # at the current centres, one block) feeds it in, runs one MD step and
     # reads the new state and forces back into the same block, with one host
-    # synchronisation per step.  rb_set_forces hands the forces back, so the
-    # step does not evaluate them again at the state it was given.
+    # synchronisation per step (rb_step_host_state: rb_set_state, rb_set_forces,
+    # rb_step and the copies back in one call; the forces handed back spare the
+    # step an evaluation at the state it was given).
     keys4 = ("pos", "quat", "vel", "angmom")
     e2e_paths = [head]
     blk = {p: torch.empty((6, N_BODIES, 4), dtype=torch.float32).pin_memory() for p in e2e_paths}
@@ -1178,13 +1179,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for p, se in e2e_sys.items():
-            b = blk[p]
-            se.set_state(b[0], b[1], b[2], b[3])
-            se.set_forces(b[4], b[5], **pcfg(p))
-            se.step(1, DT, **pcfg(p))
-            se.get_state(to_host=True, out={k: b[i] for i, k in enumerate(keys4)}, sync=False)
-            se.get_forces(to_host=True, out=(b[4], b[5]), sync=False)
+        for p, se in e2e_sys.items():  # state and forces in, one step, both out
+            se.step_host_state(blk[p], 1, DT, sync=False, **pcfg(p))
         torch.cuda.synchronize()
     e2e_t = (time.perf_counter() - t0) / e2e_steps
     e2e_ok = all(bool(torch.isfinite(blk[p]).all()) for p in e2e_paths)
@@ -1388,10 +1384,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "results_finite": e2e_ok, "path": head,
-                    "note": "per step: the velocity-Verlet state (centres, orientations, "
-                            "momenta, forces) in from page-locked host memory (rb_set_state, one "
-                            "copy; rb_set_forces, two), one MD step through rb_step, the new "
-                            "state and forces out to the same block (three copies); one host "
+                    "note": "per step, one rb_step_host_state call: the velocity-Verlet "
+                            "state (centres, orientations, momenta, forces) in from one "
+                            "page-locked host block (three copies), one MD step, the new state "
+                            "and forces out to the same block (three copies); one host "
                             "synchronisation per step"},
             # per MD step and path: integrate (with the skin check), cell assign,
             # pair build (+ scan), emit (+ finish), pair kernel, reduce; plus the

@@ -169,6 +169,19 @@ rb_status rb_get_forces(const rb_system* sys, float* force, float* torque, int32
  * argument or an unknown path or precision. */
 rb_status rb_set_forces(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
                         const float* force, const float* torque, int32_t from_host);
+/* MD steps for a client that keeps the whole velocity-Verlet state in host
+ * memory, in one call: `state_host` is one block of 6 N float4 rows
+ * (pos | quat | vel | angmom | force | torque, each N rows, the forces those of
+ * `path` at the block's state, as the previous call left them).  Enqueues on
+ * the system's stream what rb_set_state, rb_set_forces, rb_step(n_steps, dt)
+ * and rb_get_state / rb_get_forces (to_host = 2) would: the block in, the
+ * steps, the new state and its forces back into the same block.  The block
+ * should be page-locked (for asynchronous copies) and must stay valid until
+ * the stream has passed the copies.  sync != 0: returns after the block is
+ * updated, reporting sticky device errors as rb_sync does; sync = 0: after
+ * queueing.  Arguments and errors as those calls'. */
+rb_status rb_step_host_state(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
+                             int64_t n_steps, float dt, float* state_host, int32_t sync);
 
 /* Verlet skin (default 0): the pair list then holds every pair within
  * Rc + skin and is rebuilt only when some centre has moved more than skin / 2

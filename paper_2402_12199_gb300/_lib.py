@@ -83,6 +83,7 @@ SIGNATURES = {
     "rb_get_state": (I32, [P, P, P, P, P, I32]),
     "rb_get_forces": (I32, [P, P, P, I32]),
     "rb_set_forces": (I32, [P, I32, P, I32, P, P, I32]),
+    "rb_step_host_state": (I32, [P, I32, P, I32, I64, F32, P, I32]),
     "rb_build_pairs": (I32, [P, I64P]),
     "rb_get_pairs": (I32, [P, I32P, I64, I64P]),
     "rb_forces_beads": (I32, [P, P, P, DP, DP]),

@@ -156,6 +156,18 @@ class System:
         check(load().rb_get_forces(self._h, F.data_ptr(), T.data_ptr(), mode))
         return F, T
 
+    def step_host_state(self, block: torch.Tensor, n_steps: int, dt: float,
+                        path: int = RB_PATH_BEADS, mlp: "MLP" = None, precision="fp32",
+                        sync: bool = True):
+        """rb_step_host_state: `block` is a page-locked (6, N, 4) FP32 host tensor
+        (pos, quat, vel, angmom, force, torque), updated in place."""
+        if block.is_cuda or block.dtype != torch.float32 or tuple(block.shape) != (6, self.N, 4) \
+                or not block.is_contiguous():
+            raise ValueError("block must be a contiguous (6, N, 4) float32 host tensor")
+        check(load().rb_step_host_state(self._h, path, mlp.handle if mlp is not None else None,
+                                        PRECISION[precision], int(n_steps), float(dt),
+                                        block.data_ptr(), 1 if sync else 0))
+
     def set_forces(self, force, torque, path: int = RB_PATH_BEADS, mlp: "MLP" = None,
                    precision="fp32"):
         """rb_set_forces: give back the forces of the current state on `path`

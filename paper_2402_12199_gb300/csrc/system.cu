@@ -1516,4 +1516,19 @@ rb_status rb_sync(rb_system* s) {
     return check_status(s);
 }
 
+rb_status rb_step_host_state(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
+                             int64_t n_steps, float dt, float* state_host, int32_t sync) {
+    if (!s || !state_host) return fail(RB_EINVAL, "null argument");
+    if (path != RB_PATH_BEADS && path != RB_PATH_NN)
+        return fail(RB_EINVAL, "path: RB_PATH_BEADS or RB_PATH_NN");
+    const size_t n4 = 4 * (size_t)s->N;  // floats per array
+    float* x = state_host;
+    RB_TRY(rb_set_state(s, x, x + n4, x + 2 * n4, x + 3 * n4, 1));
+    RB_TRY(rb_set_forces(s, path, m, precision, x + 4 * n4, x + 5 * n4, 1));
+    RB_TRY(rb_step(s, path, m, precision, n_steps, dt));
+    RB_TRY(rb_get_state(s, x, x + n4, x + 2 * n4, x + 3 * n4, 2));
+    RB_TRY(rb_get_forces(s, x + 4 * n4, x + 5 * n4, 2));
+    return sync ? check_status(s) : RB_OK;
+}
+
 }  // extern "C"

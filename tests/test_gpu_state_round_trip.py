@@ -116,3 +116,27 @@ def test_set_forces_refuses_bad_arguments():
         s.set_forces(F, F, path=api.RB_PATH_NN, mlp=None, precision="bf16")
     with pytest.raises(ValueError):
         s.set_forces(F, torch.zeros((64, 4)))
+
+
+@pytest.mark.parametrize("kind", ["beads", "bf16"])
+def test_step_host_state_matches_the_uninterrupted_run(kind):
+    import torch
+
+    keys = ("pos", "quat", "vel", "angmom")
+    st, L, _ = make_state(1500, 0.20, 34)
+    cfg = _cfg(kind)
+    a, b = _system(st, L), _system(st, L)
+    a.step(4, DT, **cfg)
+    b.step(1, DT, **cfg)
+    blk = torch.empty((6, 1500, 4), dtype=torch.float32).pin_memory()
+    b.get_state(to_host=True, out={k: blk[i] for i, k in enumerate(keys)})
+    b.get_forces(to_host=True, out=(blk[4], blk[5]))
+    for _ in range(3):
+        b.step_host_state(blk, 1, DT, **cfg)
+    sa = a.get_state()
+    fa = a.get_forces()
+    for i, k in enumerate(keys):
+        assert torch.equal(sa[k].cpu(), blk[i]), k
+    assert torch.equal(fa[0].cpu(), blk[4]) and torch.equal(fa[1].cpu(), blk[5])
+    with pytest.raises(ValueError):
+        b.step_host_state(blk[:5], 1, DT, **cfg)
