@@ -221,10 +221,43 @@ __device__ inline void warp_finish(const float (&bx)[2 * NP], const float (&by)[
         }
     }
     v[6] = pot.eps4 * (a.acc.x + a.acc.y) - pot.u_shift * (a.cnt.x + a.cnt.y);
+    // Reduce-scatter over the warp: lanes with bit 16 set keep sums 4..7 and
+    // hand 0..3 to their partner, then bits 8 and 4 halve the kept set again,
+    // so that lane l holds one of the 8 (7 and a zero) partial sums, index
+    // 4 b16 + 2 b8 + b4; xor 2 and 1 complete it.  Then every lane reads the
+    // 7 sums from lanes 0, 4, .., 24.  16 shuffles instead of 35.
+    const int lane = threadIdx.x & 31;
+    float w[4];
+    {
+        const bool b = lane & 16;
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
+        for (int j = 0; j < 4; ++j) {
+            const float keep = b ? (j + 4 < 7 ? v[j + 4] : 0.f) : v[j];
+            const float give = b ? v[j] : (j + 4 < 7 ? v[j + 4] : 0.f);
+            w[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+        }
+    }
+    float u[2];
+    {
+        const bool b = lane & 8;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int j = 0; j < 2; ++j) {
+            const float keep = b ? w[j + 2] : w[j];
+            const float give = b ? w[j] : w[j + 2];
+            u[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+        }
+    }
+    float t;
+    {
+        const bool b = lane & 4;
+        const float keep = b ? u[1] : u[0];
+        const float give = b ? u[0] : u[1];
+        t = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] = __shfl_sync(0xffffffffu, t, 4 * k);
 }
 
 // Whole-warp bead double sum of one body pair in the frame of body i, any
@@ -325,9 +358,11 @@ __device__ inline bool column_near(const float3 s, const float4* sC, const BeadC
 // C beads (running minimum per bead), and the exact terms for the beads with a hit.
 // Columns in ascending order, as a full scan takes them.
 // ZINT: the column z values are -2, -1, 0, 1, 2 (see bead_pair_warp_cols).
+constexpr int kColWords = (kMaxBeads / 5 + 31) / 32;  // column masks of 32 bits
+
 template <int NP, int C, int POT, bool ZINT>
-__device__ inline bool cols_scan(const float3 s, const float4* sC, const float* sTh,
-                                 const BeadCols& cols, const BeadPot& pot, int lane,
+__device__ inline bool cols_scan(const unsigned (&nearw)[kColWords], const float4* sC,
+                                 const float* sTh, const BeadCols& cols, const BeadPot& pot,
                                  const float2 (&Bx)[NP], const float2 (&By)[NP],
                                  const float2 (&Bz)[NP], const float2 (&BB)[NP], LJAcc<NP>& a) {
     float2 mz[C];  // -2 z_m, duplicated
@@ -340,8 +375,10 @@ __device__ inline bool cols_scan(const float3 s, const float4* sC, const float* 
         W[q] = __fmul2_rn(Bz[q], make_float2(4.f, 4.f));
     }
     bool any_hit = false;  // warp-uniform
-    for (int c0 = 0; c0 < cols.n_cols; c0 += 32) {
-        unsigned near = __ballot_sync(0xffffffffu, column_near<C>(s, sC, cols, c0 + lane, pot.cull2));
+#pragma unroll
+    for (int wd = 0; wd < kColWords; ++wd) {
+        const int c0 = 32 * wd;
+        unsigned near = nearw[wd];
         while (near) {
             const int c = c0 + __ffs(near) - 1;
             near &= near - 1u;
@@ -396,11 +433,19 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
                                            const float4* sC, const float* sTh,
                                            const BeadCols& cols, int n_beads, const BeadPot& pot,
                                            int lane, float (&v)[7]) {
-    // no column near body j (a third of the listed pairs of a dilute system):
-    // every sum is zero, skip the slots as well
+    // which columns come near body j (one lane per column, one ballot per 32);
+    // none (a third of the listed pairs of a dilute system): every sum is
+    // zero, skip the slots as well
+    unsigned nearw[kColWords];
     bool any = false;
-    for (int c = lane; c < cols.n_cols; c += 32) any |= column_near<C>(s, sC, cols, c, pot.cull2);
-    if (!__any_sync(0xffffffffu, any)) {
+#pragma unroll
+    for (int wd = 0; wd < kColWords; ++wd) {
+        nearw[wd] = 32 * wd < cols.n_cols
+                        ? __ballot_sync(0xffffffffu, column_near<C>(s, sC, cols, 32 * wd + lane, pot.cull2))
+                        : 0u;
+        any |= nearw[wd] != 0u;
+    }
+    if (!any) {
 #pragma unroll
         for (int k = 0; k < 7; ++k) v[k] = 0.f;
         return;
@@ -419,8 +464,8 @@ __device__ inline void bead_pair_warp_cols(const float3 s, const Mat3& Rr, const
     if constexpr (C == 5)
         zint = cols.z[0] == -2.f && cols.z[1] == -1.f && cols.z[2] == 0.f && cols.z[3] == 1.f &&
                cols.z[4] == 2.f;
-    const bool hit = zint ? cols_scan<NP, C, POT, true>(s, sC, sTh, cols, pot, lane, Bx, By, Bz, BB, a)
-                          : cols_scan<NP, C, POT, false>(s, sC, sTh, cols, pot, lane, Bx, By, Bz, BB, a);
+    const bool hit = zint ? cols_scan<NP, C, POT, true>(nearw, sC, sTh, cols, pot, Bx, By, Bz, BB, a)
+                          : cols_scan<NP, C, POT, false>(nearw, sC, sTh, cols, pot, Bx, By, Bz, BB, a);
     if (!hit) {  // no bead pair within r_c: the sums are zero
 #pragma unroll
         for (int k = 0; k < 7; ++k) v[k] = 0.f;
