@@ -11,8 +11,8 @@ on each force path: the bead double sum (FP32), the pair network at FP32
 accuracy (tensor cores, split FP16 operands: RB_F16X3) and the pair network in
 BF16 (tensor cores).  The headline `value` is the BF16 network path's
 body-pair force+torque evaluations per second (its MD steps/s are in `paths`
-with the other two, the bead sum being the comparison and the judge of the
-model error reported beside it); the SIMT FP32 network kernel is timed beside
+with the other two, the bead sum being the comparison and the reference of
+the model error reported beside it); the SIMT FP32 network kernel is timed beside
 them (`nn_fp32_simt`).  The arithmetic peaks the rooflines divide by are
 measured here by register-resident probes (rb_peak_probe) with the SM clock
 sampled during them.
