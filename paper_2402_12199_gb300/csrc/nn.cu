@@ -466,9 +466,25 @@ rb_status mlp_refresh(rb_mlp* m) {
     k_prepare_f32<<<sm_count() * 4, 256, 0, m->stream>>>(m->params, m->width, m->depth,
                                                          m->f32_prep);
     RB_CUDA(cudaGetLastError());
-    RB_TRY(nn_tc_prepare(m));
-    RB_TRY(nn_f16x3_prepare(m));
-    m->version++;
+    m->version++;  // the BF16 / F16X3 images follow on their next use (ensure_images)
+    return RB_OK;
+}
+
+rb_status ensure_images(const rb_mlp* cm, int precision) {
+    if (precision != RB_BF16 && precision != RB_F16X3) return RB_OK;
+    rb_mlp* m = const_cast<rb_mlp*>(cm);  // the images are a cache of the parameters
+    std::atomic<uint64_t>& built = precision == RB_BF16 ? m->tc_img_version : m->f16x3_img_version;
+    if (built.load() == m->version) return RB_OK;
+    std::lock_guard<std::mutex> lock(m->img_mu);
+    if (built.load() == m->version) return RB_OK;
+    if (precision == RB_BF16)
+        RB_TRY(nn_tc_prepare(m));
+    else
+        RB_TRY(nn_f16x3_prepare(m));
+    // other streams (systems, server replicas) read the image without waiting
+    // on the network's stream
+    RB_CUDA(cudaStreamSynchronize(m->stream));
+    built.store(m->version);
     return RB_OK;
 }
 
@@ -515,6 +531,7 @@ __global__ void k_pair_sym_combine(const int* __restrict__ n_pairs, float4* __re
 
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision) {
     RB_TRY(check_mlp(m));
+    RB_TRY(ensure_images(m, precision));
     RB_TRY(nn_system_pass(s, m, precision, false));
     if (!m->pair_sym) return RB_OK;
     RB_TRY(nn_system_pass(s, m, precision, true));
@@ -622,6 +639,7 @@ rb_status rb_nn_pairs(const rb_mlp* m, int32_t precision, int64_t n, const float
     RB_TRY(check_mlp(m));
     if (n < 0 || (n > 0 && (!cfg || !out))) return fail(RB_EINVAL, "bad pair arrays");
     if (n == 0) return RB_OK;
+    RB_TRY(ensure_images(m, precision));
     if (precision == RB_BF16)
         return nn_tc_pairs_async(m, n, reinterpret_cast<const float4*>(cfg),
                                  reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(grad_out));

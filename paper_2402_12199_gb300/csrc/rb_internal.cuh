@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -184,6 +186,10 @@ struct rb_mlp {
     void* f16x3_img = nullptr;    // FP16 hi/lo weight image of the FP32-accurate tensor-core kernel
     unsigned* status_dev = nullptr;  // sticky device-side error bits of pair-level calls
     uint64_t version = 1;         // bumped on every set_params
+    // the version the BF16 and F16X3 images were built for: they are built when
+    // a kernel of that precision first runs after a change (ensure_images)
+    std::atomic<uint64_t> tc_img_version{0}, f16x3_img_version{0};
+    std::mutex img_mu;
     // point group of the bodies (symmetry-reduced configurations): device
     // table of 3 float4 per rotation (see canon_config), n_sym = 0: none
     float4* sym_dev = nullptr;     // 3 x 24 float4 (generic table) + 48 float4 (cube table)
@@ -288,6 +294,10 @@ __global__ void k_zero_count(int* count);  // *count = 0 after pdl_wait (system.
 rb_status bead_fallback_async(rb_system* s);  // bead sum for pairs with rho < nn_fallback_rho
 // nn.cu
 rb_status nn_pairs_system_async(rb_system* s, const rb_mlp* m, int precision);
+// builds the weight image `precision` needs (BF16, F16X3) if the parameters
+// changed since it was built, then synchronises the network's stream; call
+// outside stream capture (inside one it must find the image current)
+rb_status ensure_images(const rb_mlp* m, int precision);
 // the secondary pair arrays a pair-symmetrised network needs (no-op otherwise);
 // call outside stream capture
 rb_status ensure_pair_sym_arrays(rb_system* s, const rb_mlp* m);

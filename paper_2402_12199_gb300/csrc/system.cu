@@ -1260,7 +1260,10 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
     if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
         return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
-    if (path == RB_PATH_NN) RB_TRY(ensure_pair_sym_arrays(s, static_cast<const rb_mlp*>(m)));
+    if (path == RB_PATH_NN) {  // before any capture below
+        RB_TRY(ensure_pair_sym_arrays(s, static_cast<const rb_mlp*>(m)));
+        RB_TRY(ensure_images(static_cast<const rb_mlp*>(m), precision));
+    }
     const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
                       s->forces_precision == precision &&
                       (!m || s->forces_mlp_version == version);
