@@ -1386,9 +1386,9 @@ def main():
                     "results_finite": e2e_ok, "path": head,
                     "note": "per step, one rb_step_host_state call: the velocity-Verlet "
                             "state (centres, orientations, momenta, forces) in from one "
-                            "page-locked host block (three copies), one MD step, the new state "
-                            "and forces out to the same block (three copies); one host "
-                            "synchronisation per step"},
+                            "page-locked host block (one copy), one MD step, the new state and "
+                            "forces out to the same block (one copy); one host synchronisation "
+                            "per step"},
             # per MD step and path: integrate (with the skin check), cell assign,
             # pair build (+ scan), emit (+ finish), pair kernel, reduce; plus the
             # bead fallback kernel on the network paths

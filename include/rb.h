@@ -177,7 +177,8 @@ rb_status rb_set_forces(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t
  * and rb_get_state / rb_get_forces (to_host = 2) would: the block in, the
  * steps, the new state and its forces back into the same block.  The block
  * should be page-locked (for asynchronous copies) and must stay valid until
- * the stream has passed the copies.  sync != 0: returns after the block is
+ * the stream has passed the copies (one copy each way: the system keeps the
+ * same six arrays as one block).  sync != 0: returns after the block is
  * updated, reporting sticky device errors as rb_sync does; sync = 0: after
  * queueing.  Arguments and errors as those calls'. */
 rb_status rb_step_host_state(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,

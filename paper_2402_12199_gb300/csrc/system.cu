@@ -869,16 +869,17 @@ rb_status rb_create_system(const rb_system_desc* d, void* stream, rb_system** ou
 #define ALLOC(ptr, bytes) \
     if (e == cudaSuccess) e = A((void**)&(ptr), (bytes))
     ALLOC(s->tmpl_dev, sizeof(float4) * s->n_beads);
-    // the four state arrays as one block (pos | quat | vel | angmom), so that a
-    // caller's contiguous state moves in one copy
-    ALLOC(s->pos, sizeof(float4) * 4 * N);
+    // the state arrays and the forces as one block (pos | quat | vel | angmom |
+    // force | torque), so that a caller's contiguous state (and a host-state
+    // client's whole block) moves in one copy
+    ALLOC(s->pos, sizeof(float4) * 6 * N);
     if (e == cudaSuccess) {
         s->quat = s->pos + N;
         s->vel = s->pos + 2 * N;
         s->angmom = s->pos + 3 * N;
+        s->force = s->pos + 4 * N;
+        s->torque = s->pos + 5 * N;
     }
-    ALLOC(s->force, sizeof(float4) * N);
-    ALLOC(s->torque, sizeof(float4) * N);
     ALLOC(s->cells.count, sizeof(int) * s->cells.n_cells);
     ALLOC(s->cells.bodies, sizeof(int) * (size_t)s->cells.n_cells * s->cells.cap);
     ALLOC(s->pl.half_count, sizeof(int) * N);
@@ -981,7 +982,7 @@ rb_status rb_destroy_system(rb_system* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-    void* ptrs[] = {s->tmpl_dev, s->pos, s->force, s->torque,
+    void* ptrs[] = {s->tmpl_dev, s->pos,  // force and torque live in the pos block
                     s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
                     s->pl.half_nbr, s->pl.lower_nbr, s->pl.half_off, s->pl.done,
                     s->pl.pairs, s->pl.n_pairs,
@@ -1013,6 +1014,49 @@ rb_status rb_body_template(const rb_system* s, float* xyz) {
     return RB_OK;
 }
 
+// What follows a copy of a new state into the system: the image counters
+// restart, the list is checked (or rebuilt without a skin), the thermostat
+// re-reads K, and the stored forces no longer belong to the state.
+static rb_status state_replaced(rb_system* s, bool positions, bool momenta) {
+    if (positions) {
+        // With a skin the list stays valid while every centre is within skin/2
+        // of the positions it was built for, however the centres got there:
+        // the skin check of the next evaluation decides (a state close to the
+        // previous one, as a caller feeding each step's state back, keeps it).
+        if (!(s->skin > 0.f)) k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
+        RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
+    }
+    if (s->nh && momenta)
+        k_thermo_init<<<1, 1024, 0, s->stream>>>(
+            (int)s->N, s->mass,
+            make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]), s->vel,
+            s->angmom, s->nh, 0);
+    RB_CUDA(cudaGetLastError());
+    s->forces_valid = false;
+    return RB_OK;
+}
+
+// The forces in s->force / s->torque are those of `path` (network m at
+// `precision`) at the current state: check the arguments, then record it.
+static rb_status forces_given(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision) {
+    if (path == RB_PATH_BEADS) {
+        m = nullptr;
+        precision = RB_FP32;
+    } else if (path == RB_PATH_NN) {
+        RB_TRY(check_mlp(m));
+        if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
+            return fail(RB_EINVAL, "unknown precision");
+    } else {
+        return fail(RB_EINVAL, "path: RB_PATH_BEADS or RB_PATH_NN");
+    }
+    s->forces_valid = true;
+    s->forces_path = path;
+    s->forces_precision = precision;
+    s->forces_mlp = m;
+    s->forces_mlp_version = m ? m->version : 0;
+    return RB_OK;
+}
+
 rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const float* vel,
                        const float* angmom, int32_t from_host) {
     if (!s) return fail(RB_EINVAL, "null system");
@@ -1027,21 +1071,7 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
         if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
         if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
     }
-    if (pos) {
-        // With a skin the list stays valid while every centre is within skin/2
-        // of the positions it was built for, however the centres got there:
-        // the skin check of the next evaluation decides (a state close to the
-        // previous one, as a caller feeding each step's state back, keeps it).
-        if (!(s->skin > 0.f)) k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
-        RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
-    }
-    if (s->nh && (vel || angmom))
-        k_thermo_init<<<1, 1024, 0, s->stream>>>(
-            (int)s->N, s->mass,
-            make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]), s->vel,
-            s->angmom, s->nh, 0);
-    s->forces_valid = false;
-    return RB_OK;
+    return state_replaced(s, pos != nullptr, vel || angmom);
 }
 
 rb_status rb_set_thermostat(rb_system* s, float kT, float tau) {
@@ -1131,26 +1161,14 @@ rb_status rb_get_forces(const rb_system* s, float* force, float* torque, int32_t
 rb_status rb_set_forces(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
                         const float* force, const float* torque, int32_t from_host) {
     if (!s || !force || !torque) return fail(RB_EINVAL, "null argument");
-    if (path == RB_PATH_BEADS) {
-        m = nullptr;
-        precision = RB_FP32;
-    } else if (path == RB_PATH_NN) {
-        RB_TRY(check_mlp(m));
-        if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
-            return fail(RB_EINVAL, "unknown precision");
-    } else {
+    if (path != RB_PATH_BEADS && path != RB_PATH_NN)
         return fail(RB_EINVAL, "path: RB_PATH_BEADS or RB_PATH_NN");
-    }
+    if (path == RB_PATH_NN) RB_TRY(check_mlp(m));
     const size_t b = sizeof(float4) * s->N;
     const cudaMemcpyKind k = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     RB_CUDA(cudaMemcpyAsync(s->force, force, b, k, s->stream));
     RB_CUDA(cudaMemcpyAsync(s->torque, torque, b, k, s->stream));
-    s->forces_valid = true;
-    s->forces_path = path;
-    s->forces_precision = precision;
-    s->forces_mlp = m;
-    s->forces_mlp_version = m ? m->version : 0;
-    return RB_OK;
+    return forces_given(s, path, m, precision);
 }
 
 rb_status rb_build_pairs(rb_system* s, int64_t* n_pairs) {
@@ -1524,13 +1542,18 @@ rb_status rb_step_host_state(rb_system* s, int32_t path, const rb_mlp* m, int32_
     if (!s || !state_host) return fail(RB_EINVAL, "null argument");
     if (path != RB_PATH_BEADS && path != RB_PATH_NN)
         return fail(RB_EINVAL, "path: RB_PATH_BEADS or RB_PATH_NN");
-    const size_t n4 = 4 * (size_t)s->N;  // floats per array
-    float* x = state_host;
-    RB_TRY(rb_set_state(s, x, x + n4, x + 2 * n4, x + 3 * n4, 1));
-    RB_TRY(rb_set_forces(s, path, m, precision, x + 4 * n4, x + 5 * n4, 1));
+    if (path == RB_PATH_NN) {
+        RB_TRY(check_mlp(m));
+        if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
+            return fail(RB_EINVAL, "unknown precision");
+    }
+    // the device side is one block in the same order (pos .. torque): one copy each way
+    const size_t bytes = 6 * sizeof(float4) * s->N;
+    RB_CUDA(cudaMemcpyAsync(s->pos, state_host, bytes, cudaMemcpyHostToDevice, s->stream));
+    RB_TRY(state_replaced(s, true, true));
+    RB_TRY(forces_given(s, path, m, precision));
     RB_TRY(rb_step(s, path, m, precision, n_steps, dt));
-    RB_TRY(rb_get_state(s, x, x + n4, x + 2 * n4, x + 3 * n4, 2));
-    RB_TRY(rb_get_forces(s, x + 4 * n4, x + 5 * n4, 2));
+    RB_CUDA(cudaMemcpyAsync(state_host, s->pos, bytes, cudaMemcpyDeviceToHost, s->stream));
     return sync ? check_status(s) : RB_OK;
 }
 
