@@ -96,9 +96,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar = smem_u32(sm + Ly.bar + 8 * g);
     const uint32_t s_base = smem_u32(sm);
 
+    // Weights: bulk asynchronous copies on wbar, so that the first tile's
+    // pair data and features are formed while they arrive; each pipeline's
+    // leader waits for them before its first MMA.
+    const uint32_t wbar = smem_u32(sm + Ly.bar + 24);
+    if (tid == 0) {
+        mbar_init(wbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(img);
+        mbar_expect_tx(wbar, Ly.weights);
+        for (uint32_t o = 0; o < Ly.weights; o += 16384u) {
+            const uint32_t n = Ly.weights - o < 16384u ? Ly.weights - o : 16384u;
+            bulk_g2s(smem_u32(sm + o), src + o, n, wbar);
+        }
+    }
     {
-        uint4* dstw = reinterpret_cast<uint4*>(sm);
-        for (uint32_t t = tid; t < Ly.weights / 16; t += kThreads) dstw[t] = __ldg(img + t);
         for (int t = tid; t < D * kW; t += kThreads)  // half biases: silu2 works on z / 2
             hbias[t] = 0.5f * flat[fl.b_(1 + t / kW, kW) + t % kW];
         for (int t = tid; t < kW; t += kThreads) wo[t] = flat[fl.wo + t];
@@ -141,7 +153,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // one GEMM stage of this pipeline: publish the A tile, issue, wait
     // (bounded).  The publishing barrier also ORs the previous stage's failed
-    // waits, so every thread leaves through the same stage.
+    // waits, so every thread leaves through the same stage.  The leader first
+    // checks (bounded wait; at once after the first tile) that the weights
+    // have arrived; if they have not, it issues nothing and the stage's wait
+    // fails.
     auto stage = [&](uint32_t a_base, uint32_t b_base, int K, int rows_b, uint32_t idesc) {
         fence_proxy_async();
         fence_before();
@@ -149,7 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             return;
         }
-        if (leader) issue_gemm(tmem, a_base, b_base, K, rows_b, idesc, bar);
+        if (leader) {
+            if (mbar_wait(wbar, 0, kWaitCycles)) issue_gemm(tmem, a_base, b_base, K, rows_b, idesc, bar);
+        }
         waited = mbar_wait(bar, phase, kWaitCycles);
         phase ^= 1u;
         fence_after();
@@ -280,6 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     }
     if (wg_any(g, !waited)) ok = false;  // the last stage's wait
+    if (tid == 0) {  // no bulk copy may still be writing shared memory at exit
+        if (!mbar_wait(wbar, 0, kWaitCycles)) ok = false;
+    }
     fence_before();
     __syncthreads();
     if (warp == 0) {
