@@ -123,7 +123,7 @@ def combine_ranks(ms_step: float, units: float, device=None):
 
 
 def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=5,
-                rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None):
+                rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None, lanes=None):
     """Serving workload: cube/cylinder replicas with N log-uniform in
     [512, n_max], phi in [0.05, 0.25], kT in [0.5, 1.5], `steps` MD steps each,
     Poisson arrivals at rate_factor / (solo run time of the first request), so
@@ -152,14 +152,14 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
         path = api.RB_PATH_NN if (shape == "cube" and mlp is not None) else api.RB_PATH_BEADS
         reqs.append((st, L, shape, path))
     # calibration: one solo request to set the arrival rate
-    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8)
+    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
     st, L, shape, path = reqs[0]
     t0 = _t.perf_counter()
     srv.wait(srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4))
     t_solo = _t.perf_counter() - t0
     srv.close()
     gaps = rng.exponential(t_solo / rate_factor, size=n_requests)
-    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8)
+    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
     t0 = _t.perf_counter()
     tickets = []
     for (st, L, shape, path), g in zip(reqs, gaps):
@@ -171,7 +171,7 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     srv.close()
     # capacity: the same requests all submitted at once (a closed queue), so
     # the aggregate rate is the server's, not the arrival process's
-    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8)
+    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
     t0 = _t.perf_counter()
     tk = [srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4) for st, L, shape, path in reqs]
     for t in tk:

@@ -296,8 +296,10 @@ rb_status rb_restore(rb_system* sys, const char* path);
 /* MD steps taken by rb_step since creation (or as restored). */
 rb_status rb_get_step(const rb_system* sys, int64_t* step_host);
 
-/* Wait for the system's stream and report any sticky device-side error
- * (capacity overflow, non-finite values). */
+/* Wait for the system's stream and report any sticky device-side error:
+ * RB_EOVERFLOW (cell or neighbour capacity), RB_EFAULT (non-finite values,
+ * or a tensor-core kernel of the network path that gave up waiting for an
+ * MMA, its forces then invalid).  The flag is cleared once reported. */
 rb_status rb_sync(rb_system* sys);
 
 /* Bead-sum forces for callers that cannot allocate device memory (plug-ins of
@@ -538,11 +540,20 @@ int64_t rb_system_footprint(const rb_system_desc* desc);
 /* A server runs many independent MD replicas (the paper runs one simulation
  * per GPU; serving many is this library's extension) with continuous
  * batching: a scheduler thread admits queued requests whenever a slot is free
- * and the replica's footprint fits in `hbm_budget_bytes`, runs each resident
- * replica on its own stream (their work overlaps on the device), advances
- * every replica by `steps_per_tick` steps per tick, and retires finished ones.
- * A network-path replica whose forces turn non-finite is rolled back to the
- * start of its tick and continued on the bead path (rb_result.fell_back). */
+ * and the replica's footprint fits in `hbm_budget_bytes`, steps the resident
+ * replicas together (each MD step is one launch per phase for all of them:
+ * the per-body kernels over a grid split among the replicas, the pair
+ * kernels over their concatenated pair lists, as one CUDA graph; see
+ * rb_server_set_lanes for running several such batches side by side), advances
+ * them by `steps_per_tick` steps per tick (fewer when one finishes sooner),
+ * and retires finished ones.  A replica's result is bit for bit the same
+ * whatever else is resident; it is its own rb_step run's to rounding (the
+ * batched kernels do the same arithmetic, but the compiler may form their
+ * fused multiply-adds differently).  A network-path replica whose
+ * forces turn non-finite (or whose tensor-core kernel gave up waiting) is
+ * rolled back to the start of its tick and continued on the bead path
+ * (rb_result.fell_back).  step_ms_* are device times per step of the batch
+ * the replica was in. */
 typedef struct rb_server rb_server;
 typedef struct rb_result {
     int32_t status;      /* RB_OK, or the error that ended the request */
@@ -563,8 +574,17 @@ typedef struct rb_server_stats_t {
     double step_ms_p50, step_ms_p99;  /* over every step of every request */
 } rb_server_stats_t;
 
+/* 1 <= max_slots <= 32 resident replicas (RB_EINVAL otherwise); mlp may be
+ * NULL (bead path only); steps_per_tick <= 0 selects 8. */
 rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_mlp* mlp,
                            int32_t steps_per_tick, rb_server** out);
+/* Lanes the replicas admitted from now on are spread over, 1 <= lanes <= 8
+ * (RB_EINVAL otherwise; 2 when never set).  Each lane steps its replicas
+ * together, one launch per phase, on its own stream; each new replica joins
+ * the lane with the fewest resident bodies.  One lane gives every step of
+ * every replica one launch per phase; more lanes let one lane's list and
+ * reduction kernels run beside another's pair kernels. */
+rb_status rb_server_set_lanes(rb_server* server, int32_t lanes);
 /* Stops the scheduler; requests still resident end with RB_EINVAL. */
 rb_status rb_server_destroy(rb_server* server);
 /* Queue one replica: `desc` as rb_create_system; pos, quat, vel, angmom are

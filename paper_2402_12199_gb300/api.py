@@ -662,7 +662,7 @@ class Server:
     """rb_server_create / rb_submit / rb_poll / rb_wait / rb_fetch_state."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int, mlp: MLP = None,
-                 steps_per_tick: int = 8):
+                 steps_per_tick: int = 8, lanes: int = None):
         h = ctypes.c_void_p()
         check(load().rb_server_create(int(hbm_budget_bytes), int(max_slots),
                                       mlp.handle if mlp is not None else None,
@@ -670,6 +670,12 @@ class Server:
         self._h = h
         self.mlp = mlp
         self._n = {}
+        if lanes is not None:
+            self.set_lanes(lanes)
+
+    def set_lanes(self, lanes: int):
+        """rb_server_set_lanes: lanes the replicas admitted from now on are spread over."""
+        check(load().rb_server_set_lanes(self._h, int(lanes)))
 
     def close(self):
         h = getattr(self, "_h", None)

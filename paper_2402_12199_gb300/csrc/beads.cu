@@ -60,7 +60,11 @@ __device__ __forceinline__ void write_pair_result(int lane, int p, const float3 
     }
 }
 
-template <int NP, int C, int POT>
+// BATCH (column templates only, no sel): the pair lists of n_seg systems with
+// this template and potential (segs: their lists, bodies, boxes and outputs),
+// each padded to whole warp batches of 8 pairs, so that every batch belongs
+// to one system.
+template <int NP, int C, int POT, bool BATCH = false>
 __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
     k_bead_pairs(const int2* __restrict__ pairs, const int* __restrict__ n_pairs_ptr,
                  const float4* __restrict__ pos, const float4* __restrict__ quat,
@@ -68,16 +72,39 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
                  float3 invL, BeadPot pot, float cut2, int zero_beyond,
                  float4* __restrict__ out_F, float4* __restrict__ out_ti,
                  float4* __restrict__ out_tj, const int* __restrict__ sel,
-                 const int* __restrict__ sel_count) {
+                 const int* __restrict__ sel_count, const PairSeg* __restrict__ segs, int n_seg) {
+    static_assert(!BATCH || C > 0, "the batched form is the column kernel's");
     __shared__ float4 sT[kMaxBeads + 1];
     // generic: 2 float4 per template bead; columns: 1 float4 per column, then
     // 8 floats per column and 8 more (at most kMaxBeads / 5 columns)
     constexpr int kSN = C == 0 ? 2 * (kMaxBeads + kPadBeads) : kMaxBeads / 5 + 1 + 2 * (kMaxBeads / 5 + 2);
     __shared__ float4 sN[kSN];
+    // BATCH: each system's first padded pair slot (inclusive scan over n_seg
+    // <= 32 lanes) and its pair count
+    __shared__ int s_b0[BATCH ? kMaxSeg + 1 : 1], s_np[BATCH ? kMaxSeg : 1];
     pdl_wait();
+    int n_pairs;
+    if constexpr (BATCH) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const int np = lane < n_seg ? *segs[lane].n_pairs : 0;
+            int t = (np + 7) & ~7;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += v;
+            }
+            s_b0[lane + 1] = t;
+            if (lane == 0) s_b0[0] = 0;
+            s_np[lane] = np;
+        }
+        __syncthreads();
+        n_pairs = s_b0[n_seg];
+    } else {
+        n_pairs = sel ? *sel_count : *n_pairs_ptr;
+    }
     // a CTA with no pair (most of them when only the few fallback pairs are
     // listed) leaves before staging the template
-    const int n_pairs = sel ? *sel_count : *n_pairs_ptr;
     if ((int64_t)blockIdx.x * (blockDim.x >> 5) * (C > 0 ? 8 : 1) >= n_pairs) return;
     if (C == 0) {
         load_template(tmpl, n_beads, pot.rc2_test, sT, sN);
@@ -102,19 +129,45 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
         __shared__ float4 sP[8][kPB][3];
         float4(*wp)[3] = sP[threadIdx.x >> 5];
         for (int base = gw * kPB; base < n_pairs; base += nw * kPB) {
-            const int t = base + lane;
+            // this batch's system (BATCH: the last k with s_b0[k] <= base)
+            const int2* __restrict__ prs = pairs;
+            const float4* __restrict__ ps = pos;
+            const float4* __restrict__ qs = quat;
+            float3 Ls = L, iLs = invL;
+            float4* oF = out_F;
+            float4* oti = out_ti;
+            float4* otj = out_tj;
+            int t = base + lane, lim = n_pairs;
+            if constexpr (BATCH) {
+                int lo = 0, hi = n_seg - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_b0[mid] <= base) lo = mid; else hi = mid - 1;
+                }
+                const PairSeg& q = segs[lo];
+                prs = q.pairs;
+                ps = q.pos;
+                qs = q.quat;
+                Ls = q.L;
+                iLs = q.invL;
+                oF = q.F;
+                oti = q.ti;
+                otj = q.tj;
+                t = base - s_b0[lo] + lane;
+                lim = s_np[lo];
+            }
             bool work = false;
-            if (lane < kPB && t < n_pairs) {
+            if (lane < kPB && t < lim) {
                 const int p = sel ? sel[t] : t;
-                const int2 ij = pairs[p];
-                const float4 pi = pos[ij.x], pj = pos[ij.y];
-                const float4 qi = quat[ij.x], qj = quat[ij.y];
-                const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), L, invL);
+                const int2 ij = prs[p];
+                const float4 pi = ps[ij.x], pj = ps[ij.y];
+                const float4 qi = qs[ij.x], qj = qs[ij.y];
+                const float3 R = min_image(make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z), Ls, iLs);
                 if (R.x * R.x + R.y * R.y + R.z * R.z >= cut2) {
                     if (zero_beyond) {
-                        out_F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        out_ti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        out_tj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        oF[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        oti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        otj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 } else {
                     const float3 sv = mulT(qmat(qi), R);
@@ -127,9 +180,9 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
                         wp[lane][1] = qmul(qconj(qi), qj);
                         wp[lane][2] = qi;
                     } else {  // no bead of j within r_c of a bead of i
-                        out_F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        out_ti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        out_tj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        oF[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        oti[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        otj[p] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
             }
@@ -144,7 +197,7 @@ __global__ void __launch_bounds__(256, C == 0 ? 1 : (NP <= 2 ? 3 : 2))
                 bead_pair_warp_cols<NP, C, POT>(s, qmat(wp[l][1]), sT, sN,
                                                 reinterpret_cast<const float*>(sN + kMaxBeads / 5 + 1),
                                                 cols, n_beads, pot, lane, v);
-                write_pair_result(lane, __float_as_int(a0.w), s, wp[l][2], v, out_F, out_ti, out_tj);
+                write_pair_result(lane, __float_as_int(a0.w), s, wp[l][2], v, oF, oti, otj);
             }
             __syncwarp();  // the batch's slots are read before the next batch writes them
         }
@@ -212,7 +265,49 @@ static rb_status launch_beads(rb_system* s, float cut2, int zero_beyond, const i
     RB_CUDA(launch_pdl(k_bead_pairs<NP, C, POT>, grid, 256, 0, s->stream, s->pl.pairs, s->pl.n_pairs,
                        s->pos, s->quat, s->tmpl_dev, s->n_beads, s->cols, L, invL, bead_pot(s),
                        cut2, zero_beyond, s->pair_F, s->pair_ti, s->pair_tj, sel,
-                       s->fallback_count));
+                       s->fallback_count, (const PairSeg*)nullptr, 0));
+    return RB_OK;
+}
+
+template <int NP, int C, int POT>
+static rb_status launch_beads_batch(const rb_system* s, const PairSeg* segs, int n_seg, int grid_hint,
+                                    cudaStream_t st) {
+    static int occ = 0;
+    if (occ == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bead_pairs<NP, C, POT, true>, 256, 0);
+        if (occ <= 0) occ = 1;
+    }
+    const int grid = std::max(1, std::min(grid_hint, s->num_sms * occ));
+    RB_CUDA(launch_pdl(k_bead_pairs<NP, C, POT, true>, grid, 256, 0, st, (const int2*)nullptr,
+                       (const int*)nullptr, (const float4*)nullptr, (const float4*)nullptr,
+                       s->tmpl_dev, s->n_beads, s->cols, make_float3(0.f, 0.f, 0.f),
+                       make_float3(0.f, 0.f, 0.f), bead_pot(s), s->Rc * s->Rc, 1,
+                       (float4*)nullptr, (float4*)nullptr, (float4*)nullptr, (const int*)nullptr,
+                       (const int*)nullptr, segs, n_seg));
+    return RB_OK;
+}
+
+// The bead sum over the pair lists of several systems whose template and
+// potential are those of `like` (the caller groups them).  Batched kernels
+// exist for the column templates of the built-in cube (125 beads in columns
+// of 5) and cylinder (152 beads in columns of 8); for other templates *done
+// is false and nothing is launched.
+rb_status bead_pairs_batch_async(const rb_system* like, const PairSeg* segs_dev, int n_seg,
+                                 int grid_hint, cudaStream_t st, bool* done) {
+    *done = false;
+    if (n_seg < 1 || n_seg > kMaxSeg) return fail(RB_EINVAL, "batch of 1 to 32 systems");
+    const int np = (like->n_beads + 63) / 64;
+    const bool lj = like->pot_kind == RB_POT_LJ;
+    if (like->cols.len == 5 && np <= 2) {
+        *done = true;
+        return lj ? launch_beads_batch<2, 5, 0>(like, segs_dev, n_seg, grid_hint, st)
+                  : launch_beads_batch<2, 5, 1>(like, segs_dev, n_seg, grid_hint, st);
+    }
+    if (like->cols.len == 8 && np == 3) {
+        *done = true;
+        return lj ? launch_beads_batch<3, 8, 0>(like, segs_dev, n_seg, grid_hint, st)
+                  : launch_beads_batch<3, 8, 1>(like, segs_dev, n_seg, grid_hint, st);
+    }
     return RB_OK;
 }
 

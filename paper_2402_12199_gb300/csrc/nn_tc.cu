@@ -379,6 +379,11 @@ static bool tc_two_pipelines() {
     return v == 1;
 }
 
+bool nn_tc2p_batchable(const rb_mlp* m) {
+    return !nn_tc256_supported(m) && tc_supported(m) && tc_two_pipelines() && !m->pair_sym &&
+           m->desc != RB_DESC_PAPER6;
+}
+
 rb_status nn_tc_prepare(rb_mlp* m) {
     if (nn_tc256_supported(m)) return nn_tc256_prepare(m);
     if (!tc_supported(m)) return RB_OK;  // FP32 path only for other shapes

@@ -75,10 +75,13 @@ __device__ inline bool wg_any(int g, bool flag) {
 
 // PAPER6: the network takes the paper's six numbers (a compile-time switch:
 // the runtime branch of both descriptors costs this kernel register spills).
-template <bool SYSTEM, bool PAPER6>
+// BATCH: the pair lists of n_seg systems (segs: their lists, bodies, boxes
+// and outputs; src and dst give what they share), each padded to whole tiles,
+// so that every tile belongs to one system.
+template <bool SYSTEM, bool PAPER6, bool BATCH = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_nn_tc2p(const float* __restrict__ flat, const uint4* __restrict__ img, int D, PairSrc src,
-              PairDst dst, unsigned* status) {
+              PairDst dst, unsigned* status, const PairSeg* __restrict__ segs, int n_seg) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -131,6 +134,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     pdl_wait();  // weights staged; pair data below may come from the kernels just before
+    // BATCH: each system's first tile (s_t0, inclusive scan over n_seg <= 32
+    // lanes) and its pair count
+    __shared__ int s_t0[BATCH ? kMaxSeg + 1 : 1], s_np[BATCH ? kMaxSeg : 1];
+    if constexpr (BATCH) {
+        if (warp == 0) {
+            const int lane = tid & 31;
+            const int np = lane < n_seg ? *segs[lane].n_pairs : 0;
+            int t = (np + kM - 1) / kM;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += v;
+            }
+            s_t0[lane + 1] = t;
+            if (lane == 0) s_t0[0] = 0;
+            s_np[lane] = np;
+        }
+    }
     fence_proxy_async();
     fence_before();
     __syncthreads();
@@ -146,8 +167,48 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     bool ok = true;       // the same in every thread of the warpgroup
     bool waited = true;   // this thread's last MMA wait completed
-    const int64_t n_total = SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
-    const int64_t n_tiles = (n_total + kM - 1) / kM;
+    const int64_t n_total = BATCH ? 0 : SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
+    const int64_t n_tiles = BATCH ? (int64_t)s_t0[n_seg] : (n_total + kM - 1) / kM;
+    // the system of a tile (BATCH: last k with s_t0[k] <= tile, so systems
+    // with no tile are passed over), this thread's pair in it and whether it exists
+    auto locate = [&](int64_t tile, int& sg, int64_t& lp, bool& valid) {
+        if constexpr (BATCH) {
+            int lo = 0, hi = n_seg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_t0[mid] <= tile) lo = mid; else hi = mid - 1;
+            }
+            sg = lo;
+            lp = (tile - s_t0[lo]) * kM + row;
+            valid = tile < n_tiles && lp < s_np[lo];
+        } else {
+            sg = 0;
+            lp = tile * kM + row;
+            valid = lp < n_total;
+        }
+    };
+    auto seg_src = [&](int sg) {
+        PairSrc r = src;
+        if constexpr (BATCH) {
+            const PairSeg& q = segs[sg];
+            r.pairs = q.pairs;
+            r.pos = q.pos;
+            r.quat = q.quat;
+            r.L = q.L;
+            r.invL = q.invL;
+        }
+        return r;
+    };
+    auto seg_dst = [&](int sg) {
+        PairDst r = dst;
+        if constexpr (BATCH) {
+            const PairSeg& q = segs[sg];
+            r.F = q.F;
+            r.ti = q.ti;
+            r.tj = q.tj;
+        }
+        return r;
+    };
     const int64_t stride = 2 * (int64_t)gridDim.x;
     const int64_t first = (int64_t)blockIdx.x + (int64_t)g * gridDim.x;
 
@@ -172,11 +233,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_after();
     };
 
-    PairRaw raw = fetch_pair<SYSTEM>(src, first * kM + row, first * kM + row < n_total);
+    PairRaw raw;
+    {
+        int sg;
+        int64_t lp;
+        bool v;
+        locate(first, sg, lp, v);
+        raw = fetch_pair<SYSTEM>(seg_src(sg), lp, v);
+    }
     for (int64_t tile = first; tile < n_tiles && ok; tile += stride) {
-        const int64_t gp = tile * kM + row;
-        const bool valid = gp < n_total;
-        PairGeom geo = pair_geometry<SYSTEM>(src, raw);
+        int cur;
+        int64_t gp;
+        bool valid;
+        locate(tile, cur, gp, valid);
+        PairGeom geo = pair_geometry<SYSTEM>(seg_src(cur), raw);
         geo.paper6 = PAPER6;
         {
             // features in the first 16 columns of the activation tile (10
@@ -205,8 +275,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 stage(h_addr, s_base + Ly.wf[l], kW, kW, idesc_w);
             if (!ok) break;
             if (l == 1) {  // fetch the next tile's pair data while this one runs
-                const int64_t gn = (tile + stride) * kM + row;
-                raw = fetch_pair<SYSTEM>(src, gn, gn < n_total);
+                int sg;
+                int64_t gn;
+                bool v;
+                locate(tile + stride, sg, gn, v);
+                raw = fetch_pair<SYSTEM>(seg_src(sg), gn, v);
             }
             const float* hb = hbias + (l - 1) * kW;
             float2 e2 = make_float2(0.f, 0.f);
@@ -292,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float gx[kIn];
 #pragma unroll
                 for (int k = 0; k < kIn; ++k) gx[k] = e_scale * v[k] * isd[k];
-                write_pair_outputs<SYSTEM>(dst, gp, geo, gx, E);
+                write_pair_outputs<SYSTEM>(seg_dst(cur), gp, geo, gx, E);
             }
         }
     }
@@ -307,29 +380,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot),
                      "r"(512));
     }
-    if (!ok && leader) atomicOr(status, ST_TC_TIMEOUT);
+    if (!ok && leader) {
+        if constexpr (BATCH) {
+            for (int k = 0; k < n_seg; ++k) atomicOr(segs[k].status, ST_TC_TIMEOUT);
+        } else {
+            atomicOr(status, ST_TC_TIMEOUT);
+        }
+    }
 }
 
 }  // namespace tc2p
 
-template <bool SYSTEM, bool P6>
+template <bool SYSTEM, bool P6, bool BATCH = false>
 static rb_status launch_tc2p_impl(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
-                                  const PairDst& dst, unsigned* status) {
+                                  const PairDst& dst, unsigned* status,
+                                  const PairSeg* segs = nullptr, int n_seg = 0) {
     const tc2p::Layout L = tc2p::layout(m->depth);
     const size_t smem = L.total + 1024;
     static bool attr = false;
     if (!attr) {
-        RB_CUDA(cudaFuncSetAttribute(tc2p::k_nn_tc2p<SYSTEM, P6>,
+        RB_CUDA(cudaFuncSetAttribute(tc2p::k_nn_tc2p<SYSTEM, P6, BATCH>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     if (SYSTEM)  // inside an MD step: may start while the list kernels drain
-        RB_CUDA(launch_pdl(tc2p::k_nn_tc2p<SYSTEM, P6>, grid, tc2p::kThreads, smem, stream,
+        RB_CUDA(launch_pdl(tc2p::k_nn_tc2p<SYSTEM, P6, BATCH>, grid, tc2p::kThreads, smem, stream,
                            m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst,
-                           status));
+                           status, segs, n_seg));
     else
-        tc2p::k_nn_tc2p<SYSTEM, P6><<<grid, tc2p::kThreads, smem, stream>>>(
-            m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status);
+        tc2p::k_nn_tc2p<SYSTEM, P6, BATCH><<<grid, tc2p::kThreads, smem, stream>>>(
+            m->params, static_cast<const uint4*>(m->bf16_img), m->depth, src, dst, status, segs,
+            n_seg);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -346,5 +427,22 @@ template rb_status launch_tc2p<true>(const rb_mlp*, cudaStream_t, int, const Pai
                                      const PairDst&, unsigned*);
 template rb_status launch_tc2p<false>(const rb_mlp*, cudaStream_t, int, const PairSrc&,
                                       const PairDst&, unsigned*);
+
+// The BF16 network over the pair lists of n_seg systems with the body type of
+// `like` (the same kernel, and so the same results per pair, as one system's
+// pass; the paper's six-number input and the pair-symmetrised form are not
+// batched).  A timed-out MMA wait is flagged in every system's status word.
+rb_status nn_tc2p_batch_async(const rb_mlp* m, const rb_system* like, const PairSeg* segs_dev,
+                              int n_seg, int grid, cudaStream_t st) {
+    if (n_seg < 1 || n_seg > kMaxSeg) return fail(RB_EINVAL, "batch of 1 to 32 systems");
+    if (!nn_tc2p_batchable(m) || !m->bf16_img)
+        return fail(RB_EINVAL, "network form without a batched kernel");
+    PairSrc src{};
+    set_symmetry(src, m);
+    src.Rc2 = like->Rc * like->Rc;
+    PairDst dst{};
+    set_cutoff(dst, m);
+    return launch_tc2p_impl<true, false, true>(m, st, grid, src, dst, nullptr, segs_dev, n_seg);
+}
 
 }  // namespace rb

@@ -326,4 +326,91 @@ __global__ void k_adam(int64_t n, int64_t lo, int64_t hi, float* __restrict__ p,
                        const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        float lr, float b1, float b2, float eps, float c1, float c2);
 rb_status check_mlp(const rb_mlp* m);
+
+// ---------------------------------------------------------------- batched step
+// One MD step of several independent systems (serving replicas) with one
+// launch per phase: the per-body kernels run over a flattened grid whose
+// blocks are split among the systems (a table of per-system arguments, one
+// segment each), the pair kernels over the concatenated pair lists (each
+// system's list padded to whole tiles or warp batches).
+constexpr int kMaxSeg = 32;  // systems in one batch
+constexpr int kBatchPhases = 5;  // integrate, cell assign, pair build, pair emit, reduce
+
+// One system's slice of a batched pair kernel.
+struct PairSeg {
+    unsigned* status;  // the system's status word
+    const int2* pairs;
+    const int* n_pairs;
+    const float4* pos;
+    const float4* quat;
+    float3 L, invL;
+    float4* F;
+    float4* ti;
+    float4* tj;
+};
+
+// One system's arguments of the batched per-body kernels.
+struct StepSeg {
+    int N;
+    float dt, inv_mass, half_skin2;
+    float3 invI, L, invL, invw;
+    int3 nc;
+    float4 *pos, *quat, *vel, *angmom, *force, *torque, *pos_ref;
+    int4* image;
+    int* rebuild;
+    unsigned* status;
+    int force_rebuild;  // no skin: every step rebuilds the list
+    int* cell_count;
+    int* cell_bodies;
+    int cell_cap, n_cells;
+    float Rl2;
+    int max_nbr;
+    int *half_count, *half_nbr, *lower_count, *lower_nbr, *half_off, *n_pairs, *done;
+    int64_t cap_pairs;
+    int2* pairs;
+    const float4 *pF, *pti, *ptj;
+};
+
+// A member of a batch: the system, its force path and precision, its time step.
+struct BatchMember {
+    rb_system* s;
+    int path, precision;
+    float dt;
+};
+struct StepBatch;
+// Device tables of a batch (kMaxSeg systems) and the stream its graphs are
+// captured on, allocated once by its owner and reused by every batch made on
+// them (one batch in use at a time).
+constexpr int kBatchBranches = 4;  // parallel branches of the pair phase
+struct BatchTables {
+    StepSeg* step = nullptr;
+    PairSeg* pair = nullptr;
+    int* start = nullptr;  // kBatchPhases x (kMaxSeg + 1) first blocks
+    cudaStream_t cap = nullptr;
+    cudaStream_t branch[kBatchBranches] = {};  // capture: the pair phase's branches
+    cudaEvent_t fork = nullptr, join[kBatchBranches] = {};
+};
+rb_status batch_tables_alloc(BatchTables* t);
+void batch_tables_free(BatchTables* t);
+// Checks that every member can be batched (NVE, no bead fallback, at most
+// kMaxSeg members, all on one device), writes the tables (synchronously: no
+// step of an earlier batch on them may be in flight) and captures the step as
+// one CUDA graph.  The network's images are prepared here (outside capture).
+// The members' forces must be valid for their paths.
+rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
+                       const BatchTables& tables, StepBatch** out);
+// n_steps MD steps of every member, on `stream`; each member's step counter advances.
+rb_status batch_step(StepBatch* b, cudaStream_t stream);
+void batch_destroy(StepBatch* b);
+// beads.cu: the bead sum over the pairs of several systems with one template
+// and potential (taken from `like`); false in *done if this template has no
+// batched kernel (the caller then launches per system).
+rb_status bead_pairs_batch_async(const rb_system* like, const PairSeg* segs_dev, int n_seg,
+                                 int grid_hint, cudaStream_t st, bool* done);
+// nn_tc2p.cu: the BF16 network over the pairs of several systems.
+rb_status nn_tc2p_batch_async(const rb_mlp* m, const rb_system* like, const PairSeg* segs_dev,
+                              int n_seg, int grid, cudaStream_t st);
+// nn_tc.cu: whether a system pass of this network at BF16 runs the two-pipeline
+// kernel (the one with a batched form)
+bool nn_tc2p_batchable(const rb_mlp* m);
 }  // namespace rb

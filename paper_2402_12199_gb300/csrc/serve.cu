@@ -6,18 +6,32 @@
 //   - requests wait in arrival order; each is admitted as soon as a slot is
 //     free and its device footprint fits in the memory budget (first fit over
 //     the queue, so a large request does not block smaller ones behind it);
-//   - each resident replica is its own rb_system on its own CUDA stream, so
-//     the step graphs of different replicas overlap on the device;
-//   - every tick enqueues a chunk of steps per replica whose previous chunk has
-//     completed (CUDA event query, no blocking), with one event per step, from
-//     which the per-step device latency is harvested;
+//   - the resident replicas step together in lanes (two by default; each
+//     replica joins the lane with the fewest bodies): every step of a lane is one launch per
+//     phase for all of its replicas (a StepBatch, captured as one CUDA
+//     graph: the per-body kernels over a grid split among the replicas, the
+//     pair kernels over their concatenated pair lists), so a small replica
+//     does not occupy the GPU with launches of its own; the lanes run on
+//     their own streams, so one lane's list and reduction kernels overlap
+//     another's pair kernels;
+//   - a tick runs `chunk` steps (fewer when a replica finishes sooner), with
+//     one event per step, from which the per-step device time is harvested;
+//     at its end one small kernel gathers every replica's status word and
+//     pair count into one copy, so the host learns of faults and counts
+//     without a synchronisation per replica;
+//   - the next tick is queued while the current one runs (two in flight at
+//     most, each with its own events, gather buffers and state backups; a
+//     new batch for a changed set is built on the second of two table sets
+//     meanwhile), so the GPU does not wait for the host between ticks;
 //   - a network-path replica whose forces turn non-finite is rolled back to
-//     the state at the start of the chunk and continued on the bead path;
+//     the state at the start of the tick and continued on the bead path;
 //   - finished replicas are retired (final state copied to host, memory
-//     freed) and their slots reused at once.
-// All kernels are deterministic, so a replica's result does not depend on
-// what else is resident.
+//     freed), their slots reused, and the batch rebuilt for the new set.
+// Every kernel is deterministic and a replica's arithmetic in the batch does
+// not depend on the other members, so its result does not depend on what
+// else is resident.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -49,13 +63,55 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit, t_admit, t_finish;
     // device side (scheduler thread only)
     rb_system* sys = nullptr;
-    cudaStream_t stream = nullptr;
-    std::vector<cudaEvent_t> ev;  // events of the chunk in flight (first = chunk start)
-    int64_t chunk_n = 0;
-    float4* backup = nullptr;     // state at the start of the chunk in flight (4 x N)
+    cudaStream_t stream = nullptr;  // set-up, roll-back and retirement
+    float4* backup[2] = {nullptr, nullptr};  // state at the start of a tick (4 x N), per tick slot
+    int lane = 0;
+    int64_t inflight = 0;   // steps queued in ticks not yet harvested
+    bool discard = false;   // results of the ticks in flight are void (rolled back or failed)
     std::vector<float> step_ms;
     double e_start = 0, e_end = 0;
     int64_t pairs_last = 0;
+};
+
+// Status words and pair counts of the members, gathered at the end of a tick.
+struct GatherArgs {
+    const unsigned* status[kMaxSeg];
+    const int* n_pairs[kMaxSeg];
+    int n;
+};
+
+__global__ void k_gather(GatherArgs a, unsigned* out) {
+    const int k = threadIdx.x;
+    if (k < a.n) {
+        out[k] = *a.status[k];
+        out[kMaxSeg + k] = (unsigned)*a.n_pairs[k];
+    }
+}
+
+struct Tick {
+    int64_t n = 0;
+    int slot = 0;
+    StepBatch* batch = nullptr;
+    std::vector<Request*> members;  // in the batch's order
+};
+
+// A lane: replicas stepped together by one batch on one stream.
+constexpr int kMaxLanes = 8;
+struct Lane {
+    bool ready = false;                       // its streams and buffers exist
+    cudaStream_t stream = nullptr;            // the batches' steps
+    BatchTables tables[2];
+    int batch_set = 0;                        // table set of `batch`
+    StepBatch* batch = nullptr;
+    std::vector<Request*> members;            // of `batch`, in its order
+    std::vector<int> member_paths;
+    std::vector<StepBatch*> retired;          // older batches with ticks still in flight
+    std::deque<Tick> ticks;                   // in flight, oldest first (at most 2)
+    int next_slot = 0;
+    std::vector<cudaEvent_t> ev[2];           // per tick slot: step events
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};  // per tick slot: after the gather copy
+    unsigned* gather_dev[2] = {nullptr, nullptr};  // 2 x kMaxSeg words each
+    unsigned* gather_host[2] = {nullptr, nullptr}; // pinned copies
 };
 
 }  // namespace rb
@@ -78,15 +134,18 @@ struct rb_server {
     std::thread worker;
     std::vector<float> all_step_ms;
     double pair_evals = 0;
+    std::atomic<int> n_lanes{2};              // lanes new replicas are spread over
+    // scheduler thread only
+    rb::Lane lane[rb::kMaxLanes];
 };
 
 namespace rb {
 
 static void release_device(Request* r) {
-    for (cudaEvent_t e : r->ev) cudaEventDestroy(e);
-    r->ev.clear();
-    if (r->backup) cudaFree(r->backup);
-    r->backup = nullptr;
+    for (float4*& b : r->backup) {
+        if (b) cudaFree(b);
+        b = nullptr;
+    }
     if (r->sys) rb_destroy_system(r->sys);
     r->sys = nullptr;
     if (r->stream) cudaStreamDestroy(r->stream);
@@ -97,14 +156,14 @@ static rb_status start_replica(rb_server* sv, Request* r) {
     RB_CUDA(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
     RB_TRY(rb_create_system(&r->desc, r->stream, &r->sys));
     RB_TRY(rb_set_state(r->sys, r->pos.data(), r->quat.data(), r->vel.data(), r->angmom.data(), 1));
-    RB_CUDA(cudaMalloc(&r->backup, sizeof(float4) * 4 * r->desc.n_bodies));
+    for (float4*& b : r->backup) RB_CUDA(cudaMalloc(&b, sizeof(float4) * 4 * r->desc.n_bodies));
     const rb_mlp* m = r->path == RB_PATH_NN ? sv->mlp : nullptr;
     if (r->path == RB_PATH_NN)
         RB_TRY(rb_forces_nn(r->sys, m, r->precision, nullptr, nullptr, nullptr, nullptr));
     else
         RB_TRY(rb_forces_beads(r->sys, nullptr, nullptr, nullptr, nullptr));
     double ep = 0, kt = 0, kr = 0;
-    rb_status st = rb_energy(r->sys, &ep, &kt, &kr);
+    rb_status st = rb_energy(r->sys, &ep, &kt, &kr);  // synchronises the replica's stream
     if (st == RB_EFAULT && r->path == RB_PATH_NN) {  // network unusable from the start
         r->fell_back = true;
         r->path = RB_PATH_BEADS;
@@ -114,67 +173,6 @@ static rb_status start_replica(rb_server* sv, Request* r) {
     RB_TRY(st);
     r->e_start = ep + kt + kr;
     return RB_OK;
-}
-
-static rb_status launch_chunk(rb_server* sv, Request* r) {
-    const int64_t n = std::min<int64_t>(sv->chunk, r->n_steps - r->done);
-    // the backup block has the state's layout (pos | quat | vel | angmom): one copy
-    float* bk = (float*)r->backup;
-    const int64_t n4 = 4 * r->desc.n_bodies;
-    RB_TRY(rb_get_state(r->sys, bk, bk + n4, bk + 2 * n4, bk + 3 * n4, 0));
-    while ((int64_t)r->ev.size() < n + 1) {
-        cudaEvent_t e;
-        RB_CUDA(cudaEventCreate(&e));
-        r->ev.push_back(e);
-    }
-    const rb_mlp* m = r->path == RB_PATH_NN ? sv->mlp : nullptr;
-    RB_CUDA(cudaEventRecord(r->ev[0], r->stream));
-    for (int64_t k = 0; k < n; ++k) {
-        RB_TRY(rb_step(r->sys, r->path, m, r->precision, 1, r->dt));
-        RB_CUDA(cudaEventRecord(r->ev[k + 1], r->stream));
-    }
-    r->chunk_n = n;
-    return RB_OK;
-}
-
-// Returns true when the chunk in flight has completed and was harvested.
-static bool harvest_chunk(rb_server* sv, Request* r) {
-    if (r->chunk_n == 0) return true;
-    if (cudaEventQuery(r->ev[r->chunk_n]) != cudaSuccess) return false;
-    rb_status st = rb_sync(r->sys);
-    if (st == RB_EFAULT && r->path == RB_PATH_NN) {
-        // roll back to the chunk start and continue on the bead path
-        const float4* bk = r->backup;
-        rb_set_state(r->sys, (const float*)bk, (const float*)(bk + r->desc.n_bodies),
-                     (const float*)(bk + 2 * r->desc.n_bodies),
-                     (const float*)(bk + 3 * r->desc.n_bodies), 0);
-        r->fell_back = true;
-        r->path = RB_PATH_BEADS;
-        r->chunk_n = 0;
-        return true;
-    }
-    if (st != RB_OK) {
-        r->status = st;
-        r->chunk_n = 0;
-        return true;
-    }
-    for (int64_t k = 0; k < r->chunk_n; ++k) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, r->ev[k], r->ev[k + 1]);
-        r->step_ms.push_back(ms);
-    }
-    int64_t np = 0;
-    rb_get_pairs(r->sys, nullptr, 0, &np);
-    r->pairs_last = np;
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        sv->pair_evals += (double)np * (double)r->chunk_n;
-        for (int64_t k = 0; k < r->chunk_n; ++k)
-            sv->all_step_ms.push_back(r->step_ms[r->step_ms.size() - r->chunk_n + k]);
-    }
-    r->done += r->chunk_n;
-    r->chunk_n = 0;
-    return true;
 }
 
 static void finish(rb_server* sv, Request* r) {
@@ -194,8 +192,209 @@ static void finish(rb_server* sv, Request* r) {
     sv->cv.notify_all();
 }
 
+static bool batch_in_flight(const Lane* sv, const StepBatch* b) {
+    for (const Tick& t : sv->ticks)
+        if (t.batch == b) return true;
+    return false;
+}
+
+// The batch for `act` (same members, same paths: the current one), else a
+// new one on the other table set, which must have no tick in flight.
+// Returns RB_EBUSY if it cannot be built now.
+static rb_status ensure_batch(Lane* sv, const rb_mlp* mlp, const std::vector<Request*>& act) {
+    std::vector<int> paths;
+    for (Request* r : act) paths.push_back(r->path);
+    if (sv->batch && act == sv->members && paths == sv->member_paths) return RB_OK;
+    for (const Tick& t : sv->ticks)  // the other set's last batch still running
+        if (t.batch != sv->batch) return RB_EBUSY;
+    const int set = sv->batch ? 1 - sv->batch_set : sv->batch_set;
+    std::vector<BatchMember> mem;
+    for (Request* r : act) mem.push_back({r->sys, r->path, r->precision, r->dt});
+    StepBatch* b = nullptr;
+    RB_TRY(batch_create(mem, mlp, sv->tables[set], &b));
+    if (sv->batch) {
+        if (batch_in_flight(sv, sv->batch))
+            sv->retired.push_back(sv->batch);
+        else
+            batch_destroy(sv->batch);
+    }
+    sv->batch = b;
+    sv->batch_set = set;
+    sv->members = act;
+    sv->member_paths = paths;
+    return RB_OK;
+}
+
+// Queues one tick of the current batch: a backup of each network-path
+// member's state, n steps (an event after each) and the gather of status
+// words and pair counts.
+static rb_status launch_tick(Lane* sv, int64_t n) {
+    const int slot = sv->next_slot;
+    for (Request* r : sv->members)
+        if (r->path == RB_PATH_NN)  // the state block starts with pos | quat | vel | angmom
+            RB_CUDA(cudaMemcpyAsync(r->backup[slot], r->sys->pos,
+                                    sizeof(float4) * 4 * r->desc.n_bodies,
+                                    cudaMemcpyDeviceToDevice, sv->stream));
+    std::vector<cudaEvent_t>& ev = sv->ev[slot];
+    while ((int64_t)ev.size() < n + 1) {
+        cudaEvent_t e;
+        RB_CUDA(cudaEventCreate(&e));
+        ev.push_back(e);
+    }
+    RB_CUDA(cudaEventRecord(ev[0], sv->stream));
+    for (int64_t k = 0; k < n; ++k) {
+        RB_TRY(batch_step(sv->batch, sv->stream));
+        RB_CUDA(cudaEventRecord(ev[k + 1], sv->stream));
+    }
+    GatherArgs a{};
+    a.n = (int)sv->members.size();
+    for (int k = 0; k < a.n; ++k) {
+        a.status[k] = sv->members[k]->sys->status_dev;
+        a.n_pairs[k] = sv->members[k]->sys->pl.n_pairs;
+    }
+    k_gather<<<1, kMaxSeg, 0, sv->stream>>>(a, sv->gather_dev[slot]);
+    RB_CUDA(cudaGetLastError());
+    RB_CUDA(cudaMemcpyAsync(sv->gather_host[slot], sv->gather_dev[slot],
+                            sizeof(unsigned) * 2 * kMaxSeg, cudaMemcpyDeviceToHost, sv->stream));
+    RB_CUDA(cudaEventRecord(sv->ev_done[slot], sv->stream));
+    Tick t;
+    t.n = n;
+    t.slot = slot;
+    t.batch = sv->batch;
+    t.members = sv->members;
+    for (Request* r : t.members) r->inflight += n;
+    sv->ticks.push_back(t);
+    sv->next_slot ^= 1;
+    return RB_OK;
+}
+
+// The oldest tick in flight, once complete: step times, pair counts and
+// faults of its members.  Returns false while it is still running.
+static bool harvest_tick(rb_server* server, Lane* sv) {
+    if (sv->ticks.empty()) return false;
+    Tick t = sv->ticks.front();
+    if (cudaEventQuery(sv->ev_done[t.slot]) != cudaSuccess) return false;
+    sv->ticks.pop_front();
+    std::vector<float> ms(t.n, 0.f);
+    for (int64_t k = 0; k < t.n; ++k) cudaEventElapsedTime(&ms[k], sv->ev[t.slot][k], sv->ev[t.slot][k + 1]);
+    const unsigned* gh = sv->gather_host[t.slot];
+    for (size_t k = 0; k < t.members.size(); ++k) {
+        Request* r = t.members[k];
+        r->inflight -= t.n;
+        if (r->discard) {  // rolled back or failed after an earlier tick
+            if (r->inflight == 0) r->discard = false;
+            continue;
+        }
+        if (gh[k] != 0) {  // a fault flag: settle it with the system's own report
+            if (r->inflight > 0) {  // a later tick of this member is queued: let it end, void it
+                cudaStreamSynchronize(sv->stream);
+                r->discard = true;
+            }
+            rb_status st = rb_sync(r->sys);
+            if (st == RB_EFAULT && r->path == RB_PATH_NN) {
+                // roll back to this tick's start and continue on the bead path
+                const float4* bk = r->backup[t.slot];
+                const int64_t N = r->desc.n_bodies;
+                st = rb_set_state(r->sys, (const float*)bk, (const float*)(bk + N),
+                                  (const float*)(bk + 2 * N), (const float*)(bk + 3 * N), 0);
+                if (st == RB_OK) st = rb_forces_beads(r->sys, nullptr, nullptr, nullptr, nullptr);
+                if (st == RB_OK) st = rb_sync(r->sys);
+                r->fell_back = true;
+                r->path = RB_PATH_BEADS;
+                if (st != RB_OK) r->status = st;
+                continue;
+            }
+            if (st != RB_OK) {
+                r->status = st;
+                continue;
+            }
+        }
+        r->step_ms.insert(r->step_ms.end(), ms.begin(), ms.end());
+        r->pairs_last = (int64_t)gh[kMaxSeg + k];
+        r->done += t.n;
+        std::lock_guard<std::mutex> lk(server->mu);
+        server->pair_evals += (double)r->pairs_last * (double)t.n;
+        server->all_step_ms.insert(server->all_step_ms.end(), ms.begin(), ms.end());
+    }
+    // a retired batch with no tick left in flight
+    for (auto it = sv->retired.begin(); it != sv->retired.end();) {
+        if (!batch_in_flight(sv, *it)) {
+            batch_destroy(*it);
+            it = sv->retired.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return true;
+}
+
+static void lane_release(Lane* L) {
+    if (!L->ready) return;
+    L->ready = false;
+    batch_destroy(L->batch);
+    L->batch = nullptr;
+    for (StepBatch* b : L->retired) batch_destroy(b);
+    L->retired.clear();
+    for (int k = 0; k < 2; ++k) {
+        for (cudaEvent_t e : L->ev[k]) cudaEventDestroy(e);
+        L->ev[k].clear();
+        if (L->ev_done[k]) cudaEventDestroy(L->ev_done[k]);
+        if (L->gather_dev[k]) cudaFree(L->gather_dev[k]);
+        if (L->gather_host[k]) cudaFreeHost(L->gather_host[k]);
+        batch_tables_free(&L->tables[k]);
+    }
+    if (L->stream) cudaStreamDestroy(L->stream);
+    L->stream = nullptr;
+}
+
+static bool lane_init(Lane* L) {
+    if (L->ready) return true;
+    bool ok = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = batch_tables_alloc(&L->tables[k]) == RB_OK &&
+             cudaEventCreateWithFlags(&L->ev_done[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaMalloc(&L->gather_dev[k], sizeof(unsigned) * 2 * kMaxSeg) == cudaSuccess &&
+             cudaMallocHost(&L->gather_host[k], sizeof(unsigned) * 2 * kMaxSeg) == cudaSuccess;
+    L->ready = ok;
+    return ok;
+}
+
+// Queues the lane's next tick if fewer than two are in flight: every replica
+// of the lane with steps left beyond those already queued.
+static bool lane_launch(rb_server* sv, Lane* L, int li) {
+    if (L->ticks.size() >= 2) return false;
+    std::vector<Request*> next;
+    int64_t n = sv->chunk;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (Request* r : sv->active) {
+            const int64_t left = r->n_steps - r->done - r->inflight;
+            if (r->lane == li && r->status == RB_OK && !r->discard && left > 0) {
+                next.push_back(r);
+                n = std::min(n, left);
+            }
+        }
+    }
+    if (next.empty()) return false;
+    rb_status st = ensure_batch(L, sv->mlp, next);
+    if (st == RB_EBUSY) return false;
+    if (st == RB_OK) st = launch_tick(L, n);
+    if (st != RB_OK) {  // no tick for this set: end its members
+        cudaStreamSynchronize(L->stream);
+        while (harvest_tick(sv, L)) {
+        }
+        for (Request* r : next) r->status = st;
+    }
+    return true;
+}
+
 static void worker_loop(rb_server* sv) {
     cudaSetDevice(sv->device);
+    const bool ok = lane_init(&sv->lane[0]);
+    if (!ok) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;  // requests end at shutdown below
+    }
     for (;;) {
         std::vector<Request*> admitted;
         {
@@ -206,6 +405,13 @@ static void worker_loop(rb_server* sv) {
                 if ((int)sv->active.size() >= sv->max_slots) break;
                 if (sv->used + (size_t)r->footprint <= sv->budget) {
                     sv->used += (size_t)r->footprint;
+                    // the lane with the fewest resident bodies
+                    const int nl = sv->n_lanes.load();
+                    int64_t load[kMaxLanes] = {};
+                    for (Request* a : sv->active) load[a->lane] += a->desc.n_bodies;
+                    r->lane = 0;
+                    for (int k = 1; k < nl; ++k)
+                        if (load[k] < load[r->lane]) r->lane = k;
                     sv->active.push_back(r);
                     r->state = 1;
                     r->t_admit = std::chrono::steady_clock::now();
@@ -217,38 +423,46 @@ static void worker_loop(rb_server* sv) {
             }
             sv->peak_resident = std::max<int64_t>(sv->peak_resident, (int64_t)sv->active.size());
         }
+        // set-up runs on the new replicas' own streams while ticks are in flight
         for (Request* r : admitted) {
-            rb_status st = start_replica(sv, r);
+            rb_status st = lane_init(&sv->lane[r->lane]) ? start_replica(sv, r)
+                                                         : fail(RB_ECUDA, "lane set-up failed");
             if (st != RB_OK) {
                 r->status = st;
                 finish(sv, r);
             }
         }
+        bool progressed = !admitted.empty();
+        for (Lane& L : sv->lane)
+            while (harvest_tick(sv, &L)) progressed = true;
         std::vector<Request*> act;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             act = sv->active;
         }
-        bool progressed = !admitted.empty();
-        for (Request* r : act) {
-            if (!harvest_chunk(sv, r)) continue;
-            progressed = true;
-            if (r->status != RB_OK || r->done >= r->n_steps) {
+        // retire what is done or failed and has nothing in flight
+        for (Request* r : act)
+            if (r->inflight == 0 && (r->status != RB_OK || r->done >= r->n_steps)) {
                 finish(sv, r);
-                continue;
+                progressed = true;
             }
-            rb_status st = launch_chunk(sv, r);
-            if (st != RB_OK) {
-                r->status = st;
-                finish(sv, r);
-            }
-        }
+        for (int li = 0; li < kMaxLanes; ++li)
+            if (sv->lane[li].ready && lane_launch(sv, &sv->lane[li], li)) progressed = true;
         if (!progressed) {
+            bool busy = false;
+            for (const Lane& L : sv->lane) busy = busy || !L.ticks.empty();
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv.wait_for(lk, std::chrono::microseconds(50));
+            sv->cv.wait_for(lk, std::chrono::microseconds(busy ? 20 : 50));
         }
     }
     // shut down: drain whatever is resident
+    for (Lane& L : sv->lane) {
+        if (!L.ready) continue;
+        cudaStreamSynchronize(L.stream);
+        while (harvest_tick(sv, &L)) {
+        }
+        L.ticks.clear();
+    }
     std::vector<Request*> act;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -259,6 +473,7 @@ static void worker_loop(rb_server* sv) {
         r->status = RB_EINVAL;
         finish(sv, r);
     }
+    for (Lane& L : sv->lane) lane_release(&L);
 }
 
 static double percentile(std::vector<float> v, double q) {
@@ -295,7 +510,8 @@ rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_
                            int32_t steps_per_tick, rb_server** out) {
     if (!out) return fail(RB_EINVAL, "null out");
     *out = nullptr;
-    if (max_slots < 1 || hbm_budget_bytes == 0) return fail(RB_EINVAL, "need max_slots >= 1 and a budget");
+    if (max_slots < 1 || max_slots > kMaxSeg || hbm_budget_bytes == 0)
+        return fail(RB_EINVAL, "need 1 <= max_slots <= 32 and a budget");
     rb_server* sv = new (std::nothrow) rb_server();
     if (!sv) return fail(RB_ENOMEM, "host allocation");
     sv->budget = hbm_budget_bytes;
@@ -305,6 +521,13 @@ rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_
     cudaGetDevice(&sv->device);
     sv->worker = std::thread(worker_loop, sv);
     *out = sv;
+    return RB_OK;
+}
+
+rb_status rb_server_set_lanes(rb_server* sv, int32_t lanes) {
+    if (!sv) return fail(RB_EINVAL, "null server");
+    if (lanes < 1 || lanes > kMaxLanes) return fail(RB_EINVAL, "1 <= lanes <= 8");
+    sv->n_lanes.store(lanes);
     return RB_OK;
 }
 

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 
 #include "rb_internal.cuh"
@@ -69,14 +70,15 @@ __device__ inline double nh_half(double& xi, double& eta, double& K, double h, c
 // then sees every other CTA's writes (each thread fences before the CTA
 // barrier, thread 0 fences and counts; the last CTA fences again before it
 // reads).  That CTA resets the counter for the next launch.  No CTA waits on
-// another, so this needs no co-residency.
-__device__ inline bool last_cta_done(int* done) {
+// another, so this needs no co-residency.  nblk: the CTAs that count (the
+// kernel's grid, or one system's share of a batched grid).
+__device__ inline bool last_cta_done(int* done, int nblk) {
     __shared__ int is_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const int prev = atomicAdd(done, 1);
-        is_last = prev == (int)gridDim.x - 1;
+        is_last = prev == nblk - 1;
         if (is_last) *done = 0;
     }
     __syncthreads();
@@ -124,14 +126,19 @@ __device__ inline void scan_counts(const int* __restrict__ cnt, int N, int* __re
 
 // zero_count (nullable): a counter this step's later kernels append to (the
 // bead-fallback list), reset here so that it needs no launch of its own.
-__global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, float3 invL,
-                              float3 invw, int3 nc, int* __restrict__ count,
-                              int* __restrict__ bodies, int cap, unsigned* status,
-                              const int* __restrict__ rebuild, int* zero_count) {
+// The per-body kernels below are written as bodies that take the block's
+// index among the system's blocks (bid) and their number (nblk): the kernel
+// of one system passes its own grid, the batched kernels a system's share.
+__device__ __forceinline__ void cell_assign_body(const float4* __restrict__ pos, int N, float3 L,
+                                                 float3 invL, float3 invw, int3 nc,
+                                                 int* __restrict__ count, int* __restrict__ bodies,
+                                                 int cap, unsigned* status,
+                                                 const int* __restrict__ rebuild, int* zero_count,
+                                                 int bid) {
     pdl_wait();
-    if (zero_count && blockIdx.x == 0 && threadIdx.x == 0) *zero_count = 0;
+    if (zero_count && bid == 0 && threadIdx.x == 0) *zero_count = 0;
     if (!*rebuild) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float4 p = pos[i];
     float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
@@ -144,6 +151,14 @@ __global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, f
         bodies[c * cap + slot] = i;
     else
         atomicOr(status, ST_CELL_OVERFLOW);
+}
+
+__global__ void k_cell_assign(const float4* __restrict__ pos, int N, float3 L, float3 invL,
+                              float3 invw, int3 nc, int* __restrict__ count,
+                              int* __restrict__ bodies, int cap, unsigned* status,
+                              const int* __restrict__ rebuild, int* zero_count) {
+    cell_assign_body(pos, N, L, invL, invw, nc, count, bodies, cap, status, rebuild, zero_count,
+                     blockIdx.x);
 }
 
 __device__ inline void sort_row(int* row, int n) {
@@ -166,20 +181,18 @@ __device__ inline void sort_row(int* row, int n) {
 // lane 0 sorts each row by j so the list does not depend on the cell fill
 // order or on the lane interleaving.
 // The CTA that finishes last then scans the half-row counts (k_scan_counts).
-__global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, float3 invL,
-                             float3 invw, int3 nc, const int* __restrict__ count,
-                             const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
-                             int* __restrict__ half_count, int* __restrict__ half_nbr,
-                             int* __restrict__ lower_count, int* __restrict__ lower_nbr,
-                             unsigned* status, const int* __restrict__ rebuild,
-                             int* __restrict__ half_off, int* total, int64_t cap_pairs,
-                             int* done) {
+__device__ __forceinline__ void pair_build_body(
+    const float4* __restrict__ pos, int N, float3 L, float3 invL, float3 invw, int3 nc,
+    const int* __restrict__ count, const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
+    int* __restrict__ half_count, int* __restrict__ half_nbr, int* __restrict__ lower_count,
+    int* __restrict__ lower_nbr, unsigned* status, const int* __restrict__ rebuild,
+    int* __restrict__ half_off, int* total, int64_t cap_pairs, int* done, int bid, int nblk) {
     pdl_wait();
     if (!*rebuild) return;
     const int lane = threadIdx.x & 31;
     // a warp per body, grid-stride (one wave of CTAs: cheap when no rebuild is due)
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
+    const int nw = nblk * (blockDim.x >> 5);
+    for (int i = bid * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
         const float4 p = pos[i];
         const float x = wrap1(p.x, L.x, invL.x), y = wrap1(p.y, L.y, invL.y), z = wrap1(p.z, L.z, invL.z);
         const int c[3] = {min(max(int(x * invw.x), 0), nc.x - 1), min(max(int(y * invw.y), 0), nc.y - 1),
@@ -240,7 +253,20 @@ __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, fl
             lower_count[i] = nl;
         }
     }
-    if (last_cta_done(done)) scan_counts(half_count, N, half_off, total, cap_pairs, status);
+    if (last_cta_done(done, nblk)) scan_counts(half_count, N, half_off, total, cap_pairs, status);
+}
+
+__global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, float3 invL,
+                             float3 invw, int3 nc, const int* __restrict__ count,
+                             const int* __restrict__ bodies, int cap, float Rc2, int max_nbr,
+                             int* __restrict__ half_count, int* __restrict__ half_nbr,
+                             int* __restrict__ lower_count, int* __restrict__ lower_nbr,
+                             unsigned* status, const int* __restrict__ rebuild,
+                             int* __restrict__ half_off, int* total, int64_t cap_pairs,
+                             int* done) {
+    pair_build_body(pos, N, L, invL, invw, nc, count, bodies, cap, Rc2, max_nbr, half_count,
+                    half_nbr, lower_count, lower_nbr, status, rebuild, half_off, total, cap_pairs,
+                    done, blockIdx.x, gridDim.x);
 }
 
 // Emit the compact pair list and turn each lower-row entry j (< i) into the
@@ -248,17 +274,16 @@ __global__ void k_pair_build(const float4* __restrict__ pos, int N, float3 L, fl
 // list was built for and clear the cell counts for the next rebuild.  The
 // CTA that finishes last lowers the rebuild flag (every CTA has read it by
 // then).
-__global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_count,
-                            const int* __restrict__ half_nbr, const int* __restrict__ half_off,
-                            const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
-                            int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status,
-                            int n_cells, const float4* __restrict__ pos,
-                            float4* __restrict__ pos_ref, int* __restrict__ cell_count,
-                            int* rebuild, int* done) {
+__device__ __forceinline__ void pair_emit_body(
+    int N, int max_nbr, const int* __restrict__ half_count, const int* __restrict__ half_nbr,
+    const int* __restrict__ half_off, const int* __restrict__ lower_count,
+    int* __restrict__ lower_nbr, int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status,
+    int n_cells, const float4* __restrict__ pos, float4* __restrict__ pos_ref,
+    int* __restrict__ cell_count, int* rebuild, int* done, int bid, int nblk) {
     pdl_wait();
     if (!*rebuild) return;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const int stride = nblk * blockDim.x;
+    for (int i = bid * blockDim.x + threadIdx.x; i < N; i += stride) {
         const int off = half_off[i];
         const int n = half_count[i];
         const int* hrow = half_nbr + (size_t)i * max_nbr;
@@ -286,8 +311,20 @@ __global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_cou
         }
         pos_ref[i] = pos[i];
     }
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) cell_count[c] = 0;
-    if (last_cta_done(done) && threadIdx.x == 0) *rebuild = 0;
+    for (int c = bid * blockDim.x + threadIdx.x; c < n_cells; c += stride) cell_count[c] = 0;
+    if (last_cta_done(done, nblk) && threadIdx.x == 0) *rebuild = 0;
+}
+
+__global__ void k_pair_emit(int N, int max_nbr, const int* __restrict__ half_count,
+                            const int* __restrict__ half_nbr, const int* __restrict__ half_off,
+                            const int* __restrict__ lower_count, int* __restrict__ lower_nbr,
+                            int2* __restrict__ pairs, int64_t cap_pairs, unsigned* status,
+                            int n_cells, const float4* __restrict__ pos,
+                            float4* __restrict__ pos_ref, int* __restrict__ cell_count,
+                            int* rebuild, int* done) {
+    pair_emit_body(N, max_nbr, half_count, half_nbr, half_off, lower_count, lower_nbr, pairs,
+                   cap_pairs, status, n_cells, pos, pos_ref, cell_count, rebuild, done, blockIdx.x,
+                   gridDim.x);
 }
 
 __global__ void k_flag_set(int* rebuild) { *rebuild = 1; }
@@ -316,16 +353,16 @@ __global__ void k_skin_check(int N, float half_skin2, float3 L, float3 invL,
 // state the kick needs are loaded together with the row counts, so the chain
 // of dependent loads is two deep.  Optionally applies the second
 // velocity-Verlet half kick.
-__global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
-                         const int* __restrict__ half_count, const int* __restrict__ lower_count,
-                         const int* __restrict__ lower_pair, const float4* __restrict__ pF,
-                         const float4* __restrict__ pti, const float4* __restrict__ ptj,
-                         float4* __restrict__ force, float4* __restrict__ torque, float kick,
-                         float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
-                         const float4* __restrict__ quat, unsigned* status, float mass,
-                         float3 invI, double* __restrict__ ke_part) {
+__device__ __forceinline__ void reduce_body(
+    int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
+    const int* __restrict__ half_count, const int* __restrict__ lower_count,
+    const int* __restrict__ lower_pair, const float4* __restrict__ pF,
+    const float4* __restrict__ pti, const float4* __restrict__ ptj, float4* __restrict__ force,
+    float4* __restrict__ torque, float kick, float inv_mass, float4* __restrict__ vel,
+    float4* __restrict__ angmom, const float4* __restrict__ quat, unsigned* status, float mass,
+    float3 invI, double* __restrict__ ke_part, int bid) {
     pdl_wait();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bid * blockDim.x + threadIdx.x;
     const int i = t >> 2, sub = t & 3;
     const bool live = i < N;
     float3 F = make_float3(0.f, 0.f, 0.f), T = make_float3(0.f, 0.f, 0.f);
@@ -404,9 +441,22 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
         if (threadIdx.x == 0) {
             double a = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_ke[w];
-            ke_part[blockIdx.x] = a;
+            ke_part[bid] = a;
         }
     }
+}
+
+__global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
+                         const int* __restrict__ half_count, const int* __restrict__ lower_count,
+                         const int* __restrict__ lower_pair, const float4* __restrict__ pF,
+                         const float4* __restrict__ pti, const float4* __restrict__ ptj,
+                         float4* __restrict__ force, float4* __restrict__ torque, float kick,
+                         float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
+                         const float4* __restrict__ quat, unsigned* status, float mass,
+                         float3 invI, double* __restrict__ ke_part) {
+    reduce_body(N, max_nbr, cap_pairs, half_off, half_count, lower_count, lower_pair, pF, pti, ptj,
+                force, torque, kick, inv_mass, vel, angmom, quat, status, mass, invI, ke_part,
+                blockIdx.x);
 }
 
 // Second thermostat half of an NVT step, after the force reduction: every
@@ -473,14 +523,15 @@ __global__ void k_thermo_init(int N, float mass, float3 invI, const float4* __re
 // First half of a velocity-Verlet step: half kick, drift (wrapped), and the
 // NO_SQUISH free rotation about body axes 3, 2, 1, 2, 3 for dt/2, dt/2, dt,
 // dt/2, dt/2; q is renormalised once per step.
-__global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, float3 L,
-                                  float3 invL, float4* __restrict__ pos, float4* __restrict__ quat,
-                                  float4* __restrict__ vel, float4* __restrict__ angmom,
-                                  const float4* __restrict__ force,
-                                  const float4* __restrict__ torque,
-                                  const float4* __restrict__ pos_ref, float half_skin2,
-                                  int* rebuild, NHDev* nh, int4* __restrict__ image) {
+// force_rebuild: no skin, so every step rebuilds the list (raised by one thread).
+__device__ __forceinline__ void integrate_body(
+    int N, float dt, float inv_mass, float3 invI, float3 L, float3 invL, float4* __restrict__ pos,
+    float4* __restrict__ quat, float4* __restrict__ vel, float4* __restrict__ angmom,
+    const float4* __restrict__ force, const float4* __restrict__ torque,
+    const float4* __restrict__ pos_ref, float half_skin2, int* rebuild, NHDev* nh,
+    int4* __restrict__ image, int force_rebuild, int bid) {
     pdl_wait();
+    if (force_rebuild && bid == 0 && threadIdx.x == 0) *rebuild = 1;
     // NVT: first thermostat half T(dt/2) from the state between steps; one
     // thread per block computes it (FP64, identical in every block), block 0
     // stores it for the second half
@@ -489,7 +540,7 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
         if (threadIdx.x == 0) {
             double xi = nh->xi_b, eta = nh->eta_b, K = nh->K_b;
             s_scale = (float)nh_half(xi, eta, K, 0.5 * (double)dt, nh);
-            if (blockIdx.x == 0) {
+            if (bid == 0) {
                 nh->xi_a = xi;
                 nh->eta_a = eta;
                 nh->K_a = K;
@@ -497,7 +548,7 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
         }
         __syncthreads();
     }
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float h = 0.5f * dt;
     float4 f = force[i], t = torque[i];
@@ -556,6 +607,17 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
         const float3 d = min_image(make_float3(p.x - r.x, p.y - r.y, p.z - r.z), L, invL);
         if (d.x * d.x + d.y * d.y + d.z * d.z > half_skin2) *rebuild = 1;
     }
+}
+
+__global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, float3 L,
+                                  float3 invL, float4* __restrict__ pos, float4* __restrict__ quat,
+                                  float4* __restrict__ vel, float4* __restrict__ angmom,
+                                  const float4* __restrict__ force,
+                                  const float4* __restrict__ torque,
+                                  const float4* __restrict__ pos_ref, float half_skin2,
+                                  int* rebuild, NHDev* nh, int4* __restrict__ image) {
+    integrate_body(N, dt, inv_mass, invI, L, invL, pos, quat, vel, angmom, force, torque, pos_ref,
+                   half_skin2, rebuild, nh, image, 0, blockIdx.x);
 }
 
 // Deterministic block reduction of NV doubles; thread 0 writes the block sums.
@@ -631,6 +693,68 @@ __global__ void k_energy_final(const double* __restrict__ pb, int nb_b,
             if (c == 0) out[0] = x; else out[3 + c - 1] = x;
         }
     }
+}
+
+// ------------------------------------------------------------------ batched step
+// The per-body kernels of several systems in one launch each: block b of the
+// flattened grid belongs to the system k with start[k] <= b < start[k + 1]
+// (every system has at least one block) and runs that system's body with its
+// index among the system's blocks.  The same bodies as the one-system
+// kernels, and nothing in a system's arithmetic depends on the other
+// members of the batch.
+
+__device__ __forceinline__ int seg_of_block(const int* __restrict__ start, int n_seg, int b) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_integrate_batch(const StepSeg* __restrict__ segs, const int* __restrict__ start,
+                                  int n_seg) {
+    const int k = seg_of_block(start, n_seg, blockIdx.x);
+    const StepSeg& S = segs[k];
+    integrate_body(S.N, S.dt, S.inv_mass, S.invI, S.L, S.invL, S.pos, S.quat, S.vel, S.angmom,
+                   S.force, S.torque, S.pos_ref, S.half_skin2, S.rebuild, nullptr, S.image,
+                   S.force_rebuild, blockIdx.x - start[k]);
+}
+
+__global__ void k_cell_assign_batch(const StepSeg* __restrict__ segs, const int* __restrict__ start,
+                                    int n_seg) {
+    const int k = seg_of_block(start, n_seg, blockIdx.x);
+    const StepSeg& S = segs[k];
+    cell_assign_body(S.pos, S.N, S.L, S.invL, S.invw, S.nc, S.cell_count, S.cell_bodies, S.cell_cap,
+                     S.status, S.rebuild, nullptr, blockIdx.x - start[k]);
+}
+
+__global__ void k_pair_build_batch(const StepSeg* __restrict__ segs, const int* __restrict__ start,
+                                   int n_seg) {
+    const int k = seg_of_block(start, n_seg, blockIdx.x);
+    const StepSeg& S = segs[k];
+    pair_build_body(S.pos, S.N, S.L, S.invL, S.invw, S.nc, S.cell_count, S.cell_bodies, S.cell_cap,
+                    S.Rl2, S.max_nbr, S.half_count, S.half_nbr, S.lower_count, S.lower_nbr,
+                    S.status, S.rebuild, S.half_off, S.n_pairs, S.cap_pairs, S.done,
+                    blockIdx.x - start[k], start[k + 1] - start[k]);
+}
+
+__global__ void k_pair_emit_batch(const StepSeg* __restrict__ segs, const int* __restrict__ start,
+                                  int n_seg) {
+    const int k = seg_of_block(start, n_seg, blockIdx.x);
+    const StepSeg& S = segs[k];
+    pair_emit_body(S.N, S.max_nbr, S.half_count, S.half_nbr, S.half_off, S.lower_count, S.lower_nbr,
+                   S.pairs, S.cap_pairs, S.status, S.n_cells, S.pos, S.pos_ref, S.cell_count,
+                   S.rebuild, S.done + 1, blockIdx.x - start[k], start[k + 1] - start[k]);
+}
+
+__global__ void k_reduce_batch(const StepSeg* __restrict__ segs, const int* __restrict__ start,
+                               int n_seg) {
+    const int k = seg_of_block(start, n_seg, blockIdx.x);
+    const StepSeg& S = segs[k];
+    reduce_body(S.N, S.max_nbr, S.cap_pairs, S.half_off, S.half_count, S.lower_count, S.lower_nbr,
+                S.pF, S.pti, S.ptj, S.force, S.torque, 0.5f * S.dt, S.inv_mass, S.vel, S.angmom,
+                S.quat, S.status, 1.f / S.inv_mass, S.invI, nullptr, blockIdx.x - start[k]);
 }
 
 static inline int blocks_for(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -724,6 +848,335 @@ static rb_status check_status(rb_system* s) {
         RB_CUDA(cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream));
         return fail(RB_EFAULT, "non-finite force, torque or energy");
     }
+    if (st & ST_TC_TIMEOUT) {
+        RB_CUDA(cudaMemsetAsync(s->status_dev, 0, sizeof(unsigned), s->stream));
+        s->forces_valid = false;
+        return fail(RB_EFAULT, "a tensor-core kernel gave up waiting for an MMA; forces invalid");
+    }
+    return RB_OK;
+}
+
+// ------------------------------------------------------------------ batched step, host
+
+struct StepBatch {
+    std::vector<BatchMember> mem;
+    const rb_mlp* mlp = nullptr;
+    uint64_t mlp_version = 0;
+    int grid[kBatchPhases] = {0, 0, 0, 0, 0};
+    cudaGraphExec_t exec = nullptr;
+};
+
+rb_status batch_tables_alloc(BatchTables* t) {
+    RB_CUDA(cudaMalloc(&t->step, sizeof(StepSeg) * kMaxSeg));
+    RB_CUDA(cudaMalloc(&t->pair, sizeof(PairSeg) * kMaxSeg));
+    RB_CUDA(cudaMalloc(&t->start, sizeof(int) * kBatchPhases * (kMaxSeg + 1)));
+    RB_CUDA(cudaStreamCreateWithFlags(&t->cap, cudaStreamNonBlocking));
+    RB_CUDA(cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming));
+    for (int k = 0; k < kBatchBranches; ++k) {
+        RB_CUDA(cudaStreamCreateWithFlags(&t->branch[k], cudaStreamNonBlocking));
+        RB_CUDA(cudaEventCreateWithFlags(&t->join[k], cudaEventDisableTiming));
+    }
+    return RB_OK;
+}
+
+void batch_tables_free(BatchTables* t) {
+    if (t->step) cudaFree(t->step);
+    if (t->pair) cudaFree(t->pair);
+    if (t->start) cudaFree(t->start);
+    if (t->cap) cudaStreamDestroy(t->cap);
+    if (t->fork) cudaEventDestroy(t->fork);
+    for (int k = 0; k < kBatchBranches; ++k) {
+        if (t->branch[k]) cudaStreamDestroy(t->branch[k]);
+        if (t->join[k]) cudaEventDestroy(t->join[k]);
+    }
+    *t = BatchTables();
+}
+
+void batch_destroy(StepBatch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+}
+
+// What the bead kernel of a system depends on besides its pairs, bodies and
+// box: systems with equal keys share one batched bead launch.
+static std::vector<float> bead_key(const rb_system* s) {
+    std::vector<float> k = {(float)s->n_beads, (float)s->cols.len, s->rcut, s->sigma, s->eps,
+                            s->u_shift, (float)s->pot_kind, s->hphc[0], s->hphc[1], s->hphc[2],
+                            s->hphc[3], s->Rc, s->r_circ};
+    k.insert(k.end(), s->tmpl.begin(), s->tmpl.end());
+    return k;
+}
+
+static StepSeg step_seg(const rb_system* s, float dt) {
+    StepSeg q{};
+    q.N = (int)s->N;
+    q.dt = dt;
+    q.inv_mass = 1.f / s->mass;
+    q.half_skin2 = s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f;
+    q.force_rebuild = s->skin > 0.f ? 0 : 1;
+    q.invI = make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]);
+    q.L = f3(s->box);
+    q.invL = inv3(s->box);
+    q.invw = inv3(s->cells.width);
+    q.nc = make_int3(s->cells.nc[0], s->cells.nc[1], s->cells.nc[2]);
+    q.pos = s->pos;
+    q.quat = s->quat;
+    q.vel = s->vel;
+    q.angmom = s->angmom;
+    q.force = s->force;
+    q.torque = s->torque;
+    q.pos_ref = s->pos_ref;
+    q.image = s->image;
+    q.rebuild = s->rebuild_flag;
+    q.status = s->status_dev;
+    q.cell_count = s->cells.count;
+    q.cell_bodies = s->cells.bodies;
+    q.cell_cap = s->cells.cap;
+    q.n_cells = s->cells.n_cells;
+    const float Rl = s->Rc + s->skin;
+    q.Rl2 = Rl * Rl;
+    q.max_nbr = s->pl.max_nbr;
+    q.half_count = s->pl.half_count;
+    q.half_nbr = s->pl.half_nbr;
+    q.lower_count = s->pl.lower_count;
+    q.lower_nbr = s->pl.lower_nbr;
+    q.half_off = s->pl.half_off;
+    q.n_pairs = s->pl.n_pairs;
+    q.done = s->pl.done;
+    q.cap_pairs = s->pl.cap_pairs;
+    q.pairs = s->pl.pairs;
+    q.pF = s->pair_F;
+    q.pti = s->pair_ti;
+    q.ptj = s->pair_tj;
+    return q;
+}
+
+static PairSeg pair_seg(const rb_system* s) {
+    PairSeg q{};
+    q.status = s->status_dev;
+    q.pairs = s->pl.pairs;
+    q.n_pairs = s->pl.n_pairs;
+    q.pos = s->pos;
+    q.quat = s->quat;
+    q.L = f3(s->box);
+    q.invL = inv3(s->box);
+    q.F = s->pair_F;
+    q.ti = s->pair_ti;
+    q.tj = s->pair_tj;
+    return q;
+}
+
+rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
+                       const BatchTables& tables, StepBatch** out) {
+    *out = nullptr;
+    if (!tables.step || !tables.pair || !tables.start) return fail(RB_EINVAL, "batch tables not allocated");
+    const int n = (int)members.size();
+    if (n < 1 || n > kMaxSeg) return fail(RB_EINVAL, "a batch holds 1 to 32 systems");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (const BatchMember& b : members) {
+        const rb_system* s = b.s;
+        if (!s || s->device != dev) return fail(RB_EINVAL, "batch member missing or on another device");
+        if (b.path != RB_PATH_BEADS && b.path != RB_PATH_NN) return fail(RB_EINVAL, "batch member: unknown path");
+        if (!(b.dt > 0.f)) return fail(RB_EINVAL, "batch member: dt > 0 required");
+        if (s->nh) return fail(RB_EINVAL, "batch member: thermostat not batched (NVE only)");
+        if (b.path == RB_PATH_NN) {
+            if (!m) return fail(RB_EINVAL, "batch member on the network path without a network");
+            RB_TRY(check_mlp(m));
+            if (s->nn_fallback_rho > 0.f) return fail(RB_EINVAL, "batch member: bead fallback not batched");
+        }
+        const bool valid = s->forces_valid && s->forces_path == b.path &&
+                           (b.path != RB_PATH_NN ||
+                            (s->forces_mlp == m && s->forces_precision == b.precision &&
+                             s->forces_mlp_version == m->version));
+        if (!valid) return fail(RB_EINVAL, "batch member: forces not evaluated for its path");
+    }
+    for (const BatchMember& b : members) {
+        if (b.path != RB_PATH_NN) continue;
+        RB_TRY(ensure_pair_sym_arrays(b.s, m));
+        RB_TRY(ensure_images(m, b.precision));
+    }
+    StepBatch* B = new (std::nothrow) StepBatch();
+    if (!B) return fail(RB_ENOMEM, "host allocation");
+    B->mem = members;
+    B->mlp = m;
+    B->mlp_version = m ? m->version : 0;
+    const int num_sms = members[0].s->num_sms;
+
+    // per-body phases: each system's blocks as in its own step; the two list
+    // kernels (one wave of CTAs each when no rebuild is due) share one wave
+    // in proportion to what the systems would take alone
+    std::vector<StepSeg> seg(n);
+    std::vector<int> start(kBatchPhases * (kMaxSeg + 1), 0);
+    {
+        std::vector<int64_t> need[kBatchPhases];
+        for (int k = 0; k < n; ++k) {
+            const rb_system* s = members[k].s;
+            seg[k] = step_seg(s, members[k].dt);
+            const int N = (int)s->N;
+            need[0].push_back(blocks_for(N, 256));
+            need[1].push_back(blocks_for(N, 256));
+            need[2].push_back(std::min(blocks_for((int64_t)N * 32, 256), num_sms * 8));
+            need[3].push_back(std::min(blocks_for(std::max(N, s->cells.n_cells), 256), num_sms * 8));
+            need[4].push_back(blocks_for((int64_t)N * 4, 256));
+        }
+        for (int ph = 0; ph < kBatchPhases; ++ph) {
+            int64_t tot = 0;
+            for (int64_t v : need[ph]) tot += v;
+            const int64_t cap = (int64_t)num_sms * 8;
+            int* st = start.data() + ph * (kMaxSeg + 1);
+            int acc = 0;
+            for (int k = 0; k < n; ++k) {
+                int64_t v = need[ph][k];
+                if ((ph == 2 || ph == 3) && tot > cap) v = std::max<int64_t>(1, v * cap / tot);
+                st[k] = acc;
+                acc += (int)v;
+            }
+            st[n] = acc;
+            B->grid[ph] = acc;
+        }
+    }
+
+    // pair phase: the BF16 network's systems (one launch per body cutoff)
+    // and the bead systems (one launch per template and potential) batched;
+    // the rest launch per system inside the same graph
+    std::vector<PairSeg> pseg;
+    struct Group {
+        int kind;  // 0 network, 1 beads
+        int first, count;
+        const rb_system* like;
+        int grid_hint;
+    };
+    std::vector<Group> groups;
+    std::vector<int> single;  // members with no batched pair kernel
+    std::vector<bool> taken(n, false);
+    for (int k = 0; k < n; ++k) {
+        if (taken[k]) continue;
+        const BatchMember& a = members[k];
+        const bool nn = a.path == RB_PATH_NN && a.precision == RB_BF16 && nn_tc2p_batchable(m);
+        const bool bd = a.path == RB_PATH_BEADS && a.s->cols.len > 0;
+        if (!nn && !bd) {
+            single.push_back(k);
+            taken[k] = true;
+            continue;
+        }
+        const std::vector<float> key = bd ? bead_key(a.s) : std::vector<float>();
+        Group g{nn ? 0 : 1, (int)pseg.size(), 0, a.s, 0};
+        for (int j = k; j < n; ++j) {
+            if (taken[j]) continue;
+            const BatchMember& b = members[j];
+            const bool same = nn ? (b.path == RB_PATH_NN && b.precision == RB_BF16 && b.s->Rc == a.s->Rc)
+                                 : (b.path == RB_PATH_BEADS && bead_key(b.s) == key);
+            if (!same) continue;
+            taken[j] = true;
+            pseg.push_back(pair_seg(b.s));
+            ++g.count;
+            g.grid_hint += nn ? pair_grid(b.s, 128, num_sms) : pair_grid(b.s, 8, 1 << 30);
+        }
+        groups.push_back(g);
+    }
+
+    rb_status st = RB_OK;
+    auto upload = [&]() -> rb_status {
+        RB_CUDA(cudaMemcpy(tables.step, seg.data(), sizeof(StepSeg) * n, cudaMemcpyHostToDevice));
+        RB_CUDA(cudaMemcpy(tables.start, start.data(), sizeof(int) * start.size(),
+                           cudaMemcpyHostToDevice));
+        if (!pseg.empty())
+            RB_CUDA(cudaMemcpy(tables.pair, pseg.data(), sizeof(PairSeg) * pseg.size(),
+                               cudaMemcpyHostToDevice));
+        return RB_OK;
+    };
+    st = upload();
+    if (st != RB_OK) {
+        batch_destroy(B);
+        return st;
+    }
+    // one step of every member as one graph
+    cudaStream_t cs = tables.cap;
+    auto launches = [&]() -> rb_status {
+        void (*phase[4])(const StepSeg*, const int*, int) = {k_integrate_batch, k_cell_assign_batch,
+                                                            k_pair_build_batch, k_pair_emit_batch};
+        for (int ph = 0; ph < 4; ++ph)
+            RB_CUDA(launch_pdl(phase[ph], B->grid[ph], 256, 0, cs, (const StepSeg*)tables.step,
+                               (const int*)(tables.start + ph * (kMaxSeg + 1)), n));
+        // the pair phase: each group (and the members launched one by one,
+        // together) on its own branch, so that their kernels share the GPU
+        std::vector<std::function<rb_status(cudaStream_t)>> work;
+        for (const Group& g : groups)
+            work.push_back([&, g](cudaStream_t st) -> rb_status {
+                if (g.kind == 0)
+                    return nn_tc2p_batch_async(m, g.like, tables.pair + g.first, g.count,
+                                               std::max(1, std::min(num_sms, g.grid_hint)), st);
+                bool done = false;
+                RB_TRY(bead_pairs_batch_async(g.like, tables.pair + g.first, g.count, g.grid_hint,
+                                              st, &done));
+                return done ? RB_OK : fail(RB_ENOTSUP, "bead template without a batched kernel");
+            });
+        if (!single.empty())
+            work.push_back([&](cudaStream_t st) -> rb_status {
+                for (int k : single) {  // as in a system's own step graph, on this branch
+                    rb_system* s = members[k].s;
+                    cudaStream_t user = s->stream;
+                    s->stream = st;
+                    rb_status r = members[k].path == RB_PATH_NN
+                                      ? nn_pairs_system_async(s, m, members[k].precision)
+                                      : bead_pairs_async(s);
+                    s->stream = user;
+                    RB_TRY(r);
+                }
+                return RB_OK;
+            });
+        const int nb = (int)work.size();
+        if (nb == 1) {
+            RB_TRY(work[0](cs));
+        } else {
+            RB_CUDA(cudaEventRecord(tables.fork, cs));
+            for (int w = 0; w < nb; ++w) {
+                cudaStream_t st = tables.branch[w % kBatchBranches];
+                if (w < kBatchBranches) RB_CUDA(cudaStreamWaitEvent(st, tables.fork, 0));
+                RB_TRY(work[w](st));
+            }
+            for (int b = 0; b < std::min(nb, kBatchBranches); ++b) {
+                RB_CUDA(cudaEventRecord(tables.join[b], tables.branch[b]));
+                RB_CUDA(cudaStreamWaitEvent(cs, tables.join[b], 0));
+            }
+        }
+        if (nb == 1)
+            RB_CUDA(launch_pdl(k_reduce_batch, B->grid[4], 256, 0, cs, (const StepSeg*)tables.step,
+                               (const int*)(tables.start + 4 * (kMaxSeg + 1)), n));
+        else  // after the join: a plain dependency on every branch
+            k_reduce_batch<<<B->grid[4], 256, 0, cs>>>(tables.step, tables.start + 4 * (kMaxSeg + 1), n);
+        return RB_OK;
+    };
+    cudaError_t be = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (be != cudaSuccess) {
+        batch_destroy(B);
+        return cuda_fail(be, "cudaStreamBeginCapture");
+    }
+    st = launches();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (st == RB_OK && ce != cudaSuccess) st = cuda_fail(ce, "cudaStreamEndCapture");
+    if (st == RB_OK) {
+        const cudaError_t ie = cudaGraphInstantiate(&B->exec, graph, 0);
+        if (ie != cudaSuccess) st = cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != RB_OK) {
+        batch_destroy(B);
+        return st;
+    }
+    *out = B;
+    return RB_OK;
+}
+
+rb_status batch_step(StepBatch* b, cudaStream_t stream) {
+    if (!b || !b->exec) return fail(RB_EINVAL, "null batch");
+    if (b->mlp && b->mlp->version != b->mlp_version)
+        return fail(RB_EINVAL, "network parameters changed since the batch was made");
+    RB_CUDA(cudaGraphLaunch(b->exec, stream));
+    for (BatchMember& m : b->mem) m.s->step += 1;
     return RB_OK;
 }
 

@@ -115,3 +115,49 @@ def test_non_finite_network_falls_back_to_beads():
     # the fallback replica followed the bead path from its start
     for k in ("pos", "quat", "vel", "angmom"):
         assert np.array_equal(fin[k], finb[k]), k
+
+
+def test_batched_replicas_match_their_own_runs():
+    """Resident replicas step together (one launch per phase for all of them,
+    the pair kernels over their concatenated lists); each ends where its own
+    rb_step run ends, to rounding: the batched kernels do the same arithmetic
+    but are separate kernels, whose fused multiply-adds the compiler may form
+    differently (a * b + c * d), so the last bit may differ.  A wrong system,
+    box or pair slot for any pair would be far outside the bound.  The mix
+    covers both batched pair kernels (BF16 network, bead sum of the cube and
+    of the cylinder), a precision launched per replica inside the batch
+    (F16X3), skin and no skin, and ticks of 4 and 2 steps."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    m = net()
+    cases = [
+        (make_state(600, 0.20, 51), "cube", api.RB_PATH_NN, "bf16", 0.4),
+        (make_state(700, 0.15, 52, "cylinder"), "cylinder", api.RB_PATH_BEADS, "fp32", 0.4),
+        (make_state(500, 0.20, 53), "cube", api.RB_PATH_BEADS, "fp32", 0.0),
+        (make_state(800, 0.20, 54), "cube", api.RB_PATH_NN, "bf16", 0.0),
+        (make_state(400, 0.20, 55), "cube", api.RB_PATH_NN, "f16x3", 0.4),
+        (make_state(300, 0.10, 56), "cube", api.RB_PATH_BEADS, "fp32", 0.4),
+    ]
+    steps = 14
+    srv = api.Server(8 << 30, 8, m, steps_per_tick=4)
+    tickets = [srv.submit(st, [L] * 3, shape, path, prec, steps, skin=skin)
+               for (st, L, _), shape, path, prec, skin in cases]
+    results = [srv.wait(t) for t in tickets]
+    finals = [srv.fetch_state(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert stats["peak_resident"] == len(cases)
+    keys = ("pos", "quat", "vel", "angmom")
+    for ((st, L, _), shape, path, prec, skin), r, fin in zip(cases, results, finals):
+        assert r["status"] == 0 and r["steps_done"] == steps and r["fell_back"] == 0, r
+        s = api.System(len(st["pos"]), [L] * 3, shape, skin=skin)
+        s.set_state(*(torch.from_numpy(np.ascontiguousarray(st[k])).cuda() for k in keys))
+        cfg = dict(path=path) if path == api.RB_PATH_BEADS else dict(path=path, mlp=m, precision=prec)
+        s.step(steps, 0.002, **cfg)
+        own = s.get_state(to_host=True)
+        for k in keys:
+            a, b = np.asarray(fin[k], np.float64), np.asarray(own[k], np.float64)
+            d = float(np.max(np.abs(a - b)))
+            assert d <= 1e-5 * float(np.max(np.abs(b))), (shape, path, prec, skin, k, d)
