@@ -1317,6 +1317,14 @@ def main():
         serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
                               mlp, n_requests=args.serving_requests, steps=args.serving_steps,
                               n_max=args.serving_nmax, solo_rates=solo)
+        # many small replicas (where stepping them together pays most): N in
+        # [512, 4096], 32 slots, about 32 in flight, the server's default lanes
+        small = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
+                            mlp, n_requests=args.serving_requests, steps=args.serving_steps,
+                            n_max=4096, rate_factor=32.0, budget_bytes=4 << 30, slots=32)
+        serving["small_replicas"] = {k: small[k] for k in
+                                     ("workload", "makespan_s", "pair_evals_per_s", "step_ms_p50",
+                                      "step_ms_p99", "peak_resident", "completed_ok", "saturated")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
