@@ -1176,13 +1176,21 @@ def main():
         se.get_forces(to_host=True, out=(blk[p][4], blk[p][5]))
         e2e_sys[p] = se
     e2e_steps = max(3, min(args.steps, 50))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for p, se in e2e_sys.items():  # state and forces in, one step, both out
-            se.step_host_state(blk[p], 1, DT, sync=False, **pcfg(p))
+
+    def e2e_time(copies):
         torch.cuda.synchronize()
-    e2e_t = (time.perf_counter() - t0) / e2e_steps
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for p, se in e2e_sys.items():  # state and forces in, one step, both out
+                se.step_host_state(blk[p], 1, DT, sync=False, copies=copies, **pcfg(p))
+            torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / e2e_steps
+
+    # the copy form (one copy each way around the step) for comparison, then
+    # the direct form the call takes for a page-locked block (the step's
+    # kernels read and write the block in host memory)
+    e2e_t_copies = e2e_time(True)
+    e2e_t = e2e_time(False)
     e2e_ok = all(bool(torch.isfinite(blk[p]).all()) for p in e2e_paths)
     for se in e2e_sys.values():
         se.sync()
@@ -1190,6 +1198,7 @@ def main():
     h2d = len(e2e_paths) * 6 * N_BODIES * 16
     d2h = len(e2e_paths) * 6 * N_BODIES * 16
     e2e_value = sum(n_pairs[p] for p in e2e_paths) * world / e2e_t
+    e2e_value_copies = sum(n_pairs[p] for p in e2e_paths) * world / e2e_t_copies
 
     model_error = None
     if any(p.startswith("nn") for p in paths):
@@ -1394,9 +1403,14 @@ def main():
                     "results_finite": e2e_ok, "path": head,
                     "note": "per step, one rb_step_host_state call: the velocity-Verlet "
                             "state (centres, orientations, momenta, forces) in from one "
-                            "page-locked host block (one copy), one MD step, the new state and "
-                            "forces out to the same block (one copy); one host synchronisation "
-                            "per step"},
+                            "page-locked host block, one MD step, the new state and forces out "
+                            "to the same block; one host synchronisation per step.  Direct form: "
+                            "the step's integrator reads the block from host memory and it and "
+                            "the force reduction write the new state back (the bytes cross the "
+                            "host link inside the kernels, no copy is queued)",
+                    "copies_form": {"value": e2e_value_copies, "unit": UNIT,
+                                    "note": "the same with one cudaMemcpyAsync each way around "
+                                            "the step"}},
             # per MD step and path: integrate (with the skin check), cell assign,
             # pair build (+ scan), emit (+ finish), pair kernel, reduce; plus the
             # bead fallback kernel on the network paths

@@ -176,11 +176,19 @@ rb_status rb_set_forces(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t
  * the system's stream what rb_set_state, rb_set_forces, rb_step(n_steps, dt)
  * and rb_get_state / rb_get_forces (to_host = 2) would: the block in, the
  * steps, the new state and its forces back into the same block.  The block
- * should be page-locked (for asynchronous copies) and must stay valid until
- * the stream has passed the copies (one copy each way: the system keeps the
- * same six arrays as one block).  sync != 0: returns after the block is
- * updated, reporting sticky device errors as rb_sync does; sync = 0: after
- * queueing.  Arguments and errors as those calls'. */
+ * must stay valid until the stream has passed the step.
+ * Two forms:
+ *  - direct (one step, no thermostat, a page-locked 16-byte-aligned block):
+ *    the step's integrator reads the block from host memory and writes the
+ *    new centres and orientations back to it, its force reduction the new
+ *    momenta and forces; no copy is queued (the GPU's own loads and stores
+ *    move the block across the host link);
+ *  - copies (otherwise, or with bit 1 of sync set): one copy each way (the
+ *    system keeps the same six arrays as one block) around rb_step.
+ * Both give the same state and forces as rb_set_state .. rb_get_forces.
+ * sync bit 0 (1): returns after the block is updated, reporting sticky
+ * device errors as rb_sync does; clear: after queueing.  Arguments and
+ * errors as those calls'. */
 rb_status rb_step_host_state(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
                              int64_t n_steps, float dt, float* state_host, int32_t sync);
 

@@ -158,15 +158,16 @@ class System:
 
     def step_host_state(self, block: torch.Tensor, n_steps: int, dt: float,
                         path: int = RB_PATH_BEADS, mlp: "MLP" = None, precision="fp32",
-                        sync: bool = True):
+                        sync: bool = True, copies: bool = False):
         """rb_step_host_state: `block` is a page-locked (6, N, 4) FP32 host tensor
-        (pos, quat, vel, angmom, force, torque), updated in place."""
+        (pos, quat, vel, angmom, force, torque), updated in place.  copies: the
+        copy form even where the direct form applies."""
         if block.is_cuda or block.dtype != torch.float32 or tuple(block.shape) != (6, self.N, 4) \
                 or not block.is_contiguous():
             raise ValueError("block must be a contiguous (6, N, 4) float32 host tensor")
         check(load().rb_step_host_state(self._h, path, mlp.handle if mlp is not None else None,
                                         PRECISION[precision], int(n_steps), float(dt),
-                                        block.data_ptr(), 1 if sync else 0))
+                                        block.data_ptr(), (1 if sync else 0) | (2 if copies else 0)))
 
     def set_forces(self, force, torque, path: int = RB_PATH_BEADS, mlp: "MLP" = None,
                    precision="fp32"):

@@ -155,6 +155,7 @@ struct CellList {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
+    const void* host = nullptr;  // the host state block the graph reads and writes (or none)
     int path = -1;
     int precision = -1;
     const void* mlp = nullptr;
@@ -238,6 +239,7 @@ struct rb_system {
     unsigned* status_dev = nullptr;
     int num_sms = 0;
     rb::GraphCache graph;
+    rb::GraphCache graph_hs;  // the one-step graph of rb_step_host_state's direct form
     // network path: pairs closer than this (outside the trained domain) are
     // evaluated by the bead sum instead (0 = off); count of such pairs
     float nn_fallback_rho = 0.f;
@@ -286,7 +288,9 @@ inline int pair_grid(const rb_system* s, int pairs_per_cta, int max_ctas) {
     return (int)std::max(1.0, std::min((double)max_ctas, ctas));
 }
   // force: rebuild regardless of the skin; checked: skin already checked (by the integrator)
-rb_status reduce_forces_async(rb_system* s, float half_kick_dt);
+// hs (nullable): a host state block (pos | quat | vel | angmom | force | torque,
+// N float4 each) that the reduction also writes the momenta and forces to
+rb_status reduce_forces_async(rb_system* s, float half_kick_dt, float4* hs = nullptr);
 rb_status energy_async(rb_system* s);
 // beads.cu
 rb_status bead_pairs_async(rb_system* s);

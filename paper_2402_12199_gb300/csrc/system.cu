@@ -353,6 +353,9 @@ __global__ void k_skin_check(int N, float half_skin2, float3 L, float3 invL,
 // state the kick needs are loaded together with the row counts, so the chain
 // of dependent loads is two deep.  Optionally applies the second
 // velocity-Verlet half kick.
+// HS: the forces, torques and (kicked) momenta also go to the host state
+// block hs (pos | quat | vel | angmom | force | torque).
+template <bool HS = false>
 __device__ __forceinline__ void reduce_body(
     int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
     const int* __restrict__ half_count, const int* __restrict__ lower_count,
@@ -360,7 +363,7 @@ __device__ __forceinline__ void reduce_body(
     const float4* __restrict__ pti, const float4* __restrict__ ptj, float4* __restrict__ force,
     float4* __restrict__ torque, float kick, float inv_mass, float4* __restrict__ vel,
     float4* __restrict__ angmom, const float4* __restrict__ quat, unsigned* status, float mass,
-    float3 invI, double* __restrict__ ke_part, int bid) {
+    float3 invI, double* __restrict__ ke_part, int bid, float4* __restrict__ hs = nullptr) {
     pdl_wait();
     const int t = bid * blockDim.x + threadIdx.x;
     const int i = t >> 2, sub = t & 3;
@@ -415,6 +418,10 @@ __device__ __forceinline__ void reduce_body(
             atomicOr(status, ST_NONFINITE);
         force[i] = make_float4(F.x, F.y, F.z, e);
         torque[i] = make_float4(T.x, T.y, T.z, 0.f);
+        if (HS) {
+            hs[4 * (size_t)N + i] = make_float4(F.x, F.y, F.z, e);
+            hs[5 * (size_t)N + i] = make_float4(T.x, T.y, T.z, 0.f);
+        }
         if (kick != 0.f) {
             vv.x += kick * F.x * inv_mass;
             vv.y += kick * F.y * inv_mass;
@@ -426,6 +433,10 @@ __device__ __forceinline__ void reduce_body(
             Lb.y += kick * tb.y;
             Lb.z += kick * tb.z;
             angmom[i] = Lb;
+            if (HS) {
+                hs[2 * (size_t)N + i] = vv;
+                hs[3 * (size_t)N + i] = Lb;
+            }
             if (ke_part)
                 ke2 = (double)mass * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z) +
                       (double)Lb.x * Lb.x * invI.x + (double)Lb.y * Lb.y * invI.y +
@@ -457,6 +468,21 @@ __global__ void k_reduce(int N, int max_nbr, int64_t cap_pairs, const int* __res
     reduce_body(N, max_nbr, cap_pairs, half_off, half_count, lower_count, lower_pair, pF, pti, ptj,
                 force, torque, kick, inv_mass, vel, angmom, quat, status, mass, invI, ke_part,
                 blockIdx.x);
+}
+
+// k_reduce (with a kick) that also writes to the host state block hs.
+__global__ void k_reduce_hs(int N, int max_nbr, int64_t cap_pairs, const int* __restrict__ half_off,
+                            const int* __restrict__ half_count,
+                            const int* __restrict__ lower_count,
+                            const int* __restrict__ lower_pair, const float4* __restrict__ pF,
+                            const float4* __restrict__ pti, const float4* __restrict__ ptj,
+                            float4* __restrict__ force, float4* __restrict__ torque, float kick,
+                            float inv_mass, float4* __restrict__ vel, float4* __restrict__ angmom,
+                            const float4* __restrict__ quat, unsigned* status, float3 invI,
+                            float4* __restrict__ hs) {
+    reduce_body<true>(N, max_nbr, cap_pairs, half_off, half_count, lower_count, lower_pair, pF, pti,
+                      ptj, force, torque, kick, inv_mass, vel, angmom, quat, status, 0.f, invI,
+                      nullptr, blockIdx.x, hs);
 }
 
 // Second thermostat half of an NVT step, after the force reduction: every
@@ -524,12 +550,18 @@ __global__ void k_thermo_init(int N, float mass, float3 invI, const float4* __re
 // NO_SQUISH free rotation about body axes 3, 2, 1, 2, 3 for dt/2, dt/2, dt,
 // dt/2, dt/2; q is renormalised once per step.
 // force_rebuild: no skin, so every step rebuilds the list (raised by one thread).
+// HS: the state comes from a host state block hs (pos | quat | vel | angmom |
+// force | torque, N float4 each: the GPU reads it from page-locked host
+// memory), the new centres and orientations go to it as well as to the
+// device arrays, and the image counters are those of this step alone (the
+// state was replaced before it).
+template <bool HS = false>
 __device__ __forceinline__ void integrate_body(
     int N, float dt, float inv_mass, float3 invI, float3 L, float3 invL, float4* __restrict__ pos,
     float4* __restrict__ quat, float4* __restrict__ vel, float4* __restrict__ angmom,
     const float4* __restrict__ force, const float4* __restrict__ torque,
     const float4* __restrict__ pos_ref, float half_skin2, int* rebuild, NHDev* nh,
-    int4* __restrict__ image, int force_rebuild, int bid) {
+    int4* __restrict__ image, int force_rebuild, int bid, float4* __restrict__ hs = nullptr) {
     pdl_wait();
     if (force_rebuild && bid == 0 && threadIdx.x == 0) *rebuild = 1;
     // NVT: first thermostat half T(dt/2) from the state between steps; one
@@ -551,9 +583,15 @@ __device__ __forceinline__ void integrate_body(
     int i = bid * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float h = 0.5f * dt;
-    float4 f = force[i], t = torque[i];
-    float4 v = vel[i];
-    float4 Lw = angmom[i];
+    const float4* __restrict__ src_f = HS ? hs + 4 * (size_t)N : force;
+    const float4* __restrict__ src_t = HS ? hs + 5 * (size_t)N : torque;
+    const float4* __restrict__ src_v = HS ? hs + 2 * (size_t)N : vel;
+    const float4* __restrict__ src_L = HS ? hs + 3 * (size_t)N : angmom;
+    const float4* __restrict__ src_q = HS ? hs + (size_t)N : quat;
+    const float4* __restrict__ src_p = HS ? hs : pos;
+    float4 f = src_f[i], t = src_t[i];
+    float4 v = src_v[i];
+    float4 Lw = src_L[i];
     if (nh) {
         const float sc = s_scale;
         v.x *= sc; v.y *= sc; v.z *= sc;
@@ -562,16 +600,18 @@ __device__ __forceinline__ void integrate_body(
     v.x += h * f.x * inv_mass;
     v.y += h * f.y * inv_mass;
     v.z += h * f.z * inv_mass;
-    float4 q = quat[i];
+    float4 q = src_q[i];
     Mat3 R = qmat(q);
     float3 tb = mulT(R, make_float3(t.x, t.y, t.z));
     float Lb[3] = {Lw.x + h * tb.x, Lw.y + h * tb.y, Lw.z + h * tb.z};
-    float4 p = pos[i];
+    float4 p = src_p[i];
     int kx, ky, kz;
     p.x = wrap1_count(p.x + dt * v.x, L.x, invL.x, kx);
     p.y = wrap1_count(p.y + dt * v.y, L.y, invL.y, ky);
     p.z = wrap1_count(p.z + dt * v.z, L.z, invL.z, kz);
-    if ((kx | ky | kz) != 0) {  // crossed a face: count it (rare, so no traffic otherwise)
+    if (HS) {
+        image[i] = make_int4(kx, ky, kz, 0);
+    } else if ((kx | ky | kz) != 0) {  // crossed a face: count it (rare, so no traffic otherwise)
         int4 im = image[i];
         im.x += kx;
         im.y += ky;
@@ -602,6 +642,10 @@ __device__ __forceinline__ void integrate_body(
     quat[i] = q;
     vel[i] = v;
     angmom[i] = make_float4(Lb[0], Lb[1], Lb[2], Lw.w);
+    if (HS) {
+        hs[i] = p;
+        hs[(size_t)N + i] = q;
+    }
     if (half_skin2 > 0.f) {  // the skin check of the pair list, fused here
         const float4 r = pos_ref[i];
         const float3 d = min_image(make_float3(p.x - r.x, p.y - r.y, p.z - r.z), L, invL);
@@ -618,6 +662,18 @@ __global__ void k_integrate_first(int N, float dt, float inv_mass, float3 invI, 
                                   int* rebuild, NHDev* nh, int4* __restrict__ image) {
     integrate_body(N, dt, inv_mass, invI, L, invL, pos, quat, vel, angmom, force, torque, pos_ref,
                    half_skin2, rebuild, nh, image, 0, blockIdx.x);
+}
+
+// k_integrate_first with the state read from (and the new centres and
+// orientations also written to) the host state block hs.
+__global__ void k_integrate_first_hs(int N, float dt, float inv_mass, float3 invI, float3 L,
+                                     float3 invL, float4* __restrict__ pos,
+                                     float4* __restrict__ quat, float4* __restrict__ vel,
+                                     float4* __restrict__ angmom, const float4* __restrict__ pos_ref,
+                                     float half_skin2, int* rebuild, int4* __restrict__ image,
+                                     float4* __restrict__ hs) {
+    integrate_body<true>(N, dt, inv_mass, invI, L, invL, pos, quat, vel, angmom, nullptr, nullptr,
+                         pos_ref, half_skin2, rebuild, nullptr, image, 0, blockIdx.x, hs);
 }
 
 // Deterministic block reduction of NV doubles; thread 0 writes the block sums.
@@ -800,8 +856,18 @@ rb_status build_pairs_async(rb_system* s, bool force, bool checked, int* zero_co
     return RB_OK;
 }
 
-rb_status reduce_forces_async(rb_system* s, float kick) {
+rb_status reduce_forces_async(rb_system* s, float kick, float4* hs) {
     const int N = (int)s->N;
+    if (hs) {  // a step of rb_step_host_state's direct form (NVE, with a kick)
+        RB_CUDA(launch_pdl(k_reduce_hs, blocks_for((int64_t)N * 4, 256), 256, 0, s->stream, N,
+                           s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count,
+                           s->pl.lower_count, s->pl.lower_nbr, s->pair_F, s->pair_ti, s->pair_tj,
+                           s->force, s->torque, kick, 1.f / s->mass, s->vel, s->angmom, s->quat,
+                           s->status_dev,
+                           make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
+                           hs));
+        return RB_OK;
+    }
     const bool nvt = s->nh && kick != 0.f;  // kinetic-energy partials for the thermostat
     RB_CUDA(launch_pdl(k_reduce, blocks_for((int64_t)N * 4, 256), 256, 0, s->stream, N,
                        s->pl.max_nbr, s->pl.cap_pairs, s->pl.half_off, s->pl.half_count,
@@ -1434,6 +1500,7 @@ rb_status rb_destroy_system(rb_system* s) {
     if (!s) return RB_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
+    if (s->graph_hs.exec) cudaGraphExecDestroy(s->graph_hs.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     void* ptrs[] = {s->tmpl_dev, s->pos,  // force and torque live in the pos block
                     s->cells.count, s->cells.bodies, s->pl.half_count, s->pl.lower_count,
@@ -1470,14 +1537,16 @@ rb_status rb_body_template(const rb_system* s, float* xyz) {
 // What follows a copy of a new state into the system: the image counters
 // restart, the list is checked (or rebuilt without a skin), the thermostat
 // re-reads K, and the stored forces no longer belong to the state.
-static rb_status state_replaced(rb_system* s, bool positions, bool momenta) {
+// images: reset the image counters (the host-state step's integrator writes
+// them itself).
+static rb_status state_replaced(rb_system* s, bool positions, bool momenta, bool images = true) {
     if (positions) {
         // With a skin the list stays valid while every centre is within skin/2
         // of the positions it was built for, however the centres got there:
         // the skin check of the next evaluation decides (a state close to the
         // previous one, as a caller feeding each step's state back, keeps it).
         if (!(s->skin > 0.f)) k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
-        RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
+        if (images) RB_CUDA(cudaMemsetAsync(s->image, 0, sizeof(int4) * s->N, s->stream));
     }
     if (s->nh && momenta)
         k_thermo_init<<<1, 1024, 0, s->stream>>>(
@@ -1530,10 +1599,11 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
 rb_status rb_set_thermostat(rb_system* s, float kT, float tau) {
     if (!s) return fail(RB_EINVAL, "null system");
     auto drop_graph = [&] {  // the captured step graph holds the thermostat pointer
-        if (s->graph.exec) {
-            cudaGraphExecDestroy(s->graph.exec);
-            s->graph.exec = nullptr;
-        }
+        for (GraphCache* g : {&s->graph, &s->graph_hs})
+            if (g->exec) {
+                cudaGraphExecDestroy(g->exec);
+                g->exec = nullptr;
+            }
     };
     if (!(tau > 0.f)) {  // off
         if (s->nh) {
@@ -1700,7 +1770,7 @@ rb_status rb_forces_nn(rb_system* s, const rb_mlp* m, int32_t precision, float* 
 
 // model: the rb_mlp of RB_PATH_NN or the rb_fnet of RB_PATH_FNET (unused for beads)
 static rb_status eval_forces_async(rb_system* s, int path, const void* model, int precision,
-                                   float kick, bool checked = false) {
+                                   float kick, bool checked = false, float4* hs = nullptr) {
     RB_TRY(build_pairs_async(s, false, checked, path == RB_PATH_NN ? fallback_counter(s) : nullptr));
     if (path == RB_PATH_BEADS) {
         RB_TRY(bead_pairs_async(s));
@@ -1710,7 +1780,7 @@ static rb_status eval_forces_async(rb_system* s, int path, const void* model, in
         RB_TRY(nn_pairs_system_async(s, static_cast<const rb_mlp*>(model), precision));
         if (s->nn_fallback_rho > 0.f) RB_TRY(bead_fallback_async(s));
     }
-    return reduce_forces_async(s, kick);
+    return reduce_forces_async(s, kick, hs);
 }
 
 rb_status rb_eval_pairs(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision) {
@@ -1726,8 +1796,10 @@ rb_status rb_eval_pairs(rb_system* s, int32_t path, const rb_mlp* m, int32_t pre
 
 // The MD step of every force path: `model` is null (beads), an rb_mlp (NN) or
 // an rb_fnet (FNET) whose parameter version is `version`.
+// hs (nullable): rb_step_host_state's direct form, one NVE step whose state
+// comes from and goes back to the host state block hs (forces given with it).
 static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t version,
-                           int32_t precision, int64_t n_steps, float dt) {
+                           int32_t precision, int64_t n_steps, float dt, float4* hs = nullptr) {
     if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
         return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
@@ -1738,6 +1810,8 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
     const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
                       s->forces_precision == precision &&
                       (!m || s->forces_mlp_version == version);
+    if (hs && (!same || n_steps != 1 || s->nh))
+        return fail(RB_EINVAL, "host-state step: one NVE step with the forces given");
     if (!same) {
         RB_TRY(eval_forces_async(s, path, m, precision, 0.f));
         s->forces_valid = true;
@@ -1747,9 +1821,9 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
         s->forces_mlp_version = m ? version : 0;
     }
     if (n_steps == 0) return RB_OK;
-    GraphCache& g = s->graph;
+    GraphCache& g = hs ? s->graph_hs : s->graph;
     if (!g.exec || g.path != path || g.precision != precision || g.mlp != m || g.dt != dt ||
-        (m && g.mlp_version != version) || g.nvt != (s->nh != nullptr)) {
+        (m && g.mlp_version != version) || g.nvt != (s->nh != nullptr) || g.host != hs) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1765,14 +1839,19 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
             return cuda_fail(be, "cudaStreamBeginCapture");
         }
         const int N = (int)s->N;
-        const cudaError_t le = launch_pdl(
-            k_integrate_first, blocks_for(N, 256), 256, 0, s->stream, N, dt, 1.f / s->mass,
-            make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]),
-            f3(s->box), inv3(s->box), s->pos, s->quat, s->vel, s->angmom, s->force, s->torque,
-            s->pos_ref, s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f, s->rebuild_flag, s->nh,
-            s->image);
-        rb_status st = le == cudaSuccess ? eval_forces_async(s, path, m, precision, 0.5f * dt, true)
-                                         : cuda_fail(le, "k_integrate_first");
+        const float3 invI = make_float3(1.f / s->inertia[0], 1.f / s->inertia[1], 1.f / s->inertia[2]);
+        const float hs2 = s->skin > 0.f ? 0.25f * s->skin * s->skin : 0.f;
+        const cudaError_t le =
+            hs ? launch_pdl(k_integrate_first_hs, blocks_for(N, 256), 256, 0, s->stream, N, dt,
+                            1.f / s->mass, invI, f3(s->box), inv3(s->box), s->pos, s->quat, s->vel,
+                            s->angmom, s->pos_ref, hs2, s->rebuild_flag, s->image, hs)
+               : launch_pdl(k_integrate_first, blocks_for(N, 256), 256, 0, s->stream, N, dt,
+                            1.f / s->mass, invI, f3(s->box), inv3(s->box), s->pos, s->quat, s->vel,
+                            s->angmom, s->force, s->torque, s->pos_ref, hs2, s->rebuild_flag, s->nh,
+                            s->image);
+        rb_status st = le == cudaSuccess
+                           ? eval_forces_async(s, path, m, precision, 0.5f * dt, true, hs)
+                           : cuda_fail(le, "k_integrate_first");
         cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
         s->stream = user;
         if (st != RB_OK) {
@@ -1789,6 +1868,7 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
         g.mlp_version = m ? version : 0;
         g.dt = dt;
         g.nvt = s->nh != nullptr;
+        g.host = hs;
     }
     for (int64_t k = 0; k < n_steps; ++k) RB_CUDA(cudaGraphLaunch(g.exec, s->stream));
     s->step += n_steps;
@@ -1847,10 +1927,11 @@ rb_status rb_set_skin(rb_system* s, float skin) {
         RB_CUDA(cudaMemsetAsync(s->cells.count, 0, sizeof(int) * s->cells.n_cells, s->stream));
         k_flag_set<<<1, 1, 0, s->stream>>>(s->rebuild_flag);
         s->forces_valid = false;
-        if (s->graph.exec) {
-            cudaGraphExecDestroy(s->graph.exec);
-            s->graph.exec = nullptr;
-        }
+        for (GraphCache* g : {&s->graph, &s->graph_hs})
+            if (g->exec) {
+                cudaGraphExecDestroy(g->exec);
+                g->exec = nullptr;
+            }
     }
     return RB_OK;
 }
@@ -1990,6 +2071,18 @@ rb_status rb_sync(rb_system* s) {
     return check_status(s);
 }
 
+// Page-locked host memory that kernels may address with the host pointer
+// itself (the unified address space maps it), 16-byte aligned.
+static bool host_block_mapped(const void* p) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 rb_status rb_step_host_state(rb_system* s, int32_t path, const rb_mlp* m, int32_t precision,
                              int64_t n_steps, float dt, float* state_host, int32_t sync) {
     if (!s || !state_host) return fail(RB_EINVAL, "null argument");
@@ -2000,6 +2093,18 @@ rb_status rb_step_host_state(rb_system* s, int32_t path, const rb_mlp* m, int32_
         if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
             return fail(RB_EINVAL, "unknown precision");
     }
+    if (n_steps == 1 && !s->nh && !(sync & 2) && host_block_mapped(state_host)) {
+        // direct form: the integrator reads the block from page-locked host
+        // memory (the GPU's loads move it across the host link) and writes the
+        // new centres and orientations back, the reduction the momenta and
+        // forces; no copy is queued
+        RB_TRY(state_replaced(s, true, true, false));
+        RB_TRY(forces_given(s, path, m, precision));
+        const rb_mlp* mm = path == RB_PATH_NN ? m : nullptr;
+        RB_TRY(step_impl(s, path, mm, mm ? mm->version : 0, path == RB_PATH_NN ? precision : RB_FP32,
+                         1, dt, reinterpret_cast<float4*>(state_host)));
+        return (sync & 1) ? check_status(s) : RB_OK;
+    }
     // the device side is one block in the same order (pos .. torque): one copy each way
     const size_t bytes = 6 * sizeof(float4) * s->N;
     RB_CUDA(cudaMemcpyAsync(s->pos, state_host, bytes, cudaMemcpyHostToDevice, s->stream));
@@ -2007,7 +2112,7 @@ rb_status rb_step_host_state(rb_system* s, int32_t path, const rb_mlp* m, int32_
     RB_TRY(forces_given(s, path, m, precision));
     RB_TRY(rb_step(s, path, m, precision, n_steps, dt));
     RB_CUDA(cudaMemcpyAsync(state_host, s->pos, bytes, cudaMemcpyDeviceToHost, s->stream));
-    return sync ? check_status(s) : RB_OK;
+    return (sync & 1) ? check_status(s) : RB_OK;
 }
 
 }  // extern "C"

@@ -118,8 +118,9 @@ def test_set_forces_refuses_bad_arguments():
         s.set_forces(F, torch.zeros((64, 4)))
 
 
+@pytest.mark.parametrize("copies", [False, True])
 @pytest.mark.parametrize("kind", ["beads", "bf16"])
-def test_step_host_state_matches_the_uninterrupted_run(kind):
+def test_step_host_state_matches_the_uninterrupted_run(kind, copies):
     import torch
 
     keys = ("pos", "quat", "vel", "angmom")
@@ -132,11 +133,16 @@ def test_step_host_state_matches_the_uninterrupted_run(kind):
     b.get_state(to_host=True, out={k: blk[i] for i, k in enumerate(keys)})
     b.get_forces(to_host=True, out=(blk[4], blk[5]))
     for _ in range(3):
-        b.step_host_state(blk, 1, DT, **cfg)
+        b.step_host_state(blk, 1, DT, copies=copies, **cfg)
     sa = a.get_state()
     fa = a.get_forces()
     for i, k in enumerate(keys):
         assert torch.equal(sa[k].cpu(), blk[i]), k
     assert torch.equal(fa[0].cpu(), blk[4]) and torch.equal(fa[1].cpu(), blk[5])
+    # the device side holds the same state and forces as the block
+    sb, fb = b.get_state(), b.get_forces()
+    for i, k in enumerate(keys):
+        assert torch.equal(sb[k].cpu(), blk[i]), k
+    assert torch.equal(fb[0].cpu(), blk[4]) and torch.equal(fb[1].cpu(), blk[5])
     with pytest.raises(ValueError):
         b.step_host_state(blk[:5], 1, DT, **cfg)
