@@ -161,3 +161,29 @@ def test_batched_replicas_match_their_own_runs():
             a, b = np.asarray(fin[k], np.float64), np.asarray(own[k], np.float64)
             d = float(np.max(np.abs(a - b)))
             assert d <= 1e-5 * float(np.max(np.abs(b))), (shape, path, prec, skin, k, d)
+
+
+def test_lanes_do_not_change_results():
+    """The same requests spread over one lane, three lanes or eight end bit for
+    bit alike: a replica's arithmetic does not depend on which batch it is in."""
+    from paper_2402_12199_gb300 import api
+
+    m = net()
+    reqs = [(make_state(400 + 150 * k, (0.10 if k % 2 else 0.15) + 0.01 * (k % 3), 60 + k,
+                        "cylinder" if k % 2 else "cube"), k % 2) for k in range(6)]
+    finals = []
+    for lanes in (1, 3, 8):
+        srv = api.Server(8 << 30, 6, m, steps_per_tick=3, lanes=lanes)
+        tickets = [srv.submit(st, [L] * 3, "cylinder" if cyl else "cube",
+                              api.RB_PATH_BEADS if cyl else api.RB_PATH_NN, "bf16", 10, skin=0.4)
+                   for (st, L, _), cyl in reqs]
+        res = [srv.wait(t) for t in tickets]
+        assert all(r["status"] == 0 and r["steps_done"] == 10 for r in res), res
+        finals.append([srv.fetch_state(t) for t in tickets])
+        srv.close()
+    for other in finals[1:]:
+        for a, b in zip(finals[0], other):
+            for k in ("pos", "quat", "vel", "angmom"):
+                assert np.array_equal(a[k], b[k]), k
+    with pytest.raises(api.RBError):
+        api.Server(1 << 30, 2, m, lanes=9)
