@@ -123,15 +123,17 @@ def combine_ranks(ms_step: float, units: float, device=None):
 
 
 def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=5,
-                rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None, lanes=None):
+                rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None, lanes=None,
+                cyl_mlp=None):
     """Serving workload: cube/cylinder replicas with N log-uniform in
     [512, n_max], phi in [0.05, 0.25], kT in [0.5, 1.5], `steps` MD steps each,
     Poisson arrivals at rate_factor / (solo run time of the first request), so
-    about rate_factor replicas are in flight; cubes on the network (BF16),
-    cylinders on the bead path (the network is a cube model).  solo_rates
-    (optional): pair evaluations/s of each path on one large system alone,
-    {"nn": ..., "beads": ...}; the mix's reference rate then weights them by
-    each path's share of the pairs evaluated."""
+    about rate_factor replicas are in flight; cubes on the cube network (BF16),
+    cylinders on the cylinder network (cyl_mlp, BF16) or, without one, on the
+    bead path.  solo_rates (optional): pair evaluations/s of each path on one
+    large system alone, {"nn": ..., "nn_cyl": ..., "beads": ...}; the mix's
+    reference rate then weights them by each path's share of the pairs
+    evaluated."""
     import time as _t
 
     rng = np.random.default_rng(seed)
@@ -149,17 +151,18 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
                 break
             except ValueError:
                 phi -= 0.02
-        path = api.RB_PATH_NN if (shape == "cube" and mlp is not None) else api.RB_PATH_BEADS
+        net = mlp if shape == "cube" else cyl_mlp
+        path = api.RB_PATH_NN if net is not None else api.RB_PATH_BEADS
         reqs.append((st, L, shape, path))
     # calibration: one solo request to set the arrival rate
-    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
+    srv = server(api, budget_bytes, slots, mlp, cyl_mlp, lanes)
     st, L, shape, path = reqs[0]
     t0 = _t.perf_counter()
     srv.wait(srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4))
     t_solo = _t.perf_counter() - t0
     srv.close()
     gaps = rng.exponential(t_solo / rate_factor, size=n_requests)
-    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
+    srv = server(api, budget_bytes, slots, mlp, cyl_mlp, lanes)
     t0 = _t.perf_counter()
     tickets = []
     for (st, L, shape, path), g in zip(reqs, gaps):
@@ -171,7 +174,7 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     srv.close()
     # capacity: the same requests all submitted at once (a closed queue), so
     # the aggregate rate is the server's, not the arrival process's
-    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
+    srv = server(api, budget_bytes, slots, mlp, cyl_mlp, lanes)
     t0 = _t.perf_counter()
     tk = [srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4) for st, L, shape, path in reqs]
     for t in tk:
@@ -180,18 +183,23 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     sat = srv.stats()
     srv.close()
     ok = sum(r["status"] == 0 for r in res)
-    by_path = {"nn": 0.0, "beads": 0.0}
-    for (_, _, _, path), r in zip(reqs, res):
-        key = "nn" if (path == api.RB_PATH_NN and not r["fell_back"]) else "beads"
-        by_path[key] += float(r["pairs"]) * float(r["steps_done"])
+
+    def path_key(shape, path, r):
+        if path == api.RB_PATH_NN and not r["fell_back"]:
+            return "nn" if shape == "cube" else "nn_cyl"
+        return "beads"
+
+    by_path = {"nn": 0.0, "nn_cyl": 0.0, "beads": 0.0}
+    for (_, _, shape, path), r in zip(reqs, res):
+        by_path[path_key(shape, path, r)] += float(r["pairs"]) * float(r["steps_done"])
     mix = None
     if solo_rates and all(solo_rates.get(k) for k in by_path if by_path[k] > 0):
         tot = sum(by_path.values())
         ref = tot / sum(v / solo_rates[k] for k, v in by_path.items() if v > 0)
         # per request: its median step time over the time its pairs take alone on the GPU
         slow = []
-        for (_, _, _, path), r in zip(reqs, res):
-            key = "nn" if (path == api.RB_PATH_NN and not r["fell_back"]) else "beads"
+        for (_, _, shape, path), r in zip(reqs, res):
+            key = path_key(shape, path, r)
             if r["pairs"] > 0 and solo_rates.get(key):
                 slow.append(r["step_ms_p50"] / (1e3 * r["pairs"] / solo_rates[key]))
         mix = {"pairs_by_path": by_path, "solo_rates": solo_rates, "reference_rate": ref,
@@ -204,13 +212,15 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
                "efficiency_poisson": stats["pair_evals"] / makespan / ref,
                "efficiency_saturated": sat["pair_evals"] / sat_span / ref,
                "note": "reference_rate: the same pairs at each path's rate on one large system "
-                       "alone (cubes: BF16 network, 32768-cube bench system; cylinders: bead "
-                       "sum, 32768-cylinder system)"}
+                       "alone (cubes: BF16 network, 32768-cube bench system; cylinders: the "
+                       "width-256 cylinder network or the bead sum, 32768-cylinder system)"}
     return {"requests": n_requests, "completed_ok": ok, "steps_each": steps,
             "workload": f"cube or cylinder with probability 1/2, N log-uniform in [512, {n_max}], "
                         f"phi in [0.05, 0.25], kT in [0.5, 1.5]; Poisson arrivals, about "
                         f"{rate_factor:g} replicas in flight; HBM budget {budget_bytes >> 20} MiB, "
-                        f"{slots} slots",
+                        f"{slots} slots; cubes on the BF16 cube network, cylinders on "
+                        + ("the BF16 width-256 cylinder network" if cyl_mlp is not None
+                           else "the bead path"),
             "makespan_s": makespan, "pair_evals_per_s": stats["pair_evals"] / makespan,
             "step_ms_p50": stats["step_ms_p50"], "step_ms_p99": stats["step_ms_p99"],
             "mix_reference": mix,
@@ -221,6 +231,14 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
             "fell_back": sum(r["fell_back"] for r in res),
             "max_rel_energy_drift": max(abs(r["e_end"] - r["e_start"]) / (r["n_bodies"])
                                         for r in res)}
+
+
+def server(api, budget_bytes, slots, mlp, cyl_mlp, lanes):
+    """A server whose network-path cubes use `mlp` and cylinders `cyl_mlp`."""
+    srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
+    if cyl_mlp is not None:
+        srv.set_network("cylinder", cyl_mlp)
+    return srv
 
 
 def path_info_rate(per_path_ms, n_pairs, p):
@@ -874,6 +892,8 @@ def main():
     # ---- cylinder training throughput at width 256: 1M pairs drawn and
     # labelled on the device, then Adam steps on batches of 4096
     train_cyl = None
+    cyl_net = None        # the trained cylinder network, kept for the serving leg
+    cyl_nn_rate = None    # its pair evaluations/s on the 32768-cylinder system (no fallback)
     if args.train_steps > 0 and any(p.startswith("nn") for p in paths):
         from paper_2402_12199_gb300 import train_net
 
@@ -891,7 +911,24 @@ def main():
         s_cy.set_state(*(torch.from_numpy(st_cy[k]).cuda() for k in ("pos", "quat", "vel", "angmom")))
         s_cy.set_nn_fallback(rc["rho_contact_min"])
         err_cy = train_net.force_error(s_cy, m_cyl, "bf16")
-        del s_cy, m_cyl
+        # MD steps on the network without the bead fallback, as the server runs it
+        s_cy.set_nn_fallback(0.0)
+        for _ in range(3):
+            s_cy.step(1, DT, path=api.RB_PATH_NN, mlp=m_cyl, precision="bf16")
+        ev_cy = []
+        for _ in range(30):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s_cy.step(1, DT, path=api.RB_PATH_NN, mlp=m_cyl, precision="bf16")
+            b.record(stream)
+            ev_cy.append((a, b))
+        torch.cuda.synchronize()
+        s_cy.sync()
+        ms_cy = statistics.mean(a.elapsed_time(b) for a, b in ev_cy)
+        cyl_nn_rate = len(s_cy.pairs()) / (ms_cy * 1e-3)
+        cyl_net = m_cyl
+        del s_cy
         train_cyl = {"workload": "cylinders (8 x 19 beads), network 10-256x3-1, 1M training pairs",
                      "symmetry": rc["symmetry"],
                      "sampler_pairs_per_s": (rc["samples"] + 10000) / rc["t_sample_s"],
@@ -901,7 +938,10 @@ def main():
                                 "contact to Rc: dominated by contact forces)",
                      "model_error_md_state": dict(err_cy, vs="bead path on 32768 cylinders at "
                                                   "phi 0.15 (model error, not parity), BF16, "
-                                                  "bead fallback below the contact separation")}
+                                                  "bead fallback below the contact separation"),
+                     "ms_per_md_step": ms_cy, "pair_evals_per_s": cyl_nn_rate,
+                     "md_note": "32768 cylinders at phi 0.15 on this network (k_nn_tc256), "
+                                "no bead fallback"}
 
     # ---- network width 256 (BF16, streamed weights), same workload, timed alone
     width256 = None
@@ -1320,17 +1360,18 @@ def main():
 
     serving = None
     if not args.no_serving and world == 1:
-        solo = {"nn": path_info_rate(per_path_ms, n_pairs, "nn_bf16")}
+        solo = {"nn": path_info_rate(per_path_ms, n_pairs, "nn_bf16"), "nn_cyl": cyl_nn_rate}
         if fnet_leg is not None:
             solo["beads"] = fnet_leg["pairs"] / (fnet_leg["ms_per_md_step"]["beads"] * 1e-3)
         serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
                               mlp, n_requests=args.serving_requests, steps=args.serving_steps,
-                              n_max=args.serving_nmax, solo_rates=solo)
+                              n_max=args.serving_nmax, solo_rates=solo, cyl_mlp=cyl_net)
         # many small replicas (where stepping them together pays most): N in
         # [512, 4096], 32 slots, about 32 in flight, the server's default lanes
         small = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
                             mlp, n_requests=args.serving_requests, steps=args.serving_steps,
-                            n_max=4096, rate_factor=32.0, budget_bytes=4 << 30, slots=32)
+                            n_max=4096, rate_factor=32.0, budget_bytes=4 << 30, slots=32,
+                            cyl_mlp=cyl_net)
         serving["small_replicas"] = {k: small[k] for k in
                                      ("workload", "makespan_s", "pair_evals_per_s", "step_ms_p50",
                                       "step_ms_p99", "peak_resident", "completed_ok", "saturated")}

@@ -586,6 +586,13 @@ typedef struct rb_server_stats_t {
  * NULL (bead path only); steps_per_tick <= 0 selects 8. */
 rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_mlp* mlp,
                            int32_t steps_per_tick, rb_server** out);
+/* The network that network-path requests of bodies of `shape` (RB_SHAPE_*)
+ * use from now on (their rb_submit calls; NULL: the server's own network
+ * again); the network given to rb_server_create serves every shape that has
+ * none of its own.  A network must stay valid while requests that use it
+ * are queued or resident.  RB_EINVAL for an unknown shape or an unusable
+ * network. */
+rb_status rb_server_set_network(rb_server* server, int32_t shape, const rb_mlp* mlp);
 /* Lanes the replicas admitted from now on are spread over, 1 <= lanes <= 8
  * (RB_EINVAL otherwise; 2 when never set).  Each lane steps its replicas
  * together, one launch per phase, on its own stream; each new replica joins
@@ -596,8 +603,9 @@ rb_status rb_server_set_lanes(rb_server* server, int32_t lanes);
 /* Stops the scheduler; requests still resident end with RB_EINVAL. */
 rb_status rb_server_destroy(rb_server* server);
 /* Queue one replica: `desc` as rb_create_system; pos, quat, vel, angmom are
- * HOST float4 rows (copied); path RB_PATH_BEADS or RB_PATH_NN (the server's
- * network) at `precision`; n_steps of size dt.  RB_ENOMEM if the replica
+ * HOST float4 rows (copied); path RB_PATH_BEADS or RB_PATH_NN (the network
+ * of the body's shape, see rb_server_set_network) at `precision`; n_steps of
+ * size dt.  RB_ENOMEM if the replica
  * could never fit in the budget.  Never blocks on the device. */
 rb_status rb_submit(rb_server* server, const rb_system_desc* desc, const float* pos,
                     const float* quat, const float* vel, const float* angmom, int32_t path,

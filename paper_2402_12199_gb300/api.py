@@ -674,6 +674,15 @@ class Server:
         if lanes is not None:
             self.set_lanes(lanes)
 
+    def set_network(self, shape: str, mlp: "MLP" = None):
+        """rb_server_set_network: the network of network-path requests of bodies
+        of this shape ("cube", "cylinder" or "custom"); None: the server's own."""
+        check(load().rb_server_set_network(self._h, SHAPES[shape],
+                                           mlp.handle if mlp is not None else None))
+        if mlp is not None:
+            self._nets = getattr(self, "_nets", {})
+            self._nets[shape] = mlp  # keep it alive while the server may use it
+
     def set_lanes(self, lanes: int):
         """rb_server_set_lanes: lanes the replicas admitted from now on are spread over."""
         check(load().rb_server_set_lanes(self._h, int(lanes)))

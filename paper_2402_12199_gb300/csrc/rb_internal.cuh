@@ -375,11 +375,13 @@ struct StepSeg {
     const float4 *pF, *pti, *ptj;
 };
 
-// A member of a batch: the system, its force path and precision, its time step.
+// A member of a batch: the system, its force path (with its network on the
+// network path) and precision, its time step.
 struct BatchMember {
     rb_system* s;
     int path, precision;
     float dt;
+    const rb_mlp* mlp;  // RB_PATH_NN only
 };
 struct StepBatch;
 // Device tables of a batch (kMaxSeg systems) and the stream its graphs are
@@ -401,8 +403,8 @@ void batch_tables_free(BatchTables* t);
 // step of an earlier batch on them may be in flight) and captures the step as
 // one CUDA graph.  The network's images are prepared here (outside capture).
 // The members' forces must be valid for their paths.
-rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
-                       const BatchTables& tables, StepBatch** out);
+rb_status batch_create(const std::vector<BatchMember>& members, const BatchTables& tables,
+                       StepBatch** out);
 // n_steps MD steps of every member, on `stream`; each member's step counter advances.
 rb_status batch_step(StepBatch* b, cudaStream_t stream);
 void batch_destroy(StepBatch* b);

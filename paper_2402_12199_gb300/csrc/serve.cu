@@ -53,6 +53,7 @@ struct Request {
     std::vector<float> tmpl;  // custom template copy (desc points into it)
     std::vector<float> pos, quat, vel, angmom;  // initial, then final state
     int path = RB_PATH_BEADS, precision = RB_FP32;
+    const rb_mlp* mlp = nullptr;  // the network of the request's body shape (network path)
     int64_t n_steps = 0, done = 0;
     float dt = 0.002f;
     int64_t footprint = 0;
@@ -119,7 +120,8 @@ struct Lane {
 struct rb_server {
     size_t budget = 0;
     int max_slots = 1;
-    const rb_mlp* mlp = nullptr;
+    const rb_mlp* mlp = nullptr;        // network of the shapes without one of their own
+    const rb_mlp* shape_mlp[3] = {nullptr, nullptr, nullptr};  // per body shape (RB_SHAPE_*)
     int device = 0;
     int chunk = 8;
     std::mutex mu;
@@ -157,9 +159,8 @@ static rb_status start_replica(rb_server* sv, Request* r) {
     RB_TRY(rb_create_system(&r->desc, r->stream, &r->sys));
     RB_TRY(rb_set_state(r->sys, r->pos.data(), r->quat.data(), r->vel.data(), r->angmom.data(), 1));
     for (float4*& b : r->backup) RB_CUDA(cudaMalloc(&b, sizeof(float4) * 4 * r->desc.n_bodies));
-    const rb_mlp* m = r->path == RB_PATH_NN ? sv->mlp : nullptr;
     if (r->path == RB_PATH_NN)
-        RB_TRY(rb_forces_nn(r->sys, m, r->precision, nullptr, nullptr, nullptr, nullptr));
+        RB_TRY(rb_forces_nn(r->sys, r->mlp, r->precision, nullptr, nullptr, nullptr, nullptr));
     else
         RB_TRY(rb_forces_beads(r->sys, nullptr, nullptr, nullptr, nullptr));
     double ep = 0, kt = 0, kr = 0;
@@ -201,7 +202,7 @@ static bool batch_in_flight(const Lane* sv, const StepBatch* b) {
 // The batch for `act` (same members, same paths: the current one), else a
 // new one on the other table set, which must have no tick in flight.
 // Returns RB_EBUSY if it cannot be built now.
-static rb_status ensure_batch(Lane* sv, const rb_mlp* mlp, const std::vector<Request*>& act) {
+static rb_status ensure_batch(Lane* sv, const std::vector<Request*>& act) {
     std::vector<int> paths;
     for (Request* r : act) paths.push_back(r->path);
     if (sv->batch && act == sv->members && paths == sv->member_paths) return RB_OK;
@@ -209,9 +210,10 @@ static rb_status ensure_batch(Lane* sv, const rb_mlp* mlp, const std::vector<Req
         if (t.batch != sv->batch) return RB_EBUSY;
     const int set = sv->batch ? 1 - sv->batch_set : sv->batch_set;
     std::vector<BatchMember> mem;
-    for (Request* r : act) mem.push_back({r->sys, r->path, r->precision, r->dt});
+    for (Request* r : act)
+        mem.push_back({r->sys, r->path, r->precision, r->dt, r->path == RB_PATH_NN ? r->mlp : nullptr});
     StepBatch* b = nullptr;
-    RB_TRY(batch_create(mem, mlp, sv->tables[set], &b));
+    RB_TRY(batch_create(mem, sv->tables[set], &b));
     if (sv->batch) {
         if (batch_in_flight(sv, sv->batch))
             sv->retired.push_back(sv->batch);
@@ -376,7 +378,7 @@ static bool lane_launch(rb_server* sv, Lane* L, int li) {
         }
     }
     if (next.empty()) return false;
-    rb_status st = ensure_batch(L, sv->mlp, next);
+    rb_status st = ensure_batch(L, next);
     if (st == RB_EBUSY) return false;
     if (st == RB_OK) st = launch_tick(L, n);
     if (st != RB_OK) {  // no tick for this set: end its members
@@ -524,6 +526,15 @@ rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_
     return RB_OK;
 }
 
+rb_status rb_server_set_network(rb_server* sv, int32_t shape, const rb_mlp* mlp) {
+    if (!sv) return fail(RB_EINVAL, "null server");
+    if (shape < 0 || shape > 2) return fail(RB_EINVAL, "shape: RB_SHAPE_CUBE, _CYLINDER or _CUSTOM");
+    if (mlp) RB_TRY(check_mlp(mlp));
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->shape_mlp[shape] = mlp;
+    return RB_OK;
+}
+
 rb_status rb_server_set_lanes(rb_server* sv, int32_t lanes) {
     if (!sv) return fail(RB_EINVAL, "null server");
     if (lanes < 1 || lanes > kMaxLanes) return fail(RB_EINVAL, "1 <= lanes <= 8");
@@ -549,7 +560,13 @@ rb_status rb_submit(rb_server* sv, const rb_system_desc* desc, const float* pos,
     if (!sv || !desc || !pos || !quat || !vel || !angmom || !ticket)
         return fail(RB_EINVAL, "null argument");
     if (path != RB_PATH_BEADS && path != RB_PATH_NN) return fail(RB_EINVAL, "unknown path");
-    if (path == RB_PATH_NN && !sv->mlp) return fail(RB_EINVAL, "server has no network");
+    const rb_mlp* net = nullptr;
+    if (path == RB_PATH_NN) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        const int sh = desc->body.shape;
+        net = (sh >= 0 && sh < 3 && sv->shape_mlp[sh]) ? sv->shape_mlp[sh] : sv->mlp;
+        if (!net) return fail(RB_EINVAL, "server has no network for this body shape");
+    }
     if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
         return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
@@ -568,6 +585,7 @@ rb_status rb_submit(rb_server* sv, const rb_system_desc* desc, const float* pos,
     r->vel.assign(vel, vel + n4);
     r->angmom.assign(angmom, angmom + n4);
     r->path = path;
+    r->mlp = net;
     r->precision = precision;
     r->n_steps = n_steps;
     r->dt = dt;

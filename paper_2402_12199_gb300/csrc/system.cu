@@ -926,8 +926,7 @@ static rb_status check_status(rb_system* s) {
 
 struct StepBatch {
     std::vector<BatchMember> mem;
-    const rb_mlp* mlp = nullptr;
-    uint64_t mlp_version = 0;
+    std::vector<std::pair<const rb_mlp*, uint64_t>> nets;  // networks and their versions
     int grid[kBatchPhases] = {0, 0, 0, 0, 0};
     cudaGraphExec_t exec = nullptr;
 };
@@ -1033,8 +1032,8 @@ static PairSeg pair_seg(const rb_system* s) {
     return q;
 }
 
-rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
-                       const BatchTables& tables, StepBatch** out) {
+rb_status batch_create(const std::vector<BatchMember>& members, const BatchTables& tables,
+                       StepBatch** out) {
     *out = nullptr;
     if (!tables.step || !tables.pair || !tables.start) return fail(RB_EINVAL, "batch tables not allocated");
     const int n = (int)members.size();
@@ -1047,6 +1046,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
         if (b.path != RB_PATH_BEADS && b.path != RB_PATH_NN) return fail(RB_EINVAL, "batch member: unknown path");
         if (!(b.dt > 0.f)) return fail(RB_EINVAL, "batch member: dt > 0 required");
         if (s->nh) return fail(RB_EINVAL, "batch member: thermostat not batched (NVE only)");
+        const rb_mlp* m = b.mlp;
         if (b.path == RB_PATH_NN) {
             if (!m) return fail(RB_EINVAL, "batch member on the network path without a network");
             RB_TRY(check_mlp(m));
@@ -1060,14 +1060,18 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
     }
     for (const BatchMember& b : members) {
         if (b.path != RB_PATH_NN) continue;
-        RB_TRY(ensure_pair_sym_arrays(b.s, m));
-        RB_TRY(ensure_images(m, b.precision));
+        RB_TRY(ensure_pair_sym_arrays(b.s, b.mlp));
+        RB_TRY(ensure_images(b.mlp, b.precision));
     }
     StepBatch* B = new (std::nothrow) StepBatch();
     if (!B) return fail(RB_ENOMEM, "host allocation");
     B->mem = members;
-    B->mlp = m;
-    B->mlp_version = m ? m->version : 0;
+    for (const BatchMember& b : members)
+        if (b.path == RB_PATH_NN &&
+            std::find_if(B->nets.begin(), B->nets.end(),
+                         [&](const std::pair<const rb_mlp*, uint64_t>& e) { return e.first == b.mlp; }) ==
+                B->nets.end())
+            B->nets.push_back({b.mlp, b.mlp->version});
     const int num_sms = members[0].s->num_sms;
 
     // per-body phases: each system's blocks as in its own step; the two list
@@ -1113,6 +1117,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
         int first, count;
         const rb_system* like;
         int grid_hint;
+        const rb_mlp* mlp;  // kind 0
     };
     std::vector<Group> groups;
     std::vector<int> single;  // members with no batched pair kernel
@@ -1120,7 +1125,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
     for (int k = 0; k < n; ++k) {
         if (taken[k]) continue;
         const BatchMember& a = members[k];
-        const bool nn = a.path == RB_PATH_NN && a.precision == RB_BF16 && nn_tc2p_batchable(m);
+        const bool nn = a.path == RB_PATH_NN && a.precision == RB_BF16 && nn_tc2p_batchable(a.mlp);
         const bool bd = a.path == RB_PATH_BEADS && a.s->cols.len > 0;
         if (!nn && !bd) {
             single.push_back(k);
@@ -1128,11 +1133,12 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
             continue;
         }
         const std::vector<float> key = bd ? bead_key(a.s) : std::vector<float>();
-        Group g{nn ? 0 : 1, (int)pseg.size(), 0, a.s, 0};
+        Group g{nn ? 0 : 1, (int)pseg.size(), 0, a.s, 0, a.mlp};
         for (int j = k; j < n; ++j) {
             if (taken[j]) continue;
             const BatchMember& b = members[j];
-            const bool same = nn ? (b.path == RB_PATH_NN && b.precision == RB_BF16 && b.s->Rc == a.s->Rc)
+            const bool same = nn ? (b.path == RB_PATH_NN && b.precision == RB_BF16 &&
+                                    b.mlp == a.mlp && b.s->Rc == a.s->Rc)
                                  : (b.path == RB_PATH_BEADS && bead_key(b.s) == key);
             if (!same) continue;
             taken[j] = true;
@@ -1172,7 +1178,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
         for (const Group& g : groups)
             work.push_back([&, g](cudaStream_t st) -> rb_status {
                 if (g.kind == 0)
-                    return nn_tc2p_batch_async(m, g.like, tables.pair + g.first, g.count,
+                    return nn_tc2p_batch_async(g.mlp, g.like, tables.pair + g.first, g.count,
                                                std::max(1, std::min(num_sms, g.grid_hint)), st);
                 bool done = false;
                 RB_TRY(bead_pairs_batch_async(g.like, tables.pair + g.first, g.count, g.grid_hint,
@@ -1186,7 +1192,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
                     cudaStream_t user = s->stream;
                     s->stream = st;
                     rb_status r = members[k].path == RB_PATH_NN
-                                      ? nn_pairs_system_async(s, m, members[k].precision)
+                                      ? nn_pairs_system_async(s, members[k].mlp, members[k].precision)
                                       : bead_pairs_async(s);
                     s->stream = user;
                     RB_TRY(r);
@@ -1239,8 +1245,9 @@ rb_status batch_create(const std::vector<BatchMember>& members, const rb_mlp* m,
 
 rb_status batch_step(StepBatch* b, cudaStream_t stream) {
     if (!b || !b->exec) return fail(RB_EINVAL, "null batch");
-    if (b->mlp && b->mlp->version != b->mlp_version)
-        return fail(RB_EINVAL, "network parameters changed since the batch was made");
+    for (const auto& e : b->nets)
+        if (e.first->version != e.second)
+            return fail(RB_EINVAL, "network parameters changed since the batch was made");
     RB_CUDA(cudaGraphLaunch(b->exec, stream));
     for (BatchMember& m : b->mem) m.s->step += 1;
     return RB_OK;

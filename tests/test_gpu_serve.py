@@ -187,3 +187,44 @@ def test_lanes_do_not_change_results():
                 assert np.array_equal(a[k], b[k]), k
     with pytest.raises(api.RBError):
         api.Server(1 << 30, 2, m, lanes=9)
+
+
+def test_networks_per_body_shape():
+    """Network-path requests use the network set for their body shape, the
+    server's own network serving the other shapes: each replica ends where its
+    own rb_step run with that network ends (to rounding, as above)."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    m_cube, m_cyl = net(3), net(5)
+    A = make_state(600, 0.20, 71)
+    B = make_state(500, 0.12, 72, "cylinder")
+    srv = api.Server(4 << 30, 4, m_cube, steps_per_tick=4)
+    srv.set_network("cylinder", m_cyl)
+    ta = srv.submit(A[0], [A[1]] * 3, "cube", api.RB_PATH_NN, "bf16", 9, skin=0.4)
+    tb = srv.submit(B[0], [B[1]] * 3, "cylinder", api.RB_PATH_NN, "bf16", 9, skin=0.4)
+    fins = {}
+    for t, name in ((ta, "cube"), (tb, "cylinder")):
+        r = srv.wait(t)
+        assert r["status"] == 0 and r["steps_done"] == 9 and r["fell_back"] == 0, r
+        fins[name] = srv.fetch_state(t)
+    srv.close()
+    keys = ("pos", "quat", "vel", "angmom")
+    for (st, L, _), shape, m in ((A, "cube", m_cube), (B, "cylinder", m_cyl)):
+        s = api.System(len(st["pos"]), [L] * 3, shape, skin=0.4)
+        s.set_state(*(torch.from_numpy(np.ascontiguousarray(st[k])).cuda() for k in keys))
+        s.step(9, 0.002, path=api.RB_PATH_NN, mlp=m, precision="bf16")
+        own = s.get_state(to_host=True)
+        for k in keys:
+            a, b = np.asarray(fins[shape][k], np.float64), np.asarray(own[k], np.float64)
+            d = float(np.max(np.abs(a - b)))
+            assert d <= 1e-5 * float(np.max(np.abs(b))), (shape, k, d)
+    # the cylinder really ran on its own network: the cube network gives another trajectory
+    s = api.System(len(B[0]["pos"]), [B[1]] * 3, "cylinder", skin=0.4)
+    s.set_state(*(torch.from_numpy(np.ascontiguousarray(B[0][k])).cuda() for k in keys))
+    s.step(9, 0.002, path=api.RB_PATH_NN, mlp=m_cube, precision="bf16")
+    other = s.get_state(to_host=True)
+    assert not np.array_equal(np.asarray(other["vel"]), fins["cylinder"]["vel"])
+    with pytest.raises(api.RBError):
+        api.Server(1 << 30, 2, m_cube).set_network("custom", api.MLP(128, 3))
