@@ -94,10 +94,14 @@ __global__ void k_prepare_bf16_256(const float* __restrict__ flat, int D,
     }
 }
 
-template <bool SYSTEM>
+// BATCH: the pair lists of n_seg systems (segs: their lists, bodies, boxes
+// and outputs; src and dst give what they share), each padded to whole tiles,
+// so that every tile belongs to one system.
+template <bool SYSTEM, bool BATCH = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_nn_tc256(const float* __restrict__ flat, const unsigned char* __restrict__ img, int D,
-               PairSrc src, PairDst dst, unsigned* status) {
+               PairSrc src, PairDst dst, unsigned* status, const PairSeg* __restrict__ segs,
+               int n_seg) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -140,6 +144,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     pdl_wait();  // weights staged; pair data below may come from the kernels just before
+    // BATCH: each system's first tile (inclusive scan over n_seg <= 32 lanes)
+    // and its pair count
+    __shared__ int s_t0[BATCH ? kMaxSeg + 1 : 1], s_np[BATCH ? kMaxSeg : 1];
+    if constexpr (BATCH) {
+        if (warp == 0) {
+            const int lane = tid & 31;
+            const int np = lane < n_seg ? *segs[lane].n_pairs : 0;
+            int t = (np + kM - 1) / kM;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += v;
+            }
+            s_t0[lane + 1] = t;
+            if (lane == 0) s_t0[0] = 0;
+            s_np[lane] = np;
+        }
+    }
     fence_proxy_async();
     fence_before();
     __syncthreads();
@@ -181,8 +203,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t ph_mma = 0, ph_ld = 0;
     bool ok = true;
     bool ld_pending = false;
-    const int64_t n_total = SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
-    const int64_t n_tiles = (n_total + kM - 1) / kM;
+    const int64_t n_total = BATCH ? 0 : SYSTEM ? (int64_t)(*src.n_pairs_ptr) : src.n_explicit;
+    const int64_t n_tiles = BATCH ? (int64_t)s_t0[n_seg] : (n_total + kM - 1) / kM;
     const int n_stages = 2 * D;
     if ((int64_t)blockIdx.x < n_tiles) {
         if (tid == 0) load_weights(0);
@@ -190,9 +212,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t gp = tile * kM + row;
-        const bool valid = gp < n_total;
-        const PairGeom geo = load_pair<SYSTEM>(src, gp, valid && half == 0);
+        // the tile's system (BATCH: last k with s_t0[k] <= tile), this thread's pair in it
+        int sg = 0;
+        int64_t gp = tile * kM + row;
+        bool valid = gp < n_total;
+        PairSrc sr = src;
+        PairDst dr = dst;
+        if constexpr (BATCH) {
+            int lo = 0, hi = n_seg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_t0[mid] <= tile) lo = mid; else hi = mid - 1;
+            }
+            sg = lo;
+            gp = (tile - s_t0[lo]) * kM + row;
+            valid = gp < s_np[lo];
+            const PairSeg& q = segs[sg];
+            sr.pairs = q.pairs;
+            sr.pos = q.pos;
+            sr.quat = q.quat;
+            sr.L = q.L;
+            sr.invL = q.invL;
+            dr.F = q.F;
+            dr.ti = q.ti;
+            dr.tj = q.tj;
+        }
+        const PairGeom geo = load_pair<SYSTEM>(sr, gp, valid && half == 0);
         if (half == 0) {
             float x[kIn];
             raw_features(geo, x);
@@ -308,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float gx[kIn];
 #pragma unroll
                     for (int k = 0; k < kIn; ++k) gx[k] = e_scale * v[k] * isd[k];
-                    write_pair_outputs<SYSTEM>(dst, gp, geo, gx, E);
+                    write_pair_outputs<SYSTEM>(dr, gp, geo, gx, E);
                 }
             }
         }
@@ -321,7 +366,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
-    if (!ok && tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    if (!ok && tid == 0) {
+        if constexpr (BATCH) {
+            for (int k = 0; k < n_seg; ++k) atomicOr(segs[k].status, ST_TC_TIMEOUT);
+        } else {
+            atomicOr(status, ST_TC_TIMEOUT);
+        }
+    }
 }
 
 }  // namespace tc256
@@ -345,29 +396,56 @@ rb_status nn_tc256_prepare(rb_mlp* m) {
     return RB_OK;
 }
 
-template <bool SYSTEM>
-rb_status launch_tc256(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
-                       const PairDst& dst, unsigned* status) {
+template <bool SYSTEM, bool BATCH = false>
+static rb_status launch_tc256_impl(const rb_mlp* m, cudaStream_t stream, int grid,
+                                   const PairSrc& src, const PairDst& dst, unsigned* status,
+                                   const PairSeg* segs = nullptr, int n_seg = 0) {
     if (!nn_tc256_supported(m) || !m->bf16_img)
         return fail(RB_ENOTSUP, "BF16 width-256 network needs depth 1..3");
     const tc256::Layout L = tc256::layout(m->depth);
     const size_t smem = L.s_total + 1024;
-    static bool attr[2] = {false, false};
-    if (!attr[SYSTEM ? 1 : 0]) {
-        RB_CUDA(cudaFuncSetAttribute(tc256::k_nn_tc256<SYSTEM>,
+    static bool attr = false;
+    if (!attr) {
+        RB_CUDA(cudaFuncSetAttribute(tc256::k_nn_tc256<SYSTEM, BATCH>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[SYSTEM ? 1 : 0] = true;
+        attr = true;
     }
     if (SYSTEM)  // inside an MD step: may start while the list kernels drain
-        RB_CUDA(launch_pdl(tc256::k_nn_tc256<SYSTEM>, grid, tc256::kThreads, smem, stream,
+        RB_CUDA(launch_pdl(tc256::k_nn_tc256<SYSTEM, BATCH>, grid, tc256::kThreads, smem, stream,
                            m->params, static_cast<const unsigned char*>(m->bf16_img), m->depth,
-                           src, dst, status));
+                           src, dst, status, segs, n_seg));
     else
-        tc256::k_nn_tc256<SYSTEM><<<grid, tc256::kThreads, smem, stream>>>(
+        tc256::k_nn_tc256<SYSTEM, BATCH><<<grid, tc256::kThreads, smem, stream>>>(
             m->params, static_cast<const unsigned char*>(m->bf16_img), m->depth, src, dst,
-            status);
+            status, segs, n_seg);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
+}
+
+template <bool SYSTEM>
+rb_status launch_tc256(const rb_mlp* m, cudaStream_t stream, int grid, const PairSrc& src,
+                       const PairDst& dst, unsigned* status) {
+    return launch_tc256_impl<SYSTEM>(m, stream, grid, src, dst, status);
+}
+
+bool nn_tc256_batchable(const rb_mlp* m) {
+    return nn_tc256_supported(m) && !m->pair_sym && m->desc != RB_DESC_PAPER6;
+}
+
+// The width-256 BF16 network over the pair lists of n_seg systems with the
+// body type of `like` (the same kernel, and so the same arithmetic per pair,
+// as one system's pass).  A timed-out MMA wait is flagged in every system's
+// status word.
+rb_status nn_tc256_batch_async(const rb_mlp* m, const rb_system* like, const PairSeg* segs_dev,
+                               int n_seg, int grid, cudaStream_t st) {
+    if (n_seg < 1 || n_seg > kMaxSeg) return fail(RB_EINVAL, "batch of 1 to 32 systems");
+    if (!nn_tc256_batchable(m)) return fail(RB_EINVAL, "network form without a batched kernel");
+    PairSrc src{};
+    set_symmetry(src, m);
+    src.Rc2 = like->Rc * like->Rc;
+    PairDst dst{};
+    set_cutoff(dst, m);
+    return launch_tc256_impl<true, true>(m, st, grid, src, dst, nullptr, segs_dev, n_seg);
 }
 
 template rb_status launch_tc256<true>(const rb_mlp*, cudaStream_t, int, const PairSrc&,

@@ -419,4 +419,8 @@ rb_status nn_tc2p_batch_async(const rb_mlp* m, const rb_system* like, const Pair
 // nn_tc.cu: whether a system pass of this network at BF16 runs the two-pipeline
 // kernel (the one with a batched form)
 bool nn_tc2p_batchable(const rb_mlp* m);
+// nn_tc256.cu: the width-256 BF16 network over the pair lists of several systems
+bool nn_tc256_batchable(const rb_mlp* m);
+rb_status nn_tc256_batch_async(const rb_mlp* m, const rb_system* like, const PairSeg* segs_dev,
+                               int n_seg, int grid, cudaStream_t st);
 }  // namespace rb

@@ -1113,7 +1113,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
     // the rest launch per system inside the same graph
     std::vector<PairSeg> pseg;
     struct Group {
-        int kind;  // 0 network, 1 beads
+        int kind;  // 0 network (width 128), 1 beads, 2 network (width 256)
         int first, count;
         const rb_system* like;
         int grid_hint;
@@ -1125,7 +1125,10 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
     for (int k = 0; k < n; ++k) {
         if (taken[k]) continue;
         const BatchMember& a = members[k];
-        const bool nn = a.path == RB_PATH_NN && a.precision == RB_BF16 && nn_tc2p_batchable(a.mlp);
+        const bool nn2p = a.path == RB_PATH_NN && a.precision == RB_BF16 && nn_tc2p_batchable(a.mlp);
+        const bool nn256 = a.path == RB_PATH_NN && a.precision == RB_BF16 && !nn2p &&
+                           nn_tc256_batchable(a.mlp);
+        const bool nn = nn2p || nn256;
         const bool bd = a.path == RB_PATH_BEADS && a.s->cols.len > 0;
         if (!nn && !bd) {
             single.push_back(k);
@@ -1133,7 +1136,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
             continue;
         }
         const std::vector<float> key = bd ? bead_key(a.s) : std::vector<float>();
-        Group g{nn ? 0 : 1, (int)pseg.size(), 0, a.s, 0, a.mlp};
+        Group g{nn2p ? 0 : nn256 ? 2 : 1, (int)pseg.size(), 0, a.s, 0, a.mlp};
         for (int j = k; j < n; ++j) {
             if (taken[j]) continue;
             const BatchMember& b = members[j];
@@ -1180,6 +1183,9 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
                 if (g.kind == 0)
                     return nn_tc2p_batch_async(g.mlp, g.like, tables.pair + g.first, g.count,
                                                std::max(1, std::min(num_sms, g.grid_hint)), st);
+                if (g.kind == 2)
+                    return nn_tc256_batch_async(g.mlp, g.like, tables.pair + g.first, g.count,
+                                                std::max(1, std::min(num_sms, g.grid_hint)), st);
                 bool done = false;
                 RB_TRY(bead_pairs_batch_async(g.like, tables.pair + g.first, g.count, g.grid_hint,
                                               st, &done));

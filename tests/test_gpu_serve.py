@@ -197,29 +197,35 @@ def test_networks_per_body_shape():
 
     from paper_2402_12199_gb300 import api
 
-    m_cube, m_cyl = net(3), net(5)
+    m_cube = net(3)
+    m_cyl = api.MLP(256, 3)  # width 256: the batched width-256 kernel for the cylinders
+    mu, isd = inputs.feature_normalisation(5.0, 4 * 3 ** 0.5 + 2.5)
+    m_cyl.set_params(inputs.mlp_params(256, 3, 5, mu=mu, inv_sd=isd))
     A = make_state(600, 0.20, 71)
     B = make_state(500, 0.12, 72, "cylinder")
+    C = make_state(700, 0.10, 73, "cylinder")
     srv = api.Server(4 << 30, 4, m_cube, steps_per_tick=4)
     srv.set_network("cylinder", m_cyl)
     ta = srv.submit(A[0], [A[1]] * 3, "cube", api.RB_PATH_NN, "bf16", 9, skin=0.4)
     tb = srv.submit(B[0], [B[1]] * 3, "cylinder", api.RB_PATH_NN, "bf16", 9, skin=0.4)
+    tc = srv.submit(C[0], [C[1]] * 3, "cylinder", api.RB_PATH_NN, "bf16", 9, skin=0.4)
     fins = {}
-    for t, name in ((ta, "cube"), (tb, "cylinder")):
+    for t, name in ((ta, "cube"), (tb, "cylinder"), (tc, "cylinder2")):
         r = srv.wait(t)
         assert r["status"] == 0 and r["steps_done"] == 9 and r["fell_back"] == 0, r
         fins[name] = srv.fetch_state(t)
     srv.close()
     keys = ("pos", "quat", "vel", "angmom")
-    for (st, L, _), shape, m in ((A, "cube", m_cube), (B, "cylinder", m_cyl)):
+    for (st, L, _), shape, m, name in ((A, "cube", m_cube, "cube"), (B, "cylinder", m_cyl, "cylinder"),
+                                       (C, "cylinder", m_cyl, "cylinder2")):
         s = api.System(len(st["pos"]), [L] * 3, shape, skin=0.4)
         s.set_state(*(torch.from_numpy(np.ascontiguousarray(st[k])).cuda() for k in keys))
         s.step(9, 0.002, path=api.RB_PATH_NN, mlp=m, precision="bf16")
         own = s.get_state(to_host=True)
         for k in keys:
-            a, b = np.asarray(fins[shape][k], np.float64), np.asarray(own[k], np.float64)
+            a, b = np.asarray(fins[name][k], np.float64), np.asarray(own[k], np.float64)
             d = float(np.max(np.abs(a - b)))
-            assert d <= 1e-5 * float(np.max(np.abs(b))), (shape, k, d)
+            assert d <= 1e-5 * float(np.max(np.abs(b))), (name, k, d)
     # the cylinder really ran on its own network: the cube network gives another trajectory
     s = api.System(len(B[0]["pos"]), [B[1]] * 3, "cylinder", skin=0.4)
     s.set_state(*(torch.from_numpy(np.ascontiguousarray(B[0][k])).cuda() for k in keys))
