@@ -124,7 +124,7 @@ def combine_ranks(ms_step: float, units: float, device=None):
 
 def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=5,
                 rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None, lanes=None,
-                cyl_mlp=None):
+                cyl_mlp=None, rho=(0.0, 0.0)):
     """Serving workload: cube/cylinder replicas with N log-uniform in
     [512, n_max], phi in [0.05, 0.25], kT in [0.5, 1.5], `steps` MD steps each,
     Poisson arrivals at rate_factor / (solo run time of the first request), so
@@ -133,7 +133,8 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     bead path.  solo_rates (optional): pair evaluations/s of each path on one
     large system alone, {"nn": ..., "nn_cyl": ..., "beads": ...}; the mix's
     reference rate then weights them by each path's share of the pairs
-    evaluated."""
+    evaluated.  rho: the bead-fallback radii of the cube and the cylinder
+    network (0: none)."""
     import time as _t
 
     rng = np.random.default_rng(seed)
@@ -155,14 +156,14 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
         path = api.RB_PATH_NN if net is not None else api.RB_PATH_BEADS
         reqs.append((st, L, shape, path))
     # calibration: one solo request to set the arrival rate
-    srv = server(api, budget_bytes, slots, mlp, cyl_mlp, lanes)
+    srv = make_server(api, budget_bytes, slots, mlp, cyl_mlp, lanes, rho)
     st, L, shape, path = reqs[0]
     t0 = _t.perf_counter()
     srv.wait(srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4))
     t_solo = _t.perf_counter() - t0
     srv.close()
     gaps = rng.exponential(t_solo / rate_factor, size=n_requests)
-    srv = server(api, budget_bytes, slots, mlp, cyl_mlp, lanes)
+    srv = make_server(api, budget_bytes, slots, mlp, cyl_mlp, lanes, rho)
     t0 = _t.perf_counter()
     tickets = []
     for (st, L, shape, path), g in zip(reqs, gaps):
@@ -174,7 +175,7 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     srv.close()
     # capacity: the same requests all submitted at once (a closed queue), so
     # the aggregate rate is the server's, not the arrival process's
-    srv = server(api, budget_bytes, slots, mlp, cyl_mlp, lanes)
+    srv = make_server(api, budget_bytes, slots, mlp, cyl_mlp, lanes, rho)
     t0 = _t.perf_counter()
     tk = [srv.submit(st, [L] * 3, shape, path, "bf16", steps, skin=0.4) for st, L, shape, path in reqs]
     for t in tk:
@@ -220,7 +221,9 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
                         f"{rate_factor:g} replicas in flight; HBM budget {budget_bytes >> 20} MiB, "
                         f"{slots} slots; cubes on the BF16 cube network, cylinders on "
                         + ("the BF16 width-256 cylinder network" if cyl_mlp is not None
-                           else "the bead path"),
+                           else "the bead path")
+                        + (f"; network pairs closer than {rho[0]:.3f} (cubes) / {rho[1]:.3f} "
+                           f"(cylinders) sigma take the bead sum" if max(rho) > 0 else ""),
             "makespan_s": makespan, "pair_evals_per_s": stats["pair_evals"] / makespan,
             "step_ms_p50": stats["step_ms_p50"], "step_ms_p99": stats["step_ms_p99"],
             "mix_reference": mix,
@@ -233,11 +236,14 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
                                         for r in res)}
 
 
-def server(api, budget_bytes, slots, mlp, cyl_mlp, lanes):
-    """A server whose network-path cubes use `mlp` and cylinders `cyl_mlp`."""
+def make_server(api, budget_bytes, slots, mlp, cyl_mlp, lanes, rho=(0.0, 0.0)):
+    """A server whose network-path cubes use `mlp` and cylinders `cyl_mlp`,
+    with the bead-fallback radii rho = (cube, cylinder)."""
     srv = api.Server(budget_bytes, slots, mlp, steps_per_tick=8, lanes=lanes)
+    if mlp is not None:
+        srv.set_network("cube", mlp, rho_min=rho[0])
     if cyl_mlp is not None:
-        srv.set_network("cylinder", cyl_mlp)
+        srv.set_network("cylinder", cyl_mlp, rho_min=rho[1])
     return srv
 
 
@@ -894,6 +900,7 @@ def main():
     train_cyl = None
     cyl_net = None        # the trained cylinder network, kept for the serving leg
     cyl_nn_rate = None    # its pair evaluations/s on the 32768-cylinder system (no fallback)
+    cyl_rho = 0.0         # its bead-fallback radius (the training set's smallest contact)
     if args.train_steps > 0 and any(p.startswith("nn") for p in paths):
         from paper_2402_12199_gb300 import train_net
 
@@ -928,6 +935,7 @@ def main():
         ms_cy = statistics.mean(a.elapsed_time(b) for a, b in ev_cy)
         cyl_nn_rate = len(s_cy.pairs()) / (ms_cy * 1e-3)
         cyl_net = m_cyl
+        cyl_rho = rc["rho_contact_min"]
         del s_cy
         train_cyl = {"workload": "cylinders (8 x 19 beads), network 10-256x3-1, 1M training pairs",
                      "symmetry": rc["symmetry"],
@@ -1365,13 +1373,14 @@ def main():
             solo["beads"] = fnet_leg["pairs"] / (fnet_leg["ms_per_md_step"]["beads"] * 1e-3)
         serving = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
                               mlp, n_requests=args.serving_requests, steps=args.serving_steps,
-                              n_max=args.serving_nmax, solo_rates=solo, cyl_mlp=cyl_net)
+                              n_max=args.serving_nmax, solo_rates=solo, cyl_mlp=cyl_net,
+                              rho=(rho_fallback, cyl_rho))
         # many small replicas (where stepping them together pays most): N in
         # [512, 4096], 32 slots, about 32 in flight, the server's default lanes
         small = serving_run(api, __import__("paper_2402_12199_gb300.inputs", fromlist=["x"]),
                             mlp, n_requests=args.serving_requests, steps=args.serving_steps,
                             n_max=4096, rate_factor=32.0, budget_bytes=4 << 30, slots=32,
-                            cyl_mlp=cyl_net)
+                            cyl_mlp=cyl_net, rho=(rho_fallback, cyl_rho))
         serving["small_replicas"] = {k: small[k] for k in
                                      ("workload", "makespan_s", "pair_evals_per_s", "step_ms_p50",
                                       "step_ms_p99", "peak_resident", "completed_ok", "saturated")}

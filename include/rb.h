@@ -588,11 +588,13 @@ rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_
                            int32_t steps_per_tick, rb_server** out);
 /* The network that network-path requests of bodies of `shape` (RB_SHAPE_*)
  * use from now on (their rb_submit calls; NULL: the server's own network
- * again); the network given to rb_server_create serves every shape that has
- * none of its own.  A network must stay valid while requests that use it
- * are queued or resident.  RB_EINVAL for an unknown shape or an unusable
- * network. */
-rb_status rb_server_set_network(rb_server* server, int32_t shape, const rb_mlp* mlp);
+ * again), and its bead-fallback radius: rho_min > 0 makes the replica's
+ * pairs closer than rho_min take the bead sum (rb_set_nn_fallback), 0 none.
+ * The network given to rb_server_create serves every shape that has none of
+ * its own, without a fallback.  A network must stay valid while requests
+ * that use it are queued or resident.  RB_EINVAL for an unknown shape, an
+ * unusable network or rho_min < 0. */
+rb_status rb_server_set_network(rb_server* server, int32_t shape, const rb_mlp* mlp, float rho_min);
 /* Lanes the replicas admitted from now on are spread over, 1 <= lanes <= 8
  * (RB_EINVAL otherwise; 2 when never set).  Each lane steps its replicas
  * together, one launch per phase, on its own stream; each new replica joins

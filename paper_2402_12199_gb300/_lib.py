@@ -138,7 +138,7 @@ SIGNATURES = {
     "rb_server_create": (I32, [ctypes.c_size_t, I32, P, I32, ctypes.POINTER(P)]),
     "rb_server_destroy": (I32, [P]),
     "rb_server_set_lanes": (I32, [P, I32]),
-    "rb_server_set_network": (I32, [P, I32, P]),
+    "rb_server_set_network": (I32, [P, I32, P, ctypes.c_float]),
     "rb_submit": (I32, [P, ctypes.POINTER(rb_system_desc), P, P, P, P, I32, I32, I64, F32,
                         ctypes.POINTER(ctypes.c_uint64)]),
     "rb_poll": (I32, [P, ctypes.c_uint64, ctypes.POINTER(rb_result)]),

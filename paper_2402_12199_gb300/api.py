@@ -674,11 +674,12 @@ class Server:
         if lanes is not None:
             self.set_lanes(lanes)
 
-    def set_network(self, shape: str, mlp: "MLP" = None):
+    def set_network(self, shape: str, mlp: "MLP" = None, rho_min: float = 0.0):
         """rb_server_set_network: the network of network-path requests of bodies
-        of this shape ("cube", "cylinder" or "custom"); None: the server's own."""
+        of this shape ("cube", "cylinder" or "custom"; None: the server's own)
+        and its bead-fallback radius (0: none)."""
         check(load().rb_server_set_network(self._h, SHAPES[shape],
-                                           mlp.handle if mlp is not None else None))
+                                           mlp.handle if mlp is not None else None, float(rho_min)))
         if mlp is not None:
             self._nets = getattr(self, "_nets", {})
             self._nets[shape] = mlp  # keep it alive while the server may use it

@@ -236,6 +236,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             dr.F = q.F;
             dr.ti = q.ti;
             dr.tj = q.tj;
+            dr.fb_list = q.fb_list;
+            dr.fb_count = q.fb_count;
+            dr.fb_rho2 = q.fb_rho2;
         }
         const PairGeom geo = load_pair<SYSTEM>(sr, gp, valid && half == 0);
         if (half == 0) {

@@ -206,6 +206,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             r.F = q.F;
             r.ti = q.ti;
             r.tj = q.tj;
+            r.fb_list = q.fb_list;
+            r.fb_count = q.fb_count;
+            r.fb_rho2 = q.fb_rho2;
         }
         return r;
     };

@@ -343,6 +343,11 @@ constexpr int kBatchPhases = 5;  // integrate, cell assign, pair build, pair emi
 // One system's slice of a batched pair kernel.
 struct PairSeg {
     unsigned* status;  // the system's status word
+    // the network path's bead fallback (fb_rho2 = 0: none): pairs closer than
+    // sqrt(fb_rho2) appended to fb_list, count in *fb_count
+    int* fb_list;
+    int* fb_count;
+    float fb_rho2;
     const int2* pairs;
     const int* n_pairs;
     const float4* pos;
@@ -363,6 +368,7 @@ struct StepSeg {
     int4* image;
     int* rebuild;
     unsigned* status;
+    int* zero_count;    // reset by the cell-assign kernel (the bead-fallback count), or null
     int force_rebuild;  // no skin: every step rebuilds the list
     int* cell_count;
     int* cell_bodies;

@@ -54,6 +54,7 @@ struct Request {
     std::vector<float> pos, quat, vel, angmom;  // initial, then final state
     int path = RB_PATH_BEADS, precision = RB_FP32;
     const rb_mlp* mlp = nullptr;  // the network of the request's body shape (network path)
+    float rho_min = 0.f;          // its bead-fallback radius (0: none)
     int64_t n_steps = 0, done = 0;
     float dt = 0.002f;
     int64_t footprint = 0;
@@ -122,6 +123,7 @@ struct rb_server {
     int max_slots = 1;
     const rb_mlp* mlp = nullptr;        // network of the shapes without one of their own
     const rb_mlp* shape_mlp[3] = {nullptr, nullptr, nullptr};  // per body shape (RB_SHAPE_*)
+    float shape_rho[3] = {0.f, 0.f, 0.f};  // their bead-fallback radii (0: none)
     int device = 0;
     int chunk = 8;
     std::mutex mu;
@@ -159,6 +161,7 @@ static rb_status start_replica(rb_server* sv, Request* r) {
     RB_TRY(rb_create_system(&r->desc, r->stream, &r->sys));
     RB_TRY(rb_set_state(r->sys, r->pos.data(), r->quat.data(), r->vel.data(), r->angmom.data(), 1));
     for (float4*& b : r->backup) RB_CUDA(cudaMalloc(&b, sizeof(float4) * 4 * r->desc.n_bodies));
+    if (r->path == RB_PATH_NN && r->rho_min > 0.f) RB_TRY(rb_set_nn_fallback(r->sys, r->rho_min));
     if (r->path == RB_PATH_NN)
         RB_TRY(rb_forces_nn(r->sys, r->mlp, r->precision, nullptr, nullptr, nullptr, nullptr));
     else
@@ -526,12 +529,14 @@ rb_status rb_server_create(size_t hbm_budget_bytes, int32_t max_slots, const rb_
     return RB_OK;
 }
 
-rb_status rb_server_set_network(rb_server* sv, int32_t shape, const rb_mlp* mlp) {
+rb_status rb_server_set_network(rb_server* sv, int32_t shape, const rb_mlp* mlp, float rho_min) {
     if (!sv) return fail(RB_EINVAL, "null server");
     if (shape < 0 || shape > 2) return fail(RB_EINVAL, "shape: RB_SHAPE_CUBE, _CYLINDER or _CUSTOM");
     if (mlp) RB_TRY(check_mlp(mlp));
+    if (!(rho_min >= 0.f)) return fail(RB_EINVAL, "rho_min >= 0 required");
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->shape_mlp[shape] = mlp;
+    sv->shape_rho[shape] = mlp ? rho_min : 0.f;
     return RB_OK;
 }
 
@@ -561,10 +566,13 @@ rb_status rb_submit(rb_server* sv, const rb_system_desc* desc, const float* pos,
         return fail(RB_EINVAL, "null argument");
     if (path != RB_PATH_BEADS && path != RB_PATH_NN) return fail(RB_EINVAL, "unknown path");
     const rb_mlp* net = nullptr;
+    float rho = 0.f;
     if (path == RB_PATH_NN) {
         std::lock_guard<std::mutex> lk(sv->mu);
         const int sh = desc->body.shape;
-        net = (sh >= 0 && sh < 3 && sv->shape_mlp[sh]) ? sv->shape_mlp[sh] : sv->mlp;
+        const bool own = sh >= 0 && sh < 3 && sv->shape_mlp[sh];
+        net = own ? sv->shape_mlp[sh] : sv->mlp;
+        rho = own ? sv->shape_rho[sh] : 0.f;
         if (!net) return fail(RB_EINVAL, "server has no network for this body shape");
     }
     if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
@@ -586,6 +594,7 @@ rb_status rb_submit(rb_server* sv, const rb_system_desc* desc, const float* pos,
     r->angmom.assign(angmom, angmom + n4);
     r->path = path;
     r->mlp = net;
+    r->rho_min = rho;
     r->precision = precision;
     r->n_steps = n_steps;
     r->dt = dt;

@@ -782,7 +782,7 @@ __global__ void k_cell_assign_batch(const StepSeg* __restrict__ segs, const int*
     const int k = seg_of_block(start, n_seg, blockIdx.x);
     const StepSeg& S = segs[k];
     cell_assign_body(S.pos, S.N, S.L, S.invL, S.invw, S.nc, S.cell_count, S.cell_bodies, S.cell_cap,
-                     S.status, S.rebuild, nullptr, blockIdx.x - start[k]);
+                     S.status, S.rebuild, S.zero_count, blockIdx.x - start[k]);
 }
 
 __global__ void k_pair_build_batch(const StepSeg* __restrict__ segs, const int* __restrict__ start,
@@ -1017,9 +1017,16 @@ static StepSeg step_seg(const rb_system* s, float dt) {
     return q;
 }
 
-static PairSeg pair_seg(const rb_system* s) {
+// fb: the member's network pass lists its bead-fallback pairs (its fallback radius)
+static PairSeg pair_seg(const rb_system* s, bool fb) {
     PairSeg q{};
     q.status = s->status_dev;
+    if (fb) {
+        const float r = std::min(s->nn_fallback_rho, s->Rc);
+        q.fb_list = s->fb_list;
+        q.fb_count = s->fallback_count;
+        q.fb_rho2 = r * r;
+    }
     q.pairs = s->pl.pairs;
     q.n_pairs = s->pl.n_pairs;
     q.pos = s->pos;
@@ -1050,7 +1057,6 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
         if (b.path == RB_PATH_NN) {
             if (!m) return fail(RB_EINVAL, "batch member on the network path without a network");
             RB_TRY(check_mlp(m));
-            if (s->nn_fallback_rho > 0.f) return fail(RB_EINVAL, "batch member: bead fallback not batched");
         }
         const bool valid = s->forces_valid && s->forces_path == b.path &&
                            (b.path != RB_PATH_NN ||
@@ -1117,7 +1123,8 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
         int first, count;
         const rb_system* like;
         int grid_hint;
-        const rb_mlp* mlp;  // kind 0
+        const rb_mlp* mlp;        // kinds 0, 2
+        std::vector<int> fb;      // members whose network pass lists bead-fallback pairs
     };
     std::vector<Group> groups;
     std::vector<int> single;  // members with no batched pair kernel
@@ -1136,7 +1143,7 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
             continue;
         }
         const std::vector<float> key = bd ? bead_key(a.s) : std::vector<float>();
-        Group g{nn2p ? 0 : nn256 ? 2 : 1, (int)pseg.size(), 0, a.s, 0, a.mlp};
+        Group g{nn2p ? 0 : nn256 ? 2 : 1, (int)pseg.size(), 0, a.s, 0, a.mlp, {}};
         for (int j = k; j < n; ++j) {
             if (taken[j]) continue;
             const BatchMember& b = members[j];
@@ -1145,7 +1152,12 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
                                  : (b.path == RB_PATH_BEADS && bead_key(b.s) == key);
             if (!same) continue;
             taken[j] = true;
-            pseg.push_back(pair_seg(b.s));
+            const bool fb = nn && b.s->nn_fallback_rho > 0.f;
+            if (fb) {
+                g.fb.push_back(j);
+                seg[j].zero_count = b.s->fallback_count;  // reset by the batch's cell assign
+            }
+            pseg.push_back(pair_seg(b.s, fb));
             ++g.count;
             g.grid_hint += nn ? pair_grid(b.s, 128, num_sms) : pair_grid(b.s, 8, 1 << 30);
         }
@@ -1178,14 +1190,26 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
         // the pair phase: each group (and the members launched one by one,
         // together) on its own branch, so that their kernels share the GPU
         std::vector<std::function<rb_status(cudaStream_t)>> work;
+        // a member's bead fallback on stream st, after its network pass there
+        auto fallback = [&](int k, cudaStream_t st) -> rb_status {
+            rb_system* s = members[k].s;
+            cudaStream_t user = s->stream;
+            s->stream = st;
+            const rb_status r = bead_fallback_async(s);
+            s->stream = user;
+            return r;
+        };
         for (const Group& g : groups)
             work.push_back([&, g](cudaStream_t st) -> rb_status {
-                if (g.kind == 0)
-                    return nn_tc2p_batch_async(g.mlp, g.like, tables.pair + g.first, g.count,
-                                               std::max(1, std::min(num_sms, g.grid_hint)), st);
-                if (g.kind == 2)
-                    return nn_tc256_batch_async(g.mlp, g.like, tables.pair + g.first, g.count,
-                                                std::max(1, std::min(num_sms, g.grid_hint)), st);
+                if (g.kind == 0 || g.kind == 2) {
+                    const int grid = std::max(1, std::min(num_sms, g.grid_hint));
+                    RB_TRY(g.kind == 0 ? nn_tc2p_batch_async(g.mlp, g.like, tables.pair + g.first,
+                                                             g.count, grid, st)
+                                       : nn_tc256_batch_async(g.mlp, g.like, tables.pair + g.first,
+                                                              g.count, grid, st));
+                    for (int k : g.fb) RB_TRY(fallback(k, st));
+                    return RB_OK;
+                }
                 bool done = false;
                 RB_TRY(bead_pairs_batch_async(g.like, tables.pair + g.first, g.count, g.grid_hint,
                                               st, &done));
@@ -1202,6 +1226,8 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
                                       : bead_pairs_async(s);
                     s->stream = user;
                     RB_TRY(r);
+                    if (members[k].path == RB_PATH_NN && s->nn_fallback_rho > 0.f)
+                        RB_TRY(fallback(k, st));
                 }
                 return RB_OK;
             });

@@ -190,9 +190,11 @@ def test_lanes_do_not_change_results():
 
 
 def test_networks_per_body_shape():
-    """Network-path requests use the network set for their body shape, the
-    server's own network serving the other shapes: each replica ends where its
-    own rb_step run with that network ends (to rounding, as above)."""
+    """Network-path requests use the network set for their body shape (with
+    its bead-fallback radius): each replica ends where its own rb_step run
+    with that network and fallback ends (to rounding, as above).  The cube
+    network's radius, 8.5 sigma, sends the closer pairs to the bead sum inside
+    the batched step."""
     import torch
 
     from paper_2402_12199_gb300 import api
@@ -205,6 +207,7 @@ def test_networks_per_body_shape():
     B = make_state(500, 0.12, 72, "cylinder")
     C = make_state(700, 0.10, 73, "cylinder")
     srv = api.Server(4 << 30, 4, m_cube, steps_per_tick=4)
+    srv.set_network("cube", m_cube, rho_min=8.5)
     srv.set_network("cylinder", m_cyl)
     ta = srv.submit(A[0], [A[1]] * 3, "cube", api.RB_PATH_NN, "bf16", 9, skin=0.4)
     tb = srv.submit(B[0], [B[1]] * 3, "cylinder", api.RB_PATH_NN, "bf16", 9, skin=0.4)
@@ -220,12 +223,16 @@ def test_networks_per_body_shape():
                                        (C, "cylinder", m_cyl, "cylinder2")):
         s = api.System(len(st["pos"]), [L] * 3, shape, skin=0.4)
         s.set_state(*(torch.from_numpy(np.ascontiguousarray(st[k])).cuda() for k in keys))
+        if shape == "cube":
+            s.set_nn_fallback(8.5)
         s.step(9, 0.002, path=api.RB_PATH_NN, mlp=m, precision="bf16")
         own = s.get_state(to_host=True)
         for k in keys:
             a, b = np.asarray(fins[name][k], np.float64), np.asarray(own[k], np.float64)
             d = float(np.max(np.abs(a - b)))
             assert d <= 1e-5 * float(np.max(np.abs(b))), (name, k, d)
+        if shape == "cube":  # the fallback took pairs in this run
+            assert s.nn_fallback_count() > 0
     # the cylinder really ran on its own network: the cube network gives another trajectory
     s = api.System(len(B[0]["pos"]), [B[1]] * 3, "cylinder", skin=0.4)
     s.set_state(*(torch.from_numpy(np.ascontiguousarray(B[0][k])).cuda() for k in keys))
@@ -234,3 +241,5 @@ def test_networks_per_body_shape():
     assert not np.array_equal(np.asarray(other["vel"]), fins["cylinder"]["vel"])
     with pytest.raises(api.RBError):
         api.Server(1 << 30, 2, m_cube).set_network("custom", api.MLP(128, 3))
+    with pytest.raises(api.RBError):
+        api.Server(1 << 30, 2, m_cube).set_network("cube", m_cube, rho_min=-1.0)
