@@ -548,7 +548,8 @@ int64_t rb_system_footprint(const rb_system_desc* desc);
 /* A server runs many independent MD replicas (the paper runs one simulation
  * per GPU; serving many is this library's extension) with continuous
  * batching: a scheduler thread admits queued requests whenever a slot is free
- * and the replica's footprint fits in `hbm_budget_bytes`, steps the resident
+ * and the replica's footprint (rb_system_footprint plus 128 bytes per body of
+ * the server's state backups) fits in `hbm_budget_bytes`, steps the resident
  * replicas together (each MD step is one launch per phase for all of them:
  * the per-body kernels over a grid split among the replicas, the pair
  * kernels over their concatenated pair lists, as one CUDA graph; see

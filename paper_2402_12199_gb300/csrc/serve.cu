@@ -578,8 +578,10 @@ rb_status rb_submit(rb_server* sv, const rb_system_desc* desc, const float* pos,
     if (precision != RB_FP32 && precision != RB_BF16 && precision != RB_F16X3)
         return fail(RB_EINVAL, "unknown precision");
     if (n_steps < 0 || !(dt > 0.f)) return fail(RB_EINVAL, "n_steps >= 0 and dt > 0 required");
-    const int64_t fp = rb_system_footprint(desc);
-    if (fp < 0) return fail(RB_EINVAL, "invalid system description");
+    // the system and the server's two state backups of it (one per tick in flight)
+    const int64_t fp_sys = rb_system_footprint(desc);
+    if (fp_sys < 0) return fail(RB_EINVAL, "invalid system description");
+    const int64_t fp = fp_sys + 2 * 4 * (int64_t)sizeof(float4) * desc->n_bodies;
     if ((size_t)fp > sv->budget) return fail(RB_ENOMEM, "request larger than the whole memory budget");
     auto r = std::make_unique<Request>();
     r->desc = *desc;
