@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--serving-steps", type=int, default=1000)
     ap.add_argument("--serving-nmax", type=int, default=65536)
     ap.add_argument("--skin", type=float, default=0.4)
+    ap.add_argument("--large-system", type=int, default=524288,
+                    help="bodies of the larger system the BF16 kernel is also timed on (0: skip)")
     ap.add_argument("--drift-steps", type=int, default=10000)
     ap.add_argument("--drift-every", type=int, default=500)
     return ap.parse_args()
@@ -812,6 +814,36 @@ def main():
                             "peak_gops": unit["tanh_gops"], "frac": mufu / 1e9 / unit["tanh_gops"],
                             "note": "one tanh.approx per SiLU evaluation (silu' from the same "
                                     "tanh); peak = measured tanh.approx rate"}}
+        # context: the same kernel and network on a system 16 times larger, where
+        # the tiles fill the 304 pipelines evenly (at 98304 pairs 768 tiles take 3
+        # rounds for 2.53 rounds of work)
+        if world == 1 and args.large_system > 0:
+            nb = args.large_system
+            st_big, L_big = inputs_mod.system_state(nb, PHI, KT, SEED + 21, 125.0, [500.0] * 3,
+                                                    "cube")
+            sb = api.System(nb, [L_big] * 3, "cube", skin=args.skin)
+            sb.set_state(*(torch.from_numpy(st_big[k]).cuda()
+                           for k in ("pos", "quat", "vel", "angmom")))
+            np_big = sb.build_pairs()
+            for _ in range(3):
+                sb.eval_pairs(api.RB_PATH_NN, mlp, "bf16")
+            durs = []
+            for _ in range(10):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sb.eval_pairs(api.RB_PATH_NN, mlp, "bf16")
+                b.record(stream)
+                durs.append((a, b))
+            torch.cuda.synchronize()
+            sb.sync()
+            d_big = statistics.mean(a.elapsed_time(b) for a, b in durs)
+            t_big = nn_flops_per_pair(WIDTH, DEPTH) * np_big / (d_big * 1e-3) / 1e12
+            roof_nn["large_system"] = {
+                "bodies": nb, "pairs": np_big, "kernel_ms": d_big, "achieved": t_big,
+                "frac": t_big / burst, "note": "context, not the headline: the same network "
+                "and kernel on a larger system of the same density"}
+            del sb
 
     def kernel_ms(s, prec):
         s.build_pairs()
