@@ -243,3 +243,53 @@ def test_networks_per_body_shape():
         api.Server(1 << 30, 2, m_cube).set_network("custom", api.MLP(128, 3))
     with pytest.raises(api.RBError):
         api.Server(1 << 30, 2, m_cube).set_network("cube", m_cube, rho_min=-1.0)
+
+
+def test_network_that_fails_mid_run_rolls_back_to_the_tick():
+    """A network that is exactly zero while every pair is farther than
+    rho_thr and overflows to infinity as soon as one comes closer: two cubes
+    coasting towards each other cross rho_thr in the third tick of four steps.
+    The replica is rolled back to that tick's start (with the next tick
+    already queued, which is voided) and continues on the bead path; both
+    force fields are exactly zero at these distances, so it ends bit for bit
+    where the bead path alone ends."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    W, D, n_in = 128, 3, 10
+    flat = np.zeros(2 * n_in + W * n_in + W + (D - 1) * (W * W + W) + W + 1 + 2, np.float32)
+    flat[n_in:2 * n_in] = 1.0                      # inv_sd: raw features
+    W1, b1 = 2 * n_in, 2 * n_in + W * n_in
+    W2 = b1 + W
+    W3 = W2 + W * W + W
+    wo = W3 + W * W + W
+    a, rho_thr = 1e25, 9.1
+    flat[W1 + 7] = -a                              # unit 0 of layer 1 reads rho (feature 7)
+    flat[b1] = a * rho_thr                         # z = a (rho_thr - rho)
+    flat[W2] = 1e25                                # overflows once z > 0
+    flat[W3] = 1.0
+    flat[wo] = 1.0
+    flat[-2] = 1.0                                 # e_scale
+    m = api.MLP(W, D)
+    m.set_params(flat)
+    L = 40.0
+    st = {"pos": np.array([[10.0, 20.0, 20.0, 0.0], [19.3, 20.0, 20.0, 0.0]], np.float32),
+          "quat": np.array([[1.0, 0.0, 0.0, 0.0]] * 2, np.float32),
+          "vel": np.array([[5.0, 0.0, 0.0, 0.0], [-5.0, 0.0, 0.0, 0.0]], np.float32),
+          "angmom": np.zeros((2, 4), np.float32)}
+    srv = api.Server(1 << 30, 2, m, steps_per_tick=4)
+    t = srv.submit(st, [L] * 3, "cube", api.RB_PATH_NN, "bf16", 24)
+    r = srv.wait(t)
+    fin = srv.fetch_state(t)
+    srv.close()
+    assert r["status"] == 0 and r["steps_done"] == 24 and r["fell_back"] == 1, r
+    keys = ("pos", "quat", "vel", "angmom")
+    s = api.System(2, [L] * 3, "cube")
+    s.set_state(*(torch.from_numpy(st[k]).cuda() for k in keys))
+    s.step(24, 0.002, path=api.RB_PATH_BEADS)
+    ref = s.get_state(to_host=True)
+    for k in keys:
+        assert np.array_equal(np.asarray(ref[k]), fin[k]), k
+    # the separation did cross rho_thr (9.3 - 24 x 0.02 = 8.82)
+    assert fin["pos"][1, 0] - fin["pos"][0, 0] < rho_thr
