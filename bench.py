@@ -51,7 +51,7 @@ WIDTH, DEPTH = 128, 3
 #                   --descriptor-comparison 0
 # None marks a kernel not captured since it last changed.
 NCU_DRAM_BYTES = {"k_bead_pairs": 1.869e6, "k_nn_f32": 2.185e6, "k_nn_tc2p": 2.051e6,
-                  "k_nn_tc256": None, "k_nn_f16x3": 2.213e6}
+                  "k_nn_tc256": 2.475e6, "k_nn_f16x3": 2.213e6}
 # The MD step's HBM-side kernels from the same captures (median launch, no
 # list rebuild due): DRAM bytes read + written and the ncu duration (cold L2,
 # serialised: the events inside the captured step graph cannot time single
@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--cpu-sample-pairs", type=int, default=100000)
     ap.add_argument("--ref-sample-pairs", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--train-steps", type=int, default=40000)
     ap.add_argument("--train-samples", type=int, default=1000000)
     ap.add_argument("--train-lr", type=float, default=3e-3)
     ap.add_argument("--train-f-scale", type=float, default=2.0)
