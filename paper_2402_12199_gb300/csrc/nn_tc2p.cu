@@ -113,7 +113,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             bulk_g2s(smem_u32(sm + o), src + o, n, wbar);
         }
     }
+    // the point group's table (the cube's 48 entries, or 3 per rotation of
+    // another group) in shared memory: the canonicalisation of every pair reads it
+    __shared__ float4 s_sym[72];
     {
+        const int n_tab = src.n_sym > 0 ? (src.sym_cube ? 48 : 3 * src.n_sym) : 0;
+        for (int t = tid; t < n_tab && t < 72; t += kThreads) s_sym[t] = src.sym[t];
         for (int t = tid; t < D * kW; t += kThreads)  // half biases: silu2 works on z / 2
             hbias[t] = 0.5f * flat[fl.b_(1 + t / kW, kW) + t % kW];
         for (int t = tid; t < kW; t += kThreads) wo[t] = flat[fl.wo + t];
@@ -189,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     auto seg_src = [&](int sg) {
         PairSrc r = src;
+        r.sym = s_sym;
         if constexpr (BATCH) {
             const PairSeg& q = segs[sg];
             r.pairs = q.pairs;
