@@ -121,6 +121,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + Ly.s_bar + 16);
     const uint32_t s_base = smem_u32(sm);
 
+    // the point group's table (the cube's 48 entries, or 3 per rotation of
+    // another group) in shared memory: the canonicalisation of every pair reads it
+    __shared__ float4 s_sym[72];
+    {
+        const int n_tab = src.n_sym > 0 ? (src.sym_cube ? 48 : 3 * src.n_sym) : 0;
+        for (int t = tid; t < n_tab && t < 72; t += kThreads) s_sym[t] = src.sym[t];
+    }
     {
         uint4* xz = reinterpret_cast<uint4*>(sm + Ly.s_x);
         for (uint32_t t = tid; t < (kM * kK1 * 2) / 16; t += kThreads) xz[t] = make_uint4(0, 0, 0, 0);
@@ -217,6 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t gp = tile * kM + row;
         bool valid = gp < n_total;
         PairSrc sr = src;
+        sr.sym = s_sym;
         PairDst dr = dst;
         if constexpr (BATCH) {
             int lo = 0, hi = n_seg - 1;
