@@ -1202,7 +1202,14 @@ def main():
         drift = {"steps": args.drift_steps, "dt": DT, "sample_every": args.drift_every,
                  "measure": "max_t |E_tot(t) - E_tot(0)| / (N kT) and the least-squares slope "
                             "per 1000 steps; E_tot = E_pot + KE_trans + KE_rot in FP64"}
-        for p in paths:
+        # the last entry: the BF16 network i<->j-symmetrised (each pair's energy
+        # averaged over both reference bodies, whose canonical-choice
+        # boundaries lie elsewhere)
+        drift_runs = list(paths) + (["nn_bf16_pair_symmetrised"] if "nn_bf16" in paths else [])
+        for p in drift_runs:
+            sym = p.endswith("_pair_symmetrised")
+            p = "nn_bf16" if sym else p
+            mlp.set_pair_symmetrised(sym)
             s = api.System(N_BODIES, [L] * 3, "cube", skin=args.skin)
             s.set_state(*(dev_state[k] for k in ("pos", "quat", "vel", "angmom")))
             if p.startswith("nn"):
@@ -1226,13 +1233,15 @@ def main():
             e = np.array(e_series)
             dev = np.abs(e - e[0]) / (N_BODIES * KT)
             finite = bool(np.all(np.isfinite(e)))
-            drift[p] = {"max_abs_drift_per_body_kT": float(dev.max()) if finite else None,
+            drift[p + ("_pair_symmetrised" if sym else "")] = {
+                        "max_abs_drift_per_body_kT": float(dev.max()) if finite else None,
                         "slope_per_body_kT_per_1k_steps":
                             float(np.polyfit(np.array(t_series) / 1000.0, e / (N_BODIES * KT), 1)[0])
                             if finite else None,
                         "E0_per_body_kT": float(e[0] / (N_BODIES * KT)) if finite else None,
                         "finite": finite, "steps_done": done, "error": err}
             del s
+        mlp.set_pair_symmetrised(False)
 
     # ---- end to end through the public API with host buffers, on the
     # headline path: a client that keeps the whole velocity-Verlet state in
