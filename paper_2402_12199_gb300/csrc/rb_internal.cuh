@@ -404,13 +404,14 @@ struct BatchTables {
 };
 rb_status batch_tables_alloc(BatchTables* t);
 void batch_tables_free(BatchTables* t);
-// Checks that every member can be batched (NVE, no bead fallback, at most
-// kMaxSeg members, all on one device), writes the tables (synchronously: no
-// step of an earlier batch on them may be in flight) and captures the step as
-// one CUDA graph.  The network's images are prepared here (outside capture).
-// The members' forces must be valid for their paths.
+// Checks that every member can be batched (NVE, at most kMaxSeg members, all
+// on one device), queues the tables' upload on `stream` (the stream the batch
+// will step on, so that its steps see them; no step of an earlier batch on
+// these tables may still be queued) and captures the step as one CUDA graph.
+// The network's images are prepared here (outside capture).  The members'
+// forces must be valid for their paths.
 rb_status batch_create(const std::vector<BatchMember>& members, const BatchTables& tables,
-                       StepBatch** out);
+                       cudaStream_t stream, StepBatch** out);
 // n_steps MD steps of every member, on `stream`; each member's step counter advances.
 rb_status batch_step(StepBatch* b, cudaStream_t stream);
 void batch_destroy(StepBatch* b);

@@ -216,7 +216,7 @@ static rb_status ensure_batch(Lane* sv, const std::vector<Request*>& act) {
     for (Request* r : act)
         mem.push_back({r->sys, r->path, r->precision, r->dt, r->path == RB_PATH_NN ? r->mlp : nullptr});
     StepBatch* b = nullptr;
-    RB_TRY(batch_create(mem, sv->tables[set], &b));
+    RB_TRY(batch_create(mem, sv->tables[set], sv->stream, &b));
     if (sv->batch) {
         if (batch_in_flight(sv, sv->batch))
             sv->retired.push_back(sv->batch);

@@ -1040,7 +1040,7 @@ static PairSeg pair_seg(const rb_system* s, bool fb) {
 }
 
 rb_status batch_create(const std::vector<BatchMember>& members, const BatchTables& tables,
-                       StepBatch** out) {
+                       cudaStream_t stream, StepBatch** out) {
     *out = nullptr;
     if (!tables.step || !tables.pair || !tables.start) return fail(RB_EINVAL, "batch tables not allocated");
     const int n = (int)members.size();
@@ -1165,13 +1165,16 @@ rb_status batch_create(const std::vector<BatchMember>& members, const BatchTable
     }
 
     rb_status st = RB_OK;
+    // stream-ordered before the batch's first step on `stream` (pageable
+    // sources: staged before each call returns, so the vectors may go)
     auto upload = [&]() -> rb_status {
-        RB_CUDA(cudaMemcpy(tables.step, seg.data(), sizeof(StepSeg) * n, cudaMemcpyHostToDevice));
-        RB_CUDA(cudaMemcpy(tables.start, start.data(), sizeof(int) * start.size(),
-                           cudaMemcpyHostToDevice));
+        RB_CUDA(cudaMemcpyAsync(tables.step, seg.data(), sizeof(StepSeg) * n,
+                                cudaMemcpyHostToDevice, stream));
+        RB_CUDA(cudaMemcpyAsync(tables.start, start.data(), sizeof(int) * start.size(),
+                                cudaMemcpyHostToDevice, stream));
         if (!pseg.empty())
-            RB_CUDA(cudaMemcpy(tables.pair, pseg.data(), sizeof(PairSeg) * pseg.size(),
-                               cudaMemcpyHostToDevice));
+            RB_CUDA(cudaMemcpyAsync(tables.pair, pseg.data(), sizeof(PairSeg) * pseg.size(),
+                                    cudaMemcpyHostToDevice, stream));
         return RB_OK;
     };
     st = upload();
