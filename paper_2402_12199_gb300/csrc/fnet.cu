@@ -43,6 +43,7 @@ struct rb_fnet {
     float* params = nullptr;  // 5 networks, flat FP32 (device), the ABI layout
     float* img = nullptr;     // 5 networks, kernel image (device)
     uint64_t version = 1;
+    std::atomic<uint64_t> ready_version{0};  // the version other streams have waited for
 };
 
 struct rb_fnet_trainer {
@@ -327,6 +328,16 @@ rb_status check_fnet(const rb_fnet* f) {
 }
 
 uint64_t fnet_version(const rb_fnet* f) { return f->version; }
+
+rb_status fnet_ready(const rb_fnet* cf) {
+    // the parameters and the kernel image are written on the network's stream;
+    // the system's stream reads them, so it waits for that stream once per change
+    rb_fnet* f = const_cast<rb_fnet*>(cf);
+    if (f->ready_version.load() == f->version) return RB_OK;
+    RB_CUDA(cudaStreamSynchronize(f->stream));
+    f->ready_version.store(f->version);
+    return RB_OK;
+}
 
 rb_status fnet_pairs_system_async(rb_system* s, const rb_fnet* f) {
     RB_TRY(check_fnet(f));

@@ -471,8 +471,17 @@ rb_status mlp_refresh(rb_mlp* m) {
 }
 
 rb_status ensure_images(const rb_mlp* cm, int precision) {
-    if (precision != RB_BF16 && precision != RB_F16X3) return RB_OK;
     rb_mlp* m = const_cast<rb_mlp*>(cm);  // the images are a cache of the parameters
+    if (precision != RB_BF16 && precision != RB_F16X3) {
+        // FP32: the kernels read the parameters and the FP32 image as written
+        // on the network's stream; other streams wait for it once per change
+        if (m->f32_seen_version.load() == m->version) return RB_OK;
+        std::lock_guard<std::mutex> lock(m->img_mu);
+        if (m->f32_seen_version.load() == m->version) return RB_OK;
+        RB_CUDA(cudaStreamSynchronize(m->stream));
+        m->f32_seen_version.store(m->version);
+        return RB_OK;
+    }
     std::atomic<uint64_t>& built = precision == RB_BF16 ? m->tc_img_version : m->f16x3_img_version;
     if (built.load() == m->version) return RB_OK;
     std::lock_guard<std::mutex> lock(m->img_mu);

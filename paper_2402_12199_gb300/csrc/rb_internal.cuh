@@ -190,6 +190,7 @@ struct rb_mlp {
     // the version the BF16 and F16X3 images were built for: they are built when
     // a kernel of that precision first runs after a change (ensure_images)
     std::atomic<uint64_t> tc_img_version{0}, f16x3_img_version{0};
+    std::atomic<uint64_t> f32_seen_version{0};  // parameters and FP32 image waited for
     std::mutex img_mu;
     // point group of the bodies (symmetry-reduced configurations): device
     // table of 3 float4 per rotation (see canon_config), n_sym = 0: none
@@ -309,6 +310,7 @@ rb_status ensure_pair_sym_arrays(rb_system* s, const rb_mlp* m);
 rb_status fnet_pairs_system_async(rb_system* s, const rb_fnet* f);
 rb_status check_fnet(const rb_fnet* f);
 uint64_t fnet_version(const rb_fnet* f);  // bumped whenever its parameters change
+rb_status fnet_ready(const rb_fnet* f);    // waits (outside any capture) for a change to land
 // train.cu: fixed-order GEMM C = beta C + alpha A B with strided operands
 // (A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn], C row-major), the
 // fixed-order column sum and Adam, shared with the per-component trainer

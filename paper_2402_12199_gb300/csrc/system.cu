@@ -1849,6 +1849,7 @@ static rb_status step_impl(rb_system* s, int32_t path, const void* m, uint64_t v
         RB_TRY(ensure_pair_sym_arrays(s, static_cast<const rb_mlp*>(m)));
         RB_TRY(ensure_images(static_cast<const rb_mlp*>(m), precision));
     }
+    if (path == RB_PATH_FNET) RB_TRY(fnet_ready(static_cast<const rb_fnet*>(m)));
     const bool same = s->forces_valid && s->forces_path == path && s->forces_mlp == m &&
                       s->forces_precision == precision &&
                       (!m || s->forces_mlp_version == version);
@@ -1940,6 +1941,7 @@ rb_status rb_forces_fnet(rb_system* s, const rb_fnet* f, float* force, float* to
                          double* virial9) {
     if (!s) return fail(RB_EINVAL, "null system");
     RB_TRY(check_fnet(f));
+    RB_TRY(fnet_ready(f));
     RB_TRY(build_pairs_async(s, false, false));
     RB_TRY(fnet_pairs_system_async(s, f));
     RB_TRY(reduce_forces_async(s, 0.f));
