@@ -126,7 +126,7 @@ def combine_ranks(ms_step: float, units: float, device=None):
 
 def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=5,
                 rate_factor=8.0, budget_bytes=2 << 30, slots=8, solo_rates=None, lanes=None,
-                cyl_mlp=None, rho=(0.0, 0.0)):
+                cyl_mlp=None, rho=(0.0, 0.0), alone_steps=100):
     """Serving workload: cube/cylinder replicas with N log-uniform in
     [512, n_max], phi in [0.05, 0.25], kT in [0.5, 1.5], `steps` MD steps each,
     Poisson arrivals at rate_factor / (solo run time of the first request), so
@@ -136,7 +136,9 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     large system alone, {"nn": ..., "nn_cyl": ..., "beads": ...}; the mix's
     reference rate then weights them by each path's share of the pairs
     evaluated.  rho: the bead-fallback radii of the cube and the cylinder
-    network (0: none)."""
+    network (0: none).  alone_steps (0: skip): each request is also run alone
+    on a fresh server for that many steps, one resident at a time, and its
+    median step time in the mix is compared with its median step time alone."""
     import time as _t
 
     rng = np.random.default_rng(seed)
@@ -186,6 +188,28 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
     sat = srv.stats()
     srv.close()
     ok = sum(r["status"] == 0 for r in res)
+    alone = None
+    if alone_steps > 0:
+        srv = make_server(api, budget_bytes, slots, mlp, cyl_mlp, lanes, rho)
+        solo_ms = []
+        for st, L, shape, path in reqs:
+            r = srv.wait(srv.submit(st, [L] * 3, shape, path, "bf16", alone_steps, skin=0.4))
+            solo_ms.append(r["step_ms_p50"] if r["status"] == 0 and r["steps_done"] > 0 else None)
+        srv.close()
+        both = [(m["step_ms_p50"], a) for m, a in zip(res, solo_ms)
+                if a and m["status"] == 0 and m["steps_done"] > 0]
+        ratio = np.array([m / a for m, a in both])
+        a_ms = np.array([a for _, a in both])
+        alone = {"requests": len(both), "steps_each": alone_steps,
+                 "slowdown_p50": float(np.percentile(ratio, 50)),
+                 "slowdown_p99": float(np.percentile(ratio, 99)),
+                 "alone_step_ms_p50": float(np.percentile(a_ms, 50)),
+                 "alone_step_ms_p99": float(np.percentile(a_ms, 99)),
+                 "note": "each request alone on the server (one resident at a time): slowdown = "
+                         "its median step time in the mix / its median step time alone; "
+                         "alone_step_ms: the spread of the requests' own step times (every "
+                         "request runs the same number of steps), the p99/p50 the size mix "
+                         "has with no sharing at all"}
 
     def path_key(shape, path, r):
         if path == api.RB_PATH_NN and not r["fell_back"]:
@@ -206,12 +230,14 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
             if r["pairs"] > 0 and solo_rates.get(key):
                 slow.append(r["step_ms_p50"] / (1e3 * r["pairs"] / solo_rates[key]))
         mix = {"pairs_by_path": by_path, "solo_rates": solo_rates, "reference_rate": ref,
-               "slowdown_p50": float(np.percentile(slow, 50)) if slow else None,
-               "slowdown_p99": float(np.percentile(slow, 99)) if slow else None,
-               "slowdown_note": "per request: median step time / (its pairs at its path's solo "
-                                "rate); the step time of a request grows with its size (N spans "
-                                "a factor 128), so step_ms_p99 / step_ms_p50 is dominated by "
-                                "the size mix; this ratio measures the cost of sharing the GPU",
+               "pair_rate_slowdown_p50": float(np.percentile(slow, 50)) if slow else None,
+               "pair_rate_slowdown_p99": float(np.percentile(slow, 99)) if slow else None,
+               "pair_rate_slowdown_note": "per request: median step time / (its pairs at its "
+                                          "path's rate on one large system); a small replica's "
+                                          "step has a fixed floor (its launches and list "
+                                          "kernels) that this ignores, so it is large for small "
+                                          "replicas: latency_vs_alone compares with each "
+                                          "request's own step time alone",
                "efficiency_poisson": stats["pair_evals"] / makespan / ref,
                "efficiency_saturated": sat["pair_evals"] / sat_span / ref,
                "note": "reference_rate: the same pairs at each path's rate on one large system "
@@ -228,7 +254,7 @@ def serving_run(api, inputs, mlp, n_requests=256, steps=1000, n_max=65536, seed=
                            f"(cylinders) sigma take the bead sum" if max(rho) > 0 else ""),
             "makespan_s": makespan, "pair_evals_per_s": stats["pair_evals"] / makespan,
             "step_ms_p50": stats["step_ms_p50"], "step_ms_p99": stats["step_ms_p99"],
-            "mix_reference": mix,
+            "mix_reference": mix, "latency_vs_alone": alone,
             "saturated": {"note": "all requests submitted at once: the server's capacity",
                           "makespan_s": sat_span, "pair_evals_per_s": sat["pair_evals"] / sat_span,
                           "step_ms_p50": sat["step_ms_p50"], "step_ms_p99": sat["step_ms_p99"]},
@@ -1424,7 +1450,8 @@ def main():
                             cyl_mlp=cyl_net, rho=(rho_fallback, cyl_rho))
         serving["small_replicas"] = {k: small[k] for k in
                                      ("workload", "makespan_s", "pair_evals_per_s", "step_ms_p50",
-                                      "step_ms_p99", "peak_resident", "completed_ok", "saturated")}
+                                      "step_ms_p99", "peak_resident", "completed_ok", "saturated",
+                                      "latency_vs_alone")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
