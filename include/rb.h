@@ -52,7 +52,7 @@ typedef enum rb_status {
     RB_ETIMEOUT = 6,   /* serving: rb_wait gave up */
     RB_EFAULT = 7,     /* non-finite forces or energies detected */
     RB_EBUSY = 8,      /* serving: no slot or memory for the request now */
-    RB_ENOTSUP = 9     /* combination not supported by this build */
+    RB_ENOTSUP = 9     /* combination the library does not support */
 } rb_status;
 
 enum { RB_SHAPE_CUBE = 0, RB_SHAPE_CYLINDER = 1, RB_SHAPE_CUSTOM = 2 };
