@@ -199,3 +199,36 @@ def test_fnet_md_conserves_momentum():
     assert np.all(np.isfinite(cur["pos"]))
     scale = np.abs(cur["vel"][:, :3]).sum() * s.mass
     assert np.abs(p1 - p0).max() < 1e-5 * scale
+
+
+def test_parameter_change_on_the_network_stream_reaches_the_system():
+    """The per-component networks' parameters and kernel image are written on
+    their own stream; a system on another stream that evaluates right after a
+    change sees the new values (the network's stream is held busy by a bounded
+    spin before each device-to-device parameter copy)."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    width, depth = 32, 3
+    sets = [torch.from_numpy(_flat(width, depth, seed)).cuda() for seed in (41, 42)]
+    st, L, tmpl = make_state(400, 0.15, 32, "cylinder")
+    s = gpu_system(st, L, "cylinder")
+    ref = []
+    for flat in sets:
+        f0 = api.FNet(width, depth)
+        f0.set_params(flat)
+        r = s.forces_fnet(f0)
+        s.sync()
+        ref.append((r["force"].clone(), r["torque"].clone()))
+    assert not torch.equal(ref[0][0], ref[1][0])
+    ns = torch.cuda.Stream()
+    f = api.FNet(width, depth, stream=ns)
+    for k in range(4):
+        with torch.cuda.stream(ns):
+            torch.cuda._sleep(2_000_000)  # about 1 ms of the network's stream
+        f.set_params(sets[k % 2])
+        r = s.forces_fnet(f)
+        s.sync()
+        assert torch.equal(r["force"], ref[k % 2][0]), k
+        assert torch.equal(r["torque"], ref[k % 2][1]), k

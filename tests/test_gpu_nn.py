@@ -156,3 +156,37 @@ def test_bead_fallback_for_close_pairs():
     Fn, Tn, _, _, _ = oracle_nn(st, L, tmpl, flat, 128, pairs=pairs[~close])
     assert_parity(r["force"][:, :3].double().cpu().numpy(), Fb + Fn, TOL_F32)
     assert_parity(r["torque"][:, :3].double().cpu().numpy(), Tb + Tn, TOL_F32)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_parameter_change_on_the_network_stream_reaches_the_system(precision):
+    """A network's parameters (and its kernel images) are written on the
+    network's own stream; a system on another stream that evaluates right after
+    the change must see the new values.  The network's stream is held busy by a
+    bounded spin before each device-to-device parameter copy, so a system that
+    did not wait for it would read the previous parameters."""
+    import torch
+
+    from paper_2402_12199_gb300 import api
+
+    st, L, tmpl = make_state(512, 0.2, 6)
+    sets = [torch.from_numpy(params(128, seed)).cuda() for seed in (11, 12)]
+    s = gpu_system(st, L)
+    ref = []
+    for flat in sets:  # each set on a fresh network on the system's own stream
+        m0 = api.MLP(128, 3)
+        m0.set_params(flat)
+        r = s.forces_nn(m0, precision)
+        s.sync()
+        ref.append((r["force"].clone(), r["torque"].clone()))
+    assert not torch.equal(ref[0][0], ref[1][0])
+    ns = torch.cuda.Stream()
+    m = api.MLP(128, 3, stream=ns)
+    for k in range(4):
+        with torch.cuda.stream(ns):
+            torch.cuda._sleep(2_000_000)  # about 1 ms of the network's stream
+        m.set_params(sets[k % 2])
+        r = s.forces_nn(m, precision)
+        s.sync()
+        assert torch.equal(r["force"], ref[k % 2][0]), k
+        assert torch.equal(r["torque"], ref[k % 2][1]), k
