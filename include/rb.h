@@ -346,6 +346,12 @@ rb_status rb_forces_beads_noalloc(int32_t shape, int64_t n_bodies, const float* 
 int64_t rb_mlp_n_params(int32_t width, int32_t depth);
 rb_status rb_mlp_create(int32_t width, int32_t depth, void* cuda_stream, rb_mlp** out);
 rb_status rb_mlp_destroy(rb_mlp* mlp);
+/* rb_mlp_set_params / _get_params: n = rb_mlp_n_params (RB_EINVAL otherwise);
+ * flat on the host or the device (flag).  Both are queued on the network's
+ * stream; a copy from or to the host synchronises, a device array must stay
+ * valid until the stream has read it.  A change is ordered before every later evaluation of the network
+ * on any stream: a system, a batch or a server lane waits once for the
+ * network's stream on its first evaluation after the change. */
 rb_status rb_mlp_set_params(rb_mlp* mlp, const float* flat, int64_t n, int32_t from_host);
 rb_status rb_mlp_get_params(const rb_mlp* mlp, float* flat, int64_t n, int32_t to_host);
 
@@ -692,7 +698,9 @@ rb_status rb_peak_probe(int32_t kind, int32_t blocks_per_sm, int64_t iters, void
  * rb_fnet_create: width 16, 32 or 64 (else RB_ENOTSUP), depth 1..8 (else
  *   RB_EINVAL); parameters start at zero; all work goes to `stream`.
  * rb_fnet_set_params / _get_params: n = rb_fnet_n_params; host or device
- *   array (flag); a host copy synchronises.
+ *   array (flag); a host copy synchronises.  A change is ordered before every
+ *   later evaluation on any stream (a system waits once for the network's
+ *   stream on its first evaluation after the change).
  * rb_fnet_pairs: n explicit pairs, cfg = (s, 0), (q_rel) as 2 float4 per
  *   pair (device); out = (F_j, 0), (tau_i, 0), (tau_j, 0) as 3 float4 per pair
  *   in body i's frame (device).  Asynchronous.

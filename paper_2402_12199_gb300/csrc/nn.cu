@@ -614,6 +614,8 @@ rb_status rb_mlp_set_params(rb_mlp* m, const float* flat, int64_t n, int32_t fro
     RB_CUDA(cudaMemcpyAsync(m->params, flat, sizeof(float) * n,
                             from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             m->stream));
+    // a page-locked host array is read asynchronously: the caller may free it on return
+    if (from_host) RB_CUDA(cudaStreamSynchronize(m->stream));
     return mlp_refresh(m);
 }
 
