@@ -137,7 +137,10 @@ rb_status rb_body_info(const rb_system* sys, float* mass_host, float* inertia3_h
 rb_status rb_body_template(const rb_system* sys, float* xyz_host);
 
 /* Copy the state in (float4 rows, see above).  from_host != 0: the pointers
- * are host memory.  Invalidates cached forces (rb_set_forces gives them back).
+ * are host memory (pageable or page-locked), and the call returns after the
+ * copies completed, so the caller may reuse it; from_host = 0: device
+ * pointers, the copies queued on the system's stream.  Invalidates cached
+ * forces (rb_set_forces gives them back).
  * When the four arrays are one
  * contiguous block (quat = pos + 4N floats, vel = pos + 8N, angmom =
  * pos + 12N) they move in a single copy (the same holds for rb_get_state). */
@@ -165,7 +168,8 @@ rb_status rb_get_forces(const rb_system* sys, float* force, float* torque, int32
  * and the forces at the current centres) and feeds it back every step.  The
  * caller vouches that the rows are that path's forces at the current state:
  * nothing checks it.  force, torque: N float4 rows each, device pointers, or
- * host pointers with from_host != 0; both required.  RB_EINVAL on a null
+ * host pointers with from_host != 0 (the call then returns after the copies
+ * completed, as rb_set_state); both required.  RB_EINVAL on a null
  * argument or an unknown path or precision. */
 rb_status rb_set_forces(rb_system* sys, int32_t path, const rb_mlp* mlp, int32_t precision,
                         const float* force, const float* torque, int32_t from_host);

@@ -1635,6 +1635,8 @@ rb_status rb_set_state(rb_system* s, const float* pos, const float* quat, const 
         if (vel) RB_CUDA(cudaMemcpyAsync(s->vel, vel, b, k, s->stream));
         if (angmom) RB_CUDA(cudaMemcpyAsync(s->angmom, angmom, b, k, s->stream));
     }
+    // a page-locked host source is read asynchronously: the caller may reuse it on return
+    if (from_host) RB_CUDA(cudaStreamSynchronize(s->stream));
     return state_replaced(s, pos != nullptr, vel || angmom);
 }
 
@@ -1733,6 +1735,7 @@ rb_status rb_set_forces(rb_system* s, int32_t path, const rb_mlp* m, int32_t pre
     const cudaMemcpyKind k = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     RB_CUDA(cudaMemcpyAsync(s->force, force, b, k, s->stream));
     RB_CUDA(cudaMemcpyAsync(s->torque, torque, b, k, s->stream));
+    if (from_host) RB_CUDA(cudaStreamSynchronize(s->stream));  // as rb_set_state
     return forces_given(s, path, m, precision);
 }
 
